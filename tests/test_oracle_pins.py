@@ -1,0 +1,351 @@
+"""Pins of the CPU oracle against facts other than itself (CPU only).
+
+Each pin_* function returns the error it measures, so test_oracle_mutations
+can show that a planted mistake in the oracle breaks at least one of them.
+Sources of truth, none of which re-types an oracle formula:
+  - hand-derived closed form of a lossless two-bus line (derived from Eq. 1);
+  - Kirchhoff's current law on the physical branch model (ideal transformer
+    m e^{j phi} : 1 plus a pi section), independent of the admittance stamps;
+  - exact invariants: zero Ybus row sums without charging/taps, symmetry
+    without phase shift, rotation invariance and degree-2 homogeneity of S;
+  - complex-step derivatives of the real-form injections (every J entry);
+  - series-branch loss identity (P_hk + P_kh = r |I_s|^2, ...);
+  - long-double central differences of the loss (adjoint);
+  - the paper's printed element count (16 values per line, Sec. V-A.2).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gridcases import (blocks, circuit_currents, make_grid, random_grid, random_state, relerr, series,
+                       three_bus_plus, two_bus_lossless)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TOL = 1e-13
+
+
+# ---------------------------------------------------------------- pins ----
+
+def pin_two_bus():
+    """Closed form of the lossless line x = 0.1 (y_s = -j10), V1 = 1, V2 = 1 at -0.1 rad.
+    With d = th1 - th2:  P1 = 10 v1 v2 sin d,  Q1 = 10 v1^2 - 10 v1 v2 cos d,
+                         P2 = -10 v1 v2 sin d, Q2 = 10 v2^2 - 10 v1 v2 cos d."""
+    gr = two_bus_lossless()
+    vm, va = np.array([1.0, 1.0]), np.array([0.0, -0.1])
+    s, c = math.sin(0.1), math.cos(0.1)
+    P_ref = np.array([10 * s, -10 * s])
+    Q_ref = np.array([10 * (1 - c), 10 * (1 - c)])
+    # rows (P1, P2, Q1, Q2) x columns (th1, th2, v1, v2)
+    Jd = np.array([
+        [10 * c, -10 * c, 10 * s, 10 * s],
+        [-10 * c, 10 * c, -10 * s, -10 * s],
+        [10 * s, -10 * s, 20 - 10 * c, -10 * c],
+        [10 * s, -10 * s, -10 * c, 20 - 10 * c],
+    ])
+    Y = oracle.ybus(gr)
+    jrp, jci = oracle.jac_pattern(Y)
+    errs = []
+    P, Q = oracle.inj_sparse(Y, vm, va)
+    errs += [np.max(np.abs(P - P_ref)), np.max(np.abs(Q - Q_ref))]
+    Pe, Qe, Je = oracle.elementwise(gr, vm, va, Y)
+    errs += [np.max(np.abs(Pe - P_ref)), np.max(np.abs(Qe - Q_ref))]
+    for J in (oracle.jac_ybus(Y, vm, va), oracle.jac_cstep(Y, vm, va), Je):
+        for r in range(4):
+            for e in range(jrp[r], jrp[r + 1]):
+                errs.append(abs(J[e] - Jd[r, jci[e]]))
+    Ydense = Y.dense()
+    errs.append(np.max(np.abs(Ydense - np.array([[-10j, 10j], [10j, -10j]]))))
+    return max(errs) / 10.0
+
+
+def pin_circuit_law(gr, seed=1):
+    """Ybus V equals the KCL bus currents of the physical model, and every
+    injection path equals V conj(I_KCL)."""
+    vm, va = random_state(gr["nb"], seed)
+    V, Ikcl = circuit_currents(gr, vm, va)
+    Y = oracle.ybus(gr)
+    Ivec = Y.dense() @ V if gr["nb"] <= 400 else None
+    S_ref = V * np.conj(Ikcl)
+    errs = []
+    if Ivec is not None:
+        errs.append(relerr(Ivec, Ikcl))
+    P, Q = oracle.inj_sparse(Y, vm, va)
+    errs += [relerr(P, S_ref.real), relerr(Q, S_ref.imag)]
+    Pe, Qe, _ = oracle.elementwise(gr, vm, va, Y, jac=False)
+    errs += [relerr(Pe, S_ref.real), relerr(Qe, S_ref.imag)]
+    if gr["nb"] <= 400:
+        Yre, Yim = oracle.ybus_dense(gr)
+        Pd, Qd = oracle.inj_dense(Yre, Yim, vm, va)
+        errs += [relerr(Pd, S_ref.real), relerr(Qd, S_ref.imag)]
+    return max(errs)
+
+
+def pin_jacobian_cstep(gr, seed=2):
+    vm, va = random_state(gr["nb"], seed)
+    Y = oracle.ybus(gr)
+    _, jci = oracle.jac_pattern(Y)
+    Ja, Jc = oracle.jac_ybus(Y, vm, va), oracle.jac_cstep(Y, vm, va)
+    return max(relerr(a, c) for a, c in zip(blocks(Ja, jci, gr["nb"], Y.nnz), blocks(Jc, jci, gr["nb"], Y.nnz)))
+
+
+def pin_invariants(gr, seed=3):
+    """Rotation invariance (theta columns of every row sum to 0) and degree-2
+    homogeneity (sum_j dS_i/dv_j v_j = 2 S_i), for both Jacobian paths."""
+    vm, va = random_state(gr["nb"], seed)
+    Y = oracle.ybus(gr)
+    nb, nnz = gr["nb"], Y.nnz
+    jrp, jci = oracle.jac_pattern(Y)
+    P, Q = oracle.inj_sparse(Y, vm, va)
+    errs = []
+    for J in (oracle.jac_ybus(Y, vm, va), oracle.elementwise(gr, vm, va, Y)[2]):
+        rot = np.zeros(2 * nb)
+        hom = np.zeros(2 * nb)
+        scale = 0.0
+        for r in range(2 * nb):
+            for e in range(jrp[r], jrp[r + 1]):
+                c = jci[e]
+                if c < nb:
+                    rot[r] += J[e]
+                else:
+                    hom[r] += J[e] * vm[c - nb]
+                scale = max(scale, abs(J[e]))
+        errs.append(np.max(np.abs(rot)) / scale)
+        S2 = 2 * np.concatenate([P, Q])
+        errs.append(relerr(hom, S2))
+    return max(errs)
+
+
+def pin_elementwise_equals_ybus(gr, seed=4, skip=None):
+    vm, va = random_state(gr["nb"], seed)
+    Y = oracle.ybus(gr, skip=skip)
+    _, jci = oracle.jac_pattern(Y)
+    P, Q = oracle.inj_sparse(Y, vm, va)
+    J = oracle.jac_ybus(Y, vm, va)
+    Pe, Qe, Je = oracle.elementwise(gr, vm, va, Y, skip=skip)
+    errs = [relerr(Pe, P), relerr(Qe, Q)]
+    errs += [relerr(a, b) for a, b in zip(blocks(Je, jci, gr["nb"], Y.nnz), blocks(J, jci, gr["nb"], Y.nnz))]
+    return max(errs)
+
+
+def pin_branch_loss(seed=5):
+    """One branch, m = 1, phi = 0: P_hk + P_kh = r |I_s|^2 and
+    Q_hk + Q_kh = x |I_s|^2 - (b_sh/2)(v_h^2 + v_k^2), I_s = y_s (V_h - V_k)."""
+    rng = np.random.default_rng(seed)
+    errs = []
+    for _ in range(20):
+        r, x, bsh = rng.uniform(0.001, 0.05), rng.uniform(0.01, 0.3), rng.uniform(0, 0.1)
+        g, b = series(r, x)
+        gr = make_grid(2, [(0, 1, g, b, bsh, 1.0, 0.0)])
+        vm, va = rng.uniform(0.9, 1.1, 2), rng.normal(0, 0.2, 2)
+        Y = oracle.ybus(gr)
+        V = vm * np.exp(1j * va)
+        Is = complex(g, b) * (V[0] - V[1])
+        for P, Q in (oracle.inj_sparse(Y, vm, va), oracle.elementwise(gr, vm, va, Y, jac=False)[:2]):
+            lossP = r * abs(Is) ** 2
+            lossQ = x * abs(Is) ** 2 - bsh / 2 * (vm[0] ** 2 + vm[1] ** 2)
+            errs.append(abs(P.sum() - lossP) / max(abs(P).max(), 1e-300))
+            errs.append(abs(Q.sum() - lossQ) / max(abs(Q).max(), 1e-300))
+    return max(errs)
+
+
+def _loss_case(nb=150, nl=210, seed=7):
+    gr = random_grid(nb, nl, seed, shift_max=0.2)
+    vm, va = random_state(nb, seed)
+    vm2, va2 = random_state(nb, seed, stream=1)
+    Y = oracle.ybus(gr)
+    Ps, Qs = oracle.inj_sparse(Y, vm2, va2)
+    rng = np.random.default_rng(seed)
+    wP, wQ = rng.uniform(0.5, 2, nb), rng.uniform(0.5, 2, nb)
+    return gr, Y, vm, va, Ps, Qs, wP, wQ
+
+
+def pin_adjoint(nb=150, nl=210, seed=7):
+    """J^T r and the complex-step parameter gradients against long-double
+    central differences (h = 1e-7) of the loss."""
+    gr, Y, vm, va, Ps, Qs, wP, wQ = _loss_case(nb, nl, seed)
+    P, Q = oracle.inj_sparse(Y, vm, va)
+    J = oracle.jac_ybus(Y, vm, va)
+    gva, gvm = oracle.adjoint_state(Y, J, P, Q, Ps, Qs, wP, wQ)
+    gg, gb, gbsh, gtap = oracle.adjoint_params_cstep(gr, Y, vm, va, Ps, Qs, wP, wQ)
+    kinds = np.concatenate([np.zeros(nb, int), np.ones(nb, int)] + [np.full(nl, k) for k in (2, 3, 4, 5)])
+    idxs = np.concatenate([np.arange(nb), np.arange(nb)] + [np.arange(nl)] * 4)
+    fd = oracle.loss_central_diff(gr, vm, va, Ps, Qs, wP, wQ, kinds, idxs, 1e-7)
+    ad = np.concatenate([gva, gvm, gg, gb, gbsh, gtap])
+    errs = []
+    off = 0
+    for n in (nb, nb, nl, nl, nl, nl):
+        errs.append(relerr(ad[off:off + n], fd[off:off + n]))
+        off += n
+    return max(errs)
+
+
+# --------------------------------------------------------------- tests ----
+
+def test_two_bus_closed_form():
+    assert pin_two_bus() < 1e-14
+
+
+@pytest.mark.parametrize("case", ["three_bus_plus", "random_shift", "random_plain"])
+def test_circuit_law(case):
+    gr = {"three_bus_plus": lambda: three_bus_plus(),
+          "random_shift": lambda: random_grid(300, 420, 11, shift_max=0.3),
+          "random_plain": lambda: random_grid(2000, 2700, 12)}[case]()
+    assert pin_circuit_law(gr) < TOL
+
+
+def test_row_sums_equal_shunts_without_charging_or_taps():
+    gr = random_grid(500, 700, 21)
+    gr["bsh"][:] = 0.0
+    gr["tap"][:] = 1.0
+    gr["shift"][:] = 0.0
+    Y = oracle.ybus(gr)
+    rows = np.add.reduceat(Y.yre + 1j * Y.yim, Y.rp[:-1])
+    ysh = gr["gs"] + 1j * gr["bs"]
+    scale = np.max(np.abs(Y.yre + 1j * Y.yim))
+    assert np.max(np.abs(rows - ysh)) / scale < 1e-14
+
+
+def test_symmetric_without_phase_shift():
+    gr = random_grid(500, 700, 22)
+    Yd = oracle.ybus(gr).dense()
+    assert np.array_equal(Yd, Yd.T)
+    gr2 = random_grid(300, 420, 23, shift_max=0.3)
+    Yd2 = oracle.ybus(gr2).dense()
+    assert not np.allclose(Yd2, Yd2.T)
+
+
+@pytest.mark.parametrize("case", ["three_bus_plus", "random_shift", "c1_like"])
+def test_jacobian_complex_step(case):
+    gr = {"three_bus_plus": lambda: three_bus_plus(),
+          "random_shift": lambda: random_grid(300, 420, 31, shift_max=0.3),
+          "c1_like": lambda: random_grid(2000, 2700, 32)}[case]()
+    assert pin_jacobian_cstep(gr) < TOL
+
+
+@pytest.mark.parametrize("case", ["three_bus_plus", "random_shift"])
+def test_jacobian_invariants(case):
+    gr = three_bus_plus() if case == "three_bus_plus" else random_grid(400, 560, 41, shift_max=0.3)
+    assert pin_invariants(gr) < TOL
+
+
+@pytest.mark.parametrize("case", ["two_bus", "three_bus_plus", "random_shift", "c1_like", "outage"])
+def test_elementwise_equals_ybus(case):
+    skip = None
+    if case == "two_bus":
+        gr = two_bus_lossless()
+    elif case == "three_bus_plus":
+        gr = three_bus_plus()
+    elif case == "random_shift":
+        gr = random_grid(300, 420, 51, shift_max=0.3)
+    elif case == "c1_like":
+        gr = random_grid(2000, 2700, 52)
+    else:
+        gr = three_bus_plus()
+        skip = np.array([0, 0, 0, 1], np.uint8)  # drop one of the parallel pair
+    assert pin_elementwise_equals_ybus(gr, skip=skip) < TOL
+
+
+def test_dense_equals_sparse():
+    gr = random_grid(300, 420, 61, shift_max=0.2)
+    vm, va = random_state(300, 61)
+    Y = oracle.ybus(gr)
+    P, Q = oracle.inj_sparse(Y, vm, va)
+    Yre, Yim = oracle.ybus_dense(gr)
+    Pd, Qd = oracle.inj_dense(Yre, Yim, vm, va)
+    assert relerr(P, Pd) < TOL and relerr(Q, Qd) < TOL
+    Yd = Y.dense()
+    assert np.max(np.abs(Yd - (Yre + 1j * Yim))) == 0.0
+
+
+def test_branch_loss_identity():
+    assert pin_branch_loss() < 1e-12
+
+
+def test_adjoint_against_central_differences():
+    assert pin_adjoint() < 1e-8
+
+
+def test_jacobian_pattern_layout():
+    gr = three_bus_plus()
+    Y = oracle.ybus(gr)
+    nb, nnz = gr["nb"], Y.nnz
+    assert nnz == nb + 2 * 3  # the parallel pair merges into one off-diagonal pair
+    jrp, jci = oracle.jac_pattern(Y)
+    assert jrp[-1] == 4 * nnz
+    for r in range(2 * nb):
+        cols = jci[jrp[r]:jrp[r + 1]]
+        assert np.all(np.diff(cols) > 0)
+        i = r % nb
+        ycols = Y.ci[Y.rp[i]:Y.rp[i + 1]]
+        assert np.array_equal(cols, np.concatenate([ycols, nb + ycols]))
+    assert Y.rp[4] - Y.rp[3] == 1  # isolated bus keeps its diagonal
+
+
+def test_contingency_pattern():
+    gr = random_grid(500, 700, 71)
+    from paper_2302_10736_gb300 import synth
+    isb = synth.bridges(500, gr["f"], gr["t"])
+    l = int(np.flatnonzero(~isb)[0])
+    skip = np.zeros(700, np.uint8)
+    skip[l] = 1
+    Y0, Y1 = oracle.ybus(gr), oracle.ybus(gr, skip=skip)
+    assert Y1.nnz == Y0.nnz - 2
+    # with a parallel pair, dropping one keeps the entries
+    g3 = three_bus_plus()
+    s3 = np.array([0, 0, 0, 1], np.uint8)
+    assert oracle.ybus(g3, skip=s3).nnz == oracle.ybus(g3).nnz
+
+
+def test_bridges_by_brute_force():
+    """The generator's bridge list (used to draw N-1 outages) equals removal + BFS."""
+    from paper_2302_10736_gb300 import synth
+    gr = random_grid(60, 75, 81)
+    isb = synth.bridges(60, gr["f"], gr["t"])
+
+    def connected(skip):
+        adj = [[] for _ in range(60)]
+        for l in range(75):
+            if l != skip:
+                adj[gr["f"][l]].append(gr["t"][l])
+                adj[gr["t"][l]].append(gr["f"][l])
+        seen, st = {0}, [0]
+        while st:
+            u = st.pop()
+            for w in adj[u]:
+                if w not in seen:
+                    seen.add(w)
+                    st.append(w)
+        return len(seen) == 60
+
+    assert connected(-1)
+    for l in range(75):
+        assert isb[l] == (not connected(l))
+
+
+def _read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for ln in fh:
+            ln = ln.strip()
+            if ln and not ln.startswith("#"):
+                k, v = ln.split()
+                vals[k] = int(v)
+    return vals
+
+
+def test_paper_element_count():
+    """Sec. V-A.2: the element-wise evaluation of SyntheticUSA computes
+    1,665,936 Jacobian element values, 16 per line; a generated grid with the
+    same number of lines must yield exactly that many."""
+    gv = _read_golden("paper_counts.txt")
+    nl = gv["synthetic_usa_jacobian_elements"] // gv["partials_per_line"]
+    assert nl * gv["partials_per_line"] == gv["synthetic_usa_jacobian_elements"]
+    nb = 82000
+    gr = random_grid(nb, nl, 91)
+    vm, va = random_state(nb, 91)
+    Y = oracle.ybus(gr)
+    oracle.elementwise(gr, vm, va, Y, jac=False)
+    assert oracle.elementwise.last_count == gv["synthetic_usa_jacobian_elements"]
