@@ -1,0 +1,289 @@
+"""Benchmark: injection + Jacobian evaluations/s on one GB300, element-wise vs
+Ybus method, FP64, on the 70,000-bus / 88,000-branch synthetic grid.
+
+One step = one full evaluation by the element-wise method (phasor step +
+fused terminal evaluation and reduction) producing P, Q [nb] and all Jacobian
+values J [4 nnzY] from (vm, va) already resident in HBM.  The Ybus method is
+timed the same way and reported beside it.  L2 (129 MB) is flushed by writing
+a 512 MB buffer between timed steps, outside the timed events.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank evaluates its own replica of the workload
+(the single-scenario path has no exchange step); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = 2
+METRIC = "injection+Jacobian evals/s (element-wise method, FP64)"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 pipe peak derived from the nominal FP64 rate: 152 SMs x 2 FP64 ops/clk x 2.07 GHz
+# (= 1.26 TFLOP/s counting an FMA as 2 flops, the nominal 1.25 TFLOP/s)
+FP64_OPS_PEAK_G = 152 * 2 * 2.070
+HBM_FALLBACK_GBS = 6800.0
+# FP64 arithmetic instructions per unit of the element-wise Jacobian kernel
+EW_OPS_PER_TERMINAL = 14
+EW_OPS_PER_BUS = 12
+YB_OPS_PER_NNZ = 16
+YB_OPS_PER_ROW = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def hbm_peak():
+    try:
+        with open(MEASURED_PEAKS) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the GPU is busy."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def run_oracle_steps(w, nsteps, seconds=None):
+    """Oracle element-wise injection + Jacobian on the workload; returns (evals, s)."""
+    import oracle
+    Y = oracle.ybus(w)
+    vm, va = w["vm"][0], w["va"][0]
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.elementwise(w, vm, va, Y)
+        n += 1
+        el = time.perf_counter() - t0
+        if (seconds is not None and el >= seconds) or (seconds is None and n >= nsteps):
+            return n, el
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(WORKLOAD)
+    run_oracle_steps(w, max(args.warmup, 1))
+    n, el = run_oracle_steps(w, args.steps)
+    v = n / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "synthetic grid, 70,000 buses / 88,000 branches, one voltage state",
+                       "global_batch": 1, "seq_len": 0, "parallelism": "none"},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d full element-wise evaluations of the 70k-bus grid" % n},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_loop(torch, fn, steps, flush):
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev0[k].record()
+        fn()
+        ev1[k].record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+
+    from paper_2302_10736_gb300 import pfgrid, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    w = synth.workload(WORKLOAD)
+    nb, nl = w["nb"], w["nl"]
+    grid = pfgrid.ybus_build(w)
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    vm, va = dev(w["vm"][0]), dev(w["va"][0])
+    P = torch.empty(nb, dtype=torch.float64, device="cuda")
+    Q = torch.empty_like(P)
+    J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+    cfg = pfgrid.grid_autotune(grid, vm, va, reps=20)
+    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")   # 512 MB > L2
+    T = 2 * nl
+
+    ew = lambda: pfgrid.jac_elementwise(grid, vm, va, P, Q, J)
+    yb = lambda: pfgrid.jac_ybus(grid, vm, va, P, Q, J)
+    iew = lambda: pfgrid.inj_elementwise(grid, vm, va, P, Q)
+    iyb = lambda: pfgrid.inj_ybus(grid, vm, va, P, Q)
+    for _ in range(max(args.warmup, 3)):
+        for f in (ew, yb, iew, iyb):
+            flush.fill_(0.0)
+            f()
+    torch.cuda.synchronize()
+    pfgrid.grid_trace_enable(grid, 8 * args.steps + 64)
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_ew = time_loop(torch, ew, args.steps, flush)
+    tr_ew = pfgrid.grid_trace_read(grid)
+    t_yb = time_loop(torch, yb, args.steps, flush)
+    tr_yb = pfgrid.grid_trace_read(grid)
+    t_iew = time_loop(torch, iew, args.steps, flush)
+    t_iyb = time_loop(torch, iyb, args.steps, flush)
+    tr_inj = pfgrid.grid_trace_read(grid)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    pfgrid.grid_trace_enable(grid, 0)
+    pfgrid.grid_check_error(grid)
+
+    ms_step = sum(t_ew) / len(t_ew)
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * 1e3 / ms_step
+
+    def kmean(tr, name):
+        xs = [ms for k, ms in tr if k == name]
+        return (sum(xs) / len(xs), len(xs)) if xs else (None, 0)
+
+    ms_jew, n_jew = kmean(tr_ew, "jac_ew")
+    ms_pu, n_pu = kmean(tr_ew, "phasor_u")
+    ms_jyb, _ = kmean(tr_yb, "jac_ybus")
+    ops_ew = EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb
+    achieved = ops_ew / (ms_jew * 1e-3) / 1e9
+    hbm, hbm_kind = hbm_peak()
+    bytes_ew = 40 * T + (32 + 36 + 16) * nb + 32 * grid.nnz
+    roof = {"bound": "alu", "kernel": "k_jac_ew", "achieved": achieved, "peak": FP64_OPS_PEAK_G,
+            "unit": "GFP64op/s", "frac": achieved / FP64_OPS_PEAK_G, "traffic": None,
+            "ops_per_launch": ops_ew, "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz",
+            "hbm": {"achieved": bytes_ew / (ms_jew * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": bytes_ew / (ms_jew * 1e-3) / 1e9 / hbm, "algorithmic_bytes": bytes_ew,
+                    "peak_source": hbm_kind}}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    try:
+        hb = lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        vm_h, va_h, P_h, Q_h, J_h = hb(nb), hb(nb), hb(nb), hb(nb), hb(grid.nnzJ)
+        vm_h[:], va_h[:] = w["vm"][0], w["va"][0]
+        for _ in range(3):
+            pfgrid.eval_host(grid, 1, vm_h, va_h, P_h, Q_h, J_h)
+        ne = min(args.steps, 100)
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            pfgrid.eval_host(grid, 1, vm_h, va_h, P_h, Q_h, J_h)
+        el = time.perf_counter() - t0
+        e2e = {"value": world * ne / el, "unit": "evals/s", "h2d_bytes_per_step": 16 * nb,
+               "d2h_bytes_per_step": 16 * nb + 8 * grid.nnzJ}
+    except Exception as ex:  # reported, never silently replaced
+        e2e = {"error": str(ex)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, el = run_oracle_steps(w, None, seconds=args.cpu_seconds)
+        cpu = {"value": n / el, "unit": "evals/s", "cores": 1, "kind": "oracle",
+               "sample": "%d full element-wise evaluations (P, Q, J) of the 70k-bus grid, single thread" % n}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "synthetic grid, 70,000 buses / 88,000 branches (nnzY %d, nnzJ %d), "
+                                   "one voltage state" % (grid.nnz, grid.nnzJ),
+                       "global_batch": world, "seq_len": 0, "parallelism": "replicas" if world > 1 else "none",
+                       "l2": "flushed between steps (512 MB write outside the timed events)",
+                       "launch_config": cfg},
+            "e2e": e2e, "gpu_launches": len(tr_ew), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "compare": {
+                "elementwise_jac_evals_per_s": 1e3 / ms_step,
+                "ybus_jac_evals_per_s": 1e3 / (sum(t_yb) / len(t_yb)),
+                "elementwise_inj_evals_per_s": 1e3 / (sum(t_iew) / len(t_iew)),
+                "ybus_inj_evals_per_s": 1e3 / (sum(t_iyb) / len(t_iyb)),
+                "kernel_ms": {"phasor_u": ms_pu, "jac_ew": ms_jew, "jac_ybus": ms_jyb,
+                              "phasor_v": kmean(tr_inj, "phasor_v")[0], "inj_ew": kmean(tr_inj, "inj_ew")[0],
+                              "inj_ybus": kmean(tr_inj, "inj_ybus")[0]},
+                "ybus_fp64_ops_per_launch": YB_OPS_PER_NNZ * grid.nnz + YB_OPS_PER_ROW * nb,
+            },
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * pfgrid.h - C ABI of libpfgrid.so: FP64 bus power injections and power-flow
+ * Jacobians on one GPU (sm_103a), by the two methods compared in
+ * "Bus Admittance Matrix Revisited: Is It Outdated on Modern Computers?"
+ * (H. Cui, arXiv 2302.10736):
+ *   - the Ybus method (Sec. II-A, Sec. IV-B): S = V . conj(Ybus V) (Eq. 1) and
+ *     the Jacobian blocks of Eqs. (2)-(4) by a row-local two-pass sweep;
+ *   - the element-wise method (Sec. II-B, Sec. IV-C): per-branch terminal
+ *     flows (Eqs. 5-6) and their 16 partials, reduced onto buses (Eq. 7) and
+ *     onto Jacobian slots.
+ *
+ * Conventions
+ *   Branch l joins h = from[l] and k = to[l] (0-based).  Series admittance
+ *   y_hk = g + j b (per unit); b_sh is the total line charging, split as
+ *   y_h = y_k = j b_sh / 2; tap m e^{j phi} sits on the h side (Eqs. 5-6);
+ *   lines have m = 1, phi = 0.  Bus shunt y_sh,i = g_s,i + j b_s,i.
+ *   Voltages are polar: vm = |V| (the "V_m" of Eq. 4), va = theta (rad).
+ *   All values are IEEE FP64; indices int32.
+ *
+ *   Ybus pattern: every diagonal (i, i) plus (h, k) and (k, h) of every
+ *   branch; parallel branches share one entry; columns sorted; explicit zeros
+ *   kept (Sec. IV-B.2).
+ *
+ *   Canonical Jacobian J (2nb x 2nb, CSR, Eq. 2 block order), nnzJ = 4 nnzY:
+ *     P-row i    (i < nb): columns = Ybus row-i columns j (theta_j), then nb + j (v_j)
+ *     Q-row nb+i         : same columns
+ *     rowptr[i] = 2 Yrowptr[i],  rowptr[nb + i] = 2 nnzY + 2 Yrowptr[i].
+ *   With d_i the Ybus row length and k the position of column j in Ybus row i:
+ *     J11 = dP_i/dtheta_j at 2 Yrowptr[i] + k
+ *     J12 = dP_i/dv_j     at 2 Yrowptr[i] + d_i + k
+ *     J21 = dQ_i/dtheta_j at 2 nnzY + 2 Yrowptr[i] + k
+ *     J22 = dQ_i/dv_j     at 2 nnzY + 2 Yrowptr[i] + d_i + k
+ *   (Alg. 2's index arrays P_xy in closed form.)
+ *
+ * Execution model
+ *   Every evaluation entry point is asynchronous on `stream` (a cudaStream_t,
+ *   NULL = the legacy default stream), allocates nothing, never synchronizes
+ *   and takes device pointers the caller owns.  A grid owns one phasor
+ *   workspace, so evaluations that use the same grid must not overlap on the
+ *   GPU (issue them on one stream).  Input checks are done at build time;
+ *   evaluation calls check only for NULL pointers and sizes.
+ *   Errors: every function returns a pf_status; pf_last_error() gives a
+ *   message for the calling thread.  Nothing aborts or throws across the ABI.
+ */
+#ifndef PFGRID_H
+#define PFGRID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pf_status;
+#define PF_OK 0
+#define PF_EINVAL 1          /* bad argument (NULL pointer, size, non-finite or non-positive tap) */
+#define PF_ENOMEM 2          /* device or host allocation failed */
+#define PF_ECUDA 3           /* a CUDA runtime call or launch failed */
+#define PF_ETOPO 4           /* bad topology: bus index out of range or self loop */
+#define PF_EDEVICE 5         /* a kernel reported an error through the grid's device error word */
+#define PF_ETIMEOUT 6        /* a bounded device-side wait gave up */
+#define PF_EUNSUPPORTED 7    /* size beyond the int32 index range of this library */
+
+typedef void *pf_stream;            /* cudaStream_t */
+typedef struct pf_grid pf_grid;     /* opaque; owns all device structure of one network */
+
+/* Host-side network description (structure of arrays).  nb >= 0, nl >= 0.
+   gs / bs may be NULL (no bus shunts). */
+typedef struct {
+    int32_t nb, nl;
+    const int32_t *from, *to;       /* [nl] bus indices, from != to */
+    const double *g, *b;            /* [nl] series conductance / susceptance (p.u.) */
+    const double *bsh;              /* [nl] total line charging susceptance */
+    const double *tap;              /* [nl] off-nominal ratio m > 0 (1 for lines) */
+    const double *shift;            /* [nl] phase shift phi (rad) */
+    const double *gs, *bs;          /* [nb] bus shunt conductance / susceptance, or NULL */
+} pf_grid_desc;
+
+/* Launch configuration (chosen by grid_autotune or set by hand). */
+typedef struct {
+    int32_t ybus_lanes;     /* lanes per Ybus row in the CSR kernels: 1, 2, 4, 8, 16 or 32 */
+    int32_t ybus_block;     /* threads per CTA of the CSR kernels (multiple of 32, <= 512) */
+    int32_t ew_window;      /* buses per CTA window of the element-wise kernels: 64, 128, 256 or 512 */
+} pf_config;
+
+/* Human-readable name of a status code (static string). */
+const char *pf_status_str(pf_status s);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *pf_last_error(void);
+
+/*
+ * Build a grid: validates the description (PF_EINVAL / PF_ETOPO), builds the
+ * Ybus pattern, the canonical J pattern, the terminal layouts of both methods
+ * and the per-terminal constants of Eqs. (5)-(6) (computed once ahead of time,
+ * Sec. IV-C.1), uploads everything and computes the Ybus values on `stream`.
+ * Synchronizes `stream` before returning (setup, not the hot path).
+ * The description's arrays are read during the call only.
+ */
+pf_status ybus_build(const pf_grid_desc *desc, pf_stream stream, pf_grid **out);
+
+/* Free every device and host resource of a grid (NULL is allowed). */
+void grid_destroy(pf_grid *grid);
+
+/* Sizes of a grid. Any output pointer may be NULL. */
+pf_status grid_info(const pf_grid *grid, int32_t *nb, int32_t *nl, int32_t *nnzY);
+
+/*
+ * Replace the branch and bus-shunt parameters from DEVICE arrays (same
+ * meaning as in pf_grid_desc: g, b, bsh, tap, shift [nl]; gs, bs [nb] or
+ * NULL for zero) without changing the topology; recomputes the terminal
+ * constants and the Ybus values on `stream`.  Taps are not re-validated.
+ */
+pf_status grid_set_params(pf_grid *grid, const double *g, const double *b, const double *bsh,
+                          const double *tap, const double *shift, const double *gs, const double *bs,
+                          pf_stream stream);
+
+/*
+ * Device pointers to the grid's Ybus (owned by the grid, valid until
+ * grid_destroy): rowptr [nb+1], colidx [nnz], values [nnz] as interleaved
+ * (re, im) pairs.
+ */
+pf_status ybus_get(const pf_grid *grid, int32_t *nnz, const int32_t **rowptr, const int32_t **colidx,
+                   const double **values);
+
+/* Device pointers to the canonical J pattern (owned by the grid):
+   rowptr [2nb+1], colidx [nnzJ]. */
+pf_status jac_pattern(const pf_grid *grid, int32_t *nnzJ, const int32_t **rowptr, const int32_t **colidx);
+
+/*
+ * Bus injections by the Ybus method (Eq. 1; Sec. IV-B.1 steps 1-3):
+ * phasors U = e^{j theta}, V = vm U; I = Ybus V by a CSR SpMV with
+ * config.ybus_lanes lanes per row; S = V . conj(I).
+ * vm, va [nb] in; P, Q [nb] out (device, caller-owned).
+ */
+pf_status inj_ybus(pf_grid *grid, const double *vm, const double *va, double *P, double *Q, pf_stream stream);
+
+/*
+ * Bus injections by the element-wise method (Eqs. 5-7): every branch
+ * terminal's flow from its precomputed constants and the gathered bus
+ * phasors, then a deterministic segmented sum onto its bus plus the bus
+ * shunt.  Same arguments as inj_ybus.
+ */
+pf_status inj_elementwise(pf_grid *grid, const double *vm, const double *va, double *P, double *Q,
+                          pf_stream stream);
+
+/*
+ * Jacobian values by the Ybus method (Eqs. 2-4): per Ybus row, one sweep
+ * forms Y_ij U_j, the off-diagonal entries and the row current I_i; the
+ * diagonal entry is completed once I_i is known (the two passes of Alg. 1,
+ * kept row-local).  Values land directly in the canonical layout (Alg. 2).
+ * vm, va [nb] in; J [4 nnzY] out; P, Q [nb] out or NULL.
+ */
+pf_status jac_ybus(pf_grid *grid, const double *vm, const double *va, double *P, double *Q, double *J,
+                   pf_stream stream);
+
+/*
+ * Jacobian values by the element-wise method: each terminal evaluates its
+ * flow and 8 partials (16 per branch, Sec. II-B), which are reduced without
+ * atomics onto the diagonal slot of its bus and the off-diagonal slot of its
+ * (bus, other bus) pair.  Same arguments as jac_ybus.
+ */
+pf_status jac_elementwise(pf_grid *grid, const double *vm, const double *va, double *P, double *Q, double *J,
+                          pf_stream stream);
+
+/*
+ * End-to-end evaluation from HOST buffers: copies vm, va [nb] to grid-owned
+ * device buffers, runs jac_ybus (method 0) or jac_elementwise (method 1),
+ * copies P, Q [nb] and J [4 nnzY] back, and synchronizes `stream`.  The
+ * device staging buffers are allocated on the first call and kept by the
+ * grid.  Host buffers may be pageable or pinned (pinned is faster).
+ */
+pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P, double *Q,
+                    double *J, pf_stream stream);
+
+/* Current launch configuration. */
+pf_status grid_get_config(const pf_grid *grid, pf_config *cfg);
+
+/*
+ * Set the launch configuration.  Changing ew_window rebuilds the
+ * element-wise terminal layout (host work + upload, synchronizes `stream`).
+ */
+pf_status grid_set_config(pf_grid *grid, const pf_config *cfg, pf_stream stream);
+
+/*
+ * Autotuner: times every candidate configuration of each kernel (CUDA
+ * events, `reps` launches each, on `stream`) with the given device state
+ * vm, va [nb], keeps the fastest, and writes the chosen configuration to
+ * *best (may be NULL).  Allocates temporary device outputs; synchronizes.
+ */
+pf_status grid_autotune(pf_grid *grid, const double *vm, const double *va, int32_t reps, pf_stream stream,
+                        pf_config *best);
+
+/*
+ * Synchronize `stream` and report device-side errors recorded by the grid's
+ * kernels (PF_EDEVICE, PF_ETIMEOUT); clears the error word.
+ */
+pf_status grid_check_error(pf_grid *grid, pf_stream stream);
+
+/*
+ * Host-only self-check (no GPU needed, nothing allocated on the device):
+ * validates `desc` like ybus_build, builds the index structures of the grid
+ * and of an element-wise layout with `window` buses per CTA, and verifies
+ * every invariant the kernels' memory accesses rely on (index ranges,
+ * one slot per bus, one entry per terminal, staging offsets inside the
+ * window's slice, shared-memory size).  PF_OK or PF_EINVAL with a message.
+ */
+pf_status grid_selfcheck(const pf_grid_desc *desc, int32_t window);
+
+/* ------------------------------------------------------------ tracing -- */
+
+/* Kernel identifiers reported by the tracer. */
+#define PF_K_PHASOR_U 0      /* phasor step for the Jacobian kernels */
+#define PF_K_PHASOR_V 1      /* phasor step for the injection kernels */
+#define PF_K_INJ_YBUS 2
+#define PF_K_JAC_YBUS 3
+#define PF_K_INJ_EW 4
+#define PF_K_JAC_EW 5
+#define PF_K_COUNT 6
+
+typedef struct {
+    int32_t kernel;          /* PF_K_* */
+    float ms;                /* device time between CUDA events recorded around the launch */
+} pf_trace_rec;
+
+/* Static name of a kernel identifier ("?" if unknown). */
+const char *pf_kernel_name(int32_t kernel);
+
+/*
+ * Per-launch tracing: with capacity > 0, every kernel launch of this grid's
+ * evaluation calls is bracketed by two CUDA events recorded on the launching
+ * stream, for up to `capacity` launches (later launches are not recorded).
+ * capacity = 0 turns tracing off and frees the events.  Evaluation calls
+ * stay asynchronous; tracing adds two cudaEventRecord calls per launch.
+ */
+pf_status grid_trace_enable(pf_grid *grid, int32_t capacity);
+
+/*
+ * Wait for the recorded events, copy up to `cap` records (in launch order)
+ * to `out`, set *n to the number of records, and start a new trace.
+ */
+pf_status grid_trace_read(pf_grid *grid, pf_trace_rec *out, int32_t cap, int32_t *n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFGRID_H */

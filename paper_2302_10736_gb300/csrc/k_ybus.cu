@@ -1,0 +1,167 @@
+// k_ybus.cu - Ybus method on the CSR admittance matrix (Sec. II-A, IV-B).
+//
+// W lanes serve one Ybus row (W = 1 .. 32, the "vector CSR" family; W = 32 is
+// the warp-per-row SpMV).  Rows are independent, so the two passes of Alg. 1
+// (pass 1: I = Ybus V and the products Y_ij V_j, Y_ij U_j; pass 2: the
+// diag(V) and diag(I) corrections) fuse into one sweep per row: only the
+// diagonal entry needs the finished row current I_i, and it is completed by
+// the lane that holds it after a W-lane shuffle reduction.
+//
+// Per structural (i, j), with U_j = e^{j theta_j} and YU = Y_ij U_j:
+//     dS_i/dv_j     = V_i conj(YU)                         (Eq. 4, off-diagonal term)
+//     dS_i/dtheta_j = -j V_i conj(Y_ij V_j) = -j v_j dS_i/dv_j   (Eq. 3)
+//     I_i          += v_j YU
+// and on the diagonal additionally  +j V_i conj(I_i)  and  +conj(I_i) U_i.
+// (Alg. 1 as printed carries the opposite sign on dS/dtheta; Eq. 3 is used.)
+// Values are written straight into the canonical J layout, i.e. the copy of
+// Alg. 2 with its index arrays in closed form.
+#include "pf_internal.h"
+
+namespace pf {
+
+template <int W>
+__global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                    const double2 *__restrict__ Y, const double2 *__restrict__ V,
+                                                    double *__restrict__ P, double *__restrict__ Q)
+{
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = (int)(gid / W), lane = (int)(gid % W);
+    const bool valid = row < nb;
+    double Ir = 0.0, Ii = 0.0;
+    if (valid) {
+        const int e1 = rp[row + 1];
+        for (int e = rp[row] + lane; e < e1; e += W) {
+            const double2 y = Y[e];
+            const double2 v = V[ci[e]];
+            Ir = fma(y.x, v.x, Ir);
+            Ir = fma(-y.y, v.y, Ir);
+            Ii = fma(y.x, v.y, Ii);
+            Ii = fma(y.y, v.x, Ii);
+        }
+    }
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+        Ir += __shfl_xor_sync(0xffffffffu, Ir, off, W);
+        Ii += __shfl_xor_sync(0xffffffffu, Ii, off, W);
+    }
+    if (valid && lane == 0) {
+        const double2 Vi = V[row];
+        P[row] = fma(Vi.x, Ir, Vi.y * Ii);   // S = V conj(I)
+        Q[row] = fma(Vi.y, Ir, -Vi.x * Ii);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__restrict__ rp,
+                                                    const int *__restrict__ ci, const double2 *__restrict__ Y,
+                                                    const double4_32a *__restrict__ U, double *__restrict__ P,
+                                                    double *__restrict__ Q, double *__restrict__ J)
+{
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = (int)(gid / W), lane = (int)(gid % W);
+    const bool valid = row < nb;
+    double Ir = 0.0, Ii = 0.0;
+    double dTr = 0.0, dTi = 0.0, dVr = 0.0, dVi = 0.0;  // diagonal partials (lane that owns it)
+    int kd = -1, rs = 0, d = 0;
+    double4_32a ui = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    if (valid) {
+        rs = rp[row];
+        d = rp[row + 1] - rs;
+        ui = U[row];
+        const double Vr = ui.z * ui.x, Vi = ui.z * ui.y;
+        for (int k = lane; k < d; k += W) {
+            const int e = rs + k;
+            const int j = ci[e];
+            const double2 y = Y[e];
+            const double4_32a uj = U[j];
+            const double YUr = fma(y.x, uj.x, -y.y * uj.y);
+            const double YUi = fma(y.x, uj.y, y.y * uj.x);
+            const double sVr = fma(Vr, YUr, Vi * YUi);    // V_i conj(YU)
+            const double sVi = fma(Vi, YUr, -Vr * YUi);
+            const double vj = uj.z;
+            Ir = fma(vj, YUr, Ir);
+            Ii = fma(vj, YUi, Ii);
+            const double sTr = vj * sVi, sTi = -vj * sVr;   // -j v_j dS/dv_j
+            if (j == row) {
+                kd = k;
+                dTr = sTr;
+                dTi = sTi;
+                dVr = sVr;
+                dVi = sVi;
+            } else {
+                const int p = 2 * rs + k;
+                J[p] = sTr;
+                J[p + d] = sVr;
+                J[2 * nnz + p] = sTi;
+                J[2 * nnz + p + d] = sVi;
+            }
+        }
+    }
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+        Ir += __shfl_xor_sync(0xffffffffu, Ir, off, W);
+        Ii += __shfl_xor_sync(0xffffffffu, Ii, off, W);
+    }
+    if (!valid) return;
+    const double Vr = ui.z * ui.x, Vi = ui.z * ui.y;
+    const double Sr = fma(Vr, Ir, Vi * Ii), Si = fma(Vi, Ir, -Vr * Ii);
+    if (kd >= 0) {
+        dTr -= Si;                           // + j S_i  (= j V_i conj(I_i))
+        dTi += Sr;
+        dVr += fma(Ir, ui.x, Ii * ui.y);     // + conj(I_i) U_i
+        dVi += fma(Ir, ui.y, -Ii * ui.x);
+        const int p = 2 * rs + kd;
+        J[p] = dTr;
+        J[p + d] = dVr;
+        J[2 * nnz + p] = dTi;
+        J[2 * nnz + p + d] = dVi;
+    }
+    if (lane == 0 && P) {
+        P[row] = Sr;
+        Q[row] = Si;
+    }
+}
+
+template <int W>
+static cudaError_t inj_w(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s)
+{
+    const long long threads = (long long)g->nb * W;
+    const int blk = g->cfg.ybus_block;
+    k_inj_ybus<W><<<(int)((threads + blk - 1) / blk), blk, 0, s>>>(g->nb, g->rp, g->ci, g->yv, V, P, Q);
+    return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t jac_w(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s)
+{
+    const long long threads = (long long)g->nb * W;
+    const int blk = g->cfg.ybus_block;
+    k_jac_ybus<W><<<(int)((threads + blk - 1) / blk), blk, 0, s>>>(g->nb, g->nnz, g->rp, g->ci, g->yv, U, P, Q, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s)
+{
+    switch (g->cfg.ybus_lanes) {
+    case 1: return inj_w<1>(g, V, P, Q, s);
+    case 2: return inj_w<2>(g, V, P, Q, s);
+    case 4: return inj_w<4>(g, V, P, Q, s);
+    case 8: return inj_w<8>(g, V, P, Q, s);
+    case 16: return inj_w<16>(g, V, P, Q, s);
+    default: return inj_w<32>(g, V, P, Q, s);
+    }
+}
+
+cudaError_t launch_jac_ybus(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s)
+{
+    switch (g->cfg.ybus_lanes) {
+    case 1: return jac_w<1>(g, U, P, Q, J, s);
+    case 2: return jac_w<2>(g, U, P, Q, J, s);
+    case 4: return jac_w<4>(g, U, P, Q, J, s);
+    case 8: return jac_w<8>(g, U, P, Q, J, s);
+    case 16: return jac_w<16>(g, U, P, Q, J, s);
+    default: return jac_w<32>(g, U, P, Q, J, s);
+    }
+}
+
+}  // namespace pf

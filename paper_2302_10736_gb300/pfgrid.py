@@ -1,0 +1,325 @@
+"""Thin ctypes binding of libpfgrid.so (the C ABI declared in include/pfgrid.h).
+
+Argument marshalling only: every evaluation step runs in the library's CUDA
+kernels.  Device arrays are torch CUDA tensors (float64, contiguous); the
+stream defaults to torch's current stream.  There is no CPU fallback: if the
+library is missing or fails to load, importing this module raises.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB_PFGRID
+HEADER = os.path.join(_build.INCLUDE, "pfgrid.h")
+
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETOPO, PF_EDEVICE, PF_ETIMEOUT, PF_EUNSUPPORTED = range(8)
+
+
+class PfError(RuntimeError):
+    def __init__(self, status, name, msg):
+        super().__init__("%s failed: %s (%s)" % (name, _status_name(status), msg))
+        self.status = status
+
+
+class pf_grid_desc(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int32), ("nl", ctypes.c_int32),
+                ("from_", ctypes.c_void_p), ("to", ctypes.c_void_p),
+                ("g", ctypes.c_void_p), ("b", ctypes.c_void_p), ("bsh", ctypes.c_void_p),
+                ("tap", ctypes.c_void_p), ("shift", ctypes.c_void_p),
+                ("gs", ctypes.c_void_p), ("bs", ctypes.c_void_p)]
+
+
+class pf_config(ctypes.Structure):
+    _fields_ = [("ybus_lanes", ctypes.c_int32), ("ybus_block", ctypes.c_int32), ("ew_window", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class pf_trace_rec(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpfgrid.so is not built (%s); run __graft_entry__.build() first" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, pi32 = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)
+    st = ctypes.c_int32
+    sig = {
+        "pf_status_str": (ctypes.c_char_p, [st]),
+        "pf_last_error": (ctypes.c_char_p, []),
+        "ybus_build": (st, [ctypes.POINTER(pf_grid_desc), vp, ctypes.POINTER(vp)]),
+        "grid_destroy": (None, [vp]),
+        "grid_info": (st, [vp, pi32, pi32, pi32]),
+        "grid_set_params": (st, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "ybus_get": (st, [vp, pi32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "jac_pattern": (st, [vp, pi32, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "inj_ybus": (st, [vp, vp, vp, vp, vp, vp]),
+        "inj_elementwise": (st, [vp, vp, vp, vp, vp, vp]),
+        "jac_ybus": (st, [vp, vp, vp, vp, vp, vp, vp]),
+        "jac_elementwise": (st, [vp, vp, vp, vp, vp, vp, vp]),
+        "eval_host": (st, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "grid_get_config": (st, [vp, ctypes.POINTER(pf_config)]),
+        "grid_set_config": (st, [vp, ctypes.POINTER(pf_config), vp]),
+        "grid_autotune": (st, [vp, vp, vp, i32, vp, ctypes.POINTER(pf_config)]),
+        "grid_check_error": (st, [vp, vp]),
+        "pf_kernel_name": (ctypes.c_char_p, [i32]),
+        "grid_trace_enable": (st, [vp, i32]),
+        "grid_trace_read": (st, [vp, ctypes.POINTER(pf_trace_rec), i32, pi32]),
+        "grid_selfcheck": (st, [ctypes.POINTER(pf_grid_desc), i32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _status_name(s):
+    return _lib.pf_status_str(s).decode()
+
+
+def last_error():
+    return _lib.pf_last_error().decode()
+
+
+def _check(status, name):
+    if status != PF_OK:
+        raise PfError(status, name, last_error())
+
+
+def header_functions():
+    """Names of the functions declared in include/pfgrid.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", txt, flags=re.M)))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(x, name, n=None):
+    """Device pointer of a float64 contiguous CUDA tensor (None -> NULL)."""
+    if x is None:
+        return None
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+    if n is not None and x.numel() < n:
+        raise ValueError("%s has %d elements, needs %d" % (name, x.numel(), n))
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _hptr(a, dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+class Grid:
+    """Owner of a pf_grid handle."""
+
+    def __init__(self, handle):
+        self.handle = ctypes.c_void_p(handle)
+        nb, nl, nnz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.grid_info(self.handle, ctypes.byref(nb), ctypes.byref(nl), ctypes.byref(nnz)), "grid_info")
+        self.nb, self.nl, self.nnz = nb.value, nl.value, nnz.value
+
+    @property
+    def nnzJ(self):
+        return 4 * self.nnz
+
+    def close(self):
+        if self.handle:
+            _lib.grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _desc(gr, keep):
+    nb, nl = int(gr["nb"]), int(gr["nl"])
+
+    def h(key, dtype):
+        arr, p = _hptr(gr.get(key), dtype)
+        keep.append(arr)
+        return p
+
+    return pf_grid_desc(nb, nl, h("f", np.int32), h("t", np.int32), h("g", np.float64), h("b", np.float64),
+                        h("bsh", np.float64), h("tap", np.float64), h("shift", np.float64), h("gs", np.float64),
+                        h("bs", np.float64))
+
+
+def grid_selfcheck(gr, window):
+    """Host-only check of every index invariant of the kernels (no GPU)."""
+    keep = []
+    d = _desc(gr, keep)
+    _check(_lib.grid_selfcheck(ctypes.byref(d), int(window)), "grid_selfcheck")
+
+
+def ybus_build(gr, stream=None):
+    """Build a grid from a dict with nb, nl, f, t, g, b, bsh, tap, shift and
+    optional gs, bs (host arrays)."""
+    keep = []
+    d = _desc(gr, keep)
+    out = ctypes.c_void_p()
+    s = ctypes.c_void_p(0) if stream is None and not _cuda_ready() else _stream(stream)
+    _check(_lib.ybus_build(ctypes.byref(d), s, ctypes.byref(out)), "ybus_build")
+    return Grid(out.value)
+
+
+def _cuda_ready():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def grid_set_params(grid, g, b, bsh, tap, shift, gs=None, bs=None, stream=None):
+    n, nb = grid.nl, grid.nb
+    _check(_lib.grid_set_params(grid.handle, _dptr(g, "g", n), _dptr(b, "b", n), _dptr(bsh, "bsh", n),
+                                _dptr(tap, "tap", n), _dptr(shift, "shift", n), _dptr(gs, "gs", nb),
+                                _dptr(bs, "bs", nb), _stream(stream)), "grid_set_params")
+
+
+def _device_copy(src_ptr, n, dtype):
+    import torch
+    out = torch.empty(n, dtype=dtype, device="cuda")
+    if n:
+        cudart = _cudart()
+        nbytes = n * out.element_size()
+        rc = cudart.cudaMemcpy(ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(src_ptr), ctypes.c_size_t(nbytes), 3)
+        if rc != 0:
+            raise RuntimeError("cudaMemcpy failed (%d)" % rc)
+    return out
+
+
+_cudart_lib = None
+
+
+def _cudart():
+    global _cudart_lib
+    if _cudart_lib is None:
+        for name in ("libcudart.so.13", "libcudart.so"):
+            try:
+                _cudart_lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        _cudart_lib.cudaMemcpy.restype = ctypes.c_int
+        _cudart_lib.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    return _cudart_lib
+
+
+def ybus_get(grid):
+    """(rowptr, colidx, values[nnz, 2]) as new torch CUDA tensors (copies)."""
+    import torch
+    nnz = ctypes.c_int32()
+    rp, ci, yv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(_lib.ybus_get(grid.handle, ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci), ctypes.byref(yv)),
+           "ybus_get")
+    n = nnz.value
+    return (_device_copy(rp.value, grid.nb + 1, torch.int32), _device_copy(ci.value, n, torch.int32),
+            _device_copy(yv.value, 2 * n, torch.float64).view(n, 2))
+
+
+def jac_pattern(grid):
+    """(rowptr, colidx) of the canonical J as new torch CUDA tensors."""
+    import torch
+    nnzJ = ctypes.c_int32()
+    rp, ci = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(_lib.jac_pattern(grid.handle, ctypes.byref(nnzJ), ctypes.byref(rp), ctypes.byref(ci)), "jac_pattern")
+    return _device_copy(rp.value, 2 * grid.nb + 1, torch.int32), _device_copy(ci.value, nnzJ.value, torch.int32)
+
+
+def inj_ybus(grid, vm, va, P, Q, stream=None):
+    n = grid.nb
+    _check(_lib.inj_ybus(grid.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(P, "P", n), _dptr(Q, "Q", n),
+                         _stream(stream)), "inj_ybus")
+
+
+def inj_elementwise(grid, vm, va, P, Q, stream=None):
+    n = grid.nb
+    _check(_lib.inj_elementwise(grid.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(P, "P", n),
+                                _dptr(Q, "Q", n), _stream(stream)), "inj_elementwise")
+
+
+def jac_ybus(grid, vm, va, P, Q, J, stream=None):
+    n = grid.nb
+    _check(_lib.jac_ybus(grid.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(P, "P", n), _dptr(Q, "Q", n),
+                         _dptr(J, "J", grid.nnzJ), _stream(stream)), "jac_ybus")
+
+
+def jac_elementwise(grid, vm, va, P, Q, J, stream=None):
+    n = grid.nb
+    _check(_lib.jac_elementwise(grid.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(P, "P", n),
+                                _dptr(Q, "Q", n), _dptr(J, "J", grid.nnzJ), _stream(stream)), "jac_elementwise")
+
+
+def eval_host(grid, method, vm, va, P, Q, J, stream=None):
+    """Host numpy buffers in and out (vm, va, P, Q [nb]; J [4 nnzY])."""
+    for name, a, n in (("vm", vm, grid.nb), ("va", va, grid.nb), ("P", P, grid.nb), ("Q", Q, grid.nb),
+                       ("J", J, grid.nnzJ)):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size >= n):
+            raise TypeError("%s must be a contiguous float64 numpy array with >= %d elements" % (name, n))
+    m = {"ybus": 0, "elementwise": 1}.get(method, method)
+    vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+    _check(_lib.eval_host(grid.handle, int(m), vp(vm), vp(va), vp(P), vp(Q), vp(J), _stream(stream)), "eval_host")
+
+
+def grid_get_config(grid):
+    c = pf_config()
+    _check(_lib.grid_get_config(grid.handle, ctypes.byref(c)), "grid_get_config")
+    return c.as_dict()
+
+
+def grid_set_config(grid, stream=None, **kw):
+    c = pf_config(**{**grid_get_config(grid), **kw})
+    _check(_lib.grid_set_config(grid.handle, ctypes.byref(c), _stream(stream)), "grid_set_config")
+
+
+def grid_autotune(grid, vm, va, reps=20, stream=None):
+    c = pf_config()
+    _check(_lib.grid_autotune(grid.handle, _dptr(vm, "vm", grid.nb), _dptr(va, "va", grid.nb), int(reps),
+                              _stream(stream), ctypes.byref(c)), "grid_autotune")
+    return c.as_dict()
+
+
+def grid_check_error(grid, stream=None):
+    _check(_lib.grid_check_error(grid.handle, _stream(stream)), "grid_check_error")
+
+
+def kernel_name(k):
+    return _lib.pf_kernel_name(int(k)).decode()
+
+
+def grid_trace_enable(grid, capacity):
+    _check(_lib.grid_trace_enable(grid.handle, int(capacity)), "grid_trace_enable")
+
+
+def grid_trace_read(grid, cap=1 << 16):
+    """List of (kernel name, ms) for the launches traced since the last read."""
+    buf = (pf_trace_rec * cap)()
+    n = ctypes.c_int32()
+    _check(_lib.grid_trace_read(grid.handle, buf, cap, ctypes.byref(n)), "grid_trace_read")
+    return [(kernel_name(buf[i].kernel), float(buf[i].ms)) for i in range(n.value)]

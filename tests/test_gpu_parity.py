@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Bar (per output vector, each J block separately):
+    max |x - x_oracle| / max |x_oracle| <= 1e-12,
+with the Ybus and Jacobian sparsity patterns bit-exact and results
+bit-identical from run to run.  The tolerance covers FMA contraction and a
+different summation order; the expected error is a few 1e-16.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gridcases import blocks, make_grid, random_grid, random_state, relerr, three_bus_plus, two_bus_lossless
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pf():
+    from paper_2302_10736_gb300 import _build
+    _build.build_pfgrid()
+    from paper_2302_10736_gb300 import pfgrid
+    return pfgrid
+
+
+def _d(x):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def gpu_eval(pf, grid, vm, va):
+    import torch
+    nb = grid.nb
+    vm_d, va_d = _d(vm), _d(va)
+    res = {}
+    for name in ("inj_ybus", "inj_elementwise"):
+        P = torch.full((nb,), np.nan, dtype=torch.float64, device="cuda")
+        Q = torch.full((nb,), np.nan, dtype=torch.float64, device="cuda")
+        getattr(pf, name)(grid, vm_d, va_d, P, Q)
+        res[name] = (P.cpu().numpy(), Q.cpu().numpy(), None)
+    for name in ("jac_ybus", "jac_elementwise"):
+        P = torch.full((nb,), np.nan, dtype=torch.float64, device="cuda")
+        Q = torch.full((nb,), np.nan, dtype=torch.float64, device="cuda")
+        J = torch.full((max(grid.nnzJ, 1),), np.nan, dtype=torch.float64, device="cuda")
+        getattr(pf, name)(grid, vm_d, va_d, P, Q, J)
+        res[name] = (P.cpu().numpy(), Q.cpu().numpy(), J.cpu().numpy()[:grid.nnzJ])
+    torch.cuda.synchronize()
+    pf.grid_check_error(grid)
+    return res
+
+
+def check_against_oracle(pf, gr, vm, va, grid=None, tol=TOL):
+    grid = grid or pf.ybus_build(gr)
+    Y = oracle.ybus(gr)
+    jrp, jci = oracle.jac_pattern(Y)
+    rp, ci, yv = pf.ybus_get(grid)
+    assert np.array_equal(rp.cpu().numpy(), Y.rp)
+    assert np.array_equal(ci.cpu().numpy(), Y.ci)
+    yv = yv.cpu().numpy()
+    assert relerr(yv[:, 0] + 1j * yv[:, 1], Y.yre + 1j * Y.yim) <= tol
+    Jrp, Jci = pf.jac_pattern(grid)
+    assert np.array_equal(Jrp.cpu().numpy(), jrp)
+    assert np.array_equal(Jci.cpu().numpy(), jci)
+
+    P_ref, Q_ref = oracle.inj_sparse(Y, vm, va)
+    J_ref = oracle.jac_ybus(Y, vm, va)
+    Pe_ref, Qe_ref, Je_ref = oracle.elementwise(gr, vm, va, Y)
+    refs = {"inj_ybus": (P_ref, Q_ref, None), "jac_ybus": (P_ref, Q_ref, J_ref),
+            "inj_elementwise": (Pe_ref, Qe_ref, None), "jac_elementwise": (Pe_ref, Qe_ref, Je_ref)}
+    res = gpu_eval(pf, grid, vm, va)
+    errs = {}
+    for name, (P, Q, J) in res.items():
+        Pr, Qr, Jr = refs[name]
+        errs[name + ".P"] = relerr(P, Pr)
+        errs[name + ".Q"] = relerr(Q, Qr)
+        if J is not None:
+            for bname, a, b in zip(("J11", "J12", "J21", "J22"), blocks(J, jci, gr["nb"], Y.nnz),
+                                   blocks(Jr, jci, gr["nb"], Y.nnz)):
+                errs[name + "." + bname] = relerr(a, b)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, bad
+    return res, errs
+
+
+CASES = {
+    "two_bus": lambda: (two_bus_lossless(), np.array([1.0, 1.0]), np.array([0.0, -0.1])),
+    "three_bus_plus": lambda: (three_bus_plus(),) + random_state(4, 3),
+    "random_shift_300": lambda: (random_grid(300, 420, 5, shift_max=0.3),) + random_state(300, 5),
+    "ragged_1001": lambda: (random_grid(1001, 1400, 6, shift_max=0.2),) + random_state(1001, 6),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_hand_and_small_grids(pf, case):
+    gr, vm, va = CASES[case]()
+    check_against_oracle(pf, gr, vm, va)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_workloads_full_size(pf, k):
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(k)
+    check_against_oracle(pf, w, w["vm"][0], w["va"][0])
+
+
+def test_single_bus_no_branches(pf):
+    gr = make_grid(1, [], shunts={0: (0.03, -0.02)})
+    check_against_oracle(pf, gr, np.array([1.02]), np.array([0.3]))
+
+
+def test_empty_grid(pf):
+    import torch
+    gr = make_grid(0, [])
+    grid = pf.ybus_build(gr)
+    assert (grid.nb, grid.nl, grid.nnz) == (0, 0, 0)
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    pf.inj_ybus(grid, e, e, e, e)
+    pf.jac_elementwise(grid, e, e, e, e, torch.empty(1, dtype=torch.float64, device="cuda"))
+    pf.grid_check_error(grid)
+
+
+def test_isolated_buses_and_parallel_runs(pf):
+    # a star with a triple-parallel spoke, two isolated buses, shunts everywhere
+    br = [(0, 1, 1.0, -10.0, 0.02, 1.0, 0.0), (1, 0, 2.0, -8.0, 0.01, 1.03, 0.05),
+          (0, 1, 0.5, -12.0, 0.0, 0.98, -0.02), (0, 2, 1.5, -9.0, 0.03, 1.0, 0.0),
+          (3, 0, 0.7, -7.0, 0.04, 1.0, 0.0)]
+    gr = make_grid(6, br, shunts={i: (0.01 * i, -0.02 * i) for i in range(6)})
+    vm, va = random_state(6, 9)
+    check_against_oracle(pf, gr, vm, va)
+
+
+def test_large_angles(pf):
+    gr = random_grid(500, 700, 8, shift_max=0.3)
+    vm, va = random_state(500, 8)
+    va = va * 400.0   # angles up to a few hundred radians
+    check_against_oracle(pf, gr, vm, va)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("window", [64, 128, 256, 512])
+def test_every_launch_configuration(pf, lanes, window):
+    gr = random_grid(1500, 2100, 10, shift_max=0.2)
+    vm, va = random_state(1500, 10)
+    grid = pf.ybus_build(gr)
+    pf.grid_set_config(grid, ybus_lanes=lanes, ew_window=window, ybus_block=256)
+    assert pf.grid_get_config(grid)["ew_window"] == window
+    check_against_oracle(pf, gr, vm, va, grid=grid)
+
+
+def test_bitwise_determinism(pf):
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    grid = pf.ybus_build(w)
+    a = gpu_eval(pf, grid, w["vm"][0], w["va"][0])
+    b = gpu_eval(pf, grid, w["vm"][0], w["va"][0])
+    for k in a:
+        for x, y in zip(a[k], b[k]):
+            if x is not None:
+                assert np.array_equal(x.view(np.uint64), y.view(np.uint64)), k
+
+
+def test_eval_host_matches_device(pf):
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    grid = pf.ybus_build(w)
+    vm, va = w["vm"][0].copy(), w["va"][0].copy()
+    dev = gpu_eval(pf, grid, vm, va)
+    for m, name in ((0, "jac_ybus"), (1, "jac_elementwise")):
+        P, Q, J = np.zeros(grid.nb), np.zeros(grid.nb), np.zeros(grid.nnzJ)
+        pf.eval_host(grid, m, vm, va, P, Q, J)
+        assert np.array_equal(P, dev[name][0]) and np.array_equal(Q, dev[name][1])
+        assert np.array_equal(J, dev[name][2])
+
+
+def test_set_params_matches_rebuild(pf):
+    import torch
+    gr = random_grid(800, 1100, 12, shift_max=0.2)
+    vm, va = random_state(800, 12)
+    grid = pf.ybus_build(gr)
+    rng = np.random.default_rng(12)
+    gr2 = dict(gr)
+    for k in ("g", "b", "bsh"):
+        gr2[k] = gr[k] * rng.uniform(0.8, 1.2, gr["nl"])
+    gr2["tap"] = gr["tap"] * rng.uniform(0.95, 1.05, gr["nl"])
+    gr2["gs"] = gr["gs"] + 0.01
+    pf.grid_set_params(grid, *(_d(gr2[k]) for k in ("g", "b", "bsh", "tap", "shift", "gs", "bs")))
+    torch.cuda.synchronize()
+    check_against_oracle(pf, gr2, vm, va, grid=grid)
+
+
+def test_autotune_keeps_results(pf):
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    grid = pf.ybus_build(w)
+    best = pf.grid_autotune(grid, _d(w["vm"][0]), _d(w["va"][0]), reps=3)
+    assert best["ybus_lanes"] in (1, 2, 4, 8, 16, 32) and best["ew_window"] in (64, 128, 256, 512)
+    check_against_oracle(pf, w, w["vm"][0], w["va"][0], grid=grid)
+
+
+def test_null_outputs_rejected(pf):
+    import torch
+    gr, vm, va = CASES["three_bus_plus"]()
+    grid = pf.ybus_build(gr)
+    with pytest.raises(pf.PfError):
+        pf.jac_ybus(grid, _d(vm), _d(va), None, None, None)
+    with pytest.raises(pf.PfError):
+        pf.inj_elementwise(grid, _d(vm), _d(va), None, torch.zeros(4, dtype=torch.float64, device="cuda"))
