@@ -33,8 +33,8 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_OPS_PEAK_G = 152 * 2 * 2.070
 HBM_FALLBACK_GBS = 6800.0
 # FP64 arithmetic instructions per unit of the element-wise Jacobian kernel
-EW_OPS_PER_TERMINAL = 14
-EW_OPS_PER_BUS = 12
+EW_OPS_PER_TERMINAL = 12   # E = V_o conj(U_q) 4, G = conj(Yc) E 4, K = v_q G 2, sum K 2
+EW_OPS_PER_BUS = 31        # fused phasor (sincos 15, 1/v 4, V 2) + diagonal entries and S (10)
 YB_OPS_PER_NNZ = 16
 YB_OPS_PER_ROW = 16
 
@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     return ap.parse_args()
 
 
@@ -141,14 +143,18 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def time_loop(torch, fn, steps, flush):
+def time_loop(torch, fn, steps, flush, name):
+    """Per-step device time (ms) of fn(), L2 flushed before every step outside
+    the events; the loop is an NVTX range so profilers can select it."""
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.nvtx.range_push(name)
     for k in range(steps):
         flush.fill_(float(k))
         ev0[k].record()
         fn()
         ev1[k].record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
 
@@ -175,7 +181,7 @@ def main():
     P = torch.empty(nb, dtype=torch.float64, device="cuda")
     Q = torch.empty_like(P)
     J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
-    cfg = pfgrid.grid_autotune(grid, vm, va, reps=20)
+    cfg = pfgrid.grid_get_config(grid) if args.no_autotune else pfgrid.grid_autotune(grid, vm, va, reps=20)
     flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")   # 512 MB > L2
     T = 2 * nl
 
@@ -188,23 +194,28 @@ def main():
             flush.fill_(0.0)
             f()
     torch.cuda.synchronize()
-    pfgrid.grid_trace_enable(grid, 8 * args.steps + 64)
     sampler = ClockSampler(local)
     time.sleep(0.3)
 
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    t_ew = time_loop(torch, ew, args.steps, flush)
-    tr_ew = pfgrid.grid_trace_read(grid)
-    t_yb = time_loop(torch, yb, args.steps, flush)
-    tr_yb = pfgrid.grid_trace_read(grid)
-    t_iew = time_loop(torch, iew, args.steps, flush)
-    t_iyb = time_loop(torch, iyb, args.steps, flush)
-    tr_inj = pfgrid.grid_trace_read(grid)
+    t_ew = time_loop(torch, ew, args.steps, flush, "ew")
+    t_yb = time_loop(torch, yb, args.steps, flush, "ybus")
+    t_iew = time_loop(torch, iew, args.steps, flush, "inj_ew")
+    t_iyb = time_loop(torch, iyb, args.steps, flush, "inj_ybus")
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    # per-kernel times: the same loops again with the library's launch tracer on
+    pfgrid.grid_trace_enable(grid, 8 * args.steps + 64)
+    time_loop(torch, ew, args.steps, flush, "traced_ew")
+    tr_ew = pfgrid.grid_trace_read(grid)
+    time_loop(torch, yb, args.steps, flush, "traced_ybus")
+    tr_yb = pfgrid.grid_trace_read(grid)
+    time_loop(torch, iew, args.steps, flush, "traced_inj_ew")
+    time_loop(torch, iyb, args.steps, flush, "traced_inj_ybus")
+    tr_inj = pfgrid.grid_trace_read(grid)
     clocks = sampler.stop()
     pfgrid.grid_trace_enable(grid, 0)
     pfgrid.grid_check_error(grid)
@@ -221,7 +232,7 @@ def main():
         return (sum(xs) / len(xs), len(xs)) if xs else (None, 0)
 
     ms_jew, n_jew = kmean(tr_ew, "jac_ew")
-    ms_pu, n_pu = kmean(tr_ew, "phasor_u")
+    ms_pu, n_pu = kmean(tr_yb, "phasor")   # the Ybus path's separate phasor step
     ms_jyb, _ = kmean(tr_yb, "jac_ybus")
     ops_ew = EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb
     achieved = ops_ew / (ms_jew * 1e-3) / 1e9
@@ -237,6 +248,8 @@ def main():
     # end to end through the C ABI with pinned host buffers
     e2e = None
     try:
+        if args.no_e2e:
+            raise RuntimeError("skipped (--no-e2e)")
         hb = lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
         vm_h, va_h, P_h, Q_h, J_h = hb(nb), hb(nb), hb(nb), hb(nb), hb(grid.nnzJ)
         vm_h[:], va_h[:] = w["vm"][0], w["va"][0]
@@ -274,9 +287,8 @@ def main():
                 "ybus_jac_evals_per_s": 1e3 / (sum(t_yb) / len(t_yb)),
                 "elementwise_inj_evals_per_s": 1e3 / (sum(t_iew) / len(t_iew)),
                 "ybus_inj_evals_per_s": 1e3 / (sum(t_iyb) / len(t_iyb)),
-                "kernel_ms": {"phasor_u": ms_pu, "jac_ew": ms_jew, "jac_ybus": ms_jyb,
-                              "phasor_v": kmean(tr_inj, "phasor_v")[0], "inj_ew": kmean(tr_inj, "inj_ew")[0],
-                              "inj_ybus": kmean(tr_inj, "inj_ybus")[0]},
+                "kernel_ms": {"phasor": ms_pu, "jac_ew": ms_jew, "jac_ybus": ms_jyb,
+                              "inj_ew": kmean(tr_inj, "inj_ew")[0], "inj_ybus": kmean(tr_inj, "inj_ybus")[0]},
                 "ybus_fp64_ops_per_launch": YB_OPS_PER_NNZ * grid.nnz + YB_OPS_PER_ROW * nb,
             },
         }

@@ -80,7 +80,8 @@ typedef struct {
 typedef struct {
     int32_t ybus_lanes;     /* lanes per Ybus row in the CSR kernels: 1, 2, 4, 8, 16 or 32 */
     int32_t ybus_block;     /* threads per CTA of the CSR kernels (multiple of 32, <= 512) */
-    int32_t ew_window;      /* buses per CTA window of the element-wise kernels: 64, 128, 256 or 512 */
+    int32_t ew_window;      /* threads per CTA of the element-wise kernels: 128 or 256; a CTA owns a
+                               window of consecutive buses with at most that many buses and terminals */
 } pf_config;
 
 /* Human-readable name of a status code (static string). */
@@ -173,6 +174,18 @@ pf_status jac_elementwise(pf_grid *grid, const double *vm, const double *va, dou
 pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P, double *Q,
                     double *J, pf_stream stream);
 
+/*
+ * The phasor step alone (Sec. IV-B.1 step 1), as run at the start of every
+ * evaluation: for i < n, U[4i..4i+3] = {cos va_i, sin va_i, vm_i, 1/vm_i} and
+ * V[2i..2i+1] = vm_i (cos va_i, sin va_i).  Device pointers; U 32-byte and V
+ * 16-byte aligned (PF_EINVAL otherwise).  sin/cos by a table-driven method
+ * with Cody-Waite reduction (a few ulp; the library sincos for |va| >= 2^16),
+ * 1/vm by two Newton steps from the hardware approximation (vm must be a
+ * normal, nonzero number).  The first call on a device fills a 4 KB constant
+ * table and synchronizes; make it before any stream capture.
+ */
+pf_status phasor(int32_t n, const double *vm, const double *va, double *U, double *V, pf_stream stream);
+
 /* Current launch configuration. */
 pf_status grid_get_config(const pf_grid *grid, pf_config *cfg);
 
@@ -200,23 +213,33 @@ pf_status grid_check_error(pf_grid *grid, pf_stream stream);
 /*
  * Host-only self-check (no GPU needed, nothing allocated on the device):
  * validates `desc` like ybus_build, builds the index structures of the grid
- * and of an element-wise layout with `window` buses per CTA, and verifies
- * every invariant the kernels' memory accesses rely on (index ranges,
- * one slot per bus, one entry per terminal, staging offsets inside the
- * window's slice, shared-memory size).  PF_OK or PF_EINVAL with a message.
+ * and the element-wise windows for CTAs of `window` threads, and verifies
+ * every invariant the kernels' memory accesses rely on (index ranges, sorted
+ * terminal order, parallel-run flags, staging offsets inside each window's
+ * Jacobian slice, bulk-copy alignment, shared-memory size).  PF_OK or
+ * PF_EINVAL with a message.
  */
 pf_status grid_selfcheck(const pf_grid_desc *desc, int32_t window);
+
+/*
+ * Fault injection for tests of the bounded device-side waits (no GPU fault
+ * is involved): moves the arrival counter of the element-wise kernels' grid
+ * barrier out of range, so in the next element-wise evaluation no CTA ever
+ * sees the last arrival; each CTA gives up after 1 s, skips its work and sets
+ * the device error word, and grid_check_error then returns PF_ETIMEOUT and
+ * resets the barrier.  Synchronizes `stream`.
+ */
+pf_status grid_inject_barrier_fault(pf_grid *grid, pf_stream stream);
 
 /* ------------------------------------------------------------ tracing -- */
 
 /* Kernel identifiers reported by the tracer. */
-#define PF_K_PHASOR_U 0      /* phasor step for the Jacobian kernels */
-#define PF_K_PHASOR_V 1      /* phasor step for the injection kernels */
-#define PF_K_INJ_YBUS 2
-#define PF_K_JAC_YBUS 3
-#define PF_K_INJ_EW 4
-#define PF_K_JAC_EW 5
-#define PF_K_COUNT 6
+#define PF_K_PHASOR 0        /* phasor step U = e^{j theta}, V = v U (Sec. IV-B.1 step 1) */
+#define PF_K_INJ_YBUS 1
+#define PF_K_JAC_YBUS 2
+#define PF_K_INJ_EW 3
+#define PF_K_JAC_EW 4
+#define PF_K_COUNT 5
 
 typedef struct {
     int32_t kernel;          /* PF_K_* */

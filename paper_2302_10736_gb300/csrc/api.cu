@@ -110,6 +110,11 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
     if ((st = upload(a, &g->yend, H.yend, s))) return st;
     if ((st = upload(a, &g->ydiag, H.ydiag, s))) return st;
     if ((st = upload(a, &g->tpos, H.tpos, s))) return st;
+    if ((st = upload(a, &g->tp, H.tp, s))) return st;
+    if ((st = upload(a, &g->kd, H.kd, s))) return st;
+    if ((st = upload(a, &g->tnbr, H.tnbr, s))) return st;
+    if ((st = upload(a, &g->town, H.town, s))) return st;
+    PF_CUDA(a.alloc(&g->bus_yd, (size_t)nb));
     if ((st = upload(a, &g->jrp, H.jrp, s))) return st;
     if ((st = upload(a, &g->jci, H.jci, s))) return st;
     PF_CUDA(a.alloc(&g->yv, (size_t)g->nnz));
@@ -120,49 +125,35 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
     PF_CUDA(a.alloc(&g->ph_v, (size_t)nb));
     PF_CUDA(a.alloc(&g->err, 1));
     PF_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+    PF_CUDA(a.alloc(&g->bar, 2));
+    PF_CUDA(cudaMemsetAsync(g->bar, 0, 2 * sizeof(unsigned int), s));
     PF_CUDA(cudaStreamSynchronize(s));  // host vectors stay alive, but keep setup ordered
     return PF_OK;
 }
 
-static void free_ew(Grid *g)
-{
-    EwDev &e = g->ew;
-    void *ps[] = {e.slot_meta, e.slot_kd, e.slot_ysh, e.warp_meta, e.ent_ys, e.ent_yc, e.ent_nbr, e.term_ent};
-    for (void *p : ps) g->arena.release(p);
-    e = EwDev{};
-}
-
-// Build (host), check and upload the element-wise layout for `window` buses
-// per CTA.  The constants are filled by launch_ew_scatter afterwards.
-static pf_status build_ew_layout(Grid *g, int window, cudaStream_t s)
+// Build (host), check and upload the element-wise windows for CTAs of `tb`
+// threads (at most tb buses and tb terminals per window).
+static pf_status build_ew_layout(Grid *g, int tb, cudaStream_t s)
 {
     HostEw E;
-    pf_status st = host_ew(g->topo, window, E);
+    pf_status st = host_ew(g->topo, tb, E);
     if (st) return st;
-    if (ew_jac_smem_bytes(E) > 227 * 1024)
-        return set_error(PF_EUNSUPPORTED, "a window of %d buses needs %zu bytes of shared memory (max 232448); "
-                                          "use a smaller ew_window", window, ew_jac_smem_bytes(E));
+    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true);
+    if (plan.total > kMaxSmem)
+        return set_error(PF_EUNSUPPORTED, "an element-wise window needs %u bytes of shared memory (max %u): a bus "
+                                          "has too many branches for this library", plan.total, kMaxSmem);
 #ifdef PF_SELFCHECK
     if ((st = host_selfcheck(g->topo, E))) return st;
 #endif
-    free_ew(g);
-    EwDev &L = g->ew;
-    L.window = E.window;
-    L.nwin = E.nwin;
-    L.nent = E.nent;
-    L.max_L = E.max_L;
-    DevArena &a = g->arena;
-    if ((st = upload(a, &L.slot_meta, E.meta, s))) return st;
-    if ((st = upload(a, &L.slot_kd, E.kd, s))) return st;
-    if ((st = upload(a, &L.warp_meta, E.wmeta, s))) return st;
-    if ((st = upload(a, &L.ent_nbr, E.nbr, s))) return st;
-    if ((st = upload(a, &L.term_ent, E.term_ent, s))) return st;
-    const size_t nslot = (size_t)E.nwin * E.window;
-    PF_CUDA(a.alloc(&L.slot_ysh, nslot));
-    PF_CUDA(a.alloc(&L.ent_ys, (size_t)E.nent));
-    PF_CUDA(a.alloc(&L.ent_yc, (size_t)E.nent));
-    PF_CUDA(cudaMemsetAsync(L.ent_ys, 0, sizeof(double2) * (size_t)std::max(E.nent, 1), s));
-    PF_CUDA(cudaMemsetAsync(L.ent_yc, 0, sizeof(double2) * (size_t)std::max(E.nent, 1), s));
+    g->arena.release(g->ew.win_bus);
+    g->ew = EwDev{};
+    if ((st = upload(g->arena, &g->ew.win_bus, E.win_bus, s))) return st;
+    g->ew.tb = E.tb;
+    g->ew.nwin = E.nwin;
+    g->ew.max_L = E.max_L;
+    g->ew.max_nt = E.max_nt;
+    g->ew.max_nbus = E.max_nbus;
+    g->ew_resident_jac = g->ew_resident_inj = 0;   // shared-memory needs changed
     PF_CUDA(cudaStreamSynchronize(s));  // E's vectors are freed on return
     return PF_OK;
 }
@@ -172,7 +163,6 @@ pf_status refresh_values(Grid *g, const double *gg, const double *gb, const doub
 {
     PF_CUDA(launch_branch_constants(g, gg, gb, gbsh, gtap, gshift, s));
     PF_CUDA(launch_ybus_values(g, gs, bs, s));
-    PF_CUDA(launch_ew_scatter(g, s));
     return PF_OK;
 }
 
@@ -220,7 +210,7 @@ PF_API pf_status ybus_build(const pf_grid_desc *d, pf_stream stream, pf_grid **o
     g->nl = d->nl;
     g->cfg.ybus_lanes = 4;
     g->cfg.ybus_block = 256;
-    g->cfg.ew_window = 128;
+    g->cfg.ew_window = 256;
     if ((st = host_topology(d->nb, d->nl, d->from, d->to, g->topo))) {
         delete pg;
         return st;
@@ -231,15 +221,10 @@ PF_API pf_status ybus_build(const pf_grid_desc *d, pf_stream stream, pf_grid **o
     size_t len[7] = {(size_t)d->nl, (size_t)d->nl, (size_t)d->nl, (size_t)d->nl, (size_t)d->nl, (size_t)d->nb,
                      (size_t)d->nb};
     try {
+        cudaError_t te = ensure_trig_table();
+        if (te != cudaSuccess) throw cuda_error(te, "ybus_build: trig table");
         if ((st = upload_topology(g, s))) throw st;
-        // default window; fall back to smaller windows when a very high-degree
-        // bus makes the shared-memory staging of a window too large
-        for (int win : {128, 64}) {
-            g->cfg.ew_window = win;
-            st = build_ew_layout(g, win, s);
-            if (st != PF_EUNSUPPORTED) break;
-        }
-        if (st) throw st;
+        if ((st = build_ew_layout(g, g->cfg.ew_window, s))) throw st;
         for (int q = 0; q < 7; ++q) {
             if (!src[q]) continue;
             cudaError_t e = cudaMalloc(&p[q], std::max<size_t>(len[q], 1) * sizeof(double));
@@ -325,8 +310,8 @@ PF_API pf_status inj_ybus(pf_grid *grid, const double *vm, const double *va, dou
     if (!P || !Q) return set_error(PF_EINVAL, "inj_ybus: P or Q is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     {
-        TraceScope t(g, PF_K_PHASOR_V, s);
-        PF_CUDA(launch_phasor_v(g->nb, vm, va, g->ph_v, s));
+        TraceScope t(g, PF_K_PHASOR, s);
+        PF_CUDA(launch_phasor(g->nb, vm, va, g->ph_u, g->ph_v, s));
     }
     {
         TraceScope t(g, PF_K_INJ_YBUS, s);
@@ -345,12 +330,8 @@ PF_API pf_status inj_elementwise(pf_grid *grid, const double *vm, const double *
     if (!P || !Q) return set_error(PF_EINVAL, "inj_elementwise: P or Q is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     {
-        TraceScope t(g, PF_K_PHASOR_V, s);
-        PF_CUDA(launch_phasor_v(g->nb, vm, va, g->ph_v, s));
-    }
-    {
         TraceScope t(g, PF_K_INJ_EW, s);
-        PF_CUDA(launch_inj_ew_vm(g, vm, g->ph_v, P, Q, s));
+        PF_CUDA(launch_inj_ew(g, vm, va, P, Q, s));
     }
     return PF_OK;
 }
@@ -366,8 +347,8 @@ PF_API pf_status jac_ybus(pf_grid *grid, const double *vm, const double *va, dou
     if ((P == nullptr) != (Q == nullptr)) return set_error(PF_EINVAL, "jac_ybus: P and Q must both be set or both NULL");
     cudaStream_t s = (cudaStream_t)stream;
     {
-        TraceScope t(g, PF_K_PHASOR_U, s);
-        PF_CUDA(launch_phasor_u(g->nb, vm, va, g->ph_u, s));
+        TraceScope t(g, PF_K_PHASOR, s);
+        PF_CUDA(launch_phasor(g->nb, vm, va, g->ph_u, g->ph_v, s));
     }
     {
         TraceScope t(g, PF_K_JAC_YBUS, s);
@@ -388,12 +369,8 @@ PF_API pf_status jac_elementwise(pf_grid *grid, const double *vm, const double *
         return set_error(PF_EINVAL, "jac_elementwise: P and Q must both be set or both NULL");
     cudaStream_t s = (cudaStream_t)stream;
     {
-        TraceScope t(g, PF_K_PHASOR_U, s);
-        PF_CUDA(launch_phasor_u(g->nb, vm, va, g->ph_u, s));
-    }
-    {
         TraceScope t(g, PF_K_JAC_EW, s);
-        PF_CUDA(launch_jac_ew(g, g->ph_u, P, Q, J, s));
+        PF_CUDA(launch_jac_ew(g, vm, va, P, Q, J, s));
     }
     return PF_OK;
 }
@@ -428,6 +405,28 @@ PF_API pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, cons
     return PF_OK;
 }
 
+PF_API pf_status phasor(int32_t n, const double *vm, const double *va, double *U, double *V, pf_stream stream)
+{
+    if (n < 0) return set_error(PF_EINVAL, "phasor: n = %d", n);
+    if (n == 0) return PF_OK;
+    if (!vm || !va || !U || !V) return set_error(PF_EINVAL, "phasor: NULL pointer");
+    if (((uintptr_t)U & 31u) || ((uintptr_t)V & 15u))
+        return set_error(PF_EINVAL, "phasor: U must be 32-byte and V 16-byte aligned");
+    PF_CUDA(ensure_trig_table());
+    PF_CUDA(launch_phasor(n, vm, va, reinterpret_cast<double4_32a *>(U), reinterpret_cast<double2 *>(V),
+                          (cudaStream_t)stream));
+    return PF_OK;
+}
+
+PF_API pf_status grid_inject_barrier_fault(pf_grid *grid, pf_stream stream)
+{
+    if (!grid) return set_error(PF_EINVAL, "grid_inject_barrier_fault: grid is NULL");
+    const unsigned int phantom = 0x80000000u;   // arrivals never reach nblocks - 1
+    PF_CUDA(cudaMemcpyAsync(grid->g.bar, &phantom, sizeof(phantom), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    PF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));   // `phantom` is a stack variable
+    return PF_OK;
+}
+
 PF_API pf_status grid_get_config(const pf_grid *grid, pf_config *cfg)
 {
     if (!grid || !cfg) return set_error(PF_EINVAL, "grid_get_config: NULL argument");
@@ -445,11 +444,10 @@ PF_API pf_status grid_set_config(pf_grid *grid, const pf_config *cfg, pf_stream 
         return set_error(PF_EINVAL, "ybus_block must be a multiple of 32 in [32, 512]");
     Grid *g = &grid->g;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cfg->ew_window != g->ew.window) {
+    if (cfg->ew_window != g->ew.tb) {
         pf_status st = build_ew_layout(g, cfg->ew_window, s);
-        if (st) g->cfg.ew_window = g->ew.window;
+        if (st) g->cfg.ew_window = g->ew.tb;
         if (st) return st;
-        PF_CUDA(launch_ew_scatter(g, s));
         PF_CUDA(cudaStreamSynchronize(s));
     }
     g->cfg = *cfg;
@@ -465,6 +463,8 @@ PF_API pf_status grid_check_error(pf_grid *grid, pf_stream stream)
     PF_CUDA(cudaStreamSynchronize(s));
     if (h == DEV_OK) return PF_OK;
     PF_CUDA(cudaMemsetAsync(grid->g.err, 0, sizeof(int), s));
+    // a kernel that gave up may have left the grid barrier half-way: start it afresh
+    PF_CUDA(cudaMemsetAsync(grid->g.bar, 0, 2 * sizeof(unsigned int), s));
     PF_CUDA(cudaStreamSynchronize(s));
     if (h == DEV_TIMEOUT) return set_error(PF_ETIMEOUT, "a device-side wait gave up (error word %d)", h);
     return set_error(PF_EDEVICE, "a kernel reported device error word %d", h);
@@ -545,7 +545,7 @@ PF_API pf_status grid_autotune(pf_grid *grid, const double *vm, const double *va
         }
     g->cfg.ybus_lanes = cfg.ybus_lanes;
     g->cfg.ybus_block = cfg.ybus_block;
-    for (int win : {64, 128, 256, 512}) {
+    for (int win : {128, 256}) {
         pf_config c2 = g->cfg;
         c2.ew_window = win;
         if ((st = grid_set_config(grid, &c2, stream))) {
@@ -576,7 +576,7 @@ out:
 
 PF_API const char *pf_kernel_name(int32_t k)
 {
-    static const char *names[PF_K_COUNT] = {"phasor_u", "phasor_v", "inj_ybus", "jac_ybus", "inj_ew", "jac_ew"};
+    static const char *names[PF_K_COUNT] = {"phasor", "inj_ybus", "jac_ybus", "inj_ew", "jac_ew"};
     return (k >= 0 && k < PF_K_COUNT) ? names[k] : "?";
 }
 

@@ -1,15 +1,17 @@
 // host_layout.cpp - host-only construction of every index structure the
 // kernels use, plus a self-check of the invariants their memory accesses rely
-// on (run on the CPU by the tests, and in debug builds before upload).
+// on (run on the CPU by the tests, and in PF_SELFCHECK builds before upload).
 //
 //   sorted terminals   terminal t = 2l (h = from[l] end) or 2l+1 (k = to[l]
 //                      end), ordered by (owner bus, other bus, branch): the
-//                      terminal-to-bus permutation of the reduction (Eq. 7)
+//                      terminal-to-bus permutation of the reduction (Eq. 7);
+//                      a bus's terminals, and the parallel runs among them,
+//                      are contiguous
 //   Ybus pattern       row i = {i} U {other bus of i's terminals}, sorted;
 //                      parallel branches share an entry; per entry the range
 //                      of sorted terminals whose stamps it sums
 //   J pattern          closed form of Alg. 2 (see include/pfgrid.h)
-//   element-wise       sliced-ELL by bus window (see EwLayout)
+//   element-wise       windows of consecutive buses for one CTA each
 #include <algorithm>
 #include <cstdint>
 
@@ -80,7 +82,14 @@ pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo
     }
     H.nnz = H.rp[nb];
     H.tpos.assign(T, 0);
-    for (int p = 0; p < T; ++p) H.tpos[H.tsort[p]] = p;
+    H.tnbr.assign(T, make_int2(0, 0));
+    H.town.assign(T, 0);
+    for (int p = 0; p < T; ++p) {
+        const int t = H.tsort[p];
+        H.tpos[t] = p;
+        H.tnbr[p] = make_int2(H.other(t), H.tkpos[t] | (H.taccum[t] ? EW_ACCUM : 0));
+        H.town[p] = H.owner(t);
+    }
     const int nnz = H.nnz;
     H.jrp.assign(2 * (size_t)nb + 1, 0);
     H.jci.assign(4 * (size_t)nnz, 0);
@@ -97,60 +106,34 @@ pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo
     return PF_OK;
 }
 
-pf_status host_ew(const HostTopo &H, int window, HostEw &E)
+pf_status host_ew(const HostTopo &H, int tb, HostEw &E)
 {
-    if (window != 64 && window != 128 && window != 256 && window != 512)
-        return set_error(PF_EINVAL, "ew_window must be 64, 128, 256 or 512 (got %d)", window);
-    const int nb = H.nb, T = 2 * H.nl;
+    if (tb != 128 && tb != 256)
+        return set_error(PF_EINVAL, "ew_window (threads per element-wise CTA) must be 128 or 256 (got %d)", tb);
+    const int nb = H.nb;
     E = HostEw{};
-    E.window = window;
-    E.nwin = (nb + window - 1) / window;
-    const int nslot = E.nwin * window, nwarp = nslot / 32;
-    E.meta.assign(nslot, make_int4(-1, 0, 0, 0));
-    E.kd.assign(nslot, 0);
-    E.wmeta.assign(nwarp, make_int2(0, 0));
-    E.term_ent.assign(T, 0);
-    std::vector<int> order(window);
-    long long nent = 0;
-    for (int w = 0; w < E.nwin; ++w) {
-        const int b0 = w * window, b1 = std::min(b0 + window, nb), n = b1 - b0;
-        for (int r = 0; r < n; ++r) order[r] = b0 + r;
-        std::stable_sort(order.begin(), order.begin() + n,
-                         [&](int x, int y) { return (H.tp[x + 1] - H.tp[x]) > (H.tp[y + 1] - H.tp[y]); });
-        E.max_L = std::max(E.max_L, 2 * (H.rp[b1] - H.rp[b0]));
-        for (int r = 0; r < n; ++r) {
-            const int bus = order[r];
-            E.meta[w * window + r] =
-                make_int4(bus, H.tp[bus + 1] - H.tp[bus], 2 * (H.rp[bus] - H.rp[b0]), H.rp[bus + 1] - H.rp[bus]);
-            E.kd[w * window + r] = H.kd[bus];
+    E.tb = tb;
+    E.win_bus.push_back(0);
+    int b = 0;
+    while (b < nb) {
+        const int b0 = b;
+        int nt = 0;
+        // greedy: at most tb buses and tb terminals; a bus with more than tb
+        // terminals still forms a window by itself
+        while (b < nb && b - b0 < tb) {
+            const int t_here = H.tp[b + 1] - H.tp[b];
+            if (b > b0 && nt + t_here > tb) break;
+            nt += t_here;
+            ++b;
         }
-        for (int wi = 0; wi < window / 32; ++wi) {
-            int mx = 0;
-            for (int l = 0; l < 32; ++l) mx = std::max(mx, E.meta[w * window + wi * 32 + l].y);
-            E.wmeta[w * (window / 32) + wi] = make_int2((int)nent, mx);
-            nent += 32LL * mx;
-        }
+        E.win_bus.push_back(b);
+        E.max_nt = std::max(E.max_nt, nt);
+        E.max_nbus = std::max(E.max_nbus, b - b0);
+        E.max_L = std::max(E.max_L, 2 * (H.rp[b] - H.rp[b0]));
     }
-    if (nent > INT32_MAX / 2) return set_error(PF_EUNSUPPORTED, "element-wise layout too large (%lld entries)", nent);
-    E.nent = (int)nent;
-    E.nbr.assign((size_t)nent, make_int2(0, 0));
-    for (int sl = 0; sl < nslot; ++sl) {
-        const int bus = E.meta[sl].x;
-        if (bus < 0) continue;
-        const int2 wm = E.wmeta[sl / 32];
-        const int lane = sl % 32;
-        for (int k = 0; k < E.meta[sl].y; ++k) {
-            const int t = H.tsort[H.tp[bus] + k];
-            const int e = wm.x + 32 * k + lane;
-            E.term_ent[t] = e;
-            E.nbr[e] = make_int2(H.other(t), H.tkpos[t] | (H.taccum[t] ? EW_ACCUM : 0));
-        }
-        for (int k = E.meta[sl].y; k < wm.y; ++k) E.nbr[wm.x + 32 * k + lane] = make_int2(bus, 0);
-    }
+    E.nwin = (int)E.win_bus.size() - 1;
     return PF_OK;
 }
-
-size_t ew_jac_smem_bytes(const HostEw &E) { return (size_t)(2 * E.max_L + 2 * E.window) * sizeof(double); }
 
 #define CHECK(cond, ...)                                       \
     do {                                                       \
@@ -163,8 +146,10 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
     // Ybus CSR
     CHECK((int)H.rp.size() == nb + 1 && H.rp[0] == 0 && H.rp[nb] == nnz, "rowptr ends");
     CHECK((long long)nnz * 4 < INT32_MAX, "nnzJ exceeds int32");
+    CHECK((int)H.tp.size() == nb + 1 && H.tp[0] == 0 && H.tp[nb] == T, "terminal offsets");
     for (int i = 0; i < nb; ++i) {
         CHECK(H.rp[i + 1] > H.rp[i], "row %d empty (diagonal missing)", i);
+        CHECK(H.tp[i + 1] >= H.tp[i], "terminal offsets not monotone at %d", i);
         for (int e = H.rp[i]; e < H.rp[i + 1]; ++e) {
             CHECK(H.ci[e] >= 0 && H.ci[e] < nb, "colidx out of range at %d", e);
             if (e > H.rp[i]) CHECK(H.ci[e] > H.ci[e - 1], "row %d not strictly sorted", i);
@@ -179,50 +164,40 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
         CHECK(H.ci[H.rp[o] + H.tkpos[t]] == q, "kpos column t=%d", t);
         CHECK(H.tsort[H.tpos[t]] == t, "tpos inverse t=%d", t);
     }
-    // element-wise layout: every access of k_jac_ew / k_inj_ew stays in bounds
-    const int W = E.window, nslot = E.nwin * W;
-    CHECK((int)E.meta.size() == nslot && (int)E.kd.size() == nslot && (int)E.wmeta.size() == nslot / 32,
-          "slot array sizes");
-    std::vector<int> seen_bus(nb, 0), seen_ent(E.nent, 0);
+    for (int p = 0; p < T; ++p) {
+        const int o = H.town[p], q = H.tnbr[p].x, kp = H.tnbr[p].y & EW_KMASK;
+        CHECK(o >= 0 && o < nb && p >= H.tp[o] && p < H.tp[o + 1], "owner of sorted terminal %d", p);
+        CHECK(q >= 0 && q < nb && q != o, "other bus of sorted terminal %d", p);
+        CHECK(kp >= 0 && kp < H.rp[o + 1] - H.rp[o] && kp != H.kd[o], "slot of sorted terminal %d", p);
+        const bool acc = (H.tnbr[p].y & EW_ACCUM) != 0;
+        CHECK(acc == (p > H.tp[o] && H.tnbr[p - 1].x == q), "parallel-run flag of sorted terminal %d", p);
+    }
+    // element-wise windows: every access of k_jac_ew / k_inj_ew stays in bounds
+    CHECK(E.nwin == (int)E.win_bus.size() - 1 && E.win_bus[0] == 0 && E.win_bus[E.nwin] == nb, "window cover");
     for (int w = 0; w < E.nwin; ++w) {
-        const int b0 = w * W, b1 = std::min(b0 + W, nb);
+        const int b0 = E.win_bus[w], b1 = E.win_bus[w + 1];
+        const int nbus = b1 - b0, nt = H.tp[b1] - H.tp[b0];
         const int L = 2 * (H.rp[b1] - H.rp[b0]);
-        CHECK(L <= E.max_L, "window %d L > max_L", w);
-        for (int r = 0; r < W; ++r) {
-            const int sl = w * W + r;
-            const int4 m = E.meta[sl];
-            const int2 wm = E.wmeta[sl / 32];
-            if (m.x < 0) {
-                CHECK(r >= b1 - b0, "empty slot inside a full window %d", w);
-                continue;
-            }
-            CHECK(m.x >= b0 && m.x < b1, "slot bus outside window");
-            CHECK(++seen_bus[m.x] == 1, "bus %d in two slots", m.x);
-            CHECK(m.y == H.tp[m.x + 1] - H.tp[m.x] && m.y <= wm.y, "terminal count slot %d", sl);
-            CHECK(m.w == H.rp[m.x + 1] - H.rp[m.x], "row length slot %d", sl);
-            CHECK(m.z >= 0 && m.z + 2 * m.w <= L, "row slice outside the window slice, slot %d", sl);
-            CHECK(E.kd[sl] >= 0 && E.kd[sl] < m.w, "diag pos slot %d", sl);
-            for (int k = 0; k < wm.y; ++k) {
-                const long long e = (long long)wm.x + 32LL * k + (sl % 32);
-                CHECK(e >= 0 && e < E.nent, "entry %lld outside [0, %d)", e, E.nent);
-                const int2 nq = E.nbr[e];
-                CHECK(nq.x >= 0 && nq.x < nb, "gather index out of range at entry %lld", e);
-                if (k < m.y) {
-                    CHECK(++seen_ent[e] == 1, "entry %lld used twice", e);
-                    const int kp = nq.y & EW_KMASK;
-                    CHECK(kp >= 0 && kp < m.w && kp != E.kd[sl], "kpos entry %lld", e);
-                    CHECK(m.z + kp + m.w < L, "staging index entry %lld", e);
-                }
+        CHECK(nbus >= 1 && nbus <= E.tb && nbus <= E.max_nbus, "window %d bus count %d", w, nbus);
+        CHECK(nt <= E.max_nt && (nt <= E.tb || nbus == 1), "window %d terminal count %d", w, nt);
+        CHECK(L >= 2 && L <= E.max_L, "window %d slice length", w);
+        // bulk-store constraints: the J slices start on 16 bytes and are 16-byte multiples
+        CHECK((2LL * H.rp[b0]) % 2 == 0 && (8LL * L) % 16 == 0, "window %d J slice alignment", w);
+        for (int o = b0; o < b1; ++o) {
+            const int lrow = 2 * (H.rp[o] - H.rp[b0]), d = H.rp[o + 1] - H.rp[o];
+            CHECK(lrow >= 0 && lrow + 2 * d <= L, "bus %d row slice outside the window slice", o);
+            CHECK(lrow + H.kd[o] + d < L, "bus %d diagonal staging index", o);
+            for (int p = H.tp[o]; p < H.tp[o + 1]; ++p) {
+                const int kp = H.tnbr[p].y & EW_KMASK;
+                CHECK(lrow + kp + d < L, "terminal %d staging index", p);
+                CHECK(p - H.tp[b0] >= 0 && p - H.tp[b0] < E.max_nt, "terminal %d local index", p);
             }
         }
     }
-    for (int i = 0; i < nb; ++i) CHECK(seen_bus[i] == 1, "bus %d has no slot", i);
-    for (int t = 0; t < T; ++t) {
-        const int e = E.term_ent[t];
-        CHECK(e >= 0 && e < E.nent && seen_ent[e] == 1, "terminal %d entry", t);
-        CHECK(E.nbr[e].x == H.other(t), "terminal %d gather index", t);
-    }
-    CHECK(ew_jac_smem_bytes(E) <= 227 * 1024, "window needs %zu bytes of shared memory", ew_jac_smem_bytes(E));
+    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true);
+    CHECK(plan.total <= kMaxSmem, "a window needs %u bytes of shared memory", plan.total);
+    CHECK(plan.yd % 16 == 0 && plan.kg % 16 == 0 && plan.jst % 16 == 0 && plan.pq % 16 == 0,
+          "shared-memory plan alignment");
     return PF_OK;
 }
 

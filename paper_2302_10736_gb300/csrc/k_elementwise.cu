@@ -1,184 +1,345 @@
-// k_elementwise.cu - element-wise method (Sec. II-B, IV-C) on the GPU.
+// k_elementwise.cu - element-wise method (Sec. II-B, IV-C) on the GPU, one
+// cooperative kernel per evaluation.
 //
-// Evaluation.  Each branch terminal t (owner bus o, other bus q) evaluates
-// its flow from two precomputed constants (see k_setup.cu):
-//     S_t = v_o^2 conj(Ys_t) + K_t,   K_t = conj(Yc_t) V_o conj(V_q)      (Eqs. 5-6)
+// The element-wise method has no separate phasor step (the paper evaluates
+// the angle-difference terms inside the per-line loop); here each CTA first
+// forms the phasors of its own buses (phase 1), a grid-wide barrier makes
+// them visible, and the evaluation and reduction run in phase 2.
+//
+// Evaluation step (Listing 1's per-element loop, one terminal per thread).
+// Terminal t of a branch (owner bus o, other bus q) has precomputed constants
+// Ys_t, Yc_t (k_setup.cu) such that its complex power (Eqs. 5-6) is
+//     S_t = v_o^2 conj(Ys_t) + K_t,   K_t = conj(Yc_t) V_o conj(V_q),
 // where V_o conj(V_q) = v_o v_q e^{j(theta_o - theta_q)} carries the sine and
-// cosine of the angle difference in registers (formed from the per-bus
-// phasors, no per-branch trigonometry).  Its 8 partials (16 per branch):
+// cosine of the angle difference in registers (from per-bus phasors: no
+// per-branch trigonometry).  Its 8 partials (16 per branch):
 //     dS_t/dtheta_q = -j K_t            dS_t/dv_q = K_t / v_q = conj(Yc_t) V_o conj(U_q)
 //     dS_t/dtheta_o = +j K_t            dS_t/dv_o = 2 v_o conj(Ys_t) + K_t / v_o
+// The thread computes E = V_o conj(U_q), G = conj(Yc_t) E (= dS_t/dv_q) and
+// K_t = v_q G: 10 FP64 instructions, all 32 lanes busy.
 //
-// Reduction (Eq. 7 and the copy-add of Fig. 2, without atomics).  The
-// terminals are laid out by bus window (one CTA) and, inside a window, by
-// owner bus sorted on terminal count, so a lane owns one bus and every one of
-// its terminals: the segmented sum onto the bus and onto its diagonal
-// Jacobian slot runs in registers in a fixed order, and each off-diagonal
-// slot (o, q) is written by that lane alone (parallel branches, adjacent in
-// the layout, are added in order).  The 32 lanes of a warp own buses with
-// equally many terminals, so the evaluation runs with all lanes busy and the
-// k-th terminals of a warp are read with coalesced loads.
-//     S_o           = v_o^2 conj(sum Ys + y_sh,o) + sum K
+// Reduction step (Eq. 7 and the copy-add of Fig. 2, without atomics).
+// Terminals are stored sorted by (owner, other bus), so a CTA owns a window of
+// consecutive buses together with all of their terminals: the off-diagonal
+// slot (o, q) is written by the terminal's thread (parallel branches,
+// adjacent in the sorted order, are added by the owner's thread below), and
+// one thread per bus sums its terminals' K in a fixed order:
+//     S_o           = v_o^2 conj(Yd_o) + sum K
 //     dS_o/dtheta_o = j sum K
-//     dS_o/dv_o     = 2 v_o conj(sum Ys + y_sh,o) + (sum K) / v_o
-// A window's Jacobian rows are one contiguous slice of each of the P and Q
-// halves of J (canonical layout), so the CTA stages its slice in shared
-// memory and writes it back with coalesced stores, together with P and Q.
+//     dS_o/dv_o     = 2 v_o conj(Yd_o) + (sum K) / v_o
+// with Yd_o = sum_t Ys_t + y_sh,o, a parameter-only per-bus constant formed at
+// setup from the same terminal constants.
+//
+// GB300 data movement.  The static data of a CTA's first window is loaded
+// before the grid barrier, so it overlaps the other CTAs' phase 1.  A window's
+// Jacobian rows are one contiguous slice of each of the P and Q halves of J
+// (canonical layout): it is assembled in shared memory and written back with
+// TMA bulk stores, together with P and Q.
+#include "fastmath.cuh"
 #include "pf_internal.h"
+#include "ptx.cuh"
 
 namespace pf {
 
-__global__ void __launch_bounds__(512) k_jac_ew(int nb, int nnz, int window, const int *__restrict__ rp,
-                                                const int4 *__restrict__ slot_meta, const int *__restrict__ slot_kd,
-                                                const double2 *__restrict__ slot_ysh,
-                                                const int2 *__restrict__ warp_meta,
-                                                const double2 *__restrict__ ent_ys,
-                                                const double2 *__restrict__ ent_yc,
-                                                const int2 *__restrict__ ent_nbr, const double4_32a *__restrict__ U,
-                                                double *__restrict__ P, double *__restrict__ Q,
-                                                double *__restrict__ J)
+constexpr uint64_t kBarrierLimitNs = 1000000000ull;   // bounded grid-barrier wait (1 s), then PF_ETIMEOUT
+
+struct EwArgs {
+    int nwin, nnz, max_nbus, max_nt, max_L, aligned;
+    const int *win_bus, *tp, *rp, *kd;
+    const double2 *yd, *tcoup;
+    const int2 *tnbr;
+    const int *town;
+    const double *vm, *va;
+    const double2 *trig;
+    double4_32a *U;
+    double2 *V;
+    double *P, *Q, *J;
+    unsigned int *bar;
+    int *err;
+};
+
+// Write x[b0 .. b1) from shared staging `s` (element b0 at s[b0 & 1]) to
+// global memory: an unaligned head and tail element by plain stores, the
+// 16-byte aligned middle by one bulk store (issued by the calling thread).
+__device__ __forceinline__ void store_range(double *x, const double *s, int b0, int b1)
 {
-    extern __shared__ double stg[];
-    const int w = blockIdx.x;
-    const int b0 = w * window, b1 = min(b0 + window, nb);
-    const int r0 = rp[b0];
-    const int L = 2 * (rp[b1] - r0);
-    double *stP = stg + 2 * L;
-    double *stQ = stP + window;
-    const int slot = w * window + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const int4 meta = slot_meta[slot];
-    if (meta.x >= 0) {
-        const int o = meta.x, nt = meta.y, lrow = meta.z, d = meta.w;
-        const double4_32a uo = U[o];
-        const double v = uo.z, iv = uo.w;
-        const double Vr = v * uo.x, Vi = v * uo.y;
-        const int2 wm = warp_meta[slot >> 5];
-        double sKr = 0.0, sKi = 0.0, sYr = 0.0, sYi = 0.0;
-        for (int k = 0; k < nt; ++k) {
-            const int e = wm.x + 32 * k + lane;
-            const double2 ys = ent_ys[e];
-            const double2 yc = ent_yc[e];
-            const int2 nq = ent_nbr[e];
-            const double4_32a uq = U[nq.x];
-            const double Er = fma(Vr, uq.x, Vi * uq.y);     // V_o conj(U_q)
-            const double Ei = fma(Vi, uq.x, -Vr * uq.y);
-            const double Gr = fma(yc.x, Er, yc.y * Ei);     // conj(Yc) E = dS_t/dv_q
-            const double Gi = fma(yc.x, Ei, -yc.y * Er);
-            const double Kr = uq.z * Gr, Ki = uq.z * Gi;    // K_t = v_q G
-            sKr += Kr;
-            sKi += Ki;
-            sYr += ys.x;
-            sYi += ys.y;
-            const int pos = lrow + (nq.y & EW_KMASK);
-            if (nq.y & EW_ACCUM) {  // second and later branch of a parallel run
-                stg[pos] += Ki;
-                stg[pos + d] += Gr;
-                stg[L + pos] -= Kr;
-                stg[L + pos + d] += Gi;
+    const int par = b0 & 1;
+    if (par) x[b0] = s[1];
+    const int ge = b0 + par;
+    const int cm = (b1 - ge) & ~1;
+    if (cm > 0) bulk_s2g(x + ge, s + 2 * par, 8u * (uint32_t)cm);
+    if ((b1 - ge) & 1) x[b1 - 1] = s[b1 - 1 - b0 + par];
+}
+
+// At most 48 registers (5 CTAs of 256 or 10 of 128 threads per SM): every
+// window of the 70k-bus grid gets its own co-resident CTA.
+template <bool JAC>
+__global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
+{
+    extern __shared__ __align__(16) char smem[];
+    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, JAC ? a.max_L : 0, JAC);
+    int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
+    double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
+    double2 *skg = reinterpret_cast<double2 *>(smem + sp.kg);
+    int *skp = reinterpret_cast<int *>(smem + sp.kp);
+    double *jst = reinterpret_cast<double *>(smem + sp.jst);
+    double *spq = reinterpret_cast<double *>(smem + sp.pq);
+    double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
+    const int tid = threadIdx.x, TB = blockDim.x;
+
+    // ---- phase 1: phasors of this CTA's buses (Sec. IV-B.1 step 1) ----
+    // All loads of the first window (its vm, va, and the static data phase 2
+    // needs) are issued together, before any arithmetic.
+    const int w0 = blockIdx.x;
+    double2 yc = make_double2(0.0, 0.0);
+    int2 nq = make_int2(0, 0);
+    int ol = 0;
+    {
+        const int b0 = a.win_bus[w0], b1 = a.win_bus[w0 + 1], t0 = a.tp[b0], nt = a.tp[b1] - t0;
+        const int r0 = a.rp[b0];
+        double th = 0.0, v = 0.0;
+        int4 bm = make_int4(0, 0, 0, 0);
+        double2 y = make_double2(0.0, 0.0);
+        const bool mine = tid < b1 - b0;
+        if (mine) {
+            const int o = b0 + tid, rs = a.rp[o];
+            th = a.va[o];
+            v = a.vm[o];
+            bm = make_int4(2 * (rs - r0), a.rp[o + 1] - rs, a.kd[o], a.tp[o] - t0);
+            y = a.yd[o];
+        }
+        if (tid < nt) {
+            yc = a.tcoup[t0 + tid];
+            nq = a.tnbr[t0 + tid];
+            ol = a.town[t0 + tid] - b0;
+        }
+        for (int k = tid; k < kTrigN; k += TB) tab[k] = a.trig[k];
+        __syncthreads();
+        if (mine) {
+            double s, c;
+            fast_sincos(th, tab, &s, &c);
+            if (JAC) a.U[b0 + tid] = make_double4_32a(c, s, v, fast_rcp(v));
+            a.V[b0 + tid] = make_double2(v * c, v * s);
+            sbm[tid] = bm;
+            syd[tid] = y;
+        }
+    }
+    for (int w = w0 + gridDim.x; w < a.nwin; w += gridDim.x) {   // further windows (large grids)
+        const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1];
+        for (int o = b0 + tid; o < b1; o += TB) {
+            double s, c;
+            fast_sincos(a.va[o], tab, &s, &c);
+            const double v = a.vm[o];
+            if (JAC) a.U[o] = make_double4_32a(c, s, v, fast_rcp(v));
+            a.V[o] = make_double2(v * c, v * s);
+        }
+    }
+    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBarrierLimitNs)) return;
+
+    // ---- phase 2: evaluation and reduction, window by window ----
+    for (int w = w0; w < a.nwin; w += gridDim.x) {
+        const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
+        const int t0 = a.tp[b0], nt = a.tp[b1] - t0;
+        const int r0 = a.rp[b0], L = JAC ? 2 * (a.rp[b1] - r0) : 0;
+        const bool first = w == w0;
+        if (!first) {   // previous window's stores have read shared memory (thread 0 waited)
+            __syncthreads();
+            for (int b = tid; b < nbus; b += TB) {
+                const int o = b0 + b, rs = a.rp[o];
+                sbm[b] = make_int4(2 * (rs - r0), a.rp[o + 1] - rs, a.kd[o], a.tp[o] - t0);
+                syd[b] = a.yd[o];
+            }
+            __syncthreads();
+        }
+        // the bus thread's own phasor, fetched together with the gathers
+        double4_32a ub = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        double vb = 0.0;
+        if (tid < nbus) {
+            if (JAC)
+                ub = a.U[b0 + tid];
+            else
+                vb = a.vm[b0 + tid];
+        }
+        for (int i = tid; i < nt; i += TB) {
+            if (!(first && i == tid)) {
+                yc = a.tcoup[t0 + i];
+                nq = a.tnbr[t0 + i];
+                ol = a.town[t0 + i] - b0;
+            }
+            const double2 Vo = a.V[b0 + ol];
+            if (JAC) {
+                const double4_32a uq = a.U[nq.x];
+                const double Er = fma(Vo.x, uq.x, Vo.y * uq.y);   // V_o conj(U_q)
+                const double Ei = fma(Vo.y, uq.x, -Vo.x * uq.y);
+                const double Gr = fma(yc.x, Er, yc.y * Ei);       // conj(Yc) E = dS_t/dv_q
+                const double Gi = fma(yc.x, Ei, -yc.y * Er);
+                const double Kr = uq.z * Gr, Ki = uq.z * Gi;       // K_t = v_q G
+                skg[2 * i] = make_double2(Kr, Ki);
+                skg[2 * i + 1] = make_double2(Gr, Gi);
+                skp[i] = nq.y;
+                if (!(nq.y & EW_ACCUM)) {
+                    const int4 bm = sbm[ol];
+                    const int pos = bm.x + (nq.y & EW_KMASK), d = bm.y;
+                    jst[pos] = Ki;           // J11 = Re(-j K)
+                    jst[pos + d] = Gr;       // J12
+                    jst[L + pos] = -Kr;      // J21 = Im(-j K)
+                    jst[L + pos + d] = Gi;   // J22
+                }
             } else {
-                stg[pos] = Ki;           // J11: Re(-j K)
-                stg[pos + d] = Gr;       // J12
-                stg[L + pos] = -Kr;      // J21: Im(-j K)
-                stg[L + pos + d] = Gi;   // J22
+                const double2 Vq = a.V[nq.x];
+                const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y);   // V_o conj(V_q)
+                const double Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
+                skg[i] = make_double2(fma(yc.x, Wr, yc.y * Wi), fma(yc.x, Wi, -yc.y * Wr));   // K_t
             }
         }
-        const double2 ysh = slot_ysh[slot];
-        const double Ydr = sYr + ysh.x, Ydi = sYi + ysh.y;
-        const double v2 = v * v, tv = v + v;
-        const int pos = lrow + slot_kd[slot];
-        stg[pos] = -sKi;                          // Re(j sum K)
-        stg[pos + d] = fma(tv, Ydr, sKr * iv);
-        stg[L + pos] = sKr;                       // Im(j sum K)
-        stg[L + pos + d] = fma(-tv, Ydi, sKi * iv);
-        stP[o - b0] = fma(v2, Ydr, sKr);
-        stQ[o - b0] = fma(-v2, Ydi, sKi);
-    }
-    __syncthreads();
-    double *Jp = J + 2 * (long long)r0;
-    double *Jq = J + 2 * (long long)nnz + 2 * (long long)r0;
-    for (int x = threadIdx.x; x < L; x += blockDim.x) {
-        Jp[x] = stg[x];
-        Jq[x] = stg[L + x];
-    }
-    if (P) {
-        for (int x = threadIdx.x; x < b1 - b0; x += blockDim.x) {
-            P[b0 + x] = stP[x];
-            Q[b0 + x] = stQ[x];
+        __syncthreads();
+
+        const int pqs = (int)sp.pqs, par = b0 & 1;
+        for (int b = tid; b < nbus; b += TB) {
+            const int4 bm = sbm[b];
+            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+            const double2 y = syd[b];
+            double sKr = 0.0, sKi = 0.0;
+            if (JAC) {
+                const int d = bm.y;
+                for (int i = bm.w; i < tend; ++i) {
+                    const double2 K = skg[2 * i];
+                    sKr += K.x;
+                    sKi += K.y;
+                    const int kp = skp[i];
+                    if (kp & EW_ACCUM) {   // later branch of a parallel run: add into the run's slot
+                        const double2 G = skg[2 * i + 1];
+                        const int pos = bm.x + (kp & EW_KMASK);
+                        jst[pos] += K.y;
+                        jst[pos + d] += G.x;
+                        jst[L + pos] -= K.x;
+                        jst[L + pos + d] += G.y;
+                    }
+                }
+                const double4_32a uo = b == tid ? ub : a.U[b0 + b];
+                const double v = uo.z, iv = uo.w, v2 = v * v, tv = v + v;
+                const int pos = bm.x + bm.z;
+                jst[pos] = -sKi;                         // Re(j sum K)
+                jst[pos + d] = fma(tv, y.x, sKr * iv);
+                jst[L + pos] = sKr;                      // Im(j sum K)
+                jst[L + pos + d] = fma(-tv, y.y, sKi * iv);
+                spq[b + par] = fma(v2, y.x, sKr);
+                spq[pqs + b + par] = fma(-v2, y.y, sKi);
+            } else {
+                for (int i = bm.w; i < tend; ++i) {
+                    sKr += skg[i].x;
+                    sKi += skg[i].y;
+                }
+                const double v = b == tid ? vb : a.vm[b0 + b], v2 = v * v;
+                spq[b + par] = fma(v2, y.x, sKr);
+                spq[pqs + b + par] = fma(-v2, y.y, sKi);
+            }
+        }
+
+        if (a.aligned) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                if (JAC) {
+                    bulk_s2g(a.J + 2 * (long long)r0, jst, 8u * (uint32_t)L);
+                    bulk_s2g(a.J + 2 * (long long)a.nnz + 2 * (long long)r0, jst + L, 8u * (uint32_t)L);
+                }
+                if (a.P) {
+                    store_range(a.P, spq, b0, b1);
+                    store_range(a.Q, spq + pqs, b0, b1);
+                }
+                bulk_commit();
+                bulk_wait_read();
+            }
+        } else {
+            __syncthreads();
+            if (JAC) {
+                double *Jp = a.J + 2 * (long long)r0;
+                double *Jq = a.J + 2 * (long long)a.nnz + 2 * (long long)r0;
+                for (int x = tid; x < L; x += TB) {
+                    Jp[x] = jst[x];
+                    Jq[x] = jst[L + x];
+                }
+            }
+            if (a.P)
+                for (int b = tid; b < nbus; b += TB) {
+                    a.P[b0 + b] = spq[b + par];
+                    a.Q[b0 + b] = spq[pqs + b + par];
+                }
         }
     }
 }
 
-__global__ void __launch_bounds__(512) k_inj_ew(int nb, int window, const int4 *__restrict__ slot_meta,
-                                                const double2 *__restrict__ slot_ysh,
-                                                const int2 *__restrict__ warp_meta,
-                                                const double2 *__restrict__ ent_ys,
-                                                const double2 *__restrict__ ent_yc,
-                                                const int2 *__restrict__ ent_nbr, const double *__restrict__ vm,
-                                                const double2 *__restrict__ V, double *__restrict__ P,
-                                                double *__restrict__ Q)
-{
-    extern __shared__ double stg[];
-    const int w = blockIdx.x;
-    const int b0 = w * window, b1 = min(b0 + window, nb);
-    double *stP = stg;
-    double *stQ = stg + window;
-    const int slot = w * window + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const int4 meta = slot_meta[slot];
-    if (meta.x >= 0) {
-        const int o = meta.x, nt = meta.y;
-        const double2 Vo = V[o];
-        const int2 wm = warp_meta[slot >> 5];
-        double sKr = 0.0, sKi = 0.0, sYr = 0.0, sYi = 0.0;
-        for (int k = 0; k < nt; ++k) {
-            const int e = wm.x + 32 * k + lane;
-            const double2 ys = ent_ys[e];
-            const double2 yc = ent_yc[e];
-            const double2 Vq = V[ent_nbr[e].x];
-            const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y);  // V_o conj(V_q)
-            const double Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
-            sKr += fma(yc.x, Wr, yc.y * Wi);                // conj(Yc) W
-            sKi += fma(yc.x, Wi, -yc.y * Wr);
-            sYr += ys.x;
-            sYi += ys.y;
-        }
-        const double2 ysh = slot_ysh[slot];
-        const double v = vm[o], v2 = v * v;
-        stP[o - b0] = fma(v2, sYr + ysh.x, sKr);
-        stQ[o - b0] = fma(-v2, sYi + ysh.y, sKi);
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < b1 - b0; x += blockDim.x) {
-        P[b0 + x] = stP[x];
-        Q[b0 + x] = stQ[x];
-    }
-}
+static bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-static size_t jac_smem(const Grid *g) { return (size_t)(2 * g->ew.max_L + 2 * g->ew.window) * sizeof(double); }
-
-cudaError_t launch_jac_ew(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s)
+template <bool JAC>
+static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
+                             cudaStream_t s)
 {
     const EwDev &L = g->ew;
     if (L.nwin == 0) return cudaSuccess;
-    const size_t smem = jac_smem(g);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_jac_ew, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    const EwSmem sp = ew_smem_plan(L.max_nbus, L.max_nt, JAC ? L.max_L : 0, JAC);
+    const size_t smem = sp.total + kTrigN * sizeof(double2);
+    cudaError_t e;
+    int &resident = JAC ? g->ew_resident_jac : g->ew_resident_inj;
+    if (resident == 0) {   // CTAs that fit at once (cooperative launch bound), cached per layout
+        if (smem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(k_ew<JAC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+            return e;
+        int per_sm = 0, dev = 0, nsm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ew<JAC>, L.tb, smem))) return e;
+        if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
+            return e;
+        resident = per_sm * nsm;
+        if (resident <= 0) return cudaErrorInvalidConfiguration;
     }
-    k_jac_ew<<<L.nwin, L.window, smem, s>>>(g->nb, g->nnz, L.window, g->rp, L.slot_meta, L.slot_kd, L.slot_ysh,
-                                            L.warp_meta, L.ent_ys, L.ent_yc, L.ent_nbr, U, P, Q, J);
-    return cudaGetLastError();
+    EwArgs a;
+    a.nwin = L.nwin;
+    a.nnz = g->nnz;
+    a.max_nbus = L.max_nbus;
+    a.max_nt = L.max_nt;
+    a.max_L = L.max_L;
+    a.aligned = (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
+    a.win_bus = L.win_bus;
+    a.tp = g->tp;
+    a.rp = g->rp;
+    a.kd = g->kd;
+    a.yd = g->bus_yd;
+    a.tcoup = g->tcoup;
+    a.tnbr = g->tnbr;
+    a.town = g->town;
+    a.vm = vm;
+    a.va = va;
+    a.trig = trig_table();
+    a.U = g->ph_u;
+    a.V = g->ph_v;
+    a.P = P;
+    a.Q = Q;
+    a.J = J;
+    a.bar = g->bar;
+    a.err = g->err;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min(L.nwin, resident));
+    cfg.blockDim = dim3((unsigned)L.tb);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_ew<JAC>, a);
 }
 
-cudaError_t launch_inj_ew_vm(const Grid *g, const double *vm, const double2 *V, double *P, double *Q, cudaStream_t s)
+cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
+                          cudaStream_t s)
 {
-    const EwDev &L = g->ew;
-    if (L.nwin == 0) return cudaSuccess;
-    k_inj_ew<<<L.nwin, L.window, 2 * L.window * sizeof(double), s>>>(g->nb, L.window, L.slot_meta, L.slot_ysh,
-                                                                     L.warp_meta, L.ent_ys, L.ent_yc, L.ent_nbr,
-                                                                     vm, V, P, Q);
-    return cudaGetLastError();
+    return launch_ew<true>(g, vm, va, P, Q, J, s);
+}
+
+cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s)
+{
+    return launch_ew<false>(g, vm, va, P, Q, nullptr, s);
 }
 
 }  // namespace pf

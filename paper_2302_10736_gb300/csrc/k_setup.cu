@@ -11,7 +11,11 @@
 // of (i, j) is the sum of the coupling constants of the terminals (i -> j)
 // and the diagonal is the bus shunt plus the self constants of all terminals
 // of bus i, summed in a fixed order (no atomics).
+#include <mutex>
+
+#include "fastmath.cuh"
 #include "pf_internal.h"
+#include "ptx.cuh"
 
 namespace pf {
 
@@ -65,48 +69,83 @@ __global__ void k_ybus_values(int nnz, const int *__restrict__ ybeg, const int *
     yv[e] = acc;
 }
 
-__global__ void k_ew_scatter(int T, const int *__restrict__ term_ent, const int *__restrict__ tpos,
-                             const double2 *__restrict__ tself, const double2 *__restrict__ tcoup,
-                             double2 *__restrict__ ent_ys, double2 *__restrict__ ent_yc)
-{
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    const int e = term_ent[t], p = tpos[t];
-    ent_ys[e] = tself[p];
-    ent_yc[e] = tcoup[p];
-}
-
-__global__ void k_ew_slot_ysh(int nslot, const int4 *__restrict__ meta, const double2 *__restrict__ bus_ysh,
-                              double2 *__restrict__ slot_ysh)
-{
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nslot) return;
-    const int bus = meta[s].x;
-    slot_ysh[s] = bus >= 0 ? bus_ysh[bus] : make_double2(0.0, 0.0);
-}
-
-// Phasor step (Sec. IV-B.1 step 1): U = e^{j theta}; stored with v and 1/v
-// for the Jacobian kernels, or V = v U for the injection kernels.
-__global__ void k_phasor_u(int nb, const double *__restrict__ vm, const double *__restrict__ va,
-                           double4_32a *__restrict__ out)
+// Per-bus self sum Yd = y_sh + sum of the self constants of the bus's
+// terminals (sorted order): the parameter-only part of Eq. 7.
+__global__ void k_bus_yd(int nb, const int *__restrict__ tp, const double2 *__restrict__ tself,
+                         const double2 *__restrict__ bus_ysh, double2 *__restrict__ yd)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
-    double s, c;
-    sincos(va[i], &s, &c);
-    const double v = vm[i];
-    out[i] = make_double4_32a(c, s, v, __drcp_rn(v));
+    double2 acc = bus_ysh[i];
+    for (int p = tp[i]; p < tp[i + 1]; ++p) {
+        acc.x += tself[p].x;
+        acc.y += tself[p].y;
+    }
+    yd[i] = acc;
 }
 
-__global__ void k_phasor_v(int nb, const double *__restrict__ vm, const double *__restrict__ va,
-                           double2 *__restrict__ out)
+__device__ double2 g_trig_tab[kTrigN];
+
+// (cos, sin)(2 pi k / 256) by the library's sincospi (exact argument k / 128)
+__global__ void k_trig_table_init()
 {
+    const int k = threadIdx.x;
+    double s, c;
+    sincospi(2.0 * k / kTrigN, &s, &c);
+    g_trig_tab[k] = make_double2(c, s);
+}
+
+// Phasor step (Sec. IV-B.1 step 1): U = e^{j theta} with v and 1/v (gathered
+// by the Jacobian kernels) and V = v U (gathered by the injection kernels and
+// by the element-wise Jacobian for the owner bus).  22 FP64 instructions per
+// bus (fast_sincos 15, fast_rcp 4 + the hardware approximation, V 2).
+__global__ void __launch_bounds__(kTrigN) k_phasor(int nb, const double *__restrict__ vm,
+                                                   const double *__restrict__ va, double4_32a *__restrict__ U,
+                                                   double2 *__restrict__ V)
+{
+    __shared__ double2 tab[kTrigN];
+    pdl_launch_dependents();   // the evaluation kernel may start loading its static data now
+    tab[threadIdx.x] = g_trig_tab[threadIdx.x];
+    __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     double s, c;
-    sincos(va[i], &s, &c);
+    fast_sincos(va[i], tab, &s, &c);
     const double v = vm[i];
-    out[i] = make_double2(v * c, v * s);
+    U[i] = make_double4_32a(c, s, v, fast_rcp(v));
+    V[i] = make_double2(v * c, v * s);
+}
+
+// Fill the trig table once per device (synchronous, first use only).
+static std::mutex g_trig_mu;
+static const double2 *g_trig_ptr[256] = {nullptr};
+
+const double2 *trig_table()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+    std::lock_guard<std::mutex> lk(g_trig_mu);
+    return g_trig_ptr[dev];
+}
+
+cudaError_t ensure_trig_table()
+{
+    static std::mutex &mu = g_trig_mu;
+    static bool done[256] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+    k_trig_table_init<<<1, kTrigN>>>();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    void *p = nullptr;
+    if ((e = cudaGetSymbolAddress(&p, g_trig_tab)) != cudaSuccess) return e;
+    g_trig_ptr[dev] = static_cast<const double2 *>(p);
+    done[dev] = true;
+    return cudaSuccess;
 }
 
 cudaError_t launch_branch_constants(Grid *g, const double *gg, const double *gb, const double *gbsh,
@@ -124,28 +163,13 @@ cudaError_t launch_ybus_values(Grid *g, const double *gs, const double *bs, cuda
     if (g->nnz > 0)
         k_ybus_values<<<nblk(g->nnz, 256), 256, 0, s>>>(g->nnz, g->ybeg, g->yend, g->ydiag, g->tself, g->tcoup,
                                                         g->bus_ysh, g->yv);
+    if (g->nb > 0) k_bus_yd<<<nblk(g->nb, 256), 256, 0, s>>>(g->nb, g->tp, g->tself, g->bus_ysh, g->bus_yd);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ew_scatter(Grid *g, cudaStream_t s)
+cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32a *U, double2 *V, cudaStream_t s)
 {
-    const int T = 2 * g->nl, nslot = g->ew.nwin * g->ew.window;
-    if (T > 0)
-        k_ew_scatter<<<nblk(T, 256), 256, 0, s>>>(T, g->ew.term_ent, g->tpos, g->tself, g->tcoup, g->ew.ent_ys,
-                                                  g->ew.ent_yc);
-    if (nslot > 0) k_ew_slot_ysh<<<nblk(nslot, 256), 256, 0, s>>>(nslot, g->ew.slot_meta, g->bus_ysh, g->ew.slot_ysh);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_phasor_u(int nb, const double *vm, const double *va, double4_32a *out, cudaStream_t s)
-{
-    if (nb > 0) k_phasor_u<<<nblk(nb, 256), 256, 0, s>>>(nb, vm, va, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_phasor_v(int nb, const double *vm, const double *va, double2 *out, cudaStream_t s)
-{
-    if (nb > 0) k_phasor_v<<<nblk(nb, 256), 256, 0, s>>>(nb, vm, va, out);
+    if (nb > 0) k_phasor<<<nblk(nb, kTrigN), kTrigN, 0, s>>>(nb, vm, va, U, V);
     return cudaGetLastError();
 }
 

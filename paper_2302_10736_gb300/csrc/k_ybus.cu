@@ -8,35 +8,72 @@
 // the lane that holds it after a W-lane shuffle reduction.
 //
 // Per structural (i, j), with U_j = e^{j theta_j} and YU = Y_ij U_j:
-//     dS_i/dv_j     = V_i conj(YU)                         (Eq. 4, off-diagonal term)
-//     dS_i/dtheta_j = -j V_i conj(Y_ij V_j) = -j v_j dS_i/dv_j   (Eq. 3)
+//     dS_i/dv_j     = V_i conj(YU)                               (Eq. 4)
+//     dS_i/dtheta_j = -j V_i conj(Y_ij V_j) = -j v_j dS_i/dv_j    (Eq. 3)
 //     I_i          += v_j YU
 // and on the diagonal additionally  +j V_i conj(I_i)  and  +conj(I_i) U_i.
 // (Alg. 1 as printed carries the opposite sign on dS/dtheta; Eq. 3 is used.)
 // Values are written straight into the canonical J layout, i.e. the copy of
 // Alg. 2 with its index arrays in closed form.
+//
+// The row's first kChunk entries (column index and Y value, static data) are
+// loaded before the programmatic-dependent-launch wait; the phasor gathers of
+// a chunk are issued together before its arithmetic.
 #include "pf_internal.h"
+#include "ptx.cuh"
 
 namespace pf {
 
+constexpr int kChunk = 4;
+
 template <int W>
 __global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                    const double2 *__restrict__ Y, const double2 *__restrict__ V,
-                                                    double *__restrict__ P, double *__restrict__ Q)
+                                                   const double2 *__restrict__ Y, const double2 *__restrict__ V,
+                                                   double *__restrict__ P, double *__restrict__ Q)
 {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int row = (int)(gid / W), lane = (int)(gid % W);
     const bool valid = row < nb;
-    double Ir = 0.0, Ii = 0.0;
+    int rs = 0, d = 0;
+    int jj[kChunk];
+    double2 yy[kChunk];
     if (valid) {
-        const int e1 = rp[row + 1];
-        for (int e = rp[row] + lane; e < e1; e += W) {
-            const double2 y = Y[e];
-            const double2 v = V[ci[e]];
-            Ir = fma(y.x, v.x, Ir);
-            Ir = fma(-y.y, v.y, Ir);
-            Ii = fma(y.x, v.y, Ii);
-            Ii = fma(y.y, v.x, Ii);
+        rs = rp[row];
+        d = rp[row + 1] - rs;
+    }
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+        const int k = lane + W * j;
+        if (k < d) {
+            jj[j] = ci[rs + k];
+            yy[j] = Y[rs + k];
+        }
+    }
+    pdl_wait();
+    double Ir = 0.0, Ii = 0.0;
+    for (int k0 = lane; k0 < d; k0 += W * kChunk) {
+        if (k0 != lane) {
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) {
+                const int k = k0 + W * j;
+                if (k < d) {
+                    jj[j] = ci[rs + k];
+                    yy[j] = Y[rs + k];
+                }
+            }
+        }
+        double2 vv[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+            if (k0 + W * j < d) vv[j] = V[jj[j]];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            if (k0 + W * j < d) {
+                Ir = fma(yy[j].x, vv[j].x, Ir);
+                Ir = fma(-yy[j].y, vv[j].y, Ir);
+                Ii = fma(yy[j].x, vv[j].y, Ii);
+                Ii = fma(yy[j].y, vv[j].x, Ii);
+            }
         }
     }
 #pragma unroll
@@ -53,47 +90,75 @@ __global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict_
 
 template <int W>
 __global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__restrict__ rp,
-                                                    const int *__restrict__ ci, const double2 *__restrict__ Y,
-                                                    const double4_32a *__restrict__ U, double *__restrict__ P,
-                                                    double *__restrict__ Q, double *__restrict__ J)
+                                                   const int *__restrict__ ci, const double2 *__restrict__ Y,
+                                                   const double4_32a *__restrict__ U, double *__restrict__ P,
+                                                   double *__restrict__ Q, double *__restrict__ J)
 {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int row = (int)(gid / W), lane = (int)(gid % W);
     const bool valid = row < nb;
-    double Ir = 0.0, Ii = 0.0;
-    double dTr = 0.0, dTi = 0.0, dVr = 0.0, dVi = 0.0;  // diagonal partials (lane that owns it)
-    int kd = -1, rs = 0, d = 0;
-    double4_32a ui = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    int rs = 0, d = 0;
+    int jj[kChunk];
+    double2 yy[kChunk];
     if (valid) {
         rs = rp[row];
         d = rp[row + 1] - rs;
-        ui = U[row];
-        const double Vr = ui.z * ui.x, Vi = ui.z * ui.y;
-        for (int k = lane; k < d; k += W) {
-            const int e = rs + k;
-            const int j = ci[e];
-            const double2 y = Y[e];
-            const double4_32a uj = U[j];
-            const double YUr = fma(y.x, uj.x, -y.y * uj.y);
-            const double YUi = fma(y.x, uj.y, y.y * uj.x);
-            const double sVr = fma(Vr, YUr, Vi * YUi);    // V_i conj(YU)
-            const double sVi = fma(Vi, YUr, -Vr * YUi);
-            const double vj = uj.z;
-            Ir = fma(vj, YUr, Ir);
-            Ii = fma(vj, YUi, Ii);
-            const double sTr = vj * sVi, sTi = -vj * sVr;   // -j v_j dS/dv_j
-            if (j == row) {
-                kd = k;
-                dTr = sTr;
-                dTi = sTi;
-                dVr = sVr;
-                dVi = sVi;
-            } else {
-                const int p = 2 * rs + k;
-                J[p] = sTr;
-                J[p + d] = sVr;
-                J[2 * nnz + p] = sTi;
-                J[2 * nnz + p + d] = sVi;
+    }
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+        const int k = lane + W * j;
+        if (k < d) {
+            jj[j] = ci[rs + k];
+            yy[j] = Y[rs + k];
+        }
+    }
+    pdl_wait();
+    double Ir = 0.0, Ii = 0.0;
+    double dTr = 0.0, dTi = 0.0, dVr = 0.0, dVi = 0.0;  // diagonal partials (lane that owns it)
+    int kd = -1;
+    double4_32a ui = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    if (valid) ui = U[row];
+    const double Vr = ui.z * ui.x, Vi = ui.z * ui.y;
+    for (int k0 = lane; k0 < d; k0 += W * kChunk) {
+        if (k0 != lane) {
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) {
+                const int k = k0 + W * j;
+                if (k < d) {
+                    jj[j] = ci[rs + k];
+                    yy[j] = Y[rs + k];
+                }
+            }
+        }
+        double4_32a uu[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+            if (k0 + W * j < d) uu[j] = U[jj[j]];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            const int k = k0 + W * j;
+            if (k < d) {
+                const double YUr = fma(yy[j].x, uu[j].x, -yy[j].y * uu[j].y);
+                const double YUi = fma(yy[j].x, uu[j].y, yy[j].y * uu[j].x);
+                const double sVr = fma(Vr, YUr, Vi * YUi);    // V_i conj(YU)
+                const double sVi = fma(Vi, YUr, -Vr * YUi);
+                const double vj = uu[j].z;
+                Ir = fma(vj, YUr, Ir);
+                Ii = fma(vj, YUi, Ii);
+                const double sTr = vj * sVi, sTi = -vj * sVr;   // -j v_j dS/dv_j
+                if (jj[j] == row) {
+                    kd = k;
+                    dTr = sTr;
+                    dTi = sTi;
+                    dVr = sVr;
+                    dVi = sVi;
+                } else {
+                    const int p = 2 * rs + k;
+                    J[p] = sTr;
+                    J[p + d] = sVr;
+                    J[2 * nnz + p] = sTi;
+                    J[2 * nnz + p + d] = sVi;
+                }
             }
         }
     }
@@ -103,7 +168,6 @@ __global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__
         Ii += __shfl_xor_sync(0xffffffffu, Ii, off, W);
     }
     if (!valid) return;
-    const double Vr = ui.z * ui.x, Vi = ui.z * ui.y;
     const double Sr = fma(Vr, Ir, Vi * Ii), Si = fma(Vi, Ir, -Vr * Ii);
     if (kd >= 0) {
         dTr -= Si;                           // + j S_i  (= j V_i conj(I_i))
@@ -127,8 +191,8 @@ static cudaError_t inj_w(const Grid *g, const double2 *V, double *P, double *Q, 
 {
     const long long threads = (long long)g->nb * W;
     const int blk = g->cfg.ybus_block;
-    k_inj_ybus<W><<<(int)((threads + blk - 1) / blk), blk, 0, s>>>(g->nb, g->rp, g->ci, g->yv, V, P, Q);
-    return cudaGetLastError();
+    return launch_k(k_inj_ybus<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, (const int *)g->rp,
+                    (const int *)g->ci, (const double2 *)g->yv, V, P, Q);
 }
 
 template <int W>
@@ -136,8 +200,8 @@ static cudaError_t jac_w(const Grid *g, const double4_32a *U, double *P, double 
 {
     const long long threads = (long long)g->nb * W;
     const int blk = g->cfg.ybus_block;
-    k_jac_ybus<W><<<(int)((threads + blk - 1) / blk), blk, 0, s>>>(g->nb, g->nnz, g->rp, g->ci, g->yv, U, P, Q, J);
-    return cudaGetLastError();
+    return launch_k(k_jac_ybus<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, g->nnz,
+                    (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, U, P, Q, J);
 }
 
 cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s)

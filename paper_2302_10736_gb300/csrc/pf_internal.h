@@ -26,13 +26,15 @@ pf_status cuda_error(cudaError_t e, const char *what);
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADINDEX = 2 };
 
 // ------------------------------------------------- device buffer owner --
+// Every buffer gets 64 bytes of slack so vector loads of the last element
+// never leave the allocation.
 struct DevArena {
     std::vector<void *> ptrs;
     template <class T>
     cudaError_t alloc(T **p, size_t n)
     {
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, n > 0 ? n * sizeof(T) : 16);
+        cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 64);
         if (e == cudaSuccess) {
             ptrs.push_back(q);
             *p = static_cast<T *>(q);
@@ -45,14 +47,18 @@ struct DevArena {
 
 // ------------------------------------------------ host index structures --
 // Topology-only structures, built once on the host (host_layout.cpp).
+enum : int { EW_ACCUM = 0x40000000, EW_KMASK = 0x3fffffff };
+
 struct HostTopo {
     int nb = 0, nl = 0, nnz = 0;
     std::vector<int> from, to;
-    std::vector<int> tp;        // [nb+1] terminals of bus i: tsort[tp[i] .. tp[i+1])
+    std::vector<int> tp;        // [nb+1] terminals of bus i: sorted positions tp[i] .. tp[i+1]
     std::vector<int> tsort;     // [2nl] terminal ids sorted by (owner, other, branch)
     std::vector<int> tpos;      // [2nl] sorted position of terminal t
     std::vector<int> tkpos;     // [2nl] position of the other bus in the owner's Ybus row
     std::vector<int> taccum;    // [2nl] 1 if not the first terminal of its (owner, other) run
+    std::vector<int2> tnbr;     // [2nl] by sorted position: {other bus, kpos | EW_ACCUM}
+    std::vector<int> town;      // [2nl] by sorted position: owner bus
     std::vector<int> rp, ci;    // Ybus CSR pattern
     std::vector<int> ybeg, yend, ydiag;  // per nnz: sorted-terminal stamp range; row if diagonal else -1
     std::vector<int> kd;        // [nb] position of the diagonal in row i
@@ -61,38 +67,51 @@ struct HostTopo {
     int other(int t) const { return (t & 1) ? from[t >> 1] : to[t >> 1]; }
 };
 
-// Element-wise layout (sliced-ELL by bus window): one CTA per window of W
-// buses, one bus per thread; inside a window buses are ordered by terminal
-// count (descending) so the 32 lanes of a warp loop over equally many
-// terminals; entry (warp, k, lane) lives at warp_ebase + 32 k + lane, so the
-// k-th terminals of a warp's buses are read with coalesced loads.
+// Element-wise windows: consecutive bus ranges whose terminals (contiguous in
+// sorted order) are evaluated one per thread by one CTA of `tb` threads; a
+// window holds at most tb buses and at most tb terminals (a single bus with
+// more terminals gets a window of its own and its terminals are looped over).
 struct HostEw {
-    int window = 0, nwin = 0, nent = 0;
-    int max_L = 0;                 // max over windows of 2 * (Ybus nnz of the window's rows)
-    std::vector<int4> meta;        // [nwin*W] {bus or -1, terminal count, 2*(rp[bus]-rp[b0]), row length d}
-    std::vector<int> kd;           // [nwin*W] diagonal position in the slot bus's row
-    std::vector<int2> wmeta;       // [nwin*W/32] {entry base, max terminal count}
-    std::vector<int2> nbr;         // [nent] {other bus, kpos | EW_ACCUM}
-    std::vector<int> term_ent;     // [2nl] entry of terminal t
+    int tb = 0, nwin = 0;
+    int max_L = 0;      // max over windows of 2 * (Ybus nnz of the window's rows)
+    int max_nt = 0;     // max terminals in a window
+    int max_nbus = 0;   // max buses in a window
+    std::vector<int> win_bus;   // [nwin+1]
 };
-enum : int { EW_ACCUM = 0x40000000, EW_KMASK = 0x3fffffff };
 
 pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo &H);
-pf_status host_ew(const HostTopo &H, int window, HostEw &E);
+pf_status host_ew(const HostTopo &H, int tb, HostEw &E);
 pf_status host_selfcheck(const HostTopo &H, const HostEw &E);
-size_t ew_jac_smem_bytes(const HostEw &E);
+
+// Shared-memory plan of the element-wise kernels (byte offsets, 16-aligned):
+//   bm  int4    [max_nbus]   per bus {J-slice row offset, row length, diagonal position, first terminal}
+//   yd  double2 [max_nbus]   per bus self sum
+//   kg  double2 [2 max_nt]   per terminal K and G (injection kernel: K only)
+//   kp  int     [max_nt]     per terminal slot position | EW_ACCUM (Jacobian kernel)
+//   jst double  [2 max_L]    the window's J slice (P half, then Q half)
+//   pq  double  [2 pqs]      P then Q of the window, parity-aligned with global memory
+struct EwSmem {
+    uint32_t bm, yd, kg, kp, jst, pq, pqs, total;
+};
+__host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max_L, bool jac)
+{
+    EwSmem p;
+    p.pqs = ((uint32_t)max_nbus + 3u) & ~1u;   // even, >= max_nbus + 2
+    p.bm = 0;
+    p.yd = p.bm + 16u * (uint32_t)max_nbus;
+    p.kg = p.yd + 16u * (uint32_t)max_nbus;
+    p.kp = p.kg + (jac ? 32u : 16u) * (uint32_t)max_nt;
+    p.jst = p.kp + (jac ? ((4u * (uint32_t)max_nt + 15u) & ~15u) : 0u);
+    p.pq = p.jst + (jac ? 16u * (uint32_t)max_L : 0u);
+    p.total = p.pq + 16u * p.pqs;
+    return p;
+}
+constexpr uint32_t kMaxSmem = 227u * 1024u;
 
 // ------------------------------------------------ device-side structure --
 struct EwDev {
-    int window = 0, nwin = 0, nent = 0, max_L = 0;
-    int4 *slot_meta = nullptr;
-    int *slot_kd = nullptr;
-    double2 *slot_ysh = nullptr;   // [nwin*W] bus shunt of the slot's bus
-    int2 *warp_meta = nullptr;
-    double2 *ent_ys = nullptr;     // [nent] self constant of the terminal
-    double2 *ent_yc = nullptr;     // [nent] coupling constant of the terminal
-    int2 *ent_nbr = nullptr;
-    int *term_ent = nullptr;
+    int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0;
+    int *win_bus = nullptr;   // [nwin+1]
 };
 
 struct Grid {
@@ -104,13 +123,20 @@ struct Grid {
     int *rp = nullptr, *ci = nullptr;
     double2 *yv = nullptr;
     int *ybeg = nullptr, *yend = nullptr, *ydiag = nullptr;
+    int *kd = nullptr;                     // [nb] diagonal position per row
     // J pattern (device)
     int *jrp = nullptr, *jci = nullptr;
-    // terminal constants in sorted-terminal order (device)
+    // terminals in sorted order (device)
+    int *tp = nullptr;                     // [nb+1]
     double2 *tself = nullptr, *tcoup = nullptr;
-    int *tpos = nullptr;
-    double2 *bus_ysh = nullptr;
+    int2 *tnbr = nullptr;                  // {other bus, kpos | EW_ACCUM}
+    int *town = nullptr;                   // owner bus
+    int *tpos = nullptr;                   // [2nl] sorted position of terminal t
+    double2 *bus_ysh = nullptr;            // [nb]
+    double2 *bus_yd = nullptr;             // [nb] bus shunt + sum of the bus's terminal self constants
     EwDev ew;
+    int ew_resident_jac = 0, ew_resident_inj = 0;   // co-resident CTAs of the fused kernels (0 = unknown)
+    unsigned int *bar = nullptr;   // grid-barrier state {arrivals, generation}
     // per-call workspace (device)
     double4_32a *ph_u = nullptr;   // [nb] {cos, sin, v, 1/v}
     double2 *ph_v = nullptr;       // [nb] V = v e^{j theta}
@@ -142,17 +168,39 @@ struct TraceScope {
     }
 };
 
-// kernel launchers (k_*.cu); each returns cudaGetLastError() of its launch(es)
+// Launch with cudaLaunchKernelEx; `pdl` allows programmatic dependent launch
+// (the kernel may start while the preceding kernel in the stream finishes and
+// must call griddepcontrol.wait before reading that kernel's results).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
+                            Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// kernel launchers (k_*.cu); each returns the status of its launch(es)
 cudaError_t launch_branch_constants(Grid *g, const double *gg, const double *gb, const double *gbsh,
                                     const double *gtap, const double *gshift, cudaStream_t s);
 cudaError_t launch_ybus_values(Grid *g, const double *gs, const double *bs, cudaStream_t s);
-cudaError_t launch_ew_scatter(Grid *g, cudaStream_t s);
-cudaError_t launch_phasor_u(int nb, const double *vm, const double *va, double4_32a *out, cudaStream_t s);
-cudaError_t launch_phasor_v(int nb, const double *vm, const double *va, double2 *out, cudaStream_t s);
+cudaError_t ensure_trig_table();   // once per device, synchronous
+const double2 *trig_table();       // device address of the (cos, sin) table of fastmath.cuh
+cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32a *U, double2 *V, cudaStream_t s);
 cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ybus(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s);
-cudaError_t launch_inj_ew_vm(const Grid *g, const double *vm, const double2 *V, double *P, double *Q, cudaStream_t s);
-cudaError_t launch_jac_ew(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s);
+// element-wise: one cooperative kernel (phasors of each window's buses, grid barrier, evaluation)
+cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s);
+cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
+                          cudaStream_t s);
 
 }  // namespace pf
 

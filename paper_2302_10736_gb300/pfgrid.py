@@ -72,6 +72,8 @@ def _load():
         "grid_trace_enable": (st, [vp, i32]),
         "grid_trace_read": (st, [vp, ctypes.POINTER(pf_trace_rec), i32, pi32]),
         "grid_selfcheck": (st, [ctypes.POINTER(pf_grid_desc), i32]),
+        "phasor": (st, [i32, vp, vp, vp, vp, vp]),
+        "grid_inject_barrier_fault": (st, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -285,6 +287,17 @@ def eval_host(grid, method, vm, va, P, Q, J, stream=None):
     m = {"ybus": 0, "elementwise": 1}.get(method, method)
     vp = lambda a: ctypes.c_void_p(a.ctypes.data)
     _check(_lib.eval_host(grid.handle, int(m), vp(vm), vp(va), vp(P), vp(Q), vp(J), _stream(stream)), "eval_host")
+
+
+def phasor(vm, va, U, V, stream=None):
+    """Phasor step alone: U [n, 4] = (cos, sin, vm, 1/vm), V [n, 2] = vm (cos, sin)."""
+    n = vm.numel()
+    _check(_lib.phasor(n, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(U, "U", 4 * n), _dptr(V, "V", 2 * n),
+                       _stream(stream)), "phasor")
+
+
+def grid_inject_barrier_fault(grid, stream=None):
+    _check(_lib.grid_inject_barrier_fault(grid.handle, _stream(stream)), "grid_inject_barrier_fault")
 
 
 def grid_get_config(grid):

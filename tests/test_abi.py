@@ -70,7 +70,7 @@ def test_oversized_grid_rejected(pf):
     assert st == 7
 
 
-@pytest.mark.parametrize("window", [64, 128, 256, 512])
+@pytest.mark.parametrize("window", [128, 256])
 @pytest.mark.parametrize("case", ["three_bus_plus", "parallel_star", "single_bus", "empty", "c1", "c2", "c3", "c4"])
 def test_layout_selfcheck(pf, case, window):
     """Every index the kernels read or write stays inside its buffer (host check)."""

@@ -138,7 +138,7 @@ def test_large_angles(pf):
 
 
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
-@pytest.mark.parametrize("window", [64, 128, 256, 512])
+@pytest.mark.parametrize("window", [128, 256])
 def test_every_launch_configuration(pf, lanes, window):
     gr = random_grid(1500, 2100, 10, shift_max=0.2)
     vm, va = random_state(1500, 10)
@@ -194,8 +194,60 @@ def test_autotune_keeps_results(pf):
     w = synth.workload(1)
     grid = pf.ybus_build(w)
     best = pf.grid_autotune(grid, _d(w["vm"][0]), _d(w["va"][0]), reps=3)
-    assert best["ybus_lanes"] in (1, 2, 4, 8, 16, 32) and best["ew_window"] in (64, 128, 256, 512)
+    assert best["ybus_lanes"] in (1, 2, 4, 8, 16, 32) and best["ew_window"] in (128, 256)
     check_against_oracle(pf, w, w["vm"][0], w["va"][0], grid=grid)
+
+
+def test_phasor_accuracy_against_library(pf):
+    """The table-driven sin/cos and the Newton reciprocal of the phasor step
+    against the CUDA library (torch float64 cos/sin and division on the GPU):
+    absolute error within 4 ulp of 1, reciprocal within 1 ulp."""
+    import torch
+    rng = np.random.default_rng(3)
+    step = 2 * np.pi / 256
+    va = np.concatenate([
+        rng.normal(0, 0.25, 20000), rng.uniform(-700, 700, 20000),
+        np.arange(-3000, 3000) * step, np.arange(-3000, 3000) * step + step / 2,   # table nodes, midpoints
+        [0.0, -0.0, 1e-300, -1e-300, np.pi, -np.pi, np.pi / 2, 65535.9, -65535.9, 65536.0, 1e6, -3e7, 1e300],
+    ])
+    vm = rng.uniform(0.5, 1.5, va.size)
+    n = va.size
+    U = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    V = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+    vm_d, va_d = _d(vm), _d(va)
+    pf.phasor(vm_d, va_d, U, V)
+    c_ref, s_ref = torch.cos(va_d), torch.sin(va_d)
+    ulp1 = np.finfo(np.float64).eps
+    assert float((U[:, 0] - c_ref).abs().max()) <= 4 * ulp1
+    assert float((U[:, 1] - s_ref).abs().max()) <= 4 * ulp1
+    assert torch.equal(U[:, 2], vm_d)
+    rel = ((U[:, 3] - 1.0 / vm_d) / (1.0 / vm_d)).abs().max()
+    assert float(rel) <= ulp1
+    assert float((V[:, 0] - vm_d * c_ref).abs().max()) <= 8 * ulp1
+    assert float((V[:, 1] - vm_d * s_ref).abs().max()) <= 8 * ulp1
+
+
+def test_bounded_barrier_wait_reports_timeout(pf):
+    """A grid barrier whose arrivals never complete (host-injected phantom
+    arrival) ends after its 1 s limit with PF_ETIMEOUT; the context stays
+    usable and the next evaluation is correct."""
+    import time
+
+    import torch
+    gr = random_grid(3000, 4100, 14)
+    vm, va = random_state(3000, 14)
+    grid = pf.ybus_build(gr)
+    P = torch.empty(grid.nb, dtype=torch.float64, device="cuda")
+    Q = torch.empty_like(P)
+    J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+    pf.grid_inject_barrier_fault(grid)
+    t0 = time.time()
+    pf.jac_elementwise(grid, _d(vm), _d(va), P, Q, J)
+    with pytest.raises(pf.PfError) as ei:
+        pf.grid_check_error(grid)
+    assert ei.value.status == pf.PF_ETIMEOUT
+    assert 0.9 < time.time() - t0 < 30.0
+    check_against_oracle(pf, gr, vm, va, grid=grid)
 
 
 def test_null_outputs_rejected(pf):
