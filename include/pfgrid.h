@@ -186,6 +186,25 @@ pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, const doubl
  */
 pf_status phasor(int32_t n, const double *vm, const double *va, double *U, double *V, pf_stream stream);
 
+/*
+ * Bus injections by the Ybus method without any device allocation, for
+ * callers that cannot call cudaMalloc: host frameworks that hand out all
+ * device memory from their own pool and forbid driver allocations, or
+ * latency-critical loops where an allocation is not acceptable.  The paper
+ * has no counterpart; this is a deployment variant of inj_ybus.
+ *   nb        buses, 0 <= nb <= 262144 (PF_EUNSUPPORTED above: the phasor
+ *             scratch is a fixed 4 MiB device array in the library)
+ *   rowptr [nb+1], colidx [nnz], yval [nnz][2] (re, im; 16-byte aligned):
+ *             a Ybus in CSR form owned by the caller (for example the arrays
+ *             returned by ybus_get), read during the call
+ *   vm, va [nb] in; P, Q [nb] out (device pointers, caller-owned)
+ * The scratch array is shared by all calls on a device and keeps the last
+ * call's contents; calls that overlap on the GPU race on it, so issue them on
+ * one stream.  The first call on a device looks up the array's address.
+ */
+pf_status inj_ybus_noalloc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *yval,
+                           const double *vm, const double *va, double *P, double *Q, pf_stream stream);
+
 /* Current launch configuration. */
 pf_status grid_get_config(const pf_grid *grid, pf_config *cfg);
 

@@ -74,6 +74,7 @@ def _load():
         "grid_selfcheck": (st, [ctypes.POINTER(pf_grid_desc), i32]),
         "phasor": (st, [i32, vp, vp, vp, vp, vp]),
         "grid_inject_barrier_fault": (st, [vp, vp]),
+        "inj_ybus_noalloc": (st, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -294,6 +295,19 @@ def phasor(vm, va, U, V, stream=None):
     n = vm.numel()
     _check(_lib.phasor(n, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(U, "U", 4 * n), _dptr(V, "V", 2 * n),
                        _stream(stream)), "phasor")
+
+
+def inj_ybus_noalloc(rowptr, colidx, yval, vm, va, P, Q, stream=None):
+    """Ybus-method injections from a caller-owned CSR Ybus (int32 rowptr/colidx,
+    float64 yval [nnz, 2]); the library allocates nothing for this call."""
+    import torch
+    nb = rowptr.numel() - 1
+    for name, x in (("rowptr", rowptr), ("colidx", colidx)):
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.int32 and x.is_contiguous()):
+            raise TypeError("%s must be a contiguous int32 CUDA tensor" % name)
+    _check(_lib.inj_ybus_noalloc(nb, ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(colidx.data_ptr()),
+                                 _dptr(yval, "yval"), _dptr(vm, "vm", nb), _dptr(va, "va", nb), _dptr(P, "P", nb),
+                                 _dptr(Q, "Q", nb), _stream(stream)), "inj_ybus_noalloc")
 
 
 def grid_inject_barrier_fault(grid, stream=None):
