@@ -240,6 +240,78 @@ pf_status grid_check_error(pf_grid *grid, pf_stream stream);
  */
 pf_status grid_selfcheck(const pf_grid_desc *desc, int32_t window);
 
+/* ------------------------------------------------------------ batches -- */
+
+typedef struct pf_batch pf_batch;   /* opaque; S scenarios over one grid */
+
+/*
+ * A batch of `nscen` scenarios over `grid` (the grid must outlive the batch).
+ * Scenario s has its own voltage state and, when outage != NULL and
+ * outage[s] >= 0, loses branch outage[s] (an N-1 contingency: the
+ * element-wise method of Sec. II-B applied to the grid without that branch).
+ * Scenario s's Jacobian lives on its own pattern: the base pattern without
+ * the (h, k), (k, h) entries of the removed branch, unless a parallel branch
+ * keeps them; its values start at offset joff[s] of the batch's J array
+ * (batch_jac_offsets), nnzJ_s = 4 (nnzY - 2 removed).  outage is a host array
+ * read during the call; values outside [-1, nl) give PF_EINVAL.  Allocates
+ * the batch workspaces (phasors and residuals, 64 bytes per scenario-bus) and
+ * synchronizes `stream`.
+ */
+pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outage, pf_stream stream, pf_batch **out);
+
+/* Free a batch (NULL is allowed). */
+void batch_destroy(pf_batch *batch);
+
+/* Number of scenarios and total Jacobian values of the batch (either may be NULL). */
+pf_status batch_info(const pf_batch *batch, int32_t *nscen, int64_t *nnzJ_total);
+
+/* Device pointer (owned by the batch) to the offsets joff [nscen + 1] of each
+   scenario's Jacobian values in the batch's J array. */
+pf_status batch_jac_offsets(const pf_batch *batch, const int64_t **offsets);
+
+/*
+ * Host copy of scenario s's Jacobian pattern in the canonical layout of this
+ * header: rowptr [2nb + 1] and colidx [nnzJ_s] (either may be NULL; *nnzJ_s
+ * receives the count, so a first call with NULL arrays gives the size).
+ */
+pf_status batch_jac_pattern(const pf_batch *batch, int32_t s, int32_t *rowptr, int32_t *colidx, int32_t *nnzJ_s);
+
+/*
+ * Element-wise injections of every scenario in one persistent cooperative
+ * launch (capturable in a CUDA graph): vm, va [nscen][nb] in; P, Q
+ * [nscen][nb] out (device, caller-owned).  The batch owns the phasor
+ * workspace, so launches on one batch or grid must not overlap on the GPU.
+ */
+pf_status inj_elementwise_batched(pf_batch *batch, const double *vm, const double *va, double *P, double *Q,
+                                  pf_stream stream);
+
+/*
+ * Element-wise injections and Jacobian values of every scenario in one
+ * persistent cooperative launch: as inj_elementwise_batched plus J
+ * [nnzJ_total] (scenario s at joff[s], on its own pattern); P, Q may be NULL.
+ */
+pf_status jac_elementwise_batched(pf_batch *batch, const double *vm, const double *va, double *P, double *Q,
+                                  double *J, pf_stream stream);
+
+/*
+ * Adjoint of the mismatch loss, one cooperative launch (the paper has no
+ * adjoint; it differentiates the element-wise flows of Eqs. 5-7):
+ *   L_s = sum_i wP_i (P_si - Pspec_i)^2 + wQ_i (Q_si - Qspec_i)^2
+ * for every scenario s of the batch (outages honoured), with
+ *   L [nscen]            the loss per scenario (may be NULL)
+ *   gvm, gva [nscen][nb] dL_s/d|V| and dL_s/dtheta (J^T r without forming J)
+ *   gg, gb, gbsh, gtap [nl]  d(sum_s L_s)/d(g, b, b_sh, tap) per branch,
+ *                        scenarios summed in ascending order (all four NULL
+ *                        to skip; a branch removed in scenario s gets no
+ *                        contribution from s; tap derivative at the branch's
+ *                        own ratio, 1 for lines; phase shift not differentiated)
+ * Pspec, Qspec, wP, wQ [nb] are shared by all scenarios.  Device pointers.
+ * The loss and gradients use the grid's current parameters (grid_set_params).
+ */
+pf_status adjoint_elementwise(pf_batch *batch, const double *vm, const double *va, const double *Pspec,
+                              const double *Qspec, const double *wP, const double *wQ, double *L, double *gvm,
+                              double *gva, double *gg, double *gb, double *gbsh, double *gtap, pf_stream stream);
+
 /*
  * Fault injection for tests of the bounded device-side waits (no GPU fault
  * is involved): moves the arrival counter of the element-wise kernels' grid
@@ -258,7 +330,10 @@ pf_status grid_inject_barrier_fault(pf_grid *grid, pf_stream stream);
 #define PF_K_JAC_YBUS 2
 #define PF_K_INJ_EW 3
 #define PF_K_JAC_EW 4
-#define PF_K_COUNT 5
+#define PF_K_INJ_EW_BATCHED 5
+#define PF_K_JAC_EW_BATCHED 6
+#define PF_K_ADJOINT 7
+#define PF_K_COUNT 8
 
 typedef struct {
     int32_t kernel;          /* PF_K_* */

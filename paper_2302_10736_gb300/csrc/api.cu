@@ -114,6 +114,13 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
     if ((st = upload(a, &g->kd, H.kd, s))) return st;
     if ((st = upload(a, &g->tnbr, H.tnbr, s))) return st;
     if ((st = upload(a, &g->town, H.town, s))) return st;
+    if ((st = upload(a, &g->tmir, H.tmir, s))) return st;
+    const size_t nl = (size_t)g->nl;
+    PF_CUDA(a.alloc(&g->p_g, nl));
+    PF_CUDA(a.alloc(&g->p_b, nl));
+    PF_CUDA(a.alloc(&g->p_bsh, nl));
+    PF_CUDA(a.alloc(&g->p_tap, nl));
+    PF_CUDA(a.alloc(&g->p_shift, nl));
     PF_CUDA(a.alloc(&g->bus_yd, (size_t)nb));
     if ((st = upload(a, &g->jrp, H.jrp, s))) return st;
     if ((st = upload(a, &g->jci, H.jci, s))) return st;
@@ -163,6 +170,14 @@ pf_status refresh_values(Grid *g, const double *gg, const double *gb, const doub
 {
     PF_CUDA(launch_branch_constants(g, gg, gb, gbsh, gtap, gshift, s));
     PF_CUDA(launch_ybus_values(g, gs, bs, s));
+    const size_t bytes = (size_t)g->nl * sizeof(double);
+    if (bytes) {
+        PF_CUDA(cudaMemcpyAsync(g->p_g, gg, bytes, cudaMemcpyDeviceToDevice, s));
+        PF_CUDA(cudaMemcpyAsync(g->p_b, gb, bytes, cudaMemcpyDeviceToDevice, s));
+        PF_CUDA(cudaMemcpyAsync(g->p_bsh, gbsh, bytes, cudaMemcpyDeviceToDevice, s));
+        PF_CUDA(cudaMemcpyAsync(g->p_tap, gtap, bytes, cudaMemcpyDeviceToDevice, s));
+        PF_CUDA(cudaMemcpyAsync(g->p_shift, gshift, bytes, cudaMemcpyDeviceToDevice, s));
+    }
     return PF_OK;
 }
 
@@ -576,7 +591,8 @@ out:
 
 PF_API const char *pf_kernel_name(int32_t k)
 {
-    static const char *names[PF_K_COUNT] = {"phasor", "inj_ybus", "jac_ybus", "inj_ew", "jac_ew"};
+    static const char *names[PF_K_COUNT] = {"phasor",     "inj_ybus",      "jac_ybus",      "inj_ew",
+                                            "jac_ew",     "inj_ew_batched", "jac_ew_batched", "adjoint"};
     return (k >= 0 && k < PF_K_COUNT) ? names[k] : "?";
 }
 

@@ -1,0 +1,187 @@
+// batch.cu - C ABI of scenario batches: N-1 contingency evaluation and the
+// adjoint of the mismatch loss (see k_batched.cu for the kernels).
+#include <algorithm>
+#include <new>
+
+#include "pf_internal.h"
+
+using namespace pf;
+
+namespace pf {
+
+// Outage metadata of branch l on the grid's sorted-terminal structure.
+static ScenOut scen_outage(const HostTopo &H, int l)
+{
+    ScenOut o{-1, -1, -1, -1, 0, 0, 0, -1};
+    if (l < 0) return o;
+    const int th = 2 * l, tk = 2 * l + 1;
+    o.l = l;
+    o.h = H.owner(th);
+    o.k = H.owner(tk);
+    o.ph = H.tpos[th];
+    o.pk = H.tpos[tk];
+    o.kh = H.tkpos[th];
+    o.kk = H.tkpos[tk];
+    // the entry pair disappears unless another terminal of h runs to k
+    int run = 0;
+    for (int p = H.tp[o.h]; p < H.tp[o.h + 1]; ++p) run += H.tnbr[p].x == o.k;
+    o.del = run == 1 ? 1 : 0;
+    return o;
+}
+
+}  // namespace pf
+
+PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outage, pf_stream stream, pf_batch **out)
+{
+    if (!out) return set_error(PF_EINVAL, "batch_create: out is NULL");
+    *out = nullptr;
+    if (!grid) return set_error(PF_EINVAL, "batch_create: grid is NULL");
+    if (nscen < 0) return set_error(PF_EINVAL, "batch_create: nscen = %d", nscen);
+    Grid *g = &grid->g;
+    if ((long long)nscen * g->nb > (1LL << 40)) return set_error(PF_EUNSUPPORTED, "batch_create: batch too large");
+    for (int s = 0; outage && s < nscen; ++s)
+        if (outage[s] < -1 || outage[s] >= g->nl)
+            return set_error(PF_EINVAL, "batch_create: outage[%d] = %d outside [-1, %d)", s, outage[s], g->nl);
+    pf_batch *pb = new (std::nothrow) pf_batch;
+    if (!pb) return set_error(PF_ENOMEM, "batch_create: host allocation failed");
+    Batch *b = &pb->b;
+    b->g = g;
+    b->S = nscen;
+    b->h_sc.resize(nscen);
+    b->h_joff.assign(nscen + 1, 0);
+    for (int s = 0; s < nscen; ++s) {
+        b->h_sc[s] = scen_outage(g->topo, outage ? outage[s] : -1);
+        b->h_joff[s + 1] = b->h_joff[s] + 4LL * (g->nnz - 2 * b->h_sc[s].del);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)nscen * g->nb;
+    const size_t nw = (size_t)nscen * std::max(g->ew.nwin, 1);
+    cudaError_t e = cudaSuccess;
+    if ((e = b->arena.alloc(&b->sc, std::max(nscen, 1))) || (e = b->arena.alloc(&b->joff, nscen + 1)) ||
+        (e = b->arena.alloc(&b->U, n)) || (e = b->arena.alloc(&b->V, n)) || (e = b->arena.alloc(&b->r, n)) ||
+        (e = b->arena.alloc(&b->lpart, nw)) ||
+        (nscen && (e = cudaMemcpyAsync(b->sc, b->h_sc.data(), sizeof(ScenOut) * nscen, cudaMemcpyHostToDevice, st))) ||
+        (e = cudaMemcpyAsync(b->joff, b->h_joff.data(), sizeof(long long) * (nscen + 1), cudaMemcpyHostToDevice,
+                             st)) ||
+        (e = cudaStreamSynchronize(st))) {
+        b->arena.free_all();
+        delete pb;
+        return cuda_error(e, "batch_create");
+    }
+    *out = pb;
+    return PF_OK;
+}
+
+PF_API void batch_destroy(pf_batch *batch)
+{
+    if (!batch) return;
+    batch->b.arena.free_all();
+    delete batch;
+}
+
+PF_API pf_status batch_info(const pf_batch *batch, int32_t *nscen, int64_t *nnzJ_total)
+{
+    if (!batch) return set_error(PF_EINVAL, "batch_info: batch is NULL");
+    if (nscen) *nscen = batch->b.S;
+    if (nnzJ_total) *nnzJ_total = batch->b.h_joff.back();
+    return PF_OK;
+}
+
+PF_API pf_status batch_jac_offsets(const pf_batch *batch, const int64_t **offsets)
+{
+    if (!batch || !offsets) return set_error(PF_EINVAL, "batch_jac_offsets: NULL argument");
+    *offsets = reinterpret_cast<const int64_t *>(batch->b.joff);
+    return PF_OK;
+}
+
+PF_API pf_status batch_jac_pattern(const pf_batch *batch, int32_t s, int32_t *rowptr, int32_t *colidx,
+                                   int32_t *nnzJ_s)
+{
+    if (!batch) return set_error(PF_EINVAL, "batch_jac_pattern: batch is NULL");
+    const Batch *b = &batch->b;
+    if (s < 0 || s >= b->S) return set_error(PF_EINVAL, "batch_jac_pattern: scenario %d outside [0, %d)", s, b->S);
+    const HostTopo &H = b->g->topo;
+    const ScenOut &o = b->h_sc[s];
+    const int nb = H.nb;
+    // the scenario's Ybus pattern: the base rows without the removed pair
+    std::vector<int> rps(nb + 1, 0), cis;
+    cis.reserve(H.ci.size());
+    for (int i = 0; i < nb; ++i) {
+        for (int e = H.rp[i]; e < H.rp[i + 1]; ++e) {
+            const int j = H.ci[e];
+            if (o.del && ((i == o.h && j == o.k) || (i == o.k && j == o.h))) continue;
+            cis.push_back(j);
+        }
+        rps[i + 1] = (int)cis.size();
+    }
+    const int nnz = rps[nb];
+    if (nnzJ_s) *nnzJ_s = 4 * nnz;
+    if (rowptr) {
+        for (int blk = 0; blk < 2; ++blk)
+            for (int i = 0; i < nb; ++i) rowptr[blk * nb + i] = 2 * nnz * blk + 2 * rps[i];
+        rowptr[2 * nb] = 4 * nnz;
+    }
+    if (colidx) {
+        for (int blk = 0; blk < 2; ++blk)
+            for (int i = 0; i < nb; ++i) {
+                const int d = rps[i + 1] - rps[i], base = 2 * nnz * blk + 2 * rps[i];
+                for (int k = 0; k < d; ++k) {
+                    colidx[base + k] = cis[rps[i] + k];
+                    colidx[base + d + k] = nb + cis[rps[i] + k];
+                }
+            }
+    }
+    return PF_OK;
+}
+
+static pf_status check_batch(pf_batch *batch, const void *vm, const void *va, const char *name)
+{
+    if (!batch) return set_error(PF_EINVAL, "%s: batch is NULL", name);
+    if (batch->b.S > 0 && batch->b.g->nb > 0 && (!vm || !va)) return set_error(PF_EINVAL, "%s: vm or va is NULL", name);
+    return PF_OK;
+}
+
+PF_API pf_status inj_elementwise_batched(pf_batch *batch, const double *vm, const double *va, double *P, double *Q,
+                                         pf_stream stream)
+{
+    pf_status st = check_batch(batch, vm, va, "inj_elementwise_batched");
+    if (st) return st;
+    if (batch->b.S == 0 || batch->b.g->nb == 0) return PF_OK;
+    if (!P || !Q) return set_error(PF_EINVAL, "inj_elementwise_batched: P or Q is NULL");
+    TraceScope t(batch->b.g, PF_K_INJ_EW_BATCHED, (cudaStream_t)stream);
+    PF_CUDA(launch_ew_batched(&batch->b, false, vm, va, P, Q, nullptr, (cudaStream_t)stream));
+    return PF_OK;
+}
+
+PF_API pf_status jac_elementwise_batched(pf_batch *batch, const double *vm, const double *va, double *P, double *Q,
+                                         double *J, pf_stream stream)
+{
+    pf_status st = check_batch(batch, vm, va, "jac_elementwise_batched");
+    if (st) return st;
+    if (batch->b.S == 0 || batch->b.g->nb == 0) return PF_OK;
+    if (!J) return set_error(PF_EINVAL, "jac_elementwise_batched: J is NULL");
+    if ((P == nullptr) != (Q == nullptr))
+        return set_error(PF_EINVAL, "jac_elementwise_batched: P and Q must both be set or both NULL");
+    TraceScope t(batch->b.g, PF_K_JAC_EW_BATCHED, (cudaStream_t)stream);
+    PF_CUDA(launch_ew_batched(&batch->b, true, vm, va, P, Q, J, (cudaStream_t)stream));
+    return PF_OK;
+}
+
+PF_API pf_status adjoint_elementwise(pf_batch *batch, const double *vm, const double *va, const double *Pspec,
+                                     const double *Qspec, const double *wP, const double *wQ, double *L, double *gvm,
+                                     double *gva, double *gg, double *gb, double *gbsh, double *gtap,
+                                     pf_stream stream)
+{
+    pf_status st = check_batch(batch, vm, va, "adjoint_elementwise");
+    if (st) return st;
+    if (batch->b.S == 0 || batch->b.g->nb == 0) return PF_OK;
+    if (!Pspec || !Qspec || !wP || !wQ || !gvm || !gva)
+        return set_error(PF_EINVAL, "adjoint_elementwise: a required array is NULL");
+    const bool any = gg || gb || gbsh || gtap;
+    if (any && !(gg && gb && gbsh && gtap))
+        return set_error(PF_EINVAL, "adjoint_elementwise: gg, gb, gbsh, gtap must all be set or all NULL");
+    TraceScope t(batch->b.g, PF_K_ADJOINT, (cudaStream_t)stream);
+    PF_CUDA(launch_adjoint(&batch->b, vm, va, Pspec, Qspec, wP, wQ, L, gvm, gva, any ? gg : nullptr, gb, gbsh, gtap,
+                           (cudaStream_t)stream));
+    return PF_OK;
+}

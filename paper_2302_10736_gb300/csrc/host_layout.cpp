@@ -84,12 +84,14 @@ pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo
     H.tpos.assign(T, 0);
     H.tnbr.assign(T, make_int2(0, 0));
     H.town.assign(T, 0);
+    H.tmir.assign(T, 0);
     for (int p = 0; p < T; ++p) {
         const int t = H.tsort[p];
         H.tpos[t] = p;
         H.tnbr[p] = make_int2(H.other(t), H.tkpos[t] | (H.taccum[t] ? EW_ACCUM : 0));
         H.town[p] = H.owner(t);
     }
+    for (int p = 0; p < T; ++p) H.tmir[p] = H.tpos[H.tsort[p] ^ 1];
     const int nnz = H.nnz;
     H.jrp.assign(2 * (size_t)nb + 1, 0);
     H.jci.assign(4 * (size_t)nnz, 0);
@@ -171,6 +173,8 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
         CHECK(kp >= 0 && kp < H.rp[o + 1] - H.rp[o] && kp != H.kd[o], "slot of sorted terminal %d", p);
         const bool acc = (H.tnbr[p].y & EW_ACCUM) != 0;
         CHECK(acc == (p > H.tp[o] && H.tnbr[p - 1].x == q), "parallel-run flag of sorted terminal %d", p);
+        const int m = H.tmir[p];
+        CHECK(m >= 0 && m < T && H.town[m] == q && H.tnbr[m].x == o && H.tmir[m] == p, "mirror of terminal %d", p);
     }
     // element-wise windows: every access of k_jac_ew / k_inj_ew stays in bounds
     CHECK(E.nwin == (int)E.win_bus.size() - 1 && E.win_bus[0] == 0 && E.win_bus[E.nwin] == nb, "window cover");

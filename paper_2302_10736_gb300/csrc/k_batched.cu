@@ -1,0 +1,563 @@
+// k_batched.cu - element-wise method over many scenarios in one persistent
+// cooperative launch: N-1 contingency batches and the adjoint of the mismatch
+// loss.  (The paper evaluates one state of one grid; batching and
+// differentiation are the two extensions this library adds around the same
+// per-terminal evaluation and reduction, see k_elementwise.cu.)
+//
+// Work items are (scenario, window) pairs in scenario-major order, handed to
+// the resident CTAs round-robin, so the CTAs active at any time share a few
+// scenarios' phasors in L2.  Phase 1 forms every scenario's phasors; a grid
+// barrier follows; phase 2 evaluates.  The adjoint adds a residual phase and a
+// second barrier.
+//
+// Scenario s may remove one branch (outage).  Its two terminals are masked
+// (they contribute nothing) and the self sums of its end buses lose the
+// branch's self constants.  Unless a parallel branch keeps it, the Ybus entry
+// pair (h, k), (k, h) disappears from scenario s's pattern; the Jacobian of
+// scenario s is stored compacted on its own pattern at J + joff[s]: with
+// del = 1 if the pair disappears, a base slot (row i, position k) moves to
+//   rowptr_s[i] = rowptr[i] - del ([h < i] + [k < i]),  d_s(i) = d(i) - del [i in {h, k}],
+//   k_s = k - del [(i == h and k > pos(h, k)) or (i == k and k > pos(k, h))],
+// the canonical closed form of the scenario's own pattern.
+//
+// Adjoint (loss L_s = sum_i wP (P_i - Ps_i)^2 + wQ (Q_i - Qs_i)^2, residual
+// r_i = (2 wP dP_i, 2 wQ dQ_i), <r, z> = r_P Re z + r_Q Im z):
+//   dL/dtheta_q = sum over q's terminals t (other bus o, mirror terminal m):
+//                 <r_q, j K_t> + <r_o, -j K_m>
+//   dL/dv_q     = <r_q, 2 v_q conj(Yd_q)> + (sum_t <r_q, K_t> + <r_o, K_m>) / v_q
+// with K_t = conj(Yc_t) V_q conj(V_o), K_m = conj(Yc_m) V_o conj(V_q): each bus
+// sums over its own terminals only (no scatter, fixed order).  Branch
+// parameter gradients come from the partials of Eqs. (5)-(6) by g, b, b_sh and
+// the tap, one thread per branch summing the scenarios in ascending order.
+#include "fastmath.cuh"
+#include "pf_internal.h"
+#include "ptx.cuh"
+
+namespace pf {
+
+constexpr uint64_t kBatchBarrierNs = 2000000000ull;   // bounded grid-barrier wait (2 s)
+
+struct BatchArgs {
+    int S, nb, nl, nnz, nwin, max_nbus, max_nt, max_L, aligned;
+    const int *win_bus, *tp, *rp, *kd, *town, *tmir, *tpos;
+    const int2 *tnbr;
+    const double2 *yd, *tself, *tcoup, *trig;
+    const ScenOut *sc;
+    const long long *joff;
+    const double *vm, *va;
+    double4_32a *U;
+    double2 *V;
+    double *P, *Q, *J;
+    unsigned int *bar;
+    int *err;
+    // adjoint
+    const double *Ps, *Qs, *wP, *wQ;
+    double2 *r;
+    double *lpart, *L, *gvm, *gva, *gg, *gb, *gbsh, *gtap;
+    const double *pg, *pb, *pbsh, *ptap, *pshift;
+};
+
+__device__ __forceinline__ void store_range_ll(double *x, const double *s, long long b0, long long b1)
+{
+    const int par = (int)(b0 & 1);
+    if (par) x[b0] = s[1];
+    const long long ge = b0 + par;
+    const long long cm = (b1 - ge) & ~1LL;
+    if (cm > 0) bulk_s2g(x + ge, s + 2 * par, 8u * (uint32_t)cm);
+    if ((b1 - ge) & 1) x[b1 - 1] = s[b1 - 1 - b0 + par];
+}
+
+// phase 1: phasors of every (scenario, window) item of this CTA
+__device__ __forceinline__ void batch_phasors(const BatchArgs &a, const double2 *tab, bool needU)
+{
+    const int tid = threadIdx.x, TB = blockDim.x;
+    const long long nitem = (long long)a.S * a.nwin;
+    for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
+        const int s = (int)(it / a.nwin), w = (int)(it % a.nwin);
+        const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1];
+        for (int o = b0 + tid; o < b1; o += TB) {
+            const long long x = (long long)s * a.nb + o;
+            double sn, cs;
+            fast_sincos(a.va[x], tab, &sn, &cs);
+            const double v = a.vm[x];
+            if (needU) a.U[x] = make_double4_32a(cs, sn, v, fast_rcp(v));
+            a.V[x] = make_double2(v * cs, v * sn);
+        }
+    }
+}
+
+// Window metadata of item (s, w) into shared memory, corrected for the
+// scenario's outage: {J-slice row offset, row length, diagonal position,
+// first terminal} per bus and the self sum Yd without the outage branch.
+__device__ __forceinline__ void batch_window_meta(const BatchArgs &a, const ScenOut &sc, int b0, int b1, int t0,
+                                                  int4 *sbm, double2 *syd)
+{
+    const int r0 = a.rp[b0];
+    for (int b = threadIdx.x; b < b1 - b0; b += blockDim.x) {
+        const int o = b0 + b, rs = a.rp[o], kdo = a.kd[o];
+        const int del = sc.del;
+        const int shift = 2 * del * ((sc.h >= b0 && sc.h < o) + (sc.k >= b0 && sc.k < o));
+        const int d = a.rp[o + 1] - rs - del * ((o == sc.h) + (o == sc.k));
+        const int kds = kdo - del * ((o == sc.h && kdo > sc.kh) + (o == sc.k && kdo > sc.kk));
+        sbm[b] = make_int4(2 * (rs - r0) - shift, d, kds, a.tp[o] - t0);
+        double2 y = a.yd[o];
+        if (o == sc.h) {
+            y.x -= a.tself[sc.ph].x;
+            y.y -= a.tself[sc.ph].y;
+        }
+        if (o == sc.k) {
+            y.x -= a.tself[sc.pk].x;
+            y.y -= a.tself[sc.pk].y;
+        }
+        syd[b] = y;
+    }
+}
+
+template <bool JAC>
+__global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
+{
+    extern __shared__ __align__(16) char smem[];
+    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, JAC ? a.max_L : 0, JAC);
+    int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
+    double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
+    double2 *skg = reinterpret_cast<double2 *>(smem + sp.kg);
+    int *skp = reinterpret_cast<int *>(smem + sp.kp);
+    double *jst = reinterpret_cast<double *>(smem + sp.jst);
+    double *spq = reinterpret_cast<double *>(smem + sp.pq);
+    double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
+    const int tid = threadIdx.x, TB = blockDim.x;
+    for (int k = tid; k < kTrigN; k += TB) tab[k] = a.trig[k];
+    __syncthreads();
+    batch_phasors(a, tab, JAC);
+    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+
+    const long long nitem = (long long)a.S * a.nwin;
+    for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
+        const int s = (int)(it / a.nwin), w = (int)(it % a.nwin);
+        const ScenOut sc = a.sc[s];
+        const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
+        const int t0 = a.tp[b0], nt = a.tp[b1] - t0;
+        const int del = sc.del;
+        const int ndb = del * ((sc.h >= 0 && sc.h < b0) + (sc.k >= 0 && sc.k < b0));
+        const int ndw = del * ((sc.h >= b0 && sc.h < b1) + (sc.k >= b0 && sc.k < b1));
+        const int r0s = a.rp[b0] - ndb;
+        const int Ls = JAC ? 2 * (a.rp[b1] - a.rp[b0]) - 2 * ndw : 0;
+        const int nnzs = a.nnz - 2 * del;
+        const long long sb = (long long)s * a.nb;
+        __syncthreads();   // previous item's shared-memory readers are done
+        batch_window_meta(a, sc, b0, b1, t0, sbm, syd);
+        double4_32a ub = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        double vb = 0.0;
+        if (tid < nbus) {
+            if (JAC)
+                ub = a.U[sb + b0 + tid];
+            else
+                vb = a.vm[sb + b0 + tid];
+        }
+        __syncthreads();
+        for (int i = tid; i < nt; i += TB) {
+            const int p = t0 + i;
+            const double2 yc = a.tcoup[p];
+            const int2 nq = a.tnbr[p];
+            const int ol = a.town[p] - b0, o = b0 + ol;
+            const bool masked = p == sc.ph || p == sc.pk;
+            const double2 Vo = a.V[sb + o];
+            if (JAC) {
+                const double4_32a uq = a.U[sb + nq.x];
+                double Er = fma(Vo.x, uq.x, Vo.y * uq.y), Ei = fma(Vo.y, uq.x, -Vo.x * uq.y);
+                double Gr = fma(yc.x, Er, yc.y * Ei), Gi = fma(yc.x, Ei, -yc.y * Er);
+                if (masked) Gr = Gi = 0.0;
+                const double Kr = uq.z * Gr, Ki = uq.z * Gi;
+                const int kp = nq.y & EW_KMASK;
+                const int kps = kp - del * ((o == sc.h && kp > sc.kh) + (o == sc.k && kp > sc.kk));
+                const bool gone = del && ((o == sc.h && kp == sc.kh) || (o == sc.k && kp == sc.kk));
+                skg[2 * i] = make_double2(Kr, Ki);
+                skg[2 * i + 1] = make_double2(Gr, Gi);
+                skp[i] = gone ? 0 : (kps | (nq.y & EW_ACCUM));
+                if (!gone && !(nq.y & EW_ACCUM)) {
+                    const int4 bm = sbm[ol];
+                    const int pos = bm.x + kps, d = bm.y;
+                    jst[pos] = Ki;
+                    jst[pos + d] = Gr;
+                    jst[Ls + pos] = -Kr;
+                    jst[Ls + pos + d] = Gi;
+                }
+            } else {
+                const double2 Vq = a.V[sb + nq.x];
+                const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
+                double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);
+                if (masked) Kr = Ki = 0.0;
+                skg[i] = make_double2(Kr, Ki);
+            }
+        }
+        __syncthreads();
+        const int pqs = (int)sp.pqs;
+        const int par = (int)((sb + b0) & 1);
+        for (int b = tid; b < nbus; b += TB) {
+            const int4 bm = sbm[b];
+            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+            const double2 y = syd[b];
+            double sKr = 0.0, sKi = 0.0;
+            if (JAC) {
+                const int d = bm.y;
+                for (int i = bm.w; i < tend; ++i) {
+                    const double2 K = skg[2 * i];
+                    sKr += K.x;
+                    sKi += K.y;
+                    const int kp = skp[i];
+                    if (kp & EW_ACCUM) {
+                        const double2 G = skg[2 * i + 1];
+                        const int pos = bm.x + (kp & EW_KMASK);
+                        jst[pos] += K.y;
+                        jst[pos + d] += G.x;
+                        jst[Ls + pos] -= K.x;
+                        jst[Ls + pos + d] += G.y;
+                    }
+                }
+                const double4_32a uo = b == tid ? ub : a.U[sb + b0 + b];
+                const double v = uo.z, iv = uo.w, v2 = v * v, tv = v + v;
+                const int pos = bm.x + bm.z;
+                jst[pos] = -sKi;
+                jst[pos + d] = fma(tv, y.x, sKr * iv);
+                jst[Ls + pos] = sKr;
+                jst[Ls + pos + d] = fma(-tv, y.y, sKi * iv);
+                spq[b + par] = fma(v2, y.x, sKr);
+                spq[pqs + b + par] = fma(-v2, y.y, sKi);
+            } else {
+                for (int i = bm.w; i < tend; ++i) {
+                    sKr += skg[i].x;
+                    sKi += skg[i].y;
+                }
+                const double v = b == tid ? vb : a.vm[sb + b0 + b], v2 = v * v;
+                spq[b + par] = fma(v2, y.x, sKr);
+                spq[pqs + b + par] = fma(-v2, y.y, sKi);
+            }
+        }
+        double *Js = JAC ? a.J + a.joff[s] : nullptr;
+        if (a.aligned) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                if (JAC) {
+                    bulk_s2g(Js + 2 * (long long)r0s, jst, 8u * (uint32_t)Ls);
+                    bulk_s2g(Js + 2 * (long long)nnzs + 2 * (long long)r0s, jst + Ls, 8u * (uint32_t)Ls);
+                }
+                if (a.P) {
+                    store_range_ll(a.P, spq, sb + b0, sb + b1);
+                    store_range_ll(a.Q, spq + pqs, sb + b0, sb + b1);
+                }
+                bulk_commit();
+                bulk_wait_read();
+            }
+        } else {
+            __syncthreads();
+            if (JAC) {
+                for (int x = tid; x < Ls; x += TB) {
+                    Js[2 * (long long)r0s + x] = jst[x];
+                    Js[2 * (long long)nnzs + 2 * (long long)r0s + x] = jst[Ls + x];
+                }
+            }
+            if (a.P)
+                for (int b = tid; b < nbus; b += TB) {
+                    a.P[sb + b0 + b] = spq[b + par];
+                    a.Q[sb + b0 + b] = spq[pqs + b + par];
+                }
+        }
+    }
+}
+
+// ------------------------------------------------------------ adjoint ----
+
+__global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
+{
+    extern __shared__ __align__(16) char smem[];
+    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false);
+    int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
+    double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
+    double2 *skg = reinterpret_cast<double2 *>(smem + sp.kg);
+    double *spq = reinterpret_cast<double *>(smem + sp.pq);
+    double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
+    const int tid = threadIdx.x, TB = blockDim.x;
+    for (int k = tid; k < kTrigN; k += TB) tab[k] = a.trig[k];
+    __syncthreads();
+    batch_phasors(a, tab, true);
+    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+
+    const long long nitem = (long long)a.S * a.nwin;
+    // ---- phase 2: injections, residuals and per-window loss partial sums ----
+    for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
+        const int s = (int)(it / a.nwin), w = (int)(it % a.nwin);
+        const ScenOut sc = a.sc[s];
+        const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
+        const int t0 = a.tp[b0], nt = a.tp[b1] - t0;
+        const long long sb = (long long)s * a.nb;
+        __syncthreads();
+        batch_window_meta(a, sc, b0, b1, t0, sbm, syd);
+        __syncthreads();
+        for (int i = tid; i < nt; i += TB) {
+            const int p = t0 + i;
+            const double2 yc = a.tcoup[p];
+            const int q = a.tnbr[p].x, o = a.town[p];
+            const double2 Vo = a.V[sb + o], Vq = a.V[sb + q];
+            const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
+            double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);
+            if (p == sc.ph || p == sc.pk) Kr = Ki = 0.0;
+            skg[i] = make_double2(Kr, Ki);
+        }
+        __syncthreads();
+        for (int b = tid; b < nbus; b += TB) {
+            const int4 bm = sbm[b];
+            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+            double sKr = 0.0, sKi = 0.0;
+            for (int i = bm.w; i < tend; ++i) {
+                sKr += skg[i].x;
+                sKi += skg[i].y;
+            }
+            const int o = b0 + b;
+            const double v = a.vm[sb + o], v2 = v * v;
+            const double2 y = syd[b];
+            const double dP = fma(v2, y.x, sKr) - a.Ps[o];
+            const double dQ = fma(-v2, y.y, sKi) - a.Qs[o];
+            const double wp = a.wP[o], wq = a.wQ[o];
+            a.r[sb + o] = make_double2(2.0 * wp * dP, 2.0 * wq * dQ);
+            spq[b] = fma(wp * dP, dP, wq * dQ * dQ);
+        }
+        __syncthreads();
+        if (tid == 0) {   // fixed-order partial sum of the window's loss terms
+            double acc = 0.0;
+            for (int b = 0; b < nbus; ++b) acc += spq[b];
+            a.lpart[(long long)s * a.nwin + w] = acc;
+        }
+    }
+    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+
+    // ---- phase 3a: state gradients, one bus per thread over its own terminals ----
+    for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
+        const int s = (int)(it / a.nwin), w = (int)(it % a.nwin);
+        const ScenOut sc = a.sc[s];
+        const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
+        const int t0 = a.tp[b0], nt = a.tp[b1] - t0;
+        const long long sb = (long long)s * a.nb;
+        __syncthreads();
+        batch_window_meta(a, sc, b0, b1, t0, sbm, syd);
+        __syncthreads();
+        for (int i = tid; i < nt; i += TB) {
+            const int p = t0 + i;
+            const double2 yc = a.tcoup[p], ym = a.tcoup[a.tmir[p]];
+            const int q = a.town[p], o = a.tnbr[p].x;   // q owns the terminal, o is the other end
+            const double2 Vq = a.V[sb + q], Vo = a.V[sb + o];
+            const double2 rq = a.r[sb + q], ro = a.r[sb + o];
+            const double Wr = fma(Vq.x, Vo.x, Vq.y * Vo.y), Wi = fma(Vq.y, Vo.x, -Vq.x * Vo.y);   // V_q conj(V_o)
+            const double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);           // K_t
+            const double Mr = fma(ym.x, Wr, -ym.y * Wi), Mi = fma(-ym.x, Wi, -ym.y * Wr);         // K_m = conj(Yc_m) conj(W)
+            double th = fma(-rq.x, Ki, rq.y * Kr) + fma(ro.x, Mi, -ro.y * Mr);
+            double vv = fma(rq.x, Kr, rq.y * Ki) + fma(ro.x, Mr, ro.y * Mi);
+            if (p == sc.ph || p == sc.pk) th = vv = 0.0;
+            skg[i] = make_double2(th, vv);
+        }
+        __syncthreads();
+        const int pqs = (int)sp.pqs;
+        const int par = (int)((sb + b0) & 1);
+        for (int b = tid; b < nbus; b += TB) {
+            const int4 bm = sbm[b];
+            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+            double gth = 0.0, gv = 0.0;
+            for (int i = bm.w; i < tend; ++i) {
+                gth += skg[i].x;
+                gv += skg[i].y;
+            }
+            const int q = b0 + b;
+            const double4_32a uq = a.U[sb + q];
+            const double2 rq = a.r[sb + q];
+            const double2 y = syd[b];
+            const double tv = uq.z + uq.z;
+            // <r_q, 2 v_q conj(Yd)> + (sum) / v_q
+            spq[b + par] = gth;
+            spq[pqs + b + par] = fma(gv, uq.w, tv * fma(rq.x, y.x, -rq.y * y.y));
+        }
+        if (a.aligned) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                store_range_ll(a.gva, spq, sb + b0, sb + b1);
+                store_range_ll(a.gvm, spq + pqs, sb + b0, sb + b1);
+                bulk_commit();
+                bulk_wait_read();
+            }
+        } else {
+            __syncthreads();
+            for (int b = tid; b < nbus; b += TB) {
+                a.gva[sb + b0 + b] = spq[b + par];
+                a.gvm[sb + b0 + b] = spq[pqs + b + par];
+            }
+        }
+    }
+
+    // ---- phase 3b: branch-parameter gradients, scenarios summed in order ----
+    if (a.gg) {
+        for (int l = blockIdx.x * TB + tid; l < a.nl; l += gridDim.x * TB) {
+            const int h = a.town[a.tpos[2 * l]], k = a.town[a.tpos[2 * l + 1]];
+            const double g = a.pg[l], bb = a.pb[l], bsh = a.pbsh[l], m = a.ptap[l];
+            const double im = 1.0 / m, im2 = im * im;
+            double sphi, cphi;
+            fast_sincos(a.pshift[l], tab, &sphi, &cphi);
+            const double c1r = g, c1i = -(bb + 0.5 * bsh);   // conj(y_s + j b_sh / 2)
+            double agg = 0.0, agb = 0.0, agsh = 0.0, agt = 0.0;
+            for (int s = 0; s < a.S; ++s) {
+                if (a.sc[s].l == l) continue;   // removed in this scenario
+                const long long sb = (long long)s * a.nb;
+                const double2 Vh = a.V[sb + h], Vk = a.V[sb + k];
+                const double2 rh = a.r[sb + h], rk = a.r[sb + k];
+                const double vh2 = fma(Vh.x, Vh.x, Vh.y * Vh.y), vk2 = fma(Vk.x, Vk.x, Vk.y * Vk.y);
+                const double Wr = fma(Vh.x, Vk.x, Vh.y * Vk.y), Wi = fma(Vh.y, Vk.x, -Vh.x * Vk.y);
+                const double Br = fma(Wr, cphi, Wi * sphi) * im, Bi = fma(Wi, cphi, -Wr * sphi) * im;   // W e^{-j phi}/m
+                const double Ah = vh2 * im2;
+                const double zhr = Ah - Br, zhi = -Bi;     // dS_hk/dg
+                const double zkr = vk2 - Br, zki = Bi;     // dS_kh/dg
+                agg += fma(rh.x, zhr, rh.y * zhi) + fma(rk.x, zkr, rk.y * zki);
+                agb += fma(rh.x, zhi, -rh.y * zhr) + fma(rk.x, zki, -rk.y * zkr);   // <r, -j z>
+                agsh -= 0.5 * fma(rh.y, Ah, rk.y * vk2);
+                // dS_hk/dm = im (-2 Ah conj(y_s + j b_sh/2) + conj(y_s) B), dS_kh/dm = im conj(y_s) conj(B)
+                const double dhr = im * (-2.0 * Ah * c1r + fma(g, Br, bb * Bi));
+                const double dhi = im * (-2.0 * Ah * c1i + fma(g, Bi, -bb * Br));
+                const double dkr = im * fma(g, Br, -bb * Bi);
+                const double dki = im * fma(-g, Bi, -bb * Br);
+                agt += fma(rh.x, dhr, rh.y * dhi) + fma(rk.x, dkr, rk.y * dki);
+            }
+            a.gg[l] = agg;
+            a.gb[l] = agb;
+            a.gbsh[l] = agsh;
+            a.gtap[l] = agt;
+        }
+    }
+    // ---- loss per scenario: window partial sums in window order ----
+    if (a.L)
+        for (int s = blockIdx.x * TB + tid; s < a.S; s += gridDim.x * TB) {
+            double acc = 0.0;
+            for (int w = 0; w < a.nwin; ++w) acc += a.lpart[(long long)s * a.nwin + w];
+            a.L[s] = acc;
+        }
+}
+
+// ----------------------------------------------------------- launchers ----
+
+static bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static BatchArgs batch_args(Batch *b)
+{
+    Grid *g = b->g;
+    BatchArgs a = {};
+    a.S = b->S;
+    a.nb = g->nb;
+    a.nl = g->nl;
+    a.nnz = g->nnz;
+    a.nwin = g->ew.nwin;
+    a.max_nbus = g->ew.max_nbus;
+    a.max_nt = g->ew.max_nt;
+    a.max_L = g->ew.max_L;
+    a.win_bus = g->ew.win_bus;
+    a.tp = g->tp;
+    a.rp = g->rp;
+    a.kd = g->kd;
+    a.town = g->town;
+    a.tmir = g->tmir;
+    a.tpos = g->tpos;
+    a.tnbr = g->tnbr;
+    a.yd = g->bus_yd;
+    a.tself = g->tself;
+    a.tcoup = g->tcoup;
+    a.trig = trig_table();
+    a.sc = b->sc;
+    a.joff = b->joff;
+    a.U = b->U;
+    a.V = b->V;
+    a.bar = g->bar;
+    a.err = g->err;
+    a.r = b->r;
+    a.lpart = b->lpart;
+    a.pg = g->p_g;
+    a.pb = g->p_b;
+    a.pbsh = g->p_bsh;
+    a.ptap = g->p_tap;
+    a.pshift = g->p_shift;
+    return a;
+}
+
+template <typename K>
+static cudaError_t coop_launch(K kernel, int &resident, Batch *b, size_t smem, long long items, cudaStream_t s,
+                               const BatchArgs &a)
+{
+    cudaError_t e;
+    const int tb = b->g->ew.tb;
+    if (resident == 0 || b->tb != tb) {
+        if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)smem)))
+            return e;
+        int per_sm = 0, dev = 0, nsm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, tb, smem))) return e;
+        if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
+            return e;
+        resident = per_sm * nsm;
+        b->tb = tb;
+        if (resident <= 0) return cudaErrorInvalidConfiguration;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::max<long long>(1, std::min<long long>(items, resident)));
+    cfg.blockDim = dim3((unsigned)tb);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,
+                              double *J, cudaStream_t s)
+{
+    Grid *g = b->g;
+    if (g->ew.nwin == 0 || b->S == 0) return cudaSuccess;
+    BatchArgs a = batch_args(b);
+    a.vm = vm;
+    a.va = va;
+    a.P = P;
+    a.Q = Q;
+    a.J = J;
+    a.aligned = (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
+    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, jac ? a.max_L : 0, jac);
+    const size_t smem = sp.total + kTrigN * sizeof(double2);
+    const long long items = (long long)b->S * g->ew.nwin;
+    if (jac) return coop_launch(k_ewb<true>, b->resident[1], b, smem, items, s, a);
+    return coop_launch(k_ewb<false>, b->resident[0], b, smem, items, s, a);
+}
+
+cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
+                           const double *wP, const double *wQ, double *L, double *gvm, double *gva, double *gg,
+                           double *gb, double *gbsh, double *gtap, cudaStream_t s)
+{
+    Grid *g = b->g;
+    if (g->ew.nwin == 0 || b->S == 0) return cudaSuccess;
+    BatchArgs a = batch_args(b);
+    a.vm = vm;
+    a.va = va;
+    a.Ps = Ps;
+    a.Qs = Qs;
+    a.wP = wP;
+    a.wQ = wQ;
+    a.L = L;
+    a.gvm = gvm;
+    a.gva = gva;
+    a.gg = gg;
+    a.gb = gb;
+    a.gbsh = gbsh;
+    a.gtap = gtap;
+    a.aligned = al16(gvm) && al16(gva);
+    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false);
+    const size_t smem = sp.total + kTrigN * sizeof(double2);
+    const long long items = std::max<long long>((long long)b->S * g->ew.nwin, (g->nl + 255) / 256);
+    return coop_launch(k_adj, b->resident[2], b, smem, items, s, a);
+}
+
+}  // namespace pf

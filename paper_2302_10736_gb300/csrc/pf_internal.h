@@ -59,6 +59,7 @@ struct HostTopo {
     std::vector<int> taccum;    // [2nl] 1 if not the first terminal of its (owner, other) run
     std::vector<int2> tnbr;     // [2nl] by sorted position: {other bus, kpos | EW_ACCUM}
     std::vector<int> town;      // [2nl] by sorted position: owner bus
+    std::vector<int> tmir;      // [2nl] by sorted position: sorted position of the other end's terminal
     std::vector<int> rp, ci;    // Ybus CSR pattern
     std::vector<int> ybeg, yend, ydiag;  // per nnz: sorted-terminal stamp range; row if diagonal else -1
     std::vector<int> kd;        // [nb] position of the diagonal in row i
@@ -136,6 +137,9 @@ struct Grid {
     double2 *bus_yd = nullptr;             // [nb] bus shunt + sum of the bus's terminal self constants
     EwDev ew;
     int ew_resident_jac = 0, ew_resident_inj = 0;   // co-resident CTAs of the fused kernels (0 = unknown)
+    int *tmir = nullptr;                   // [2nl] by sorted position: sorted position of the mirror terminal
+    // device copies of the current parameters (branch gradients need them)
+    double *p_g = nullptr, *p_b = nullptr, *p_bsh = nullptr, *p_tap = nullptr, *p_shift = nullptr;
     unsigned int *bar = nullptr;   // grid-barrier state {arrivals, generation}
     // per-call workspace (device)
     double4_32a *ph_u = nullptr;   // [nb] {cos, sin, v, 1/v}
@@ -202,8 +206,47 @@ cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
                           cudaStream_t s);
 
+// ----------------------------------------------------------- batches ----
+// S scenarios over one grid: per-scenario voltage states and an optional N-1
+// outage (one branch removed).  Scenario s's Jacobian is stored on its own
+// pattern (the base pattern without the outage's off-diagonal pair when no
+// parallel branch keeps it) at J + joff[s].
+struct ScenOut {
+    int h, k;          // outage branch end buses (-1: none)
+    int ph, pk;        // sorted positions of its two terminals
+    int del;           // 1 if the (h, k) / (k, h) Ybus entries disappear
+    int kh, kk;        // positions of k in row h and of h in row k (base pattern)
+    int l;             // outage branch (-1: none)
+};
+
+struct Batch {
+    Grid *g = nullptr;
+    int S = 0;
+    DevArena arena;
+    std::vector<ScenOut> h_sc;
+    std::vector<long long> h_joff;   // [S+1]
+    ScenOut *sc = nullptr;           // [S]
+    long long *joff = nullptr;       // [S+1]
+    double4_32a *U = nullptr;        // [S][nb]
+    double2 *V = nullptr;            // [S][nb]
+    double2 *r = nullptr;            // [S][nb] loss residual (2 wP dP, 2 wQ dQ)
+    double *lpart = nullptr;         // [S][nwin] per-window loss partial sums
+    int resident[3] = {0, 0, 0};     // co-resident CTAs of the batched kernels (inj, jac, adjoint)
+    int tb = 0;                      // element-wise window size the residency was computed for
+};
+
+cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,
+                              double *J, cudaStream_t s);
+cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
+                           const double *wP, const double *wQ, double *L, double *gvm, double *gva, double *gg,
+                           double *gb, double *gbsh, double *gtap, cudaStream_t s);
+
 }  // namespace pf
 
 struct pf_grid {
     pf::Grid g;
+};
+
+struct pf_batch {
+    pf::Batch b;
 };

@@ -350,3 +350,143 @@ def grid_trace_read(grid, cap=1 << 16):
     n = ctypes.c_int32()
     _check(_lib.grid_trace_read(grid.handle, buf, cap, ctypes.byref(n)), "grid_trace_read")
     return [(kernel_name(buf[i].kernel), float(buf[i].ms)) for i in range(n.value)]
+
+
+# ------------------------------------------------------------------ batches --
+
+def _bind_batches():
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    st = ctypes.c_int32
+    sig = {
+        "batch_create": (st, [vp, i32, vp, vp, ctypes.POINTER(vp)]),
+        "batch_destroy": (None, [vp]),
+        "batch_info": (st, [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]),
+        "batch_jac_offsets": (st, [vp, ctypes.POINTER(vp)]),
+        "batch_jac_pattern": (st, [vp, i32, vp, vp, ctypes.POINTER(i32)]),
+        "inj_elementwise_batched": (st, [vp, vp, vp, vp, vp, vp]),
+        "jac_elementwise_batched": (st, [vp, vp, vp, vp, vp, vp, vp]),
+        "adjoint_elementwise": (st, [vp] + [vp] * 14),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(_lib, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+_bind_batches()
+
+
+class Batch:
+    """Owner of a pf_batch handle (keeps its grid alive)."""
+
+    def __init__(self, handle, grid):
+        self.handle = ctypes.c_void_p(handle)
+        self.grid = grid
+        n, tot = ctypes.c_int32(), ctypes.c_int64()
+        _check(_lib.batch_info(self.handle, ctypes.byref(n), ctypes.byref(tot)), "batch_info")
+        self.nscen, self.nnzJ_total = n.value, tot.value
+
+    def close(self):
+        if self.handle:
+            _lib.batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_create(grid, nscen, outage=None, stream=None):
+    """Batch of nscen scenarios; outage: host int array [nscen] (-1 = none) or None."""
+    arr, p = _hptr(outage, np.int32) if outage is not None else (None, None)
+    out = ctypes.c_void_p()
+    _check(_lib.batch_create(grid.handle, int(nscen), p, _stream(stream), ctypes.byref(out)), "batch_create")
+    return Batch(out.value, grid)
+
+
+def batch_jac_offsets(batch):
+    """Offsets joff [nscen+1] of each scenario's Jacobian values (new torch CUDA tensor)."""
+    import torch
+    ptr = ctypes.c_void_p()
+    _check(_lib.batch_jac_offsets(batch.handle, ctypes.byref(ptr)), "batch_jac_offsets")
+    return _device_copy(ptr.value, batch.nscen + 1, torch.int64)
+
+
+def batch_jac_pattern(batch, s):
+    """(rowptr, colidx) numpy arrays of scenario s's Jacobian pattern."""
+    n = ctypes.c_int32()
+    _check(_lib.batch_jac_pattern(batch.handle, int(s), None, None, ctypes.byref(n)), "batch_jac_pattern")
+    nb = batch.grid.nb
+    rp = np.zeros(2 * nb + 1, np.int32)
+    ci = np.zeros(max(n.value, 1), np.int32)
+    _check(_lib.batch_jac_pattern(batch.handle, int(s), rp.ctypes.data_as(ctypes.c_void_p),
+                                  ci.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)), "batch_jac_pattern")
+    return rp, ci[:n.value]
+
+
+def inj_elementwise_batched(batch, vm, va, P, Q, stream=None):
+    n = batch.nscen * batch.grid.nb
+    _check(_lib.inj_elementwise_batched(batch.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(P, "P", n),
+                                        _dptr(Q, "Q", n), _stream(stream)), "inj_elementwise_batched")
+
+
+def jac_elementwise_batched(batch, vm, va, P, Q, J, stream=None):
+    n = batch.nscen * batch.grid.nb
+    _check(_lib.jac_elementwise_batched(batch.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(P, "P", n),
+                                        _dptr(Q, "Q", n), _dptr(J, "J", batch.nnzJ_total), _stream(stream)),
+           "jac_elementwise_batched")
+
+
+def adjoint_elementwise(batch, vm, va, Pspec, Qspec, wP, wQ, L, gvm, gva, gg=None, gb=None, gbsh=None, gtap=None,
+                        stream=None):
+    nb, nl, S = batch.grid.nb, batch.grid.nl, batch.nscen
+    _check(_lib.adjoint_elementwise(batch.handle, _dptr(vm, "vm", S * nb), _dptr(va, "va", S * nb),
+                                    _dptr(Pspec, "Pspec", nb), _dptr(Qspec, "Qspec", nb), _dptr(wP, "wP", nb),
+                                    _dptr(wQ, "wQ", nb), _dptr(L, "L", S), _dptr(gvm, "gvm", S * nb),
+                                    _dptr(gva, "gva", S * nb), _dptr(gg, "gg", nl), _dptr(gb, "gb", nl),
+                                    _dptr(gbsh, "gbsh", nl), _dptr(gtap, "gtap", nl), _stream(stream)),
+           "adjoint_elementwise")
+
+
+def _mismatch_loss_function():
+    import torch
+
+    class MismatchLoss(torch.autograd.Function):
+        """Total mismatch loss sum_s L_s of a batch (see adjoint_elementwise) as a
+        differentiable function of the voltage states and the branch parameters.
+
+        forward(batch, vm, va, g, b, bsh, tap, shift, gs, bs, Pspec, Qspec, wP, wQ)
+        sets the grid's parameters, runs the adjoint kernel once (loss and all
+        gradients) and keeps the gradients for backward."""
+
+        @staticmethod
+        def forward(ctx, batch, vm, va, g, b, bsh, tap, shift, gs, bs, Pspec, Qspec, wP, wQ):
+            grid = batch.grid
+            c = lambda x: x.detach().contiguous()
+            grid_set_params(grid, c(g), c(b), c(bsh), c(tap), c(shift), None if gs is None else c(gs),
+                            None if bs is None else c(bs))
+            S, nb, nl = batch.nscen, grid.nb, grid.nl
+            dev = vm.device
+            L = torch.empty(S, dtype=torch.float64, device=dev)
+            gvm = torch.empty(S * nb, dtype=torch.float64, device=dev)
+            gva = torch.empty_like(gvm)
+            gp = [torch.empty(nl, dtype=torch.float64, device=dev) for _ in range(4)]
+            adjoint_elementwise(batch, c(vm), c(va), c(Pspec), c(Qspec), c(wP), c(wQ), L, gvm, gva, *gp)
+            ctx.save_for_backward(gvm.view_as(vm), gva.view_as(va), *gp)
+            return L.sum()
+
+        @staticmethod
+        def backward(ctx, grad):
+            gvm, gva, gg, gb, gbsh, gtap = ctx.saved_tensors
+            return (None, grad * gvm, grad * gva, grad * gg, grad * gb, grad * gbsh, grad * gtap,
+                    None, None, None, None, None, None, None)
+
+    return MismatchLoss
+
+
+try:
+    MismatchLoss = _mismatch_loss_function()
+except ImportError:   # torch absent: the C ABI binding still works on numpy inputs
+    MismatchLoss = None

@@ -1,0 +1,269 @@
+"""Batched N-1 evaluation and the adjoint against the oracle (GPU).
+
+Scenario s of a batch is checked against the oracle run from scratch on the
+grid without its outage branch: values within 1e-12 (max-norm relative per
+vector and Jacobian block), its Jacobian pattern bit-exact.  The adjoint is
+checked against J^T r of the oracle's Jacobian, complex-step branch-parameter
+gradients, and (25k-bus workload) long-double central differences on 200
+seeded coordinates.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gridcases import blocks, make_grid, random_grid, random_state, relerr
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pf():
+    from paper_2302_10736_gb300 import _build
+    _build.build_pfgrid()
+    from paper_2302_10736_gb300 import pfgrid
+    return pfgrid
+
+
+def _d(x):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def _skip(nl, l):
+    m = np.zeros(nl, np.uint8)
+    if l >= 0:
+        m[l] = 1
+    return m
+
+
+def _reduced(gr, l):
+    """The grid without branch l (branch arrays filtered) and the index map."""
+    if l < 0:
+        return gr, np.arange(gr["nl"])
+    keep = np.array([i for i in range(gr["nl"]) if i != l])
+    out = dict(gr)
+    for k in ("f", "t", "g", "b", "bsh", "tap", "shift"):
+        out[k] = gr[k][keep]
+    out["nl"] = gr["nl"] - 1
+    return out, keep
+
+
+def with_parallel(gr):
+    """Add a branch parallel to branch 0 so that an outage of either keeps the entry."""
+    out = dict(gr)
+    for k in ("f", "t", "g", "b", "bsh", "tap", "shift"):
+        v = gr[k][0] * (1.0 if k in ("f", "t", "tap", "shift") else 0.7)
+        out[k] = np.concatenate([gr[k], [v]]).astype(gr[k].dtype)
+    out["nl"] = gr["nl"] + 1
+    return out
+
+
+def check_batch(pf, gr, vm, va, outage, scenarios=None, tol=TOL):
+    import torch
+    S, nb = vm.shape
+    grid = pf.ybus_build(gr)
+    batch = pf.batch_create(grid, S, outage)
+    joff = pf.batch_jac_offsets(batch).cpu().numpy()
+    assert joff[0] == 0 and joff[-1] == batch.nnzJ_total
+    P = torch.full((S * nb,), np.nan, dtype=torch.float64, device="cuda")
+    Q = torch.full_like(P, np.nan)
+    J = torch.full((batch.nnzJ_total,), np.nan, dtype=torch.float64, device="cuda")
+    Pi = torch.full_like(P, np.nan)
+    Qi = torch.full_like(P, np.nan)
+    pf.jac_elementwise_batched(batch, _d(vm), _d(va), P, Q, J)
+    pf.inj_elementwise_batched(batch, _d(vm), _d(va), Pi, Qi)
+    torch.cuda.synchronize()
+    pf.grid_check_error(grid)
+    P, Q, J = P.cpu().numpy().reshape(S, nb), Q.cpu().numpy().reshape(S, nb), J.cpu().numpy()
+    Pi, Qi = Pi.cpu().numpy().reshape(S, nb), Qi.cpu().numpy().reshape(S, nb)
+    for s in (range(S) if scenarios is None else scenarios):
+        l = int(outage[s]) if outage is not None else -1
+        skip = _skip(gr["nl"], l)
+        Y = oracle.ybus(gr, skip=skip)
+        jrp, jci = oracle.jac_pattern(Y)
+        rp_s, ci_s = pf.batch_jac_pattern(batch, s)
+        assert np.array_equal(rp_s, jrp) and np.array_equal(ci_s, jci), s
+        assert joff[s + 1] - joff[s] == 4 * Y.nnz
+        Pr, Qr, Jr = oracle.elementwise(gr, vm[s], va[s], Y, skip=skip)
+        Js = J[joff[s]:joff[s + 1]]
+        errs = [relerr(P[s], Pr), relerr(Q[s], Qr), relerr(Pi[s], Pr), relerr(Qi[s], Qr)]
+        errs += [relerr(a, b) for a, b in zip(blocks(Js, jci, nb, Y.nnz), blocks(Jr, jci, nb, Y.nnz))]
+        assert max(errs) <= tol, (s, l, errs)
+    return batch
+
+
+def test_small_batch_with_outages_and_parallels(pf):
+    from paper_2302_10736_gb300 import synth
+    gr = with_parallel(random_grid(400, 560, 21, shift_max=0.2))
+    isb = synth.bridges(400, gr["f"], gr["t"])
+    nonbridge = np.flatnonzero(~isb)
+    outage = np.array([-1, int(nonbridge[3]), 0, gr["nl"] - 1, int(nonbridge[10]), int(np.flatnonzero(isb)[0]), -1,
+                       int(nonbridge[20])], np.int32)   # none, plain, both of a parallel pair, a bridge
+    vm, va = synth.voltages(400, len(outage), 21, 0, 0.93, 1.07, 0.25)
+    check_batch(pf, gr, vm, va, outage)
+
+
+def test_batch_without_outages_equals_single_evaluation(pf):
+    import torch
+    gr = random_grid(2000, 2700, 22)
+    vm, va = random_state(2000, 22, nscen=3)
+    grid = pf.ybus_build(gr)
+    batch = pf.batch_create(grid, 3, None)
+    J = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
+    P = torch.empty(3 * 2000, dtype=torch.float64, device="cuda")
+    Q = torch.empty_like(P)
+    pf.jac_elementwise_batched(batch, _d(vm), _d(va), P, Q, J)
+    for s in range(3):
+        P1 = torch.empty(2000, dtype=torch.float64, device="cuda")
+        Q1 = torch.empty_like(P1)
+        J1 = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+        pf.jac_elementwise(grid, _d(vm[s]), _d(va[s]), P1, Q1, J1)
+        assert torch.equal(P[s * 2000:(s + 1) * 2000], P1) and torch.equal(Q[s * 2000:(s + 1) * 2000], Q1)
+        assert torch.equal(J[s * grid.nnzJ:(s + 1) * grid.nnzJ], J1)
+
+
+def test_workload3_n1_batch(pf):
+    """10,000 buses x 1,024 scenarios with distinct non-bridge outages: every
+    scenario's P and Q, and the Jacobian of 48 spread scenarios, against the
+    oracle on the grid without the branch."""
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(3)
+    sample = sorted(set(np.linspace(0, 1023, 48).astype(int).tolist()))
+    batch = check_batch(pf, w, w["vm"], w["va"], w["outage"], scenarios=sample)
+    assert batch.nscen == 1024
+
+
+def _adjoint_case(nb, nl, seed, S, outage=None):
+    from paper_2302_10736_gb300 import synth
+    gr = random_grid(nb, nl, seed, shift_max=0.2)
+    vm, va = synth.voltages(nb, S, seed, 0, 0.95, 1.05, 0.2)
+    vm2, va2 = synth.voltages(nb, 1, seed, 1, 0.95, 1.05, 0.2)
+    Y = oracle.ybus(gr)
+    Ps, Qs = oracle.inj_sparse(Y, vm2[0], va2[0])
+    wP, wQ = synth.weights(nb, seed)
+    return gr, vm, va, Ps, Qs, wP, wQ
+
+
+def run_adjoint(pf, gr, vm, va, Ps, Qs, wP, wQ, outage=None):
+    import torch
+    S, nb = vm.shape
+    grid = pf.ybus_build(gr)
+    batch = pf.batch_create(grid, S, outage)
+    L = torch.empty(S, dtype=torch.float64, device="cuda")
+    gvm = torch.empty(S * nb, dtype=torch.float64, device="cuda")
+    gva = torch.empty_like(gvm)
+    gp = [torch.empty(gr["nl"], dtype=torch.float64, device="cuda") for _ in range(4)]
+    pf.adjoint_elementwise(batch, _d(vm), _d(va), _d(Ps), _d(Qs), _d(wP), _d(wQ), L, gvm, gva, *gp)
+    torch.cuda.synchronize()
+    pf.grid_check_error(grid)
+    return (L.cpu().numpy(), gvm.cpu().numpy().reshape(S, nb), gva.cpu().numpy().reshape(S, nb),
+            [x.cpu().numpy() for x in gp])
+
+
+def oracle_adjoint(gr, vm, va, Ps, Qs, wP, wQ, outage=None):
+    S, nb = vm.shape
+    Ls, gvm, gva = np.zeros(S), np.zeros((S, nb)), np.zeros((S, nb))
+    gp = [np.zeros(gr["nl"]) for _ in range(4)]
+    for s in range(S):
+        l = int(outage[s]) if outage is not None else -1
+        skip = _skip(gr["nl"], l)
+        Y = oracle.ybus(gr, skip=skip)
+        P, Q = oracle.inj_sparse(Y, vm[s], va[s])
+        J = oracle.jac_ybus(Y, vm[s], va[s])
+        Ls[s] = oracle.loss(P, Q, Ps, Qs, wP, wQ)
+        gva[s], gvm[s] = oracle.adjoint_state(Y, J, P, Q, Ps, Qs, wP, wQ)
+        gr_s, keep = _reduced(gr, l)
+        Y_s = oracle.ybus(gr_s)
+        for acc, part in zip(gp, oracle.adjoint_params_cstep(gr_s, Y_s, vm[s], va[s], Ps, Qs, wP, wQ)):
+            acc[keep] += part
+    return Ls, gvm, gva, gp
+
+
+@pytest.mark.parametrize("S,with_outage", [(1, False), (3, True)])
+def test_adjoint_matches_oracle(pf, S, with_outage):
+    gr, vm, va, Ps, Qs, wP, wQ = _adjoint_case(500, 700, 31 + S, S)
+    outage = None
+    if with_outage:
+        from paper_2302_10736_gb300 import synth
+        isb = synth.bridges(500, gr["f"], gr["t"])
+        nb_ = np.flatnonzero(~isb)
+        outage = np.array([int(nb_[0]), -1, int(nb_[5])][:S], np.int32)
+    L, gvm, gva, gp = run_adjoint(pf, gr, vm, va, Ps, Qs, wP, wQ, outage)
+    Lr, gvmr, gvar, gpr = oracle_adjoint(gr, vm, va, Ps, Qs, wP, wQ, outage)
+    assert relerr(L, Lr) <= TOL
+    for s in range(S):
+        assert relerr(gvm[s], gvmr[s]) <= TOL and relerr(gva[s], gvar[s]) <= TOL, s
+    for name, a, b in zip(("g", "b", "bsh", "tap"), gp, gpr):
+        assert relerr(a, b) <= TOL, name
+
+
+def test_adjoint_workload4_against_oracle_and_central_differences(pf):
+    """25,000 buses: J^T r and complex-step parameter gradients to 1e-12, and
+    central differences (h = 1e-7, long double) on 200 seeded coordinates."""
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(4)
+    Y = oracle.ybus(w)
+    Ps, Qs = oracle.inj_sparse(Y, w["vm2"], w["va2"])
+    vm, va = w["vm"], w["va"]
+    L, gvm, gva, gp = run_adjoint(pf, w, vm, va, Ps, Qs, w["wP"], w["wQ"])
+    Lr, gvmr, gvar, gpr = oracle_adjoint(w, vm, va, Ps, Qs, w["wP"], w["wQ"])
+    assert relerr(L, Lr) <= TOL
+    assert relerr(gvm[0], gvmr[0]) <= TOL and relerr(gva[0], gvar[0]) <= TOL
+    for a, b in zip(gp, gpr):
+        assert relerr(a, b) <= TOL
+    nb, nl = w["nb"], w["nl"]
+    kinds = synth.randint(w["seed"], 7, 200, 6)
+    idxs = np.array([synth.randint(w["seed"], 8 + i, 1, nb if k <= 1 else nl)[0] for i, k in enumerate(kinds)])
+    fd = oracle.loss_central_diff(w, vm[0], va[0], Ps, Qs, w["wP"], w["wQ"], kinds, idxs, 1e-7)
+    allg = [gva[0], gvm[0]] + gp
+    ad = np.array([allg[k][i] for k, i in zip(kinds, idxs)])
+    scale = np.array([np.max(np.abs(allg[k])) for k in kinds])
+    err = np.abs(ad - fd) / np.maximum(np.abs(fd), 1e-3 * scale)
+    assert err.max() <= 1e-6, err.max()
+
+
+def test_adjoint_workload5_sixteen_scenarios(pf):
+    """250,000 buses x 16 scenarios: losses and the scenario-summed parameter
+    gradients against the oracle; state gradients of 4 scenarios."""
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(5)
+    Y = oracle.ybus(w)
+    Ps, Qs = oracle.inj_sparse(Y, w["vm2"], w["va2"])
+    L, gvm, gva, gp = run_adjoint(pf, w, w["vm"], w["va"], Ps, Qs, w["wP"], w["wQ"])
+    Lr = np.zeros(16)
+    gpr = [np.zeros(w["nl"]) for _ in range(4)]
+    for s in range(16):
+        P, Q = oracle.inj_sparse(Y, w["vm"][s], w["va"][s])
+        Lr[s] = oracle.loss(P, Q, Ps, Qs, w["wP"], w["wQ"])
+        for acc, part in zip(gpr, oracle.adjoint_params_cstep(w, Y, w["vm"][s], w["va"][s], Ps, Qs, w["wP"],
+                                                              w["wQ"])):
+            acc += part
+        if s % 5 == 0:
+            P, Q = oracle.inj_sparse(Y, w["vm"][s], w["va"][s])
+            J = oracle.jac_ybus(Y, w["vm"][s], w["va"][s])
+            gar, gvr = oracle.adjoint_state(Y, J, P, Q, Ps, Qs, w["wP"], w["wQ"])
+            assert relerr(gva[s], gar) <= TOL and relerr(gvm[s], gvr) <= TOL, s
+    assert relerr(L, Lr) <= TOL
+    for a, b in zip(gp, gpr):
+        assert relerr(a, b) <= TOL
+
+
+def test_mismatch_loss_autograd(pf):
+    import torch
+    gr, vm, va, Ps, Qs, wP, wQ = _adjoint_case(300, 420, 41, 2)
+    grid = pf.ybus_build(gr)
+    batch = pf.batch_create(grid, 2, None)
+    t = lambda x, rg=False: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda",
+                                         requires_grad=rg)
+    vm_t, va_t = t(vm, True), t(va, True)
+    g_t, b_t, bsh_t, tap_t = t(gr["g"], True), t(gr["b"], True), t(gr["bsh"], True), t(gr["tap"], True)
+    loss = pf.MismatchLoss.apply(batch, vm_t, va_t, g_t, b_t, bsh_t, tap_t, t(gr["shift"]), t(gr["gs"]),
+                                 t(gr["bs"]), t(Ps), t(Qs), t(wP), t(wQ))
+    (2.0 * loss).backward()
+    Lr, gvmr, gvar, gpr = oracle_adjoint(gr, vm, va, Ps, Qs, wP, wQ)
+    assert abs(loss.item() - Lr.sum()) <= TOL * abs(Lr.sum())
+    assert relerr(vm_t.grad.cpu().numpy(), 2 * gvmr) <= TOL
+    assert relerr(va_t.grad.cpu().numpy(), 2 * gvar) <= TOL
+    for tt, ref in zip((g_t, b_t, bsh_t, tap_t), gpr):
+        assert relerr(tt.grad.cpu().numpy(), 2 * ref) <= TOL
