@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
     return ap.parse_args()
 
 
@@ -157,6 +158,96 @@ def time_loop(torch, fn, steps, flush, name):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+
+
+def graph_of(torch, fn):
+    """Capture fn (one library launch) into a CUDA graph after one eager warm-up."""
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
+def timed_replays(torch, g, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_workloads(torch, pfgrid, synth, reps):
+    """The batched and adjoint workloads, each timed from a CUDA-graph replay
+    (inputs larger than L2 for the batched ones, so no flush is needed)."""
+    out = {}
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+    # N-1 batch: 10,000 buses x 1,024 scenarios, each without a distinct non-bridge branch
+    w = synth.workload(3)
+    grid = pfgrid.ybus_build(w)
+    S, nb, T = w["nscen"], w["nb"], 2 * w["nl"]
+    batch = pfgrid.batch_create(grid, S, w["outage"])
+    vm, va = dev(w["vm"]), dev(w["va"])
+    P = torch.empty(S * nb, dtype=torch.float64, device="cuda")
+    Q = torch.empty_like(P)
+    J = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
+    g = graph_of(torch, lambda: pfgrid.jac_elementwise_batched(batch, vm, va, P, Q, J))
+    ms = timed_replays(torch, g, reps)
+    ops = S * (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb)
+    byt = S * (16 * nb + 16 * nb) + 8 * batch.nnzJ_total + 40 * T + 84 * nb
+    out["n1_batch_10k_x1024"] = {
+        "evals_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
+        "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / FP64_OPS_PEAK_G,
+        "hbm_gbs": byt / (ms * 1e-3) / 1e9, "jacobian_values": batch.nnzJ_total}
+    pfgrid.grid_check_error(grid)
+    del batch, J, P, Q, g
+
+    # adjoint of the mismatch loss: 25,000 buses, one state
+    for k, key in ((4, "adjoint_25k"), (5, "batched_jac_and_adjoint_250k_x16")):
+        w = synth.workload(k)
+        grid = pfgrid.ybus_build(w)
+        S, nb, nl, T = w["nscen"], w["nb"], w["nl"], 2 * w["nl"]
+        batch = pfgrid.batch_create(grid, S, None)
+        Ps = torch.empty(nb, dtype=torch.float64, device="cuda")
+        Qs = torch.empty_like(Ps)
+        pfgrid.inj_elementwise(grid, dev(w["vm2"]), dev(w["va2"]), Ps, Qs)
+        vm, va, wP, wQ = dev(w["vm"]), dev(w["va"]), dev(w["wP"]), dev(w["wQ"])
+        L = torch.empty(S, dtype=torch.float64, device="cuda")
+        gvm = torch.empty(S * nb, dtype=torch.float64, device="cuda")
+        gva = torch.empty_like(gvm)
+        gp = [torch.empty(nl, dtype=torch.float64, device="cuda") for _ in range(4)]
+        g = graph_of(torch, lambda: pfgrid.adjoint_elementwise(batch, vm, va, Ps, Qs, wP, wQ, L, gvm, gva, *gp))
+        ms = timed_replays(torch, g, reps)
+        ops = S * ((21 + 8 + 8) * nb + (10 + 22) * T + 48 * nl)
+        res = {"loss_and_gradients_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
+               "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / FP64_OPS_PEAK_G}
+        if k == 5:
+            P = torch.empty(S * nb, dtype=torch.float64, device="cuda")
+            Q = torch.empty_like(P)
+            J = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
+            g2 = graph_of(torch, lambda: pfgrid.jac_elementwise_batched(batch, vm, va, P, Q, J))
+            ms2 = timed_replays(torch, g2, reps)
+            ops2 = S * (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb)
+            res.update({"jac_evals_per_s": S / (ms2 * 1e-3), "jac_ms_per_launch": ms2,
+                        "jac_fp64_frac": ops2 / (ms2 * 1e-3) / 1e9 / FP64_OPS_PEAK_G})
+            # the plain single-scenario Ybus path on the same grid, for comparison
+            J1 = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+            P1 = torch.empty(nb, dtype=torch.float64, device="cuda")
+            Q1 = torch.empty_like(P1)
+            g3 = graph_of(torch, lambda: pfgrid.jac_ybus(grid, vm[:nb], va[:nb], P1, Q1, J1))
+            res["single_scenario_ybus_jac_evals_per_s"] = 1e3 / timed_replays(torch, g3, reps)
+            del g2, g3
+        out[key] = res
+        pfgrid.grid_check_error(grid)
+        del batch, g
+    return out
 
 
 def main():
@@ -271,6 +362,13 @@ def main():
         cpu = {"value": n / el, "unit": "evals/s", "cores": 1, "kind": "oracle",
                "sample": "%d full element-wise evaluations (P, Q, J) of the 70k-bus grid, single thread" % n}
 
+    extra = None
+    if rank == 0 and not args.no_extra:
+        try:
+            extra = extra_workloads(torch, pfgrid, synth, max(3, min(args.steps, 20)))
+        except Exception as ex:  # reported, never silently replaced
+            extra = {"error": str(ex)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -291,6 +389,7 @@ def main():
                               "inj_ew": kmean(tr_inj, "inj_ew")[0], "inj_ybus": kmean(tr_inj, "inj_ybus")[0]},
                 "ybus_fp64_ops_per_launch": YB_OPS_PER_NNZ * grid.nnz + YB_OPS_PER_ROW * nb,
             },
+            "workloads": extra,
         }
         print(json.dumps(line), flush=True)
     if dist:
