@@ -39,7 +39,7 @@ YB_OPS_PER_NNZ = 16
 YB_OPS_PER_ROW = 16
 
 
-def parse():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
-    return ap.parse_args()
+    ap.add_argument("--profile-workload", choices=["n1", "adjoint4", "batched5", "permuted"],
+                    help="run only this batched/adjoint workload (few launches, for profilers) and exit")
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -144,6 +146,17 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def job_throughput(torch, ms_local, world, dist, device):
+    """(step time, whole-job evals/s) of `world` replicas that each evaluate
+    one grid per step: the job's step time is the slowest rank's."""
+    ms = ms_local
+    if dist is not None:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * 1e3 / ms
+
+
 def time_loop(torch, fn, steps, flush, name):
     """Per-step device time (ms) of fn(), L2 flushed before every step outside
     the events; the loop is an NVTX range so profilers can select it."""
@@ -170,22 +183,62 @@ def graph_of(torch, fn):
     return g
 
 
-def timed_replays(torch, g, reps):
+def timed_replays(torch, g, reps, name="replays"):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(2):
         g.replay()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push(name)
     e0.record()
     for _ in range(reps):
         g.replay()
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
 
 
-def extra_workloads(torch, pfgrid, synth, reps):
+def extra_workloads(torch, pfgrid, synth, reps, only=None):
     """The batched and adjoint workloads, each timed from a CUDA-graph replay
-    (inputs larger than L2 for the batched ones, so no flush is needed)."""
+    (inputs larger than L2 for the batched ones, so no flush is needed).
+    `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted"."""
+    out = {}
+    if only in (None, "n1"):
+        out.update(_n1_workload(torch, pfgrid, synth, reps))
+    for k, key, tag in ((4, "adjoint_25k", "adjoint4"), (5, "batched_jac_and_adjoint_250k_x16", "batched5")):
+        if only in (None, tag):
+            out[key] = _adjoint_workload(torch, pfgrid, synth, reps, k)
+    if only in (None, "permuted"):
+        out["c2_random_bus_order"] = _permuted_workload(torch, pfgrid, synth, max(reps, 20))
+    return out
+
+
+def _permuted_workload(torch, pfgrid, synth, steps):
+    """The 70k-bus grid with its buses renumbered at random (no locality in
+    the numbering): single evaluations by both methods, L2 flushed between
+    steps, against the same grid in its own numbering."""
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    res = {}
+    base = synth.workload(WORKLOAD)
+    for tag, w in (("own_numbering", base), ("random_numbering", synth.renumber_buses(base, synth.BASE_SEED))):
+        grid = pfgrid.ybus_build(w)
+        pfgrid.grid_autotune(grid, dev(w["vm"][0]), dev(w["va"][0]), reps=10)
+        vm, va = dev(w["vm"][0]), dev(w["va"][0])
+        P = torch.empty(w["nb"], dtype=torch.float64, device="cuda")
+        Q = torch.empty_like(P)
+        J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+        for name, fn in (("elementwise", pfgrid.jac_elementwise), ("ybus", pfgrid.jac_ybus)):
+            f = lambda: fn(grid, vm, va, P, Q, J)
+            for _ in range(3):
+                f()
+            t = time_loop(torch, f, steps, flush, "perm_" + name)
+            res["%s_%s_evals_per_s" % (name, tag)] = 1e3 / (sum(t) / len(t))
+        pfgrid.grid_check_error(grid)
+    return res
+
+
+def _n1_workload(torch, pfgrid, synth, reps):
     out = {}
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
@@ -199,59 +252,74 @@ def extra_workloads(torch, pfgrid, synth, reps):
     Q = torch.empty_like(P)
     J = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
     g = graph_of(torch, lambda: pfgrid.jac_elementwise_batched(batch, vm, va, P, Q, J))
-    ms = timed_replays(torch, g, reps)
+    ms = timed_replays(torch, g, reps, "n1_batch")
     ops = S * (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb)
     byt = S * (16 * nb + 16 * nb) + 8 * batch.nnzJ_total + 40 * T + 84 * nb
     out["n1_batch_10k_x1024"] = {
         "evals_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
         "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / FP64_OPS_PEAK_G,
         "hbm_gbs": byt / (ms * 1e-3) / 1e9, "jacobian_values": batch.nnzJ_total}
+    # the same batch by the Ybus method (phasor launch + row launch)
+    g2 = graph_of(torch, lambda: pfgrid.jac_ybus_batched(batch, vm, va, P, Q, J))
+    ms2 = timed_replays(torch, g2, reps, "n1_batch_ybus")
+    out["n1_batch_10k_x1024"].update({"ybus_evals_per_s": S / (ms2 * 1e-3), "ybus_ms_per_launch": ms2,
+                                      "ybus_launches": 2})
+    # the plain single-scenario paths on the base grid, one state per launch (L2 warm)
+    P1 = torch.empty(nb, dtype=torch.float64, device="cuda")
+    Q1 = torch.empty_like(P1)
+    J1 = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+    for key, fn in (("single_elementwise_evals_per_s", pfgrid.jac_elementwise),
+                    ("single_ybus_evals_per_s", pfgrid.jac_ybus)):
+        g3 = graph_of(torch, lambda: fn(grid, vm[:nb], va[:nb], P1, Q1, J1))
+        out["n1_batch_10k_x1024"][key] = 1e3 / timed_replays(torch, g3, reps, "n1_single")
     pfgrid.grid_check_error(grid)
-    del batch, J, P, Q, g
-
-    # adjoint of the mismatch loss: 25,000 buses, one state
-    for k, key in ((4, "adjoint_25k"), (5, "batched_jac_and_adjoint_250k_x16")):
-        w = synth.workload(k)
-        grid = pfgrid.ybus_build(w)
-        S, nb, nl, T = w["nscen"], w["nb"], w["nl"], 2 * w["nl"]
-        batch = pfgrid.batch_create(grid, S, None)
-        Ps = torch.empty(nb, dtype=torch.float64, device="cuda")
-        Qs = torch.empty_like(Ps)
-        pfgrid.inj_elementwise(grid, dev(w["vm2"]), dev(w["va2"]), Ps, Qs)
-        vm, va, wP, wQ = dev(w["vm"]), dev(w["va"]), dev(w["wP"]), dev(w["wQ"])
-        L = torch.empty(S, dtype=torch.float64, device="cuda")
-        gvm = torch.empty(S * nb, dtype=torch.float64, device="cuda")
-        gva = torch.empty_like(gvm)
-        gp = [torch.empty(nl, dtype=torch.float64, device="cuda") for _ in range(4)]
-        g = graph_of(torch, lambda: pfgrid.adjoint_elementwise(batch, vm, va, Ps, Qs, wP, wQ, L, gvm, gva, *gp))
-        ms = timed_replays(torch, g, reps)
-        ops = S * ((21 + 8 + 8) * nb + (10 + 22) * T + 48 * nl)
-        res = {"loss_and_gradients_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
-               "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / FP64_OPS_PEAK_G}
-        if k == 5:
-            P = torch.empty(S * nb, dtype=torch.float64, device="cuda")
-            Q = torch.empty_like(P)
-            J = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
-            g2 = graph_of(torch, lambda: pfgrid.jac_elementwise_batched(batch, vm, va, P, Q, J))
-            ms2 = timed_replays(torch, g2, reps)
-            ops2 = S * (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb)
-            res.update({"jac_evals_per_s": S / (ms2 * 1e-3), "jac_ms_per_launch": ms2,
-                        "jac_fp64_frac": ops2 / (ms2 * 1e-3) / 1e9 / FP64_OPS_PEAK_G})
-            # the plain single-scenario Ybus path on the same grid, for comparison
-            J1 = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
-            P1 = torch.empty(nb, dtype=torch.float64, device="cuda")
-            Q1 = torch.empty_like(P1)
-            g3 = graph_of(torch, lambda: pfgrid.jac_ybus(grid, vm[:nb], va[:nb], P1, Q1, J1))
-            res["single_scenario_ybus_jac_evals_per_s"] = 1e3 / timed_replays(torch, g3, reps)
-            del g2, g3
-        out[key] = res
-        pfgrid.grid_check_error(grid)
-        del batch, g
     return out
 
 
+def _adjoint_workload(torch, pfgrid, synth, reps, k):
+    """Adjoint of the mismatch loss on workload k (25k buses x 1, or 250k x 16
+    with the batched Jacobian and the single-scenario Ybus Jacobian beside it)."""
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    w = synth.workload(k)
+    grid = pfgrid.ybus_build(w)
+    S, nb, nl, T = w["nscen"], w["nb"], w["nl"], 2 * w["nl"]
+    batch = pfgrid.batch_create(grid, S, None)
+    Ps = torch.empty(nb, dtype=torch.float64, device="cuda")
+    Qs = torch.empty_like(Ps)
+    pfgrid.inj_elementwise(grid, dev(w["vm2"]), dev(w["va2"]), Ps, Qs)
+    vm, va, wP, wQ = dev(w["vm"]), dev(w["va"]), dev(w["wP"]), dev(w["wQ"])
+    L = torch.empty(S, dtype=torch.float64, device="cuda")
+    gvm = torch.empty(S * nb, dtype=torch.float64, device="cuda")
+    gva = torch.empty_like(gvm)
+    gp = [torch.empty(nl, dtype=torch.float64, device="cuda") for _ in range(4)]
+    g = graph_of(torch, lambda: pfgrid.adjoint_elementwise(batch, vm, va, Ps, Qs, wP, wQ, L, gvm, gva, *gp))
+    ms = timed_replays(torch, g, reps, "adjoint%d" % k)
+    ops = S * ((21 + 8 + 8) * nb + (10 + 22) * T + 48 * nl)
+    res = {"loss_and_gradients_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
+           "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / FP64_OPS_PEAK_G}
+    if k == 5:
+        P = torch.empty(S * nb, dtype=torch.float64, device="cuda")
+        Q = torch.empty_like(P)
+        J = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
+        g2 = graph_of(torch, lambda: pfgrid.jac_elementwise_batched(batch, vm, va, P, Q, J))
+        ms2 = timed_replays(torch, g2, reps, "batched5")
+        ops2 = S * (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb)
+        res.update({"jac_evals_per_s": S / (ms2 * 1e-3), "jac_ms_per_launch": ms2,
+                    "jac_fp64_frac": ops2 / (ms2 * 1e-3) / 1e9 / FP64_OPS_PEAK_G})
+        g4 = graph_of(torch, lambda: pfgrid.jac_ybus_batched(batch, vm, va, P, Q, J))
+        res["ybus_batched_jac_evals_per_s"] = S * 1e3 / timed_replays(torch, g4, reps, "ybus_batched5")
+        # the plain single-scenario Ybus path on the same grid, for comparison
+        J1 = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+        P1 = torch.empty(nb, dtype=torch.float64, device="cuda")
+        Q1 = torch.empty_like(P1)
+        g3 = graph_of(torch, lambda: pfgrid.jac_ybus(grid, vm[:nb], va[:nb], P1, Q1, J1))
+        res["single_scenario_ybus_jac_evals_per_s"] = 1e3 / timed_replays(torch, g3, reps, "ybus5")
+    pfgrid.grid_check_error(grid)
+    return res
+
+
 def main():
-    args = parse()
+    args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
     import torch
@@ -259,6 +327,9 @@ def main():
     from paper_2302_10736_gb300 import pfgrid, synth
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if args.profile_workload:
+        print(json.dumps(extra_workloads(torch, pfgrid, synth, max(1, args.steps), args.profile_workload)))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -311,12 +382,7 @@ def main():
     pfgrid.grid_trace_enable(grid, 0)
     pfgrid.grid_check_error(grid)
 
-    ms_step = sum(t_ew) / len(t_ew)
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * 1e3 / ms_step
+    ms_step, value = job_throughput(torch, sum(t_ew) / len(t_ew), world, dist, "cuda")
 
     def kmean(tr, name):
         xs = [ms for k, ms in tr if k == name]

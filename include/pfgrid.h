@@ -294,6 +294,27 @@ pf_status jac_elementwise_batched(pf_batch *batch, const double *vm, const doubl
                                   double *J, pf_stream stream);
 
 /*
+ * Ybus-method injections of every scenario (Eq. 1 per scenario): the phasor
+ * step over all nscen * nb buses, then W = config.ybus_lanes lanes per
+ * (scenario, row) of the shared base CSR Ybus, with the outage branch's
+ * terminal constants taken out of its two end rows on the fly (the coupling
+ * entry dropped when it leaves the pattern).  Two launches, capturable in a
+ * CUDA graph.  Same arguments as inj_elementwise_batched; PF_EUNSUPPORTED if
+ * nscen * nb exceeds 2^31 - 1.
+ */
+pf_status inj_ybus_batched(pf_batch *batch, const double *vm, const double *va, double *P, double *Q,
+                           pf_stream stream);
+
+/*
+ * Ybus-method Jacobian values of every scenario (Eqs. 2-4 per scenario, as
+ * jac_ybus on the scenario's admittance matrix), written compacted onto the
+ * scenario's own pattern like jac_elementwise_batched.  Same arguments and
+ * layout as jac_elementwise_batched.
+ */
+pf_status jac_ybus_batched(pf_batch *batch, const double *vm, const double *va, double *P, double *Q, double *J,
+                           pf_stream stream);
+
+/*
  * Adjoint of the mismatch loss, one cooperative launch (the paper has no
  * adjoint; it differentiates the element-wise flows of Eqs. 5-7):
  *   L_s = sum_i wP_i (P_si - Pspec_i)^2 + wQ_i (Q_si - Qspec_i)^2
@@ -314,11 +335,13 @@ pf_status adjoint_elementwise(pf_batch *batch, const double *vm, const double *v
 
 /*
  * Fault injection for tests of the bounded device-side waits (no GPU fault
- * is involved): moves the arrival counter of the element-wise kernels' grid
- * barrier out of range, so in the next element-wise evaluation no CTA ever
- * sees the last arrival; each CTA gives up after 1 s, skips its work and sets
- * the device error word, and grid_check_error then returns PF_ETIMEOUT and
- * resets the barrier.  Synchronizes `stream`.
+ * is involved): moves the arrival counter of the grid barrier that the
+ * batched element-wise and adjoint kernels of this grid's batches share out
+ * of range, so in the next such launch no CTA ever sees the last arrival;
+ * each CTA gives up after 2 s, skips its work and sets the device error word,
+ * and grid_check_error then returns PF_ETIMEOUT and resets the barrier.
+ * (The single-scenario kernels have no grid-wide wait.)  Synchronizes
+ * `stream`.
  */
 pf_status grid_inject_barrier_fault(pf_grid *grid, pf_stream stream);
 
@@ -333,7 +356,9 @@ pf_status grid_inject_barrier_fault(pf_grid *grid, pf_stream stream);
 #define PF_K_INJ_EW_BATCHED 5
 #define PF_K_JAC_EW_BATCHED 6
 #define PF_K_ADJOINT 7
-#define PF_K_COUNT 8
+#define PF_K_INJ_YBUS_BATCHED 8
+#define PF_K_JAC_YBUS_BATCHED 9
+#define PF_K_COUNT 10
 
 typedef struct {
     int32_t kernel;          /* PF_K_* */

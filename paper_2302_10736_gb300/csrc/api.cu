@@ -18,6 +18,7 @@
 #include <new>
 #include <numeric>
 
+#include "fastmath.cuh"
 #include "pf_internal.h"
 
 namespace pf {
@@ -145,22 +146,27 @@ static pf_status build_ew_layout(Grid *g, int tb, cudaStream_t s)
     HostEw E;
     pf_status st = host_ew(g->topo, tb, E);
     if (st) return st;
-    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true);
-    if (plan.total > kMaxSmem)
+    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true, E.max_nbus + E.max_nh);
+    if (plan.total + kTrigN * sizeof(double2) > kMaxSmem)
         return set_error(PF_EUNSUPPORTED, "an element-wise window needs %u bytes of shared memory (max %u): a bus "
                                           "has too many branches for this library", plan.total, kMaxSmem);
 #ifdef PF_SELFCHECK
     if ((st = host_selfcheck(g->topo, E))) return st;
 #endif
     g->arena.release(g->ew.win_bus);
+    g->arena.release(g->ew.hptr);
+    g->arena.release(g->ew.hbus);
+    g->arena.release(g->ew.tloc);
     g->ew = EwDev{};
-    if ((st = upload(g->arena, &g->ew.win_bus, E.win_bus, s))) return st;
+    if ((st = upload(g->arena, &g->ew.win_bus, E.win_bus, s)) || (st = upload(g->arena, &g->ew.hptr, E.hptr, s)) ||
+        (st = upload(g->arena, &g->ew.hbus, E.hbus, s)) || (st = upload(g->arena, &g->ew.tloc, E.tloc, s)))
+        return st;
     g->ew.tb = E.tb;
     g->ew.nwin = E.nwin;
     g->ew.max_L = E.max_L;
     g->ew.max_nt = E.max_nt;
     g->ew.max_nbus = E.max_nbus;
-    g->ew_resident_jac = g->ew_resident_inj = 0;   // shared-memory needs changed
+    g->ew.max_nh = E.max_nh;
     PF_CUDA(cudaStreamSynchronize(s));  // E's vectors are freed on return
     return PF_OK;
 }
@@ -591,8 +597,9 @@ out:
 
 PF_API const char *pf_kernel_name(int32_t k)
 {
-    static const char *names[PF_K_COUNT] = {"phasor",     "inj_ybus",      "jac_ybus",      "inj_ew",
-                                            "jac_ew",     "inj_ew_batched", "jac_ew_batched", "adjoint"};
+    static const char *names[PF_K_COUNT] = {"phasor",         "inj_ybus",       "jac_ybus",        "inj_ew",
+                                            "jac_ew",         "inj_ew_batched", "jac_ew_batched",  "adjoint",
+                                            "inj_ybus_batched", "jac_ybus_batched"};
     return (k >= 0 && k < PF_K_COUNT) ? names[k] : "?";
 }
 

@@ -1,8 +1,10 @@
 // batch.cu - C ABI of scenario batches: N-1 contingency evaluation and the
 // adjoint of the mismatch loss (see k_batched.cu for the kernels).
 #include <algorithm>
+#include <climits>
 #include <new>
 
+#include "fastmath.cuh"
 #include "pf_internal.h"
 
 using namespace pf;
@@ -53,11 +55,40 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
         b->h_sc[s] = scen_outage(g->topo, outage ? outage[s] : -1);
         b->h_joff[s + 1] = b->h_joff[s] + 4LL * (g->nnz - 2 * b->h_sc[s].del);
     }
+    // the batch's own windows: 256 buses and up to 3 x 256 terminals each
+    // (fewer terminals per thread if a window would not fit in shared memory)
+    HostEw E;
+    for (int tfac = 3; tfac >= 1; --tfac) {
+        pf_status hs = host_ew(g->topo, 256, E, tfac);
+        if (hs) {
+            delete pb;
+            return hs;
+        }
+        if (ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true).total + kTrigN * sizeof(double2) <= kMaxSmem) break;
+        if (tfac == 1) {
+            delete pb;
+            return set_error(PF_EUNSUPPORTED, "batch_create: a window exceeds shared memory");
+        }
+    }
+#ifdef PF_SELFCHECK
+    if (pf_status hs = host_selfcheck(g->topo, E)) {
+        delete pb;
+        return hs;
+    }
+#endif
+    b->tb = E.tb;
+    b->nwin = E.nwin;
+    b->max_L = E.max_L;
+    b->max_nt = E.max_nt;
+    b->max_nbus = E.max_nbus;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)nscen * g->nb;
-    const size_t nw = (size_t)nscen * std::max(g->ew.nwin, 1);
+    const size_t nw = (size_t)nscen * std::max(b->nwin, 1);
     cudaError_t e = cudaSuccess;
     if ((e = b->arena.alloc(&b->sc, std::max(nscen, 1))) || (e = b->arena.alloc(&b->joff, nscen + 1)) ||
+        (e = b->arena.alloc(&b->win_bus, E.win_bus.size())) ||
+        (e = cudaMemcpyAsync(b->win_bus, E.win_bus.data(), sizeof(int) * E.win_bus.size(), cudaMemcpyHostToDevice,
+                             st)) ||
         (e = b->arena.alloc(&b->U, n)) || (e = b->arena.alloc(&b->V, n)) || (e = b->arena.alloc(&b->r, n)) ||
         (e = b->arena.alloc(&b->lpart, nw)) ||
         (nscen && (e = cudaMemcpyAsync(b->sc, b->h_sc.data(), sizeof(ScenOut) * nscen, cudaMemcpyHostToDevice, st))) ||
@@ -164,6 +195,41 @@ PF_API pf_status jac_elementwise_batched(pf_batch *batch, const double *vm, cons
         return set_error(PF_EINVAL, "jac_elementwise_batched: P and Q must both be set or both NULL");
     TraceScope t(batch->b.g, PF_K_JAC_EW_BATCHED, (cudaStream_t)stream);
     PF_CUDA(launch_ew_batched(&batch->b, true, vm, va, P, Q, J, (cudaStream_t)stream));
+    return PF_OK;
+}
+
+static pf_status check_ybus_batch(pf_batch *batch, const char *name)
+{
+    if ((long long)batch->b.S * batch->b.g->nb > INT32_MAX)
+        return set_error(PF_EUNSUPPORTED, "%s: nscen * nb above 2^31 - 1", name);
+    return PF_OK;
+}
+
+PF_API pf_status inj_ybus_batched(pf_batch *batch, const double *vm, const double *va, double *P, double *Q,
+                                  pf_stream stream)
+{
+    pf_status st = check_batch(batch, vm, va, "inj_ybus_batched");
+    if (st) return st;
+    if (batch->b.S == 0 || batch->b.g->nb == 0) return PF_OK;
+    if (!P || !Q) return set_error(PF_EINVAL, "inj_ybus_batched: P or Q is NULL");
+    if ((st = check_ybus_batch(batch, "inj_ybus_batched"))) return st;
+    TraceScope t(batch->b.g, PF_K_INJ_YBUS_BATCHED, (cudaStream_t)stream);
+    PF_CUDA(launch_ybus_batched(&batch->b, false, vm, va, P, Q, nullptr, (cudaStream_t)stream));
+    return PF_OK;
+}
+
+PF_API pf_status jac_ybus_batched(pf_batch *batch, const double *vm, const double *va, double *P, double *Q,
+                                  double *J, pf_stream stream)
+{
+    pf_status st = check_batch(batch, vm, va, "jac_ybus_batched");
+    if (st) return st;
+    if (batch->b.S == 0 || batch->b.g->nb == 0) return PF_OK;
+    if (!J) return set_error(PF_EINVAL, "jac_ybus_batched: J is NULL");
+    if ((P == nullptr) != (Q == nullptr))
+        return set_error(PF_EINVAL, "jac_ybus_batched: P and Q must both be set or both NULL");
+    if ((st = check_ybus_batch(batch, "jac_ybus_batched"))) return st;
+    TraceScope t(batch->b.g, PF_K_JAC_YBUS_BATCHED, (cudaStream_t)stream);
+    PF_CUDA(launch_ybus_batched(&batch->b, true, vm, va, P, Q, J, (cudaStream_t)stream));
     return PF_OK;
 }
 

@@ -11,7 +11,8 @@
 //                      parallel branches share an entry; per entry the range
 //                      of sorted terminals whose stamps it sums
 //   J pattern          closed form of Alg. 2 (see include/pfgrid.h)
-//   element-wise       windows of consecutive buses for one CTA each
+//   element-wise       windows of consecutive buses for one CTA each, with
+//                      their ghost buses (other ends outside the window)
 #include <algorithm>
 #include <cstdint>
 
@@ -108,23 +109,25 @@ pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo
     return PF_OK;
 }
 
-pf_status host_ew(const HostTopo &H, int tb, HostEw &E)
+pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac)
 {
     if (tb != 128 && tb != 256)
         return set_error(PF_EINVAL, "ew_window (threads per element-wise CTA) must be 128 or 256 (got %d)", tb);
+    if (tfac < 1 || tfac > 4) return set_error(PF_EINVAL, "terminals per thread must be 1 .. 4 (got %d)", tfac);
     const int nb = H.nb;
     E = HostEw{};
     E.tb = tb;
+    E.tfac = tfac;
     E.win_bus.push_back(0);
     int b = 0;
     while (b < nb) {
         const int b0 = b;
         int nt = 0;
-        // greedy: at most tb buses and tb terminals; a bus with more than tb
+        // greedy: at most tb buses and tfac * tb terminals; a bus with more
         // terminals still forms a window by itself
         while (b < nb && b - b0 < tb) {
             const int t_here = H.tp[b + 1] - H.tp[b];
-            if (b > b0 && nt + t_here > tb) break;
+            if (b > b0 && nt + t_here > tfac * tb) break;
             nt += t_here;
             ++b;
         }
@@ -134,6 +137,31 @@ pf_status host_ew(const HostTopo &H, int tb, HostEw &E)
         E.max_L = std::max(E.max_L, 2 * (H.rp[b] - H.rp[b0]));
     }
     E.nwin = (int)E.win_bus.size() - 1;
+    // ghost buses and the window-local slot of every terminal's other bus
+    E.hptr.assign(E.nwin + 1, 0);
+    E.hbus.clear();
+    E.tloc.assign(H.tp[nb], make_int2(0, 0));
+    std::vector<int> ghosts;
+    for (int w = 0; w < E.nwin; ++w) {
+        const int b0 = E.win_bus[w], b1 = E.win_bus[w + 1], nbus = b1 - b0;
+        ghosts.clear();
+        for (int p = H.tp[b0]; p < H.tp[b1]; ++p) {
+            const int q = H.tnbr[p].x;
+            if (q < b0 || q >= b1) ghosts.push_back(q);
+        }
+        std::sort(ghosts.begin(), ghosts.end());
+        ghosts.erase(std::unique(ghosts.begin(), ghosts.end()), ghosts.end());
+        for (int p = H.tp[b0]; p < H.tp[b1]; ++p) {
+            const int q = H.tnbr[p].x;
+            const int slot = (q >= b0 && q < b1)
+                                 ? q - b0
+                                 : nbus + (int)(std::lower_bound(ghosts.begin(), ghosts.end(), q) - ghosts.begin());
+            E.tloc[p] = make_int2(slot, H.tnbr[p].y);
+        }
+        E.hbus.insert(E.hbus.end(), ghosts.begin(), ghosts.end());
+        E.hptr[w + 1] = (int)E.hbus.size();
+        E.max_nh = std::max(E.max_nh, (int)ghosts.size());
+    }
     return PF_OK;
 }
 
@@ -183,7 +211,7 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
         const int nbus = b1 - b0, nt = H.tp[b1] - H.tp[b0];
         const int L = 2 * (H.rp[b1] - H.rp[b0]);
         CHECK(nbus >= 1 && nbus <= E.tb && nbus <= E.max_nbus, "window %d bus count %d", w, nbus);
-        CHECK(nt <= E.max_nt && (nt <= E.tb || nbus == 1), "window %d terminal count %d", w, nt);
+        CHECK(nt <= E.max_nt && (nt <= E.tfac * E.tb || nbus == 1), "window %d terminal count %d", w, nt);
         CHECK(L >= 2 && L <= E.max_L, "window %d slice length", w);
         // bulk-store constraints: the J slices start on 16 bytes and are 16-byte multiples
         CHECK((2LL * H.rp[b0]) % 2 == 0 && (8LL * L) % 16 == 0, "window %d J slice alignment", w);
@@ -198,9 +226,30 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
             }
         }
     }
-    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true);
+    // ghost buses: sorted, outside the window, and every terminal's slot
+    // names its other bus
+    CHECK((int)E.hptr.size() == E.nwin + 1 && E.hptr[0] == 0 && E.hptr[E.nwin] == (int)E.hbus.size(),
+          "ghost-bus offsets");
+    CHECK((int)E.tloc.size() == T, "terminal slots");
+    for (int w = 0; w < E.nwin; ++w) {
+        const int b0 = E.win_bus[w], b1 = E.win_bus[w + 1], nbus = b1 - b0;
+        const int h0 = E.hptr[w], nh = E.hptr[w + 1] - h0;
+        CHECK(nh >= 0 && nh <= E.max_nh, "window %d ghost count %d", w, nh);
+        for (int j = 0; j < nh; ++j) {
+            const int q = E.hbus[h0 + j];
+            CHECK(q >= 0 && q < nb && (q < b0 || q >= b1), "window %d ghost %d", w, j);
+            if (j > 0) CHECK(q > E.hbus[h0 + j - 1], "window %d ghosts not strictly sorted", w);
+        }
+        for (int p = H.tp[b0]; p < H.tp[b1]; ++p) {
+            const int slot = E.tloc[p].x, q = H.tnbr[p].x;
+            CHECK(E.tloc[p].y == H.tnbr[p].y, "terminal %d slot flags", p);
+            CHECK(slot >= 0 && slot < nbus + nh, "terminal %d phasor slot %d", p, slot);
+            CHECK(slot < nbus ? b0 + slot == q : E.hbus[h0 + slot - nbus] == q, "terminal %d slot bus", p);
+        }
+    }
+    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true, E.max_nbus + E.max_nh);
     CHECK(plan.total <= kMaxSmem, "a window needs %u bytes of shared memory", plan.total);
-    CHECK(plan.yd % 16 == 0 && plan.kg % 16 == 0 && plan.jst % 16 == 0 && plan.pq % 16 == 0,
+    CHECK(plan.yd % 16 == 0 && plan.kg % 16 == 0 && plan.jst % 16 == 0 && plan.pq % 16 == 0 && plan.ph % 16 == 0,
           "shared-memory plan alignment");
     return PF_OK;
 }

@@ -67,15 +67,17 @@ __device__ __forceinline__ void store_range_ll(double *x, const double *s, long 
     if ((b1 - ge) & 1) x[b1 - 1] = s[b1 - 1 - b0 + par];
 }
 
-// phase 1: phasors of every (scenario, window) item of this CTA
+// phase 1: phasors of every scenario, in chunks of blockDim.x consecutive
+// buses so that every lane has a bus
 __device__ __forceinline__ void batch_phasors(const BatchArgs &a, const double2 *tab, bool needU)
 {
     const int tid = threadIdx.x, TB = blockDim.x;
-    const long long nitem = (long long)a.S * a.nwin;
+    const int nchunk = (a.nb + TB - 1) / TB;
+    const long long nitem = (long long)a.S * nchunk;
     for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
-        const int s = (int)(it / a.nwin), w = (int)(it % a.nwin);
-        const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1];
-        for (int o = b0 + tid; o < b1; o += TB) {
+        const int s = (int)(it / nchunk), c = (int)(it % nchunk);
+        const int o = c * TB + tid;
+        if (o < a.nb) {
             const long long x = (long long)s * a.nb + o;
             double sn, cs;
             fast_sincos(a.va[x], tab, &sn, &cs);
@@ -451,11 +453,11 @@ static BatchArgs batch_args(Batch *b)
     a.nb = g->nb;
     a.nl = g->nl;
     a.nnz = g->nnz;
-    a.nwin = g->ew.nwin;
-    a.max_nbus = g->ew.max_nbus;
-    a.max_nt = g->ew.max_nt;
-    a.max_L = g->ew.max_L;
-    a.win_bus = g->ew.win_bus;
+    a.nwin = b->nwin;
+    a.max_nbus = b->max_nbus;
+    a.max_nt = b->max_nt;
+    a.max_L = b->max_L;
+    a.win_bus = b->win_bus;
     a.tp = g->tp;
     a.rp = g->rp;
     a.kd = g->kd;
@@ -488,8 +490,8 @@ static cudaError_t coop_launch(K kernel, int &resident, Batch *b, size_t smem, l
                                const BatchArgs &a)
 {
     cudaError_t e;
-    const int tb = b->g->ew.tb;
-    if (resident == 0 || b->tb != tb) {
+    const int tb = b->tb;
+    if (resident == 0) {
         if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                           (int)smem)))
             return e;
@@ -498,7 +500,6 @@ static cudaError_t coop_launch(K kernel, int &resident, Batch *b, size_t smem, l
         if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
             return e;
         resident = per_sm * nsm;
-        b->tb = tb;
         if (resident <= 0) return cudaErrorInvalidConfiguration;
     }
     cudaLaunchConfig_t cfg = {};
@@ -517,8 +518,7 @@ static cudaError_t coop_launch(K kernel, int &resident, Batch *b, size_t smem, l
 cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,
                               double *J, cudaStream_t s)
 {
-    Grid *g = b->g;
-    if (g->ew.nwin == 0 || b->S == 0) return cudaSuccess;
+    if (b->nwin == 0 || b->S == 0) return cudaSuccess;
     BatchArgs a = batch_args(b);
     a.vm = vm;
     a.va = va;
@@ -528,7 +528,7 @@ cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double
     a.aligned = (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, jac ? a.max_L : 0, jac);
     const size_t smem = sp.total + kTrigN * sizeof(double2);
-    const long long items = (long long)b->S * g->ew.nwin;
+    const long long items = (long long)b->S * b->nwin;
     if (jac) return coop_launch(k_ewb<true>, b->resident[1], b, smem, items, s, a);
     return coop_launch(k_ewb<false>, b->resident[0], b, smem, items, s, a);
 }
@@ -538,7 +538,7 @@ cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const d
                            double *gb, double *gbsh, double *gtap, cudaStream_t s)
 {
     Grid *g = b->g;
-    if (g->ew.nwin == 0 || b->S == 0) return cudaSuccess;
+    if (b->nwin == 0 || b->S == 0) return cudaSuccess;
     BatchArgs a = batch_args(b);
     a.vm = vm;
     a.va = va;
@@ -556,7 +556,7 @@ cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const d
     a.aligned = al16(gvm) && al16(gva);
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false);
     const size_t smem = sp.total + kTrigN * sizeof(double2);
-    const long long items = std::max<long long>((long long)b->S * g->ew.nwin, (g->nl + 255) / 256);
+    const long long items = std::max<long long>((long long)b->S * b->nwin, (g->nl + 255) / 256);
     return coop_launch(k_adj, b->resident[2], b, smem, items, s, a);
 }
 

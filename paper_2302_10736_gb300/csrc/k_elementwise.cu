@@ -1,18 +1,22 @@
-// k_elementwise.cu - element-wise method (Sec. II-B, IV-C) on the GPU, one
-// cooperative kernel per evaluation.
+// k_elementwise.cu - element-wise method (Sec. II-B, IV-C) on the GPU: one
+// CTA per window of consecutive buses, one launch per evaluation and no
+// synchronisation between CTAs.
 //
-// The element-wise method has no separate phasor step (the paper evaluates
-// the angle-difference terms inside the per-line loop); here each CTA first
-// forms the phasors of its own buses (phase 1), a grid-wide barrier makes
-// them visible, and the evaluation and reduction run in phase 2.
+// Phasors.  The paper's element-wise loop evaluates the angle-difference terms
+// inside its per-line loop; here each CTA first forms the phasors
+// U = e^{j theta}, V = v U of every bus its terminals touch - its own buses
+// and its ghost buses (the other ends outside the window, listed at setup) -
+// into a window-local table in shared memory.  A bus is transformed once per
+// window that touches it (about 1.6-1.8 times per bus on grids numbered with
+// spatial locality) instead of once per terminal, and no CTA waits for
+// another: the kernel is a plain launch of one CTA per window.
 //
-// Evaluation step (Listing 1's per-element loop, one terminal per thread).
-// Terminal t of a branch (owner bus o, other bus q) has precomputed constants
-// Ys_t, Yc_t (k_setup.cu) such that its complex power (Eqs. 5-6) is
+// Evaluation step (the per-element loop of Sec. IV-C, one terminal per
+// thread).  Terminal t of a branch (owner bus o, other bus q) has precomputed
+// constants Ys_t, Yc_t (k_setup.cu) such that its complex power (Eqs. 5-6) is
 //     S_t = v_o^2 conj(Ys_t) + K_t,   K_t = conj(Yc_t) V_o conj(V_q),
 // where V_o conj(V_q) = v_o v_q e^{j(theta_o - theta_q)} carries the sine and
-// cosine of the angle difference in registers (from per-bus phasors: no
-// per-branch trigonometry).  Its 8 partials (16 per branch):
+// cosine of the angle difference.  Its 8 partials (16 per branch):
 //     dS_t/dtheta_q = -j K_t            dS_t/dv_q = K_t / v_q = conj(Yc_t) V_o conj(U_q)
 //     dS_t/dtheta_o = +j K_t            dS_t/dv_o = 2 v_o conj(Ys_t) + K_t / v_o
 // The thread computes E = V_o conj(U_q), G = conj(Yc_t) E (= dS_t/dv_q) and
@@ -30,32 +34,25 @@
 // with Yd_o = sum_t Ys_t + y_sh,o, a parameter-only per-bus constant formed at
 // setup from the same terminal constants.
 //
-// GB300 data movement.  The static data of a CTA's first window is loaded
-// before the grid barrier, so it overlaps the other CTAs' phase 1.  A window's
-// Jacobian rows are one contiguous slice of each of the P and Q halves of J
-// (canonical layout): it is assembled in shared memory and written back with
-// TMA bulk stores, together with P and Q.
+// GB300 data movement.  Every global load of a window (its voltages, the
+// ghost voltages, the terminal constants of the first pass, the bus metadata)
+// is issued before any arithmetic.  A window's Jacobian rows are one
+// contiguous slice of each of the P and Q halves of J (canonical layout): it
+// is assembled in shared memory and written back with TMA bulk stores,
+// together with P and Q.
 #include "fastmath.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
 
 namespace pf {
 
-constexpr uint64_t kBarrierLimitNs = 1000000000ull;   // bounded grid-barrier wait (1 s), then PF_ETIMEOUT
-
 struct EwArgs {
-    int nwin, nnz, max_nbus, max_nt, max_L, aligned;
-    const int *win_bus, *tp, *rp, *kd;
-    const double2 *yd, *tcoup;
-    const int2 *tnbr;
-    const int *town;
+    int nnz, max_nbus, max_nt, max_L, max_nph, aligned;
+    const int *win_bus, *hptr, *hbus, *tp, *rp, *kd, *town;
+    const double2 *yd, *tcoup, *trig;
+    const int2 *tloc;
     const double *vm, *va;
-    const double2 *trig;
-    double4_32a *U;
-    double2 *V;
     double *P, *Q, *J;
-    unsigned int *bar;
-    int *err;
 };
 
 // Write x[b0 .. b1) from shared staging `s` (element b0 at s[b0 & 1]) to
@@ -71,202 +68,180 @@ __device__ __forceinline__ void store_range(double *x, const double *s, int b0, 
     if ((b1 - ge) & 1) x[b1 - 1] = s[b1 - 1 - b0 + par];
 }
 
-// At most 48 registers (5 CTAs of 256 or 10 of 128 threads per SM): every
-// window of the 70k-bus grid gets its own co-resident CTA.
+// At most 48 registers: 5 CTAs of 256 or 10 of 128 threads per SM.
 template <bool JAC>
 __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
 {
     extern __shared__ __align__(16) char smem[];
-    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, JAC ? a.max_L : 0, JAC);
+    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, JAC ? a.max_L : 0, JAC, a.max_nph);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
     double2 *skg = reinterpret_cast<double2 *>(smem + sp.kg);
     int *skp = reinterpret_cast<int *>(smem + sp.kp);
     double *jst = reinterpret_cast<double *>(smem + sp.jst);
     double *spq = reinterpret_cast<double *>(smem + sp.pq);
+    double2 *sV = reinterpret_cast<double2 *>(smem + sp.ph);                 // v e^{j theta}
+    double2 *sU = sV + a.max_nph;                                            // (cos, sin)
+    double2 *sW = sU + a.max_nph;                                            // (v, 1/v)
     double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
-    const int tid = threadIdx.x, TB = blockDim.x;
+    const int tid = threadIdx.x, TB = blockDim.x, w = blockIdx.x;
+    const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
+    const int t0 = a.tp[b0], nt = a.tp[b1] - t0;
+    const int h0 = a.hptr[w], nph = nbus + a.hptr[w + 1] - h0;
+    const int r0 = a.rp[b0], L = JAC ? 2 * (a.rp[b1] - r0) : 0;
 
-    // ---- phase 1: phasors of this CTA's buses (Sec. IV-B.1 step 1) ----
-    // All loads of the first window (its vm, va, and the static data phase 2
-    // needs) are issued together, before any arithmetic.
-    const int w0 = blockIdx.x;
+    // ---- loads: voltages of the first table slot, bus metadata, the first
+    // terminal, the sine/cosine table ----
+    double th = 0.0, v = 0.0;
+    if (tid < nph) {
+        const int o = tid < nbus ? b0 + tid : a.hbus[h0 + tid - nbus];
+        th = a.va[o];
+        v = a.vm[o];
+    }
+    const double vb = v;   // the bus thread's own magnitude (slot tid < nbus)
+    for (int b = tid; b < nbus; b += TB) {
+        const int o = b0 + b, rs = a.rp[o];
+        sbm[b] = make_int4(2 * (rs - r0), a.rp[o + 1] - rs, a.kd[o], a.tp[o] - t0);
+        syd[b] = a.yd[o];
+    }
     double2 yc = make_double2(0.0, 0.0);
     int2 nq = make_int2(0, 0);
     int ol = 0;
-    {
-        const int b0 = a.win_bus[w0], b1 = a.win_bus[w0 + 1], t0 = a.tp[b0], nt = a.tp[b1] - t0;
-        const int r0 = a.rp[b0];
-        double th = 0.0, v = 0.0;
-        int4 bm = make_int4(0, 0, 0, 0);
-        double2 y = make_double2(0.0, 0.0);
-        const bool mine = tid < b1 - b0;
-        if (mine) {
-            const int o = b0 + tid, rs = a.rp[o];
+    if (tid < nt) {
+        yc = a.tcoup[t0 + tid];
+        nq = a.tloc[t0 + tid];
+        ol = a.town[t0 + tid] - b0;
+    }
+    for (int k = tid; k < kTrigN; k += TB) tab[k] = a.trig[k];
+    __syncthreads();
+
+    // ---- phasor table of the window (Sec. IV-B.1 step 1, own and ghost buses) ----
+    for (int j = tid; j < nph; j += TB) {
+        if (j != tid) {
+            const int o = j < nbus ? b0 + j : a.hbus[h0 + j - nbus];
             th = a.va[o];
             v = a.vm[o];
-            bm = make_int4(2 * (rs - r0), a.rp[o + 1] - rs, a.kd[o], a.tp[o] - t0);
-            y = a.yd[o];
         }
-        if (tid < nt) {
-            yc = a.tcoup[t0 + tid];
-            nq = a.tnbr[t0 + tid];
-            ol = a.town[t0 + tid] - b0;
-        }
-        for (int k = tid; k < kTrigN; k += TB) tab[k] = a.trig[k];
-        __syncthreads();
-        if (mine) {
-            double s, c;
-            fast_sincos(th, tab, &s, &c);
-            if (JAC) a.U[b0 + tid] = make_double4_32a(c, s, v, fast_rcp(v));
-            a.V[b0 + tid] = make_double2(v * c, v * s);
-            sbm[tid] = bm;
-            syd[tid] = y;
+        double s, c;
+        fast_sincos(th, tab, &s, &c);
+        sV[j] = make_double2(v * c, v * s);
+        if (JAC) {
+            sU[j] = make_double2(c, s);
+            sW[j] = make_double2(v, j < nbus ? fast_rcp(v) : 0.0);
         }
     }
-    for (int w = w0 + gridDim.x; w < a.nwin; w += gridDim.x) {   // further windows (large grids)
-        const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1];
-        for (int o = b0 + tid; o < b1; o += TB) {
-            double s, c;
-            fast_sincos(a.va[o], tab, &s, &c);
-            const double v = a.vm[o];
-            if (JAC) a.U[o] = make_double4_32a(c, s, v, fast_rcp(v));
-            a.V[o] = make_double2(v * c, v * s);
-        }
-    }
-    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBarrierLimitNs)) return;
+    __syncthreads();
 
-    // ---- phase 2: evaluation and reduction, window by window ----
-    for (int w = w0; w < a.nwin; w += gridDim.x) {
-        const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
-        const int t0 = a.tp[b0], nt = a.tp[b1] - t0;
-        const int r0 = a.rp[b0], L = JAC ? 2 * (a.rp[b1] - r0) : 0;
-        const bool first = w == w0;
-        if (!first) {   // previous window's stores have read shared memory (thread 0 waited)
-            __syncthreads();
-            for (int b = tid; b < nbus; b += TB) {
-                const int o = b0 + b, rs = a.rp[o];
-                sbm[b] = make_int4(2 * (rs - r0), a.rp[o + 1] - rs, a.kd[o], a.tp[o] - t0);
-                syd[b] = a.yd[o];
-            }
-            __syncthreads();
+    // ---- evaluation: one terminal per thread ----
+    for (int i = tid; i < nt; i += TB) {
+        if (i != tid) {
+            yc = a.tcoup[t0 + i];
+            nq = a.tloc[t0 + i];
+            ol = a.town[t0 + i] - b0;
         }
-        // the bus thread's own phasor, fetched together with the gathers
-        double4_32a ub = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-        double vb = 0.0;
-        if (tid < nbus) {
-            if (JAC)
-                ub = a.U[b0 + tid];
-            else
-                vb = a.vm[b0 + tid];
-        }
-        for (int i = tid; i < nt; i += TB) {
-            if (!(first && i == tid)) {
-                yc = a.tcoup[t0 + i];
-                nq = a.tnbr[t0 + i];
-                ol = a.town[t0 + i] - b0;
-            }
-            const double2 Vo = a.V[b0 + ol];
-            if (JAC) {
-                const double4_32a uq = a.U[nq.x];
-                const double Er = fma(Vo.x, uq.x, Vo.y * uq.y);   // V_o conj(U_q)
-                const double Ei = fma(Vo.y, uq.x, -Vo.x * uq.y);
-                const double Gr = fma(yc.x, Er, yc.y * Ei);       // conj(Yc) E = dS_t/dv_q
-                const double Gi = fma(yc.x, Ei, -yc.y * Er);
-                const double Kr = uq.z * Gr, Ki = uq.z * Gi;       // K_t = v_q G
-                skg[2 * i] = make_double2(Kr, Ki);
-                skg[2 * i + 1] = make_double2(Gr, Gi);
-                skp[i] = nq.y;
-                if (!(nq.y & EW_ACCUM)) {
-                    const int4 bm = sbm[ol];
-                    const int pos = bm.x + (nq.y & EW_KMASK), d = bm.y;
-                    jst[pos] = Ki;           // J11 = Re(-j K)
-                    jst[pos + d] = Gr;       // J12
-                    jst[L + pos] = -Kr;      // J21 = Im(-j K)
-                    jst[L + pos + d] = Gi;   // J22
-                }
-            } else {
-                const double2 Vq = a.V[nq.x];
-                const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y);   // V_o conj(V_q)
-                const double Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
-                skg[i] = make_double2(fma(yc.x, Wr, yc.y * Wi), fma(yc.x, Wi, -yc.y * Wr));   // K_t
-            }
-        }
-        __syncthreads();
-
-        const int pqs = (int)sp.pqs, par = b0 & 1;
-        for (int b = tid; b < nbus; b += TB) {
-            const int4 bm = sbm[b];
-            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
-            const double2 y = syd[b];
-            double sKr = 0.0, sKi = 0.0;
-            if (JAC) {
-                const int d = bm.y;
-                for (int i = bm.w; i < tend; ++i) {
-                    const double2 K = skg[2 * i];
-                    sKr += K.x;
-                    sKi += K.y;
-                    const int kp = skp[i];
-                    if (kp & EW_ACCUM) {   // later branch of a parallel run: add into the run's slot
-                        const double2 G = skg[2 * i + 1];
-                        const int pos = bm.x + (kp & EW_KMASK);
-                        jst[pos] += K.y;
-                        jst[pos + d] += G.x;
-                        jst[L + pos] -= K.x;
-                        jst[L + pos + d] += G.y;
-                    }
-                }
-                const double4_32a uo = b == tid ? ub : a.U[b0 + b];
-                const double v = uo.z, iv = uo.w, v2 = v * v, tv = v + v;
-                const int pos = bm.x + bm.z;
-                jst[pos] = -sKi;                         // Re(j sum K)
-                jst[pos + d] = fma(tv, y.x, sKr * iv);
-                jst[L + pos] = sKr;                      // Im(j sum K)
-                jst[L + pos + d] = fma(-tv, y.y, sKi * iv);
-                spq[b + par] = fma(v2, y.x, sKr);
-                spq[pqs + b + par] = fma(-v2, y.y, sKi);
-            } else {
-                for (int i = bm.w; i < tend; ++i) {
-                    sKr += skg[i].x;
-                    sKi += skg[i].y;
-                }
-                const double v = b == tid ? vb : a.vm[b0 + b], v2 = v * v;
-                spq[b + par] = fma(v2, y.x, sKr);
-                spq[pqs + b + par] = fma(-v2, y.y, sKi);
-            }
-        }
-
-        if (a.aligned) {
-            fence_proxy_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-                if (JAC) {
-                    bulk_s2g(a.J + 2 * (long long)r0, jst, 8u * (uint32_t)L);
-                    bulk_s2g(a.J + 2 * (long long)a.nnz + 2 * (long long)r0, jst + L, 8u * (uint32_t)L);
-                }
-                if (a.P) {
-                    store_range(a.P, spq, b0, b1);
-                    store_range(a.Q, spq + pqs, b0, b1);
-                }
-                bulk_commit();
-                bulk_wait_read();
+        const double2 Vo = sV[ol];
+        if (JAC) {
+            const double2 uq = sU[nq.x];
+            const double vq = sW[nq.x].x;
+            const double Er = fma(Vo.x, uq.x, Vo.y * uq.y);   // V_o conj(U_q)
+            const double Ei = fma(Vo.y, uq.x, -Vo.x * uq.y);
+            const double Gr = fma(yc.x, Er, yc.y * Ei);       // conj(Yc) E = dS_t/dv_q
+            const double Gi = fma(yc.x, Ei, -yc.y * Er);
+            const double Kr = vq * Gr, Ki = vq * Gi;           // K_t = v_q G
+            skg[2 * i] = make_double2(Kr, Ki);
+            skg[2 * i + 1] = make_double2(Gr, Gi);
+            skp[i] = nq.y;
+            if (!(nq.y & EW_ACCUM)) {
+                const int4 bm = sbm[ol];
+                const int pos = bm.x + (nq.y & EW_KMASK), d = bm.y;
+                jst[pos] = Ki;           // J11 = Re(-j K)
+                jst[pos + d] = Gr;       // J12
+                jst[L + pos] = -Kr;      // J21 = Im(-j K)
+                jst[L + pos + d] = Gi;   // J22
             }
         } else {
-            __syncthreads();
-            if (JAC) {
-                double *Jp = a.J + 2 * (long long)r0;
-                double *Jq = a.J + 2 * (long long)a.nnz + 2 * (long long)r0;
-                for (int x = tid; x < L; x += TB) {
-                    Jp[x] = jst[x];
-                    Jq[x] = jst[L + x];
+            const double2 Vq = sV[nq.x];
+            const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y);   // V_o conj(V_q)
+            const double Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
+            skg[i] = make_double2(fma(yc.x, Wr, yc.y * Wi), fma(yc.x, Wi, -yc.y * Wr));   // K_t
+        }
+    }
+    __syncthreads();
+
+    // ---- reduction: one thread per bus, its terminals in sorted order ----
+    const int pqs = (int)sp.pqs, par = b0 & 1;
+    for (int b = tid; b < nbus; b += TB) {
+        const int4 bm = sbm[b];
+        const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+        const double2 y = syd[b];
+        double sKr = 0.0, sKi = 0.0;
+        if (JAC) {
+            const int d = bm.y;
+            for (int i = bm.w; i < tend; ++i) {
+                const double2 K = skg[2 * i];
+                sKr += K.x;
+                sKi += K.y;
+                const int kp = skp[i];
+                if (kp & EW_ACCUM) {   // later branch of a parallel run: add into the run's slot
+                    const double2 G = skg[2 * i + 1];
+                    const int pos = bm.x + (kp & EW_KMASK);
+                    jst[pos] += K.y;
+                    jst[pos + d] += G.x;
+                    jst[L + pos] -= K.x;
+                    jst[L + pos + d] += G.y;
                 }
             }
-            if (a.P)
-                for (int b = tid; b < nbus; b += TB) {
-                    a.P[b0 + b] = spq[b + par];
-                    a.Q[b0 + b] = spq[pqs + b + par];
-                }
+            const double2 vw = sW[b];
+            const double vo = vw.x, iv = vw.y, v2 = vo * vo, tv = vo + vo;
+            const int pos = bm.x + bm.z;
+            jst[pos] = -sKi;                         // Re(j sum K)
+            jst[pos + d] = fma(tv, y.x, sKr * iv);
+            jst[L + pos] = sKr;                      // Im(j sum K)
+            jst[L + pos + d] = fma(-tv, y.y, sKi * iv);
+            spq[b + par] = fma(v2, y.x, sKr);
+            spq[pqs + b + par] = fma(-v2, y.y, sKi);
+        } else {
+            for (int i = bm.w; i < tend; ++i) {
+                sKr += skg[i].x;
+                sKi += skg[i].y;
+            }
+            const double vo = b == tid ? vb : a.vm[b0 + b], v2 = vo * vo;
+            spq[b + par] = fma(v2, y.x, sKr);
+            spq[pqs + b + par] = fma(-v2, y.y, sKi);
         }
+    }
+
+    // ---- stores ----
+    if (a.aligned) {
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            if (JAC) {
+                bulk_s2g(a.J + 2 * (long long)r0, jst, 8u * (uint32_t)L);
+                bulk_s2g(a.J + 2 * (long long)a.nnz + 2 * (long long)r0, jst + L, 8u * (uint32_t)L);
+            }
+            if (a.P) {
+                store_range(a.P, spq, b0, b1);
+                store_range(a.Q, spq + pqs, b0, b1);
+            }
+            bulk_commit();
+            bulk_wait_read();   // shared memory stays allocated until the copies have read it
+        }
+    } else {
+        __syncthreads();
+        if (JAC) {
+            double *Jp = a.J + 2 * (long long)r0;
+            double *Jq = a.J + 2 * (long long)a.nnz + 2 * (long long)r0;
+            for (int x = tid; x < L; x += TB) {
+                Jp[x] = jst[x];
+                Jq[x] = jst[L + x];
+            }
+        }
+        if (a.P)
+            for (int b = tid; b < nbus; b += TB) {
+                a.P[b0 + b] = spq[b + par];
+                a.Q[b0 + b] = spq[pqs + b + par];
+            }
     }
 }
 
@@ -278,57 +253,40 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
 {
     const EwDev &L = g->ew;
     if (L.nwin == 0) return cudaSuccess;
-    const EwSmem sp = ew_smem_plan(L.max_nbus, L.max_nt, JAC ? L.max_L : 0, JAC);
-    const size_t smem = sp.total + kTrigN * sizeof(double2);
-    cudaError_t e;
-    int &resident = JAC ? g->ew_resident_jac : g->ew_resident_inj;
-    if (resident == 0) {   // CTAs that fit at once (cooperative launch bound), cached per layout
-        if (smem > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_ew<JAC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-            return e;
-        int per_sm = 0, dev = 0, nsm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ew<JAC>, L.tb, smem))) return e;
-        if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
-            return e;
-        resident = per_sm * nsm;
-        if (resident <= 0) return cudaErrorInvalidConfiguration;
+    const int max_nph = L.max_nbus + L.max_nh;
+    const EwSmem sp = ew_smem_plan(L.max_nbus, L.max_nt, JAC ? L.max_L : 0, JAC, max_nph);
+    const uint32_t smem = sp.total + kTrigN * (uint32_t)sizeof(double2);
+    uint32_t &conf = JAC ? g->ew_smem_jac : g->ew_smem_inj;
+    if (smem > 48u * 1024u && smem > conf) {
+        cudaError_t e = cudaFuncSetAttribute(k_ew<JAC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        conf = smem;
     }
     EwArgs a;
-    a.nwin = L.nwin;
     a.nnz = g->nnz;
     a.max_nbus = L.max_nbus;
     a.max_nt = L.max_nt;
     a.max_L = L.max_L;
+    a.max_nph = max_nph;
     a.aligned = (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
     a.win_bus = L.win_bus;
+    a.hptr = L.hptr;
+    a.hbus = L.hbus;
     a.tp = g->tp;
     a.rp = g->rp;
     a.kd = g->kd;
+    a.town = g->town;
     a.yd = g->bus_yd;
     a.tcoup = g->tcoup;
-    a.tnbr = g->tnbr;
-    a.town = g->town;
+    a.trig = trig_table();
+    a.tloc = L.tloc;
     a.vm = vm;
     a.va = va;
-    a.trig = trig_table();
-    a.U = g->ph_u;
-    a.V = g->ph_v;
     a.P = P;
     a.Q = Q;
     a.J = J;
-    a.bar = g->bar;
-    a.err = g->err;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)std::min(L.nwin, resident));
-    cfg.blockDim = dim3((unsigned)L.tb);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_ew<JAC>, a);
+    k_ew<JAC><<<(unsigned)L.nwin, (unsigned)L.tb, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,

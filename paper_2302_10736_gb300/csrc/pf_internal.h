@@ -74,14 +74,23 @@ struct HostTopo {
 // more terminals gets a window of its own and its terminals are looped over).
 struct HostEw {
     int tb = 0, nwin = 0;
+    int tfac = 1;       // at most tfac * tb terminals per window (threads loop over them)
     int max_L = 0;      // max over windows of 2 * (Ybus nnz of the window's rows)
     int max_nt = 0;     // max terminals in a window
     int max_nbus = 0;   // max buses in a window
+    int max_nh = 0;     // max ghost buses of a window
     std::vector<int> win_bus;   // [nwin+1]
+    // Ghost buses: the buses outside a window that its terminals reach,
+    // sorted, window w's at hbus[hptr[w] .. hptr[w+1]).  A window's phasor
+    // table holds its own buses (slots 0 .. nbus-1) then its ghost buses.
+    std::vector<int> hptr, hbus;
+    // per sorted terminal: {phasor-table slot of the other bus, Ybus slot
+    // position | EW_ACCUM} (tnbr with the bus replaced by its window slot)
+    std::vector<int2> tloc;
 };
 
 pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo &H);
-pf_status host_ew(const HostTopo &H, int tb, HostEw &E);
+pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac = 1);
 pf_status host_selfcheck(const HostTopo &H, const HostEw &E);
 
 // Shared-memory plan of the element-wise kernels (byte offsets, 16-aligned):
@@ -92,9 +101,11 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E);
 //   jst double  [2 max_L]    the window's J slice (P half, then Q half)
 //   pq  double  [2 pqs]      P then Q of the window, parity-aligned with global memory
 struct EwSmem {
-    uint32_t bm, yd, kg, kp, jst, pq, pqs, total;
+    uint32_t bm, yd, kg, kp, jst, pq, pqs, ph, total;
 };
-__host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max_L, bool jac)
+// max_nph > 0 adds a phasor table of that many slots: V = v e^{j theta}, and
+// with the Jacobian also (cos, sin) and (v, 1/v), each a double2 array
+__host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max_L, bool jac, int max_nph = 0)
 {
     EwSmem p;
     p.pqs = ((uint32_t)max_nbus + 3u) & ~1u;   // even, >= max_nbus + 2
@@ -104,15 +115,18 @@ __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max
     p.kp = p.kg + (jac ? 32u : 16u) * (uint32_t)max_nt;
     p.jst = p.kp + (jac ? ((4u * (uint32_t)max_nt + 15u) & ~15u) : 0u);
     p.pq = p.jst + (jac ? 16u * (uint32_t)max_L : 0u);
-    p.total = p.pq + 16u * p.pqs;
+    p.ph = p.pq + 16u * p.pqs;
+    p.total = p.ph + (jac ? 48u : 16u) * (uint32_t)max_nph;
     return p;
 }
 constexpr uint32_t kMaxSmem = 227u * 1024u;
 
 // ------------------------------------------------ device-side structure --
 struct EwDev {
-    int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0;
+    int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0, max_nh = 0;
     int *win_bus = nullptr;   // [nwin+1]
+    int *hptr = nullptr, *hbus = nullptr;   // ghost buses per window
+    int2 *tloc = nullptr;     // [T] {phasor slot of the other bus, slot position | flags}
 };
 
 struct Grid {
@@ -136,7 +150,7 @@ struct Grid {
     double2 *bus_ysh = nullptr;            // [nb]
     double2 *bus_yd = nullptr;             // [nb] bus shunt + sum of the bus's terminal self constants
     EwDev ew;
-    int ew_resident_jac = 0, ew_resident_inj = 0;   // co-resident CTAs of the fused kernels (0 = unknown)
+    uint32_t ew_smem_jac = 0, ew_smem_inj = 0;   // dynamic shared memory the kernels are configured for
     int *tmir = nullptr;                   // [2nl] by sorted position: sorted position of the mirror terminal
     // device copies of the current parameters (branch gradients need them)
     double *p_g = nullptr, *p_b = nullptr, *p_bsh = nullptr, *p_tap = nullptr, *p_shift = nullptr;
@@ -232,11 +246,16 @@ struct Batch {
     double2 *r = nullptr;            // [S][nb] loss residual (2 wP dP, 2 wQ dQ)
     double *lpart = nullptr;         // [S][nwin] per-window loss partial sums
     int resident[3] = {0, 0, 0};     // co-resident CTAs of the batched kernels (inj, jac, adjoint)
-    int tb = 0;                      // element-wise window size the residency was computed for
+    // the batch's own element-wise windows: throughput-bound, so every thread
+    // owns a bus in the reduction and loops over up to tfac terminals
+    int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0;
+    int *win_bus = nullptr;          // [nwin+1]
 };
 
 cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,
                               double *J, cudaStream_t s);
+cudaError_t launch_ybus_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,
+                                double *J, cudaStream_t s);
 cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
                            const double *wP, const double *wQ, double *L, double *gvm, double *gva, double *gg,
                            double *gb, double *gbsh, double *gtap, cudaStream_t s);

@@ -365,6 +365,8 @@ def _bind_batches():
         "batch_jac_pattern": (st, [vp, i32, vp, vp, ctypes.POINTER(i32)]),
         "inj_elementwise_batched": (st, [vp, vp, vp, vp, vp, vp]),
         "jac_elementwise_batched": (st, [vp, vp, vp, vp, vp, vp, vp]),
+        "inj_ybus_batched": (st, [vp, vp, vp, vp, vp, vp]),
+        "jac_ybus_batched": (st, [vp, vp, vp, vp, vp, vp, vp]),
         "adjoint_elementwise": (st, [vp] + [vp] * 14),
     }
     for name, (res, args) in sig.items():
@@ -437,6 +439,19 @@ def jac_elementwise_batched(batch, vm, va, P, Q, J, stream=None):
     _check(_lib.jac_elementwise_batched(batch.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(P, "P", n),
                                         _dptr(Q, "Q", n), _dptr(J, "J", batch.nnzJ_total), _stream(stream)),
            "jac_elementwise_batched")
+
+
+def inj_ybus_batched(batch, vm, va, P, Q, stream=None):
+    n = batch.nscen * batch.grid.nb
+    _check(_lib.inj_ybus_batched(batch.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(P, "P", n),
+                                 _dptr(Q, "Q", n), _stream(stream)), "inj_ybus_batched")
+
+
+def jac_ybus_batched(batch, vm, va, P, Q, J, stream=None):
+    n = batch.nscen * batch.grid.nb
+    _check(_lib.jac_ybus_batched(batch.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), _dptr(P, "P", n),
+                                 _dptr(Q, "Q", n), _dptr(J, "J", batch.nnzJ_total), _stream(stream)),
+           "jac_ybus_batched")
 
 
 def adjoint_elementwise(batch, vm, va, Pspec, Qspec, wP, wQ, L, gvm, gva, gg=None, gb=None, gbsh=None, gtap=None,

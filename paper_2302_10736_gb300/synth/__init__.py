@@ -113,6 +113,31 @@ def randint(seed, stream, count, n):
     return out[:count]
 
 
+def renumber_buses(gr, seed, stream=7):
+    """The same grid (and voltage states) with its buses renumbered by a
+    seeded random permutation: old bus i becomes bus perm[i].  Destroys the
+    spatial locality of the numbering (a sensitivity case)."""
+    nb = gr["nb"]
+    keys = randint(seed, stream, nb, 2**31 - 1)
+    perm = np.empty(nb, np.int64)
+    perm[np.argsort(keys, kind="stable")] = np.arange(nb)
+    out = dict(gr)
+    out["f"] = perm[gr["f"]].astype(np.int32)
+    out["t"] = perm[gr["t"]].astype(np.int32)
+    for key in ("gs", "bs", "bustype", "x", "y", "vm2", "va2", "wP", "wQ"):
+        if key in gr:
+            v = np.empty_like(gr[key])
+            v[perm] = gr[key]
+            out[key] = v
+    for key in ("vm", "va"):
+        if key in gr:
+            v = np.empty_like(gr[key])
+            v[:, perm] = gr[key]
+            out[key] = v
+    out["perm"] = perm
+    return out
+
+
 def workload(k, nscen=None):
     """Full seeded input set of workload k (see the module docstring).
 

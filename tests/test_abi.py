@@ -94,3 +94,11 @@ def test_layout_selfcheck(pf, case, window):
 def test_selfcheck_rejects_bad_window(pf):
     with pytest.raises(pf.PfError):
         pf.grid_selfcheck(three_bus_plus(), 100)
+
+
+@pytest.mark.parametrize("window", [128, 256])
+def test_layout_selfcheck_random_numbering(window):
+    """The ghost-bus layout of a grid numbered without locality."""
+    from paper_2302_10736_gb300 import pfgrid, synth
+    w = synth.renumber_buses(synth.workload(1), 99)
+    pfgrid.grid_selfcheck(w, window)

@@ -59,10 +59,12 @@ def with_parallel(gr):
     return out
 
 
-def check_batch(pf, gr, vm, va, outage, scenarios=None, tol=TOL):
+def check_batch(pf, gr, vm, va, outage, scenarios=None, tol=TOL, cfg=None):
     import torch
     S, nb = vm.shape
     grid = pf.ybus_build(gr)
+    if cfg:
+        pf.grid_set_config(grid, **cfg)
     batch = pf.batch_create(grid, S, outage)
     joff = pf.batch_jac_offsets(batch).cpu().numpy()
     assert joff[0] == 0 and joff[-1] == batch.nnzJ_total
@@ -71,12 +73,18 @@ def check_batch(pf, gr, vm, va, outage, scenarios=None, tol=TOL):
     J = torch.full((batch.nnzJ_total,), np.nan, dtype=torch.float64, device="cuda")
     Pi = torch.full_like(P, np.nan)
     Qi = torch.full_like(P, np.nan)
+    Py, Qy, Jy = torch.full_like(P, np.nan), torch.full_like(P, np.nan), torch.full_like(J, np.nan)
+    Pyi, Qyi = torch.full_like(P, np.nan), torch.full_like(P, np.nan)
     pf.jac_elementwise_batched(batch, _d(vm), _d(va), P, Q, J)
     pf.inj_elementwise_batched(batch, _d(vm), _d(va), Pi, Qi)
+    pf.jac_ybus_batched(batch, _d(vm), _d(va), Py, Qy, Jy)
+    pf.inj_ybus_batched(batch, _d(vm), _d(va), Pyi, Qyi)
     torch.cuda.synchronize()
     pf.grid_check_error(grid)
-    P, Q, J = P.cpu().numpy().reshape(S, nb), Q.cpu().numpy().reshape(S, nb), J.cpu().numpy()
-    Pi, Qi = Pi.cpu().numpy().reshape(S, nb), Qi.cpu().numpy().reshape(S, nb)
+    host = lambda x: x.cpu().numpy().reshape(S, nb)
+    P, Q, J = host(P), host(Q), J.cpu().numpy()
+    Pi, Qi = host(Pi), host(Qi)
+    Py, Qy, Jy, Pyi, Qyi = host(Py), host(Qy), Jy.cpu().numpy(), host(Pyi), host(Qyi)
     for s in (range(S) if scenarios is None else scenarios):
         l = int(outage[s]) if outage is not None else -1
         skip = _skip(gr["nl"], l)
@@ -86,9 +94,11 @@ def check_batch(pf, gr, vm, va, outage, scenarios=None, tol=TOL):
         assert np.array_equal(rp_s, jrp) and np.array_equal(ci_s, jci), s
         assert joff[s + 1] - joff[s] == 4 * Y.nnz
         Pr, Qr, Jr = oracle.elementwise(gr, vm[s], va[s], Y, skip=skip)
-        Js = J[joff[s]:joff[s + 1]]
-        errs = [relerr(P[s], Pr), relerr(Q[s], Qr), relerr(Pi[s], Pr), relerr(Qi[s], Qr)]
+        Js, Jys = J[joff[s]:joff[s + 1]], Jy[joff[s]:joff[s + 1]]
+        errs = [relerr(x[s], r) for x, r in ((P, Pr), (Q, Qr), (Pi, Pr), (Qi, Qr), (Py, Pr), (Qy, Qr), (Pyi, Pr),
+                                              (Qyi, Qr))]
         errs += [relerr(a, b) for a, b in zip(blocks(Js, jci, nb, Y.nnz), blocks(Jr, jci, nb, Y.nnz))]
+        errs += [relerr(a, b) for a, b in zip(blocks(Jys, jci, nb, Y.nnz), blocks(Jr, jci, nb, Y.nnz))]
         assert max(errs) <= tol, (s, l, errs)
     return batch
 
@@ -102,6 +112,16 @@ def test_small_batch_with_outages_and_parallels(pf):
                        int(nonbridge[20])], np.int32)   # none, plain, both of a parallel pair, a bridge
     vm, va = synth.voltages(400, len(outage), 21, 0, 0.93, 1.07, 0.25)
     check_batch(pf, gr, vm, va, outage)
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+def test_ybus_batched_every_lane_count(pf, lanes):
+    from paper_2302_10736_gb300 import synth
+    gr = with_parallel(random_grid(300, 420, 23, shift_max=0.2))
+    nonbridge = np.flatnonzero(~synth.bridges(300, gr["f"], gr["t"]))
+    outage = np.array([int(nonbridge[5]), -1, 0, gr["nl"] - 1, int(nonbridge[40])], np.int32)
+    vm, va = synth.voltages(300, len(outage), 23, 0, 0.93, 1.07, 0.25)
+    check_batch(pf, gr, vm, va, outage, cfg=dict(ybus_lanes=lanes, ybus_block=128))
 
 
 def test_batch_without_outages_equals_single_evaluation(pf):
