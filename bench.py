@@ -37,6 +37,9 @@ EW_OPS_PER_TERMINAL = 12   # E = V_o conj(U_q) 4, G = conj(Yc) E 4, K = v_q G 2,
 EW_OPS_PER_BUS = 31        # fused phasor (sincos 15, 1/v 4, V 2) + diagonal entries and S (10)
 YB_OPS_PER_NNZ = 16
 YB_OPS_PER_ROW = 16
+# DRAM bytes of one k_ew<1> launch on the 70k-bus grid (dram__bytes_read.sum + dram__bytes_write.sum
+# of an ncu capture of that launch); None whenever the kernel changes, until it is captured again
+EW_TRAFFIC_BYTES = 8249856 + 0
 
 
 def parse_args(argv=None):
@@ -394,9 +397,11 @@ def main():
     ops_ew = EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb
     achieved = ops_ew / (ms_jew * 1e-3) / 1e9
     hbm, hbm_kind = hbm_peak()
-    bytes_ew = 40 * T + (32 + 36 + 16) * nb + 32 * grid.nnz
-    roof = {"bound": "alu", "kernel": "k_jac_ew", "achieved": achieved, "peak": FP64_OPS_PEAK_G,
-            "unit": "GFP64op/s", "frac": achieved / FP64_OPS_PEAK_G, "traffic": None,
+    # algorithmic bytes of an element-wise injection + Jacobian evaluation: branch ends and 5 parameters
+    # per branch (48 B), vm, va, shunt and P, Q per bus (48 B), one value per Jacobian slot (32 B per nnzY)
+    bytes_ew = 48 * nl + 48 * nb + 32 * grid.nnz
+    roof = {"bound": "alu", "kernel": "k_ew<1>", "achieved": achieved, "peak": FP64_OPS_PEAK_G,
+            "unit": "GFP64op/s", "frac": achieved / FP64_OPS_PEAK_G, "traffic": EW_TRAFFIC_BYTES,
             "ops_per_launch": ops_ew, "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz",
             "hbm": {"achieved": bytes_ew / (ms_jew * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                     "frac": bytes_ew / (ms_jew * 1e-3) / 1e9 / hbm, "algorithmic_bytes": bytes_ew,
