@@ -232,13 +232,16 @@ pf_status grid_check_error(pf_grid *grid, pf_stream stream);
 /*
  * Host-only self-check (no GPU needed, nothing allocated on the device):
  * validates `desc` like ybus_build, builds the index structures of the grid
- * and the element-wise windows for CTAs of `window` threads, and verifies
- * every invariant the kernels' memory accesses rely on (index ranges, sorted
- * terminal order, parallel-run flags, staging offsets inside each window's
- * Jacobian slice, bulk-copy alignment, shared-memory size).  PF_OK or
- * PF_EINVAL with a message.
+ * and the element-wise windows for CTAs of `window` threads - cut at equal
+ * estimated cost into at most `nwin_target` windows when nwin_target is
+ * larger than the plain cut's count (ybus_build targets a whole number of
+ * waves of resident CTAs), the plain cut when it is 0 - and verifies every
+ * invariant the kernels' memory accesses rely on (index ranges, sorted
+ * terminal order, parallel-run flags, ghost-bus slots, window descriptors,
+ * staging offsets inside each window's Jacobian slice, bulk-copy alignment,
+ * shared-memory size).  PF_OK or PF_EINVAL with a message.
  */
-pf_status grid_selfcheck(const pf_grid_desc *desc, int32_t window);
+pf_status grid_selfcheck(const pf_grid_desc *desc, int32_t window, int32_t nwin_target);
 
 /* ------------------------------------------------------------ batches -- */
 

@@ -140,33 +140,57 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
 }
 
 // Build (host), check and upload the element-wise windows for CTAs of `tb`
-// threads (at most tb buses and tb terminals per window).
+// threads (at most tb buses and tb terminals per window).  The windows are cut
+// at equal estimated cost into a whole number of waves of the CTAs that fit
+// on the GPU at once, so that every SM gets the same work.
+static pf_status ew_fits(const HostEw &E, size_t *smem)
+{
+    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true, E.max_nph);
+    *smem = plan.total + kTrigN * sizeof(double2);
+    if (*smem > kMaxSmem)
+        return set_error(PF_EUNSUPPORTED, "an element-wise window needs %u bytes of shared memory (max %u): a bus "
+                                          "has too many branches for this library", (unsigned)*smem, kMaxSmem);
+    return PF_OK;
+}
+
 static pf_status build_ew_layout(Grid *g, int tb, cudaStream_t s)
 {
     HostEw E;
+    size_t smem = 0;
     pf_status st = host_ew(g->topo, tb, E);
-    if (st) return st;
-    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true, E.max_nbus + E.max_nh);
-    if (plan.total + kTrigN * sizeof(double2) > kMaxSmem)
-        return set_error(PF_EUNSUPPORTED, "an element-wise window needs %u bytes of shared memory (max %u): a bus "
-                                          "has too many branches for this library", plan.total, kMaxSmem);
+    if (st || (st = ew_fits(E, &smem))) return st;
+    int dev = 0, nsm = 0, per_sm = 0;
+    PF_CUDA(cudaGetDevice(&dev));
+    PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    PF_CUDA(ew_blocks_per_sm(tb, smem, &per_sm));
+    for (int pass = 0; pass < 2 && per_sm > 0 && E.nwin > 1; ++pass) {
+        const long long wave = (long long)nsm * per_sm;
+        const int target = (int)std::min<long long>(wave * ((E.nwin + wave - 1) / wave), INT32_MAX);
+        HostEw B;
+        size_t smem_b = 0;
+        if ((st = host_ew(g->topo, tb, B, 1, target)) || (st = ew_fits(B, &smem_b))) return st;
+        int per_sm_b = 0;
+        PF_CUDA(ew_blocks_per_sm(tb, smem_b, &per_sm_b));
+        E = std::move(B);
+        if (per_sm_b >= per_sm) break;   // the balanced windows still fit as planned
+        per_sm = per_sm_b;               // fewer fit: balance again for the smaller wave
+    }
 #ifdef PF_SELFCHECK
     if ((st = host_selfcheck(g->topo, E))) return st;
 #endif
-    g->arena.release(g->ew.win_bus);
-    g->arena.release(g->ew.hptr);
-    g->arena.release(g->ew.hbus);
+    g->arena.release(g->ew.desc);
+    g->arena.release(g->ew.slotbus);
     g->arena.release(g->ew.tloc);
     g->ew = EwDev{};
-    if ((st = upload(g->arena, &g->ew.win_bus, E.win_bus, s)) || (st = upload(g->arena, &g->ew.hptr, E.hptr, s)) ||
-        (st = upload(g->arena, &g->ew.hbus, E.hbus, s)) || (st = upload(g->arena, &g->ew.tloc, E.tloc, s)))
+    if ((st = upload(g->arena, &g->ew.desc, E.desc, s)) || (st = upload(g->arena, &g->ew.slotbus, E.slotbus, s)) ||
+        (st = upload(g->arena, &g->ew.tloc, E.tloc, s)))
         return st;
     g->ew.tb = E.tb;
     g->ew.nwin = E.nwin;
     g->ew.max_L = E.max_L;
     g->ew.max_nt = E.max_nt;
     g->ew.max_nbus = E.max_nbus;
-    g->ew.max_nh = E.max_nh;
+    g->ew.max_nph = E.max_nph;
     PF_CUDA(cudaStreamSynchronize(s));  // E's vectors are freed on return
     return PF_OK;
 }
@@ -645,13 +669,14 @@ PF_API pf_status grid_trace_read(pf_grid *grid, pf_trace_rec *out, int32_t cap, 
 
 // ---------------------------------------------------------- self-check ----
 
-PF_API pf_status grid_selfcheck(const pf_grid_desc *d, int32_t window)
+PF_API pf_status grid_selfcheck(const pf_grid_desc *d, int32_t window, int32_t nwin_target)
 {
     pf_status st = validate(d);
     if (st) return st;
+    if (nwin_target < 0) return set_error(PF_EINVAL, "grid_selfcheck: nwin_target = %d", nwin_target);
     HostTopo H;
     HostEw E;
     if ((st = host_topology(d->nb, d->nl, d->from, d->to, H))) return st;
-    if ((st = host_ew(H, window, E))) return st;
+    if ((st = host_ew(H, window, E, 1, nwin_target))) return st;
     return host_selfcheck(H, E);
 }

@@ -15,6 +15,7 @@
 //                      their ghost buses (other ends outside the window)
 #include <algorithm>
 #include <cstdint>
+#include <limits>
 
 #include "pf_internal.h"
 
@@ -109,7 +110,52 @@ pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo
     return PF_OK;
 }
 
-pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac)
+namespace {
+
+// FP64 instructions of a window's work in the element-wise kernel: per
+// terminal (evaluation and its share of the bus sums), per own bus (phasor,
+// diagonal entries, S), per ghost bus (phasor)
+constexpr long long kCostTerminal = 12, kCostBus = 33, kCostGhost = 17;
+
+// Greedy cut into windows of consecutive buses with at most tb buses, tcap
+// terminals and `cap` cost each (a single bus always forms a window); mark[]
+// (size nb) is scratch.  A window's cost grows with every bus added, so a
+// larger cap never gives more windows.
+void cut_windows(const HostTopo &H, int tb, int tcap, long long cap, std::vector<int> &wb, std::vector<int> &mark)
+{
+    const int nb = H.nb;
+    wb.assign(1, 0);
+    std::fill(mark.begin(), mark.end(), -1);
+    int b = 0, w = 0;
+    while (b < nb) {
+        const int b0 = b;
+        int nt = 0;
+        long long cost = 0;
+        while (b < nb && b - b0 < tb) {
+            const int p0 = H.tp[b], p1 = H.tp[b + 1], th = p1 - p0;
+            long long add = kCostBus + kCostTerminal * th - (mark[b] == w ? kCostGhost : 0);
+            for (int p = p0; p < p1; ++p) {
+                const int q = H.tnbr[p].x;
+                if ((q >= b0 && q < b) || mark[q] == w || (p > p0 && H.tnbr[p - 1].x == q)) continue;
+                add += kCostGhost;
+            }
+            if (b > b0 && (nt + th > tcap || cost + add > cap)) break;
+            for (int p = p0; p < p1; ++p) {
+                const int q = H.tnbr[p].x;
+                if (q < b0 || q > b) mark[q] = w;
+            }
+            nt += th;
+            cost += add;
+            ++b;
+        }
+        wb.push_back(b);
+        ++w;
+    }
+}
+
+}  // namespace
+
+pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac, int target_nwin)
 {
     if (tb != 128 && tb != 256)
         return set_error(PF_EINVAL, "ew_window (threads per element-wise CTA) must be 128 or 256 (got %d)", tb);
@@ -118,32 +164,36 @@ pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac)
     E = HostEw{};
     E.tb = tb;
     E.tfac = tfac;
-    E.win_bus.push_back(0);
-    int b = 0;
-    while (b < nb) {
-        const int b0 = b;
-        int nt = 0;
-        // greedy: at most tb buses and tfac * tb terminals; a bus with more
-        // terminals still forms a window by itself
-        while (b < nb && b - b0 < tb) {
-            const int t_here = H.tp[b + 1] - H.tp[b];
-            if (b > b0 && nt + t_here > tfac * tb) break;
-            nt += t_here;
-            ++b;
+    std::vector<int> mark(nb);
+    cut_windows(H, tb, tfac * tb, std::numeric_limits<long long>::max(), E.win_bus, mark);
+    if (target_nwin > 0 && (int)E.win_bus.size() - 1 < target_nwin) {
+        // balance: the smallest cost cap that still gives at most target_nwin windows
+        long long lo = 1, hi = 0;
+        for (int b = 0; b < nb; ++b) hi += kCostBus + (kCostTerminal + kCostGhost) * (H.tp[b + 1] - H.tp[b]);
+        std::vector<int> wb;
+        while (lo < hi) {
+            const long long mid = lo + (hi - lo) / 2;
+            cut_windows(H, tb, tfac * tb, mid, wb, mark);
+            if ((int)wb.size() - 1 <= target_nwin)
+                hi = mid;
+            else
+                lo = mid + 1;
         }
-        E.win_bus.push_back(b);
-        E.max_nt = std::max(E.max_nt, nt);
-        E.max_nbus = std::max(E.max_nbus, b - b0);
-        E.max_L = std::max(E.max_L, 2 * (H.rp[b] - H.rp[b0]));
+        cut_windows(H, tb, tfac * tb, lo, wb, mark);
+        if ((int)wb.size() - 1 <= target_nwin) E.win_bus.swap(wb);
     }
     E.nwin = (int)E.win_bus.size() - 1;
-    // ghost buses and the window-local slot of every terminal's other bus
+    // per window: sizes, ghost buses, the window-local slot of every terminal's other bus
     E.hptr.assign(E.nwin + 1, 0);
     E.hbus.clear();
     E.tloc.assign(H.tp[nb], make_int2(0, 0));
     std::vector<int> ghosts;
     for (int w = 0; w < E.nwin; ++w) {
         const int b0 = E.win_bus[w], b1 = E.win_bus[w + 1], nbus = b1 - b0;
+        const int nt = H.tp[b1] - H.tp[b0];
+        E.max_nt = std::max(E.max_nt, nt);
+        E.max_nbus = std::max(E.max_nbus, nbus);
+        E.max_L = std::max(E.max_L, 2 * (H.rp[b1] - H.rp[b0]));
         ghosts.clear();
         for (int p = H.tp[b0]; p < H.tp[b1]; ++p) {
             const int q = H.tnbr[p].x;
@@ -161,6 +211,19 @@ pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac)
         E.hbus.insert(E.hbus.end(), ghosts.begin(), ghosts.end());
         E.hptr[w + 1] = (int)E.hbus.size();
         E.max_nh = std::max(E.max_nh, (int)ghosts.size());
+        E.max_nph = std::max(E.max_nph, nbus + (int)ghosts.size());
+    }
+    // fixed-stride per-window records: the descriptor and the bus of every phasor slot
+    // (padding slots repeat the window's first bus)
+    E.desc.assign(2 * (size_t)E.nwin, make_int4(0, 0, 0, 0));
+    E.slotbus.assign((size_t)E.nwin * E.max_nph, 0);
+    for (int w = 0; w < E.nwin; ++w) {
+        const int b0 = E.win_bus[w], b1 = E.win_bus[w + 1], nbus = b1 - b0;
+        const int h0 = E.hptr[w], nph = nbus + E.hptr[w + 1] - h0;
+        E.desc[2 * w] = make_int4(b0, nbus, H.tp[b0], H.tp[b1] - H.tp[b0]);
+        E.desc[2 * w + 1] = make_int4(H.rp[b0], 2 * (H.rp[b1] - H.rp[b0]), nph, 0);
+        int *sb = E.slotbus.data() + (size_t)w * E.max_nph;
+        for (int j = 0; j < E.max_nph; ++j) sb[j] = j < nbus ? b0 + j : (j < nph ? E.hbus[h0 + j - nbus] : b0);
     }
     return PF_OK;
 }
@@ -231,6 +294,7 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
     CHECK((int)E.hptr.size() == E.nwin + 1 && E.hptr[0] == 0 && E.hptr[E.nwin] == (int)E.hbus.size(),
           "ghost-bus offsets");
     CHECK((int)E.tloc.size() == T, "terminal slots");
+    CHECK(E.desc.size() == 2 * (size_t)E.nwin && E.slotbus.size() == (size_t)E.nwin * E.max_nph, "window records");
     for (int w = 0; w < E.nwin; ++w) {
         const int b0 = E.win_bus[w], b1 = E.win_bus[w + 1], nbus = b1 - b0;
         const int h0 = E.hptr[w], nh = E.hptr[w + 1] - h0;
@@ -240,6 +304,16 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
             CHECK(q >= 0 && q < nb && (q < b0 || q >= b1), "window %d ghost %d", w, j);
             if (j > 0) CHECK(q > E.hbus[h0 + j - 1], "window %d ghosts not strictly sorted", w);
         }
+        const int4 d0 = E.desc[2 * w], d1 = E.desc[2 * w + 1];
+        CHECK(d0.x == b0 && d0.y == nbus && d0.z == H.tp[b0] && d0.w == H.tp[b1] - H.tp[b0], "window %d descriptor", w);
+        CHECK(d1.x == H.rp[b0] && d1.y == 2 * (H.rp[b1] - H.rp[b0]) && d1.z == nbus + nh && nbus + nh <= E.max_nph,
+              "window %d descriptor (rows, slots)", w);
+        for (int j = 0; j < E.max_nph; ++j) {
+            const int q = E.slotbus[(size_t)w * E.max_nph + j];
+            CHECK(q >= 0 && q < nb, "window %d slot %d bus", w, j);
+            if (j < nbus) CHECK(q == b0 + j, "window %d own slot %d", w, j);
+            else if (j < nbus + nh) CHECK(q == E.hbus[h0 + j - nbus], "window %d ghost slot %d", w, j);
+        }
         for (int p = H.tp[b0]; p < H.tp[b1]; ++p) {
             const int slot = E.tloc[p].x, q = H.tnbr[p].x;
             CHECK(E.tloc[p].y == H.tnbr[p].y, "terminal %d slot flags", p);
@@ -247,7 +321,7 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
             CHECK(slot < nbus ? b0 + slot == q : E.hbus[h0 + slot - nbus] == q, "terminal %d slot bus", p);
         }
     }
-    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true, E.max_nbus + E.max_nh);
+    const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true, E.max_nph);
     CHECK(plan.total <= kMaxSmem, "a window needs %u bytes of shared memory", plan.total);
     CHECK(plan.yd % 16 == 0 && plan.kg % 16 == 0 && plan.jst % 16 == 0 && plan.pq % 16 == 0 && plan.ph % 16 == 0,
           "shared-memory plan alignment");

@@ -34,9 +34,14 @@
 // with Yd_o = sum_t Ys_t + y_sh,o, a parameter-only per-bus constant formed at
 // setup from the same terminal constants.
 //
+// Work balance.  The windows are cut at equal estimated FP64 cost into a
+// whole number of waves of the CTAs that fit on the GPU (host_layout.cpp), so
+// every SM gets the same work.
+//
 // GB300 data movement.  Every global load of a window (its voltages, the
 // ghost voltages, the terminal constants of the first pass, the bus metadata)
-// is issued before any arithmetic.  A window's Jacobian rows are one
+// is issued before any arithmetic, in two levels of dependent loads (the
+// fixed-stride window records, then what they index).  A window's Jacobian rows are one
 // contiguous slice of each of the P and Q halves of J (canonical layout): it
 // is assembled in shared memory and written back with TMA bulk stores,
 // together with P and Q.
@@ -48,7 +53,8 @@ namespace pf {
 
 struct EwArgs {
     int nnz, max_nbus, max_nt, max_L, max_nph, aligned;
-    const int *win_bus, *hptr, *hbus, *tp, *rp, *kd, *town;
+    const int4 *desc;
+    const int *slotbus, *tp, *rp, *kd, *town;
     const double2 *yd, *tcoup, *trig;
     const int2 *tloc;
     const double *vm, *va;
@@ -85,18 +91,20 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
     double2 *sW = sU + a.max_nph;                                            // (v, 1/v)
     double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x, w = blockIdx.x;
-    const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
-    const int t0 = a.tp[b0], nt = a.tp[b1] - t0;
-    const int h0 = a.hptr[w], nph = nbus + a.hptr[w + 1] - h0;
-    const int r0 = a.rp[b0], L = JAC ? 2 * (a.rp[b1] - r0) : 0;
+    // two levels of dependent loads: the window's records (descriptor, the
+    // bus of the thread's first phasor slot), then everything they index
+    const int *sbus = a.slotbus + (long long)w * a.max_nph;
+    const int o0 = tid < a.max_nph ? sbus[tid] : 0;
+    const int4 d0 = a.desc[2 * w], d1 = a.desc[2 * w + 1];
+    const int b0 = d0.x, nbus = d0.y, b1 = b0 + nbus, t0 = d0.z, nt = d0.w;
+    const int r0 = d1.x, L = JAC ? d1.y : 0, nph = d1.z;
 
     // ---- loads: voltages of the first table slot, bus metadata, the first
     // terminal, the sine/cosine table ----
     double th = 0.0, v = 0.0;
     if (tid < nph) {
-        const int o = tid < nbus ? b0 + tid : a.hbus[h0 + tid - nbus];
-        th = a.va[o];
-        v = a.vm[o];
+        th = a.va[o0];
+        v = a.vm[o0];
     }
     const double vb = v;   // the bus thread's own magnitude (slot tid < nbus)
     for (int b = tid; b < nbus; b += TB) {
@@ -118,7 +126,7 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
     // ---- phasor table of the window (Sec. IV-B.1 step 1, own and ghost buses) ----
     for (int j = tid; j < nph; j += TB) {
         if (j != tid) {
-            const int o = j < nbus ? b0 + j : a.hbus[h0 + j - nbus];
+            const int o = sbus[j];
             th = a.va[o];
             v = a.vm[o];
         }
@@ -253,7 +261,7 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
 {
     const EwDev &L = g->ew;
     if (L.nwin == 0) return cudaSuccess;
-    const int max_nph = L.max_nbus + L.max_nh;
+    const int max_nph = L.max_nph;
     const EwSmem sp = ew_smem_plan(L.max_nbus, L.max_nt, JAC ? L.max_L : 0, JAC, max_nph);
     const uint32_t smem = sp.total + kTrigN * (uint32_t)sizeof(double2);
     uint32_t &conf = JAC ? g->ew_smem_jac : g->ew_smem_inj;
@@ -269,9 +277,8 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.max_L = L.max_L;
     a.max_nph = max_nph;
     a.aligned = (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
-    a.win_bus = L.win_bus;
-    a.hptr = L.hptr;
-    a.hbus = L.hbus;
+    a.desc = L.desc;
+    a.slotbus = L.slotbus;
     a.tp = g->tp;
     a.rp = g->rp;
     a.kd = g->kd;
@@ -287,6 +294,15 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.J = J;
     k_ew<JAC><<<(unsigned)L.nwin, (unsigned)L.tb, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm)
+{
+    if (smem > 48u * 1024u) {
+        cudaError_t e = cudaFuncSetAttribute(k_ew<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ew<true>, tb, smem);
 }
 
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,

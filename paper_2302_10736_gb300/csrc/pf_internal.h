@@ -79,6 +79,7 @@ struct HostEw {
     int max_nt = 0;     // max terminals in a window
     int max_nbus = 0;   // max buses in a window
     int max_nh = 0;     // max ghost buses of a window
+    int max_nph = 0;    // max phasor slots (own + ghost buses) of a window
     std::vector<int> win_bus;   // [nwin+1]
     // Ghost buses: the buses outside a window that its terminals reach,
     // sorted, window w's at hbus[hptr[w] .. hptr[w+1]).  A window's phasor
@@ -87,10 +88,18 @@ struct HostEw {
     // per sorted terminal: {phasor-table slot of the other bus, Ybus slot
     // position | EW_ACCUM} (tnbr with the bus replaced by its window slot)
     std::vector<int2> tloc;
+    // per window w: desc[2w] = {first bus, buses, first terminal, terminals},
+    // desc[2w+1] = {first Ybus row entry, J slice length, phasor slots, 0};
+    // slotbus[w * max_nph + j] = bus of phasor slot j
+    std::vector<int4> desc;
+    std::vector<int> slotbus;
 };
 
 pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo &H);
-pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac = 1);
+// Windows of consecutive buses (<= tb buses, <= tfac * tb terminals).  With
+// target_nwin > 0 they are cut at equal estimated cost into at most
+// target_nwin windows when the plain greedy cut gives fewer.
+pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac = 1, int target_nwin = 0);
 pf_status host_selfcheck(const HostTopo &H, const HostEw &E);
 
 // Shared-memory plan of the element-wise kernels (byte offsets, 16-aligned):
@@ -123,9 +132,9 @@ constexpr uint32_t kMaxSmem = 227u * 1024u;
 
 // ------------------------------------------------ device-side structure --
 struct EwDev {
-    int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0, max_nh = 0;
-    int *win_bus = nullptr;   // [nwin+1]
-    int *hptr = nullptr, *hbus = nullptr;   // ghost buses per window
+    int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0, max_nph = 0;
+    int4 *desc = nullptr;     // [2 nwin] window descriptors (HostEw::desc)
+    int *slotbus = nullptr;   // [nwin * max_nph] bus of every phasor slot
     int2 *tloc = nullptr;     // [T] {phasor slot of the other bus, slot position | flags}
 };
 
@@ -216,6 +225,7 @@ cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32
 cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ybus(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s);
 // element-wise: one cooperative kernel (phasors of each window's buses, grid barrier, evaluation)
+cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm);   // CTAs of k_ew<true> that fit on one SM
 cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
                           cudaStream_t s);

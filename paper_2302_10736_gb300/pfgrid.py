@@ -71,7 +71,7 @@ def _load():
         "pf_kernel_name": (ctypes.c_char_p, [i32]),
         "grid_trace_enable": (st, [vp, i32]),
         "grid_trace_read": (st, [vp, ctypes.POINTER(pf_trace_rec), i32, pi32]),
-        "grid_selfcheck": (st, [ctypes.POINTER(pf_grid_desc), i32]),
+        "grid_selfcheck": (st, [ctypes.POINTER(pf_grid_desc), i32, i32]),
         "phasor": (st, [i32, vp, vp, vp, vp, vp]),
         "grid_inject_barrier_fault": (st, [vp, vp]),
         "inj_ybus_noalloc": (st, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
@@ -172,11 +172,11 @@ def _desc(gr, keep):
                         h("bs", np.float64))
 
 
-def grid_selfcheck(gr, window):
+def grid_selfcheck(gr, window, nwin_target=0):
     """Host-only check of every index invariant of the kernels (no GPU)."""
     keep = []
     d = _desc(gr, keep)
-    _check(_lib.grid_selfcheck(ctypes.byref(d), int(window)), "grid_selfcheck")
+    _check(_lib.grid_selfcheck(ctypes.byref(d), int(window), int(nwin_target)), "grid_selfcheck")
 
 
 def ybus_build(gr, stream=None):

@@ -70,9 +70,10 @@ def test_oversized_grid_rejected(pf):
     assert st == 7
 
 
+@pytest.mark.parametrize("target", [0, 760])
 @pytest.mark.parametrize("window", [128, 256])
 @pytest.mark.parametrize("case", ["three_bus_plus", "parallel_star", "single_bus", "empty", "c1", "c2", "c3", "c4"])
-def test_layout_selfcheck(pf, case, window):
+def test_layout_selfcheck(pf, case, window, target):
     """Every index the kernels read or write stays inside its buffer (host check)."""
     from gridcases import make_grid
     from paper_2302_10736_gb300 import synth
@@ -88,7 +89,7 @@ def test_layout_selfcheck(pf, case, window):
     else:
         w = synth.WORKLOADS[int(case[1])]
         gr = synth.grid(w["nb"], w["nl"], synth.BASE_SEED + int(case[1]), pv_frac=w["pv"])
-    pf.grid_selfcheck(gr, window)
+    pf.grid_selfcheck(gr, window, target)
 
 
 def test_selfcheck_rejects_bad_window(pf):
@@ -96,9 +97,10 @@ def test_selfcheck_rejects_bad_window(pf):
         pf.grid_selfcheck(three_bus_plus(), 100)
 
 
+@pytest.mark.parametrize("target", [0, 1520])
 @pytest.mark.parametrize("window", [128, 256])
-def test_layout_selfcheck_random_numbering(window):
+def test_layout_selfcheck_random_numbering(window, target):
     """The ghost-bus layout of a grid numbered without locality."""
     from paper_2302_10736_gb300 import pfgrid, synth
     w = synth.renumber_buses(synth.workload(1), 99)
-    pfgrid.grid_selfcheck(w, window)
+    pfgrid.grid_selfcheck(w, window, target)
