@@ -55,8 +55,15 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
         b->h_sc[s] = scen_outage(g->topo, outage ? outage[s] : -1);
         b->h_joff[s + 1] = b->h_joff[s] + 4LL * (g->nnz - 2 * b->h_sc[s].del);
     }
-    // the batch's own windows: 256 buses and up to 3 x 256 terminals each
-    // (fewer terminals per thread if a window would not fit in shared memory)
+    // The batch's own windows: 256 buses and up to 3 x 256 terminals each
+    // (fewer terminals per thread if a window would not fit in shared memory),
+    // so that every thread owns a bus in the reduction.  When the batch has
+    // fewer (scenario, window) items than the GPU has SMs, the windows are cut
+    // at equal cost into about one item per SM (more CTAs would only make the
+    // grid barriers dearer).
+    auto fits = [](const HostEw &L) {
+        return ew_smem_plan(L.max_nbus, L.max_nt, L.max_L, true).total + kTrigN * sizeof(double2) <= kMaxSmem;
+    };
     HostEw E;
     for (int tfac = 3; tfac >= 1; --tfac) {
         pf_status hs = host_ew(g->topo, 256, E, tfac);
@@ -64,11 +71,22 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
             delete pb;
             return hs;
         }
-        if (ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true).total + kTrigN * sizeof(double2) <= kMaxSmem) break;
+        if (fits(E)) break;
         if (tfac == 1) {
             delete pb;
             return set_error(PF_EUNSUPPORTED, "batch_create: a window exceeds shared memory");
         }
+    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+        delete pb;
+        return set_error(PF_ECUDA, "batch_create: cannot query the device");
+    }
+    if (nscen > 0 && (long long)nscen * E.nwin < nsm) {
+        HostEw F;
+        const int target = (nsm + nscen - 1) / nscen;
+        if (host_ew(g->topo, 256, F, E.tfac, target) == PF_OK && F.nwin > E.nwin && fits(F)) E = std::move(F);
     }
 #ifdef PF_SELFCHECK
     if (pf_status hs = host_selfcheck(g->topo, E)) {

@@ -225,6 +225,11 @@ pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac, int target_nwi
         int *sb = E.slotbus.data() + (size_t)w * E.max_nph;
         for (int j = 0; j < E.max_nph; ++j) sb[j] = j < nbus ? b0 + j : (j < nph ? E.hbus[h0 + j - nbus] : b0);
     }
+    E.bmeta.assign(nb, make_int4(0, 0, 0, 0));
+    for (int w = 0; w < E.nwin; ++w)
+        for (int o = E.win_bus[w]; o < E.win_bus[w + 1]; ++o)
+            E.bmeta[o] = make_int4(2 * (H.rp[o] - H.rp[E.win_bus[w]]), H.rp[o + 1] - H.rp[o], H.kd[o],
+                                   H.tp[o] - H.tp[E.win_bus[w]]);
     return PF_OK;
 }
 
@@ -280,6 +285,8 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
         CHECK((2LL * H.rp[b0]) % 2 == 0 && (8LL * L) % 16 == 0, "window %d J slice alignment", w);
         for (int o = b0; o < b1; ++o) {
             const int lrow = 2 * (H.rp[o] - H.rp[b0]), d = H.rp[o + 1] - H.rp[o];
+            CHECK(E.bmeta[o].x == lrow && E.bmeta[o].y == d && E.bmeta[o].z == H.kd[o] &&
+                      E.bmeta[o].w == H.tp[o] - H.tp[b0], "bus %d window metadata", o);
             CHECK(lrow >= 0 && lrow + 2 * d <= L, "bus %d row slice outside the window slice", o);
             CHECK(lrow + H.kd[o] + d < L, "bus %d diagonal staging index", o);
             for (int p = H.tp[o]; p < H.tp[o + 1]; ++p) {
@@ -294,7 +301,8 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
     CHECK((int)E.hptr.size() == E.nwin + 1 && E.hptr[0] == 0 && E.hptr[E.nwin] == (int)E.hbus.size(),
           "ghost-bus offsets");
     CHECK((int)E.tloc.size() == T, "terminal slots");
-    CHECK(E.desc.size() == 2 * (size_t)E.nwin && E.slotbus.size() == (size_t)E.nwin * E.max_nph, "window records");
+    CHECK(E.desc.size() == 2 * (size_t)E.nwin && E.slotbus.size() == (size_t)E.nwin * E.max_nph &&
+              (int)E.bmeta.size() == nb, "window records");
     for (int w = 0; w < E.nwin; ++w) {
         const int b0 = E.win_bus[w], b1 = E.win_bus[w + 1], nbus = b1 - b0;
         const int h0 = E.hptr[w], nh = E.hptr[w + 1] - h0;

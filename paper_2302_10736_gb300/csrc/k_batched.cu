@@ -556,7 +556,7 @@ cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const d
     a.aligned = al16(gvm) && al16(gva);
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false);
     const size_t smem = sp.total + kTrigN * sizeof(double2);
-    const long long items = std::max<long long>((long long)b->S * b->nwin, (g->nl + 255) / 256);
+    const long long items = std::max<long long>((long long)b->S * b->nwin, (g->nl + b->tb - 1) / b->tb);
     return coop_launch(k_adj, b->resident[2], b, smem, items, s, a);
 }
 

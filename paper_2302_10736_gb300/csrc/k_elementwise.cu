@@ -53,8 +53,8 @@ namespace pf {
 
 struct EwArgs {
     int nnz, max_nbus, max_nt, max_L, max_nph, aligned;
-    const int4 *desc;
-    const int *slotbus, *tp, *rp, *kd, *town;
+    const int4 *desc, *bmeta;
+    const int *slotbus, *town;
     const double2 *yd, *tcoup, *trig;
     const int2 *tloc;
     const double *vm, *va;
@@ -107,10 +107,13 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
         v = a.vm[o0];
     }
     const double vb = v;   // the bus thread's own magnitude (slot tid < nbus)
-    for (int b = tid; b < nbus; b += TB) {
-        const int o = b0 + b, rs = a.rp[o];
-        sbm[b] = make_int4(2 * (rs - r0), a.rp[o + 1] - rs, a.kd[o], a.tp[o] - t0);
-        syd[b] = a.yd[o];
+    // the bus thread's metadata (a window has at most blockDim.x buses), kept
+    // in registers until the phasors are done so its latency hides behind them
+    int4 bmo = make_int4(0, 0, 0, 0);
+    double2 ydo = make_double2(0.0, 0.0);
+    if (tid < nbus) {
+        bmo = a.bmeta[b0 + tid];
+        ydo = a.yd[b0 + tid];
     }
     double2 yc = make_double2(0.0, 0.0);
     int2 nq = make_int2(0, 0);
@@ -137,6 +140,10 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
             sU[j] = make_double2(c, s);
             sW[j] = make_double2(v, j < nbus ? fast_rcp(v) : 0.0);
         }
+    }
+    if (tid < nbus) {
+        sbm[tid] = bmo;
+        syd[tid] = ydo;
     }
     __syncthreads();
 
@@ -279,9 +286,7 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.aligned = (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
     a.desc = L.desc;
     a.slotbus = L.slotbus;
-    a.tp = g->tp;
-    a.rp = g->rp;
-    a.kd = g->kd;
+    a.bmeta = L.bmeta;
     a.town = g->town;
     a.yd = g->bus_yd;
     a.tcoup = g->tcoup;

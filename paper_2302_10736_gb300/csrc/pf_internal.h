@@ -93,6 +93,9 @@ struct HostEw {
     // slotbus[w * max_nph + j] = bus of phasor slot j
     std::vector<int4> desc;
     std::vector<int> slotbus;
+    // per bus o of window w: {2 (rowptr[o] - rowptr[b0]) (its row in the
+    // window's J slice), Ybus row length, diagonal position, tp[o] - tp[b0]}
+    std::vector<int4> bmeta;
 };
 
 pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo &H);
@@ -135,6 +138,7 @@ struct EwDev {
     int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0, max_nph = 0;
     int4 *desc = nullptr;     // [2 nwin] window descriptors (HostEw::desc)
     int *slotbus = nullptr;   // [nwin * max_nph] bus of every phasor slot
+    int4 *bmeta = nullptr;    // [nb] window-relative bus metadata (HostEw::bmeta)
     int2 *tloc = nullptr;     // [T] {phasor slot of the other bus, slot position | flags}
 };
 
