@@ -183,39 +183,48 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
     }
     __syncthreads();
 
-    // ---- reduction: one thread per bus, its terminals in sorted order ----
+    // ---- reduction: its terminals in sorted order onto every bus ----
     const int pqs = (int)sp.pqs, par = b0 & 1;
-    for (int b = tid; b < nbus; b += TB) {
-        const int4 bm = sbm[b];
-        const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
-        const double2 y = syd[b];
-        double sKr = 0.0, sKi = 0.0;
-        if (JAC) {
+    if (JAC) {
+        // two threads per bus: x = 2b + im sums the real (im = 0) or imaginary
+        // (im = 1) parts of K and writes the entries that depend on them only;
+        // the arithmetic is uniform across the pair (no divergence)
+        const double *kg = reinterpret_cast<const double *>(skg);   // K.x, K.y, G.x, G.y per terminal
+        for (int x = tid; x < 2 * nbus; x += TB) {
+            const int b = x >> 1, im = x & 1;
+            const int4 bm = sbm[b];
+            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
             const int d = bm.y;
+            double sK = 0.0;
             for (int i = bm.w; i < tend; ++i) {
-                const double2 K = skg[2 * i];
-                sKr += K.x;
-                sKi += K.y;
+                sK += kg[4 * i + im];
                 const int kp = skp[i];
                 if (kp & EW_ACCUM) {   // later branch of a parallel run: add into the run's slot
-                    const double2 G = skg[2 * i + 1];
                     const int pos = bm.x + (kp & EW_KMASK);
-                    jst[pos] += K.y;
-                    jst[pos + d] += G.x;
-                    jst[L + pos] -= K.x;
-                    jst[L + pos + d] += G.y;
+                    if (im) {
+                        jst[pos] += kg[4 * i + 1];           // J11 += Re(-j K)
+                        jst[L + pos + d] += kg[4 * i + 3];   // J22 += Im G
+                    } else {
+                        jst[pos + d] += kg[4 * i + 2];       // J12 += Re G
+                        jst[L + pos] -= kg[4 * i];           // J21 += Im(-j K)
+                    }
                 }
             }
-            const double2 vw = sW[b];
+            const double2 y = syd[b], vw = sW[b];
             const double vo = vw.x, iv = vw.y, v2 = vo * vo, tv = vo + vo;
+            // real part: Re conj(Yd) = y.x; imaginary part: Im conj(Yd) = -y.y (sign flips are exact)
+            const double yr = im ? -y.y : y.x;
             const int pos = bm.x + bm.z;
-            jst[pos] = -sKi;                         // Re(j sum K)
-            jst[pos + d] = fma(tv, y.x, sKr * iv);
-            jst[L + pos] = sKr;                      // Im(j sum K)
-            jst[L + pos + d] = fma(-tv, y.y, sKi * iv);
-            spq[b + par] = fma(v2, y.x, sKr);
-            spq[pqs + b + par] = fma(-v2, y.y, sKi);
-        } else {
+            jst[(im ? 0 : L) + pos] = im ? -sK : sK;              // Re / Im of j sum K
+            jst[(im ? L : 0) + pos + d] = fma(tv, yr, sK * iv);   // 2 v conj(Yd) + sum K / v
+            spq[(im ? pqs : 0) + b + par] = fma(v2, yr, sK);      // S = v^2 conj(Yd) + sum K
+        }
+    } else {
+        for (int b = tid; b < nbus; b += TB) {
+            const int4 bm = sbm[b];
+            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+            const double2 y = syd[b];
+            double sKr = 0.0, sKi = 0.0;
             for (int i = bm.w; i < tend; ++i) {
                 sKr += skg[i].x;
                 sKi += skg[i].y;
