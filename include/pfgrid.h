@@ -167,9 +167,13 @@ pf_status jac_elementwise(pf_grid *grid, const double *vm, const double *va, dou
 /*
  * End-to-end evaluation from HOST buffers: copies vm, va [nb] to grid-owned
  * device buffers, runs jac_ybus (method 0) or jac_elementwise (method 1),
- * copies P, Q [nb] and J [4 nnzY] back, and synchronizes `stream`.  The
+ * brings P, Q [nb] and J [4 nnzY] back, and synchronizes `stream`.  The
  * device staging buffers are allocated on the first call and kept by the
- * grid.  Host buffers may be pageable or pinned (pinned is faster).
+ * grid.  Host buffers may be pageable or page-locked; when P, Q and J are
+ * page-locked and mapped (cudaHostAlloc, cudaHostRegister) the element-wise
+ * kernel stores its results straight into them (and reads vm, va straight
+ * from them when those are page-locked too), so the transfers overlap the
+ * evaluation instead of preceding and following it.
  */
 pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P, double *Q,
                     double *J, pf_stream stream);

@@ -421,6 +421,18 @@ PF_API pf_status jac_elementwise(pf_grid *grid, const double *vm, const double *
     return PF_OK;
 }
 
+// Device address of a host buffer that kernels can write directly
+// (page-locked and mapped: cudaHostAlloc, cudaHostRegister), else nullptr.
+static void *mapped_device_ptr(const void *h)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 PF_API pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P, double *Q,
                            double *J, pf_stream stream)
 {
@@ -438,6 +450,26 @@ PF_API pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, cons
         PF_CUDA(g->arena.alloc(&g->st_P, nb));
         PF_CUDA(g->arena.alloc(&g->st_Q, nb));
         PF_CUDA(g->arena.alloc(&g->st_J, nJ));
+    }
+    if (method == 1) {
+        // page-locked, mapped host buffers: the kernel reads vm, va and stores
+        // P, Q, J (plain coalesced stores) across the host link while it runs;
+        // no staging copies
+        void *dvm = mapped_device_ptr(vm), *dva = mapped_device_ptr(va);
+        void *dP = mapped_device_ptr(P), *dQ = mapped_device_ptr(Q), *dJ = mapped_device_ptr(J);
+        if (dP && dQ && dJ) {
+            if (!dvm || !dva) {
+                PF_CUDA(cudaMemcpyAsync(g->st_vm, vm, nb * 8, cudaMemcpyHostToDevice, s));
+                PF_CUDA(cudaMemcpyAsync(g->st_va, va, nb * 8, cudaMemcpyHostToDevice, s));
+                dvm = g->st_vm;
+                dva = g->st_va;
+            }
+            TraceScope t(g, PF_K_JAC_EW, s);
+            PF_CUDA(launch_jac_ew(g, (const double *)dvm, (const double *)dva, (double *)dP, (double *)dQ,
+                                  (double *)dJ, s, true));
+            PF_CUDA(cudaStreamSynchronize(s));
+            return PF_OK;
+        }
     }
     PF_CUDA(cudaMemcpyAsync(g->st_vm, vm, nb * 8, cudaMemcpyHostToDevice, s));
     PF_CUDA(cudaMemcpyAsync(g->st_va, va, nb * 8, cudaMemcpyHostToDevice, s));

@@ -273,7 +273,7 @@ static bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 template <bool JAC>
 static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
-                             cudaStream_t s)
+                             cudaStream_t s, bool host_out)
 {
     const EwDev &L = g->ew;
     if (L.nwin == 0) return cudaSuccess;
@@ -292,7 +292,8 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.max_nt = L.max_nt;
     a.max_L = L.max_L;
     a.max_nph = max_nph;
-    a.aligned = (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
+    // bulk (TMA) stores for device outputs; plain coalesced stores for host memory
+    a.aligned = !host_out && (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
     a.desc = L.desc;
     a.slotbus = L.slotbus;
     a.bmeta = L.bmeta;
@@ -320,14 +321,14 @@ cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm)
 }
 
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
-                          cudaStream_t s)
+                          cudaStream_t s, bool host_out)
 {
-    return launch_ew<true>(g, vm, va, P, Q, J, s);
+    return launch_ew<true>(g, vm, va, P, Q, J, s, host_out);
 }
 
 cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s)
 {
-    return launch_ew<false>(g, vm, va, P, Q, nullptr, s);
+    return launch_ew<false>(g, vm, va, P, Q, nullptr, s, false);
 }
 
 }  // namespace pf

@@ -232,7 +232,7 @@ cudaError_t launch_jac_ybus(const Grid *g, const double4_32a *U, double *P, doub
 cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm);   // CTAs of k_ew<true> that fit on one SM
 cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
-                          cudaStream_t s);
+                          cudaStream_t s, bool host_out = false);   // host_out: P, Q, J in mapped host memory
 
 // ----------------------------------------------------------- batches ----
 // S scenarios over one grid: per-scenario voltage states and an optional N-1

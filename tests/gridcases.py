@@ -93,3 +93,29 @@ def relerr(x, ref):
     den = np.max(np.abs(ref))
     num = np.max(np.abs(x - ref))
     return float(num / den) if den > 0 else float(num)
+
+
+def hub_grid(nspokes, seed, nring=600):
+    """A ring of `nring` buses plus one hub bus joined to `nspokes` ring buses
+    (some twice: parallel spokes): a window holding the hub alone has more
+    terminals, and more ghost buses, than a CTA has threads."""
+    rng = np.random.default_rng(seed)
+    nb = nring + 1
+    hub = nring // 2
+    br = []
+    for i in range(nring + 1):
+        if i == hub:
+            continue
+        j = i + 1 if i + 1 != hub else i + 2
+        if j <= nring:
+            g, b = series(rng.uniform(0.001, 0.05), rng.uniform(0.01, 0.3))
+            br.append((i, j, g, b, rng.uniform(0, 0.1), 1.0, 0.0))
+    targets = rng.choice([i for i in range(nb) if i != hub], size=nspokes, replace=False)
+    for n, q in enumerate(targets):
+        g, b = series(rng.uniform(0.001, 0.05), rng.uniform(0.01, 0.3))
+        tap = rng.uniform(0.9, 1.1) if n % 5 == 0 else 1.0
+        e = (hub, int(q)) if n % 2 else (int(q), hub)
+        br.append(e + (g, b, rng.uniform(0, 0.1), tap, rng.uniform(-0.1, 0.1) if n % 7 == 0 else 0.0))
+        if n % 50 == 0:
+            br.append(e + (0.5 * g, 0.5 * b, 0.0, tap, 0.0))
+    return make_grid(nb, br, shunts={hub: (0.02, -0.01), 3: (0.01, 0.04)})

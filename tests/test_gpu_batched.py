@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gridcases import blocks, make_grid, random_grid, random_state, relerr
+from gridcases import blocks, hub_grid, make_grid, random_grid, random_state, relerr
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -122,6 +122,20 @@ def test_ybus_batched_every_lane_count(pf, lanes):
     outage = np.array([int(nonbridge[5]), -1, 0, gr["nl"] - 1, int(nonbridge[40])], np.int32)
     vm, va = synth.voltages(300, len(outage), 23, 0, 0.93, 1.07, 0.25)
     check_batch(pf, gr, vm, va, outage, cfg=dict(ybus_lanes=lanes, ybus_block=128))
+
+
+def test_batch_with_a_hub_bus(pf):
+    """Windows whose single bus has more terminals than the CTA has threads,
+    outages of a hub spoke, of one of a parallel pair of spokes and of a ring
+    branch."""
+    from paper_2302_10736_gb300 import synth
+    gr = hub_grid(400, 32)
+    S = 4
+    hub = (gr["nb"] - 1) // 2
+    spokes = [l for l in range(gr["nl"]) if hub in (gr["f"][l], gr["t"][l])]
+    outage = np.array([spokes[3], -1, spokes[0], 5], np.int32)
+    vm, va = synth.voltages(gr["nb"], S, 32, 0, 0.93, 1.07, 0.25)
+    check_batch(pf, gr, vm, va, outage)
 
 
 def test_batch_without_outages_equals_single_evaluation(pf):

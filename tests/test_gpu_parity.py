@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gridcases import blocks, make_grid, random_grid, random_state, relerr, three_bus_plus, two_bus_lossless
+from gridcases import (blocks, hub_grid, make_grid, random_grid, random_state, relerr, three_bus_plus,
+                       two_bus_lossless)
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -114,6 +115,17 @@ def test_random_bus_numbering(pf, window):
     check_against_oracle(pf, w, w["vm"][0], w["va"][0], grid=grid)
 
 
+@pytest.mark.parametrize("window", [128, 256])
+def test_hub_bus_beyond_one_thread_per_terminal(pf, window):
+    """A bus with 400 branches: its window has more terminals and phasor
+    slots than the CTA has threads."""
+    gr = hub_grid(400, 31)
+    vm, va = random_state(gr["nb"], 31)
+    grid = pf.ybus_build(gr)
+    pf.grid_set_config(grid, ew_window=window)
+    check_against_oracle(pf, gr, vm, va, grid=grid)
+
+
 def test_single_bus_no_branches(pf):
     gr = make_grid(1, [], shunts={0: (0.03, -0.02)})
     check_against_oracle(pf, gr, np.array([1.02]), np.array([0.3]))
@@ -176,11 +188,17 @@ def test_eval_host_matches_device(pf):
     grid = pf.ybus_build(w)
     vm, va = w["vm"][0].copy(), w["va"][0].copy()
     dev = gpu_eval(pf, grid, vm, va)
+    import torch
+    pinned = lambda n: torch.full((n,), np.nan, dtype=torch.float64, pin_memory=True).numpy()
     for m, name in ((0, "jac_ybus"), (1, "jac_elementwise")):
-        P, Q, J = np.zeros(grid.nb), np.zeros(grid.nb), np.zeros(grid.nnzJ)
-        pf.eval_host(grid, m, vm, va, P, Q, J)
-        assert np.array_equal(P, dev[name][0]) and np.array_equal(Q, dev[name][1])
-        assert np.array_equal(J, dev[name][2])
+        # pageable outputs (staged copies) and page-locked outputs (written by the kernel)
+        for alloc in (lambda n: np.full(n, np.nan), pinned):
+            P, Q, J = alloc(grid.nb), alloc(grid.nb), alloc(grid.nnzJ)
+            for vin, ain in ((vm, va), (pinned(grid.nb), pinned(grid.nb))):
+                vin[:], ain[:] = vm, va
+                pf.eval_host(grid, m, vin, ain, P, Q, J)
+                assert np.array_equal(P, dev[name][0]) and np.array_equal(Q, dev[name][1])
+                assert np.array_equal(J, dev[name][2])
 
 
 def test_set_params_matches_rebuild(pf):
