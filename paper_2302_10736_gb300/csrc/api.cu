@@ -9,7 +9,8 @@
 //   * the Ybus CSR pattern and, per nonzero, the range of sorted terminals
 //     whose stamps it sums (deterministic value assembly on the device);
 //   * the canonical J pattern (closed form of Alg. 2);
-//   * the element-wise sliced-ELL layout (EwLayout in pf_internal.h).
+//   * the element-wise windows of consecutive buses, cut at equal cost, with
+//     their ghost buses and fixed-stride descriptors (host_layout.cpp).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>

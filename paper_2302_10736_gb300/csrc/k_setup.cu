@@ -1,6 +1,6 @@
 // k_setup.cu - parameter-dependent setup kernels and the phasor step.
 //
-// Branch constants (Sec. IV-C.1: constants "calculated once ahead of time"):
+// Branch constants (Sec. IV-C.1 precomputes them once per parameter set):
 // every terminal t of branch l gets a self constant Ys_t and a coupling
 // constant Yc_t such that its complex power (Eqs. 5-6) is
 //     S_t = v_o^2 conj(Ys_t) + conj(Yc_t) V_o conj(V_q)      (o owner, q other bus)

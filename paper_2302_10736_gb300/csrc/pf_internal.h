@@ -167,8 +167,8 @@ struct Grid {
     int *tmir = nullptr;                   // [2nl] by sorted position: sorted position of the mirror terminal
     // device copies of the current parameters (branch gradients need them)
     double *p_g = nullptr, *p_b = nullptr, *p_bsh = nullptr, *p_tap = nullptr, *p_shift = nullptr;
-    unsigned int *bar = nullptr;   // grid-barrier state {arrivals, generation}
-    // per-call workspace (device)
+    unsigned int *bar = nullptr;   // grid-barrier state {arrivals, generation} of the batched kernels
+    // per-call workspace of the Ybus method's phasor step (device)
     double4_32a *ph_u = nullptr;   // [nb] {cos, sin, v, 1/v}
     double2 *ph_v = nullptr;       // [nb] V = v e^{j theta}
     int *err = nullptr;            // device error word
@@ -228,7 +228,7 @@ const double2 *trig_table();       // device address of the (cos, sin) table of 
 cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32a *U, double2 *V, cudaStream_t s);
 cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ybus(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s);
-// element-wise: one cooperative kernel (phasors of each window's buses, grid barrier, evaluation)
+// element-wise: one CTA per window (phasors of its own and ghost buses, evaluation, reduction)
 cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm);   // CTAs of k_ew<true> that fit on one SM
 cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
