@@ -16,7 +16,7 @@
 // Values are written straight into the canonical J layout, i.e. the copy of
 // Alg. 2 with its index arrays in closed form.
 //
-// The row's first kChunk entries (column index and Y value, static data) are
+// The row's first entries (column index and Y value, static data) are
 // loaded before the programmatic-dependent-launch wait; the phasor gathers of
 // a chunk are issued together before its arithmetic.
 #include "pf_internal.h"
@@ -24,7 +24,10 @@
 
 namespace pf {
 
-constexpr int kChunk = 4;
+// entries per lane prefetched together: a row of the synthetic grids has about 3.5
+// entries, so wide rows (W >= 4 lanes) hold one each and narrow ones several
+template <int W>
+constexpr int kChunkW = W >= 4 ? 1 : (W == 2 ? 2 : 4);
 
 template <int W>
 __global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict__ rp, const int *__restrict__ ci,
@@ -35,14 +38,14 @@ __global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict_
     const int row = (int)(gid / W), lane = (int)(gid % W);
     const bool valid = row < nb;
     int rs = 0, d = 0;
-    int jj[kChunk];
-    double2 yy[kChunk];
+    int jj[kChunkW<W>];
+    double2 yy[kChunkW<W>];
     if (valid) {
         rs = rp[row];
         d = rp[row + 1] - rs;
     }
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) {
+    for (int j = 0; j < kChunkW<W>; ++j) {
         const int k = lane + W * j;
         if (k < d) {
             jj[j] = ci[rs + k];
@@ -51,10 +54,10 @@ __global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict_
     }
     pdl_wait();
     double Ir = 0.0, Ii = 0.0;
-    for (int k0 = lane; k0 < d; k0 += W * kChunk) {
+    for (int k0 = lane; k0 < d; k0 += W * kChunkW<W>) {
         if (k0 != lane) {
 #pragma unroll
-            for (int j = 0; j < kChunk; ++j) {
+            for (int j = 0; j < kChunkW<W>; ++j) {
                 const int k = k0 + W * j;
                 if (k < d) {
                     jj[j] = ci[rs + k];
@@ -62,12 +65,12 @@ __global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict_
                 }
             }
         }
-        double2 vv[kChunk];
+        double2 vv[kChunkW<W>];
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j)
+        for (int j = 0; j < kChunkW<W>; ++j)
             if (k0 + W * j < d) vv[j] = V[jj[j]];
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
+        for (int j = 0; j < kChunkW<W>; ++j) {
             if (k0 + W * j < d) {
                 Ir = fma(yy[j].x, vv[j].x, Ir);
                 Ir = fma(-yy[j].y, vv[j].y, Ir);
@@ -98,14 +101,14 @@ __global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__
     const int row = (int)(gid / W), lane = (int)(gid % W);
     const bool valid = row < nb;
     int rs = 0, d = 0;
-    int jj[kChunk];
-    double2 yy[kChunk];
+    int jj[kChunkW<W>];
+    double2 yy[kChunkW<W>];
     if (valid) {
         rs = rp[row];
         d = rp[row + 1] - rs;
     }
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) {
+    for (int j = 0; j < kChunkW<W>; ++j) {
         const int k = lane + W * j;
         if (k < d) {
             jj[j] = ci[rs + k];
@@ -119,10 +122,10 @@ __global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__
     double4_32a ui = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     if (valid) ui = U[row];
     const double Vr = ui.z * ui.x, Vi = ui.z * ui.y;
-    for (int k0 = lane; k0 < d; k0 += W * kChunk) {
+    for (int k0 = lane; k0 < d; k0 += W * kChunkW<W>) {
         if (k0 != lane) {
 #pragma unroll
-            for (int j = 0; j < kChunk; ++j) {
+            for (int j = 0; j < kChunkW<W>; ++j) {
                 const int k = k0 + W * j;
                 if (k < d) {
                     jj[j] = ci[rs + k];
@@ -130,12 +133,12 @@ __global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__
                 }
             }
         }
-        double4_32a uu[kChunk];
+        double4_32a uu[kChunkW<W>];
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j)
+        for (int j = 0; j < kChunkW<W>; ++j)
             if (k0 + W * j < d) uu[j] = U[jj[j]];
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
+        for (int j = 0; j < kChunkW<W>; ++j) {
             const int k = k0 + W * j;
             if (k < d) {
                 const double YUr = fma(yy[j].x, uu[j].x, -yy[j].y * uu[j].y);

@@ -18,7 +18,10 @@
 
 namespace pf {
 
-constexpr int kChunkB = 4;
+// entries per lane prefetched together (measured: the batched kernels run
+// faster with 4 for every W, although that costs registers)
+template <int W>
+constexpr int kChunkBW = 4;
 
 // Per-row view of the scenario's outage: the base position of the outage
 // branch's entry in this row (-1 if the row is not an outage end) and the
@@ -70,14 +73,14 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
     const bool valid = row < (long long)S * nb;
     const int s = valid ? (int)(row / nb) : 0, i = valid ? (int)(row % nb) : 0;
     int rs = 0, d = 0;
-    int jj[kChunkB];
-    double2 yy[kChunkB];
+    int jj[kChunkBW<W>];
+    double2 yy[kChunkBW<W>];
     if (valid) {
         rs = rp[i];
         d = rp[i + 1] - rs;
     }
 #pragma unroll
-    for (int j = 0; j < kChunkB; ++j) {
+    for (int j = 0; j < kChunkBW<W>; ++j) {
         const int k = lane + W * j;
         if (k < d) {
             jj[j] = ci[rs + k];
@@ -89,10 +92,10 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
     pdl_wait();
     const double2 *Vs = V + (long long)s * nb;
     double Ir = 0.0, Ii = 0.0;
-    for (int k0 = lane; k0 < d; k0 += W * kChunkB) {
+    for (int k0 = lane; k0 < d; k0 += W * kChunkBW<W>) {
         if (k0 != lane) {
 #pragma unroll
-            for (int j = 0; j < kChunkB; ++j) {
+            for (int j = 0; j < kChunkBW<W>; ++j) {
                 const int k = k0 + W * j;
                 if (k < d) {
                     jj[j] = ci[rs + k];
@@ -100,12 +103,12 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
                 }
             }
         }
-        double2 vv[kChunkB];
+        double2 vv[kChunkBW<W>];
 #pragma unroll
-        for (int j = 0; j < kChunkB; ++j)
+        for (int j = 0; j < kChunkBW<W>; ++j)
             if (k0 + W * j < d) vv[j] = Vs[jj[j]];
 #pragma unroll
-        for (int j = 0; j < kChunkB; ++j) {
+        for (int j = 0; j < kChunkBW<W>; ++j) {
             double2 y = yy[j];
             if (k0 + W * j < d && scen_value(ro, i, k0 + W * j, jj[j], y)) {
                 Ir = fma(y.x, vv[j].x, Ir);
@@ -143,14 +146,14 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
     const bool valid = row < (long long)S * nb;
     const int s = valid ? (int)(row / nb) : 0, i = valid ? (int)(row % nb) : 0;
     int rs = 0, d = 0;
-    int jj[kChunkB];
-    double2 yy[kChunkB];
+    int jj[kChunkBW<W>];
+    double2 yy[kChunkBW<W>];
     if (valid) {
         rs = rp[i];
         d = rp[i + 1] - rs;
     }
 #pragma unroll
-    for (int j = 0; j < kChunkB; ++j) {
+    for (int j = 0; j < kChunkBW<W>; ++j) {
         const int k = lane + W * j;
         if (k < d) {
             jj[j] = ci[rs + k];
@@ -178,10 +181,10 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
     double4_32a ui = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     if (valid) ui = Us[i];
     const double Vr = ui.z * ui.x, Vi = ui.z * ui.y;
-    for (int k0 = lane; k0 < d; k0 += W * kChunkB) {
+    for (int k0 = lane; k0 < d; k0 += W * kChunkBW<W>) {
         if (k0 != lane) {
 #pragma unroll
-            for (int j = 0; j < kChunkB; ++j) {
+            for (int j = 0; j < kChunkBW<W>; ++j) {
                 const int k = k0 + W * j;
                 if (k < d) {
                     jj[j] = ci[rs + k];
@@ -189,12 +192,12 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
                 }
             }
         }
-        double4_32a uu[kChunkB];
+        double4_32a uu[kChunkBW<W>];
 #pragma unroll
-        for (int j = 0; j < kChunkB; ++j)
+        for (int j = 0; j < kChunkBW<W>; ++j)
             if (k0 + W * j < d) uu[j] = Us[jj[j]];
 #pragma unroll
-        for (int j = 0; j < kChunkB; ++j) {
+        for (int j = 0; j < kChunkBW<W>; ++j) {
             const int k = k0 + W * j;
             double2 y = yy[j];
             if (k < d && scen_value(ro, i, k, jj[j], y)) {
