@@ -15,6 +15,10 @@ Every function follows a passage of arXiv 2302.10736 (cited in oracle.c):
   loss / adjoint_state     L = sum w (S - S_spec)^2 and J^T r
   adjoint_params_cstep     dL/d(g, b, b_sh, tap) by complex step
   loss_central_diff        long-double central differences of L
+  reduced_index / jac_reduced / mismatch
+                           the Newton step's Jacobian without the slack and PV
+                           rows and columns, in CSC order, and its mismatch
+                           vector (selection and reordering of Eq. (2)'s entries)
 """
 import ctypes
 import os
@@ -245,3 +249,53 @@ def loss_central_diff(gr, vm, va, Ps, Qs, wP, wQ, kinds, idxs, step=1e-7):
     if rc != 0:
         raise MemoryError("or_loss_central_diff")
     return out[:len(kinds)]
+
+
+# ----------------------------------------------------- reduced Jacobian ----
+# Bus types as in MATPOWER: 1 PQ, 2 PV, 3 reference (slack), 4 isolated.
+# A Newton step on the power-flow equations solves for theta of the PV and PQ
+# buses and v of the PQ buses, from the P equations of the PV and PQ buses and
+# the Q equations of the PQ buses: the blocks of Eq. (2) restricted to those
+# rows and columns.  Ordering (this library's convention): theta / P part
+# first, then v / Q, each in ascending bus order.
+
+def reduced_index(bustype):
+    """(red, n_pvpq, n_pq): red[R] is the reduced index of full row/column R
+    of Eq. (2) (R < nb: theta_R / P_R, R >= nb: v_{R-nb} / Q_{R-nb}), or -1."""
+    bt = np.asarray(bustype)
+    nb = len(bt)
+    pvpq = [i for i in range(nb) if bt[i] in (1, 2)]
+    pq = [i for i in range(nb) if bt[i] == 1]
+    red = -np.ones(2 * nb, np.int64)
+    for k, i in enumerate(pvpq):
+        red[i] = k
+    for k, i in enumerate(pq):
+        red[nb + i] = len(pvpq) + k
+    return red, len(pvpq), len(pq)
+
+
+def jac_reduced(Y, J, bustype):
+    """The reduced Jacobian in CSC form (colptr [n+1], rowidx, values): every
+    structural entry of the full Jacobian (canonical CSR of jac_pattern,
+    values J) whose row and column are both kept, ordered by (column, row).
+    Structural zeros are kept."""
+    jrp, jci = jac_pattern(Y)
+    red, npvpq, npq = reduced_index(bustype)
+    n = npvpq + npq
+    rows = np.repeat(np.arange(2 * Y.nb), np.diff(jrp))
+    r, c = red[rows], red[np.asarray(jci, np.int64)]
+    keep = (r >= 0) & (c >= 0)
+    r, c, v = r[keep], c[keep], np.asarray(J)[keep]
+    order = np.lexsort((r, c))
+    colptr = np.zeros(n + 1, np.int64)
+    colptr[1:] = np.cumsum(np.bincount(c, minlength=n))
+    return colptr, r[order], v[order]
+
+
+def mismatch(P, Q, Pspec, Qspec, bustype):
+    """F = [P - Pspec on the PV and PQ buses; Q - Qspec on the PQ buses]."""
+    bt = np.asarray(bustype)
+    pvpq = (bt == 1) | (bt == 2)
+    pq = bt == 1
+    P, Q, Pspec, Qspec = (np.asarray(x, float) for x in (P, Q, Pspec, Qspec))
+    return np.concatenate([(P - Pspec)[pvpq], (Q - Qspec)[pq]])

@@ -11,7 +11,10 @@ Sources of truth, none of which re-types an oracle formula:
   - complex-step derivatives of the real-form injections (every J entry);
   - series-branch loss identity (P_hk + P_kh = r |I_s|^2, ...);
   - long-double central differences of the loss (adjoint);
-  - the paper's printed element count (16 values per line, Sec. V-A.2).
+  - the paper's printed element count (16 values per line, Sec. V-A.2);
+  - reduced Jacobian: the two-bus closed form, and Newton's method on it
+    converging quadratically to a known solution (a wrong, transposed or
+    misordered reduced Jacobian converges linearly at best).
 """
 import math
 import os
@@ -349,3 +352,133 @@ def test_paper_element_count():
     Y = oracle.ybus(gr)
     oracle.elementwise(gr, vm, va, Y, jac=False)
     assert oracle.elementwise.last_count == gv["synthetic_usa_jacobian_elements"]
+
+
+# ------------------------------------------------------ reduced Jacobian ----
+
+def pin_reduced_two_bus():
+    """Bus types of the two-bus line (slack/PQ, slack/PV, PV/slack): the
+    reduced Jacobian is the matching block of the hand-derived closed form,
+    rows (P2, Q2) x columns (th2, v2) for a PQ bus 2, and F = S - S_spec."""
+    gr = two_bus_lossless()
+    vm, va = np.array([1.0, 1.0]), np.array([0.0, -0.1])
+    s, c = math.sin(0.1), math.cos(0.1)
+    Y = oracle.ybus(gr)
+    P, Q, J = oracle.elementwise(gr, vm, va, Y)
+    errs = []
+    cases = [([3, 1], [0, 2, 4], [0, 1, 0, 1], [10 * c, -10 * s, -10 * s, 20 - 10 * c]),
+             ([3, 2], [0, 1], [0], [10 * c]),
+             ([2, 3], [0, 1], [0], [10 * c]),
+             ([3, 4], [0], [], [])]
+    for bt, cp, ri, vals in cases:
+        colptr, rowidx, v = oracle.jac_reduced(Y, J, bt)
+        if list(colptr) != cp or list(rowidx) != ri:
+            return math.inf
+        errs.append(np.max(np.abs(v - np.array(vals))) if vals else 0.0)
+    F = oracle.mismatch(P, Q, [0.5, -0.25], [0.125, 0.0625], [3, 1])
+    errs.append(np.max(np.abs(F - np.array([-10 * s + 0.25, 10 * (1 - c) - 0.0625]))))
+    return max(errs)
+
+
+def newton_errors(gr, bustype, vm_true, va_true, vm0, va0, iters=6, transpose=False):
+    """Max-norm mismatch of each Newton iterate, solving the reduced system
+    (dense solve of the CSC matrix) from (vm0, va0) towards the state whose
+    injections define S_spec."""
+    Y = oracle.ybus(gr)
+    Ps, Qs = oracle.inj_sparse(Y, vm_true, va_true)
+    red, npvpq, npq = oracle.reduced_index(bustype)
+    n = npvpq + npq
+    bt = np.asarray(bustype)
+    pvpq, pq = np.flatnonzero((bt == 1) | (bt == 2)), np.flatnonzero(bt == 1)
+    vm, va = vm0.copy(), va0.copy()
+    out = []
+    for _ in range(iters):
+        P, Q = oracle.inj_sparse(Y, vm, va)
+        F = oracle.mismatch(P, Q, Ps, Qs, bustype)
+        out.append(float(np.max(np.abs(F))))
+        colptr, rowidx, v = oracle.jac_reduced(Y, oracle.jac_ybus(Y, vm, va), bustype)
+        A = np.zeros((n, n))
+        for col in range(n):
+            for e in range(colptr[col], colptr[col + 1]):
+                A[rowidx[e], col] = v[e]
+        dx = np.linalg.solve(A.T if transpose else A, -F)
+        va[pvpq] += dx[:npvpq]
+        vm[pq] += dx[npvpq:]
+    return out
+
+
+def pin_newton_quadratic():
+    """A 30-bus meshed grid with phase shifters and a parallel pair, heavily
+    loaded (angle differences up to ~0.5 rad): from a start within 2e-3 of
+    the solution, Newton's mismatch falls quadratically to round-off."""
+    gr = random_grid(30, 45, 41, shift_max=0.2)
+    for k in ("f", "t", "g", "b", "bsh", "tap", "shift"):   # a parallel branch
+        gr[k] = np.concatenate([gr[k], gr[k][:1] * (1.0 if k in ("f", "t", "tap", "shift") else 0.6)]).astype(gr[k].dtype)
+    gr["nl"] += 1
+    bt = np.ones(30, np.int32)
+    bt[0], bt[[4, 9, 17]] = 3, 2
+    vm_t, va_t = random_state(30, 41)
+    va_t = va_t - va_t[0]
+    rng = np.random.default_rng(41)
+    vm0, va0 = vm_t.copy(), va_t.copy()
+    vm0[bt == 1] += rng.uniform(-2e-3, 2e-3, int((bt == 1).sum()))
+    va0[bt != 3] += rng.uniform(-2e-3, 2e-3, int((bt != 3).sum()))
+    e = newton_errors(gr, bt, vm_t, va_t, vm0, va0)
+    # quadratic: e_{k+1} <= C e_k^2 while above round-off, round-off reached by iteration 5
+    worst = 0.0
+    for a, b in zip(e, e[1:]):
+        if a > 1e-6:
+            worst = max(worst, b / (a * a))
+    return max(e[4] * 1e12, worst / 1e3)
+
+
+def test_reduced_two_bus_closed_form():
+    assert pin_reduced_two_bus() < 1e-14
+
+
+def test_newton_converges_quadratically():
+    assert pin_newton_quadratic() < 1.0
+
+
+def test_newton_pin_rejects_a_transposed_jacobian():
+    """The pin has teeth: the same Newton run with the transpose of the
+    (non-symmetric) reduced Jacobian does not reach round-off."""
+    gr = random_grid(30, 45, 41, shift_max=0.2)
+    bt = np.ones(30, np.int32)
+    bt[0], bt[[4, 9, 17]] = 3, 2
+    vm_t, va_t = random_state(30, 41)
+    va_t = va_t - va_t[0]
+    rng = np.random.default_rng(41)
+    vm0, va0 = vm_t.copy(), va_t.copy()
+    vm0[bt == 1] += rng.uniform(-2e-3, 2e-3, int((bt == 1).sum()))
+    va0[bt != 3] += rng.uniform(-2e-3, 2e-3, int((bt != 3).sum()))
+    good = newton_errors(gr, bt, vm_t, va_t, vm0, va0)
+    bad = newton_errors(gr, bt, vm_t, va_t, vm0, va0, transpose=True)
+    assert good[4] < 1e-12 and not bad[4] < 1e-9
+
+
+def test_reduced_pattern_is_a_csc_of_the_kept_entries():
+    gr = random_grid(200, 280, 42)
+    vm, va = random_state(200, 42)
+    Y = oracle.ybus(gr)
+    J = oracle.jac_ybus(Y, vm, va)
+    bt = np.ones(200, np.int32)
+    bt[0], bt[7], bt[11::9] = 3, 4, 2
+    colptr, rowidx, v = oracle.jac_reduced(Y, J, bt)
+    red, npvpq, npq = oracle.reduced_index(bt)
+    n = npvpq + npq
+    assert colptr[0] == 0 and colptr[-1] == len(rowidx) and len(colptr) == n + 1
+    for col in range(n):
+        seg = rowidx[colptr[col]:colptr[col + 1]]
+        assert np.all(np.diff(seg) > 0) and np.all((seg >= 0) & (seg < n))
+    # dense comparison: the reduced matrix is the full one with rows/columns deleted
+    jrp, jci = oracle.jac_pattern(Y)
+    full = np.zeros((400, 400))
+    for r in range(400):
+        full[r, jci[jrp[r]:jrp[r + 1]]] = J[jrp[r]:jrp[r + 1]]
+    keep = np.flatnonzero(red >= 0)
+    keep = keep[np.argsort(red[keep])]
+    A = np.zeros((n, n))
+    for col in range(n):
+        A[rowidx[colptr[col]:colptr[col + 1]], col] = v[colptr[col]:colptr[col + 1]]
+    assert np.array_equal(A, full[np.ix_(keep, keep)])
