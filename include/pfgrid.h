@@ -352,6 +352,43 @@ pf_status adjoint_elementwise(pf_batch *batch, const double *vm, const double *v
  */
 pf_status grid_inject_barrier_fault(pf_grid *grid, pf_stream stream);
 
+/* --------------------------------------------- reduced Newton Jacobian -- */
+
+/*
+ * Bus types for the Newton step (codes as in MATPOWER): 1 PQ, 2 PV,
+ * 3 reference (slack), 4 isolated.  The reduced system keeps, of Eq. 2's
+ * blocks, the P rows and theta columns of the PV and PQ buses and the Q rows
+ * and v columns of the PQ buses.  Ordering: theta / P part first
+ * (n_pvpq entries), then v / Q (n_pq entries), each in ascending bus order;
+ * n = n_pvpq + n_pq.  The reduced Jacobian is stored column-major (CSC:
+ * colptr [n + 1], rowidx [nnz], rows ascending within a column, structural
+ * zeros kept), the layout sparse direct solvers such as KLU take.
+ * `bus_type` is a host array [nb]; the pattern and its gather map are built
+ * on the host and uploaded (synchronizes `stream`).  PF_EINVAL for another
+ * code.  May be called again to change the types.
+ */
+pf_status grid_set_bus_types(pf_grid *grid, const int32_t *bus_type, pf_stream stream);
+
+/* Sizes of the reduced system (PF_EINVAL before grid_set_bus_types). */
+pf_status jac_reduced_info(const pf_grid *grid, int32_t *n, int32_t *n_pvpq, int64_t *nnz);
+
+/* Device pointers to the reduced CSC pattern, owned by the grid. */
+pf_status jac_reduced_pattern(const pf_grid *grid, const int32_t **colptr, const int32_t **rowidx);
+
+/*
+ * One Newton evaluation: the full injections and Jacobian by the Ybus
+ * (method 0) or element-wise (method 1) method into grid-owned scratch, then
+ * one gather launch forms the mismatch vector
+ *   F = [P - Pspec on the PV and PQ buses ; Q - Qspec on the PQ buses]  [n]
+ * and the reduced Jacobian values Jr [nnz] in the CSC order above.
+ * vm, va, Pspec, Qspec [nb], F, Jr: device pointers owned by the caller.
+ * Asynchronous; the grid's scratch makes calls on one grid serial.
+ * (The paper computes the full Jacobian; the reduction is the step its
+ * solver interface implies.)
+ */
+pf_status jac_reduced(pf_grid *grid, int32_t method, const double *vm, const double *va, const double *Pspec,
+                      const double *Qspec, double *F, double *Jr, pf_stream stream);
+
 /* ------------------------------------------------------------ tracing -- */
 
 /* Kernel identifiers reported by the tracer. */
@@ -365,7 +402,8 @@ pf_status grid_inject_barrier_fault(pf_grid *grid, pf_stream stream);
 #define PF_K_ADJOINT 7
 #define PF_K_INJ_YBUS_BATCHED 8
 #define PF_K_JAC_YBUS_BATCHED 9
-#define PF_K_COUNT 10
+#define PF_K_REDUCE 10       /* gather of the reduced Jacobian and mismatch vector */
+#define PF_K_COUNT 11
 
 typedef struct {
     int32_t kernel;          /* PF_K_* */

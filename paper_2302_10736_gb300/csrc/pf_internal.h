@@ -174,6 +174,13 @@ struct Grid {
     int *err = nullptr;            // device error word
     // eval_host staging (lazy)
     double *st_vm = nullptr, *st_va = nullptr, *st_P = nullptr, *st_Q = nullptr, *st_J = nullptr;
+    // reduced Newton Jacobian (grid_set_bus_types): CSC pattern, the canonical J
+    // position of every reduced entry, the bus of every mismatch entry, and
+    // scratch for the full evaluation it is gathered from
+    int red_set = 0, red_n = 0, red_npvpq = 0;
+    long long red_nnz = 0;
+    int *red_colptr = nullptr, *red_rowidx = nullptr, *red_jmap = nullptr, *red_fmap = nullptr;
+    double *red_P = nullptr, *red_Q = nullptr, *red_J = nullptr;
     // tracer: events [2 * capacity], kernel id per record
     std::vector<cudaEvent_t> tr_ev;
     std::vector<int> tr_kernel;

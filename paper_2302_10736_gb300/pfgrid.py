@@ -75,6 +75,10 @@ def _load():
         "phasor": (st, [i32, vp, vp, vp, vp, vp]),
         "grid_inject_barrier_fault": (st, [vp, vp]),
         "inj_ybus_noalloc": (st, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "grid_set_bus_types": (st, [vp, vp, vp]),
+        "jac_reduced_info": (st, [vp, pi32, pi32, ctypes.POINTER(ctypes.c_int64)]),
+        "jac_reduced_pattern": (st, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "jac_reduced": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -350,6 +354,45 @@ def grid_trace_read(grid, cap=1 << 16):
     n = ctypes.c_int32()
     _check(_lib.grid_trace_read(grid.handle, buf, cap, ctypes.byref(n)), "grid_trace_read")
     return [(kernel_name(buf[i].kernel), float(buf[i].ms)) for i in range(n.value)]
+
+
+# --------------------------------------------------- reduced Jacobian --
+
+def grid_set_bus_types(grid, bus_type, stream=None):
+    """Bus types (1 PQ, 2 PV, 3 reference, 4 isolated) for jac_reduced."""
+    bt = np.ascontiguousarray(bus_type, dtype=np.int32)
+    if bt.size != grid.nb:
+        raise ValueError("bus_type must have nb = %d entries" % grid.nb)
+    _check(_lib.grid_set_bus_types(grid.handle, bt.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "grid_set_bus_types")
+
+
+def jac_reduced_info(grid):
+    """(n, n_pvpq, nnz) of the reduced system."""
+    n, npvpq, nnz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.jac_reduced_info(grid.handle, ctypes.byref(n), ctypes.byref(npvpq), ctypes.byref(nnz)),
+           "jac_reduced_info")
+    return n.value, npvpq.value, nnz.value
+
+
+def jac_reduced_pattern(grid):
+    """Host copies (colptr [n+1], rowidx [nnz]) of the reduced CSC pattern."""
+    n, _, nnz = jac_reduced_info(grid)
+    cp, ri = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(_lib.jac_reduced_pattern(grid.handle, ctypes.byref(cp), ctypes.byref(ri)), "jac_reduced_pattern")
+    import torch
+    return (_device_copy(cp.value, n + 1, torch.int32).cpu().numpy(),
+            _device_copy(ri.value, nnz, torch.int32).cpu().numpy())
+
+
+def jac_reduced(grid, method, vm, va, Pspec, Qspec, F, Jr, stream=None):
+    """Mismatch F [n] and reduced Jacobian values Jr [nnz] (CSC order)."""
+    n, _, nnz = jac_reduced_info(grid)
+    nb = grid.nb
+    m = {"ybus": 0, "elementwise": 1}.get(method, method)
+    _check(_lib.jac_reduced(grid.handle, int(m), _dptr(vm, "vm", nb), _dptr(va, "va", nb),
+                            _dptr(Pspec, "Pspec", nb), _dptr(Qspec, "Qspec", nb), _dptr(F, "F", n),
+                            _dptr(Jr, "Jr", nnz), _stream(stream)), "jac_reduced")
 
 
 # ------------------------------------------------------------------ batches --
