@@ -53,7 +53,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
-    ap.add_argument("--profile-workload", choices=["n1", "adjoint4", "batched5", "permuted"],
+    ap.add_argument("--profile-workload", choices=["n1", "adjoint4", "batched5", "permuted", "reduced"],
                     help="run only this batched/adjoint workload (few launches, for profilers) and exit")
     return ap.parse_args(argv)
 
@@ -204,7 +204,7 @@ def timed_replays(torch, g, reps, name="replays"):
 def extra_workloads(torch, pfgrid, synth, reps, only=None):
     """The batched and adjoint workloads, each timed from a CUDA-graph replay
     (inputs larger than L2 for the batched ones, so no flush is needed).
-    `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted"."""
+    `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced"."""
     out = {}
     if only in (None, "n1"):
         out.update(_n1_workload(torch, pfgrid, synth, reps))
@@ -213,7 +213,48 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
             out[key] = _adjoint_workload(torch, pfgrid, synth, reps, k)
     if only in (None, "permuted"):
         out["c2_random_bus_order"] = _permuted_workload(torch, pfgrid, synth, max(reps, 20))
+    if only in (None, "reduced"):
+        out["reduced_newton_csc_70k"] = _reduced_workload(torch, pfgrid, synth, max(reps, 20))
     return out
+
+
+def _reduced_workload(torch, pfgrid, synth, steps):
+    """The Newton step's inputs on the 70k-bus grid (15 % PV buses): mismatch
+    vector and reduced Jacobian in CSC order, by both methods, L2 flushed
+    between steps; the gather launch timed by the tracer."""
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    w = synth.workload(WORKLOAD)
+    grid = pfgrid.ybus_build(w)
+    vm, va = dev(w["vm"][0]), dev(w["va"][0])
+    pfgrid.grid_autotune(grid, vm, va, reps=10)
+    pfgrid.grid_set_bus_types(grid, w["bustype"])
+    n, npvpq, nnz = pfgrid.jac_reduced_info(grid)
+    Ps = torch.zeros(w["nb"], dtype=torch.float64, device="cuda")
+    Qs = torch.zeros_like(Ps)
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    Jr = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    res = {"n": n, "nnz": nnz}
+    for name, m in (("elementwise", 1), ("ybus", 0)):
+        f = lambda: pfgrid.jac_reduced(grid, m, vm, va, Ps, Qs, F, Jr)
+        for _ in range(3):
+            f()
+        t = time_loop(torch, f, steps, flush, "reduced_" + name)
+        res["%s_evals_per_s" % name] = 1e3 / (sum(t) / len(t))
+    pfgrid.grid_trace_enable(grid, 4 * steps + 16)
+    time_loop(torch, lambda: pfgrid.jac_reduced(grid, 1, vm, va, Ps, Qs, F, Jr), steps, flush, "reduced_traced")
+    tr = pfgrid.grid_trace_read(grid)
+    pfgrid.grid_trace_enable(grid, 0)
+    ms = [x for k, x in tr if k == "reduce"]
+    if ms:
+        mean = sum(ms) / len(ms)
+        byt = 20 * nnz + 28 * n   # map, full value and reduced value per entry; map, P or Q, spec, F per row
+        hbm, kind = hbm_peak()
+        res["gather"] = {"us_per_launch": 1e3 * mean, "algorithmic_bytes": byt,
+                         "gbs": byt / (mean * 1e-3) / 1e9, "frac_of_hbm": byt / (mean * 1e-3) / 1e9 / hbm,
+                         "hbm_peak_source": kind}
+    pfgrid.grid_check_error(grid)
+    return res
 
 
 def _permuted_workload(torch, pfgrid, synth, steps):
