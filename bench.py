@@ -53,7 +53,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
-    ap.add_argument("--profile-workload", choices=["n1", "adjoint4", "batched5", "permuted", "reduced"],
+    ap.add_argument("--profile-workload", choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra"],
                     help="run only this batched/adjoint workload (few launches, for profilers) and exit")
     return ap.parse_args(argv)
 
@@ -204,7 +204,7 @@ def timed_replays(torch, g, reps, name="replays"):
 def extra_workloads(torch, pfgrid, synth, reps, only=None):
     """The batched and adjoint workloads, each timed from a CUDA-graph replay
     (inputs larger than L2 for the batched ones, so no flush is needed).
-    `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced"."""
+    `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced", "ultra"."""
     out = {}
     if only in (None, "n1"):
         out.update(_n1_workload(torch, pfgrid, synth, reps))
@@ -215,7 +215,34 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
         out["c2_random_bus_order"] = _permuted_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "reduced"):
         out["reduced_newton_csc_70k"] = _reduced_workload(torch, pfgrid, synth, max(reps, 20))
+    if only in (None, "ultra"):
+        out["single_410k"] = _single_workload(torch, pfgrid, synth, 6, max(reps, 20))
     return out
+
+
+def _single_workload(torch, pfgrid, synth, k, steps):
+    """Single evaluations of workload k by both methods, L2 flushed between steps."""
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    w = synth.workload(k)
+    grid = pfgrid.ybus_build(w)
+    vm, va = dev(w["vm"][0]), dev(w["va"][0])
+    pfgrid.grid_autotune(grid, vm, va, reps=10)
+    P = torch.empty(w["nb"], dtype=torch.float64, device="cuda")
+    Q = torch.empty_like(P)
+    J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+    res = {"nb": w["nb"], "nl": w["nl"], "launch_config": pfgrid.grid_get_config(grid)}
+    for name, fn in (("elementwise", pfgrid.jac_elementwise), ("ybus", pfgrid.jac_ybus)):
+        f = lambda: fn(grid, vm, va, P, Q, J)
+        for _ in range(3):
+            f()
+        t = time_loop(torch, f, steps, flush, "single%d_%s" % (k, name))
+        res["%s_evals_per_s" % name] = 1e3 / (sum(t) / len(t))
+    T, nb = 2 * w["nl"], w["nb"]
+    ms = 1e3 / res["elementwise_evals_per_s"]
+    res["elementwise_fp64_frac"] = (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb) / (ms * 1e-3) / 1e9 / FP64_OPS_PEAK_G
+    pfgrid.grid_check_error(grid)
+    return res
 
 
 def _reduced_workload(torch, pfgrid, synth, steps):

@@ -12,6 +12,8 @@ Workloads (seed = 20230221 + workload number; sub-streams per quantity):
   4  25,000 buses /  33,000 branches, one state + a second state for the
      loss targets, weights ~U[0.5,2]
   5  250,000 buses / 330,000 branches, 16 states + loss data as in 4
+  6  410,000 buses / 541,000 branches, one state (the size of the paper's
+     largest replicated grid)
 """
 import ctypes
 import os
@@ -28,6 +30,7 @@ WORKLOADS = {
     3: dict(nb=10000, nl=13500, pv=0.20, nscen=1024, vlo=0.93, vhi=1.07, sigma=0.25, outages=True),
     4: dict(nb=25000, nl=33000, pv=0.20, nscen=1, loss=True),
     5: dict(nb=250000, nl=330000, pv=0.20, nscen=16, loss=True),
+    6: dict(nb=410000, nl=541000, pv=0.20, nscen=1),
 }
 BASE_SEED = 20230221
 

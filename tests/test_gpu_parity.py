@@ -98,7 +98,7 @@ def test_hand_and_small_grids(pf, case):
     check_against_oracle(pf, gr, vm, va)
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 6])
 def test_workloads_full_size(pf, k):
     from paper_2302_10736_gb300 import synth
     w = synth.workload(k)
