@@ -19,6 +19,8 @@ Every function follows a passage of arXiv 2302.10736 (cited in oracle.c):
                            the Newton step's Jacobian without the slack and PV
                            rows and columns, in CSC order, and its mismatch
                            vector (selection and reordering of Eq. (2)'s entries)
+  newton                   Newton-Raphson on the reduced system (the textbook
+                           iteration; a sparse LU is its linear-solve step)
 """
 import ctypes
 import os
@@ -299,3 +301,32 @@ def mismatch(P, Q, Pspec, Qspec, bustype):
     pq = bt == 1
     P, Q, Pspec, Qspec = (np.asarray(x, float) for x in (P, Q, Pspec, Qspec))
     return np.concatenate([(P - Pspec)[pvpq], (Q - Qspec)[pq]])
+
+
+def newton(gr, bustype, vm, va, Pspec, Qspec, tol=1e-10, max_iter=20):
+    """Newton-Raphson power flow: x <- x + dx with J_r(x) dx = -F(x), x = (theta
+    of PV and PQ buses, v of PQ buses), until max |F| <= tol.  Returns
+    (vm, va, iterations, max |F| per iterate, converged)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    Y = ybus(gr)
+    bt = np.asarray(bustype)
+    red, npvpq, npq = reduced_index(bt)
+    n = npvpq + npq
+    pvpq = np.flatnonzero((bt == 1) | (bt == 2))
+    pq = np.flatnonzero(bt == 1)
+    vm, va = np.array(vm, float), np.array(va, float)
+    norms = []
+    for it in range(max_iter + 1):
+        P, Q = inj_sparse(Y, vm, va)
+        F = mismatch(P, Q, Pspec, Qspec, bt)
+        norms.append(float(np.max(np.abs(F))) if n else 0.0)
+        if norms[-1] <= tol:
+            return vm, va, it, norms, True
+        if it == max_iter:
+            break
+        colptr, rowidx, vals = jac_reduced(Y, jac_ybus(Y, vm, va), bt)
+        dx = spla.splu(sp.csc_matrix((vals, rowidx, colptr), shape=(n, n))).solve(-F)
+        va[pvpq] += dx[:npvpq]
+        vm[pq] += dx[npvpq:]
+    return vm, va, max_iter, norms, False

@@ -482,3 +482,24 @@ def test_reduced_pattern_is_a_csc_of_the_kept_entries():
     for col in range(n):
         A[rowidx[colptr[col]:colptr[col + 1]], col] = v[colptr[col]:colptr[col + 1]]
     assert np.array_equal(A, full[np.ix_(keep, keep)])
+
+
+def test_newton_oracle_finds_the_known_solution():
+    """From a start within 1e-3, the oracle's Newton iteration reaches the
+    state whose injections define the specification (the solution is unique
+    nearby), and its final mismatch is at round-off."""
+    pytest.importorskip("scipy")
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    bt = w["bustype"]
+    vm_t, va_t = w["vm"][0].copy(), 0.1 * w["va"][0]
+    Ps, Qs = oracle.inj_sparse(oracle.ybus(w), vm_t, va_t)
+    rng = np.random.default_rng(54)
+    vm0, va0 = vm_t.copy(), va_t.copy()
+    pq, pvpq = bt == 1, (bt == 1) | (bt == 2)
+    vm0[pq] += rng.uniform(-1e-3, 1e-3, int(pq.sum()))
+    va0[pvpq] += rng.uniform(-1e-3, 1e-3, int(pvpq.sum()))
+    vm, va, it, norms, ok = oracle.newton(w, bt, vm0, va0, Ps, Qs, tol=1e-11)
+    assert ok and it <= 6, norms
+    assert np.max(np.abs(vm - vm_t)) < 1e-10 and np.max(np.abs(va - va_t)) < 1e-10
+    assert np.array_equal(vm[~pq], vm_t[~pq]) and va[0] == va_t[0]   # fixed quantities untouched
