@@ -60,6 +60,7 @@ typedef int32_t pf_status;
 #define PF_EDEVICE 5         /* a kernel reported an error through the grid's device error word */
 #define PF_ETIMEOUT 6        /* a bounded device-side wait gave up */
 #define PF_EUNSUPPORTED 7    /* size beyond the int32 index range of this library */
+#define PF_ENOCONV 8         /* Newton iteration did not converge, or its Jacobian was singular */
 
 typedef void *pf_stream;            /* cudaStream_t */
 typedef struct pf_grid pf_grid;     /* opaque; owns all device structure of one network */
@@ -388,6 +389,26 @@ pf_status jac_reduced_pattern(const pf_grid *grid, const int32_t **colptr, const
  */
 pf_status jac_reduced(pf_grid *grid, int32_t method, const double *vm, const double *va, const double *Pspec,
                       const double *Qspec, double *F, double *Jr, pf_stream stream);
+
+/*
+ * Newton-Raphson power flow on the GPU (not in the paper, which stops at the
+ * Jacobian a Newton step needs): starting from vm, va [nb] (device, updated
+ * in place), repeat
+ *   full evaluation by `method` (0 Ybus, 1 element-wise) -> F and J_r
+ *   (the reduced system of jac_reduced, J_r row-major) -> stop when
+ *   max |F| <= tol -> solve J_r dx = F (cuSOLVER sparse QR, on the device)
+ *   -> theta_pvpq -= dx[0 .. n_pvpq), v_pq -= dx[n_pvpq .. n)
+ * at most max_iter steps.  Requires grid_set_bus_types; PV and reference
+ * magnitudes and reference angles stay as given.  *iterations and *mismatch
+ * (host, may be NULL) receive the steps taken and the final max |F|.
+ * PF_ENOCONV if max |F| > tol after max_iter steps or J_r is singular (vm,
+ * va then hold the last iterate).  Synchronizes `stream` once per
+ * iteration (the convergence test).  Allocates its workspace on the first
+ * call after grid_set_bus_types.
+ */
+pf_status powerflow_newton(pf_grid *grid, int32_t method, double *vm, double *va, const double *Pspec,
+                           const double *Qspec, double tol, int32_t max_iter, int32_t *iterations, double *mismatch,
+                           pf_stream stream);
 
 /* ------------------------------------------------------------ tracing -- */
 

@@ -81,7 +81,7 @@ def build_pfgrid(force=False, verbose=False, extra_flags=()):
         lib64 = os.path.join(_cuda_home(), "lib64")
         tmp = LIB_PFGRID + ".tmp"
         _run([nvcc, "-shared", "-o", tmp] + objs + ARCH +
-             ["-cudart", "shared", "-Xlinker", "-rpath," + lib64])
+             ["-cudart", "shared", "-lcusolver", "-lcusparse", "-Xlinker", "-rpath," + lib64])
         os.replace(tmp, LIB_PFGRID)
         return LIB_PFGRID
 

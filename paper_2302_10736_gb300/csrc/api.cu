@@ -237,6 +237,7 @@ PF_API const char *pf_status_str(pf_status s)
     case PF_EDEVICE: return "PF_EDEVICE";
     case PF_ETIMEOUT: return "PF_ETIMEOUT";
     case PF_EUNSUPPORTED: return "PF_EUNSUPPORTED";
+    case PF_ENOCONV: return "PF_ENOCONV";
     default: return "PF_UNKNOWN";
     }
 }
@@ -305,6 +306,7 @@ PF_API void grid_destroy(pf_grid *grid)
 {
     if (!grid) return;
     trace_free(&grid->g);
+    newton_free(&grid->g);
     grid->g.arena.free_all();
     delete grid;
 }

@@ -1,0 +1,139 @@
+// newton.cu - Newton-Raphson power flow around the evaluation kernels.
+//
+// The paper computes the injections and the Jacobian that a Newton step
+// needs and hands the Jacobian to a sparse direct solver; this file closes the
+// loop on the GPU.  Iteration k: the full evaluation (Ybus or element-wise
+// method) into the grid's scratch, the gather of the mismatch F and of the
+// reduced Jacobian J_r in row-major order (reduced.cu), max |F| to the host
+// (the only host round trip besides the solver's), then J_r dx = F by
+// cuSOLVER's sparse QR on the device and x <- x - dx, with x the angles of
+// the PV and PQ buses and the magnitudes of the PQ buses.
+#include <cusolverSp.h>
+#include <cusparse.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "pf_internal.h"
+
+namespace pf {
+
+namespace {
+
+// max |F| as the bit pattern of a non-negative double (ordered like the value;
+// NaN compares above every finite value, so it never passes a tolerance)
+__global__ void __launch_bounds__(256) k_absmax(int n, const double *__restrict__ F, unsigned long long *out)
+{
+    unsigned long long m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(F[i])));
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// x <- x - dx: unknown k < npvpq is the angle of bus fmap[k], the rest the
+// magnitude of bus fmap[k]
+__global__ void __launch_bounds__(256) k_newton_update(int n, int npvpq, const int *__restrict__ fmap,
+                                                       const double *__restrict__ dx, double *vm, double *va)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int b = fmap[k];
+        if (k < npvpq)
+            va[b] -= dx[k];
+        else
+            vm[b] -= dx[k];
+    }
+}
+
+pf_status solver_error(cusolverStatus_t st, const char *what)
+{
+    return set_error(PF_ECUDA, "%s: cuSOLVER status %d", what, (int)st);
+}
+
+}  // namespace
+
+void newton_free(Grid *g)
+{
+    if (g->nt_solver) cusolverSpDestroy((cusolverSpHandle_t)g->nt_solver);
+    if (g->nt_descr) cusparseDestroyMatDescr((cusparseMatDescr_t)g->nt_descr);
+    g->nt_solver = g->nt_descr = nullptr;
+}
+
+}  // namespace pf
+
+using namespace pf;
+
+PF_API pf_status powerflow_newton(pf_grid *grid, int32_t method, double *vm, double *va, const double *Pspec,
+                                  const double *Qspec, double tol, int32_t max_iter, int32_t *iterations,
+                                  double *mismatch, pf_stream stream)
+{
+    if (!grid) return set_error(PF_EINVAL, "powerflow_newton: grid is NULL");
+    Grid *g = &grid->g;
+    if (!g->red_set) return set_error(PF_EINVAL, "powerflow_newton: call grid_set_bus_types first");
+    if (method != 0 && method != 1)
+        return set_error(PF_EINVAL, "powerflow_newton: method must be 0 (Ybus) or 1 (element-wise)");
+    if (!(tol >= 0.0) || max_iter < 0) return set_error(PF_EINVAL, "powerflow_newton: tol < 0 or max_iter < 0");
+    if (iterations) *iterations = 0;
+    if (mismatch) *mismatch = 0.0;
+    const int n = g->red_n, nnz = (int)g->red_nnz;
+    if (g->nb == 0 || n == 0) return PF_OK;
+    if (!vm || !va || !Pspec || !Qspec) return set_error(PF_EINVAL, "powerflow_newton: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!g->nt_solver) {
+        cusolverSpHandle_t h;
+        cusparseMatDescr_t d;
+        cusolverStatus_t cs = cusolverSpCreate(&h);
+        if (cs != CUSOLVER_STATUS_SUCCESS) return solver_error(cs, "cusolverSpCreate");
+        g->nt_solver = h;
+        if (cusparseCreateMatDescr(&d) != CUSPARSE_STATUS_SUCCESS)
+            return set_error(PF_ECUDA, "powerflow_newton: cusparseCreateMatDescr failed");
+        cusparseSetMatType(d, CUSPARSE_MATRIX_TYPE_GENERAL);
+        cusparseSetMatIndexBase(d, CUSPARSE_INDEX_BASE_ZERO);
+        g->nt_descr = d;
+    }
+    if (!g->nt_F) {
+        PF_CUDA(g->arena.alloc(&g->nt_F, (size_t)n));
+        PF_CUDA(g->arena.alloc(&g->nt_J, (size_t)std::max(nnz, 1)));
+        PF_CUDA(g->arena.alloc(&g->nt_dx, (size_t)n));
+    }
+    if (!g->nt_max) PF_CUDA(g->arena.alloc(&g->nt_max, 1));
+    cusolverSpHandle_t h = (cusolverSpHandle_t)g->nt_solver;
+    cusolverStatus_t cs = cusolverSpSetStream(h, s);
+    if (cs != CUSOLVER_STATUS_SUCCESS) return solver_error(cs, "cusolverSpSetStream");
+    int dev = 0, nsm = 0;
+    PF_CUDA(cudaGetDevice(&dev));
+    PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = std::max(1, std::min((n + 255) / 256, 4 * nsm));
+    for (int it = 0;; ++it) {
+        pf_status st = method == 0 ? jac_ybus(grid, vm, va, g->red_P, g->red_Q, g->red_J, stream)
+                                   : jac_elementwise(grid, vm, va, g->red_P, g->red_Q, g->red_J, stream);
+        if (st) return st;
+        {
+            TraceScope t(g, PF_K_REDUCE, s);
+            PF_CUDA(launch_reduce(g, g->red_jmap_csr, Pspec, Qspec, g->nt_F, g->nt_J, s));
+        }
+        PF_CUDA(cudaMemsetAsync(g->nt_max, 0, sizeof(unsigned long long), s));
+        k_absmax<<<blocks, 256, 0, s>>>(n, g->nt_F, g->nt_max);
+        PF_CUDA(cudaGetLastError());
+        unsigned long long bits = 0;
+        PF_CUDA(cudaMemcpyAsync(&bits, g->nt_max, sizeof(bits), cudaMemcpyDeviceToHost, s));
+        PF_CUDA(cudaStreamSynchronize(s));
+        double fmax;
+        std::memcpy(&fmax, &bits, sizeof(fmax));
+        if (iterations) *iterations = it;
+        if (mismatch) *mismatch = fmax;
+        if (fmax <= tol) return PF_OK;
+        if (it == max_iter)
+            return set_error(PF_ENOCONV, "powerflow_newton: max |F| = %g after %d iterations (tol %g)", fmax, it,
+                             tol);
+        int singular = -1;
+        cs = cusolverSpDcsrlsvqr(h, n, nnz, (cusparseMatDescr_t)g->nt_descr, g->nt_J, g->red_rowptr, g->red_colidx,
+                                 g->nt_F, 1e-14, 1, g->nt_dx, &singular);
+        if (cs != CUSOLVER_STATUS_SUCCESS) return solver_error(cs, "cusolverSpDcsrlsvqr");
+        if (singular >= 0)
+            return set_error(PF_ENOCONV, "powerflow_newton: reduced Jacobian singular (pivot %d) at iteration %d",
+                             singular, it);
+        k_newton_update<<<blocks, 256, 0, s>>>(n, g->red_npvpq, g->red_fmap, g->nt_dx, vm, va);
+        PF_CUDA(cudaGetLastError());
+    }
+}

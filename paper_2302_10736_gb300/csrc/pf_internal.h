@@ -180,7 +180,13 @@ struct Grid {
     int red_set = 0, red_n = 0, red_npvpq = 0;
     long long red_nnz = 0;
     int *red_colptr = nullptr, *red_rowidx = nullptr, *red_jmap = nullptr, *red_fmap = nullptr;
+    int *red_rowptr = nullptr, *red_colidx = nullptr, *red_jmap_csr = nullptr;   // the same matrix row-major
     double *red_P = nullptr, *red_Q = nullptr, *red_J = nullptr;
+    // Newton-Raphson workspace (powerflow_newton): F, J_r (CSR), step, max |F|;
+    // sparse-solver handles (cusolverSpHandle_t, cusparseMatDescr_t)
+    double *nt_F = nullptr, *nt_J = nullptr, *nt_dx = nullptr;
+    unsigned long long *nt_max = nullptr;
+    void *nt_solver = nullptr, *nt_descr = nullptr;
     // tracer: events [2 * capacity], kernel id per record
     std::vector<cudaEvent_t> tr_ev;
     std::vector<int> tr_kernel;
@@ -240,6 +246,11 @@ cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm);   // CTAs of k_e
 cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
                           cudaStream_t s, bool host_out = false);   // host_out: P, Q, J in mapped host memory
+
+// reduced Newton system (reduced.cu, newton.cu)
+cudaError_t launch_reduce(Grid *g, const int *map, const double *Pspec, const double *Qspec, double *F, double *Jr,
+                          cudaStream_t s);
+void newton_free(Grid *g);
 
 // ----------------------------------------------------------- batches ----
 // S scenarios over one grid: per-scenario voltage states and an optional N-1

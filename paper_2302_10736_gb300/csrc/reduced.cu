@@ -24,6 +24,7 @@ namespace {
 struct HostReduced {
     int n = 0, npvpq = 0, npq = 0;
     std::vector<int> colptr, rowidx, jmap, fmap;
+    std::vector<int> rowptr, colidx, jmap_csr;   // row-major copy (the Newton solver's input)
 };
 
 // Reduced index of full row/column R (R < nb: theta_R / P_R; R >= nb:
@@ -67,6 +68,23 @@ pf_status host_reduced(const HostTopo &H, const int *bt, HostReduced &R)
             R.jmap[fill[c]++] = p;
         }
     }
+    // row-major: canonical rows ascending; within a row the theta block then
+    // the v block, each ascending, so the reduced columns come out ascending
+    R.rowptr.assign(R.n + 1, 0);
+    R.colidx.clear();
+    R.jmap_csr.clear();
+    R.colidx.reserve(nnz);
+    R.jmap_csr.reserve(nnz);
+    for (int Rw = 0; Rw < 2 * nb; ++Rw) {
+        if (red[Rw] < 0) continue;
+        for (int p = H.jrp[Rw]; p < H.jrp[Rw + 1]; ++p) {
+            const int c = red[H.jci[p]];
+            if (c < 0) continue;
+            R.colidx.push_back(c);
+            R.jmap_csr.push_back(p);
+        }
+        R.rowptr[red[Rw] + 1] = (int)R.colidx.size();
+    }
     return PF_OK;
 }
 
@@ -104,6 +122,22 @@ __global__ void __launch_bounds__(256) k_reduce(int n, int npvpq, int nnz, const
 
 }  // namespace
 
+// The gather after a full evaluation into the grid's scratch: F, and the
+// reduced values in the order of `map` (column- or row-major).
+cudaError_t launch_reduce(Grid *g, const int *map, const double *Pspec, const double *Qspec, double *F, double *Jr,
+                          cudaStream_t s)
+{
+    const long long total = (long long)g->red_n + g->red_nnz;
+    int dev = 0, nsm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
+        return e;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8LL * nsm));
+    return launch_k(k_reduce, blocks, 256, 0, s, true, g->red_n, g->red_npvpq, (int)g->red_nnz,
+                    (const int *)g->red_fmap, map, (const double *)g->red_P, (const double *)g->red_Q, Pspec, Qspec,
+                    (const double *)g->red_J, F, Jr);
+}
+
 }  // namespace pf
 
 using namespace pf;
@@ -118,13 +152,20 @@ PF_API pf_status grid_set_bus_types(pf_grid *grid, const int32_t *bus_type, pf_s
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     PF_CUDA(cudaStreamSynchronize(s));   // no launch may still read the old map
-    for (void *p : {(void *)g->red_colptr, (void *)g->red_rowidx, (void *)g->red_jmap, (void *)g->red_fmap})
+    for (void *p : {(void *)g->red_colptr, (void *)g->red_rowidx, (void *)g->red_jmap, (void *)g->red_fmap,
+                    (void *)g->red_rowptr, (void *)g->red_colidx, (void *)g->red_jmap_csr, (void *)g->nt_F,
+                    (void *)g->nt_J, (void *)g->nt_dx})
         if (p) g->arena.release(p);
     g->red_colptr = g->red_rowidx = g->red_jmap = g->red_fmap = nullptr;
+    g->red_rowptr = g->red_colidx = g->red_jmap_csr = nullptr;
+    g->nt_F = g->nt_J = g->nt_dx = nullptr;   // sized by n and nnz: re-allocated by the next Newton solve
     g->red_set = 0;
     if ((st = upload_vec(g->arena, &g->red_colptr, R.colptr, s)) ||
         (st = upload_vec(g->arena, &g->red_rowidx, R.rowidx, s)) ||
-        (st = upload_vec(g->arena, &g->red_jmap, R.jmap, s)) || (st = upload_vec(g->arena, &g->red_fmap, R.fmap, s)))
+        (st = upload_vec(g->arena, &g->red_jmap, R.jmap, s)) || (st = upload_vec(g->arena, &g->red_fmap, R.fmap, s)) ||
+        (st = upload_vec(g->arena, &g->red_rowptr, R.rowptr, s)) ||
+        (st = upload_vec(g->arena, &g->red_colidx, R.colidx, s)) ||
+        (st = upload_vec(g->arena, &g->red_jmap_csr, R.jmap_csr, s)))
         return st;
     if (!g->red_J) {
         PF_CUDA(g->arena.alloc(&g->red_P, (size_t)g->nb));
@@ -175,14 +216,7 @@ PF_API pf_status jac_reduced(pf_grid *grid, int32_t method, const double *vm, co
                                : jac_elementwise(grid, vm, va, g->red_P, g->red_Q, g->red_J, stream);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const long long total = (long long)g->red_n + g->red_nnz;
-    int dev = 0, nsm = 0;
-    PF_CUDA(cudaGetDevice(&dev));
-    PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * nsm);
     TraceScope t(g, PF_K_REDUCE, s);
-    PF_CUDA(launch_k(k_reduce, blocks, 256, 0, s, true, g->red_n, g->red_npvpq, (int)g->red_nnz,
-                     (const int *)g->red_fmap, (const int *)g->red_jmap, (const double *)g->red_P,
-                     (const double *)g->red_Q, Pspec, Qspec, (const double *)g->red_J, F, Jr));
+    PF_CUDA(launch_reduce(g, g->red_jmap, Pspec, Qspec, F, Jr, s));
     return PF_OK;
 }

@@ -16,7 +16,7 @@ from . import _build
 LIB_PATH = _build.LIB_PFGRID
 HEADER = os.path.join(_build.INCLUDE, "pfgrid.h")
 
-PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETOPO, PF_EDEVICE, PF_ETIMEOUT, PF_EUNSUPPORTED = range(8)
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETOPO, PF_EDEVICE, PF_ETIMEOUT, PF_EUNSUPPORTED, PF_ENOCONV = range(9)
 
 
 class PfError(RuntimeError):
@@ -79,6 +79,8 @@ def _load():
         "jac_reduced_info": (st, [vp, pi32, pi32, ctypes.POINTER(ctypes.c_int64)]),
         "jac_reduced_pattern": (st, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "jac_reduced": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
+        "powerflow_newton": (st, [vp, i32, vp, vp, vp, vp, ctypes.c_double, i32, pi32, ctypes.POINTER(ctypes.c_double),
+                                  vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -393,6 +395,20 @@ def jac_reduced(grid, method, vm, va, Pspec, Qspec, F, Jr, stream=None):
     _check(_lib.jac_reduced(grid.handle, int(m), _dptr(vm, "vm", nb), _dptr(va, "va", nb),
                             _dptr(Pspec, "Pspec", nb), _dptr(Qspec, "Qspec", nb), _dptr(F, "F", n),
                             _dptr(Jr, "Jr", nnz), _stream(stream)), "jac_reduced")
+
+
+def powerflow_newton(grid, method, vm, va, Pspec, Qspec, tol=1e-10, max_iter=20, stream=None):
+    """Newton-Raphson power flow from (vm, va) (device tensors, updated in
+    place).  Returns (converged, iterations, final max |F|)."""
+    nb = grid.nb
+    m = {"ybus": 0, "elementwise": 1}.get(method, method)
+    it, fmax = ctypes.c_int32(), ctypes.c_double()
+    st = _lib.powerflow_newton(grid.handle, int(m), _dptr(vm, "vm", nb), _dptr(va, "va", nb),
+                               _dptr(Pspec, "Pspec", nb), _dptr(Qspec, "Qspec", nb), float(tol), int(max_iter),
+                               ctypes.byref(it), ctypes.byref(fmax), _stream(stream))
+    if st not in (PF_OK, PF_ENOCONV):
+        _check(st, "powerflow_newton")
+    return st == PF_OK, it.value, fmax.value
 
 
 # ------------------------------------------------------------------ batches --

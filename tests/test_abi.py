@@ -30,8 +30,10 @@ def test_every_declared_symbol_is_exported(pf):
 
 
 def test_status_names(pf):
-    assert pf._status_name(0) == "PF_OK"
-    assert pf._status_name(4) == "PF_ETOPO"
+    names = ["PF_OK", "PF_EINVAL", "PF_ENOMEM", "PF_ECUDA", "PF_ETOPO", "PF_EDEVICE", "PF_ETIMEOUT",
+             "PF_EUNSUPPORTED", "PF_ENOCONV"]
+    for code, name in enumerate(names):
+        assert pf._status_name(code) == name and getattr(pf, name) == code
     assert pf._status_name(99) == "PF_UNKNOWN"
 
 

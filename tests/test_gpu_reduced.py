@@ -139,3 +139,50 @@ def test_newton_with_gpu_jacobian_converges_quadratically(pf):
         if a > 1e-6:
             assert b <= 1e3 * a * a, norms
     assert torch.cuda.is_available()
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_powerflow_newton_matches_the_oracle(pf, method):
+    """Newton-Raphson on the GPU (evaluation, gather, cuSOLVER sparse QR,
+    update) from the same start as the oracle's Newton iteration reaches the
+    same solution, the known state that defines the specification."""
+    import torch
+    pytest.importorskip("scipy")
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    bt = w["bustype"]
+    vm_t, va_t = w["vm"][0].copy(), 0.1 * w["va"][0]
+    Ps, Qs = oracle.inj_sparse(oracle.ybus(w), vm_t, va_t)
+    rng = np.random.default_rng(55)
+    vm0, va0 = vm_t.copy(), va_t.copy()
+    pq, pvpq = bt == 1, (bt == 1) | (bt == 2)
+    vm0[pq] += rng.uniform(-1e-3, 1e-3, int(pq.sum()))
+    va0[pvpq] += rng.uniform(-1e-3, 1e-3, int(pvpq.sum()))
+    vm_o, va_o, it_o, norms, ok_o = oracle.newton(w, bt, vm0, va0, Ps, Qs, tol=1e-11)
+    assert ok_o
+    grid = pf.ybus_build(w)
+    pf.grid_set_bus_types(grid, bt)
+    vm, va = _d(vm0), _d(va0)
+    ok, it, fmax = pf.powerflow_newton(grid, method, vm, va, _d(Ps), _d(Qs), tol=1e-11, max_iter=10)
+    assert ok and fmax <= 1e-11 and abs(it - it_o) <= 1, (it, it_o, fmax, norms)
+    vm, va = vm.cpu().numpy(), va.cpu().numpy()
+    assert np.max(np.abs(vm - vm_o)) < 1e-10 and np.max(np.abs(va - va_o)) < 1e-10
+    assert np.max(np.abs(vm - vm_t)) < 1e-10 and np.max(np.abs(va - va_t)) < 1e-10
+    assert np.array_equal(vm[~pq], vm0[~pq]) and va[0] == va0[0]
+    torch.cuda.synchronize()
+
+
+def test_powerflow_newton_reports_non_convergence(pf):
+    """Zero iterations allowed from a start that is not a solution: PF_ENOCONV
+    with the mismatch of the start, the state unchanged."""
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    grid = pf.ybus_build(w)
+    pf.grid_set_bus_types(grid, w["bustype"])
+    vm, va = _d(w["vm"][0]), _d(w["va"][0])
+    zeros = _d(np.zeros(w["nb"]))
+    ok, it, fmax = pf.powerflow_newton(grid, 1, vm, va, zeros, zeros, tol=1e-11, max_iter=0)
+    P, Q = oracle.inj_sparse(oracle.ybus(w), w["vm"][0], w["va"][0])
+    F = oracle.mismatch(P, Q, np.zeros(w["nb"]), np.zeros(w["nb"]), w["bustype"])
+    assert not ok and it == 0 and abs(fmax - np.max(np.abs(F))) <= 1e-12 * np.max(np.abs(F))
+    assert np.array_equal(vm.cpu().numpy(), w["vm"][0]) and np.array_equal(va.cpu().numpy(), w["va"][0])
