@@ -53,7 +53,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
-    ap.add_argument("--profile-workload", choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra"],
+    ap.add_argument("--profile-workload",
+                    choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra", "newton"],
                     help="run only this batched/adjoint workload (few launches, for profilers) and exit")
     return ap.parse_args(argv)
 
@@ -204,7 +205,8 @@ def timed_replays(torch, g, reps, name="replays"):
 def extra_workloads(torch, pfgrid, synth, reps, only=None):
     """The batched and adjoint workloads, each timed from a CUDA-graph replay
     (inputs larger than L2 for the batched ones, so no flush is needed).
-    `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced", "ultra"."""
+    `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced", "ultra",
+    "newton"."""
     out = {}
     if only in (None, "n1"):
         out.update(_n1_workload(torch, pfgrid, synth, reps))
@@ -217,7 +219,44 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
         out["reduced_newton_csc_70k"] = _reduced_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "ultra"):
         out["single_410k"] = _single_workload(torch, pfgrid, synth, 6, max(reps, 20))
+    if only in (None, "newton"):
+        out["newton_powerflow"] = {"2k": _newton_workload(torch, pfgrid, synth, 1),
+                                   "10k": _newton_workload(torch, pfgrid, synth, 3)}
     return out
+
+
+def _newton_workload(torch, pfgrid, synth, k, reps=5):
+    """Newton-Raphson power flow on workload k's grid and bus types, from a start
+    within 1e-3 of a known operating point (the workload's angles scaled by 0.1),
+    to max |F| <= 1e-10: wall time of the whole solve (host-timed, it synchronizes
+    every iteration) and its iteration count."""
+    w = synth.workload(k, nscen=1)
+    nb, bt = w["nb"], w["bustype"]
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    grid = pfgrid.ybus_build(w)
+    pfgrid.grid_set_bus_types(grid, bt)
+    vm_t, va_t = dev(w["vm"][0]), dev(0.1 * w["va"][0])
+    Ps = torch.empty(nb, dtype=torch.float64, device="cuda")
+    Qs = torch.empty_like(Ps)
+    pfgrid.inj_elementwise(grid, vm_t, va_t, Ps, Qs)
+    rng = np.random.default_rng(56)
+    pq, pvpq = bt == 1, (bt == 1) | (bt == 2)
+    vm0, va0 = w["vm"][0].copy(), 0.1 * w["va"][0]
+    vm0[pq] += rng.uniform(-1e-3, 1e-3, int(pq.sum()))
+    va0[pvpq] += rng.uniform(-1e-3, 1e-3, int(pvpq.sum()))
+    res = {"nb": nb, "n": pfgrid.jac_reduced_info(grid)[0]}
+    for name, m in (("elementwise", 1), ("ybus", 0)):
+        ts = []
+        for r in range(reps + 1):
+            vm, va = dev(vm0), dev(va0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ok, it, fmax = pfgrid.powerflow_newton(grid, m, vm, va, Ps, Qs, tol=1e-10, max_iter=20)
+            ts.append(time.perf_counter() - t0)
+        res[name] = {"converged": ok, "iterations": it, "max_mismatch": fmax,
+                     "ms_per_solve": 1e3 * statistics.median(ts[1:])}
+    pfgrid.grid_check_error(grid)
+    return res
 
 
 def _single_workload(torch, pfgrid, synth, k, steps):
