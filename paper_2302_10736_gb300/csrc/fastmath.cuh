@@ -24,6 +24,10 @@ namespace pf {
 
 // table size; `tab` below holds (cos, sin)(2 pi k / 256), k = 0..255
 constexpr int kTrigN = 256;
+// copies of the table in global memory: every CTA of a launch copies one into
+// shared memory at its start, and kTrigCopies copies spread those reads over
+// many L2 lines instead of 32
+constexpr int kTrigCopies = 64;
 
 __device__ __forceinline__ void fast_sincos(double x, const double2 *__restrict__ tab, double *s_out,
                                             double *c_out)

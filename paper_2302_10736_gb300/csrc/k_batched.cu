@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
     double *spq = reinterpret_cast<double *>(smem + sp.pq);
     double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x;
-    for (int k = tid; k < kTrigN; k += TB) tab[k] = a.trig[k];
+    const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
+    for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
     batch_phasors(a, tab, JAC);
     if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
@@ -280,7 +281,8 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     double *spq = reinterpret_cast<double *>(smem + sp.pq);
     double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x;
-    for (int k = tid; k < kTrigN; k += TB) tab[k] = a.trig[k];
+    const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
+    for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
     batch_phasors(a, tab, true);
     if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;

@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
         nq = a.tloc[t0 + tid];
         ol = a.town[t0 + tid] - b0;
     }
-    for (int k = tid; k < kTrigN; k += TB) tab[k] = a.trig[k];
+    const double2 *trig = a.trig + (w % kTrigCopies) * kTrigN;
+    for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
 
     // ---- phasor table of the window (Sec. IV-B.1 step 1, own and ghost buses) ----

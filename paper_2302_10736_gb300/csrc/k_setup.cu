@@ -84,15 +84,16 @@ __global__ void k_bus_yd(int nb, const int *__restrict__ tp, const double2 *__re
     yd[i] = acc;
 }
 
-__device__ double2 g_trig_tab[kTrigN];
+__device__ double2 g_trig_tab[kTrigCopies * kTrigN];
 
-// (cos, sin)(2 pi k / 256) by the library's sincospi (exact argument k / 128)
+// (cos, sin)(2 pi k / 256) by the library's sincospi (exact argument k / 128),
+// copy blockIdx.x of the table
 __global__ void k_trig_table_init()
 {
     const int k = threadIdx.x;
     double s, c;
     sincospi(2.0 * k / kTrigN, &s, &c);
-    g_trig_tab[k] = make_double2(c, s);
+    g_trig_tab[blockIdx.x * kTrigN + k] = make_double2(c, s);
 }
 
 // Phasor step (Sec. IV-B.1 step 1): U = e^{j theta} with v and 1/v (gathered
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kTrigN) k_phasor(int nb, const double *__restr
 {
     __shared__ double2 tab[kTrigN];
     pdl_launch_dependents();   // the evaluation kernel may start loading its static data now
-    tab[threadIdx.x] = g_trig_tab[threadIdx.x];
+    tab[threadIdx.x] = g_trig_tab[(blockIdx.x % kTrigCopies) * kTrigN + threadIdx.x];
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
@@ -138,7 +139,7 @@ cudaError_t ensure_trig_table()
     if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return cudaSuccess;
-    k_trig_table_init<<<1, kTrigN>>>();
+    k_trig_table_init<<<kTrigCopies, kTrigN>>>();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
     void *p = nullptr;
