@@ -58,6 +58,18 @@ __device__ __forceinline__ void fast_sincos(double x, const double2 *__restrict_
     *s_out = fma(a.y, cm1, fma(a.x, sr, a.y));
 }
 
+// -x by flipping the sign bit on the integer pipe (exact, and no FP64 instruction)
+__device__ __forceinline__ double neg(double x)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
+// x or -x, chosen per thread without a branch (sign bit on the integer pipe)
+__device__ __forceinline__ double neg_if(double x, bool flip)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (flip ? (long long)0x8000000000000000ULL : 0LL));
+}
+
 __device__ __forceinline__ double fast_rcp(double v)
 {
     double y;

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
                     const int pos = bm.x + kps, d = bm.y;
                     jst[pos] = Ki;
                     jst[pos + d] = Gr;
-                    jst[Ls + pos] = -Kr;
+                    jst[Ls + pos] = neg(Kr);
                     jst[Ls + pos + d] = Gi;
                 }
             } else {
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
                 const double4_32a uo = b == tid ? ub : a.U[sb + b0 + b];
                 const double v = uo.z, iv = uo.w, v2 = v * v, tv = v + v;
                 const int pos = bm.x + bm.z;
-                jst[pos] = -sKi;
+                jst[pos] = neg(sKi);
                 jst[pos + d] = fma(tv, y.x, sKr * iv);
                 jst[Ls + pos] = sKr;
                 jst[Ls + pos + d] = fma(-tv, y.y, sKi * iv);

@@ -106,7 +106,6 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
         th = a.va[o0];
         v = a.vm[o0];
     }
-    const double vb = v;   // the bus thread's own magnitude (slot tid < nbus)
     // the bus thread's metadata (a window has at most blockDim.x buses), kept
     // in registers until the phasors are done so its latency hides behind them
     int4 bmo = make_int4(0, 0, 0, 0);
@@ -172,7 +171,7 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
                 const int pos = bm.x + (nq.y & EW_KMASK), d = bm.y;
                 jst[pos] = Ki;           // J11 = Re(-j K)
                 jst[pos + d] = Gr;       // J12
-                jst[L + pos] = -Kr;      // J21 = Im(-j K)
+                jst[L + pos] = neg(Kr);  // J21 = Im(-j K)
                 jst[L + pos + d] = Gi;   // J22
             }
         } else {
@@ -214,25 +213,24 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
             const double2 y = syd[b], vw = sW[b];
             const double vo = vw.x, iv = vw.y, v2 = vo * vo, tv = vo + vo;
             // real part: Re conj(Yd) = y.x; imaginary part: Im conj(Yd) = -y.y (sign flips are exact)
-            const double yr = im ? -y.y : y.x;
+            const double yr = im ? neg(y.y) : y.x;
             const int pos = bm.x + bm.z;
-            jst[(im ? 0 : L) + pos] = im ? -sK : sK;              // Re / Im of j sum K
+            jst[(im ? 0 : L) + pos] = neg_if(sK, im);             // Re / Im of j sum K
             jst[(im ? L : 0) + pos + d] = fma(tv, yr, sK * iv);   // 2 v conj(Yd) + sum K / v
             spq[(im ? pqs : 0) + b + par] = fma(v2, yr, sK);      // S = v^2 conj(Yd) + sum K
         }
     } else {
-        for (int b = tid; b < nbus; b += TB) {
+        // two threads per bus as above; the magnitude comes back from L1
+        const double *k1 = reinterpret_cast<const double *>(skg);   // K.x, K.y per terminal
+        for (int x = tid; x < 2 * nbus; x += TB) {
+            const int b = x >> 1, im = x & 1;
             const int4 bm = sbm[b];
             const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+            double sK = 0.0;
+            for (int i = bm.w; i < tend; ++i) sK += k1[2 * i + im];
             const double2 y = syd[b];
-            double sKr = 0.0, sKi = 0.0;
-            for (int i = bm.w; i < tend; ++i) {
-                sKr += skg[i].x;
-                sKi += skg[i].y;
-            }
-            const double vo = b == tid ? vb : a.vm[b0 + b], v2 = vo * vo;
-            spq[b + par] = fma(v2, y.x, sKr);
-            spq[pqs + b + par] = fma(-v2, y.y, sKi);
+            const double vo = a.vm[b0 + b], v2 = vo * vo;
+            spq[(im ? pqs : 0) + b + par] = fma(v2, im ? neg(y.y) : y.x, sK);   // S = v^2 conj(Yd) + sum K
         }
     }
 
