@@ -39,7 +39,7 @@ YB_OPS_PER_NNZ = 16
 YB_OPS_PER_ROW = 16
 # DRAM bytes of one k_ew<1> launch on the 70k-bus grid (dram__bytes_read.sum + dram__bytes_write.sum
 # of an ncu capture of that launch); None whenever the kernel changes, until it is captured again
-EW_TRAFFIC_BYTES = 8883456 + 0
+EW_TRAFFIC_BYTES = 9141760 + 0
 
 
 def parse_args(argv=None):
@@ -54,7 +54,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
     ap.add_argument("--profile-workload",
-                    choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra", "newton"],
+                    choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra", "newton", "sweep"],
                     help="run only this batched/adjoint workload (few launches, for profilers) and exit")
     return ap.parse_args(argv)
 
@@ -206,7 +206,7 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
     """The batched and adjoint workloads, each timed from a CUDA-graph replay
     (inputs larger than L2 for the batched ones, so no flush is needed).
     `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced", "ultra",
-    "newton"."""
+    "newton", "sweep"."""
     out = {}
     if only in (None, "n1"):
         out.update(_n1_workload(torch, pfgrid, synth, reps))
@@ -219,10 +219,50 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
         out["reduced_newton_csc_70k"] = _reduced_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "ultra"):
         out["single_410k"] = _single_workload(torch, pfgrid, synth, 6, max(reps, 20))
+    if only in (None, "sweep"):
+        out["size_sweep"] = _size_sweep(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "newton"):
         out["newton_powerflow"] = {"2k": _newton_workload(torch, pfgrid, synth, 1),
                                    "10k": _newton_workload(torch, pfgrid, synth, 3)}
     return out
+
+
+# bus counts of the paper's test cases (Table VII and the replicated grids of Sec. V-F)
+SWEEP_SIZES = (14, 118, 300, 1354, 2736, 9241, 25000, 70000, 82000, 164000, 410000)
+
+
+def _size_sweep(torch, pfgrid, synth, steps):
+    """Single evaluations (injections + Jacobian) by both methods on synthetic
+    grids with the bus counts of the paper's cases (branches = 1.32 x buses,
+    as in the 250k / 330k workload), L2 flushed between steps, and the time
+    of each relative to the 118-bus grid (the paper's complexity study)."""
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    rows = []
+    for nb in SWEEP_SIZES:
+        nl = int(round(1.32 * nb))
+        gr = synth.grid(nb, nl, synth.BASE_SEED + 100 + nb)
+        vm, va = synth.voltages(nb, 1, synth.BASE_SEED + 100 + nb)
+        grid = pfgrid.ybus_build(gr)
+        vmd, vad = dev(vm[0]), dev(va[0])
+        pfgrid.grid_autotune(grid, vmd, vad, reps=10)
+        P = torch.empty(nb, dtype=torch.float64, device="cuda")
+        Q = torch.empty_like(P)
+        J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+        row = {"nb": nb, "nl": nl}
+        for name, fn in (("elementwise", pfgrid.jac_elementwise), ("ybus", pfgrid.jac_ybus)):
+            f = lambda: fn(grid, vmd, vad, P, Q, J)
+            for _ in range(3):
+                f()
+            t = time_loop(torch, f, steps, flush, "sweep_%s" % name)
+            row["%s_us" % name] = 1e3 * sum(t) / len(t)   # mean: one event pair resolves about 1 us
+        pfgrid.grid_check_error(grid)
+        rows.append(row)
+    base = next(r for r in rows if r["nb"] == 118)
+    for r in rows:
+        for name in ("elementwise", "ybus"):
+            r["%s_ratio_to_118" % name] = r["%s_us" % name] / base["%s_us" % name]
+    return rows
 
 
 def _newton_workload(torch, pfgrid, synth, k, reps=5):
