@@ -35,10 +35,15 @@
  * Execution model
  *   Every evaluation entry point is asynchronous on `stream` (a cudaStream_t,
  *   NULL = the legacy default stream), allocates nothing, never synchronizes
- *   and takes device pointers the caller owns.  A grid owns one phasor
- *   workspace, so evaluations that use the same grid must not overlap on the
- *   GPU (issue them on one stream).  Input checks are done at build time;
- *   evaluation calls check only for NULL pointers and sizes.
+ *   and takes device pointers the caller owns (eval_host, powerflow_newton
+ *   and the set-up calls are the documented exceptions).  The element-wise
+ *   single evaluations keep their phasors in shared memory and only read the
+ *   grid, so they may overlap on several streams; the Ybus-method
+ *   evaluations share the grid's phasor workspace and batched, reduced and
+ *   Newton calls the batch's or grid's scratch, so those must not overlap on
+ *   the GPU with another call on the same grid (issue them on one stream).
+ *   Input checks are done at build time; evaluation calls check only for
+ *   NULL pointers and sizes.
  *   Errors: every function returns a pf_status; pf_last_error() gives a
  *   message for the calling thread.  Nothing aborts or throws across the ABI.
  */
