@@ -300,3 +300,32 @@ def test_null_outputs_rejected(pf):
         pf.jac_ybus(grid, _d(vm), _d(va), None, None, None)
     with pytest.raises(pf.PfError):
         pf.inj_elementwise(grid, _d(vm), _d(va), None, torch.zeros(4, dtype=torch.float64, device="cuda"))
+
+
+def test_elementwise_evaluations_overlap_on_two_streams(pf):
+    """The element-wise single evaluations only read the grid: two states on
+    two streams at once give the same bits as one after the other."""
+    import torch
+    gr = random_grid(5000, 6800, 61)
+    grid = pf.ybus_build(gr)
+    states = [random_state(5000, 61 + k) for k in range(2)]
+    ref = []
+    for vm, va in states:
+        P = torch.empty(5000, dtype=torch.float64, device="cuda")
+        Q = torch.empty_like(P)
+        J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+        pf.jac_elementwise(grid, _d(vm), _d(va), P, Q, J)
+        torch.cuda.synchronize()
+        ref.append((P.clone(), Q.clone(), J.clone()))
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    outs = [(torch.empty(5000, dtype=torch.float64, device="cuda"), torch.empty(5000, dtype=torch.float64,
+             device="cuda"), torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")) for _ in range(2)]
+    ins = [(_d(vm), _d(va)) for vm, va in states]
+    torch.cuda.synchronize()
+    for rep in range(20):
+        for k in range(2):
+            pf.jac_elementwise(grid, ins[k][0], ins[k][1], *outs[k], stream=streams[k].cuda_stream)
+    torch.cuda.synchronize()
+    for k in range(2):
+        for a, b in zip(outs[k], ref[k]):
+            assert torch.equal(a, b)
