@@ -138,7 +138,11 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
         sV[j] = make_double2(v * c, v * s);
         if (JAC) {
             sU[j] = make_double2(c, s);
-            sW[j] = make_double2(v, j < nbus ? fast_rcp(v) : 0.0);
+            // 1/v only for the window's own buses: warps of ghost slots skip it
+            // (a warp-uniform branch), mixed warps compute it for all lanes
+            double iv = 0.0;
+            if (__any_sync(__activemask(), j < nbus)) iv = fast_rcp(v);
+            sW[j] = make_double2(v, iv);
         }
     }
     if (tid < nbus) {
