@@ -117,6 +117,12 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
     if ((st = upload(a, &g->tnbr, H.tnbr, s))) return st;
     if ((st = upload(a, &g->town, H.town, s))) return st;
     if ((st = upload(a, &g->tmir, H.tmir, s))) return st;
+    {
+        std::vector<int2> hk(g->nl);
+        for (int l = 0; l < g->nl; ++l) hk[l] = make_int2(H.from[l], H.to[l]);
+        if ((st = upload(a, &g->br_hk, hk, s))) return st;
+        PF_CUDA(cudaStreamSynchronize(s));   // hk is freed on return
+    }
     const size_t nl = (size_t)g->nl;
     PF_CUDA(a.alloc(&g->p_g, nl));
     PF_CUDA(a.alloc(&g->p_b, nl));
@@ -129,6 +135,7 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
     PF_CUDA(a.alloc(&g->yv, (size_t)g->nnz));
     PF_CUDA(a.alloc(&g->tself, (size_t)T));
     PF_CUDA(a.alloc(&g->tcoup, (size_t)T));
+    PF_CUDA(a.alloc(&g->br_aux, (size_t)g->nl));
     PF_CUDA(a.alloc(&g->bus_ysh, (size_t)nb));
     PF_CUDA(a.alloc(&g->ph_u, (size_t)nb));
     PF_CUDA(a.alloc(&g->ph_v, (size_t)nb));

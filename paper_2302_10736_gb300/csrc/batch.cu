@@ -83,10 +83,15 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
         delete pb;
         return set_error(PF_ECUDA, "batch_create: cannot query the device");
     }
+    bool ghost = false;
     if (nscen > 0 && (long long)nscen * E.nwin < nsm) {
         HostEw F;
         const int target = (nsm + nscen - 1) / nscen;
         if (host_ew(g->topo, 256, F, E.tfac, target) == PF_OK && F.nwin > E.nwin && fits(F)) E = std::move(F);
+        // latency-bound: the adjoint forms each window's phasors itself (with
+        // its ghost buses) instead of a separate phase and grid barrier
+        ghost = ew_smem_plan(E.max_nbus, E.max_nt, 0, false, E.max_nph).total + kTrigN * sizeof(double2) <=
+                kMaxSmem;
     }
 #ifdef PF_SELFCHECK
     if (pf_status hs = host_selfcheck(g->topo, E)) {
@@ -99,6 +104,8 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
     b->max_L = E.max_L;
     b->max_nt = E.max_nt;
     b->max_nbus = E.max_nbus;
+    b->ghost = ghost ? 1 : 0;
+    b->max_nph = E.max_nph;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)nscen * g->nb;
     const size_t nw = (size_t)nscen * std::max(b->nwin, 1);
@@ -107,6 +114,14 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
         (e = b->arena.alloc(&b->win_bus, E.win_bus.size())) ||
         (e = cudaMemcpyAsync(b->win_bus, E.win_bus.data(), sizeof(int) * E.win_bus.size(), cudaMemcpyHostToDevice,
                              st)) ||
+        (ghost && ((e = b->arena.alloc(&b->desc, E.desc.size())) || (e = b->arena.alloc(&b->slotbus, E.slotbus.size())) ||
+                   (e = b->arena.alloc(&b->tloc, E.tloc.size())) ||
+                   (e = cudaMemcpyAsync(b->desc, E.desc.data(), sizeof(int4) * E.desc.size(), cudaMemcpyHostToDevice,
+                                        st)) ||
+                   (e = cudaMemcpyAsync(b->slotbus, E.slotbus.data(), sizeof(int) * E.slotbus.size(),
+                                        cudaMemcpyHostToDevice, st)) ||
+                   (e = cudaMemcpyAsync(b->tloc, E.tloc.data(), sizeof(int2) * E.tloc.size(), cudaMemcpyHostToDevice,
+                                        st)))) ||
         (e = b->arena.alloc(&b->U, n)) || (e = b->arena.alloc(&b->V, n)) || (e = b->arena.alloc(&b->r, n)) ||
         (e = b->arena.alloc(&b->lpart, nw)) ||
         (nscen && (e = cudaMemcpyAsync(b->sc, b->h_sc.data(), sizeof(ScenOut) * nscen, cudaMemcpyHostToDevice, st))) ||

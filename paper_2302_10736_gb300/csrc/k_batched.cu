@@ -39,7 +39,10 @@ constexpr uint64_t kBatchBarrierNs = 2000000000ull;   // bounded grid-barrier wa
 
 struct BatchArgs {
     int S, nb, nl, nnz, nwin, max_nbus, max_nt, max_L, aligned;
-    const int *win_bus, *tp, *rp, *kd, *town, *tmir, *tpos;
+    int ghost, max_nph;
+    const int *win_bus, *tp, *rp, *kd, *town, *tmir, *tpos, *slotbus;
+    const int2 *tloc;
+    const int4 *desc;
     const int2 *tnbr;
     const double2 *yd, *tself, *tcoup, *trig;
     const ScenOut *sc;
@@ -55,6 +58,8 @@ struct BatchArgs {
     double2 *r;
     double *lpart, *L, *gvm, *gva, *gg, *gb, *gbsh, *gtap;
     const double *pg, *pb, *pbsh, *ptap, *pshift;
+    const int2 *br_hk;
+    const double4_32a *br_aux;
 };
 
 __device__ __forceinline__ void store_range_ll(double *x, const double *s, long long b0, long long b1)
@@ -274,18 +279,21 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
 __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
-    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false);
+    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false, a.ghost ? a.max_nph : 0);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
     double2 *skg = reinterpret_cast<double2 *>(smem + sp.kg);
     double *spq = reinterpret_cast<double *>(smem + sp.pq);
+    double2 *sV = reinterpret_cast<double2 *>(smem + sp.ph);   // window phasor table (ghost mode)
     double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x;
     const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
     for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
-    batch_phasors(a, tab, true);
-    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    if (!a.ghost) {   // every scenario's phasors first, visible to all CTAs after the barrier
+        batch_phasors(a, tab, true);
+        if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    }
 
     const long long nitem = (long long)a.S * a.nwin;
     // ---- phase 2: injections, residuals and per-window loss partial sums ----
@@ -297,12 +305,31 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         const long long sb = (long long)s * a.nb;
         __syncthreads();
         batch_window_meta(a, sc, b0, b1, t0, sbm, syd);
+        if (a.ghost) {
+            // phasors of the window's own and ghost buses (slot j's bus in
+            // slotbus); the own buses' phasors also go to U, V for phase 3
+            const int *sbus = a.slotbus + (long long)w * a.max_nph;
+            const int nph = a.desc[2 * w + 1].z;
+            for (int j = tid; j < nph; j += TB) {
+                const int o = sbus[j];
+                double sn, cs;
+                fast_sincos(a.va[sb + o], tab, &sn, &cs);
+                const double v = a.vm[sb + o];
+                const double2 V = make_double2(v * cs, v * sn);
+                sV[j] = V;
+                if (j < nbus) {
+                    a.U[sb + o] = make_double4_32a(cs, sn, v, fast_rcp(v));
+                    a.V[sb + o] = V;
+                }
+            }
+        }
         __syncthreads();
         for (int i = tid; i < nt; i += TB) {
             const int p = t0 + i;
             const double2 yc = a.tcoup[p];
             const int q = a.tnbr[p].x, o = a.town[p];
-            const double2 Vo = a.V[sb + o], Vq = a.V[sb + q];
+            const double2 Vo = a.ghost ? sV[o - b0] : a.V[sb + o];
+            const double2 Vq = a.ghost ? sV[a.tloc[p].x] : a.V[sb + q];
             const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
             double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);
             if (p == sc.ph || p == sc.pk) Kr = Ki = 0.0;
@@ -400,11 +427,11 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     // ---- phase 3b: branch-parameter gradients, scenarios summed in order ----
     if (a.gg) {
         for (int l = blockIdx.x * TB + tid; l < a.nl; l += gridDim.x * TB) {
-            const int h = a.town[a.tpos[2 * l]], k = a.town[a.tpos[2 * l + 1]];
-            const double g = a.pg[l], bb = a.pb[l], bsh = a.pbsh[l], m = a.ptap[l];
-            const double im = 1.0 / m, im2 = im * im;
-            double sphi, cphi;
-            fast_sincos(a.pshift[l], tab, &sphi, &cphi);
+            const int2 hk = a.br_hk[l];
+            const int h = hk.x, k = hk.y;
+            const double g = a.pg[l], bb = a.pb[l], bsh = a.pbsh[l];
+            const double4_32a aux = a.br_aux[l];   // 1/m, cos phi, sin phi (formed with the constants)
+            const double im = aux.x, im2 = im * im, cphi = aux.y, sphi = aux.z;
             const double c1r = g, c1i = -(bb + 0.5 * bsh);   // conj(y_s + j b_sh / 2)
             double agg = 0.0, agb = 0.0, agsh = 0.0, agt = 0.0;
             for (int s = 0; s < a.S; ++s) {
@@ -460,6 +487,11 @@ static BatchArgs batch_args(Batch *b)
     a.max_nt = b->max_nt;
     a.max_L = b->max_L;
     a.win_bus = b->win_bus;
+    a.ghost = b->ghost;
+    a.max_nph = b->max_nph;
+    a.desc = b->desc;
+    a.slotbus = b->slotbus;
+    a.tloc = b->tloc;
     a.tp = g->tp;
     a.rp = g->rp;
     a.kd = g->kd;
@@ -484,6 +516,8 @@ static BatchArgs batch_args(Batch *b)
     a.pbsh = g->p_bsh;
     a.ptap = g->p_tap;
     a.pshift = g->p_shift;
+    a.br_hk = g->br_hk;
+    a.br_aux = g->br_aux;
     return a;
 }
 
@@ -556,7 +590,7 @@ cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const d
     a.gbsh = gbsh;
     a.gtap = gtap;
     a.aligned = al16(gvm) && al16(gva);
-    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false);
+    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false, a.ghost ? a.max_nph : 0);
     const size_t smem = sp.total + kTrigN * sizeof(double2);
     const long long items = std::max<long long>((long long)b->S * b->nwin, (g->nl + b->tb - 1) / b->tb);
     return coop_launch(k_adj, b->resident[2], b, smem, items, s, a);

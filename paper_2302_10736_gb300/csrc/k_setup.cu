@@ -31,7 +31,8 @@ __global__ void k_bus_shunt(int nb, const double *__restrict__ gs, const double 
 __global__ void k_branch_constants(int nl, const double *__restrict__ g, const double *__restrict__ b,
                                    const double *__restrict__ bsh, const double *__restrict__ tap,
                                    const double *__restrict__ shift, const int *__restrict__ tpos,
-                                   double2 *__restrict__ tself, double2 *__restrict__ tcoup)
+                                   double2 *__restrict__ tself, double2 *__restrict__ tcoup,
+                                   double4_32a *__restrict__ aux)
 {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nl) return;
@@ -49,6 +50,7 @@ __global__ void k_branch_constants(int nl, const double *__restrict__ g, const d
     tcoup[ph] = make_double2(-ar * im, -ai * im);
     tself[pk] = ys_k;
     tcoup[pk] = make_double2(-br * im, -bi * im);
+    aux[l] = make_double4_32a(im, cp, sp, 0.0);   // for the parameter gradients of the adjoint
 }
 
 __global__ void k_ybus_values(int nnz, const int *__restrict__ ybeg, const int *__restrict__ yend,
@@ -154,7 +156,7 @@ cudaError_t launch_branch_constants(Grid *g, const double *gg, const double *gb,
 {
     if (g->nl > 0)
         k_branch_constants<<<nblk(g->nl, 256), 256, 0, s>>>(g->nl, gg, gb, gbsh, gtap, gshift, g->tpos, g->tself,
-                                                            g->tcoup);
+                                                            g->tcoup, g->br_aux);
     return cudaGetLastError();
 }
 

@@ -157,6 +157,8 @@ struct Grid {
     // terminals in sorted order (device)
     int *tp = nullptr;                     // [nb+1]
     double2 *tself = nullptr, *tcoup = nullptr;
+    int2 *br_hk = nullptr;                 // [nl] end buses (from, to) of branch l
+    double4_32a *br_aux = nullptr;         // [nl] {1/m, cos phi, sin phi, 0} of branch l (with the constants)
     int2 *tnbr = nullptr;                  // {other bus, kpos | EW_ACCUM}
     int *town = nullptr;                   // owner bus
     int *tpos = nullptr;                   // [2nl] sorted position of terminal t
@@ -282,6 +284,12 @@ struct Batch {
     // owns a bus in the reduction and loops over up to tfac terminals
     int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0;
     int *win_bus = nullptr;          // [nwin+1]
+    // small batches (about one item per SM): the adjoint forms each window's
+    // phasors with its ghost buses instead of a separate phase and barrier
+    int ghost = 0, max_nph = 0;
+    int4 *desc = nullptr;            // [2 nwin] window descriptors (HostEw::desc)
+    int *slotbus = nullptr;          // [nwin * max_nph]
+    int2 *tloc = nullptr;            // [T]
 };
 
 cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,
