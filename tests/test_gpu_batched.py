@@ -301,3 +301,48 @@ def test_mismatch_loss_autograd(pf):
     assert relerr(va_t.grad.cpu().numpy(), 2 * gvar) <= TOL
     for tt, ref in zip((g_t, b_t, bsh_t, tap_t), gpr):
         assert relerr(tt.grad.cpu().numpy(), 2 * ref) <= TOL
+
+
+def test_cuda_graph_capture_and_replay(pf):
+    """The batched evaluation, the adjoint and the single evaluation can be
+    captured in a CUDA graph (after one eager call) and replayed; replays give
+    the eager bits."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    gr = random_grid(3000, 4100, 71)
+    grid = pf.ybus_build(gr)
+    nonbridge = np.flatnonzero(~synth.bridges(3000, gr["f"], gr["t"]))
+    outage = np.array([-1, int(nonbridge[3]), int(nonbridge[9])], np.int32)
+    S = len(outage)
+    batch = pf.batch_create(grid, S, outage)
+    vm, va = synth.voltages(3000, S, 71, 0, 0.93, 1.07, 0.25)
+    vmd, vad = _d(vm.ravel()), _d(va.ravel())
+    P = torch.empty(S * 3000, dtype=torch.float64, device="cuda")
+    Q = torch.empty_like(P)
+    J = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
+    P1 = torch.empty(3000, dtype=torch.float64, device="cuda")
+    Q1 = torch.empty_like(P1)
+    J1 = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+    Ps, Qs, wP, wQ = (_d(x) for x in (np.zeros(3000), np.zeros(3000), np.ones(3000), np.ones(3000)))
+    L = torch.empty(S, dtype=torch.float64, device="cuda")
+    gvm, gva = torch.empty_like(P), torch.empty_like(P)
+
+    def work():
+        pf.jac_elementwise_batched(batch, vmd, vad, P, Q, J)
+        pf.adjoint_elementwise(batch, vmd, vad, Ps, Qs, wP, wQ, L, gvm, gva)
+        pf.jac_elementwise(grid, vmd[:3000], vad[:3000], P1, Q1, J1)
+
+    work()
+    torch.cuda.synchronize()
+    ref = [x.clone() for x in (P, Q, J, L, gvm, gva, P1, Q1, J1)]
+    for x in (P, Q, J, L, gvm, gva, P1, Q1, J1):
+        x.fill_(np.nan)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        work()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    pf.grid_check_error(grid)
+    for a, b in zip((P, Q, J, L, gvm, gva, P1, Q1, J1), ref):
+        assert torch.equal(a, b)
