@@ -12,8 +12,9 @@
  *   branch l joins h = from[l] and k = to[l]; series admittance
  *   y_hk = g + j b; total line charging b_sh split as y_h = y_k = j b_sh / 2;
  *   off-nominal tap m e^{j phi} on the primary (h) side (Eqs. 5-6).
- *   Bus shunt y_sh,i = g_s,i + j b_s,i (not in Eq. 7; added as a one-terminal
- *   element, see the readings in the design notes).
+ *   Bus shunt y_sh,i = g_s,i + j b_s,i: Eq. 7 has no shunt term, and this
+ *   file adds the shunt as a one-terminal element v_i^2 conj(y_sh,i) (its
+ *   Ybus stamp is Y_ii += y_sh,i).
  *   V_i = v_i e^{j theta_i}; S = P + j Q.
  *   J = [[Re dS/dtheta, Re dS/dv], [Im dS/dtheta, Im dS/dv]] (Eq. 2) with the
  *   canonical CSR layout: P-row i holds the Ybus row-i columns j (theta
