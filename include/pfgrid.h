@@ -415,6 +415,14 @@ pf_status powerflow_newton(pf_grid *grid, int32_t method, double *vm, double *va
                            const double *Qspec, double tol, int32_t max_iter, int32_t *iterations, double *mismatch,
                            pf_stream stream);
 
+/*
+ * Test hook for the error paths: after `after` more device allocations made
+ * through the library's buffer owner succeed, every later one fails (no
+ * cudaMalloc is attempted) and the call reports PF_ENOMEM, releasing what it
+ * had allocated.  after = -1 turns the hook off (the default).  Process-wide.
+ */
+pf_status pf_debug_fail_allocations(int32_t after);
+
 /* ------------------------------------------------------------ tracing -- */
 
 /* Kernel identifiers reported by the tracer. */

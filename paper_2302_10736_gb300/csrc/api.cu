@@ -37,8 +37,14 @@ pf_status set_error(pf_status s, const char *fmt, ...)
     return s;
 }
 
+std::atomic<int> g_alloc_countdown{-1};
+
 pf_status cuda_error(cudaError_t e, const char *what)
 {
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();   // so that a later launch check does not see this failure
+        return set_error(PF_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
     return set_error(PF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -251,6 +257,13 @@ PF_API const char *pf_status_str(pf_status s)
 
 PF_API const char *pf_last_error(void) { return g_last_error.c_str(); }
 
+PF_API pf_status pf_debug_fail_allocations(int32_t after)
+{
+    if (after < -1) return set_error(PF_EINVAL, "pf_debug_fail_allocations: after = %d", after);
+    g_alloc_countdown.store(after);
+    return PF_OK;
+}
+
 PF_API pf_status ybus_build(const pf_grid_desc *d, pf_stream stream, pf_grid **out)
 {
     if (!out) return set_error(PF_EINVAL, "ybus_build: out is NULL");
@@ -454,12 +467,10 @@ PF_API pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, cons
     if (!P || !Q || !J) return set_error(PF_EINVAL, "eval_host: P, Q and J must be non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nb = (size_t)g->nb, nJ = 4 * (size_t)g->nnz;
-    if (!g->st_vm) {
-        PF_CUDA(g->arena.alloc(&g->st_vm, nb));
-        PF_CUDA(g->arena.alloc(&g->st_va, nb));
-        PF_CUDA(g->arena.alloc(&g->st_P, nb));
-        PF_CUDA(g->arena.alloc(&g->st_Q, nb));
-        PF_CUDA(g->arena.alloc(&g->st_J, nJ));
+    if (!g->st_J) {
+        double **const out[5] = {&g->st_vm, &g->st_va, &g->st_P, &g->st_Q, &g->st_J};
+        const size_t n[5] = {nb, nb, nb, nb, nJ};
+        PF_CUDA(alloc_all(g->arena, out, n));
     }
     if (method == 1) {
         // page-locked, mapped host buffers: the kernel reads vm, va and stores

@@ -91,10 +91,10 @@ PF_API pf_status powerflow_newton(pf_grid *grid, int32_t method, double *vm, dou
         cusparseSetMatIndexBase(d, CUSPARSE_INDEX_BASE_ZERO);
         g->nt_descr = d;
     }
-    if (!g->nt_F) {
-        PF_CUDA(g->arena.alloc(&g->nt_F, (size_t)n));
-        PF_CUDA(g->arena.alloc(&g->nt_J, (size_t)std::max(nnz, 1)));
-        PF_CUDA(g->arena.alloc(&g->nt_dx, (size_t)n));
+    if (!g->nt_dx) {
+        double **const out[3] = {&g->nt_F, &g->nt_J, &g->nt_dx};
+        const size_t sz[3] = {(size_t)n, (size_t)std::max(nnz, 1), (size_t)n};
+        PF_CUDA(alloc_all(g->arena, out, sz));
     }
     if (!g->nt_max) PF_CUDA(g->arena.alloc(&g->nt_max, 1));
     cusolverSpHandle_t h = (cusolverSpHandle_t)g->nt_solver;

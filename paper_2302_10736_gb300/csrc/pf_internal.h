@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <atomic>
 #include <vector>
 
 #include "pfgrid.h"
@@ -26,6 +27,10 @@ pf_status cuda_error(cudaError_t e, const char *what);
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADINDEX = 2 };
 
 // ------------------------------------------------- device buffer owner --
+// Test hook (pf_debug_fail_allocations): when >= 0, the number of device
+// allocations that still succeed before every later one fails.
+extern std::atomic<int> g_alloc_countdown;
+
 // Every buffer gets 64 bytes of slack so vector loads of the last element
 // never leave the allocation.
 struct DevArena {
@@ -33,6 +38,10 @@ struct DevArena {
     template <class T>
     cudaError_t alloc(T **p, size_t n)
     {
+        int c = g_alloc_countdown.load();
+        while (c >= 0 && !g_alloc_countdown.compare_exchange_weak(c, c > 0 ? c - 1 : 0)) {
+        }
+        if (c == 0) return cudaErrorMemoryAllocation;   // simulated failure (test hook)
         void *q = nullptr;
         cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 64);
         if (e == cudaSuccess) {
@@ -44,6 +53,23 @@ struct DevArena {
     void release(void *p);
     void free_all();
 };
+
+// K double buffers from the arena, all or none: on failure the ones already
+// made are released and *out stays untouched.
+template <size_t K>
+inline cudaError_t alloc_all(DevArena &a, double **const (&out)[K], const size_t (&n)[K])
+{
+    double *b[K] = {};
+    for (size_t k = 0; k < K; ++k) {
+        cudaError_t e = a.alloc(&b[k], n[k]);
+        if (e != cudaSuccess) {
+            for (size_t q = 0; q < k; ++q) a.release(b[q]);
+            return e;
+        }
+    }
+    for (size_t k = 0; k < K; ++k) *out[k] = b[k];
+    return cudaSuccess;
+}
 
 // ------------------------------------------------ host index structures --
 // Topology-only structures, built once on the host (host_layout.cpp).

@@ -96,9 +96,12 @@ pf_status upload_vec(DevArena &a, T **dst, const std::vector<T> &src, cudaStream
     return PF_OK;
 }
 
-// F[0 .. n) and Jr[0 .. nnz) as one index range; each thread's first map entry
-// is read before the wait for the evaluation kernel (programmatic dependent
-// launch), the rest after.
+// F[0 .. n) and Jr[0 .. nnz) as one index range, kUnroll entries per thread
+// per round: their map entries are loaded together (before the wait for the
+// evaluation kernel: programmatic dependent launch), then their values, so a
+// round costs two load latencies instead of two per entry.
+constexpr int kUnroll = 4;
+
 __global__ void __launch_bounds__(256) k_reduce(int n, int npvpq, int nnz, const int *__restrict__ fmap,
                                                 const int *__restrict__ jmap, const double *__restrict__ P,
                                                 const double *__restrict__ Q, const double *__restrict__ Ps,
@@ -107,17 +110,37 @@ __global__ void __launch_bounds__(256) k_reduce(int n, int npvpq, int nnz, const
 {
     const long long total = (long long)n + nnz;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int src = 0;
-    if (i0 < total) src = i0 < n ? fmap[i0] : jmap[i0 - n];
-    pdl_wait();
-    for (long long i = i0; i < total; i += stride) {
-        if (i != i0) src = i < n ? fmap[i] : jmap[i - n];
-        if (i < n)
-            F[i] = i < npvpq ? P[src] - Ps[src] : Q[src] - Qs[src];
-        else
-            Jr[i - n] = J[src];
+    bool waited = false;
+    for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x; base < total;
+         base += kUnroll * stride) {
+        int src[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const long long i = base + u * stride;
+            src[u] = i < total ? (i < n ? fmap[i] : jmap[i - n]) : 0;
+        }
+        if (!waited) {
+            pdl_wait();
+            waited = true;
+        }
+        double val[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const long long i = base + u * stride;
+            if (i < total) val[u] = i < n ? (i < npvpq ? P[src[u]] - Ps[src[u]] : Q[src[u]] - Qs[src[u]]) : J[src[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const long long i = base + u * stride;
+            if (i < total) {
+                if (i < n)
+                    F[i] = val[u];
+                else
+                    Jr[i - n] = val[u];
+            }
+        }
     }
+    if (!waited) pdl_wait();   // every thread waits once (a thread with no entry too)
 }
 
 }  // namespace
@@ -132,7 +155,8 @@ cudaError_t launch_reduce(Grid *g, const int *map, const double *Pspec, const do
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
         return e;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 8LL * nsm));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((total + 256 * kUnroll - 1) / (256 * kUnroll),
+                                                                       8LL * nsm));
     return launch_k(k_reduce, blocks, 256, 0, s, true, g->red_n, g->red_npvpq, (int)g->red_nnz,
                     (const int *)g->red_fmap, map, (const double *)g->red_P, (const double *)g->red_Q, Pspec, Qspec,
                     (const double *)g->red_J, F, Jr);
@@ -168,9 +192,9 @@ PF_API pf_status grid_set_bus_types(pf_grid *grid, const int32_t *bus_type, pf_s
         (st = upload_vec(g->arena, &g->red_jmap_csr, R.jmap_csr, s)))
         return st;
     if (!g->red_J) {
-        PF_CUDA(g->arena.alloc(&g->red_P, (size_t)g->nb));
-        PF_CUDA(g->arena.alloc(&g->red_Q, (size_t)g->nb));
-        PF_CUDA(g->arena.alloc(&g->red_J, 4 * (size_t)g->nnz));
+        double **const out[3] = {&g->red_P, &g->red_Q, &g->red_J};
+        const size_t n[3] = {(size_t)g->nb, (size_t)g->nb, 4 * (size_t)g->nnz};
+        PF_CUDA(alloc_all(g->arena, out, n));
     }
     g->red_n = R.n;
     g->red_npvpq = R.npvpq;

@@ -76,6 +76,7 @@ def _load():
         "grid_inject_barrier_fault": (st, [vp, vp]),
         "inj_ybus_noalloc": (st, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "grid_set_bus_types": (st, [vp, vp, vp]),
+        "pf_debug_fail_allocations": (st, [i32]),
         "jac_reduced_info": (st, [vp, pi32, pi32, ctypes.POINTER(ctypes.c_int64)]),
         "jac_reduced_pattern": (st, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "jac_reduced": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
@@ -356,6 +357,12 @@ def grid_trace_read(grid, cap=1 << 16):
     n = ctypes.c_int32()
     _check(_lib.grid_trace_read(grid.handle, buf, cap, ctypes.byref(n)), "grid_trace_read")
     return [(kernel_name(buf[i].kernel), float(buf[i].ms)) for i in range(n.value)]
+
+
+def debug_fail_allocations(after):
+    """Test hook: the next `after` device allocations succeed, later ones fail
+    (PF_ENOMEM); -1 turns it off."""
+    _check(_lib.pf_debug_fail_allocations(int(after)), "pf_debug_fail_allocations")
 
 
 # --------------------------------------------------- reduced Jacobian --

@@ -329,3 +329,36 @@ def test_elementwise_evaluations_overlap_on_two_streams(pf):
     for k in range(2):
         for a, b in zip(outs[k], ref[k]):
             assert torch.equal(a, b)
+
+
+def test_allocation_failures_are_reported_and_released(pf):
+    """Simulated device-allocation failures at every point of grid, batch and
+    reduced-system set-up: each call reports PF_ENOMEM (or succeeds when the
+    failure comes after it), nothing stays half-built, and the library works
+    normally once the hook is off."""
+    import torch
+    gr = random_grid(400, 560, 81)
+    vm, va = random_state(400, 81)
+    bt = np.ones(400, np.int32)
+    bt[0] = 3
+    try:
+        for after in range(0, 60, 3):
+            pf.debug_fail_allocations(after)
+            try:
+                grid = pf.ybus_build(gr)
+                batch = pf.batch_create(grid, 2, np.array([-1, 3], np.int32))
+                pf.grid_set_bus_types(grid, bt)
+                P, Q = np.zeros(400), np.zeros(400)
+                J = np.zeros(grid.nnzJ)
+                pf.eval_host(grid, 1, vm, va, P, Q, J)
+                z = torch.zeros(400, dtype=torch.float64, device="cuda")
+                pf.powerflow_newton(grid, 1, _d(vm), _d(va), z, z, tol=1e-10, max_iter=0)
+            except pf.PfError as e:
+                assert e.status == pf.PF_ENOMEM, (after, e)
+    finally:
+        pf.debug_fail_allocations(-1)
+    check_against_oracle(pf, gr, vm, va)
+    grid = pf.ybus_build(gr)
+    pf.grid_set_bus_types(grid, bt)
+    assert pf.jac_reduced_info(grid)[0] == 399 + int((bt == 1).sum())
+    torch.cuda.synchronize()
