@@ -232,10 +232,12 @@ SWEEP_SIZES = (14, 118, 300, 1354, 2736, 9241, 25000, 70000, 82000, 164000, 4100
 
 
 def _size_sweep(torch, pfgrid, synth, steps):
-    """Single evaluations (injections + Jacobian) by both methods on synthetic
-    grids with the bus counts of the paper's cases (branches = 1.32 x buses,
-    as in the 250k / 330k workload), L2 flushed between steps, and the time
-    of each relative to the 118-bus grid (the paper's complexity study)."""
+    """Single evaluations by both methods on synthetic grids with the bus
+    counts of the paper's cases (branches = 1.32 x buses, as in the 250k /
+    330k workload), L2 flushed between steps: injections + Jacobian,
+    injections alone, and the Ybus method's phasor launch (the steps of the
+    paper's per-case table that separate launches expose), with the time of
+    each relative to the 118-bus grid (the paper's complexity study)."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
     flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
     rows = []
@@ -250,17 +252,24 @@ def _size_sweep(torch, pfgrid, synth, steps):
         Q = torch.empty_like(P)
         J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
         row = {"nb": nb, "nl": nl}
-        for name, fn in (("elementwise", pfgrid.jac_elementwise), ("ybus", pfgrid.jac_ybus)):
-            f = lambda: fn(grid, vmd, vad, P, Q, J)
+        for name, fn, jac in (("elementwise", pfgrid.jac_elementwise, True), ("ybus", pfgrid.jac_ybus, True),
+                              ("elementwise_inj", pfgrid.inj_elementwise, False), ("ybus_inj", pfgrid.inj_ybus, False)):
+            f = (lambda: fn(grid, vmd, vad, P, Q, J)) if jac else (lambda: fn(grid, vmd, vad, P, Q))
             for _ in range(3):
                 f()
             t = time_loop(torch, f, steps, flush, "sweep_%s" % name)
             row["%s_us" % name] = 1e3 * sum(t) / len(t)   # mean: one event pair resolves about 1 us
+        # the Ybus method's phasor step alone (its own launch), from the tracer
+        pfgrid.grid_trace_enable(grid, 4 * steps + 16)
+        time_loop(torch, lambda: pfgrid.inj_ybus(grid, vmd, vad, P, Q), steps, flush, "sweep_traced")
+        ph = [ms for k, ms in pfgrid.grid_trace_read(grid) if k == "phasor"]
+        pfgrid.grid_trace_enable(grid, 0)
+        row["ybus_phasor_us_traced"] = 1e3 * sum(ph) / max(len(ph), 1)
         pfgrid.grid_check_error(grid)
         rows.append(row)
     base = next(r for r in rows if r["nb"] == 118)
     for r in rows:
-        for name in ("elementwise", "ybus"):
+        for name in ("elementwise", "ybus", "elementwise_inj", "ybus_inj"):
             r["%s_ratio_to_118" % name] = r["%s_us" % name] / base["%s_us" % name]
     return rows
 
