@@ -6,9 +6,12 @@
 //
 // Work items are (scenario, window) pairs in scenario-major order, handed to
 // the resident CTAs round-robin, so the CTAs active at any time share a few
-// scenarios' phasors in L2.  Phase 1 forms every scenario's phasors; a grid
-// barrier follows; phase 2 evaluates.  The adjoint adds a residual phase and a
-// second barrier.
+// scenarios' phasors in L2.  Phase 1 forms every scenario's phasors (flat
+// chunks of blockDim.x buses, every lane busy); a grid barrier follows; phase
+// 2 evaluates.  The adjoint adds a residual phase and a second barrier; for a
+// small batch (about one item per SM) it instead forms each window's own and
+// ghost phasors inside the residual phase (ghost mode, as k_elementwise.cu
+// does) and keeps only the second barrier.
 //
 // Scenario s may remove one branch (outage).  Its two terminals are masked
 // (they contribute nothing) and the self sums of its end buses lose the
