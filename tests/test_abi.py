@@ -72,9 +72,10 @@ def test_oversized_grid_rejected(pf):
     assert st == 7
 
 
-@pytest.mark.parametrize("target", [0, 760])
+@pytest.mark.parametrize("target", [0, 760, 3040])
 @pytest.mark.parametrize("window", [128, 256])
-@pytest.mark.parametrize("case", ["three_bus_plus", "parallel_star", "single_bus", "empty", "c1", "c2", "c3", "c4"])
+@pytest.mark.parametrize("case", ["three_bus_plus", "parallel_star", "single_bus", "empty", "c1", "c2", "c3", "c4",
+                                  "c5", "c6"])
 def test_layout_selfcheck(pf, case, window, target):
     """Every index the kernels read or write stays inside its buffer (host check)."""
     from gridcases import make_grid
