@@ -54,7 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
     ap.add_argument("--profile-workload",
-                    choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra", "newton", "sweep"],
+                    choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra", "newton", "sweep",
+                             "study"],
                     help="run only this batched/adjoint workload (few launches, for profilers) and exit")
     return ap.parse_args(argv)
 
@@ -206,7 +207,7 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
     """The batched and adjoint workloads, each timed from a CUDA-graph replay
     (inputs larger than L2 for the batched ones, so no flush is needed).
     `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced", "ultra",
-    "newton", "sweep"."""
+    "newton", "sweep", "study"."""
     out = {}
     if only in (None, "n1"):
         out.update(_n1_workload(torch, pfgrid, synth, reps))
@@ -219,12 +220,38 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
         out["reduced_newton_csc_70k"] = _reduced_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "ultra"):
         out["single_410k"] = _single_workload(torch, pfgrid, synth, 6, max(reps, 20))
+    if only in (None, "study"):
+        out["two_step_study_70k"] = _study_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "sweep"):
         out["size_sweep"] = _size_sweep(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "newton"):
         out["newton_powerflow"] = {"2k": _newton_workload(torch, pfgrid, synth, 1),
                                    "10k": _newton_workload(torch, pfgrid, synth, 3)}
     return out
+
+
+def _study_workload(torch, pfgrid, synth, steps):
+    """The paper's two-step structure of the element-wise method (phasors,
+    evaluation into an intermediate, then a gather or an atomic copy-add
+    assembly) against the fused kernel, on the 70k-bus grid, L2 flushed."""
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    w = synth.workload(WORKLOAD)
+    grid = pfgrid.ybus_build(w)
+    vm, va = dev(w["vm"][0]), dev(w["va"][0])
+    P = torch.empty(w["nb"], dtype=torch.float64, device="cuda")
+    Q = torch.empty_like(P)
+    J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, f in (("fused", lambda: pfgrid.jac_elementwise(grid, vm, va, P, Q, J)),
+                    ("two_step_gather", lambda: pfgrid.jac_elementwise_study(grid, 0, vm, va, P, Q, J)),
+                    ("two_step_copy_add", lambda: pfgrid.jac_elementwise_study(grid, 1, vm, va, P, Q, J))):
+        for _ in range(3):
+            f()
+        t = time_loop(torch, f, steps, flush, "study_" + name)
+        res["%s_us" % name] = 1e3 * sum(t) / len(t)
+    pfgrid.grid_check_error(grid)
+    return res
 
 
 # bus counts of the paper's test cases (Table VII and the replicated grids of Sec. V-F)

@@ -416,6 +416,20 @@ pf_status powerflow_newton(pf_grid *grid, int32_t method, double *vm, double *va
                            pf_stream stream);
 
 /*
+ * Study entry point (the paper's two-step structure, Sec. IV-C, for
+ * comparison with jac_elementwise): the phasor step, then K_t and G_t of every
+ * terminal into a grid-owned intermediate, then the assembly by `strategy`:
+ * 0 gather (one thread per bus, its terminals in order; deterministic) or
+ * 1 copy-add (bus constants, then one thread per terminal adding with
+ * floating-point atomics; the addition order, hence the last bits, vary from
+ * run to run).  Same arguments and results (within rounding) as
+ * jac_elementwise, P and Q required.  Uses the grid's phasor workspace and
+ * intermediate: calls on one grid must not overlap.
+ */
+pf_status jac_elementwise_study(pf_grid *grid, int32_t strategy, const double *vm, const double *va, double *P,
+                                double *Q, double *J, pf_stream stream);
+
+/*
  * Test hook for the error paths: after `after` more device allocations made
  * through the library's buffer owner succeed, every later one fails (no
  * cudaMalloc is attempted) and the call reports PF_ENOMEM, releasing what it

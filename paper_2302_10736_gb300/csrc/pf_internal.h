@@ -200,6 +200,8 @@ struct Grid {
     double4_32a *ph_u = nullptr;   // [nb] {cos, sin, v, 1/v}
     double2 *ph_v = nullptr;       // [nb] V = v e^{j theta}
     int *err = nullptr;            // device error word
+    // the two-step study path (k_study.cu): K_t, G_t of every sorted terminal
+    double4_32a *ts_KG = nullptr;
     // eval_host staging (lazy)
     double *st_vm = nullptr, *st_va = nullptr, *st_P = nullptr, *st_Q = nullptr, *st_J = nullptr;
     // reduced Newton Jacobian (grid_set_bus_types): CSC pattern, the canonical J

@@ -77,6 +77,7 @@ def _load():
         "inj_ybus_noalloc": (st, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "grid_set_bus_types": (st, [vp, vp, vp]),
         "pf_debug_fail_allocations": (st, [i32]),
+        "jac_elementwise_study": (st, [vp, i32, vp, vp, vp, vp, vp, vp]),
         "jac_reduced_info": (st, [vp, pi32, pi32, ctypes.POINTER(ctypes.c_int64)]),
         "jac_reduced_pattern": (st, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "jac_reduced": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
@@ -357,6 +358,14 @@ def grid_trace_read(grid, cap=1 << 16):
     n = ctypes.c_int32()
     _check(_lib.grid_trace_read(grid.handle, buf, cap, ctypes.byref(n)), "grid_trace_read")
     return [(kernel_name(buf[i].kernel), float(buf[i].ms)) for i in range(n.value)]
+
+
+def jac_elementwise_study(grid, strategy, vm, va, P, Q, J, stream=None):
+    """The paper's two-step element-wise structure (strategy 0 gather, 1 copy-add)."""
+    nb = grid.nb
+    _check(_lib.jac_elementwise_study(grid.handle, int(strategy), _dptr(vm, "vm", nb), _dptr(va, "va", nb),
+                                      _dptr(P, "P", nb), _dptr(Q, "Q", nb), _dptr(J, "J", grid.nnzJ), _stream(stream)),
+           "jac_elementwise_study")
 
 
 def debug_fail_allocations(after):

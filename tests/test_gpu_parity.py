@@ -362,3 +362,40 @@ def test_allocation_failures_are_reported_and_released(pf):
     pf.grid_set_bus_types(grid, bt)
     assert pf.jac_reduced_info(grid)[0] == 399 + int((bt == 1).sum())
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("strategy", [0, 1])
+@pytest.mark.parametrize("case", ["three_bus_plus", "parallel_star", "c1"])
+def test_two_step_study_strategies(pf, strategy, case):
+    """The paper's two-step structure (evaluation into an intermediate, then a
+    gather or an atomic copy-add) gives the oracle's results; the gather is
+    bitwise reproducible."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    if case == "three_bus_plus":
+        gr, vm, va = CASES["three_bus_plus"]()
+    elif case == "parallel_star":
+        br = [(0, 1 + (i % 5), 1.0 + 0.1 * i, -10.0, 0.01, 1.0, 0.0) for i in range(40)]
+        gr = make_grid(7, br, shunts={0: (0.02, -0.01)})
+        vm, va = random_state(7, 91)
+    else:
+        gr = synth.workload(1)
+        vm, va = gr["vm"][0], gr["va"][0]
+    grid = pf.ybus_build(gr)
+    Y = oracle.ybus(gr)
+    Pr, Qr, Jr = oracle.elementwise(gr, vm, va, Y)
+    jrp, jci = oracle.jac_pattern(Y)
+    outs = []
+    for _ in range(2):
+        P = torch.full((grid.nb,), np.nan, dtype=torch.float64, device="cuda")
+        Q = torch.full_like(P, np.nan)
+        J = torch.full((grid.nnzJ,), np.nan, dtype=torch.float64, device="cuda")
+        pf.jac_elementwise_study(grid, strategy, _d(vm), _d(va), P, Q, J)
+        torch.cuda.synchronize()
+        outs.append((P.cpu().numpy(), Q.cpu().numpy(), J.cpu().numpy()))
+    P, Q, J = outs[0]
+    errs = [relerr(P, Pr), relerr(Q, Qr)] + [relerr(a, b) for a, b in zip(blocks(J, jci, grid.nb, Y.nnz),
+                                                                         blocks(Jr, jci, grid.nb, Y.nnz))]
+    assert max(errs) <= TOL, errs
+    if strategy == 0:
+        assert all(np.array_equal(a, b) for a, b in zip(outs[0], outs[1]))
