@@ -233,7 +233,8 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
 def _study_workload(torch, pfgrid, synth, steps):
     """The paper's two-step structure of the element-wise method (phasors,
     evaluation into an intermediate, then a gather or an atomic copy-add
-    assembly) against the fused kernel, on the 70k-bus grid, L2 flushed."""
+    assembly) against the fused kernel, and its interleaved-vs-separate
+    voltage storage for the Ybus injections, on the 70k-bus grid, L2 flushed."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
     flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
     w = synth.workload(WORKLOAD)
@@ -246,6 +247,12 @@ def _study_workload(torch, pfgrid, synth, steps):
     for name, f in (("fused", lambda: pfgrid.jac_elementwise(grid, vm, va, P, Q, J)),
                     ("two_step_gather", lambda: pfgrid.jac_elementwise_study(grid, 0, vm, va, P, Q, J)),
                     ("two_step_copy_add", lambda: pfgrid.jac_elementwise_study(grid, 1, vm, va, P, Q, J))):
+        for _ in range(3):
+            f()
+        t = time_loop(torch, f, steps, flush, "study_" + name)
+        res["%s_us" % name] = 1e3 * sum(t) / len(t)
+    for name, sep in (("ybus_inj_interleaved", 0), ("ybus_inj_separate", 1)):
+        f = lambda: pfgrid.inj_ybus_study(grid, sep, vm, va, P, Q)
         for _ in range(3):
             f()
         t = time_loop(torch, f, steps, flush, "study_" + name)

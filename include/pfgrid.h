@@ -430,6 +430,17 @@ pf_status jac_elementwise_study(pf_grid *grid, int32_t strategy, const double *v
                                 double *Q, double *J, pf_stream stream);
 
 /*
+ * Study entry point (the paper's storage comparison, Sec. IV-B.1): the Ybus
+ * method's injections with the complex voltages stored interleaved
+ * (separate = 0, re/im pairs) or as separate real and imaginary arrays
+ * (separate = 1): a phasor launch and a one-row-per-thread CSR SpMV, the
+ * arithmetic identical.  Same arguments and results as inj_ybus.  Uses a
+ * grid-owned voltage buffer: calls on one grid must not overlap.
+ */
+pf_status inj_ybus_study(pf_grid *grid, int32_t separate, const double *vm, const double *va, double *P, double *Q,
+                         pf_stream stream);
+
+/*
  * Test hook for the error paths: after `after` more device allocations made
  * through the library's buffer owner succeed, every later one fails (no
  * cudaMalloc is attempted) and the call reports PF_ENOMEM, releasing what it

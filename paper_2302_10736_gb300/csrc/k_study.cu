@@ -17,6 +17,13 @@
 //              contributions with floating-point atomics - the order of the
 //              additions varies from run to run.
 // Only the study entry point jac_elementwise_study uses these kernels.
+//
+// The paper also compares storing complex voltages interleaved (re, im pairs)
+// against separate real and imaginary arrays for its Ybus power calculation
+// (Sec. IV-B.1, Table I).  inj_ybus_study runs the phasor step and a
+// one-row-per-thread CSR SpMV with either layout, the arithmetic otherwise
+// identical.
+#include "fastmath.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
 
@@ -129,11 +136,81 @@ __global__ void __launch_bounds__(256) k_ts_atomic(int T, int nnz, const int *__
     atomicAdd(&Q[o], kg.y);
 }
 
+// V = v e^{j theta} as interleaved pairs (SEP = false) or separate arrays
+template <bool SEP>
+__global__ void __launch_bounds__(256) k_vs_phasor(int nb, const double *__restrict__ vm,
+                                                   const double *__restrict__ va, const double2 *__restrict__ trig,
+                                                   double *__restrict__ V)
+{
+    __shared__ double2 tab[kTrigN];
+    for (int k = threadIdx.x; k < kTrigN; k += blockDim.x)
+        tab[k] = trig[(blockIdx.x % kTrigCopies) * kTrigN + k];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    double s, c;
+    fast_sincos(va[i], tab, &s, &c);
+    const double v = vm[i];
+    if (SEP) {
+        V[i] = v * c;
+        V[nb + i] = v * s;
+    } else {
+        reinterpret_cast<double2 *>(V)[i] = make_double2(v * c, v * s);
+    }
+}
+
+// S_i = V_i conj(sum_j Y_ij V_j), one row per thread
+template <bool SEP>
+__global__ void __launch_bounds__(256) k_vs_spmv(int nb, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                 const double2 *__restrict__ Y, const double *__restrict__ V,
+                                                 double *__restrict__ P, double *__restrict__ Q)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const double2 *V2 = reinterpret_cast<const double2 *>(V);
+    double Ir = 0.0, Ii = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        const int j = ci[e];
+        const double2 y = Y[e];
+        const double vr = SEP ? V[j] : V2[j].x, vi = SEP ? V[nb + j] : V2[j].y;
+        Ir = fma(y.x, vr, Ir);
+        Ir = fma(-y.y, vi, Ir);
+        Ii = fma(y.x, vi, Ii);
+        Ii = fma(y.y, vr, Ii);
+    }
+    const double vr = SEP ? V[i] : V2[i].x, vi = SEP ? V[nb + i] : V2[i].y;
+    P[i] = fma(vr, Ir, vi * Ii);
+    Q[i] = fma(vi, Ir, -vr * Ii);
+}
+
 }  // namespace
 
 }  // namespace pf
 
 using namespace pf;
+
+PF_API pf_status inj_ybus_study(pf_grid *grid, int32_t separate, const double *vm, const double *va, double *P,
+                                double *Q, pf_stream stream)
+{
+    if (!grid) return set_error(PF_EINVAL, "inj_ybus_study: grid is NULL");
+    Grid *g = &grid->g;
+    if (separate != 0 && separate != 1) return set_error(PF_EINVAL, "inj_ybus_study: separate must be 0 or 1");
+    if (g->nb == 0) return PF_OK;
+    if (!vm || !va || !P || !Q) return set_error(PF_EINVAL, "inj_ybus_study: NULL argument");
+    const int nb = g->nb;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!g->vs_V) PF_CUDA(g->arena.alloc(&g->vs_V, 2 * (size_t)nb));
+    const int blocks = (nb + 255) / 256;
+    if (separate) {
+        k_vs_phasor<true><<<blocks, 256, 0, s>>>(nb, vm, va, trig_table(), g->vs_V);
+        k_vs_spmv<true><<<blocks, 256, 0, s>>>(nb, g->rp, g->ci, g->yv, g->vs_V, P, Q);
+    } else {
+        k_vs_phasor<false><<<blocks, 256, 0, s>>>(nb, vm, va, trig_table(), g->vs_V);
+        k_vs_spmv<false><<<blocks, 256, 0, s>>>(nb, g->rp, g->ci, g->yv, g->vs_V, P, Q);
+    }
+    PF_CUDA(cudaGetLastError());
+    return PF_OK;
+}
 
 PF_API pf_status jac_elementwise_study(pf_grid *grid, int32_t strategy, const double *vm, const double *va,
                                        double *P, double *Q, double *J, pf_stream stream)

@@ -202,6 +202,7 @@ struct Grid {
     int *err = nullptr;            // device error word
     // the two-step study path (k_study.cu): K_t, G_t of every sorted terminal
     double4_32a *ts_KG = nullptr;
+    double *vs_V = nullptr;   // [2 nb] voltages of the storage-layout study (inj_ybus_study)
     // eval_host staging (lazy)
     double *st_vm = nullptr, *st_va = nullptr, *st_P = nullptr, *st_Q = nullptr, *st_J = nullptr;
     // reduced Newton Jacobian (grid_set_bus_types): CSC pattern, the canonical J

@@ -78,6 +78,7 @@ def _load():
         "grid_set_bus_types": (st, [vp, vp, vp]),
         "pf_debug_fail_allocations": (st, [i32]),
         "jac_elementwise_study": (st, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "inj_ybus_study": (st, [vp, i32, vp, vp, vp, vp, vp]),
         "jac_reduced_info": (st, [vp, pi32, pi32, ctypes.POINTER(ctypes.c_int64)]),
         "jac_reduced_pattern": (st, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "jac_reduced": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
@@ -366,6 +367,13 @@ def jac_elementwise_study(grid, strategy, vm, va, P, Q, J, stream=None):
     _check(_lib.jac_elementwise_study(grid.handle, int(strategy), _dptr(vm, "vm", nb), _dptr(va, "va", nb),
                                       _dptr(P, "P", nb), _dptr(Q, "Q", nb), _dptr(J, "J", grid.nnzJ), _stream(stream)),
            "jac_elementwise_study")
+
+
+def inj_ybus_study(grid, separate, vm, va, P, Q, stream=None):
+    """Ybus injections with interleaved (0) or separate (1) voltage storage."""
+    nb = grid.nb
+    _check(_lib.inj_ybus_study(grid.handle, int(separate), _dptr(vm, "vm", nb), _dptr(va, "va", nb),
+                               _dptr(P, "P", nb), _dptr(Q, "Q", nb), _stream(stream)), "inj_ybus_study")
 
 
 def debug_fail_allocations(after):

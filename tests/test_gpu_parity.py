@@ -399,3 +399,24 @@ def test_two_step_study_strategies(pf, strategy, case):
     assert max(errs) <= TOL, errs
     if strategy == 0:
         assert all(np.array_equal(a, b) for a, b in zip(outs[0], outs[1]))
+
+
+@pytest.mark.parametrize("separate", [0, 1])
+def test_storage_layout_study(pf, separate):
+    """Both voltage layouts of the storage study give the oracle's injections,
+    and the same bits as each other (identical arithmetic)."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    vm, va = w["vm"][0], w["va"][0]
+    grid = pf.ybus_build(w)
+    Pr, Qr = oracle.inj_sparse(oracle.ybus(w), vm, va)
+    res = []
+    for sep in (separate, 1 - separate):
+        P = torch.full((grid.nb,), np.nan, dtype=torch.float64, device="cuda")
+        Q = torch.full_like(P, np.nan)
+        pf.inj_ybus_study(grid, sep, _d(vm), _d(va), P, Q)
+        torch.cuda.synchronize()
+        res.append((P.cpu().numpy(), Q.cpu().numpy()))
+    assert relerr(res[0][0], Pr) <= TOL and relerr(res[0][1], Qr) <= TOL
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
