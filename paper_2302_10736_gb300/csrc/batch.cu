@@ -88,10 +88,10 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
         HostEw F;
         const int target = (nsm + nscen - 1) / nscen;
         if (host_ew(g->topo, 256, F, E.tfac, target) == PF_OK && F.nwin > E.nwin && fits(F)) E = std::move(F);
-        // latency-bound: the adjoint forms each window's phasors itself (with
-        // its ghost buses) instead of a separate phase and grid barrier
-        ghost = ew_smem_plan(E.max_nbus, E.max_nt, 0, false, E.max_nph).total + kTrigN * sizeof(double2) <=
-                kMaxSmem;
+        // latency-bound: the adjoint keeps each item on one CTA (k_adj1), which
+        // forms its window's phasors itself (with its ghost buses) instead of a
+        // separate phase and grid barrier
+        ghost = adj1_smem_plan(E.max_nbus, E.max_nt, E.max_nph).total <= kMaxSmem;
     }
 #ifdef PF_SELFCHECK
     if (pf_status hs = host_selfcheck(g->topo, E)) {

@@ -8,10 +8,11 @@
 // the resident CTAs round-robin, so the CTAs active at any time share a few
 // scenarios' phasors in L2.  Phase 1 forms every scenario's phasors (flat
 // chunks of blockDim.x buses, every lane busy); a grid barrier follows; phase
-// 2 evaluates.  The adjoint adds a residual phase and a second barrier; for a
-// small batch (about one item per SM) it instead forms each window's own and
-// ghost phasors inside the residual phase (ghost mode, as k_elementwise.cu
-// does) and keeps only the second barrier.
+// 2 evaluates.  The adjoint (k_adj) adds a residual phase and a second
+// barrier.  A small batch (about one item per SM) runs k_adj1 instead: one
+// item per CTA, each window's own and ghost phasors formed inside the residual
+// phase (as k_elementwise.cu does), one grid barrier, and everything the
+// gradient phase needs kept in shared memory across it.
 //
 // Scenario s may remove one branch (outage).  Its two terminals are masked
 // (they contribute nothing) and the self sums of its end buses lose the
@@ -279,24 +280,99 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
 
 // ------------------------------------------------------------ adjoint ----
 
+// Sum over the 32 lanes of a warp; lane 0's result has a fixed association
+// order, so the sums below are the same from run to run.
+__device__ __forceinline__ double warp_sum(double x)
+{
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+}
+
+// The loss terms spq[0 .. nbus) of one window, summed by warp 0.
+__device__ __forceinline__ void window_loss(const double *spq, int nbus, double *out)
+{
+    if (threadIdx.x < 32) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < nbus; b += 32) acc += spq[b];
+        acc = warp_sum(acc);
+        if (threadIdx.x == 0) *out = acc;
+    }
+}
+
+// The loss of every scenario from its window partial sums, one warp per
+// scenario (after the last grid barrier).
+__device__ __forceinline__ void batch_loss(const BatchArgs &a)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < a.S; s += nwarp) {
+        double acc = 0.0;
+        for (int w = lane; w < a.nwin; w += 32) acc += a.lpart[s * a.nwin + w];
+        acc = warp_sum(acc);
+        if (lane == 0) a.L[s] = acc;
+    }
+}
+
+// Branch-parameter gradients (after the last grid barrier): one thread per
+// branch summing the scenarios in ascending order, from the phasors V and the
+// residuals r of every scenario in global memory.
+__device__ __forceinline__ void batch_branch_grads(const BatchArgs &a)
+{
+    const int TB = blockDim.x;
+    for (int l = blockIdx.x * TB + threadIdx.x; l < a.nl; l += gridDim.x * TB) {
+        const int2 hk = a.br_hk[l];
+        const int h = hk.x, k = hk.y;
+        const double g = a.pg[l], bb = a.pb[l], bsh = a.pbsh[l];
+        const double4_32a aux = a.br_aux[l];   // 1/m, cos phi, sin phi (formed with the constants)
+        const double im = aux.x, im2 = im * im, cphi = aux.y, sphi = aux.z;
+        const double c1r = g, c1i = -(bb + 0.5 * bsh);   // conj(y_s + j b_sh / 2)
+        double agg = 0.0, agb = 0.0, agsh = 0.0, agt = 0.0;
+        for (int s = 0; s < a.S; ++s) {
+            if (a.sc[s].l == l) continue;   // removed in this scenario
+            const long long sb = (long long)s * a.nb;
+            const double2 Vh = a.V[sb + h], Vk = a.V[sb + k];
+            const double2 rh = a.r[sb + h], rk = a.r[sb + k];
+            const double vh2 = fma(Vh.x, Vh.x, Vh.y * Vh.y), vk2 = fma(Vk.x, Vk.x, Vk.y * Vk.y);
+            const double Wr = fma(Vh.x, Vk.x, Vh.y * Vk.y), Wi = fma(Vh.y, Vk.x, -Vh.x * Vk.y);
+            const double Br = fma(Wr, cphi, Wi * sphi) * im, Bi = fma(Wi, cphi, -Wr * sphi) * im;   // W e^{-j phi}/m
+            const double Ah = vh2 * im2;
+            const double zhr = Ah - Br, zhi = -Bi;     // dS_hk/dg
+            const double zkr = vk2 - Br, zki = Bi;     // dS_kh/dg
+            agg += fma(rh.x, zhr, rh.y * zhi) + fma(rk.x, zkr, rk.y * zki);
+            agb += fma(rh.x, zhi, -rh.y * zhr) + fma(rk.x, zki, -rk.y * zkr);   // <r, -j z>
+            agsh -= 0.5 * fma(rh.y, Ah, rk.y * vk2);
+            // dS_hk/dm = im (-2 Ah conj(y_s + j b_sh/2) + conj(y_s) B), dS_kh/dm = im conj(y_s) conj(B)
+            const double dhr = im * (-2.0 * Ah * c1r + fma(g, Br, bb * Bi));
+            const double dhi = im * (-2.0 * Ah * c1i + fma(g, Bi, -bb * Br));
+            const double dkr = im * fma(g, Br, -bb * Bi);
+            const double dki = im * fma(-g, Bi, -bb * Br);
+            agt += fma(rh.x, dhr, rh.y * dhi) + fma(rk.x, dkr, rk.y * dki);
+        }
+        a.gg[l] = agg;
+        a.gb[l] = agb;
+        a.gbsh[l] = agsh;
+        a.gtap[l] = agt;
+    }
+}
+
+// Throughput adjoint (many items per CTA): every scenario's phasors, grid
+// barrier, injections and residuals, grid barrier, gradients.
 __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
-    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false, a.ghost ? a.max_nph : 0);
+    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
     double2 *skg = reinterpret_cast<double2 *>(smem + sp.kg);
     double *spq = reinterpret_cast<double *>(smem + sp.pq);
-    double2 *sV = reinterpret_cast<double2 *>(smem + sp.ph);   // window phasor table (ghost mode)
     double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x;
     const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
     for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
-    if (!a.ghost) {   // every scenario's phasors first, visible to all CTAs after the barrier
-        batch_phasors(a, tab, true);
-        if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
-    }
+    // every scenario's phasors first, visible to all CTAs after the barrier
+    batch_phasors(a, tab, true);
+    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     const long long nitem = (long long)a.S * a.nwin;
     // ---- phase 2: injections, residuals and per-window loss partial sums ----
@@ -308,31 +384,10 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         const long long sb = (long long)s * a.nb;
         __syncthreads();
         batch_window_meta(a, sc, b0, b1, t0, sbm, syd);
-        if (a.ghost) {
-            // phasors of the window's own and ghost buses (slot j's bus in
-            // slotbus); the own buses' phasors also go to U, V for phase 3
-            const int *sbus = a.slotbus + (long long)w * a.max_nph;
-            const int nph = a.desc[2 * w + 1].z;
-            for (int j = tid; j < nph; j += TB) {
-                const int o = sbus[j];
-                double sn, cs;
-                fast_sincos(a.va[sb + o], tab, &sn, &cs);
-                const double v = a.vm[sb + o];
-                const double2 V = make_double2(v * cs, v * sn);
-                sV[j] = V;
-                if (j < nbus) {
-                    a.U[sb + o] = make_double4_32a(cs, sn, v, fast_rcp(v));
-                    a.V[sb + o] = V;
-                }
-            }
-        }
-        __syncthreads();
         for (int i = tid; i < nt; i += TB) {
             const int p = t0 + i;
             const double2 yc = a.tcoup[p];
-            const int q = a.tnbr[p].x, o = a.town[p];
-            const double2 Vo = a.ghost ? sV[o - b0] : a.V[sb + o];
-            const double2 Vq = a.ghost ? sV[a.tloc[p].x] : a.V[sb + q];
+            const double2 Vo = a.V[sb + a.town[p]], Vq = a.V[sb + a.tnbr[p].x];
             const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
             double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);
             if (p == sc.ph || p == sc.pk) Kr = Ki = 0.0;
@@ -357,11 +412,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
             spq[b] = fma(wp * dP, dP, wq * dQ * dQ);
         }
         __syncthreads();
-        if (tid == 0) {   // fixed-order partial sum of the window's loss terms
-            double acc = 0.0;
-            for (int b = 0; b < nbus; ++b) acc += spq[b];
-            a.lpart[(long long)s * a.nwin + w] = acc;
-        }
+        window_loss(spq, nbus, a.lpart + (long long)s * a.nwin + w);
     }
     if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
@@ -427,50 +478,160 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         }
     }
 
-    // ---- phase 3b: branch-parameter gradients, scenarios summed in order ----
-    if (a.gg) {
-        for (int l = blockIdx.x * TB + tid; l < a.nl; l += gridDim.x * TB) {
-            const int2 hk = a.br_hk[l];
-            const int h = hk.x, k = hk.y;
-            const double g = a.pg[l], bb = a.pb[l], bsh = a.pbsh[l];
-            const double4_32a aux = a.br_aux[l];   // 1/m, cos phi, sin phi (formed with the constants)
-            const double im = aux.x, im2 = im * im, cphi = aux.y, sphi = aux.z;
-            const double c1r = g, c1i = -(bb + 0.5 * bsh);   // conj(y_s + j b_sh / 2)
-            double agg = 0.0, agb = 0.0, agsh = 0.0, agt = 0.0;
-            for (int s = 0; s < a.S; ++s) {
-                if (a.sc[s].l == l) continue;   // removed in this scenario
-                const long long sb = (long long)s * a.nb;
-                const double2 Vh = a.V[sb + h], Vk = a.V[sb + k];
-                const double2 rh = a.r[sb + h], rk = a.r[sb + k];
-                const double vh2 = fma(Vh.x, Vh.x, Vh.y * Vh.y), vk2 = fma(Vk.x, Vk.x, Vk.y * Vk.y);
-                const double Wr = fma(Vh.x, Vk.x, Vh.y * Vk.y), Wi = fma(Vh.y, Vk.x, -Vh.x * Vk.y);
-                const double Br = fma(Wr, cphi, Wi * sphi) * im, Bi = fma(Wi, cphi, -Wr * sphi) * im;   // W e^{-j phi}/m
-                const double Ah = vh2 * im2;
-                const double zhr = Ah - Br, zhi = -Bi;     // dS_hk/dg
-                const double zkr = vk2 - Br, zki = Bi;     // dS_kh/dg
-                agg += fma(rh.x, zhr, rh.y * zhi) + fma(rk.x, zkr, rk.y * zki);
-                agb += fma(rh.x, zhi, -rh.y * zhr) + fma(rk.x, zki, -rk.y * zkr);   // <r, -j z>
-                agsh -= 0.5 * fma(rh.y, Ah, rk.y * vk2);
-                // dS_hk/dm = im (-2 Ah conj(y_s + j b_sh/2) + conj(y_s) B), dS_kh/dm = im conj(y_s) conj(B)
-                const double dhr = im * (-2.0 * Ah * c1r + fma(g, Br, bb * Bi));
-                const double dhi = im * (-2.0 * Ah * c1i + fma(g, Bi, -bb * Br));
-                const double dkr = im * fma(g, Br, -bb * Bi);
-                const double dki = im * fma(-g, Bi, -bb * Br);
-                agt += fma(rh.x, dhr, rh.y * dhi) + fma(rk.x, dkr, rk.y * dki);
+    // ---- phase 3b: branch-parameter gradients; the loss of every scenario ----
+    if (a.gg) batch_branch_grads(a);
+    if (a.L) batch_loss(a);
+}
+
+// Small-batch adjoint: one (scenario, window) item per CTA (the launch has a
+// CTA for every item) and one grid barrier.  Before the barrier the item
+// forms the phasors of its own and ghost buses (slot j's bus in slotbus),
+// both flows of every terminal from the same W = V_o conj(V_q) (o owns the
+// terminal): K_t = conj(Yc_t) W and the mirror's K_m = conj(Yc_m) conj(W),
+// then its buses' injections and residuals.  All of it stays in shared
+// memory, so after the barrier the item reads back only its ghost buses'
+// residuals (one L2 round trip) before the state gradients
+//   dL/dtheta_o = sum_t <r_o, j K_t> + <r_q, -j K_m>
+//   dL/dv_o     = <r_o, 2 v_o conj(Yd_o)> + (sum_t <r_o, K_t> + <r_q, K_m>) / v_o.
+__global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
+{
+    extern __shared__ __align__(16) char smem[];
+    const Adj1Smem sp = adj1_smem_plan(a.max_nbus, a.max_nt, a.max_nph);
+    int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
+    double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
+    double2 *sK = reinterpret_cast<double2 *>(smem + sp.K);
+    double2 *sM = reinterpret_cast<double2 *>(smem + sp.M);
+    int2 *sloc = reinterpret_cast<int2 *>(smem + sp.loc);   // per terminal: {owner slot, other-bus slot}
+    double *spq = reinterpret_cast<double *>(smem + sp.pq);
+    double2 *sV = reinterpret_cast<double2 *>(smem + sp.V);
+    double2 *sR = reinterpret_cast<double2 *>(smem + sp.R);
+    double2 *sW = reinterpret_cast<double2 *>(smem + sp.W);   // own buses: (v, 1/v)
+    int *sslot = reinterpret_cast<int *>(smem + sp.slot);
+    double2 *tab = reinterpret_cast<double2 *>(smem + sp.tab);
+    const int tid = threadIdx.x, TB = blockDim.x;
+    const bool has = (long long)blockIdx.x < (long long)a.S * a.nwin;   // CTA-uniform
+    int s = 0, w = 0, b0 = 0, nbus = 0, t0 = 0, nt = 0, nph = 0;
+    long long sb = 0;
+    if (has) {
+        s = (int)(blockIdx.x / a.nwin);
+        w = (int)(blockIdx.x % a.nwin);
+        const int4 d0 = a.desc[2 * w], d1 = a.desc[2 * w + 1];
+        b0 = d0.x;
+        nbus = d0.y;
+        t0 = d0.z;
+        nt = d0.w;
+        nph = d1.z;
+        sb = (long long)s * a.nb;
+        const ScenOut sc = a.sc[s];
+        const int *sbus = a.slotbus + (long long)w * a.max_nph;
+        const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
+        for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
+        batch_window_meta(a, sc, b0, b0 + nbus, t0, sbm, syd);
+        __syncthreads();
+        // ---- phasors of the own and ghost buses ----
+        for (int j = tid; j < nph; j += TB) {
+            const int o = sbus[j];
+            sslot[j] = o;
+            double sn, cs;
+            fast_sincos(a.va[sb + o], tab, &sn, &cs);
+            const double v = a.vm[sb + o];
+            const double2 V = make_double2(v * cs, v * sn);
+            sV[j] = V;
+            if (j < nbus) {
+                sW[j] = make_double2(v, fast_rcp(v));
+                a.V[sb + o] = V;   // for the branch-parameter gradients
             }
-            a.gg[l] = agg;
-            a.gb[l] = agb;
-            a.gbsh[l] = agsh;
-            a.gtap[l] = agt;
+        }
+        __syncthreads();
+        // ---- both flows of every terminal ----
+        for (int i = tid; i < nt; i += TB) {
+            const int p = t0 + i;
+            const double2 yc = a.tcoup[p], ym = a.tcoup[a.tmir[p]];
+            const int2 loc = make_int2(a.town[p] - b0, a.tloc[p].x);
+            const double2 Vo = sV[loc.x], Vq = sV[loc.y];
+            const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);   // V_o conj(V_q)
+            double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);                 // K_t
+            double Mr = fma(ym.x, Wr, -ym.y * Wi), Mi = fma(-ym.x, Wi, -ym.y * Wr);               // K_m
+            if (p == sc.ph || p == sc.pk) Kr = Ki = Mr = Mi = 0.0;   // outage branch
+            sK[i] = make_double2(Kr, Ki);
+            sM[i] = make_double2(Mr, Mi);
+            sloc[i] = loc;
+        }
+        __syncthreads();
+        // ---- injections, residuals and loss terms of the own buses ----
+        for (int b = tid; b < nbus; b += TB) {
+            const int4 bm = sbm[b];
+            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+            double sKr = 0.0, sKi = 0.0;
+            for (int i = bm.w; i < tend; ++i) {
+                sKr += sK[i].x;
+                sKi += sK[i].y;
+            }
+            const int o = b0 + b;
+            const double v = sW[b].x, v2 = v * v;
+            const double2 y = syd[b];
+            const double dP = fma(v2, y.x, sKr) - a.Ps[o];
+            const double dQ = fma(-v2, y.y, sKi) - a.Qs[o];
+            const double wp = a.wP[o], wq = a.wQ[o];
+            const double2 r = make_double2(2.0 * wp * dP, 2.0 * wq * dQ);
+            a.r[sb + o] = r;
+            sR[b] = r;
+            spq[b] = fma(wp * dP, dP, wq * dQ * dQ);
+        }
+        __syncthreads();
+        window_loss(spq, nbus, a.lpart + (long long)s * a.nwin + w);
+    }
+    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+
+    if (has) {
+        // ---- the ghost buses' residuals ----
+        for (int j = nbus + tid; j < nph; j += TB) sR[j] = a.r[sb + sslot[j]];
+        __syncthreads();
+        // ---- state-gradient terms of every terminal ----
+        for (int i = tid; i < nt; i += TB) {
+            const double2 K = sK[i], M = sM[i];
+            const int2 loc = sloc[i];
+            const double2 ro = sR[loc.x], rq = sR[loc.y];
+            const double th = fma(-ro.x, K.y, ro.y * K.x) + fma(rq.x, M.y, -rq.y * M.x);
+            const double vv = fma(ro.x, K.x, ro.y * K.y) + fma(rq.x, M.x, rq.y * M.y);
+            sK[i] = make_double2(th, vv);
+        }
+        __syncthreads();
+        const int pqs = (int)sp.pqs;
+        const int par = (int)((sb + b0) & 1);
+        for (int b = tid; b < nbus; b += TB) {
+            const int4 bm = sbm[b];
+            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+            double gth = 0.0, gv = 0.0;
+            for (int i = bm.w; i < tend; ++i) {
+                gth += sK[i].x;
+                gv += sK[i].y;
+            }
+            const double2 vw = sW[b], ro = sR[b], y = syd[b];
+            const double tv = vw.x + vw.x;
+            // <r_o, 2 v_o conj(Yd)> + (sum) / v_o
+            spq[b + par] = gth;
+            spq[pqs + b + par] = fma(gv, vw.y, tv * fma(ro.x, y.x, -ro.y * y.y));
+        }
+        if (a.aligned) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                store_range_ll(a.gva, spq, sb + b0, sb + b0 + nbus);
+                store_range_ll(a.gvm, spq + pqs, sb + b0, sb + b0 + nbus);
+                bulk_commit();
+                bulk_wait_read();
+            }
+        } else {
+            __syncthreads();
+            for (int b = tid; b < nbus; b += TB) {
+                a.gva[sb + b0 + b] = spq[b + par];
+                a.gvm[sb + b0 + b] = spq[pqs + b + par];
+            }
         }
     }
-    // ---- loss per scenario: window partial sums in window order ----
-    if (a.L)
-        for (int s = blockIdx.x * TB + tid; s < a.S; s += gridDim.x * TB) {
-            double acc = 0.0;
-            for (int w = 0; w < a.nwin; ++w) acc += a.lpart[(long long)s * a.nwin + w];
-            a.L[s] = acc;
-        }
+    if (a.gg) batch_branch_grads(a);
+    if (a.L) batch_loss(a);
 }
 
 // ----------------------------------------------------------- launchers ----
@@ -524,12 +685,11 @@ static BatchArgs batch_args(Batch *b)
     return a;
 }
 
+// Co-resident CTAs of `kernel` at tb threads and smem bytes (cached in resident).
 template <typename K>
-static cudaError_t coop_launch(K kernel, int &resident, Batch *b, size_t smem, long long items, cudaStream_t s,
-                               const BatchArgs &a)
+static cudaError_t coop_resident(K kernel, int &resident, int tb, size_t smem)
 {
     cudaError_t e;
-    const int tb = b->tb;
     if (resident == 0) {
         if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                           (int)smem)))
@@ -541,6 +701,16 @@ static cudaError_t coop_launch(K kernel, int &resident, Batch *b, size_t smem, l
         resident = per_sm * nsm;
         if (resident <= 0) return cudaErrorInvalidConfiguration;
     }
+    return cudaSuccess;
+}
+
+// Cooperative launch of min(items, co-resident) CTAs of tb threads.
+template <typename K>
+static cudaError_t coop_launch(K kernel, int &resident, int tb, size_t smem, long long items, cudaStream_t s,
+                               const BatchArgs &a)
+{
+    cudaError_t e = coop_resident(kernel, resident, tb, smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)std::max<long long>(1, std::min<long long>(items, resident)));
     cfg.blockDim = dim3((unsigned)tb);
@@ -568,8 +738,8 @@ cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, jac ? a.max_L : 0, jac);
     const size_t smem = sp.total + kTrigN * sizeof(double2);
     const long long items = (long long)b->S * b->nwin;
-    if (jac) return coop_launch(k_ewb<true>, b->resident[1], b, smem, items, s, a);
-    return coop_launch(k_ewb<false>, b->resident[0], b, smem, items, s, a);
+    if (jac) return coop_launch(k_ewb<true>, b->resident[1], b->tb, smem, items, s, a);
+    return coop_launch(k_ewb<false>, b->resident[0], b->tb, smem, items, s, a);
 }
 
 cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
@@ -593,10 +763,18 @@ cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const d
     a.gbsh = gbsh;
     a.gtap = gtap;
     a.aligned = al16(gvm) && al16(gva);
-    const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false, a.ghost ? a.max_nph : 0);
-    const size_t smem = sp.total + kTrigN * sizeof(double2);
-    const long long items = std::max<long long>((long long)b->S * b->nwin, (g->nl + b->tb - 1) / b->tb);
-    return coop_launch(k_adj, b->resident[2], b, smem, items, s, a);
+    const long long items = (long long)b->S * b->nwin;
+    if (b->ghost) {   // one item per CTA, if they all fit on the GPU at once
+        const size_t smem = adj1_smem_plan(a.max_nbus, a.max_nt, a.max_nph).total;
+        cudaError_t e = coop_resident(k_adj1, b->resident[3], kAdj1Threads, smem);
+        if (e != cudaSuccess) return e;
+        if (items <= b->resident[3])
+            return coop_launch(k_adj1, b->resident[3], kAdj1Threads, smem,
+                               std::max<long long>(items, (g->nl + kAdj1Threads - 1) / kAdj1Threads), s, a);
+    }
+    const size_t smem = ew_smem_plan(a.max_nbus, a.max_nt, 0, false).total + kTrigN * sizeof(double2);
+    return coop_launch(k_adj, b->resident[2], b->tb, smem,
+                       std::max<long long>(items, (g->nl + b->tb - 1) / b->tb), s, a);
 }
 
 }  // namespace pf

@@ -159,6 +159,35 @@ __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max
 }
 constexpr uint32_t kMaxSmem = 227u * 1024u;
 
+// Shared memory of the small-batch adjoint (k_adj1, one item per CTA): bus
+// metadata and self sums, both flows of every terminal and its two phasor
+// slots, loss / gradient staging, the phasor, residual and bus-name tables
+// of the own and ghost slots, (v, 1/v) of the own buses, the sine/cosine table.
+struct Adj1Smem {
+    uint32_t bm, yd, K, M, loc, pq, V, R, W, slot, tab, total, pqs;
+};
+__host__ __device__ inline Adj1Smem adj1_smem_plan(int max_nbus, int max_nt, int max_nph)
+{
+    Adj1Smem p;
+    const uint32_t nbus = (uint32_t)max_nbus, nt = (uint32_t)max_nt, nph = (uint32_t)max_nph;
+    p.pqs = (nbus + 3u) & ~1u;   // even, >= max_nbus + 2
+    p.bm = 0;
+    p.yd = p.bm + 16u * nbus;
+    p.K = p.yd + 16u * nbus;
+    p.M = p.K + 16u * nt;
+    p.loc = p.M + 16u * nt;
+    p.pq = p.loc + ((8u * nt + 15u) & ~15u);
+    p.V = p.pq + 16u * p.pqs;
+    p.R = p.V + 16u * nph;
+    p.W = p.R + 16u * nph;
+    p.slot = p.W + 16u * nbus;
+    p.tab = p.slot + ((4u * nph + 15u) & ~15u);
+    p.total = p.tab + 16u * 256u;
+    return p;
+}
+// threads per CTA of k_adj1
+constexpr int kAdj1Threads = 512;
+
 // ------------------------------------------------ device-side structure --
 struct EwDev {
     int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0, max_nph = 0;
@@ -308,13 +337,14 @@ struct Batch {
     double2 *V = nullptr;            // [S][nb]
     double2 *r = nullptr;            // [S][nb] loss residual (2 wP dP, 2 wQ dQ)
     double *lpart = nullptr;         // [S][nwin] per-window loss partial sums
-    int resident[3] = {0, 0, 0};     // co-resident CTAs of the batched kernels (inj, jac, adjoint)
+    int resident[4] = {0, 0, 0, 0};  // co-resident CTAs of the batched kernels (inj, jac, adjoint, k_adj1)
     // the batch's own element-wise windows: throughput-bound, so every thread
     // owns a bus in the reduction and loops over up to tfac terminals
     int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0;
     int *win_bus = nullptr;          // [nwin+1]
-    // small batches (about one item per SM): the adjoint forms each window's
-    // phasors with its ghost buses instead of a separate phase and barrier
+    // small batches (about one item per SM): the adjoint runs k_adj1, one
+    // item per CTA, which forms each window's phasors with its ghost buses
+    // instead of a separate phase and barrier
     int ghost = 0, max_nph = 0;
     int4 *desc = nullptr;            // [2 nwin] window descriptors (HostEw::desc)
     int *slotbus = nullptr;          // [nwin * max_nph]

@@ -232,6 +232,26 @@ def test_adjoint_matches_oracle(pf, S, with_outage):
         assert relerr(a, b) <= TOL, name
 
 
+@pytest.mark.parametrize("S", [2, 170])
+def test_adjoint_both_launch_forms_with_outages(pf, S):
+    """Two scenarios on a 40-bus grid give fewer (scenario, window) items than
+    SMs: one item per CTA with one grid barrier.  170 scenarios give more items
+    than SMs: the throughput form with its phasor phase and two barriers.
+    Every scenario but every fourth removes a non-bridge branch."""
+    from paper_2302_10736_gb300 import synth
+    gr, vm, va, Ps, Qs, wP, wQ = _adjoint_case(40, 55, 57, S)
+    nbr = np.flatnonzero(~synth.bridges(40, gr["f"], gr["t"]))
+    outage = np.array([-1 if s % 4 == 0 else int(nbr[s % len(nbr)]) for s in range(S)], np.int32)
+    L, gvm, gva, gp = run_adjoint(pf, gr, vm, va, Ps, Qs, wP, wQ, outage)
+    Lr, gvmr, gvar, gpr = oracle_adjoint(gr, vm, va, Ps, Qs, wP, wQ, outage)
+    assert relerr(L, Lr) <= TOL
+    assert relerr(gvm.ravel(), gvmr.ravel()) <= TOL and relerr(gva.ravel(), gvar.ravel()) <= TOL
+    for s in (0, 1, S - 1):
+        assert relerr(gvm[s], gvmr[s]) <= TOL and relerr(gva[s], gvar[s]) <= TOL, s
+    for name, a, b in zip(("g", "b", "bsh", "tap"), gp, gpr):
+        assert relerr(a, b) <= TOL, name
+
+
 def test_adjoint_workload4_against_oracle_and_central_differences(pf):
     """25,000 buses: J^T r and complex-step parameter gradients to 1e-12, and
     central differences (h = 1e-7, long double) on 200 seeded coordinates."""
