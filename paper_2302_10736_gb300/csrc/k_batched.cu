@@ -128,6 +128,7 @@ template <bool JAC>
 __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
+    unsigned int bgen = grid_barrier_gen(a.bar);
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, JAC ? a.max_L : 0, JAC);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
     for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
     batch_phasors(a, tab, JAC);
-    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    if (!grid_barrier(a.bar, gridDim.x, bgen, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     const long long nitem = (long long)a.S * a.nwin;
     for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
@@ -316,43 +317,58 @@ __device__ __forceinline__ void batch_loss(const BatchArgs &a)
 // Branch-parameter gradients (after the last grid barrier): one thread per
 // branch summing the scenarios in ascending order, from the phasors V and the
 // residuals r of every scenario in global memory.
-__device__ __forceinline__ void batch_branch_grads(const BatchArgs &a)
+struct BranchConst {
+    int h, k;
+    double g, bb, bsh, im, cphi, sphi;
+};
+
+__device__ __forceinline__ BranchConst branch_const(const BatchArgs &a, int l)
 {
-    const int TB = blockDim.x;
-    for (int l = blockIdx.x * TB + threadIdx.x; l < a.nl; l += gridDim.x * TB) {
-        const int2 hk = a.br_hk[l];
-        const int h = hk.x, k = hk.y;
-        const double g = a.pg[l], bb = a.pb[l], bsh = a.pbsh[l];
-        const double4_32a aux = a.br_aux[l];   // 1/m, cos phi, sin phi (formed with the constants)
-        const double im = aux.x, im2 = im * im, cphi = aux.y, sphi = aux.z;
-        const double c1r = g, c1i = -(bb + 0.5 * bsh);   // conj(y_s + j b_sh / 2)
-        double agg = 0.0, agb = 0.0, agsh = 0.0, agt = 0.0;
-        for (int s = 0; s < a.S; ++s) {
-            if (a.sc[s].l == l) continue;   // removed in this scenario
-            const long long sb = (long long)s * a.nb;
-            const double2 Vh = a.V[sb + h], Vk = a.V[sb + k];
-            const double2 rh = a.r[sb + h], rk = a.r[sb + k];
-            const double vh2 = fma(Vh.x, Vh.x, Vh.y * Vh.y), vk2 = fma(Vk.x, Vk.x, Vk.y * Vk.y);
-            const double Wr = fma(Vh.x, Vk.x, Vh.y * Vk.y), Wi = fma(Vh.y, Vk.x, -Vh.x * Vk.y);
-            const double Br = fma(Wr, cphi, Wi * sphi) * im, Bi = fma(Wi, cphi, -Wr * sphi) * im;   // W e^{-j phi}/m
-            const double Ah = vh2 * im2;
-            const double zhr = Ah - Br, zhi = -Bi;     // dS_hk/dg
-            const double zkr = vk2 - Br, zki = Bi;     // dS_kh/dg
-            agg += fma(rh.x, zhr, rh.y * zhi) + fma(rk.x, zkr, rk.y * zki);
-            agb += fma(rh.x, zhi, -rh.y * zhr) + fma(rk.x, zki, -rk.y * zkr);   // <r, -j z>
-            agsh -= 0.5 * fma(rh.y, Ah, rk.y * vk2);
-            // dS_hk/dm = im (-2 Ah conj(y_s + j b_sh/2) + conj(y_s) B), dS_kh/dm = im conj(y_s) conj(B)
-            const double dhr = im * (-2.0 * Ah * c1r + fma(g, Br, bb * Bi));
-            const double dhi = im * (-2.0 * Ah * c1i + fma(g, Bi, -bb * Br));
-            const double dkr = im * fma(g, Br, -bb * Bi);
-            const double dki = im * fma(-g, Bi, -bb * Br);
-            agt += fma(rh.x, dhr, rh.y * dhi) + fma(rk.x, dkr, rk.y * dki);
-        }
-        a.gg[l] = agg;
-        a.gb[l] = agb;
-        a.gbsh[l] = agsh;
-        a.gtap[l] = agt;
+    const int2 hk = a.br_hk[l];
+    const double4_32a aux = a.br_aux[l];   // 1/m, cos phi, sin phi (formed with the constants)
+    return BranchConst{hk.x, hk.y, a.pg[l], a.pb[l], a.pbsh[l], aux.x, aux.y, aux.z};
+}
+
+__device__ __forceinline__ void branch_grad(const BatchArgs &a, int l, const BranchConst &c)
+{
+    const int h = c.h, k = c.k;
+    const double g = c.g, bb = c.bb, im = c.im, im2 = im * im, cphi = c.cphi, sphi = c.sphi;
+    const double c1r = g, c1i = -(bb + 0.5 * c.bsh);   // conj(y_s + j b_sh / 2)
+    double agg = 0.0, agb = 0.0, agsh = 0.0, agt = 0.0;
+    for (int s = 0; s < a.S; ++s) {
+        if (a.sc[s].l == l) continue;   // removed in this scenario
+        const long long sb = (long long)s * a.nb;
+        const double2 Vh = a.V[sb + h], Vk = a.V[sb + k];
+        const double2 rh = a.r[sb + h], rk = a.r[sb + k];
+        const double vh2 = fma(Vh.x, Vh.x, Vh.y * Vh.y), vk2 = fma(Vk.x, Vk.x, Vk.y * Vk.y);
+        const double Wr = fma(Vh.x, Vk.x, Vh.y * Vk.y), Wi = fma(Vh.y, Vk.x, -Vh.x * Vk.y);
+        const double Br = fma(Wr, cphi, Wi * sphi) * im, Bi = fma(Wi, cphi, -Wr * sphi) * im;   // W e^{-j phi}/m
+        const double Ah = vh2 * im2;
+        const double zhr = Ah - Br, zhi = -Bi;     // dS_hk/dg
+        const double zkr = vk2 - Br, zki = Bi;     // dS_kh/dg
+        agg += fma(rh.x, zhr, rh.y * zhi) + fma(rk.x, zkr, rk.y * zki);
+        agb += fma(rh.x, zhi, -rh.y * zhr) + fma(rk.x, zki, -rk.y * zkr);   // <r, -j z>
+        agsh -= 0.5 * fma(rh.y, Ah, rk.y * vk2);
+        // dS_hk/dm = im (-2 Ah conj(y_s + j b_sh/2) + conj(y_s) B), dS_kh/dm = im conj(y_s) conj(B)
+        const double dhr = im * (-2.0 * Ah * c1r + fma(g, Br, bb * Bi));
+        const double dhi = im * (-2.0 * Ah * c1i + fma(g, Bi, -bb * Br));
+        const double dkr = im * fma(g, Br, -bb * Bi);
+        const double dki = im * fma(-g, Bi, -bb * Br);
+        agt += fma(rh.x, dhr, rh.y * dhi) + fma(rk.x, dkr, rk.y * dki);
     }
+    a.gg[l] = agg;
+    a.gb[l] = agb;
+    a.gbsh[l] = agsh;
+    a.gtap[l] = agt;
+}
+
+// This CTA's branches: a contiguous range of ceil(nl / gridDim.x), so that
+// every SM gets the same share of the branch-gradient work.
+__device__ __forceinline__ int2 cta_branches(const BatchArgs &a)
+{
+    const int chunk = (a.nl + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int lb = min(a.nl, (int)blockIdx.x * chunk);
+    return make_int2(lb, min(a.nl, lb + chunk));
 }
 
 // Throughput adjoint (many items per CTA): every scenario's phasors, grid
@@ -360,6 +376,7 @@ __device__ __forceinline__ void batch_branch_grads(const BatchArgs &a)
 __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
+    unsigned int bgen = grid_barrier_gen(a.bar);
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
@@ -372,7 +389,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     __syncthreads();
     // every scenario's phasors first, visible to all CTAs after the barrier
     batch_phasors(a, tab, true);
-    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    if (!grid_barrier(a.bar, gridDim.x, bgen, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     const long long nitem = (long long)a.S * a.nwin;
     // ---- phase 2: injections, residuals and per-window loss partial sums ----
@@ -414,7 +431,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         __syncthreads();
         window_loss(spq, nbus, a.lpart + (long long)s * a.nwin + w);
     }
-    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    if (!grid_barrier(a.bar, gridDim.x, bgen, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     // ---- phase 3a: state gradients, one bus per thread over its own terminals ----
     for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
@@ -479,7 +496,10 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     }
 
     // ---- phase 3b: branch-parameter gradients; the loss of every scenario ----
-    if (a.gg) batch_branch_grads(a);
+    if (a.gg) {
+        const int2 lr = cta_branches(a);
+        for (int l = lr.x + tid; l < lr.y; l += TB) branch_grad(a, l, branch_const(a, l));
+    }
     if (a.L) batch_loss(a);
 }
 
@@ -496,6 +516,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
 __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
+    unsigned int bgen = grid_barrier_gen(a.bar);
     const Adj1Smem sp = adj1_smem_plan(a.max_nbus, a.max_nt, a.max_nph);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
@@ -524,17 +545,48 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         sb = (long long)s * a.nb;
         const ScenOut sc = a.sc[s];
         const int *sbus = a.slotbus + (long long)w * a.max_nph;
+        // The thread's first phasor slot, terminal and bus are loaded up
+        // front, in order of dependence, so that their latency hides behind
+        // the window metadata and the phasors.
+        const int o0 = tid < a.max_nph ? sbus[tid] : 0;
+        double2 yc0 = make_double2(0.0, 0.0), ym0 = make_double2(0.0, 0.0);
+        int2 loc0 = make_int2(0, 0);
+        int tm0 = 0;
+        if (tid < nt) {
+            const int p = t0 + tid;
+            yc0 = a.tcoup[p];
+            tm0 = a.tmir[p];
+            loc0 = make_int2(a.town[p] - b0, a.tloc[p].x);
+        }
+        double ps0 = 0.0, qs0 = 0.0, wp0 = 0.0, wq0 = 0.0;
+        if (tid < nbus) {
+            ps0 = a.Ps[b0 + tid];
+            qs0 = a.Qs[b0 + tid];
+            wp0 = a.wP[b0 + tid];
+            wq0 = a.wQ[b0 + tid];
+        }
+        double th0 = 0.0, v0 = 0.0;
+        if (tid < nph) {
+            th0 = a.va[sb + o0];
+            v0 = a.vm[sb + o0];
+        }
         const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
         for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
         batch_window_meta(a, sc, b0, b0 + nbus, t0, sbm, syd);
+        if (tid < nt) ym0 = a.tcoup[tm0];
         __syncthreads();
         // ---- phasors of the own and ghost buses ----
         for (int j = tid; j < nph; j += TB) {
-            const int o = sbus[j];
+            int o = o0;
+            double th = th0, v = v0;
+            if (j != tid) {
+                o = sbus[j];
+                th = a.va[sb + o];
+                v = a.vm[sb + o];
+            }
             sslot[j] = o;
             double sn, cs;
-            fast_sincos(a.va[sb + o], tab, &sn, &cs);
-            const double v = a.vm[sb + o];
+            fast_sincos(th, tab, &sn, &cs);
             const double2 V = make_double2(v * cs, v * sn);
             sV[j] = V;
             if (j < nbus) {
@@ -546,8 +598,13 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         // ---- both flows of every terminal ----
         for (int i = tid; i < nt; i += TB) {
             const int p = t0 + i;
-            const double2 yc = a.tcoup[p], ym = a.tcoup[a.tmir[p]];
-            const int2 loc = make_int2(a.town[p] - b0, a.tloc[p].x);
+            double2 yc = yc0, ym = ym0;
+            int2 loc = loc0;
+            if (i != tid) {
+                yc = a.tcoup[p];
+                ym = a.tcoup[a.tmir[p]];
+                loc = make_int2(a.town[p] - b0, a.tloc[p].x);
+            }
             const double2 Vo = sV[loc.x], Vq = sV[loc.y];
             const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);   // V_o conj(V_q)
             double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);                 // K_t
@@ -568,11 +625,17 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
                 sKi += sK[i].y;
             }
             const int o = b0 + b;
+            double ps = ps0, qs = qs0, wp = wp0, wq = wq0;
+            if (b != tid) {
+                ps = a.Ps[o];
+                qs = a.Qs[o];
+                wp = a.wP[o];
+                wq = a.wQ[o];
+            }
             const double v = sW[b].x, v2 = v * v;
             const double2 y = syd[b];
-            const double dP = fma(v2, y.x, sKr) - a.Ps[o];
-            const double dQ = fma(-v2, y.y, sKi) - a.Qs[o];
-            const double wp = a.wP[o], wq = a.wQ[o];
+            const double dP = fma(v2, y.x, sKr) - ps;
+            const double dQ = fma(-v2, y.y, sKi) - qs;
             const double2 r = make_double2(2.0 * wp * dP, 2.0 * wq * dQ);
             a.r[sb + o] = r;
             sR[b] = r;
@@ -581,11 +644,22 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         __syncthreads();
         window_loss(spq, nbus, a.lpart + (long long)s * a.nwin + w);
     }
-    if (!grid_barrier(a.bar, gridDim.x, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    // the thread's first branch: its constants before the barrier, and after
+    // it the branch gradient while the ghost residuals are in flight
+    const int2 lr = cta_branches(a);
+    const int l0 = lr.x + tid;
+    BranchConst bc0{};
+    if (a.gg && l0 < lr.y) bc0 = branch_const(a, l0);
+    if (!grid_barrier(a.bar, gridDim.x, bgen, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
+    const int jg = nbus + tid;
+    double2 rg = make_double2(0.0, 0.0);
+    if (has && jg < nph) rg = a.r[sb + sslot[jg]];
+    if (a.gg && l0 < lr.y) branch_grad(a, l0, bc0);
     if (has) {
         // ---- the ghost buses' residuals ----
-        for (int j = nbus + tid; j < nph; j += TB) sR[j] = a.r[sb + sslot[j]];
+        if (jg < nph) sR[jg] = rg;
+        for (int j = jg + TB; j < nph; j += TB) sR[j] = a.r[sb + sslot[j]];
         __syncthreads();
         // ---- state-gradient terms of every terminal ----
         for (int i = tid; i < nt; i += TB) {
@@ -630,7 +704,8 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             }
         }
     }
-    if (a.gg) batch_branch_grads(a);
+    if (a.gg)
+        for (int l = l0 + TB; l < lr.y; l += TB) branch_grad(a, l, branch_const(a, l));
     if (a.L) batch_loss(a);
 }
 

@@ -75,10 +75,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // Grid-wide barrier for a cooperative launch (every CTA resident).  `state`
 // holds {arrival count, generation} in global memory, both zero initially;
 // the last CTA to arrive resets the count and advances the generation, so
-// the barrier needs no per-launch host state (graph replays work).  The
-// generation is read before arriving, so it cannot have moved on already.
-// Waiting is bounded: after `limit_ns` of the global timer the CTA records
-// `timeout_code` in *err and returns false (uniformly for the whole CTA).
+// the barrier needs no per-launch host state (graph replays work).  Thread 0
+// of every CTA reads the generation once, at kernel start (grid_barrier_gen):
+// it cannot move before this CTA arrives, and each barrier advances it by
+// one, so arriving needs no further read.  Waiting is bounded: after
+// `limit_ns` of the global timer the CTA records `timeout_code` in *err and
+// returns false (uniformly for the whole CTA).
 __device__ __forceinline__ uint64_t global_timer_ns()
 {
     uint64_t t;
@@ -86,21 +88,27 @@ __device__ __forceinline__ uint64_t global_timer_ns()
     return t;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned int *state, unsigned int nblocks, int *err, int timeout_code,
-                                             uint64_t limit_ns)
+__device__ __forceinline__ unsigned int grid_barrier_gen(const unsigned int *state)
+{
+    return threadIdx.x == 0 ? *(const volatile unsigned int *)(state + 1) : 0u;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned int *state, unsigned int nblocks, unsigned int &gen, int *err,
+                                             int timeout_code, uint64_t limit_ns)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned int *vgen = state + 1;
-        const unsigned int g0 = *vgen;
+        const unsigned int g0 = gen;
         int ok = 1;
         __threadfence();   // this CTA's global writes before its arrival
         const unsigned int arrived = atomicAdd(state, 1u);
         if (arrived == nblocks - 1) {
             atomicExch(state, 0u);
-            __threadfence();
-            atomicAdd(state + 1, 1u);   // release everyone
+            // release everyone: the reset (and everything before it) is visible
+            // to a CTA that sees the new generation
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(state + 1) : "memory");
         } else {
             const uint64_t t0 = global_timer_ns();
             while (*vgen == g0) {
@@ -109,10 +117,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *state, unsigned int n
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();   // acquire the other CTAs' writes
+        gen = g0 + 1;
         s_ok = ok;
     }
     __syncthreads();
