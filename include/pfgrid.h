@@ -249,7 +249,8 @@ pf_status grid_check_error(pf_grid *grid, pf_stream stream);
  * invariant the kernels' memory accesses rely on (index ranges, sorted
  * terminal order, parallel-run flags, ghost-bus slots, window descriptors,
  * staging offsets inside each window's Jacobian slice, bulk-copy alignment,
- * shared-memory size).  PF_OK or PF_EINVAL with a message.
+ * shared-memory size, the per-window branch lists of the small-batch adjoint:
+ * every branch in exactly one window).  PF_OK or PF_EINVAL with a message.
  */
 pf_status grid_selfcheck(const pf_grid_desc *desc, int32_t window, int32_t nwin_target);
 

@@ -147,8 +147,8 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
     PF_CUDA(a.alloc(&g->ph_v, (size_t)nb));
     PF_CUDA(a.alloc(&g->err, 1));
     PF_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
-    PF_CUDA(a.alloc(&g->bar, 2));
-    PF_CUDA(cudaMemsetAsync(g->bar, 0, 2 * sizeof(unsigned int), s));
+    PF_CUDA(a.alloc(&g->bar, kBarWords));
+    PF_CUDA(cudaMemsetAsync(g->bar, 0, kBarWords * sizeof(unsigned int), s));
     PF_CUDA(cudaStreamSynchronize(s));  // host vectors stay alive, but keep setup ordered
     return PF_OK;
 }
@@ -520,9 +520,13 @@ PF_API pf_status phasor(int32_t n, const double *vm, const double *va, double *U
 PF_API pf_status grid_inject_barrier_fault(pf_grid *grid, pf_stream stream)
 {
     if (!grid) return set_error(PF_EINVAL, "grid_inject_barrier_fault: grid is NULL");
-    const unsigned int phantom = 0x80000000u;   // arrivals never reach nblocks - 1
-    PF_CUDA(cudaMemcpyAsync(grid->g.bar, &phantom, sizeof(phantom), cudaMemcpyHostToDevice, (cudaStream_t)stream));
-    PF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));   // `phantom` is a stack variable
+    // both arrival counters far below every target (as signed differences),
+    // so the next batched launch's first barrier never completes
+    const unsigned int phantom = 0x80000000u;
+    cudaStream_t st = (cudaStream_t)stream;
+    PF_CUDA(cudaMemcpyAsync(grid->g.bar + 32, &phantom, sizeof(phantom), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaMemcpyAsync(grid->g.bar + 64, &phantom, sizeof(phantom), cudaMemcpyHostToDevice, st));
+    PF_CUDA(cudaStreamSynchronize(st));   // `phantom` is a stack variable
     return PF_OK;
 }
 
@@ -563,7 +567,7 @@ PF_API pf_status grid_check_error(pf_grid *grid, pf_stream stream)
     if (h == DEV_OK) return PF_OK;
     PF_CUDA(cudaMemsetAsync(grid->g.err, 0, sizeof(int), s));
     // a kernel that gave up may have left the grid barrier half-way: start it afresh
-    PF_CUDA(cudaMemsetAsync(grid->g.bar, 0, 2 * sizeof(unsigned int), s));
+    PF_CUDA(cudaMemsetAsync(grid->g.bar, 0, kBarWords * sizeof(unsigned int), s));
     PF_CUDA(cudaStreamSynchronize(s));
     if (h == DEV_TIMEOUT) return set_error(PF_ETIMEOUT, "a device-side wait gave up (error word %d)", h);
     return set_error(PF_EDEVICE, "a kernel reported device error word %d", h);
@@ -732,5 +736,10 @@ PF_API pf_status grid_selfcheck(const pf_grid_desc *d, int32_t window, int32_t n
     HostEw E;
     if ((st = host_topology(d->nb, d->nl, d->from, d->to, H))) return st;
     if ((st = host_ew(H, window, E, 1, nwin_target))) return st;
-    return host_selfcheck(H, E);
+    if ((st = host_selfcheck(H, E))) return st;
+    // the small-batch adjoint's per-window branch lists (every branch once)
+    std::vector<int2> brl;
+    std::vector<int> nbr;
+    int max_nbr = 0;
+    return host_window_branches(H, E, brl, nbr, max_nbr);
 }

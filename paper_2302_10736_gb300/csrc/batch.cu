@@ -106,6 +106,17 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
     b->max_nbus = E.max_nbus;
     b->ghost = ghost ? 1 : 0;
     b->max_nph = E.max_nph;
+    // the small-batch adjoint's per-window branch lists; their counts ride in
+    // the otherwise unused desc[2w+1].w
+    std::vector<int2> brl;
+    if (ghost) {
+        std::vector<int> nbr;
+        if (pf_status hs = host_window_branches(g->topo, E, brl, nbr, b->max_nbr)) {
+            delete pb;
+            return hs;
+        }
+        for (int w = 0; w < E.nwin; ++w) E.desc[2 * w + 1].w = nbr[w];
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)nscen * g->nb;
     const size_t nw = (size_t)nscen * std::max(b->nwin, 1);
@@ -121,7 +132,9 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
                    (e = cudaMemcpyAsync(b->slotbus, E.slotbus.data(), sizeof(int) * E.slotbus.size(),
                                         cudaMemcpyHostToDevice, st)) ||
                    (e = cudaMemcpyAsync(b->tloc, E.tloc.data(), sizeof(int2) * E.tloc.size(), cudaMemcpyHostToDevice,
-                                        st)))) ||
+                                        st)) ||
+                   (e = b->arena.alloc(&b->brl, brl.size())) ||
+                   (e = cudaMemcpyAsync(b->brl, brl.data(), sizeof(int2) * brl.size(), cudaMemcpyHostToDevice, st)))) ||
         (e = b->arena.alloc(&b->U, n)) || (e = b->arena.alloc(&b->V, n)) || (e = b->arena.alloc(&b->r, n)) ||
         (e = b->arena.alloc(&b->lpart, nw)) ||
         (nscen && (e = cudaMemcpyAsync(b->sc, b->h_sc.data(), sizeof(ScenOut) * nscen, cudaMemcpyHostToDevice, st))) ||

@@ -336,4 +336,37 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
     return PF_OK;
 }
 
+// Per window, the branches whose from-terminal lies in it, in sorted-terminal
+// order: {window-local terminal index, branch}; window w's at
+// brl[w * max_nbr ...] (padding {0, 0}), their number in nbr[w].  Every
+// branch appears exactly once over the windows.
+pf_status host_window_branches(const HostTopo &H, const HostEw &E, std::vector<int2> &brl, std::vector<int> &nbr,
+                               int &max_nbr)
+{
+    nbr.assign(E.nwin, 0);
+    max_nbr = 0;
+    for (int w = 0; w < E.nwin; ++w) {
+        const int t0 = E.desc[2 * w].z, nt = E.desc[2 * w].w;
+        int c = 0;
+        for (int p = t0; p < t0 + nt; ++p) c += !(H.tsort[p] & 1);
+        nbr[w] = c;
+        max_nbr = std::max(max_nbr, c);
+    }
+    brl.assign((size_t)E.nwin * std::max(max_nbr, 1), make_int2(0, 0));
+    std::vector<char> seen(H.nl, 0);
+    for (int w = 0; w < E.nwin; ++w) {
+        const int t0 = E.desc[2 * w].z, nt = E.desc[2 * w].w;
+        int j = 0;
+        for (int p = t0; p < t0 + nt; ++p) {
+            const int t = H.tsort[p];
+            if (t & 1) continue;
+            brl[(size_t)w * std::max(max_nbr, 1) + j++] = make_int2(p - t0, t >> 1);
+            if (seen[t >> 1]++) return set_error(PF_EINVAL, "window branch lists: branch %d listed twice", t >> 1);
+        }
+    }
+    for (int l = 0; l < H.nl; ++l)
+        if (!seen[l]) return set_error(PF_EINVAL, "window branch lists: branch %d in no window", l);
+    return PF_OK;
+}
+
 }  // namespace pf

@@ -43,9 +43,9 @@ constexpr uint64_t kBatchBarrierNs = 2000000000ull;   // bounded grid-barrier wa
 
 struct BatchArgs {
     int S, nb, nl, nnz, nwin, max_nbus, max_nt, max_L, aligned;
-    int ghost, max_nph;
+    int ghost, max_nph, max_nbr;
     const int *win_bus, *tp, *rp, *kd, *town, *tmir, *tpos, *slotbus;
-    const int2 *tloc;
+    const int2 *tloc, *brl;
     const int4 *desc;
     const int2 *tnbr;
     const double2 *yd, *tself, *tcoup, *trig;
@@ -128,7 +128,7 @@ template <bool JAC>
 __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
-    unsigned int bgen = grid_barrier_gen(a.bar);
+    const GridBar gbar = grid_barrier_begin(a.bar);
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, JAC ? a.max_L : 0, JAC);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
     for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
     batch_phasors(a, tab, JAC);
-    if (!grid_barrier(a.bar, gridDim.x, bgen, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    if (!grid_barrier(gbar, a.bar, gridDim.x, 0, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     const long long nitem = (long long)a.S * a.nwin;
     for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
@@ -308,53 +308,78 @@ __device__ __forceinline__ void batch_loss(const BatchArgs &a)
     const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < a.S; s += nwarp) {
         double acc = 0.0;
-        for (int w = lane; w < a.nwin; w += 32) acc += a.lpart[s * a.nwin + w];
+        for (int w = lane; w < a.nwin; w += 32) acc += __ldcg(a.lpart + s * a.nwin + w);
         acc = warp_sum(acc);
         if (lane == 0) a.L[s] = acc;
     }
 }
 
-// Branch-parameter gradients (after the last grid barrier): one thread per
-// branch summing the scenarios in ascending order, from the phasors V and the
-// residuals r of every scenario in global memory.
+// Branch-parameter gradients: the partials of Eqs. (5)-(6) by g, b, b_sh and
+// the tap m of branch (h, k), paired with the end residuals.  With
+// B = V_h conj(V_k) e^{-j phi}, A_h = v_h^2 / m^2, s_x = r_h.x + r_k.x,
+// d_x = r_h.x - r_k.x (likewise s_y, d_y), Q1 = B.x s_x + B.y d_y,
+// Q2 = B.x s_y - B.y d_x and S_sh = r_h.y A_h + r_k.y v_k^2, one scenario adds
+//   dL/dg    += r_h.x A_h + r_k.x v_k^2 - Q1 / m
+//   dL/db    += Q2 / m - S_sh
+//   dL/db_sh += -S_sh / 2
+//   dL/dm    += (-2 A_h (r_h.x g + r_h.y c1i) + (g Q1 - b Q2) / m) / m,  c1i = -(b + b_sh/2).
 struct BranchConst {
     int h, k;
-    double g, bb, bsh, im, cphi, sphi;
+    double g, bb, im, cphi, sphi, c1i;
 };
 
 __device__ __forceinline__ BranchConst branch_const(const BatchArgs &a, int l)
 {
     const int2 hk = a.br_hk[l];
-    const double4_32a aux = a.br_aux[l];   // 1/m, cos phi, sin phi (formed with the constants)
-    return BranchConst{hk.x, hk.y, a.pg[l], a.pb[l], a.pbsh[l], aux.x, aux.y, aux.z};
+    const double4_32a aux = a.br_aux[l];   // 1/m, cos phi, sin phi, c1i (formed with the constants)
+    return BranchConst{hk.x, hk.y, a.pg[l], a.pb[l], aux.x, aux.y, aux.z, aux.w};
 }
 
+template <bool ACC>
+__device__ __forceinline__ void branch_terms(const BranchConst &c, double2 Vh, double2 Vk, double2 rh, double2 rk,
+                                             double &agg, double &agb, double &agsh, double &agt)
+{
+    const double im = c.im;
+    const double vh2 = fma(Vh.x, Vh.x, Vh.y * Vh.y), vk2 = fma(Vk.x, Vk.x, Vk.y * Vk.y);
+    const double Wr = fma(Vh.x, Vk.x, Vh.y * Vk.y), Wi = fma(Vh.y, Vk.x, -Vh.x * Vk.y);   // V_h conj(V_k)
+    const double Br = fma(Wr, c.cphi, Wi * c.sphi), Bi = fma(Wi, c.cphi, -Wr * c.sphi);   // W e^{-j phi}
+    const double sx = rh.x + rk.x, dx = rh.x - rk.x, sy = rh.y + rk.y, dy = rh.y - rk.y;
+    const double Q1 = fma(Br, sx, Bi * dy), Q2 = fma(Br, sy, -Bi * dx);
+    const double Ah = vh2 * (im * im);
+    const double Ssh = fma(rh.y, Ah, rk.y * vk2);
+    const double tg = fma(-im, Q1, fma(rh.x, Ah, rk.x * vk2));
+    const double tb = fma(im, Q2, -Ssh);
+    const double tsh = -0.5 * Ssh;
+    const double C = fma(rh.x, c.g, rh.y * c.c1i);
+    const double tt = im * fma(-2.0 * Ah, C, im * fma(c.g, Q1, -c.bb * Q2));
+    if (ACC) {
+        agg += tg;
+        agb += tb;
+        agsh += tsh;
+        agt += tt;
+    } else {
+        agg = tg;
+        agb = tb;
+        agsh = tsh;
+        agt = tt;
+    }
+}
+
+// one thread per branch summing the scenarios in ascending order, from the
+// phasors V and the residuals r of every scenario in global memory
 __device__ __forceinline__ void branch_grad(const BatchArgs &a, int l, const BranchConst &c)
 {
-    const int h = c.h, k = c.k;
-    const double g = c.g, bb = c.bb, im = c.im, im2 = im * im, cphi = c.cphi, sphi = c.sphi;
-    const double c1r = g, c1i = -(bb + 0.5 * c.bsh);   // conj(y_s + j b_sh / 2)
     double agg = 0.0, agb = 0.0, agsh = 0.0, agt = 0.0;
+    bool first = true;
     for (int s = 0; s < a.S; ++s) {
         if (a.sc[s].l == l) continue;   // removed in this scenario
         const long long sb = (long long)s * a.nb;
-        const double2 Vh = a.V[sb + h], Vk = a.V[sb + k];
-        const double2 rh = a.r[sb + h], rk = a.r[sb + k];
-        const double vh2 = fma(Vh.x, Vh.x, Vh.y * Vh.y), vk2 = fma(Vk.x, Vk.x, Vk.y * Vk.y);
-        const double Wr = fma(Vh.x, Vk.x, Vh.y * Vk.y), Wi = fma(Vh.y, Vk.x, -Vh.x * Vk.y);
-        const double Br = fma(Wr, cphi, Wi * sphi) * im, Bi = fma(Wi, cphi, -Wr * sphi) * im;   // W e^{-j phi}/m
-        const double Ah = vh2 * im2;
-        const double zhr = Ah - Br, zhi = -Bi;     // dS_hk/dg
-        const double zkr = vk2 - Br, zki = Bi;     // dS_kh/dg
-        agg += fma(rh.x, zhr, rh.y * zhi) + fma(rk.x, zkr, rk.y * zki);
-        agb += fma(rh.x, zhi, -rh.y * zhr) + fma(rk.x, zki, -rk.y * zkr);   // <r, -j z>
-        agsh -= 0.5 * fma(rh.y, Ah, rk.y * vk2);
-        // dS_hk/dm = im (-2 Ah conj(y_s + j b_sh/2) + conj(y_s) B), dS_kh/dm = im conj(y_s) conj(B)
-        const double dhr = im * (-2.0 * Ah * c1r + fma(g, Br, bb * Bi));
-        const double dhi = im * (-2.0 * Ah * c1i + fma(g, Bi, -bb * Br));
-        const double dkr = im * fma(g, Br, -bb * Bi);
-        const double dki = im * fma(-g, Bi, -bb * Br);
-        agt += fma(rh.x, dhr, rh.y * dhi) + fma(rk.x, dkr, rk.y * dki);
+        const double2 Vh = a.V[sb + c.h], Vk = a.V[sb + c.k], rh = a.r[sb + c.h], rk = a.r[sb + c.k];
+        if (first)
+            branch_terms<false>(c, Vh, Vk, rh, rk, agg, agb, agsh, agt);
+        else
+            branch_terms<true>(c, Vh, Vk, rh, rk, agg, agb, agsh, agt);
+        first = false;
     }
     a.gg[l] = agg;
     a.gb[l] = agb;
@@ -376,7 +401,7 @@ __device__ __forceinline__ int2 cta_branches(const BatchArgs &a)
 __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
-    unsigned int bgen = grid_barrier_gen(a.bar);
+    const GridBar gbar = grid_barrier_begin(a.bar);
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, 0, false);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
@@ -389,7 +414,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     __syncthreads();
     // every scenario's phasors first, visible to all CTAs after the barrier
     batch_phasors(a, tab, true);
-    if (!grid_barrier(a.bar, gridDim.x, bgen, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    if (!grid_barrier(gbar, a.bar, gridDim.x, 0, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     const long long nitem = (long long)a.S * a.nwin;
     // ---- phase 2: injections, residuals and per-window loss partial sums ----
@@ -431,7 +456,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         __syncthreads();
         window_loss(spq, nbus, a.lpart + (long long)s * a.nwin + w);
     }
-    if (!grid_barrier(a.bar, gridDim.x, bgen, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    if (!grid_barrier(gbar, a.bar, gridDim.x, 1, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     // ---- phase 3a: state gradients, one bus per thread over its own terminals ----
     for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
@@ -510,19 +535,21 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
 // terminal): K_t = conj(Yc_t) W and the mirror's K_m = conj(Yc_m) conj(W),
 // then its buses' injections and residuals.  All of it stays in shared
 // memory, so after the barrier the item reads back only its ghost buses'
-// residuals (one L2 round trip) before the state gradients
+// residuals (one L2 round trip) before the state gradients (and, for a single
+// scenario, the gradients of the branches whose from-terminal it owns)
 //   dL/dtheta_o = sum_t <r_o, j K_t> + <r_q, -j K_m>
 //   dL/dv_o     = <r_o, 2 v_o conj(Yd_o)> + (sum_t <r_o, K_t> + <r_q, K_m>) / v_o.
 __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
-    unsigned int bgen = grid_barrier_gen(a.bar);
+    const GridBar gbar = grid_barrier_begin(a.bar);
     const Adj1Smem sp = adj1_smem_plan(a.max_nbus, a.max_nt, a.max_nph);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
     double2 *sK = reinterpret_cast<double2 *>(smem + sp.K);
     double2 *sM = reinterpret_cast<double2 *>(smem + sp.M);
     int2 *sloc = reinterpret_cast<int2 *>(smem + sp.loc);   // per terminal: {owner slot, other-bus slot}
+    __shared__ double swl[32];                                 // per-warp loss partials
     double *spq = reinterpret_cast<double *>(smem + sp.pq);
     double2 *sV = reinterpret_cast<double2 *>(smem + sp.V);
     double2 *sR = reinterpret_cast<double2 *>(smem + sp.R);
@@ -533,6 +560,15 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
     const bool has = (long long)blockIdx.x < (long long)a.S * a.nwin;   // CTA-uniform
     int s = 0, w = 0, b0 = 0, nbus = 0, t0 = 0, nt = 0, nph = 0;
     long long sb = 0;
+    ScenOut sc{};
+    // One scenario: each window forms the gradients of the branches whose
+    // from-terminal it owns, from its shared-memory phasors and residuals.
+    // Several scenarios: a contiguous range of branches per CTA, summing the
+    // scenarios from global memory.
+    const bool fused = a.gg && a.S == 1;
+    int nbr = 0;                          // branches of the window (fused)
+    int2 e0 = make_int2(0, 0);            // the thread's first: {window-local from-terminal, branch}
+    BranchConst bc0{};
     if (has) {
         s = (int)(blockIdx.x / a.nwin);
         w = (int)(blockIdx.x % a.nwin);
@@ -542,8 +578,9 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         t0 = d0.z;
         nt = d0.w;
         nph = d1.z;
+        if (fused) nbr = d1.w;
         sb = (long long)s * a.nb;
-        const ScenOut sc = a.sc[s];
+        sc = a.sc[s];
         const int *sbus = a.slotbus + (long long)w * a.max_nph;
         // The thread's first phasor slot, terminal and bus are loaded up
         // front, in order of dependence, so that their latency hides behind
@@ -558,12 +595,13 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             tm0 = a.tmir[p];
             loc0 = make_int2(a.town[p] - b0, a.tloc[p].x);
         }
-        double ps0 = 0.0, qs0 = 0.0, wp0 = 0.0, wq0 = 0.0;
-        if (tid < nbus) {
-            ps0 = a.Ps[b0 + tid];
-            qs0 = a.Qs[b0 + tid];
-            wp0 = a.wP[b0 + tid];
-            wq0 = a.wQ[b0 + tid];
+        if (fused && tid < a.max_nbr) e0 = a.brl[(long long)w * a.max_nbr + tid];
+        // two threads per bus below: x = 2b + im, im = 0 the P part, 1 the Q part
+        double spec0 = 0.0, wt0 = 0.0;
+        if (tid < 2 * nbus) {
+            const int o = b0 + (tid >> 1);
+            spec0 = (tid & 1) ? a.Qs[o] : a.Ps[o];
+            wt0 = (tid & 1) ? a.wQ[o] : a.wP[o];
         }
         double th0 = 0.0, v0 = 0.0;
         if (tid < nph) {
@@ -615,47 +653,76 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             sloc[i] = loc;
         }
         __syncthreads();
-        // ---- injections, residuals and loss terms of the own buses ----
-        for (int b = tid; b < nbus; b += TB) {
-            const int4 bm = sbm[b];
-            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
-            double sKr = 0.0, sKi = 0.0;
-            for (int i = bm.w; i < tend; ++i) {
-                sKr += sK[i].x;
-                sKi += sK[i].y;
+        // the first branch's constants (not thread 0: its fence on arriving at
+        // the barrier would wait for these loads)
+        if (fused && tid && tid < nbr) bc0 = branch_const(a, e0.y);
+        // ---- injections, residuals and loss terms of the own buses, two
+        // threads per bus (the P and the Q part; no divergence) ----
+        double lt = 0.0;   // the thread's loss terms
+        {
+            const double *kk = reinterpret_cast<const double *>(sK);
+            double *rr = reinterpret_cast<double *>(sR);
+            double *gr = reinterpret_cast<double *>(a.r + sb + b0);
+            for (int x = tid; x < 2 * nbus; x += TB) {
+                const int b = x >> 1, im = x & 1;
+                const int4 bm = sbm[b];
+                const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+                double sk = 0.0;
+                for (int i = bm.w; i < tend; ++i) sk += kk[2 * i + im];
+                double spec = spec0, wt = wt0;
+                if (x != tid) {
+                    spec = im ? a.Qs[b0 + b] : a.Ps[b0 + b];
+                    wt = im ? a.wQ[b0 + b] : a.wP[b0 + b];
+                }
+                const double v = sW[b].x;
+                const double2 y = syd[b];
+                // P = v^2 Re conj(Yd) + sum Re K, Q = v^2 Im conj(Yd) + sum Im K
+                const double d = fma(v * v, im ? neg(y.y) : y.x, sk) - spec;
+                const double r = 2.0 * wt * d;
+                gr[x] = r;
+                rr[x] = r;
+                lt = fma(wt * d, d, lt);
             }
-            const int o = b0 + b;
-            double ps = ps0, qs = qs0, wp = wp0, wq = wq0;
-            if (b != tid) {
-                ps = a.Ps[o];
-                qs = a.Qs[o];
-                wp = a.wP[o];
-                wq = a.wQ[o];
-            }
-            const double v = sW[b].x, v2 = v * v;
-            const double2 y = syd[b];
-            const double dP = fma(v2, y.x, sKr) - ps;
-            const double dQ = fma(-v2, y.y, sKi) - qs;
-            const double2 r = make_double2(2.0 * wp * dP, 2.0 * wq * dQ);
-            a.r[sb + o] = r;
-            sR[b] = r;
-            spq[b] = fma(wp * dP, dP, wq * dQ * dQ);
+        }
+        // the window's loss partial: per warp (the warps that hold buses),
+        // then over the warps, in a fixed order
+        const int lane = tid & 31, wid = tid >> 5, nwb = min(TB >> 5, (2 * nbus + 31) >> 5);
+        if (wid < nwb) {
+            lt = warp_sum(lt);
+            if (lane == 0) swl[wid] = lt;
         }
         __syncthreads();
-        window_loss(spq, nbus, a.lpart + (long long)s * a.nwin + w);
+        if (wid == 0) {
+            double x = lane < nwb ? swl[lane] : 0.0;
+            x = warp_sum(x);
+            if (lane == 0) a.lpart[(long long)s * a.nwin + w] = x;
+        }
     }
-    // the thread's first branch: its constants before the barrier, and after
-    // it the branch gradient while the ghost residuals are in flight
-    const int2 lr = cta_branches(a);
-    const int l0 = lr.x + tid;
-    BranchConst bc0{};
-    if (a.gg && l0 < lr.y) bc0 = branch_const(a, l0);
-    if (!grid_barrier(a.bar, gridDim.x, bgen, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
+    // several scenarios: the thread's first branch of the CTA's range
+    int2 lr = make_int2(0, 0);
+    int l0 = -1;
+    if (!fused && a.gg) {
+        lr = cta_branches(a);
+        l0 = lr.x + tid;
+        if (tid && l0 < lr.y) bc0 = branch_const(a, l0);
+    }
+    if (!grid_barrier(gbar, a.bar, gridDim.x, 0, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     const int jg = nbus + tid;
     double2 rg = make_double2(0.0, 0.0);
     if (has && jg < nph) rg = a.r[sb + sslot[jg]];
-    if (a.gg && l0 < lr.y) branch_grad(a, l0, bc0);
+    if (tid == 0 && (fused ? tid < nbr : l0 >= 0 && l0 < lr.y)) bc0 = branch_const(a, fused ? e0.y : l0);
+    if (!fused && a.gg && l0 < lr.y) branch_grad(a, l0, bc0);
+    // the loss of scenario blockIdx.x (S <= items <= CTAs), by the last warp,
+    // its loads in flight with the ghost residuals'
+    if (a.L && blockIdx.x < (unsigned)a.S && (tid >> 5) == (TB >> 5) - 1) {
+        const int lane = tid & 31;
+        const double *lp = a.lpart + (long long)blockIdx.x * a.nwin;
+        double acc = 0.0;
+        for (int w2 = lane; w2 < a.nwin; w2 += 32) acc += __ldcg(lp + w2);
+        acc = warp_sum(acc);
+        if (lane == 0) a.L[blockIdx.x] = acc;
+    }
     if (has) {
         // ---- the ghost buses' residuals ----
         if (jg < nph) sR[jg] = rg;
@@ -670,22 +737,41 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             const double vv = fma(ro.x, K.x, ro.y * K.y) + fma(rq.x, M.x, rq.y * M.y);
             sK[i] = make_double2(th, vv);
         }
+        // the window's branches: h = the from-terminal's owner, k = its other bus
+        for (int j = tid; j < nbr; j += TB) {
+            int i = e0.x, l = e0.y;
+            BranchConst c = bc0;
+            if (j != tid) {
+                const int2 e = a.brl[(long long)w * a.max_nbr + j];
+                i = e.x;
+                l = e.y;
+                c = branch_const(a, l);
+            }
+            const int2 loc = sloc[i];
+            double agg = 0.0, agb = 0.0, agsh = 0.0, agt = 0.0;
+            if (l != sc.l) branch_terms<false>(c, sV[loc.x], sV[loc.y], sR[loc.x], sR[loc.y], agg, agb, agsh, agt);
+            a.gg[l] = agg;
+            a.gb[l] = agb;
+            a.gbsh[l] = agsh;
+            a.gtap[l] = agt;
+        }
         __syncthreads();
         const int pqs = (int)sp.pqs;
         const int par = (int)((sb + b0) & 1);
-        for (int b = tid; b < nbus; b += TB) {
-            const int4 bm = sbm[b];
-            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
-            double gth = 0.0, gv = 0.0;
-            for (int i = bm.w; i < tend; ++i) {
-                gth += sK[i].x;
-                gv += sK[i].y;
+        {   // two threads per bus: x = 2b + im sums the theta (im = 0) or v (im = 1) terms
+            const double *kk = reinterpret_cast<const double *>(sK);
+            for (int x = tid; x < 2 * nbus; x += TB) {
+                const int b = x >> 1, im = x & 1;
+                const int4 bm = sbm[b];
+                const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+                double g = 0.0;
+                for (int i = bm.w; i < tend; ++i) g += kk[2 * i + im];
+                if (im) {   // <r_o, 2 v_o conj(Yd)> + (sum) / v_o
+                    const double2 vw = sW[b], ro = sR[b], y = syd[b];
+                    g = fma(g, vw.y, (vw.x + vw.x) * fma(ro.x, y.x, -ro.y * y.y));
+                }
+                spq[(im ? pqs : 0) + b + par] = g;
             }
-            const double2 vw = sW[b], ro = sR[b], y = syd[b];
-            const double tv = vw.x + vw.x;
-            // <r_o, 2 v_o conj(Yd)> + (sum) / v_o
-            spq[b + par] = gth;
-            spq[pqs + b + par] = fma(gv, vw.y, tv * fma(ro.x, y.x, -ro.y * y.y));
         }
         if (a.aligned) {
             fence_proxy_async_smem();
@@ -704,9 +790,8 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             }
         }
     }
-    if (a.gg)
+    if (!fused && a.gg)
         for (int l = l0 + TB; l < lr.y; l += TB) branch_grad(a, l, branch_const(a, l));
-    if (a.L) batch_loss(a);
 }
 
 // ----------------------------------------------------------- launchers ----
@@ -728,6 +813,8 @@ static BatchArgs batch_args(Batch *b)
     a.win_bus = b->win_bus;
     a.ghost = b->ghost;
     a.max_nph = b->max_nph;
+    a.max_nbr = b->max_nbr;
+    a.brl = b->brl;
     a.desc = b->desc;
     a.slotbus = b->slotbus;
     a.tloc = b->tloc;
@@ -766,9 +853,9 @@ static cudaError_t coop_resident(K kernel, int &resident, int tb, size_t smem)
 {
     cudaError_t e;
     if (resident == 0) {
-        if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                          (int)smem)))
-            return e;
+        // set for every size: the kernels also hold a little static shared
+        // memory, which counts against the default 48 KB
+        if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
         int per_sm = 0, dev = 0, nsm = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, tb, smem))) return e;
         if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))

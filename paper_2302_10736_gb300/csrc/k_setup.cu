@@ -50,7 +50,7 @@ __global__ void k_branch_constants(int nl, const double *__restrict__ g, const d
     tcoup[ph] = make_double2(-ar * im, -ai * im);
     tself[pk] = ys_k;
     tcoup[pk] = make_double2(-br * im, -bi * im);
-    aux[l] = make_double4_32a(im, cp, sp, 0.0);   // for the parameter gradients of the adjoint
+    aux[l] = make_double4_32a(im, cp, sp, -(bl + half));   // for the parameter gradients of the adjoint
 }
 
 __global__ void k_ybus_values(int nnz, const int *__restrict__ ybeg, const int *__restrict__ yend,

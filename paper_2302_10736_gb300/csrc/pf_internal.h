@@ -130,6 +130,10 @@ pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo
 // target_nwin windows when the plain greedy cut gives fewer.
 pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac = 1, int target_nwin = 0);
 pf_status host_selfcheck(const HostTopo &H, const HostEw &E);
+// Per window, the branches whose from-terminal lies in it: {window-local
+// terminal, branch} at brl[w * max_nbr + j], j < nbr[w] (every branch once).
+pf_status host_window_branches(const HostTopo &H, const HostEw &E, std::vector<int2> &brl, std::vector<int> &nbr,
+                               int &max_nbr);
 
 // Shared-memory plan of the element-wise kernels (byte offsets, 16-aligned):
 //   bm  int4    [max_nbus]   per bus {J-slice row offset, row length, diagonal position, first terminal}
@@ -158,11 +162,14 @@ __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max
     return p;
 }
 constexpr uint32_t kMaxSmem = 227u * 1024u;
+// words of the batched kernels' grid-barrier state: parity, two counters on their own lines
+constexpr int kBarWords = 96;
 
 // Shared memory of the small-batch adjoint (k_adj1, one item per CTA): bus
 // metadata and self sums, both flows of every terminal and its two phasor
-// slots, loss / gradient staging, the phasor, residual and bus-name tables
-// of the own and ghost slots, (v, 1/v) of the own buses, the sine/cosine table.
+// slots, loss / gradient staging, the phasor,
+// residual and bus-name tables of the own and ghost slots, (v, 1/v) of the
+// own buses, the sine/cosine table.
 struct Adj1Smem {
     uint32_t bm, yd, K, M, loc, pq, V, R, W, slot, tab, total, pqs;
 };
@@ -213,7 +220,7 @@ struct Grid {
     int *tp = nullptr;                     // [nb+1]
     double2 *tself = nullptr, *tcoup = nullptr;
     int2 *br_hk = nullptr;                 // [nl] end buses (from, to) of branch l
-    double4_32a *br_aux = nullptr;         // [nl] {1/m, cos phi, sin phi, 0} of branch l (with the constants)
+    double4_32a *br_aux = nullptr;         // [nl] {1/m, cos phi, sin phi, -(b + b_sh/2)} of branch l (with the constants)
     int2 *tnbr = nullptr;                  // {other bus, kpos | EW_ACCUM}
     int *town = nullptr;                   // owner bus
     int *tpos = nullptr;                   // [2nl] sorted position of terminal t
@@ -224,7 +231,7 @@ struct Grid {
     int *tmir = nullptr;                   // [2nl] by sorted position: sorted position of the mirror terminal
     // device copies of the current parameters (branch gradients need them)
     double *p_g = nullptr, *p_b = nullptr, *p_bsh = nullptr, *p_tap = nullptr, *p_shift = nullptr;
-    unsigned int *bar = nullptr;   // grid-barrier state {arrivals, generation} of the batched kernels
+    unsigned int *bar = nullptr;   // [kBarWords] grid-barrier state of the batched kernels (ptx.cuh)
     // per-call workspace of the Ybus method's phasor step (device)
     double4_32a *ph_u = nullptr;   // [nb] {cos, sin, v, 1/v}
     double2 *ph_v = nullptr;       // [nb] V = v e^{j theta}
@@ -346,9 +353,11 @@ struct Batch {
     // item per CTA, which forms each window's phasors with its ghost buses
     // instead of a separate phase and barrier
     int ghost = 0, max_nph = 0;
-    int4 *desc = nullptr;            // [2 nwin] window descriptors (HostEw::desc)
+    int4 *desc = nullptr;            // [2 nwin] window descriptors (HostEw::desc; desc[2w+1].w = branches of w)
     int *slotbus = nullptr;          // [nwin * max_nph]
     int2 *tloc = nullptr;            // [T]
+    int max_nbr = 0;
+    int2 *brl = nullptr;             // [nwin * max_nbr] the window's branches (host_window_branches)
 };
 
 cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,

@@ -73,14 +73,16 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Grid-wide barrier for a cooperative launch (every CTA resident).  `state`
-// holds {arrival count, generation} in global memory, both zero initially;
-// the last CTA to arrive resets the count and advances the generation, so
-// the barrier needs no per-launch host state (graph replays work).  Thread 0
-// of every CTA reads the generation once, at kernel start (grid_barrier_gen):
-// it cannot move before this CTA arrives, and each barrier advances it by
-// one, so arriving needs no further read.  Waiting is bounded: after
-// `limit_ns` of the global timer the CTA records `timeout_code` in *err and
-// returns false (uniformly for the whole CTA).
+// (zero initially) holds a launch parity at [0] and two arrival counters at
+// [32] and [64], on separate 128-byte lines.  A launch uses the counter of
+// its parity, which is zero when it starts: the k-th barrier of the launch
+// (k = 0, 1, ...) is complete when the counter reaches (k + 1) nblocks, and
+// every waiting CTA polls the counter itself.  The CTA that completes barrier
+// 0 flips the parity for the next launch (every CTA has read it by then), and
+// CTA 0 zeroes the other counter, which the previous launch used.  So the
+// barrier needs no per-launch host state (graph replays work).  Waiting is
+// bounded: after `limit_ns` of the global timer the CTA records
+// `timeout_code` in *err and returns false (uniformly for the whole CTA).
 __device__ __forceinline__ uint64_t global_timer_ns()
 {
     uint64_t t;
@@ -88,40 +90,49 @@ __device__ __forceinline__ uint64_t global_timer_ns()
     return t;
 }
 
-__device__ __forceinline__ unsigned int grid_barrier_gen(const unsigned int *state)
+struct GridBar {
+    unsigned int *cnt;     // thread 0: this launch's arrival counter
+    unsigned int parity;   // thread 0: this launch's parity
+};
+
+// at kernel start, before any CTA can have arrived
+__device__ __forceinline__ GridBar grid_barrier_begin(unsigned int *state)
 {
-    return threadIdx.x == 0 ? *(const volatile unsigned int *)(state + 1) : 0u;
+    GridBar b{nullptr, 0u};
+    if (threadIdx.x == 0) {
+        b.parity = *(volatile unsigned int *)state & 1u;
+        b.cnt = state + 32u + 32u * b.parity;
+        if (blockIdx.x == 0) *(volatile unsigned int *)(state + 32u + 32u * (b.parity ^ 1u)) = 0u;
+    }
+    return b;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned int *state, unsigned int nblocks, unsigned int &gen, int *err,
-                                             int timeout_code, uint64_t limit_ns)
+__device__ __forceinline__ bool grid_barrier(const GridBar &b, unsigned int *state, unsigned int nblocks,
+                                             unsigned int k, int *err, int timeout_code, uint64_t limit_ns)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = state + 1;
-        const unsigned int g0 = gen;
         int ok = 1;
+        const unsigned int target = (k + 1u) * nblocks;
         __threadfence();   // this CTA's global writes before its arrival
-        const unsigned int arrived = atomicAdd(state, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(state, 0u);
-            // release everyone: the reset (and everything before it) is visible
-            // to a CTA that sees the new generation
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(state + 1) : "memory");
+        unsigned int arrived;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(b.cnt) : "memory");
+        if (arrived + 1u == target) {
+            if (k == 0) *(volatile unsigned int *)state = b.parity ^ 1u;
         } else {
             const uint64_t t0 = global_timer_ns();
-            while (*vgen == g0) {
+            for (;;) {
+                unsigned int c;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(b.cnt) : "memory");
+                if ((int)(c - target) >= 0) break;
                 if (global_timer_ns() - t0 > limit_ns) {
                     atomicExch(err, timeout_code);
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
             }
         }
-        __threadfence();   // acquire the other CTAs' writes
-        gen = g0 + 1;
         s_ok = ok;
     }
     __syncthreads();

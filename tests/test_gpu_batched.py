@@ -214,7 +214,7 @@ def oracle_adjoint(gr, vm, va, Ps, Qs, wP, wQ, outage=None):
     return Ls, gvm, gva, gp
 
 
-@pytest.mark.parametrize("S,with_outage", [(1, False), (3, True)])
+@pytest.mark.parametrize("S,with_outage", [(1, False), (1, True), (3, True)])
 def test_adjoint_matches_oracle(pf, S, with_outage):
     gr, vm, va, Ps, Qs, wP, wQ = _adjoint_case(500, 700, 31 + S, S)
     outage = None
