@@ -195,10 +195,12 @@ static pf_status build_ew_layout(Grid *g, int tb, cudaStream_t s)
     g->arena.release(g->ew.desc);
     g->arena.release(g->ew.slotbus);
     g->arena.release(g->ew.bmeta);
+    g->arena.release(g->ew.rorder);
     g->arena.release(g->ew.tloc);
     g->ew = EwDev{};
     if ((st = upload(g->arena, &g->ew.desc, E.desc, s)) || (st = upload(g->arena, &g->ew.slotbus, E.slotbus, s)) ||
-        (st = upload(g->arena, &g->ew.bmeta, E.bmeta, s)) || (st = upload(g->arena, &g->ew.tloc, E.tloc, s)))
+        (st = upload(g->arena, &g->ew.bmeta, E.bmeta, s)) || (st = upload(g->arena, &g->ew.rorder, E.rorder, s)) ||
+        (st = upload(g->arena, &g->ew.tloc, E.tloc, s)))
         return st;
     g->ew.tb = E.tb;
     g->ew.nwin = E.nwin;

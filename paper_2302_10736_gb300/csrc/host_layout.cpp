@@ -230,6 +230,15 @@ pf_status host_ew(const HostTopo &H, int tb, HostEw &E, int tfac, int target_nwi
         for (int o = E.win_bus[w]; o < E.win_bus[w + 1]; ++o)
             E.bmeta[o] = make_int4(2 * (H.rp[o] - H.rp[E.win_bus[w]]), H.rp[o + 1] - H.rp[o], H.kd[o],
                                    H.tp[o] - H.tp[E.win_bus[w]]);
+    E.rorder.resize(nb);
+    for (int w = 0; w < E.nwin; ++w) {
+        const int b0 = E.win_bus[w], b1 = E.win_bus[w + 1];
+        int *ord = E.rorder.data() + b0;
+        for (int j = 0; j < b1 - b0; ++j) ord[j] = j;
+        std::stable_sort(ord, ord + (b1 - b0), [&](int x, int y) {
+            return H.tp[b0 + x + 1] - H.tp[b0 + x] > H.tp[b0 + y + 1] - H.tp[b0 + y];
+        });
+    }
     return PF_OK;
 }
 
@@ -287,6 +296,13 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
             const int lrow = 2 * (H.rp[o] - H.rp[b0]), d = H.rp[o + 1] - H.rp[o];
             CHECK(E.bmeta[o].x == lrow && E.bmeta[o].y == d && E.bmeta[o].z == H.kd[o] &&
                       E.bmeta[o].w == H.tp[o] - H.tp[b0], "bus %d window metadata", o);
+            const int j = o - b0, x = E.rorder[o];
+            CHECK(x >= 0 && x < b1 - b0, "window %d reduction order entry %d", w, j);
+            if (j > 0) {
+                const int y = E.rorder[o - 1];
+                CHECK(H.tp[b0 + y + 1] - H.tp[b0 + y] >= H.tp[b0 + x + 1] - H.tp[b0 + x],
+                      "window %d reduction order not by decreasing terminal count", w);
+            }
             CHECK(lrow >= 0 && lrow + 2 * d <= L, "bus %d row slice outside the window slice", o);
             CHECK(lrow + H.kd[o] + d < L, "bus %d diagonal staging index", o);
             for (int p = H.tp[o]; p < H.tp[o + 1]; ++p) {
@@ -294,6 +310,11 @@ pf_status host_selfcheck(const HostTopo &H, const HostEw &E)
                 CHECK(lrow + kp + d < L, "terminal %d staging index", p);
                 CHECK(p - H.tp[b0] >= 0 && p - H.tp[b0] < E.max_nt, "terminal %d local index", p);
             }
+        }
+        {
+            std::vector<char> seen(nbus, 0);
+            for (int o = b0; o < b1; ++o) seen[E.rorder[o]]++;
+            for (int j = 0; j < nbus; ++j) CHECK(seen[j] == 1, "window %d reduction order is not a permutation", w);
         }
     }
     // ghost buses: sorted, outside the window, and every terminal's slot

@@ -54,7 +54,7 @@ namespace pf {
 struct EwArgs {
     int nnz, max_nbus, max_nt, max_L, max_nph, aligned;
     const int4 *desc, *bmeta;
-    const int *slotbus, *town;
+    const int *slotbus, *town, *rorder;
     const double2 *yd, *tcoup, *trig;
     const int2 *tloc;
     const double *vm, *va;
@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
     double2 *sV = reinterpret_cast<double2 *>(smem + sp.ph);                 // v e^{j theta}
     double2 *sU = sV + a.max_nph;                                            // (cos, sin)
     double2 *sW = sU + a.max_nph;                                            // (v, 1/v)
+    int *sord = reinterpret_cast<int *>(smem + sp.ord);                     // reduction thread -> bus
     double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x, w = blockIdx.x;
     // two levels of dependent loads: the window's records (descriptor, the
@@ -110,9 +111,11 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
     // in registers until the phasors are done so its latency hides behind them
     int4 bmo = make_int4(0, 0, 0, 0);
     double2 ydo = make_double2(0.0, 0.0);
+    int ordo = 0;
     if (tid < nbus) {
         bmo = a.bmeta[b0 + tid];
         ydo = a.yd[b0 + tid];
+        ordo = a.rorder[b0 + tid];
     }
     double2 yc = make_double2(0.0, 0.0);
     int2 nq = make_int2(0, 0);
@@ -148,6 +151,7 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
     if (tid < nbus) {
         sbm[tid] = bmo;
         syd[tid] = ydo;
+        sord[tid] = ordo;
     }
     __syncthreads();
 
@@ -190,12 +194,14 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
     // ---- reduction: its terminals in sorted order onto every bus ----
     const int pqs = (int)sp.pqs, par = b0 & 1;
     if (JAC) {
-        // two threads per bus: x = 2b + im sums the real (im = 0) or imaginary
-        // (im = 1) parts of K and writes the entries that depend on them only;
-        // the arithmetic is uniform across the pair (no divergence)
+        // two threads per bus: x = 2b' + im sums the real (im = 0) or imaginary
+        // (im = 1) parts of K of bus b = sord[b'] and writes the entries that
+        // depend on them only; the arithmetic is uniform across the pair (no
+        // divergence), and with the buses taken by decreasing terminal count
+        // the lanes of a warp loop about equally long
         const double *kg = reinterpret_cast<const double *>(skg);   // K.x, K.y, G.x, G.y per terminal
         for (int x = tid; x < 2 * nbus; x += TB) {
-            const int b = x >> 1, im = x & 1;
+            const int b = sord[x >> 1], im = x & 1;
             const int4 bm = sbm[b];
             const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
             const int d = bm.y;
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
         // two threads per bus as above; the magnitude comes back from L1
         const double *k1 = reinterpret_cast<const double *>(skg);   // K.x, K.y per terminal
         for (int x = tid; x < 2 * nbus; x += TB) {
-            const int b = x >> 1, im = x & 1;
+            const int b = sord[x >> 1], im = x & 1;
             const int4 bm = sbm[b];
             const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
             double sK = 0.0;
@@ -300,6 +306,7 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.desc = L.desc;
     a.slotbus = L.slotbus;
     a.bmeta = L.bmeta;
+    a.rorder = L.rorder;
     a.town = g->town;
     a.yd = g->bus_yd;
     a.tcoup = g->tcoup;

@@ -122,6 +122,10 @@ struct HostEw {
     // per bus o of window w: {2 (rowptr[o] - rowptr[b0]) (its row in the
     // window's J slice), Ybus row length, diagonal position, tp[o] - tp[b0]}
     std::vector<int4> bmeta;
+    // per window, its buses (window-local) by decreasing terminal count (ties
+    // in bus order) at rorder[b0 ...]: the reduction's thread-to-bus map, so
+    // that the lanes of a warp loop over about as many terminals
+    std::vector<int> rorder;
 };
 
 pf_status host_topology(int nb, int nl, const int *from, const int *to, HostTopo &H);
@@ -142,8 +146,10 @@ pf_status host_window_branches(const HostTopo &H, const HostEw &E, std::vector<i
 //   kp  int     [max_nt]     per terminal slot position | EW_ACCUM (Jacobian kernel)
 //   jst double  [2 max_L]    the window's J slice (P half, then Q half)
 //   pq  double  [2 pqs]      P then Q of the window, parity-aligned with global memory
+//   ph                       phasor table (below)
+//   ord int     [max_nbus]   the reduction's thread-to-bus map (HostEw::rorder)
 struct EwSmem {
-    uint32_t bm, yd, kg, kp, jst, pq, pqs, ph, total;
+    uint32_t bm, yd, kg, kp, jst, pq, pqs, ph, ord, total;
 };
 // max_nph > 0 adds a phasor table of that many slots: V = v e^{j theta}, and
 // with the Jacobian also (cos, sin) and (v, 1/v), each a double2 array
@@ -158,7 +164,8 @@ __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max
     p.jst = p.kp + (jac ? ((4u * (uint32_t)max_nt + 15u) & ~15u) : 0u);
     p.pq = p.jst + (jac ? 16u * (uint32_t)max_L : 0u);
     p.ph = p.pq + 16u * p.pqs;
-    p.total = p.ph + (jac ? 48u : 16u) * (uint32_t)max_nph;
+    p.ord = p.ph + (jac ? 48u : 16u) * (uint32_t)max_nph;
+    p.total = p.ord + ((4u * (uint32_t)max_nbus + 15u) & ~15u);
     return p;
 }
 constexpr uint32_t kMaxSmem = 227u * 1024u;
@@ -201,6 +208,7 @@ struct EwDev {
     int4 *desc = nullptr;     // [2 nwin] window descriptors (HostEw::desc)
     int *slotbus = nullptr;   // [nwin * max_nph] bus of every phasor slot
     int4 *bmeta = nullptr;    // [nb] window-relative bus metadata (HostEw::bmeta)
+    int *rorder = nullptr;    // [nb] the reduction's thread-to-bus map (HostEw::rorder)
     int2 *tloc = nullptr;     // [T] {phasor slot of the other bus, slot position | flags}
 };
 
