@@ -125,6 +125,9 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
         (e = b->arena.alloc(&b->win_bus, E.win_bus.size())) ||
         (e = cudaMemcpyAsync(b->win_bus, E.win_bus.data(), sizeof(int) * E.win_bus.size(), cudaMemcpyHostToDevice,
                              st)) ||
+        (e = b->arena.alloc(&b->rorder, E.rorder.size())) ||
+        (e = cudaMemcpyAsync(b->rorder, E.rorder.data(), sizeof(int) * E.rorder.size(), cudaMemcpyHostToDevice,
+                             st)) ||
         (ghost && ((e = b->arena.alloc(&b->desc, E.desc.size())) || (e = b->arena.alloc(&b->slotbus, E.slotbus.size())) ||
                    (e = b->arena.alloc(&b->tloc, E.tloc.size())) ||
                    (e = cudaMemcpyAsync(b->desc, E.desc.data(), sizeof(int4) * E.desc.size(), cudaMemcpyHostToDevice,

@@ -44,7 +44,7 @@ constexpr uint64_t kBatchBarrierNs = 2000000000ull;   // bounded grid-barrier wa
 struct BatchArgs {
     int S, nb, nl, nnz, nwin, max_nbus, max_nt, max_L, aligned;
     int ghost, max_nph, max_nbr;
-    const int *win_bus, *tp, *rp, *kd, *town, *tmir, *tpos, *slotbus;
+    const int *win_bus, *tp, *rp, *kd, *town, *tmir, *tpos, *slotbus, *rorder;
     const int2 *tloc, *brl;
     const int4 *desc;
     const int2 *tnbr;
@@ -159,13 +159,16 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
         const long long sb = (long long)s * a.nb;
         __syncthreads();   // previous item's shared-memory readers are done
         batch_window_meta(a, sc, b0, b1, t0, sbm, syd);
+        // the reduction thread's bus: the window's buses by decreasing terminal count
         double4_32a ub = make_double4_32a(0.0, 0.0, 0.0, 0.0);
         double vb = 0.0;
+        int bo = 0;
         if (tid < nbus) {
+            bo = a.rorder[b0 + tid];
             if (JAC)
-                ub = a.U[sb + b0 + tid];
+                ub = a.U[sb + b0 + bo];
             else
-                vb = a.vm[sb + b0 + tid];
+                vb = a.vm[sb + b0 + bo];
         }
         __syncthreads();
         for (int i = tid; i < nt; i += TB) {
@@ -206,7 +209,8 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
         __syncthreads();
         const int pqs = (int)sp.pqs;
         const int par = (int)((sb + b0) & 1);
-        for (int b = tid; b < nbus; b += TB) {
+        for (int x = tid; x < nbus; x += TB) {
+            const int b = x == tid ? bo : a.rorder[b0 + x];
             const int4 bm = sbm[b];
             const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
             const double2 y = syd[b];
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
                         jst[Ls + pos + d] += G.y;
                     }
                 }
-                const double4_32a uo = b == tid ? ub : a.U[sb + b0 + b];
+                const double4_32a uo = x == tid ? ub : a.U[sb + b0 + b];
                 const double v = uo.z, iv = uo.w, v2 = v * v, tv = v + v;
                 const int pos = bm.x + bm.z;
                 jst[pos] = neg(sKi);
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
                     sKr += skg[i].x;
                     sKi += skg[i].y;
                 }
-                const double v = b == tid ? vb : a.vm[sb + b0 + b], v2 = v * v;
+                const double v = x == tid ? vb : a.vm[sb + b0 + b], v2 = v * v;
                 spq[b + par] = fma(v2, y.x, sKr);
                 spq[pqs + b + par] = fma(-v2, y.y, sKi);
             }
@@ -424,6 +428,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
         const int t0 = a.tp[b0], nt = a.tp[b1] - t0;
         const long long sb = (long long)s * a.nb;
+        const int bo = tid < nbus ? a.rorder[b0 + tid] : 0;   // by decreasing terminal count
         __syncthreads();
         batch_window_meta(a, sc, b0, b1, t0, sbm, syd);
         for (int i = tid; i < nt; i += TB) {
@@ -436,7 +441,8 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
             skg[i] = make_double2(Kr, Ki);
         }
         __syncthreads();
-        for (int b = tid; b < nbus; b += TB) {
+        for (int x = tid; x < nbus; x += TB) {
+            const int b = x == tid ? bo : a.rorder[b0 + x];
             const int4 bm = sbm[b];
             const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
             double sKr = 0.0, sKi = 0.0;
@@ -451,7 +457,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
             const double dQ = fma(-v2, y.y, sKi) - a.Qs[o];
             const double wp = a.wP[o], wq = a.wQ[o];
             a.r[sb + o] = make_double2(2.0 * wp * dP, 2.0 * wq * dQ);
-            spq[b] = fma(wp * dP, dP, wq * dQ * dQ);
+            spq[x] = fma(wp * dP, dP, wq * dQ * dQ);
         }
         __syncthreads();
         window_loss(spq, nbus, a.lpart + (long long)s * a.nwin + w);
@@ -465,6 +471,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
         const int t0 = a.tp[b0], nt = a.tp[b1] - t0;
         const long long sb = (long long)s * a.nb;
+        const int bo = tid < nbus ? a.rorder[b0 + tid] : 0;
         __syncthreads();
         batch_window_meta(a, sc, b0, b1, t0, sbm, syd);
         __syncthreads();
@@ -485,7 +492,8 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         __syncthreads();
         const int pqs = (int)sp.pqs;
         const int par = (int)((sb + b0) & 1);
-        for (int b = tid; b < nbus; b += TB) {
+        for (int x = tid; x < nbus; x += TB) {
+            const int b = x == tid ? bo : a.rorder[b0 + x];
             const int4 bm = sbm[b];
             const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
             double gth = 0.0, gv = 0.0;
@@ -568,6 +576,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
     const bool fused = a.gg && a.S == 1;
     int nbr = 0;                          // branches of the window (fused)
     int2 e0 = make_int2(0, 0);            // the thread's first: {window-local from-terminal, branch}
+    int bo = 0;                           // the bus of the thread's first bus-loop slot
     BranchConst bc0{};
     if (has) {
         s = (int)(blockIdx.x / a.nwin);
@@ -599,7 +608,8 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         // two threads per bus below: x = 2b + im, im = 0 the P part, 1 the Q part
         double spec0 = 0.0, wt0 = 0.0;
         if (tid < 2 * nbus) {
-            const int o = b0 + (tid >> 1);
+            bo = a.rorder[b0 + (tid >> 1)];   // buses by decreasing terminal count
+            const int o = b0 + bo;
             spec0 = (tid & 1) ? a.Qs[o] : a.Ps[o];
             wt0 = (tid & 1) ? a.wQ[o] : a.wP[o];
         }
@@ -664,7 +674,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             double *rr = reinterpret_cast<double *>(sR);
             double *gr = reinterpret_cast<double *>(a.r + sb + b0);
             for (int x = tid; x < 2 * nbus; x += TB) {
-                const int b = x >> 1, im = x & 1;
+                const int b = x == tid ? bo : a.rorder[b0 + (x >> 1)], im = x & 1;
                 const int4 bm = sbm[b];
                 const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
                 double sk = 0.0;
@@ -679,8 +689,8 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
                 // P = v^2 Re conj(Yd) + sum Re K, Q = v^2 Im conj(Yd) + sum Im K
                 const double d = fma(v * v, im ? neg(y.y) : y.x, sk) - spec;
                 const double r = 2.0 * wt * d;
-                gr[x] = r;
-                rr[x] = r;
+                gr[2 * b + im] = r;
+                rr[2 * b + im] = r;
                 lt = fma(wt * d, d, lt);
             }
         }
@@ -761,7 +771,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         {   // two threads per bus: x = 2b + im sums the theta (im = 0) or v (im = 1) terms
             const double *kk = reinterpret_cast<const double *>(sK);
             for (int x = tid; x < 2 * nbus; x += TB) {
-                const int b = x >> 1, im = x & 1;
+                const int b = x == tid ? bo : a.rorder[b0 + (x >> 1)], im = x & 1;
                 const int4 bm = sbm[b];
                 const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
                 double g = 0.0;
@@ -811,6 +821,7 @@ static BatchArgs batch_args(Batch *b)
     a.max_nt = b->max_nt;
     a.max_L = b->max_L;
     a.win_bus = b->win_bus;
+    a.rorder = b->rorder;
     a.ghost = b->ghost;
     a.max_nph = b->max_nph;
     a.max_nbr = b->max_nbr;

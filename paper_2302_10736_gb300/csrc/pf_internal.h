@@ -357,6 +357,7 @@ struct Batch {
     // owns a bus in the reduction and loops over up to tfac terminals
     int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0;
     int *win_bus = nullptr;          // [nwin+1]
+    int *rorder = nullptr;           // [nb] the reductions' thread-to-bus map (HostEw::rorder)
     // small batches (about one item per SM): the adjoint runs k_adj1, one
     // item per CTA, which forms each window's phasors with its ghost buses
     // instead of a separate phase and barrier
