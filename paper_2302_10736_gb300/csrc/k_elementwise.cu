@@ -45,6 +45,8 @@
 // contiguous slice of each of the P and Q halves of J (canonical layout): it
 // is assembled in shared memory and written back with TMA bulk stores,
 // together with P and Q.
+#include <algorithm>
+
 #include "fastmath.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
@@ -52,7 +54,7 @@
 namespace pf {
 
 struct EwArgs {
-    int nnz, max_nbus, max_nt, max_L, max_nph, aligned;
+    int nnz, nwin, max_nbus, max_nt, max_L, max_nph, aligned;
     const int4 *desc, *bmeta;
     const int *slotbus, *town, *rorder;
     const double2 *yd, *tcoup, *trig;
@@ -74,9 +76,12 @@ __device__ __forceinline__ void store_range(double *x, const double *s, int b0, 
     if ((b1 - ge) & 1) x[b1 - 1] = s[b1 - 1 - b0 + par];
 }
 
-// At most 48 registers: 5 CTAs of 256 or 10 of 128 threads per SM.
-template <bool JAC>
-__global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
+// One window per CTA; with PERSIST the CTAs loop over the windows
+// (grid-strided), so that the first windows' outputs leave while later
+// windows are evaluated (outputs in host memory, where the host link is the
+// bound).
+template <bool JAC, bool PERSIST>
+__device__ __forceinline__ void ew_windows(const EwArgs &a)
 {
     extern __shared__ __align__(16) char smem[];
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, JAC ? a.max_L : 0, JAC, a.max_nph);
@@ -91,194 +96,216 @@ __global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
     double2 *sW = sU + a.max_nph;                                            // (v, 1/v)
     int *sord = reinterpret_cast<int *>(smem + sp.ord);                     // reduction thread -> bus
     double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
-    const int tid = threadIdx.x, TB = blockDim.x, w = blockIdx.x;
-    // two levels of dependent loads: the window's records (descriptor, the
-    // bus of the thread's first phasor slot), then everything they index
-    const int *sbus = a.slotbus + (long long)w * a.max_nph;
-    const int o0 = tid < a.max_nph ? sbus[tid] : 0;
-    const int4 d0 = a.desc[2 * w], d1 = a.desc[2 * w + 1];
-    const int b0 = d0.x, nbus = d0.y, b1 = b0 + nbus, t0 = d0.z, nt = d0.w;
-    const int r0 = d1.x, L = JAC ? d1.y : 0, nph = d1.z;
+    const int tid = threadIdx.x, TB = blockDim.x;
+    for (int w = blockIdx.x; w < a.nwin; w += gridDim.x) {
+        if (PERSIST) __syncthreads();   // the previous window's shared-memory readers are done
+        // two levels of dependent loads: the window's records (descriptor, the
+        // bus of the thread's first phasor slot), then everything they index
+        const int *sbus = a.slotbus + (long long)w * a.max_nph;
+        const int o0 = tid < a.max_nph ? sbus[tid] : 0;
+        const int4 d0 = a.desc[2 * w], d1 = a.desc[2 * w + 1];
+        const int b0 = d0.x, nbus = d0.y, b1 = b0 + nbus, t0 = d0.z, nt = d0.w;
+        const int r0 = d1.x, L = JAC ? d1.y : 0, nph = d1.z;
 
-    // ---- loads: voltages of the first table slot, bus metadata, the first
-    // terminal, the sine/cosine table ----
-    double th = 0.0, v = 0.0;
-    if (tid < nph) {
-        th = a.va[o0];
-        v = a.vm[o0];
-    }
-    // the bus thread's metadata (a window has at most blockDim.x buses), kept
-    // in registers until the phasors are done so its latency hides behind them
-    int4 bmo = make_int4(0, 0, 0, 0);
-    double2 ydo = make_double2(0.0, 0.0);
-    int ordo = 0;
-    if (tid < nbus) {
-        bmo = a.bmeta[b0 + tid];
-        ydo = a.yd[b0 + tid];
-        ordo = a.rorder[b0 + tid];
-    }
-    double2 yc = make_double2(0.0, 0.0);
-    int2 nq = make_int2(0, 0);
-    int ol = 0;
-    if (tid < nt) {
-        yc = a.tcoup[t0 + tid];
-        nq = a.tloc[t0 + tid];
-        ol = a.town[t0 + tid] - b0;
-    }
-    const double2 *trig = a.trig + (w % kTrigCopies) * kTrigN;
-    for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
-    __syncthreads();
+        // ---- loads: voltages of the first table slot, bus metadata, the first
+        // terminal, the sine/cosine table ----
+        double th = 0.0, v = 0.0;
+        if (tid < nph) {
+            th = a.va[o0];
+            v = a.vm[o0];
+        }
+        // the bus thread's metadata (a window has at most blockDim.x buses), kept
+        // in registers until the phasors are done so its latency hides behind them
+        int4 bmo = make_int4(0, 0, 0, 0);
+        double2 ydo = make_double2(0.0, 0.0);
+        int ordo = 0;
+        if (tid < nbus) {
+            bmo = a.bmeta[b0 + tid];
+            ydo = a.yd[b0 + tid];
+            ordo = a.rorder[b0 + tid];
+        }
+        double2 yc = make_double2(0.0, 0.0);
+        int2 nq = make_int2(0, 0);
+        int ol = 0;
+        if (tid < nt) {
+            yc = a.tcoup[t0 + tid];
+            nq = a.tloc[t0 + tid];
+            ol = a.town[t0 + tid] - b0;
+        }
+        if (!PERSIST || w == (int)blockIdx.x) {
+            const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
+            for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
+        }
+        __syncthreads();
 
-    // ---- phasor table of the window (Sec. IV-B.1 step 1, own and ghost buses) ----
-    for (int j = tid; j < nph; j += TB) {
-        if (j != tid) {
-            const int o = sbus[j];
-            th = a.va[o];
-            v = a.vm[o];
-        }
-        double s, c;
-        fast_sincos(th, tab, &s, &c);
-        sV[j] = make_double2(v * c, v * s);
-        if (JAC) {
-            sU[j] = make_double2(c, s);
-            // 1/v only for the window's own buses: warps of ghost slots skip it
-            // (a warp-uniform branch), mixed warps compute it for all lanes
-            double iv = 0.0;
-            if (__any_sync(__activemask(), j < nbus)) iv = fast_rcp(v);
-            sW[j] = make_double2(v, iv);
-        }
-    }
-    if (tid < nbus) {
-        sbm[tid] = bmo;
-        syd[tid] = ydo;
-        sord[tid] = ordo;
-    }
-    __syncthreads();
-
-    // ---- evaluation: one terminal per thread ----
-    for (int i = tid; i < nt; i += TB) {
-        if (i != tid) {
-            yc = a.tcoup[t0 + i];
-            nq = a.tloc[t0 + i];
-            ol = a.town[t0 + i] - b0;
-        }
-        const double2 Vo = sV[ol];
-        if (JAC) {
-            const double2 uq = sU[nq.x];
-            const double vq = sW[nq.x].x;
-            const double Er = fma(Vo.x, uq.x, Vo.y * uq.y);   // V_o conj(U_q)
-            const double Ei = fma(Vo.y, uq.x, -Vo.x * uq.y);
-            const double Gr = fma(yc.x, Er, yc.y * Ei);       // conj(Yc) E = dS_t/dv_q
-            const double Gi = fma(yc.x, Ei, -yc.y * Er);
-            const double Kr = vq * Gr, Ki = vq * Gi;           // K_t = v_q G
-            skg[2 * i] = make_double2(Kr, Ki);
-            skg[2 * i + 1] = make_double2(Gr, Gi);
-            skp[i] = nq.y;
-            if (!(nq.y & EW_ACCUM)) {
-                const int4 bm = sbm[ol];
-                const int pos = bm.x + (nq.y & EW_KMASK), d = bm.y;
-                jst[pos] = Ki;           // J11 = Re(-j K)
-                jst[pos + d] = Gr;       // J12
-                jst[L + pos] = neg(Kr);  // J21 = Im(-j K)
-                jst[L + pos + d] = Gi;   // J22
+        // ---- phasor table of the window (Sec. IV-B.1 step 1, own and ghost buses) ----
+        for (int j = tid; j < nph; j += TB) {
+            if (j != tid) {
+                const int o = sbus[j];
+                th = a.va[o];
+                v = a.vm[o];
             }
-        } else {
-            const double2 Vq = sV[nq.x];
-            const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y);   // V_o conj(V_q)
-            const double Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
-            skg[i] = make_double2(fma(yc.x, Wr, yc.y * Wi), fma(yc.x, Wi, -yc.y * Wr));   // K_t
+            double s, c;
+            fast_sincos(th, tab, &s, &c);
+            sV[j] = make_double2(v * c, v * s);
+            if (JAC) {
+                sU[j] = make_double2(c, s);
+                // 1/v only for the window's own buses: warps of ghost slots skip it
+                // (a warp-uniform branch), mixed warps compute it for all lanes
+                double iv = 0.0;
+                if (__any_sync(__activemask(), j < nbus)) iv = fast_rcp(v);
+                sW[j] = make_double2(v, iv);
+            }
         }
-    }
-    __syncthreads();
+        if (tid < nbus) {
+            sbm[tid] = bmo;
+            syd[tid] = ydo;
+            sord[tid] = ordo;
+        }
+        __syncthreads();
 
-    // ---- reduction: its terminals in sorted order onto every bus ----
-    const int pqs = (int)sp.pqs, par = b0 & 1;
-    if (JAC) {
-        // two threads per bus: x = 2b' + im sums the real (im = 0) or imaginary
-        // (im = 1) parts of K of bus b = sord[b'] and writes the entries that
-        // depend on them only; the arithmetic is uniform across the pair (no
-        // divergence), and with the buses taken by decreasing terminal count
-        // the lanes of a warp loop about equally long
-        const double *kg = reinterpret_cast<const double *>(skg);   // K.x, K.y, G.x, G.y per terminal
-        for (int x = tid; x < 2 * nbus; x += TB) {
-            const int b = sord[x >> 1], im = x & 1;
-            const int4 bm = sbm[b];
-            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
-            const int d = bm.y;
-            double sK = 0.0;
-            for (int i = bm.w; i < tend; ++i) {
-                sK += kg[4 * i + im];
-                const int kp = skp[i];
-                if (kp & EW_ACCUM) {   // later branch of a parallel run: add into the run's slot
-                    const int pos = bm.x + (kp & EW_KMASK);
-                    if (im) {
-                        jst[pos] += kg[4 * i + 1];           // J11 += Re(-j K)
-                        jst[L + pos + d] += kg[4 * i + 3];   // J22 += Im G
-                    } else {
-                        jst[pos + d] += kg[4 * i + 2];       // J12 += Re G
-                        jst[L + pos] -= kg[4 * i];           // J21 += Im(-j K)
+        // ---- evaluation: one terminal per thread ----
+        for (int i = tid; i < nt; i += TB) {
+            if (i != tid) {
+                yc = a.tcoup[t0 + i];
+                nq = a.tloc[t0 + i];
+                ol = a.town[t0 + i] - b0;
+            }
+            const double2 Vo = sV[ol];
+            if (JAC) {
+                const double2 uq = sU[nq.x];
+                const double vq = sW[nq.x].x;
+                const double Er = fma(Vo.x, uq.x, Vo.y * uq.y);   // V_o conj(U_q)
+                const double Ei = fma(Vo.y, uq.x, -Vo.x * uq.y);
+                const double Gr = fma(yc.x, Er, yc.y * Ei);       // conj(Yc) E = dS_t/dv_q
+                const double Gi = fma(yc.x, Ei, -yc.y * Er);
+                const double Kr = vq * Gr, Ki = vq * Gi;           // K_t = v_q G
+                skg[2 * i] = make_double2(Kr, Ki);
+                skg[2 * i + 1] = make_double2(Gr, Gi);
+                skp[i] = nq.y;
+                if (!(nq.y & EW_ACCUM)) {
+                    const int4 bm = sbm[ol];
+                    const int pos = bm.x + (nq.y & EW_KMASK), d = bm.y;
+                    jst[pos] = Ki;           // J11 = Re(-j K)
+                    jst[pos + d] = Gr;       // J12
+                    jst[L + pos] = neg(Kr);  // J21 = Im(-j K)
+                    jst[L + pos + d] = Gi;   // J22
+                }
+            } else {
+                const double2 Vq = sV[nq.x];
+                const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y);   // V_o conj(V_q)
+                const double Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
+                skg[i] = make_double2(fma(yc.x, Wr, yc.y * Wi), fma(yc.x, Wi, -yc.y * Wr));   // K_t
+            }
+        }
+        __syncthreads();
+
+        // ---- reduction: its terminals in sorted order onto every bus ----
+        const int pqs = (int)sp.pqs, par = b0 & 1;
+        if (JAC) {
+            // two threads per bus: x = 2b' + im sums the real (im = 0) or imaginary
+            // (im = 1) parts of K of bus b = sord[b'] and writes the entries that
+            // depend on them only; the arithmetic is uniform across the pair (no
+            // divergence), and with the buses taken by decreasing terminal count
+            // the lanes of a warp loop about equally long
+            const double *kg = reinterpret_cast<const double *>(skg);   // K.x, K.y, G.x, G.y per terminal
+            for (int x = tid; x < 2 * nbus; x += TB) {
+                const int b = sord[x >> 1], im = x & 1;
+                const int4 bm = sbm[b];
+                const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+                const int d = bm.y;
+                double sK = 0.0;
+                for (int i = bm.w; i < tend; ++i) {
+                    sK += kg[4 * i + im];
+                    const int kp = skp[i];
+                    if (kp & EW_ACCUM) {   // later branch of a parallel run: add into the run's slot
+                        const int pos = bm.x + (kp & EW_KMASK);
+                        if (im) {
+                            jst[pos] += kg[4 * i + 1];           // J11 += Re(-j K)
+                            jst[L + pos + d] += kg[4 * i + 3];   // J22 += Im G
+                        } else {
+                            jst[pos + d] += kg[4 * i + 2];       // J12 += Re G
+                            jst[L + pos] -= kg[4 * i];           // J21 += Im(-j K)
+                        }
                     }
                 }
+                const double2 y = syd[b], vw = sW[b];
+                const double vo = vw.x, iv = vw.y, v2 = vo * vo, tv = vo + vo;
+                // real part: Re conj(Yd) = y.x; imaginary part: Im conj(Yd) = -y.y (sign flips are exact)
+                const double yr = im ? neg(y.y) : y.x;
+                const int pos = bm.x + bm.z;
+                jst[(im ? 0 : L) + pos] = neg_if(sK, im);             // Re / Im of j sum K
+                jst[(im ? L : 0) + pos + d] = fma(tv, yr, sK * iv);   // 2 v conj(Yd) + sum K / v
+                spq[(im ? pqs : 0) + b + par] = fma(v2, yr, sK);      // S = v^2 conj(Yd) + sum K
             }
-            const double2 y = syd[b], vw = sW[b];
-            const double vo = vw.x, iv = vw.y, v2 = vo * vo, tv = vo + vo;
-            // real part: Re conj(Yd) = y.x; imaginary part: Im conj(Yd) = -y.y (sign flips are exact)
-            const double yr = im ? neg(y.y) : y.x;
-            const int pos = bm.x + bm.z;
-            jst[(im ? 0 : L) + pos] = neg_if(sK, im);             // Re / Im of j sum K
-            jst[(im ? L : 0) + pos + d] = fma(tv, yr, sK * iv);   // 2 v conj(Yd) + sum K / v
-            spq[(im ? pqs : 0) + b + par] = fma(v2, yr, sK);      // S = v^2 conj(Yd) + sum K
+        } else {
+            // two threads per bus as above; the magnitude comes back from L1
+            const double *k1 = reinterpret_cast<const double *>(skg);   // K.x, K.y per terminal
+            for (int x = tid; x < 2 * nbus; x += TB) {
+                const int b = sord[x >> 1], im = x & 1;
+                const int4 bm = sbm[b];
+                const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+                double sK = 0.0;
+                for (int i = bm.w; i < tend; ++i) sK += k1[2 * i + im];
+                const double2 y = syd[b];
+                const double vo = a.vm[b0 + b], v2 = vo * vo;
+                spq[(im ? pqs : 0) + b + par] = fma(v2, im ? neg(y.y) : y.x, sK);   // S = v^2 conj(Yd) + sum K
+            }
         }
-    } else {
-        // two threads per bus as above; the magnitude comes back from L1
-        const double *k1 = reinterpret_cast<const double *>(skg);   // K.x, K.y per terminal
-        for (int x = tid; x < 2 * nbus; x += TB) {
-            const int b = sord[x >> 1], im = x & 1;
-            const int4 bm = sbm[b];
-            const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
-            double sK = 0.0;
-            for (int i = bm.w; i < tend; ++i) sK += k1[2 * i + im];
-            const double2 y = syd[b];
-            const double vo = a.vm[b0 + b], v2 = vo * vo;
-            spq[(im ? pqs : 0) + b + par] = fma(v2, im ? neg(y.y) : y.x, sK);   // S = v^2 conj(Yd) + sum K
-        }
-    }
 
-    // ---- stores ----
-    if (a.aligned) {
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
+        // ---- stores ----
+        if (a.aligned) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                if (JAC) {
+                    bulk_s2g(a.J + 2 * (long long)r0, jst, 8u * (uint32_t)L);
+                    bulk_s2g(a.J + 2 * (long long)a.nnz + 2 * (long long)r0, jst + L, 8u * (uint32_t)L);
+                }
+                if (a.P) {
+                    store_range(a.P, spq, b0, b1);
+                    store_range(a.Q, spq + pqs, b0, b1);
+                }
+                bulk_commit();
+                bulk_wait_read();   // shared memory stays allocated until the copies have read it
+            }
+        } else {
+            __syncthreads();
             if (JAC) {
-                bulk_s2g(a.J + 2 * (long long)r0, jst, 8u * (uint32_t)L);
-                bulk_s2g(a.J + 2 * (long long)a.nnz + 2 * (long long)r0, jst + L, 8u * (uint32_t)L);
+                double *Jp = a.J + 2 * (long long)r0;
+                double *Jq = a.J + 2 * (long long)a.nnz + 2 * (long long)r0;
+                for (int x = tid; x < L; x += TB) {
+                    Jp[x] = jst[x];
+                    Jq[x] = jst[L + x];
+                }
             }
-            if (a.P) {
-                store_range(a.P, spq, b0, b1);
-                store_range(a.Q, spq + pqs, b0, b1);
-            }
-            bulk_commit();
-            bulk_wait_read();   // shared memory stays allocated until the copies have read it
+            if (a.P)
+                for (int b = tid; b < nbus; b += TB) {
+                    a.P[b0 + b] = spq[b + par];
+                    a.Q[b0 + b] = spq[pqs + b + par];
+                }
         }
-    } else {
-        __syncthreads();
-        if (JAC) {
-            double *Jp = a.J + 2 * (long long)r0;
-            double *Jq = a.J + 2 * (long long)a.nnz + 2 * (long long)r0;
-            for (int x = tid; x < L; x += TB) {
-                Jp[x] = jst[x];
-                Jq[x] = jst[L + x];
-            }
-        }
-        if (a.P)
-            for (int b = tid; b < nbus; b += TB) {
-                a.P[b0 + b] = spq[b + par];
-                a.Q[b0 + b] = spq[pqs + b + par];
-            }
+        if (!PERSIST) break;
     }
 }
 
+// At most 48 registers: 5 CTAs of 256 or 10 of 128 threads per SM.
+template <bool JAC>
+__global__ void __launch_bounds__(256, 5) k_ew(EwArgs a)
+{
+    ew_windows<JAC, false>(a);
+}
+
+// the Jacobian evaluation with its outputs in host memory (persistent CTAs)
+__global__ void __launch_bounds__(256, 5) k_ew_host(EwArgs a)
+{
+    ew_windows<true, true>(a);
+}
+
 static bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// persistent CTAs per SM of the host-output evaluation
+constexpr int kEwHostCtasPerSm = 2;
 
 template <bool JAC>
 static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
@@ -289,14 +316,32 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     const int max_nph = L.max_nph;
     const EwSmem sp = ew_smem_plan(L.max_nbus, L.max_nt, JAC ? L.max_L : 0, JAC, max_nph);
     const uint32_t smem = sp.total + kTrigN * (uint32_t)sizeof(double2);
-    uint32_t &conf = JAC ? g->ew_smem_jac : g->ew_smem_inj;
+    // outputs in host memory: persistent CTAs (kEwHostCtasPerSm per SM) loop
+    // over the windows, so the host link carries the first windows' outputs
+    // while the later ones are evaluated
+    const bool persist = host_out && JAC;
+    uint32_t &conf = persist ? g->ew_smem_host : JAC ? g->ew_smem_jac : g->ew_smem_inj;
     if (smem > 48u * 1024u && smem > conf) {
-        cudaError_t e = cudaFuncSetAttribute(k_ew<JAC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = persist ? cudaFuncSetAttribute(k_ew_host, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)smem)
+                                : cudaFuncSetAttribute(k_ew<JAC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)smem);
         if (e != cudaSuccess) return e;
         conf = smem;
     }
+    int grid = L.nwin;
+    if (persist) {
+        if (g->nsm == 0) {
+            int dev = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+        }
+        grid = std::min(grid, kEwHostCtasPerSm * g->nsm);
+    }
     EwArgs a;
     a.nnz = g->nnz;
+    a.nwin = L.nwin;
     a.max_nbus = L.max_nbus;
     a.max_nt = L.max_nt;
     a.max_L = L.max_L;
@@ -317,7 +362,10 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.P = P;
     a.Q = Q;
     a.J = J;
-    k_ew<JAC><<<(unsigned)L.nwin, (unsigned)L.tb, smem, s>>>(a);
+    if (persist)
+        k_ew_host<<<(unsigned)grid, (unsigned)L.tb, smem, s>>>(a);
+    else
+        k_ew<JAC><<<(unsigned)grid, (unsigned)L.tb, smem, s>>>(a);
     return cudaGetLastError();
 }
 

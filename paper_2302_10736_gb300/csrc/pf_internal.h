@@ -235,7 +235,8 @@ struct Grid {
     double2 *bus_ysh = nullptr;            // [nb]
     double2 *bus_yd = nullptr;             // [nb] bus shunt + sum of the bus's terminal self constants
     EwDev ew;
-    uint32_t ew_smem_jac = 0, ew_smem_inj = 0;   // dynamic shared memory the kernels are configured for
+    uint32_t ew_smem_jac = 0, ew_smem_inj = 0, ew_smem_host = 0;   // dynamic shared memory the kernels are configured for
+    int nsm = 0;                                  // SM count (cached)
     int *tmir = nullptr;                   // [2nl] by sorted position: sorted position of the mirror terminal
     // device copies of the current parameters (branch gradients need them)
     double *p_g = nullptr, *p_b = nullptr, *p_bsh = nullptr, *p_tap = nullptr, *p_shift = nullptr;
