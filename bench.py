@@ -370,7 +370,9 @@ def _single_workload(torch, pfgrid, synth, k, steps):
 def _reduced_workload(torch, pfgrid, synth, steps):
     """The Newton step's inputs on the 70k-bus grid (15 % PV buses): mismatch
     vector and reduced Jacobian in CSC order, by both methods, L2 flushed
-    between steps; the gather launch timed by the tracer."""
+    between steps.  The element-wise method writes the reduced system from its
+    kernel (one launch); the Ybus method's gather launch is timed by the
+    tracer."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
     flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
     w = synth.workload(WORKLOAD)
@@ -391,7 +393,7 @@ def _reduced_workload(torch, pfgrid, synth, steps):
         t = time_loop(torch, f, steps, flush, "reduced_" + name)
         res["%s_evals_per_s" % name] = 1e3 / (sum(t) / len(t))
     pfgrid.grid_trace_enable(grid, 4 * steps + 16)
-    time_loop(torch, lambda: pfgrid.jac_reduced(grid, 1, vm, va, Ps, Qs, F, Jr), steps, flush, "reduced_traced")
+    time_loop(torch, lambda: pfgrid.jac_reduced(grid, 0, vm, va, Ps, Qs, F, Jr), steps, flush, "reduced_traced")
     tr = pfgrid.grid_trace_read(grid)
     pfgrid.grid_trace_enable(grid, 0)
     ms = [x for k, x in tr if k == "reduce"]

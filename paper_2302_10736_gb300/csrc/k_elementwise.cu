@@ -61,6 +61,12 @@ struct EwArgs {
     const int2 *tloc;
     const double *vm, *va;
     double *P, *Q, *J;
+    // reduced Newton outputs (k_ew_red): the reduced index of every canonical J
+    // position and of every bus's P and Q equation (-1: not kept)
+    const int *jinv;
+    const int2 *binv;
+    const double *Ps, *Qs;
+    double *F, *Jr;
 };
 
 // Write x[b0 .. b1) from shared staging `s` (element b0 at s[b0 & 1]) to
@@ -80,7 +86,7 @@ __device__ __forceinline__ void store_range(double *x, const double *s, int b0, 
 // (grid-strided), so that the first windows' outputs leave while later
 // windows are evaluated (outputs in host memory, where the host link is the
 // bound).
-template <bool JAC, bool PERSIST>
+template <bool JAC, bool PERSIST, bool RED = false>
 __device__ __forceinline__ void ew_windows(const EwArgs &a)
 {
     extern __shared__ __align__(16) char smem[];
@@ -254,7 +260,29 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         }
 
         // ---- stores ----
-        if (a.aligned) {
+        if (RED) {
+            // the reduced system directly: the kept J entries to their CSC
+            // positions, the kept P and Q mismatches to F (no full J is written)
+            __syncthreads();
+            const long long p0 = 2 * (long long)r0, q0 = 2 * (long long)a.nnz + p0 - L;
+            constexpr int U = 8;   // map loads in flight per thread and round
+            for (int base = tid; base < 2 * L; base += U * TB) {
+                int k[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int x = base + u * TB;
+                    k[u] = x < 2 * L ? a.jinv[(x < L ? p0 : q0) + x] : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (k[u] >= 0) a.Jr[k[u]] = jst[base + u * TB];
+            }
+            for (int b = tid; b < nbus; b += TB) {
+                const int2 e = a.binv[b0 + b];
+                if (e.x >= 0) a.F[e.x] = spq[b + par] - a.Ps[b0 + b];
+                if (e.y >= 0) a.F[e.y] = spq[pqs + b + par] - a.Qs[b0 + b];
+            }
+        } else if (a.aligned) {
             fence_proxy_async_smem();
             __syncthreads();
             if (tid == 0) {
@@ -302,14 +330,23 @@ __global__ void __launch_bounds__(256, 5) k_ew_host(EwArgs a)
     ew_windows<true, true>(a);
 }
 
+// the Jacobian evaluation with the reduced Newton system as its output
+__global__ void __launch_bounds__(256, 5) k_ew_red(EwArgs a)
+{
+    ew_windows<true, false, true>(a);
+}
+
 static bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 // persistent CTAs per SM of the host-output evaluation
 constexpr int kEwHostCtasPerSm = 2;
 
+enum class EwOut { device, host, reduced };
+
 template <bool JAC>
 static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
-                             cudaStream_t s, bool host_out)
+                             cudaStream_t s, EwOut out, const double *Ps = nullptr, const double *Qs = nullptr,
+                             double *F = nullptr, double *Jr = nullptr)
 {
     const EwDev &L = g->ew;
     if (L.nwin == 0) return cudaSuccess;
@@ -319,13 +356,12 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     // outputs in host memory: persistent CTAs (kEwHostCtasPerSm per SM) loop
     // over the windows, so the host link carries the first windows' outputs
     // while the later ones are evaluated
-    const bool persist = host_out && JAC;
-    uint32_t &conf = persist ? g->ew_smem_host : JAC ? g->ew_smem_jac : g->ew_smem_inj;
+    const bool persist = out == EwOut::host && JAC;
+    const bool red = out == EwOut::reduced && JAC;
+    uint32_t &conf = persist ? g->ew_smem_host : red ? g->ew_smem_red : JAC ? g->ew_smem_jac : g->ew_smem_inj;
     if (smem > 48u * 1024u && smem > conf) {
-        cudaError_t e = persist ? cudaFuncSetAttribute(k_ew_host, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)smem)
-                                : cudaFuncSetAttribute(k_ew<JAC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(persist ? k_ew_host : red ? k_ew_red : k_ew<JAC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         conf = smem;
     }
@@ -339,7 +375,7 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
         }
         grid = std::min(grid, kEwHostCtasPerSm * g->nsm);
     }
-    EwArgs a;
+    EwArgs a = {};
     a.nnz = g->nnz;
     a.nwin = L.nwin;
     a.max_nbus = L.max_nbus;
@@ -347,7 +383,7 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.max_L = L.max_L;
     a.max_nph = max_nph;
     // bulk (TMA) stores for device outputs; plain coalesced stores for host memory
-    a.aligned = !host_out && (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
+    a.aligned = out == EwOut::device && (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
     a.desc = L.desc;
     a.slotbus = L.slotbus;
     a.bmeta = L.bmeta;
@@ -362,8 +398,18 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.P = P;
     a.Q = Q;
     a.J = J;
+    if (red) {
+        a.jinv = g->red_jinv;
+        a.binv = g->red_binv;
+        a.Ps = Ps;
+        a.Qs = Qs;
+        a.F = F;
+        a.Jr = Jr;
+    }
     if (persist)
         k_ew_host<<<(unsigned)grid, (unsigned)L.tb, smem, s>>>(a);
+    else if (red)
+        k_ew_red<<<(unsigned)grid, (unsigned)L.tb, smem, s>>>(a);
     else
         k_ew<JAC><<<(unsigned)grid, (unsigned)L.tb, smem, s>>>(a);
     return cudaGetLastError();
@@ -381,12 +427,18 @@ cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm)
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
                           cudaStream_t s, bool host_out)
 {
-    return launch_ew<true>(g, vm, va, P, Q, J, s, host_out);
+    return launch_ew<true>(g, vm, va, P, Q, J, s, host_out ? EwOut::host : EwOut::device);
+}
+
+cudaError_t launch_jac_ew_reduced(Grid *g, const double *vm, const double *va, const double *Ps, const double *Qs,
+                                  double *F, double *Jr, cudaStream_t s)
+{
+    return launch_ew<true>(g, vm, va, nullptr, nullptr, nullptr, s, EwOut::reduced, Ps, Qs, F, Jr);
 }
 
 cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s)
 {
-    return launch_ew<false>(g, vm, va, P, Q, nullptr, s, false);
+    return launch_ew<false>(g, vm, va, P, Q, nullptr, s, EwOut::device);
 }
 
 }  // namespace pf

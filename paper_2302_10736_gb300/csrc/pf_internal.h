@@ -235,7 +235,7 @@ struct Grid {
     double2 *bus_ysh = nullptr;            // [nb]
     double2 *bus_yd = nullptr;             // [nb] bus shunt + sum of the bus's terminal self constants
     EwDev ew;
-    uint32_t ew_smem_jac = 0, ew_smem_inj = 0, ew_smem_host = 0;   // dynamic shared memory the kernels are configured for
+    uint32_t ew_smem_jac = 0, ew_smem_inj = 0, ew_smem_host = 0, ew_smem_red = 0;   // dynamic shared memory the kernels are configured for
     int nsm = 0;                                  // SM count (cached)
     int *tmir = nullptr;                   // [2nl] by sorted position: sorted position of the mirror terminal
     // device copies of the current parameters (branch gradients need them)
@@ -257,6 +257,10 @@ struct Grid {
     long long red_nnz = 0;
     int *red_colptr = nullptr, *red_rowidx = nullptr, *red_jmap = nullptr, *red_fmap = nullptr;
     int *red_rowptr = nullptr, *red_colidx = nullptr, *red_jmap_csr = nullptr;   // the same matrix row-major
+    // inverse maps for the fused element-wise path: the reduced (CSC) index of
+    // every canonical J position, and of every bus's P and Q equation (-1: not kept)
+    int *red_jinv = nullptr;
+    int2 *red_binv = nullptr;
     double *red_P = nullptr, *red_Q = nullptr, *red_J = nullptr;
     // Newton-Raphson workspace (powerflow_newton): F, J_r (CSR), step, max |F|;
     // sparse-solver handles (cusolverSpHandle_t, cusparseMatDescr_t)
@@ -322,6 +326,9 @@ cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm);   // CTAs of k_e
 cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
                           cudaStream_t s, bool host_out = false);   // host_out: P, Q, J in mapped host memory
+// the Jacobian evaluation with the reduced Newton system (F, CSC values) as its only output
+cudaError_t launch_jac_ew_reduced(Grid *g, const double *vm, const double *va, const double *Ps, const double *Qs,
+                                  double *F, double *Jr, cudaStream_t s);
 
 // reduced Newton system (reduced.cu, newton.cu)
 cudaError_t launch_reduce(Grid *g, const int *map, const double *Pspec, const double *Qspec, double *F, double *Jr,

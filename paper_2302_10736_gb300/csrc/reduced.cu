@@ -25,6 +25,8 @@ struct HostReduced {
     int n = 0, npvpq = 0, npq = 0;
     std::vector<int> colptr, rowidx, jmap, fmap;
     std::vector<int> rowptr, colidx, jmap_csr;   // row-major copy (the Newton solver's input)
+    std::vector<int> jinv;                       // [4 nnzY] reduced (CSC) index of each canonical position, or -1
+    std::vector<int2> binv;                      // [nb] reduced index of the bus's P and Q equation, or -1
 };
 
 // Reduced index of full row/column R (R < nb: theta_R / P_R; R >= nb:
@@ -85,6 +87,11 @@ pf_status host_reduced(const HostTopo &H, const int *bt, HostReduced &R)
         }
         R.rowptr[red[Rw] + 1] = (int)R.colidx.size();
     }
+    // inverse maps for the fused element-wise path
+    R.jinv.assign(H.jci.size(), -1);
+    for (int k = 0; k < nnz; ++k) R.jinv[R.jmap[k]] = k;
+    R.binv.resize(nb);
+    for (int i = 0; i < nb; ++i) R.binv[i] = make_int2(red[i], red[nb + i]);
     return PF_OK;
 }
 
@@ -177,11 +184,12 @@ PF_API pf_status grid_set_bus_types(pf_grid *grid, const int32_t *bus_type, pf_s
     cudaStream_t s = (cudaStream_t)stream;
     PF_CUDA(cudaStreamSynchronize(s));   // no launch may still read the old map
     for (void *p : {(void *)g->red_colptr, (void *)g->red_rowidx, (void *)g->red_jmap, (void *)g->red_fmap,
-                    (void *)g->red_rowptr, (void *)g->red_colidx, (void *)g->red_jmap_csr, (void *)g->nt_F,
-                    (void *)g->nt_J, (void *)g->nt_dx})
+                    (void *)g->red_rowptr, (void *)g->red_colidx, (void *)g->red_jmap_csr, (void *)g->red_jinv,
+                    (void *)g->red_binv, (void *)g->nt_F, (void *)g->nt_J, (void *)g->nt_dx})
         if (p) g->arena.release(p);
     g->red_colptr = g->red_rowidx = g->red_jmap = g->red_fmap = nullptr;
-    g->red_rowptr = g->red_colidx = g->red_jmap_csr = nullptr;
+    g->red_rowptr = g->red_colidx = g->red_jmap_csr = g->red_jinv = nullptr;
+    g->red_binv = nullptr;
     g->nt_F = g->nt_J = g->nt_dx = nullptr;   // sized by n and nnz: re-allocated by the next Newton solve
     g->red_set = 0;
     if ((st = upload_vec(g->arena, &g->red_colptr, R.colptr, s)) ||
@@ -189,7 +197,8 @@ PF_API pf_status grid_set_bus_types(pf_grid *grid, const int32_t *bus_type, pf_s
         (st = upload_vec(g->arena, &g->red_jmap, R.jmap, s)) || (st = upload_vec(g->arena, &g->red_fmap, R.fmap, s)) ||
         (st = upload_vec(g->arena, &g->red_rowptr, R.rowptr, s)) ||
         (st = upload_vec(g->arena, &g->red_colidx, R.colidx, s)) ||
-        (st = upload_vec(g->arena, &g->red_jmap_csr, R.jmap_csr, s)))
+        (st = upload_vec(g->arena, &g->red_jmap_csr, R.jmap_csr, s)) ||
+        (st = upload_vec(g->arena, &g->red_jinv, R.jinv, s)) || (st = upload_vec(g->arena, &g->red_binv, R.binv, s)))
         return st;
     if (!g->red_J) {
         double **const out[3] = {&g->red_P, &g->red_Q, &g->red_J};
@@ -236,10 +245,14 @@ PF_API pf_status jac_reduced(pf_grid *grid, int32_t method, const double *vm, co
     if (g->nb == 0 || g->red_n == 0) return PF_OK;
     if (!vm || !va || !Pspec || !Qspec || !F || (g->red_nnz > 0 && !Jr))
         return set_error(PF_EINVAL, "jac_reduced: NULL argument");
-    pf_status st = method == 0 ? jac_ybus(grid, vm, va, g->red_P, g->red_Q, g->red_J, stream)
-                               : jac_elementwise(grid, vm, va, g->red_P, g->red_Q, g->red_J, stream);
-    if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (method == 1) {   // one launch: the element-wise kernel writes the reduced system itself
+        TraceScope t(g, PF_K_JAC_EW, s);
+        PF_CUDA(launch_jac_ew_reduced(g, vm, va, Pspec, Qspec, F, Jr, s));
+        return PF_OK;
+    }
+    pf_status st = jac_ybus(grid, vm, va, g->red_P, g->red_Q, g->red_J, stream);
+    if (st) return st;
     TraceScope t(g, PF_K_REDUCE, s);
     PF_CUDA(launch_reduce(g, g->red_jmap, Pspec, Qspec, F, Jr, s));
     return PF_OK;

@@ -52,6 +52,18 @@ def check_reduced(pf, gr, bt, vm, va, Ps, Qs, grid=None):
         F, Jr = gpu_reduced(pf, grid, method, vm, va, Ps, Qs)
         assert relerr(F, F_ref) <= TOL, (method, relerr(F, F_ref))
         assert relerr(Jr, vals) <= TOL, (method, relerr(Jr, vals))
+    # the element-wise kernel writes the reduced system itself: bit for bit the
+    # selection of its own full evaluation (same values, same P - Pspec)
+    import torch
+    nb = gr["nb"]
+    Pd = torch.empty(nb, dtype=torch.float64, device="cuda")
+    Qd = torch.empty_like(Pd)
+    Jd = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+    pf.jac_elementwise(grid, _d(vm), _d(va), Pd, Qd, Jd)
+    _, _, vals_gpu = oracle.jac_reduced(Y, Jd.cpu().numpy(), bt)
+    F_gpu = oracle.mismatch(Pd.cpu().numpy(), Qd.cpu().numpy(), Ps, Qs, bt)
+    F1, Jr1 = gpu_reduced(pf, grid, 1, vm, va, Ps, Qs)
+    assert np.array_equal(Jr1, vals_gpu) and np.array_equal(F1, F_gpu)
     return grid
 
 
