@@ -383,11 +383,13 @@ pf_status jac_reduced_info(const pf_grid *grid, int32_t *n, int32_t *n_pvpq, int
 pf_status jac_reduced_pattern(const pf_grid *grid, const int32_t **colptr, const int32_t **rowidx);
 
 /*
- * One Newton evaluation: the full injections and Jacobian by the Ybus
- * (method 0) or element-wise (method 1) method into grid-owned scratch, then
- * one gather launch forms the mismatch vector
+ * One Newton evaluation: the mismatch vector
  *   F = [P - Pspec on the PV and PQ buses ; Q - Qspec on the PQ buses]  [n]
- * and the reduced Jacobian values Jr [nnz] in the CSC order above.
+ * and the reduced Jacobian values Jr [nnz] in the CSC order above.  Method 1
+ * (element-wise): one launch whose windows write F and Jr directly (no full
+ * Jacobian is stored); the values are bit for bit those of jac_elementwise
+ * selected.  Method 0 (Ybus): the full evaluation into grid-owned scratch,
+ * then one gather launch.
  * vm, va, Pspec, Qspec [nb], F, Jr: device pointers owned by the caller.
  * Asynchronous; the grid's scratch makes calls on one grid serial.
  * (The paper computes the full Jacobian; the reduction is the step its
