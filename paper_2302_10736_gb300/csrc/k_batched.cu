@@ -214,10 +214,18 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
             const int4 bm = sbm[b];
             const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
             const double2 y = syd[b];
+            // sums start from the first terminal (never EW_ACCUM: it starts its run)
             double sKr = 0.0, sKi = 0.0;
+            int i1 = bm.w;
+            if (i1 < tend) {
+                const double2 K = skg[JAC ? 2 * i1 : i1];
+                sKr = K.x;
+                sKi = K.y;
+                ++i1;
+            }
             if (JAC) {
                 const int d = bm.y;
-                for (int i = bm.w; i < tend; ++i) {
+                for (int i = i1; i < tend; ++i) {
                     const double2 K = skg[2 * i];
                     sKr += K.x;
                     sKi += K.y;
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
                 spq[b + par] = fma(v2, y.x, sKr);
                 spq[pqs + b + par] = fma(-v2, y.y, sKi);
             } else {
-                for (int i = bm.w; i < tend; ++i) {
+                for (int i = i1; i < tend; ++i) {
                     sKr += skg[i].x;
                     sKi += skg[i].y;
                 }
@@ -446,7 +454,13 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
             const int4 bm = sbm[b];
             const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
             double sKr = 0.0, sKi = 0.0;
-            for (int i = bm.w; i < tend; ++i) {
+            int i = bm.w;
+            if (i < tend) {
+                sKr = skg[i].x;
+                sKi = skg[i].y;
+                ++i;
+            }
+            for (; i < tend; ++i) {
                 sKr += skg[i].x;
                 sKi += skg[i].y;
             }
@@ -497,7 +511,13 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
             const int4 bm = sbm[b];
             const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
             double gth = 0.0, gv = 0.0;
-            for (int i = bm.w; i < tend; ++i) {
+            int i = bm.w;
+            if (i < tend) {
+                gth = skg[i].x;
+                gv = skg[i].y;
+                ++i;
+            }
+            for (; i < tend; ++i) {
                 gth += skg[i].x;
                 gv += skg[i].y;
             }
@@ -677,8 +697,10 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
                 const int b = x == tid ? bo : a.rorder[b0 + (x >> 1)], im = x & 1;
                 const int4 bm = sbm[b];
                 const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+                int i = bm.w;
                 double sk = 0.0;
-                for (int i = bm.w; i < tend; ++i) sk += kk[2 * i + im];
+                if (i < tend) sk = kk[2 * i++ + im];
+                for (; i < tend; ++i) sk += kk[2 * i + im];
                 double spec = spec0, wt = wt0;
                 if (x != tid) {
                     spec = im ? a.Qs[b0 + b] : a.Ps[b0 + b];
@@ -774,8 +796,10 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
                 const int b = x == tid ? bo : a.rorder[b0 + (x >> 1)], im = x & 1;
                 const int4 bm = sbm[b];
                 const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+                int i = bm.w;
                 double g = 0.0;
-                for (int i = bm.w; i < tend; ++i) g += kk[2 * i + im];
+                if (i < tend) g = kk[2 * i++ + im];
+                for (; i < tend; ++i) g += kk[2 * i + im];
                 if (im) {   // <r_o, 2 v_o conj(Yd)> + (sum) / v_o
                     const double2 vw = sW[b], ro = sR[b], y = syd[b];
                     g = fma(g, vw.y, (vw.x + vw.x) * fma(ro.x, y.x, -ro.y * y.y));

@@ -220,8 +220,12 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                 const int4 bm = sbm[b];
                 const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
                 const int d = bm.y;
+                // the sum starts from the first terminal (which starts its
+                // parallel run, so it is never EW_ACCUM): one addition fewer
+                int i = bm.w;
                 double sK = 0.0;
-                for (int i = bm.w; i < tend; ++i) {
+                if (i < tend) sK = kg[4 * i++ + im];
+                for (; i < tend; ++i) {
                     sK += kg[4 * i + im];
                     const int kp = skp[i];
                     if (kp & EW_ACCUM) {   // later branch of a parallel run: add into the run's slot
@@ -251,8 +255,10 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                 const int b = sord[x >> 1], im = x & 1;
                 const int4 bm = sbm[b];
                 const int tend = b + 1 < nbus ? sbm[b + 1].w : nt;
+                int i = bm.w;
                 double sK = 0.0;
-                for (int i = bm.w; i < tend; ++i) sK += k1[2 * i + im];
+                if (i < tend) sK = k1[2 * i++ + im];
+                for (; i < tend; ++i) sK += k1[2 * i + im];
                 const double2 y = syd[b];
                 const double vo = a.vm[b0 + b], v2 = vo * vo;
                 spq[(im ? pqs : 0) + b + par] = fma(v2, im ? neg(y.y) : y.x, sK);   // S = v^2 conj(Yd) + sum K
@@ -265,7 +271,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
             // positions, the kept P and Q mismatches to F (no full J is written)
             __syncthreads();
             const long long p0 = 2 * (long long)r0, q0 = 2 * (long long)a.nnz + p0 - L;
-            constexpr int U = 8;   // map loads in flight per thread and round
+            constexpr int U = 4;   // map loads in flight per thread and round (more spill at 48 registers)
             for (int base = tid; base < 2 * L; base += U * TB) {
                 int k[U];
 #pragma unroll
