@@ -100,6 +100,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
     double2 *sV = reinterpret_cast<double2 *>(smem + sp.ph);                 // v e^{j theta}
     double2 *sU = sV + a.max_nph;                                            // (cos, sin)
     double2 *sW = sU + a.max_nph;                                            // (v, 1/v)
+    double2 *sW2 = reinterpret_cast<double2 *>(smem + sp.w2);               // own buses: (v^2, 2 v)
     int *sord = reinterpret_cast<int *>(smem + sp.ord);                     // reduction thread -> bus
     double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x;
@@ -158,9 +159,16 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                 sU[j] = make_double2(c, s);
                 // 1/v only for the window's own buses: warps of ghost slots skip it
                 // (a warp-uniform branch), mixed warps compute it for all lanes
+                // and (v^2, 2 v) for the reduction, formed once per bus instead
+                // of by both threads of its pair
                 double iv = 0.0;
-                if (__any_sync(__activemask(), j < nbus)) iv = fast_rcp(v);
+                if (__any_sync(__activemask(), j < nbus)) {
+                    iv = fast_rcp(v);
+                    if (j < nbus) sW2[j] = make_double2(v * v, v + v);
+                }
                 sW[j] = make_double2(v, iv);
+            } else if (j < nbus) {
+                sW2[j].x = v * v;
             }
         }
         if (tid < nbus) {
@@ -239,8 +247,8 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                         }
                     }
                 }
-                const double2 y = syd[b], vw = sW[b];
-                const double vo = vw.x, iv = vw.y, v2 = vo * vo, tv = vo + vo;
+                const double2 y = syd[b], w2 = sW2[b];
+                const double iv = sW[b].y, v2 = w2.x, tv = w2.y;
                 // real part: Re conj(Yd) = y.x; imaginary part: Im conj(Yd) = -y.y (sign flips are exact)
                 const double yr = im ? neg(y.y) : y.x;
                 const int pos = bm.x + bm.z;
@@ -249,7 +257,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                 spq[(im ? pqs : 0) + b + par] = fma(v2, yr, sK);      // S = v^2 conj(Yd) + sum K
             }
         } else {
-            // two threads per bus as above; the magnitude comes back from L1
+            // two threads per bus as above; v^2 from the phasor phase
             const double *k1 = reinterpret_cast<const double *>(skg);   // K.x, K.y per terminal
             for (int x = tid; x < 2 * nbus; x += TB) {
                 const int b = sord[x >> 1], im = x & 1;
@@ -260,7 +268,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                 if (i < tend) sK = k1[2 * i++ + im];
                 for (; i < tend; ++i) sK += k1[2 * i + im];
                 const double2 y = syd[b];
-                const double vo = a.vm[b0 + b], v2 = vo * vo;
+                const double v2 = sW2[b].x;
                 spq[(im ? pqs : 0) + b + par] = fma(v2, im ? neg(y.y) : y.x, sK);   // S = v^2 conj(Yd) + sum K
             }
         }

@@ -147,12 +147,14 @@ pf_status host_window_branches(const HostTopo &H, const HostEw &E, std::vector<i
 //   jst double  [2 max_L]    the window's J slice (P half, then Q half)
 //   pq  double  [2 pqs]      P then Q of the window, parity-aligned with global memory
 //   ph                       phasor table (below)
-//   ord int     [max_nbus]   the reduction's thread-to-bus map (HostEw::rorder)
+//   ord int     [max_nbus]   the reduction's thread-to-bus map (HostEw::rorder)      (max_nph > 0)
+//   w2  double2 [max_nbus]   (v^2, 2 v) of the window's own buses                     (max_nph > 0)
 struct EwSmem {
-    uint32_t bm, yd, kg, kp, jst, pq, pqs, ph, ord, total;
+    uint32_t bm, yd, kg, kp, jst, pq, pqs, ph, ord, w2, total;
 };
-// max_nph > 0 adds a phasor table of that many slots: V = v e^{j theta}, and
-// with the Jacobian also (cos, sin) and (v, 1/v), each a double2 array
+// max_nph > 0 (the single-evaluation kernel) adds a phasor table of that many
+// slots: V = v e^{j theta}, and with the Jacobian also (cos, sin) and (v, 1/v),
+// each a double2 array, and the ord and w2 arrays
 __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max_L, bool jac, int max_nph = 0)
 {
     EwSmem p;
@@ -165,7 +167,8 @@ __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max
     p.pq = p.jst + (jac ? 16u * (uint32_t)max_L : 0u);
     p.ph = p.pq + 16u * p.pqs;
     p.ord = p.ph + (jac ? 48u : 16u) * (uint32_t)max_nph;
-    p.total = p.ord + ((4u * (uint32_t)max_nbus + 15u) & ~15u);
+    p.w2 = p.ord + (max_nph > 0 ? (4u * (uint32_t)max_nbus + 15u) & ~15u : 0u);
+    p.total = p.w2 + (max_nph > 0 ? 16u * (uint32_t)max_nbus : 0u);
     return p;
 }
 constexpr uint32_t kMaxSmem = 227u * 1024u;
