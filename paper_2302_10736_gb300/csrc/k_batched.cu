@@ -43,7 +43,7 @@ constexpr uint64_t kBatchBarrierNs = 2000000000ull;   // bounded grid-barrier wa
 
 struct BatchArgs {
     int S, nb, nl, nnz, nwin, max_nbus, max_nt, max_L, aligned;
-    int ghost, max_nph, max_nbr;
+    int max_nph, max_nbr;
     const int *win_bus, *tp, *rp, *kd, *town, *tmir, *tpos, *slotbus, *rorder;
     const int2 *tloc, *brl;
     const int4 *desc;
@@ -846,7 +846,6 @@ static BatchArgs batch_args(Batch *b)
     a.max_L = b->max_L;
     a.win_bus = b->win_bus;
     a.rorder = b->rorder;
-    a.ghost = b->ghost;
     a.max_nph = b->max_nph;
     a.max_nbr = b->max_nbr;
     a.brl = b->brl;

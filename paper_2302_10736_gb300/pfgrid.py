@@ -289,7 +289,10 @@ def jac_elementwise(grid, vm, va, P, Q, J, stream=None):
 
 
 def eval_host(grid, method, vm, va, P, Q, J, stream=None):
-    """Host numpy buffers in and out (vm, va, P, Q [nb]; J [4 nnzY])."""
+    """Host numpy buffers in and out (vm, va, P, Q [nb]; J [4 nnzY]).  With
+    page-locked buffers the element-wise kernel reads and writes them directly.
+    `stream` as an integer handle skips the per-call look-up of torch's
+    current stream."""
     for name, a, n in (("vm", vm, grid.nb), ("va", va, grid.nb), ("P", P, grid.nb), ("Q", Q, grid.nb),
                        ("J", J, grid.nnzJ)):
         if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size >= n):
