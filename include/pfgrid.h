@@ -398,6 +398,35 @@ pf_status jac_reduced_pattern(const pf_grid *grid, const int32_t **colptr, const
 pf_status jac_reduced(pf_grid *grid, int32_t method, const double *vm, const double *va, const double *Pspec,
                       const double *Qspec, double *F, double *Jr, pf_stream stream);
 
+/* ------------------------------------------- caller's Jacobian pattern -- */
+
+/*
+ * Alg. 2 (Sec. IV-B.3), the general index arrays P_xy: a caller's Jacobian
+ * pattern in CSC form, 2nb x 2nb with rows and columns in the block order of
+ * Eq. (2) (theta / P first, then v / Q), that contains every entry of the
+ * Ybus-block pattern (jac_pattern) and may hold more (series devices such as
+ * TCSC couple further buses).  colptr [2nb+1], rowidx [nnz]: host int32 arrays,
+ * read during the call; rows within a column in any order (the first match
+ * counts).  The library finds, by matching row and column, the position in
+ * this pattern of every canonical entry and keeps that map on the device
+ * (synchronizes `stream`).  PF_EINVAL if an entry of the Ybus-block pattern
+ * is missing or the arrays are malformed, PF_EUNSUPPORTED if nnz >= 2^31.
+ */
+pf_status jac_set_target_pattern(pf_grid *grid, const int32_t *colptr, const int32_t *rowidx, int64_t nnz,
+                                 pf_stream stream);
+
+/*
+ * One evaluation into that pattern: Jt[P_xy] = the Jacobian values (Jt
+ * [nnz], device, caller-owned; its other entries are left as they are: they
+ * belong to devices outside this library), and P, Q [nb] when both are
+ * non-NULL.  Method 1 (element-wise): one launch that stores through the map;
+ * method 0 (Ybus): the evaluation into grid-owned scratch, then one scatter
+ * launch.  The values are bit for bit those of jac_elementwise / jac_ybus.
+ * Asynchronous; PF_EINVAL before jac_set_target_pattern.
+ */
+pf_status jac_target(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P, double *Q,
+                     double *Jt, pf_stream stream);
+
 /*
  * Newton-Raphson power flow on the GPU (not in the paper, which stops at the
  * Jacobian a Newton step needs): starting from vm, va [nb] (device, updated

@@ -21,6 +21,9 @@ Every function follows a passage of arXiv 2302.10736 (cited in oracle.c):
                            vector (selection and reordering of Eq. (2)'s entries)
   newton                   Newton-Raphson on the reduced system (the textbook
                            iteration; a sparse LU is its linear-solve step)
+  jac_target               Alg. 2: the Jacobian's values placed into a caller's
+                           CSC pattern that contains the Ybus-block pattern, by
+                           matching row and column coordinates
 """
 import ctypes
 import os
@@ -330,3 +333,29 @@ def newton(gr, bustype, vm, va, Pspec, Qspec, tol=1e-10, max_iter=20):
         va[pvpq] += dx[:npvpq]
         vm[pq] += dx[npvpq:]
     return vm, va, max_iter, norms, False
+
+
+# ------------------------------------------------- caller's pattern (Alg. 2) --
+def jac_target(Y, J, colptr, rowidx, out):
+    """Sec. IV-B.3, Alg. 2: the Jacobian values J (the block layout of
+    jac_pattern, rows 0 .. 2nb-1 = P then Q, columns = theta then v) placed
+    into a CSC pattern (colptr [2nb+1], rowidx) that contains every entry of
+    that layout: an entry at (row R, column C) goes to the position in column
+    C whose row is R (the first such position).  `out` keeps its other
+    entries.  ValueError if an entry has no position."""
+    jrp, jci = jac_pattern(Y)
+    colptr = np.asarray(colptr)
+    rowidx = np.asarray(rowidx)
+    for R in range(2 * Y.nb):
+        for p in range(jrp[R], jrp[R + 1]):
+            C = int(jci[p])
+            hit = -1
+            for k in range(int(colptr[C]), int(colptr[C + 1])):
+                if rowidx[k] == R:
+                    hit = k
+                    break
+            if hit < 0:
+                raise ValueError("pattern lacks entry (%d, %d)" % (R, C))
+            out[hit] = J[p]
+    return out
+

@@ -61,8 +61,9 @@ struct EwArgs {
     const int2 *tloc;
     const double *vm, *va;
     double *P, *Q, *J;
-    // reduced Newton outputs (k_ew_red): the reduced index of every canonical J
-    // position and of every bus's P and Q equation (-1: not kept)
+    // mapped outputs (k_ew_red): the destination of every canonical J position
+    // in Jr (-1: not kept) and, for the reduced Newton system, the reduced index
+    // of every bus's P and Q equation
     const int *jinv;
     const int2 *binv;
     const double *Ps, *Qs;
@@ -275,8 +276,10 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
 
         // ---- stores ----
         if (RED) {
-            // the reduced system directly: the kept J entries to their CSC
-            // positions, the kept P and Q mismatches to F (no full J is written)
+            // J through a map from canonical positions (the reduced system's
+            // CSC index, or a caller's pattern's position: Alg. 2's P_xy; -1
+            // for an entry that is not kept), then the kept P and Q mismatches
+            // to F, or P and Q themselves (no canonical J is written)
             __syncthreads();
             const long long p0 = 2 * (long long)r0, q0 = 2 * (long long)a.nnz + p0 - L;
             constexpr int U = 4;   // map loads in flight per thread and round (more spill at 48 registers)
@@ -291,11 +294,17 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                 for (int u = 0; u < U; ++u)
                     if (k[u] >= 0) a.Jr[k[u]] = jst[base + u * TB];
             }
-            for (int b = tid; b < nbus; b += TB) {
-                const int2 e = a.binv[b0 + b];
-                if (e.x >= 0) a.F[e.x] = spq[b + par] - a.Ps[b0 + b];
-                if (e.y >= 0) a.F[e.y] = spq[pqs + b + par] - a.Qs[b0 + b];
-            }
+            if (a.binv)
+                for (int b = tid; b < nbus; b += TB) {
+                    const int2 e = a.binv[b0 + b];
+                    if (e.x >= 0) a.F[e.x] = spq[b + par] - a.Ps[b0 + b];
+                    if (e.y >= 0) a.F[e.y] = spq[pqs + b + par] - a.Qs[b0 + b];
+                }
+            if (a.P)
+                for (int b = tid; b < nbus; b += TB) {
+                    a.P[b0 + b] = spq[b + par];
+                    a.Q[b0 + b] = spq[pqs + b + par];
+                }
         } else if (a.aligned) {
             fence_proxy_async_smem();
             __syncthreads();
@@ -344,7 +353,8 @@ __global__ void __launch_bounds__(256, 5) k_ew_host(EwArgs a)
     ew_windows<true, true>(a);
 }
 
-// the Jacobian evaluation with the reduced Newton system as its output
+// the Jacobian evaluation with its values stored through a position map: the
+// reduced Newton system, or a caller's pattern (Alg. 2)
 __global__ void __launch_bounds__(256, 5) k_ew_red(EwArgs a)
 {
     ew_windows<true, false, true>(a);
@@ -360,7 +370,8 @@ enum class EwOut { device, host, reduced };
 template <bool JAC>
 static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
                              cudaStream_t s, EwOut out, const double *Ps = nullptr, const double *Qs = nullptr,
-                             double *F = nullptr, double *Jr = nullptr)
+                             double *F = nullptr, double *Jr = nullptr, const int *jinv = nullptr,
+                             const int2 *binv = nullptr)
 {
     const EwDev &L = g->ew;
     if (L.nwin == 0) return cudaSuccess;
@@ -413,8 +424,8 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.Q = Q;
     a.J = J;
     if (red) {
-        a.jinv = g->red_jinv;
-        a.binv = g->red_binv;
+        a.jinv = jinv;
+        a.binv = binv;
         a.Ps = Ps;
         a.Qs = Qs;
         a.F = F;
@@ -447,7 +458,15 @@ cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P
 cudaError_t launch_jac_ew_reduced(Grid *g, const double *vm, const double *va, const double *Ps, const double *Qs,
                                   double *F, double *Jr, cudaStream_t s)
 {
-    return launch_ew<true>(g, vm, va, nullptr, nullptr, nullptr, s, EwOut::reduced, Ps, Qs, F, Jr);
+    return launch_ew<true>(g, vm, va, nullptr, nullptr, nullptr, s, EwOut::reduced, Ps, Qs, F, Jr, g->red_jinv,
+                           g->red_binv);
+}
+
+cudaError_t launch_jac_ew_mapped(Grid *g, const double *vm, const double *va, double *P, double *Q, const int *map,
+                                 double *Jt, cudaStream_t s)
+{
+    return launch_ew<true>(g, vm, va, P, Q, nullptr, s, EwOut::reduced, nullptr, nullptr, nullptr, Jt, map,
+                           nullptr);
 }
 
 cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s)

@@ -264,6 +264,12 @@ struct Grid {
     // every canonical J position, and of every bus's P and Q equation (-1: not kept)
     int *red_jinv = nullptr;
     int2 *red_binv = nullptr;
+    // a caller's Jacobian pattern (jac_set_target_pattern, Alg. 2): the
+    // position in it of every canonical entry, and scratch for the Ybus method
+    int tgt_set = 0;
+    long long tgt_nnz = 0;
+    int *tgt_map = nullptr;
+    double *tgt_J = nullptr;
     double *red_P = nullptr, *red_Q = nullptr, *red_J = nullptr;
     // Newton-Raphson workspace (powerflow_newton): F, J_r (CSR), step, max |F|;
     // sparse-solver handles (cusolverSpHandle_t, cusparseMatDescr_t)
@@ -332,6 +338,10 @@ cudaError_t launch_jac_ew(Grid *g, const double *vm, const double *va, double *P
 // the Jacobian evaluation with the reduced Newton system (F, CSC values) as its only output
 cudaError_t launch_jac_ew_reduced(Grid *g, const double *vm, const double *va, const double *Ps, const double *Qs,
                                   double *F, double *Jr, cudaStream_t s);
+// the Jacobian evaluation with J stored through map (canonical position -> Jt
+// position), P and Q (may be NULL) stored as usual
+cudaError_t launch_jac_ew_mapped(Grid *g, const double *vm, const double *va, double *P, double *Q, const int *map,
+                                 double *Jt, cudaStream_t s);
 
 // reduced Newton system (reduced.cu, newton.cu)
 cudaError_t launch_reduce(Grid *g, const int *map, const double *Pspec, const double *Qspec, double *F, double *Jr,

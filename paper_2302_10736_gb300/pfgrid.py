@@ -84,6 +84,8 @@ def _load():
         "jac_reduced": (st, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "powerflow_newton": (st, [vp, i32, vp, vp, vp, vp, ctypes.c_double, i32, pi32, ctypes.POINTER(ctypes.c_double),
                                   vp]),
+        "jac_set_target_pattern": (st, [vp, vp, vp, ctypes.c_int64, vp]),
+        "jac_target": (st, [vp, i32, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -422,6 +424,28 @@ def jac_reduced(grid, method, vm, va, Pspec, Qspec, F, Jr, stream=None):
     _check(_lib.jac_reduced(grid.handle, int(m), _dptr(vm, "vm", nb), _dptr(va, "va", nb),
                             _dptr(Pspec, "Pspec", nb), _dptr(Qspec, "Qspec", nb), _dptr(F, "F", n),
                             _dptr(Jr, "Jr", nnz), _stream(stream)), "jac_reduced")
+
+
+def jac_set_target_pattern(grid, colptr, rowidx, stream=None):
+    """A caller's Jacobian pattern (CSC, 2nb x 2nb, host int32 arrays) that
+    contains the Ybus-block pattern (Alg. 2); later jac_target calls write
+    into it."""
+    cp, cpp = _hptr(colptr, np.int32)
+    ri, rip = _hptr(rowidx, np.int32)
+    if cp.size != 2 * grid.nb + 1:
+        raise ValueError("colptr needs 2 nb + 1 = %d entries" % (2 * grid.nb + 1))
+    grid._target_nnz = int(ri.size)
+    _check(_lib.jac_set_target_pattern(grid.handle, cpp, rip, int(ri.size), _stream(stream)), "jac_set_target_pattern")
+
+
+def jac_target(grid, method, vm, va, P, Q, Jt, stream=None):
+    """Jacobian values into the caller's pattern: Jt [nnz] (only the Ybus-block
+    positions are written), and P, Q [nb] unless None."""
+    nb = grid.nb
+    m = {"ybus": 0, "elementwise": 1}.get(method, method)
+    nnz = getattr(grid, "_target_nnz", 0)
+    _check(_lib.jac_target(grid.handle, int(m), _dptr(vm, "vm", nb), _dptr(va, "va", nb), _dptr(P, "P", nb),
+                           _dptr(Q, "Q", nb), _dptr(Jt, "Jt", nnz), _stream(stream)), "jac_target")
 
 
 def powerflow_newton(grid, method, vm, va, Pspec, Qspec, tol=1e-10, max_iter=20, stream=None):

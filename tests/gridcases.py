@@ -119,3 +119,30 @@ def hub_grid(nspokes, seed, nring=600):
         if n % 50 == 0:
             br.append(e + (0.5 * g, 0.5 * b, 0.0, tap, 0.0))
     return make_grid(nb, br, shunts={hub: (0.02, -0.01), 3: (0.01, 0.04)})
+
+
+def superset_pattern(Y, rng, extra):
+    """The CSC form of the Ybus-block pattern plus `extra` random coordinates
+    and one coupled bus pair (a TCSC-like device: all four blocks), rows in a
+    shuffled order within every column."""
+    import oracle
+    jrp, jci = oracle.jac_pattern(Y)
+    n2 = 2 * Y.nb
+    coords = {(R, int(jci[p])) for R in range(n2) for p in range(jrp[R], jrp[R + 1])}
+    a, c = 0, Y.nb - 1
+    for x in (a, c, Y.nb + a, Y.nb + c):
+        for y in (a, c, Y.nb + a, Y.nb + c):
+            coords.add((x, y))
+    while len(coords) < len(jci) + extra:
+        coords.add((int(rng.integers(n2)), int(rng.integers(n2))))
+    cols = [[] for _ in range(n2)]
+    for R, C in coords:
+        cols[C].append(R)
+    colptr = np.zeros(n2 + 1, np.int32)
+    rowidx = []
+    for C in range(n2):
+        rows = cols[C]
+        rng.shuffle(rows)
+        rowidx += rows
+        colptr[C + 1] = len(rowidx)
+    return colptr, np.array(rowidx, np.int32)

@@ -23,7 +23,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gridcases import (blocks, circuit_currents, make_grid, random_grid, random_state, relerr, series,
+from gridcases import (blocks, circuit_currents, make_grid, random_grid, random_state, relerr, series, superset_pattern,
                        three_bus_plus, two_bus_lossless)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -503,3 +503,55 @@ def test_newton_oracle_finds_the_known_solution():
     assert ok and it <= 6, norms
     assert np.max(np.abs(vm - vm_t)) < 1e-10 and np.max(np.abs(va - va_t)) < 1e-10
     assert np.array_equal(vm[~pq], vm_t[~pq]) and va[0] == va_t[0]   # fixed quantities untouched
+
+
+def _dense_jacobian_cstep(gr, vm, va, h=1e-30):
+    """The dense 2nb x 2nb Jacobian of Eq. (2) by complex step of the real-form
+    injections P_i = v_i sum_j v_j (G cos + B sin)(theta_i - theta_j),
+    Q_i = v_i sum_j v_j (G sin - B cos)(theta_i - theta_j): columns theta then v."""
+    Yd = oracle.ybus(gr).dense()
+    G, B = Yd.real, Yd.imag
+    nb = gr["nb"]
+
+    def pq(th, v):
+        d = th[:, None] - th[None, :]
+        vv = v[:, None] * v[None, :]
+        return np.concatenate([(vv * (G * np.cos(d) + B * np.sin(d))).sum(1),
+                               (vv * (G * np.sin(d) - B * np.cos(d))).sum(1)])
+
+    J = np.zeros((2 * nb, 2 * nb))
+    for c in range(2 * nb):
+        th, v = va.astype(complex), vm.astype(complex)
+        if c < nb:
+            th[c] += 1j * h
+        else:
+            v[c - nb] += 1j * h
+        J[:, c] = pq(th, v).imag / h
+    return J
+
+
+def test_target_pattern_assembly_equals_the_dense_jacobian():
+    """Alg. 2's placement into a larger pattern, against the dense Jacobian by
+    complex step (independent of the sparse code): with a zeroed target every
+    position holds the dense J's entry at its (row, column), the added
+    positions zero; a pattern without one of Eq. (2)'s entries is rejected."""
+    rng = np.random.default_rng(21)
+    gr = random_grid(9, 14, 21, shift_max=0.3)
+    vm, va = random_state(9, 21)
+    Y = oracle.ybus(gr)
+    Jd = _dense_jacobian_cstep(gr, vm, va)
+    colptr, rowidx = superset_pattern(Y, rng, extra=25)
+    out = oracle.jac_target(Y, oracle.jac_ybus(Y, vm, va), colptr, rowidx, np.zeros(len(rowidx)))
+    cols = np.repeat(np.arange(2 * Y.nb), np.diff(colptr))
+    ref = Jd[rowidx, cols]
+    assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(Jd))
+    assert np.count_nonzero(ref) > 0 and np.count_nonzero(out == 0.0) >= 25
+    # a missing entry of the Ybus-block pattern
+    jrp, jci = oracle.jac_pattern(Y)
+    R, C = 1, int(jci[jrp[1]])
+    k = next(k for k in range(colptr[C], colptr[C + 1]) if rowidx[k] == R)
+    rowidx2 = np.delete(rowidx, k)
+    colptr2 = colptr.copy()
+    colptr2[C + 1:] -= 1
+    with pytest.raises(ValueError):
+        oracle.jac_target(Y, oracle.jac_ybus(Y, vm, va), colptr2, rowidx2, np.zeros(len(rowidx2)))
