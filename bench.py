@@ -55,7 +55,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
     ap.add_argument("--profile-workload",
                     choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra", "newton", "sweep",
-                             "study"],
+                             "study", "target"],
                     help="run only this batched/adjoint workload (few launches, for profilers) and exit")
     return ap.parse_args(argv)
 
@@ -207,7 +207,7 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
     """The batched and adjoint workloads, each timed from a CUDA-graph replay
     (inputs larger than L2 for the batched ones, so no flush is needed).
     `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced", "ultra",
-    "newton", "sweep", "study"."""
+    "newton", "sweep", "study", "target"."""
     out = {}
     if only in (None, "n1"):
         out.update(_n1_workload(torch, pfgrid, synth, reps))
@@ -218,6 +218,8 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None):
         out["c2_random_bus_order"] = _permuted_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "reduced"):
         out["reduced_newton_csc_70k"] = _reduced_workload(torch, pfgrid, synth, max(reps, 20))
+    if only in (None, "target"):
+        out["target_pattern_70k"] = _target_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "ultra"):
         out["single_410k"] = _single_workload(torch, pfgrid, synth, 6, max(reps, 20))
     if only in (None, "study"):
@@ -404,6 +406,42 @@ def _reduced_workload(torch, pfgrid, synth, steps):
         res["gather"] = {"us_per_launch": 1e3 * mean, "algorithmic_bytes": byt,
                          "gbs": byt / (mean * 1e-3) / 1e9, "frac_of_hbm": byt / (mean * 1e-3) / 1e9 / hbm,
                          "hbm_peak_source": kind}
+    pfgrid.grid_check_error(grid)
+    return res
+
+
+def _target_workload(torch, pfgrid, synth, steps):
+    """Alg. 2 on the 70k-bus grid: the Jacobian into a caller's CSC pattern
+    that holds the Ybus blocks plus 16 coupled bus pairs (TCSC-like devices,
+    all four blocks), by both methods, L2 flushed between steps."""
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    w = synth.workload(WORKLOAD)
+    grid = pfgrid.ybus_build(w)
+    nb = w["nb"]
+    vm, va = dev(w["vm"][0]), dev(w["va"][0])
+    rp, ci = (x.cpu().numpy() for x in pfgrid.jac_pattern(grid))
+    rows = np.repeat(np.arange(2 * nb, dtype=np.int64), np.diff(rp))
+    cols = ci.astype(np.int64)
+    rng = np.random.default_rng(20230221)
+    pairs = rng.choice(nb, size=(16, 2), replace=False)
+    extra = [(x, y) for a, c in pairs for x in (a, c, nb + a, nb + c) for y in (a, c, nb + a, nb + c)]
+    key = np.unique(np.concatenate([cols * (2 * nb) + rows, [y * (2 * nb) + x for x, y in extra]]))
+    tcols, trows = key // (2 * nb), key % (2 * nb)
+    colptr = np.zeros(2 * nb + 1, np.int32)
+    np.add.at(colptr, tcols + 1, 1)
+    colptr = np.cumsum(colptr).astype(np.int32)
+    pfgrid.jac_set_target_pattern(grid, colptr, trows.astype(np.int32))
+    Jt = torch.zeros(len(trows), dtype=torch.float64, device="cuda")
+    P = torch.empty(nb, dtype=torch.float64, device="cuda")
+    Q = torch.empty_like(P)
+    res = {"nnz_target": int(len(trows)), "nnz_ybus_blocks": int(len(ci))}
+    for name, m in (("elementwise", 1), ("ybus", 0)):
+        f = lambda: pfgrid.jac_target(grid, m, vm, va, P, Q, Jt)
+        for _ in range(3):
+            f()
+        t = time_loop(torch, f, steps, flush, "target_" + name)
+        res["%s_evals_per_s" % name] = 1e3 / (sum(t) / len(t))
     pfgrid.grid_check_error(grid)
     return res
 
