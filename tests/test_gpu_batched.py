@@ -366,3 +366,37 @@ def test_cuda_graph_capture_and_replay(pf):
     pf.grid_check_error(grid)
     for a, b in zip((P, Q, J, L, gvm, gva, P1, Q1, J1), ref):
         assert torch.equal(a, b)
+
+
+def test_barrier_state_across_interleaved_kernels(pf):
+    """The batched kernels of one grid share its grid-barrier state (a launch
+    parity and two counters): alternate a small-batch adjoint (one item per
+    CTA, one barrier), a throughput adjoint (two barriers) and a batched
+    Jacobian (one barrier) with different grid sizes, 40 rounds; every launch
+    must give bitwise the results of the first and no wait may time out."""
+    import torch
+    gr, vm, va, Ps, Qs, wP, wQ = _adjoint_case(200, 280, 61, 170)
+    grid = pf.ybus_build(gr)
+    big = pf.batch_create(grid, 170, None)          # more items than SMs: k_adj, k_ewb
+    small = pf.batch_create(grid, 1, None)          # fewer: k_adj1
+    d = _d
+    vmb, vab = d(vm.ravel()), d(va.ravel())
+    vm1, va1 = d(vm[0]), d(va[0])
+    out = lambda n: torch.empty(n, dtype=torch.float64, device="cuda")
+    first = None
+    for r in range(40):
+        L1, g1m, g1a = out(1), out(200), out(200)
+        pf.adjoint_elementwise(small, vm1, va1, d(Ps), d(Qs), d(wP), d(wQ), L1, g1m, g1a)
+        L2, g2m, g2a = out(170), out(170 * 200), out(170 * 200)
+        pf.adjoint_elementwise(big, vmb, vab, d(Ps), d(Qs), d(wP), d(wQ), L2, g2m, g2a)
+        P, Q, J = out(170 * 200), out(170 * 200), out(big.nnzJ_total)
+        pf.jac_elementwise_batched(big, vmb, vab, P, Q, J)
+        torch.cuda.synchronize()
+        pf.grid_check_error(grid)
+        now = [x.cpu().numpy() for x in (L1, g1m, g1a, L2, g2m, g2a, P, Q, J)]
+        if first is None:
+            first = now
+        else:
+            assert all(np.array_equal(a, b) for a, b in zip(first, now)), r
+    # the single-state adjoint agrees with the first scenario of the big batch's
+    np.testing.assert_allclose(first[0], first[3][:1], rtol=1e-12)
