@@ -33,6 +33,7 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_OPS_PEAK_G = 152 * 2 * 2.070
 HBM_FALLBACK_GBS = 6800.0
 # FP64 arithmetic instructions per unit of the element-wise Jacobian kernel
+WORKLOAD_NAME = "synthetic grid, 70,000 buses / 88,000 branches, one voltage state"
 EW_OPS_PER_TERMINAL = 12   # E = V_o conj(U_q) 4, G = conj(Yc) E 4, K = v_q G 2, sum K 2
 EW_OPS_PER_BUS = 31        # fused phasor (sincos 15, 1/v 4, V 2) + diagonal entries and S (10)
 YB_OPS_PER_NNZ = 16
@@ -143,8 +144,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "synthetic grid, 70,000 buses / 88,000 branches, one voltage state",
-                       "global_batch": 1, "seq_len": 0, "parallelism": "none"},
+            "config": {"workload": WORKLOAD_NAME, "global_batch": 1, "seq_len": 0, "parallelism": "none"},
             "cpu_baseline": {"value": v, "unit": "evals/s", "cores": 1, "kind": "oracle",
                              "sample": "%d full element-wise evaluations of the 70k-bus grid" % n},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -676,8 +676,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "synthetic grid, 70,000 buses / 88,000 branches (nnzY %d, nnzJ %d), "
-                                   "one voltage state" % (grid.nnz, grid.nnzJ),
+            "config": {"workload": WORKLOAD_NAME, "nnzY": grid.nnz, "nnzJ": grid.nnzJ,
                        "global_batch": world, "seq_len": 0, "parallelism": "replicas" if world > 1 else "none",
                        "l2": "flushed between steps (512 MB write outside the timed events)",
                        "launch_config": cfg},
