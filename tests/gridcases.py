@@ -133,6 +133,7 @@ def superset_pattern(Y, rng, extra):
     for x in (a, c, Y.nb + a, Y.nb + c):
         for y in (a, c, Y.nb + a, Y.nb + c):
             coords.add((x, y))
+    extra = min(extra, n2 * n2 - len(coords))
     while len(coords) < len(jci) + extra:
         coords.add((int(rng.integers(n2)), int(rng.integers(n2))))
     cols = [[] for _ in range(n2)]

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gridcases import hub_grid, random_grid, random_state, relerr, superset_pattern
+from gridcases import hub_grid, make_grid, random_grid, random_state, relerr, superset_pattern
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -59,9 +59,19 @@ def check_target(pf, gr, seed, extra):
     return grid, colptr, rowidx
 
 
-@pytest.mark.parametrize("case", ["random", "hub"])
+def _star_with_parallels():
+    # a star with a triple-parallel spoke, two isolated buses, shunts everywhere
+    br = [(0, 1, 1.0, -10.0, 0.02, 1.0, 0.0), (1, 0, 2.0, -8.0, 0.01, 1.03, 0.05),
+          (0, 1, 0.5, -12.0, 0.0, 0.98, -0.02), (0, 2, 1.5, -9.0, 0.03, 1.0, 0.0),
+          (3, 0, 0.7, -7.0, 0.04, 1.0, 0.0)]
+    return make_grid(6, br, shunts={i: (0.01 * i, -0.02 * i) for i in range(6)})
+
+
+@pytest.mark.parametrize("case", ["random", "hub", "parallels", "single"])
 def test_target_pattern_both_methods(pf, case):
-    gr = random_grid(700, 980, 31, shift_max=0.2) if case == "random" else hub_grid(300, 33)
+    gr = {"random": lambda: random_grid(700, 980, 31, shift_max=0.2), "hub": lambda: hub_grid(300, 33),
+          "parallels": _star_with_parallels,
+          "single": lambda: make_grid(1, [], shunts={0: (0.03, -0.02)})}[case]()
     check_target(pf, gr, 31, extra=500)
 
 
