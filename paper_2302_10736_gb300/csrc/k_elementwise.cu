@@ -27,7 +27,9 @@
 // consecutive buses together with all of their terminals: the off-diagonal
 // slot (o, q) is written by the terminal's thread (parallel branches,
 // adjacent in the sorted order, are added by the owner's thread below), and
-// one thread per bus sums its terminals' K in a fixed order:
+// two threads per bus (the real and the imaginary parts; the window's buses
+// taken by decreasing terminal count, so that a warp's lanes loop equally
+// long) sum its terminals' K in a fixed order:
 //     S_o           = v_o^2 conj(Yd_o) + sum K
 //     dS_o/dtheta_o = j sum K
 //     dS_o/dv_o     = 2 v_o conj(Yd_o) + (sum K) / v_o
@@ -155,21 +157,22 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
             }
             double s, c;
             fast_sincos(th, tab, &s, &c);
-            sV[j] = make_double2(v * c, v * s);
             if (JAC) {
                 sU[j] = make_double2(c, s);
-                // 1/v only for the window's own buses: warps of ghost slots skip it
-                // (a warp-uniform branch), mixed warps compute it for all lanes
-                // and (v^2, 2 v) for the reduction, formed once per bus instead
-                // of by both threads of its pair
+                // V and 1/v are read for the window's own buses only: warps of
+                // ghost slots skip them (a warp-uniform branch), mixed warps
+                // form them for all lanes; and (v^2, 2 v) for the reduction,
+                // formed once per bus instead of by both threads of its pair
                 double iv = 0.0;
                 if (__any_sync(__activemask(), j < nbus)) {
+                    sV[j] = make_double2(v * c, v * s);
                     iv = fast_rcp(v);
                     if (j < nbus) sW2[j] = make_double2(v * v, v + v);
                 }
                 sW[j] = make_double2(v, iv);
-            } else if (j < nbus) {
-                sW2[j].x = v * v;
+            } else {
+                sV[j] = make_double2(v * c, v * s);
+                if (j < nbus) sW2[j].x = v * v;
             }
         }
         if (tid < nbus) {
