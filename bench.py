@@ -4,8 +4,10 @@ Ybus method, FP64, on the 70,000-bus / 88,000-branch synthetic grid.
 One step = one full evaluation by the element-wise method (phasor step +
 fused terminal evaluation and reduction) producing P, Q [nb] and all Jacobian
 values J [4 nnzY] from (vm, va) already resident in HBM.  The Ybus method is
-timed the same way and reported beside it.  L2 (129 MB) is flushed by writing
-a 512 MB buffer between timed steps, outside the timed events.
+timed the same way and reported beside it.  L2 (129 MB) is flushed between
+timed steps, outside the timed events, by writing a 512 MB buffer and then
+reading a 256 MB one: the step's data is evicted, and the lines left in L2 are
+clean, so the step does not pay for writing back the flush's own dirty lines.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank evaluates its own replica of the workload
@@ -162,6 +164,24 @@ def job_throughput(torch, ms_local, world, dist, device):
     return ms, world * 1e3 / ms
 
 
+class L2Flush:
+    """Evicts the step's data from L2 (129 MB): writes a 512 MB buffer, then
+    reads a 256 MB one so the lines left behind are clean.  With the write
+    alone, L2 ends full of dirty lines and the timed step that follows pays
+    their write-back on its own misses (about 2 us of the 70k-bus step)."""
+
+    def __init__(self, torch, read=True):
+        self.torch = torch
+        self.w = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+        self.r = torch.ones(32 << 20, dtype=torch.float64, device="cuda") if read else None
+        self.acc = torch.zeros((), dtype=torch.float64, device="cuda")
+
+    def fill_(self, x):
+        self.w.fill_(x)
+        if self.r is not None:
+            self.torch.sum(self.r, dim=0, out=self.acc)
+
+
 def time_loop(torch, fn, steps, flush, name):
     """Per-step device time (ms) of fn(), L2 flushed before every step outside
     the events; the loop is an NVTX range so profilers can select it."""
@@ -238,7 +258,7 @@ def _study_workload(torch, pfgrid, synth, steps):
     assembly) against the fused kernel, and its interleaved-vs-separate
     voltage storage for the Ybus injections, on the 70k-bus grid, L2 flushed."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
-    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    flush = L2Flush(torch)
     w = synth.workload(WORKLOAD)
     grid = pfgrid.ybus_build(w)
     vm, va = dev(w["vm"][0]), dev(w["va"][0])
@@ -275,7 +295,7 @@ def _size_sweep(torch, pfgrid, synth, steps):
     paper's per-case table that separate launches expose), with the time of
     each relative to the 118-bus grid (the paper's complexity study)."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
-    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    flush = L2Flush(torch)
     rows = []
     for nb in SWEEP_SIZES:
         nl = int(round(1.32 * nb))
@@ -347,7 +367,7 @@ def _newton_workload(torch, pfgrid, synth, k, reps=5):
 def _single_workload(torch, pfgrid, synth, k, steps):
     """Single evaluations of workload k by both methods, L2 flushed between steps."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
-    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    flush = L2Flush(torch)
     w = synth.workload(k)
     grid = pfgrid.ybus_build(w)
     vm, va = dev(w["vm"][0]), dev(w["va"][0])
@@ -376,7 +396,7 @@ def _reduced_workload(torch, pfgrid, synth, steps):
     kernel (one launch); the Ybus method's gather launch is timed by the
     tracer."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
-    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    flush = L2Flush(torch)
     w = synth.workload(WORKLOAD)
     grid = pfgrid.ybus_build(w)
     vm, va = dev(w["vm"][0]), dev(w["va"][0])
@@ -415,7 +435,7 @@ def _target_workload(torch, pfgrid, synth, steps):
     that holds the Ybus blocks plus 16 coupled bus pairs (TCSC-like devices,
     all four blocks), by both methods, L2 flushed between steps."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
-    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    flush = L2Flush(torch)
     w = synth.workload(WORKLOAD)
     grid = pfgrid.ybus_build(w)
     nb = w["nb"]
@@ -451,7 +471,7 @@ def _permuted_workload(torch, pfgrid, synth, steps):
     the numbering): single evaluations by both methods, L2 flushed between
     steps, against the same grid in its own numbering."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
-    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")
+    flush = L2Flush(torch)
     res = {}
     base = synth.workload(WORKLOAD)
     for tag, w in (("own_numbering", base), ("random_numbering", synth.renumber_buses(base, synth.BASE_SEED))):
@@ -577,7 +597,7 @@ def main():
     Q = torch.empty_like(P)
     J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
     cfg = pfgrid.grid_get_config(grid) if args.no_autotune else pfgrid.grid_autotune(grid, vm, va, reps=20)
-    flush = torch.empty(64 << 20, dtype=torch.float64, device="cuda")   # 512 MB > L2
+    flush = L2Flush(torch)
     T = 2 * nl
 
     ew = lambda: pfgrid.jac_elementwise(grid, vm, va, P, Q, J)
@@ -599,6 +619,8 @@ def main():
     t_yb = time_loop(torch, yb, args.steps, flush, "ybus")
     t_iew = time_loop(torch, iew, args.steps, flush, "inj_ew")
     t_iyb = time_loop(torch, iyb, args.steps, flush, "inj_ybus")
+    # the headline step again after a write-only flush (L2 left full of dirty lines)
+    t_dirty = time_loop(torch, ew, args.steps, L2Flush(torch, read=False), "ew_dirty_l2")
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -678,7 +700,7 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "nnzY": grid.nnz, "nnzJ": grid.nnzJ,
                        "global_batch": world, "seq_len": 0, "parallelism": "replicas" if world > 1 else "none",
-                       "l2": "flushed between steps (512 MB write outside the timed events)",
+                       "l2": "flushed between steps outside the timed events (512 MB written, then 256 MB read, so L2 holds clean lines)",
                        "launch_config": cfg},
             "e2e": e2e, "gpu_launches": len(tr_ew), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "compare": {
@@ -686,6 +708,7 @@ def main():
                 "ybus_jac_evals_per_s": 1e3 / (sum(t_yb) / len(t_yb)),
                 "elementwise_inj_evals_per_s": 1e3 / (sum(t_iew) / len(t_iew)),
                 "ybus_inj_evals_per_s": 1e3 / (sum(t_iyb) / len(t_iyb)),
+                "elementwise_jac_evals_per_s_after_write_only_flush": 1e3 / (sum(t_dirty) / len(t_dirty)),
                 "kernel_ms": {"phasor": ms_pu, "jac_ew": ms_jew, "jac_ybus": ms_jyb,
                               "inj_ew": kmean(tr_inj, "inj_ew")[0], "inj_ybus": kmean(tr_inj, "inj_ybus")[0]},
                 "ybus_fp64_ops_per_launch": YB_OPS_PER_NNZ * grid.nnz + YB_OPS_PER_ROW * nb,

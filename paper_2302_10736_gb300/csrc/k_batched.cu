@@ -613,8 +613,14 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         const int *sbus = a.slotbus + (long long)w * a.max_nph;
         // The thread's first phasor slot, terminal and bus are loaded up
         // front, in order of dependence, so that their latency hides behind
-        // the window metadata and the phasors.
+        // the window metadata and the phasors.  The sine/cosine table goes
+        // with the first level: behind the second-level gathers it would
+        // arrive last, and the barrier before the phasors waits for it.
         const int o0 = tid < a.max_nph ? sbus[tid] : 0;
+        const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
+        double2 tv0 = make_double2(0.0, 0.0), tv1 = tv0;
+        if (tid < kTrigN) tv0 = trig[tid];
+        if (tid + TB < kTrigN) tv1 = trig[tid + TB];
         double2 yc0 = make_double2(0.0, 0.0), ym0 = make_double2(0.0, 0.0);
         int2 loc0 = make_int2(0, 0);
         int tm0 = 0;
@@ -622,26 +628,23 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             const int p = t0 + tid;
             yc0 = a.tcoup[p];
             tm0 = a.tmir[p];
-            loc0 = make_int2(a.town[p] - b0, a.tloc[p].x);
+            loc0 = make_int2(a.town[p], a.tloc[p].x);   // owner made window-local at first use
         }
         if (fused && tid < a.max_nbr) e0 = a.brl[(long long)w * a.max_nbr + tid];
         // two threads per bus below: x = 2b + im, im = 0 the P part, 1 the Q part
         double spec0 = 0.0, wt0 = 0.0;
-        if (tid < 2 * nbus) {
-            bo = a.rorder[b0 + (tid >> 1)];   // buses by decreasing terminal count
-            const int o = b0 + bo;
-            spec0 = (tid & 1) ? a.Qs[o] : a.Ps[o];
-            wt0 = (tid & 1) ? a.wQ[o] : a.wP[o];
-        }
+        if (tid < 2 * nbus) bo = a.rorder[b0 + (tid >> 1)];   // buses by decreasing terminal count
         double th0 = 0.0, v0 = 0.0;
         if (tid < nph) {
             th0 = a.va[sb + o0];
             v0 = a.vm[sb + o0];
         }
-        const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
-        for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
-        batch_window_meta(a, sc, b0, b0 + nbus, t0, sbm, syd);
-        if (tid < nt) ym0 = a.tcoup[tm0];
+        if (tid < kTrigN) tab[tid] = tv0;
+        if (tid + TB < kTrigN) tab[tid + TB] = tv1;
+        for (int k = tid + 2 * TB; k < kTrigN; k += TB) tab[k] = trig[k];
+        // nothing before this barrier waits for a second-level load: what
+        // depends on one (the bus metadata in shared memory, loads addressed by
+        // the reduction order or the mirror terminal) comes after the phasors
         __syncthreads();
         // ---- phasors of the own and ghost buses ----
         for (int j = tid; j < nph; j += TB) {
@@ -662,6 +665,13 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
                 a.V[sb + o] = V;   // for the branch-parameter gradients
             }
         }
+        batch_window_meta(a, sc, b0, b0 + nbus, t0, sbm, syd);
+        if (tid < nt) ym0 = a.tcoup[tm0];
+        if (tid < 2 * nbus) {
+            const int o = b0 + bo;
+            spec0 = (tid & 1) ? a.Qs[o] : a.Ps[o];
+            wt0 = (tid & 1) ? a.wQ[o] : a.wP[o];
+        }
         __syncthreads();
         // ---- both flows of every terminal ----
         for (int i = tid; i < nt; i += TB) {
@@ -671,8 +681,9 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             if (i != tid) {
                 yc = a.tcoup[p];
                 ym = a.tcoup[a.tmir[p]];
-                loc = make_int2(a.town[p] - b0, a.tloc[p].x);
+                loc = make_int2(a.town[p], a.tloc[p].x);
             }
+            loc.x -= b0;
             const double2 Vo = sV[loc.x], Vq = sV[loc.y];
             const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);   // V_o conj(V_q)
             double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);                 // K_t

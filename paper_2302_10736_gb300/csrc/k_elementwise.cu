@@ -114,6 +114,16 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         const int *sbus = a.slotbus + (long long)w * a.max_nph;
         const int o0 = tid < a.max_nph ? sbus[tid] : 0;
         const int4 d0 = a.desc[2 * w], d1 = a.desc[2 * w + 1];
+        // the sine/cosine table is requested with the first level: issued after
+        // the second-level gathers it would arrive at the end of the kernel's
+        // whole input burst, and every warp waits for it at the barrier below
+        const bool load_tab = !PERSIST || w == (int)blockIdx.x;
+        const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
+        double2 tv0 = make_double2(0.0, 0.0), tv1 = tv0;
+        if (load_tab) {
+            if (tid < kTrigN) tv0 = trig[tid];
+            if (tid + TB < kTrigN) tv1 = trig[tid + TB];
+        }
         const int b0 = d0.x, nbus = d0.y, b1 = b0 + nbus, t0 = d0.z, nt = d0.w;
         const int r0 = d1.x, L = JAC ? d1.y : 0, nph = d1.z;
 
@@ -140,11 +150,13 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         if (tid < nt) {
             yc = a.tcoup[t0 + tid];
             nq = a.tloc[t0 + tid];
-            ol = a.town[t0 + tid] - b0;
+            ol = a.town[t0 + tid];   // made window-local at first use: nothing before the
+                                     // barrier below may wait for a second-level load
         }
-        if (!PERSIST || w == (int)blockIdx.x) {
-            const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
-            for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
+        if (load_tab) {
+            if (tid < kTrigN) tab[tid] = tv0;
+            if (tid + TB < kTrigN) tab[tid + TB] = tv1;
+            for (int k = tid + 2 * TB; k < kTrigN; k += TB) tab[k] = trig[k];
         }
         __syncthreads();
 
@@ -187,8 +199,9 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
             if (i != tid) {
                 yc = a.tcoup[t0 + i];
                 nq = a.tloc[t0 + i];
-                ol = a.town[t0 + i] - b0;
+                ol = a.town[t0 + i];
             }
+            ol -= b0;
             const double2 Vo = sV[ol];
             if (JAC) {
                 const double2 uq = sU[nq.x];
