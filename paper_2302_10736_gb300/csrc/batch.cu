@@ -55,39 +55,54 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
         b->h_sc[s] = scen_outage(g->topo, outage ? outage[s] : -1);
         b->h_joff[s + 1] = b->h_joff[s] + 4LL * (g->nnz - 2 * b->h_sc[s].del);
     }
-    // The batch's own windows: 256 buses and up to 3 x 256 terminals each
-    // (fewer terminals per thread if a window would not fit in shared memory),
-    // so that every thread owns a bus in the reduction.  When the batch has
-    // fewer (scenario, window) items than the GPU has SMs, the windows are cut
-    // at equal cost into about one item per SM (more CTAs would only make the
-    // grid barriers dearer).
-    auto fits = [](const HostEw &L) {
-        return ew_smem_plan(L.max_nbus, L.max_nt, L.max_L, true).total + kTrigN * sizeof(double2) <= kMaxSmem;
+    // The batch's own windows: 256 buses and up to tfac x 256 terminals each,
+    // so that every thread owns a bus in the reduction.  tfac is the largest of
+    // 3, 2, 1 at which four CTAs of the batched Jacobian kernel share an SM's
+    // shared memory (its register budget allows four; with three, barrier and
+    // load stalls leave more of the FP64 pipe idle: 1.53 against 1.47 ms for
+    // 1,024 N-1 scenarios of the 10,000-bus grid), else the largest at which
+    // one fits.  When the batch has fewer (scenario, window) items than the
+    // GPU has SMs, the windows are cut at equal cost into about one item per
+    // SM (more CTAs would only make the grid barriers dearer).
+    int dev = 0, nsm = 0, smem_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+        delete pb;
+        return set_error(PF_ECUDA, "batch_create: cannot query the device");
+    }
+    auto smem_of = [](const HostEw &L) {
+        return ew_smem_plan(L.max_nbus, L.max_nt, L.max_L, true).total + kTrigN * sizeof(double2);
     };
+    const size_t kCtaReserve = 1024;   // shared memory the runtime keeps per resident CTA
     HostEw E;
+    bool have = false;
     for (int tfac = 3; tfac >= 1; --tfac) {
-        pf_status hs = host_ew(g->topo, 256, E, tfac);
+        HostEw F;
+        pf_status hs = host_ew(g->topo, 256, F, tfac);
         if (hs) {
             delete pb;
             return hs;
         }
-        if (fits(E)) break;
-        if (tfac == 1) {
-            delete pb;
-            return set_error(PF_EUNSUPPORTED, "batch_create: a window exceeds shared memory");
+        const size_t sm = smem_of(F);
+        if (sm > kMaxSmem) continue;
+        const bool four = 4 * (sm + kCtaReserve) <= (size_t)smem_sm;
+        if (!have || four) {
+            E = std::move(F);
+            have = true;
         }
+        if (four) break;
     }
-    int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess) {
+    if (!have) {
         delete pb;
-        return set_error(PF_ECUDA, "batch_create: cannot query the device");
+        return set_error(PF_EUNSUPPORTED, "batch_create: a window exceeds shared memory");
     }
     bool ghost = false;
     if (nscen > 0 && (long long)nscen * E.nwin < nsm) {
         HostEw F;
         const int target = (nsm + nscen - 1) / nscen;
-        if (host_ew(g->topo, 256, F, E.tfac, target) == PF_OK && F.nwin > E.nwin && fits(F)) E = std::move(F);
+        if (host_ew(g->topo, 256, F, E.tfac, target) == PF_OK && F.nwin > E.nwin && smem_of(F) <= kMaxSmem)
+            E = std::move(F);
         // latency-bound: the adjoint keeps each item on one CTA (k_adj1), which
         // forms its window's phasors itself (with its ghost buses) instead of a
         // separate phase and grid barrier
