@@ -458,41 +458,44 @@ static void *mapped_device_ptr(const void *h)
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
-PF_API pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P, double *Q,
-                           double *J, pf_stream stream)
+// eval_host and eval_host_async: `sync` says whether the call waits for the
+// results; the asynchronous form takes page-locked buffers only.
+static pf_status eval_host_impl(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P,
+                                double *Q, double *J, pf_stream stream, bool sync, const char *name)
 {
-    pf_status st = check_eval(grid, vm, va, "eval_host");
+    pf_status st = check_eval(grid, vm, va, name);
     if (st) return st;
-    if (method != 0 && method != 1) return set_error(PF_EINVAL, "eval_host: method must be 0 (Ybus) or 1 (element-wise)");
+    if (method != 0 && method != 1) return set_error(PF_EINVAL, "%s: method must be 0 (Ybus) or 1 (element-wise)", name);
     Grid *g = &grid->g;
     if (g->nb == 0) return PF_OK;
-    if (!P || !Q || !J) return set_error(PF_EINVAL, "eval_host: P, Q and J must be non-NULL");
+    if (!P || !Q || !J) return set_error(PF_EINVAL, "%s: P, Q and J must be non-NULL", name);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nb = (size_t)g->nb, nJ = 4 * (size_t)g->nnz;
+    void *dvm = mapped_device_ptr(vm), *dva = mapped_device_ptr(va);
+    void *dP = mapped_device_ptr(P), *dQ = mapped_device_ptr(Q), *dJ = mapped_device_ptr(J);
+    if (!sync && !(dvm && dva && dP && dQ && dJ))
+        return set_error(PF_EINVAL, "%s: vm, va, P, Q and J must all be page-locked host buffers", name);
     if (!g->st_J) {
         double **const out[5] = {&g->st_vm, &g->st_va, &g->st_P, &g->st_Q, &g->st_J};
         const size_t n[5] = {nb, nb, nb, nb, nJ};
         PF_CUDA(alloc_all(g->arena, out, n));
     }
-    if (method == 1) {
+    if (method == 1 && dP && dQ && dJ) {
         // page-locked, mapped host buffers: the kernel reads vm, va and stores
-        // P, Q, J (plain coalesced stores) across the host link while it runs;
-        // no staging copies
-        void *dvm = mapped_device_ptr(vm), *dva = mapped_device_ptr(va);
-        void *dP = mapped_device_ptr(P), *dQ = mapped_device_ptr(Q), *dJ = mapped_device_ptr(J);
-        if (dP && dQ && dJ) {
-            if (!dvm || !dva) {
-                PF_CUDA(cudaMemcpyAsync(g->st_vm, vm, nb * 8, cudaMemcpyHostToDevice, s));
-                PF_CUDA(cudaMemcpyAsync(g->st_va, va, nb * 8, cudaMemcpyHostToDevice, s));
-                dvm = g->st_vm;
-                dva = g->st_va;
-            }
+        // P, Q, J across the host link while it runs; no staging copies
+        if (!dvm || !dva) {
+            PF_CUDA(cudaMemcpyAsync(g->st_vm, vm, nb * 8, cudaMemcpyHostToDevice, s));
+            PF_CUDA(cudaMemcpyAsync(g->st_va, va, nb * 8, cudaMemcpyHostToDevice, s));
+            dvm = g->st_vm;
+            dva = g->st_va;
+        }
+        {
             TraceScope t(g, PF_K_JAC_EW, s);
             PF_CUDA(launch_jac_ew(g, (const double *)dvm, (const double *)dva, (double *)dP, (double *)dQ,
                                   (double *)dJ, s, true));
-            PF_CUDA(cudaStreamSynchronize(s));
-            return PF_OK;
         }
+        if (sync) PF_CUDA(cudaStreamSynchronize(s));
+        return PF_OK;
     }
     PF_CUDA(cudaMemcpyAsync(g->st_vm, vm, nb * 8, cudaMemcpyHostToDevice, s));
     PF_CUDA(cudaMemcpyAsync(g->st_va, va, nb * 8, cudaMemcpyHostToDevice, s));
@@ -502,8 +505,20 @@ PF_API pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, cons
     PF_CUDA(cudaMemcpyAsync(P, g->st_P, nb * 8, cudaMemcpyDeviceToHost, s));
     PF_CUDA(cudaMemcpyAsync(Q, g->st_Q, nb * 8, cudaMemcpyDeviceToHost, s));
     PF_CUDA(cudaMemcpyAsync(J, g->st_J, nJ * 8, cudaMemcpyDeviceToHost, s));
-    PF_CUDA(cudaStreamSynchronize(s));
+    if (sync) PF_CUDA(cudaStreamSynchronize(s));
     return PF_OK;
+}
+
+PF_API pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P, double *Q,
+                           double *J, pf_stream stream)
+{
+    return eval_host_impl(grid, method, vm, va, P, Q, J, stream, true, "eval_host");
+}
+
+PF_API pf_status eval_host_async(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P,
+                                 double *Q, double *J, pf_stream stream)
+{
+    return eval_host_impl(grid, method, vm, va, P, Q, J, stream, false, "eval_host_async");
 }
 
 PF_API pf_status phasor(int32_t n, const double *vm, const double *va, double *U, double *V, pf_stream stream)

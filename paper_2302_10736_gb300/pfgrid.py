@@ -64,6 +64,7 @@ def _load():
         "jac_ybus": (st, [vp, vp, vp, vp, vp, vp, vp]),
         "jac_elementwise": (st, [vp, vp, vp, vp, vp, vp, vp]),
         "eval_host": (st, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "eval_host_async": (st, [vp, i32, vp, vp, vp, vp, vp, vp]),
         "grid_get_config": (st, [vp, ctypes.POINTER(pf_config)]),
         "grid_set_config": (st, [vp, ctypes.POINTER(pf_config), vp]),
         "grid_autotune": (st, [vp, vp, vp, i32, vp, ctypes.POINTER(pf_config)]),
@@ -290,18 +291,29 @@ def jac_elementwise(grid, vm, va, P, Q, J, stream=None):
                                 _dptr(Q, "Q", n), _dptr(J, "J", grid.nnzJ), _stream(stream)), "jac_elementwise")
 
 
+def _eval_host_call(fn, name, grid, method, vm, va, P, Q, J, stream):
+    for nm, a, n in (("vm", vm, grid.nb), ("va", va, grid.nb), ("P", P, grid.nb), ("Q", Q, grid.nb),
+                     ("J", J, grid.nnzJ)):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size >= n):
+            raise TypeError("%s must be a contiguous float64 numpy array with >= %d elements" % (nm, n))
+    m = {"ybus": 0, "elementwise": 1}.get(method, method)
+    vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+    _check(fn(grid.handle, int(m), vp(vm), vp(va), vp(P), vp(Q), vp(J), _stream(stream)), name)
+
+
 def eval_host(grid, method, vm, va, P, Q, J, stream=None):
     """Host numpy buffers in and out (vm, va, P, Q [nb]; J [4 nnzY]).  With
     page-locked buffers the element-wise kernel reads and writes them directly.
-    `stream` as an integer handle skips the per-call look-up of torch's
-    current stream."""
-    for name, a, n in (("vm", vm, grid.nb), ("va", va, grid.nb), ("P", P, grid.nb), ("Q", Q, grid.nb),
-                       ("J", J, grid.nnzJ)):
-        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size >= n):
-            raise TypeError("%s must be a contiguous float64 numpy array with >= %d elements" % (name, n))
-    m = {"ybus": 0, "elementwise": 1}.get(method, method)
-    vp = lambda a: ctypes.c_void_p(a.ctypes.data)
-    _check(_lib.eval_host(grid.handle, int(m), vp(vm), vp(va), vp(P), vp(Q), vp(J), _stream(stream)), "eval_host")
+    Returns once the results are in P, Q, J.  `stream` as an integer handle
+    skips the per-call look-up of torch's current stream."""
+    _eval_host_call(_lib.eval_host, "eval_host", grid, method, vm, va, P, Q, J, stream)
+
+
+def eval_host_async(grid, method, vm, va, P, Q, J, stream=None):
+    """eval_host that returns once the work is enqueued: all five buffers must
+    be page-locked, and P, Q, J hold the results after `stream` is
+    synchronized."""
+    _eval_host_call(_lib.eval_host_async, "eval_host_async", grid, method, vm, va, P, Q, J, stream)
 
 
 def phasor(vm, va, U, V, stream=None):

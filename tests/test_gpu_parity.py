@@ -201,6 +201,45 @@ def test_eval_host_matches_device(pf):
                 assert np.array_equal(J, dev[name][2])
 
 
+def test_eval_host_async_pipelined_states(pf):
+    """Two states evaluated back to back on one stream into two sets of
+    page-locked buffers, one synchronization at the end: each set holds its
+    own state's results, bit for bit those of the device path."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    grid = pf.ybus_build(w)
+    pinned = lambda n: torch.full((n,), np.nan, dtype=torch.float64, pin_memory=True).numpy()
+    states = [(w["vm"][0].copy(), w["va"][0].copy()), (w["vm"][0] * 1.01, w["va"][0] - 0.02)]
+    for m, name in ((0, "jac_ybus"), (1, "jac_elementwise")):
+        bufs = []
+        s = torch.cuda.Stream()
+        for vm, va in states:
+            vin, ain = pinned(grid.nb), pinned(grid.nb)
+            vin[:], ain[:] = vm, va
+            P, Q, J = pinned(grid.nb), pinned(grid.nb), pinned(grid.nnzJ)
+            pf.eval_host_async(grid, m, vin, ain, P, Q, J, stream=s.cuda_stream)
+            bufs.append((P, Q, J))
+        s.synchronize()
+        for (vm, va), (P, Q, J) in zip(states, bufs):
+            dev = gpu_eval(pf, grid, vm, va)
+            assert np.array_equal(P, dev[name][0]) and np.array_equal(Q, dev[name][1])
+            assert np.array_equal(J, dev[name][2])
+
+
+def test_eval_host_async_rejects_pageable_buffers(pf):
+    import torch
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    grid = pf.ybus_build(w)
+    pinned = lambda n: torch.zeros((n,), dtype=torch.float64, pin_memory=True).numpy()
+    vin, ain, P, Q, J = pinned(grid.nb), pinned(grid.nb), pinned(grid.nb), pinned(grid.nb), np.zeros(grid.nnzJ)
+    vin[:], ain[:] = w["vm"][0], w["va"][0]
+    with pytest.raises(pf.PfError, match="page-locked"):
+        pf.eval_host_async(grid, 1, vin, ain, P, Q, J)
+    assert not np.any(P)   # nothing was enqueued
+
+
 def test_set_params_matches_rebuild(pf):
     import torch
     gr = random_grid(800, 1100, 12, shift_max=0.2)
