@@ -197,10 +197,12 @@ pf_status eval_host(pf_grid *grid, int32_t method, const double *vm, const doubl
  * element-wise kernel straight on the mapped buffers as eval_host does;
  * method 0 copies in, evaluates and copies out through the grid's staging
  * buffers, so calls on one grid that use method 0 must be issued on one
- * stream.  Successive calls overlap one evaluation's host-side call and
- * launch with the previous one's device work: on the 70k-bus grid about
- * 64 us per evaluation against 79 us for eval_host, whose return waits for
- * the results.
+ * stream, while method-1 calls only read the grid and may overlap on several
+ * streams (with distinct output buffers).  Successive calls overlap one
+ * evaluation's host-side call and launch with the previous one's device
+ * work: on the 70k-bus grid about 64 us per evaluation on one stream, 56 us
+ * alternating two streams (the 9 MB of results take 50 us on the host link),
+ * against 79 us for eval_host, whose return waits for the results.
  */
 pf_status eval_host_async(pf_grid *grid, int32_t method, const double *vm, const double *va, double *P, double *Q,
                           double *J, pf_stream stream);

@@ -202,25 +202,26 @@ def test_eval_host_matches_device(pf):
 
 
 def test_eval_host_async_pipelined_states(pf):
-    """Two states evaluated back to back on one stream into two sets of
-    page-locked buffers, one synchronization at the end: each set holds its
-    own state's results, bit for bit those of the device path."""
+    """Two states evaluated back to back into two sets of page-locked
+    buffers, one synchronization at the end: each set holds its own state's
+    results, bit for bit those of the device path.  Method 0 on one stream;
+    method 1 on one stream and on two (its calls may overlap)."""
     import torch
     from paper_2302_10736_gb300 import synth
     w = synth.workload(1)
     grid = pf.ybus_build(w)
     pinned = lambda n: torch.full((n,), np.nan, dtype=torch.float64, pin_memory=True).numpy()
     states = [(w["vm"][0].copy(), w["va"][0].copy()), (w["vm"][0] * 1.01, w["va"][0] - 0.02)]
-    for m, name in ((0, "jac_ybus"), (1, "jac_elementwise")):
+    for m, name, nstreams in ((0, "jac_ybus", 1), (1, "jac_elementwise", 1), (1, "jac_elementwise", 2)):
         bufs = []
-        s = torch.cuda.Stream()
-        for vm, va in states:
+        streams = [torch.cuda.Stream() for _ in range(nstreams)]
+        for k, (vm, va) in enumerate(states):
             vin, ain = pinned(grid.nb), pinned(grid.nb)
             vin[:], ain[:] = vm, va
             P, Q, J = pinned(grid.nb), pinned(grid.nb), pinned(grid.nnzJ)
-            pf.eval_host_async(grid, m, vin, ain, P, Q, J, stream=s.cuda_stream)
+            pf.eval_host_async(grid, m, vin, ain, P, Q, J, stream=streams[k % nstreams].cuda_stream)
             bufs.append((P, Q, J))
-        s.synchronize()
+        torch.cuda.synchronize()
         for (vm, va), (P, Q, J) in zip(states, bufs):
             dev = gpu_eval(pf, grid, vm, va)
             assert np.array_equal(P, dev[name][0]) and np.array_equal(Q, dev[name][1])
