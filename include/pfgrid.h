@@ -229,11 +229,20 @@ pf_status phasor(int32_t n, const double *vm, const double *va, double *U, doubl
  *             scratch is a fixed 4 MiB device array in the library)
  *   rowptr [nb+1], colidx [nnz], yval [nnz][2] (re, im; 16-byte aligned):
  *             a Ybus in CSR form owned by the caller (for example the arrays
- *             returned by ybus_get), read during the call
- *   vm, va [nb] in; P, Q [nb] out (device pointers, caller-owned)
+ *             returned by ybus_get), read during the call; nnz = rowptr[nb],
+ *             rowptr nondecreasing from 0, every colidx entry in [0, nb).
+ *             The call does not read rowptr on the host, so it cannot check
+ *             these: arrays shorter than nnz, or a column outside [0, nb),
+ *             make the kernels read outside the caller's buffers.
+ *   vm, va [nb] in; P, Q [nb] out (device pointers on the current device,
+ *             caller-owned)
  * The scratch array is shared by all calls on a device and keeps the last
- * call's contents; calls that overlap on the GPU race on it, so issue them on
- * one stream.  The first call on a device looks up the array's address.
+ * call's contents (each call writes the entries it reads first, so nothing
+ * needs clearing); calls that overlap on the GPU race on it, so issue them on
+ * one stream.  The first call on a device looks up the array's device
+ * address (with that device current) and keeps it for the process: make that
+ * first call before any stream capture, and do not use this entry point after
+ * cudaDeviceReset, which invalidates the kept address.
  */
 pf_status inj_ybus_noalloc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *yval,
                            const double *vm, const double *va, double *P, double *Q, pf_stream stream);

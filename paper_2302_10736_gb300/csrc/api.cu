@@ -16,6 +16,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 
@@ -38,6 +40,25 @@ pf_status set_error(pf_status s, const char *fmt, ...)
 }
 
 std::atomic<int> g_alloc_countdown{-1};
+
+// One process-wide maximum per (device, kernel): the attribute is a property
+// of the kernel on a device, shared by every grid and batch, so it is only
+// ever raised.  Lowering it for a smaller grid would make a larger grid's
+// next launch fail.
+cudaError_t ensure_dyn_smem(const void *kernel, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = set[std::make_pair(dev, kernel)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 pf_status cuda_error(cudaError_t e, const char *what)
 {

@@ -900,7 +900,7 @@ static cudaError_t coop_resident(K kernel, int &resident, int tb, size_t smem)
     if (resident == 0) {
         // set for every size: the kernels also hold a little static shared
         // memory, which counts against the default 48 KB
-        if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        if ((e = ensure_dyn_smem(reinterpret_cast<const void *>(kernel), smem))) return e;
         int per_sm = 0, dev = 0, nsm = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, tb, smem))) return e;
         if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))

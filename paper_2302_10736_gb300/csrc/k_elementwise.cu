@@ -400,9 +400,11 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     const bool persist = out == EwOut::host && JAC;
     const bool red = out == EwOut::reduced && JAC;
     uint32_t &conf = persist ? g->ew_smem_host : red ? g->ew_smem_red : JAC ? g->ew_smem_jac : g->ew_smem_inj;
+    // conf: the largest size this grid has ensured (the process-wide limit
+    // only grows, so a size ensured once stays valid)
     if (smem > 48u * 1024u && smem > conf) {
-        cudaError_t e = cudaFuncSetAttribute(persist ? k_ew_host : red ? k_ew_red : k_ew<JAC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = ensure_dyn_smem(
+            reinterpret_cast<const void *>(persist ? k_ew_host : red ? k_ew_red : k_ew<JAC>), smem);
         if (e != cudaSuccess) return e;
         conf = smem;
     }
@@ -459,7 +461,7 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
 cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm)
 {
     if (smem > 48u * 1024u) {
-        cudaError_t e = cudaFuncSetAttribute(k_ew<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = ensure_dyn_smem(reinterpret_cast<const void *>(k_ew<true>), smem);
         if (e != cudaSuccess) return e;
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ew<true>, tb, smem);

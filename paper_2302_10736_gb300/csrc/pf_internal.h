@@ -17,6 +17,9 @@ namespace pf {
 // --------------------------------------------------------------- errors --
 pf_status set_error(pf_status s, const char *fmt, ...);
 pf_status cuda_error(cudaError_t e, const char *what);
+// Raise the kernel's dynamic shared-memory limit on the current device to at
+// least `bytes` (never lowers it; thread-safe).
+cudaError_t ensure_dyn_smem(const void *kernel, size_t bytes);
 #define PF_CUDA(call)                                            \
     do {                                                         \
         cudaError_t e_ = (call);                                 \

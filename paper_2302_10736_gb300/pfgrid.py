@@ -325,15 +325,26 @@ def phasor(vm, va, U, V, stream=None):
 
 def inj_ybus_noalloc(rowptr, colidx, yval, vm, va, P, Q, stream=None):
     """Ybus-method injections from a caller-owned CSR Ybus (int32 rowptr/colidx,
-    float64 yval [nnz, 2]); the library allocates nothing for this call."""
+    float64 yval [nnz, 2]); the library allocates nothing for this call.  The
+    lengths of colidx and yval are checked against rowptr[-1] (one read of
+    that entry); column indices must lie in [0, nb)."""
     import torch
     nb = rowptr.numel() - 1
     for name, x in (("rowptr", rowptr), ("colidx", colidx)):
         if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.int32 and x.is_contiguous()):
             raise TypeError("%s must be a contiguous int32 CUDA tensor" % name)
+    cur = torch.cuda.current_device()
+    for name, x in (("rowptr", rowptr), ("colidx", colidx), ("yval", yval), ("vm", vm), ("va", va), ("P", P),
+                    ("Q", Q)):
+        if isinstance(x, torch.Tensor) and x.is_cuda and x.device.index != cur:
+            raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (name, x.device.index, cur))
+    # the C call cannot read rowptr on the host: check the array lengths here
+    nnz = int(rowptr[-1].item()) if nb >= 0 and rowptr.numel() else 0
+    if colidx.numel() < nnz:
+        raise ValueError("colidx has %d entries, rowptr[-1] = %d" % (colidx.numel(), nnz))
     _check(_lib.inj_ybus_noalloc(nb, ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(colidx.data_ptr()),
-                                 _dptr(yval, "yval"), _dptr(vm, "vm", nb), _dptr(va, "va", nb), _dptr(P, "P", nb),
-                                 _dptr(Q, "Q", nb), _stream(stream)), "inj_ybus_noalloc")
+                                 _dptr(yval, "yval", 2 * nnz), _dptr(vm, "vm", nb), _dptr(va, "va", nb),
+                                 _dptr(P, "P", nb), _dptr(Q, "Q", nb), _stream(stream)), "inj_ybus_noalloc")
 
 
 def grid_inject_barrier_fault(grid, stream=None):

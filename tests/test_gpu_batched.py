@@ -7,6 +7,8 @@ checked against J^T r of the oracle's Jacobian, complex-step branch-parameter
 gradients, and (25k-bus workload) long-double central differences on 200
 seeded coordinates.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -59,7 +61,24 @@ def with_parallel(gr):
     return out
 
 
-def check_batch(pf, gr, vm, va, outage, scenarios=None, tol=TOL, cfg=None):
+def _oracle_pq(gr, vm, va, outage, scenarios):
+    """The oracle's P and Q of the listed scenarios, each on its grid without
+    the outage branch (threads: the oracle's C calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(s):
+        l = int(outage[s]) if outage is not None else -1
+        skip = _skip(gr["nl"], l)
+        return oracle.elementwise(gr, vm[s], va[s], oracle.ybus(gr, skip=skip), skip=skip, jac=False)[:2]
+
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        return dict(zip(scenarios, ex.map(one, scenarios)))
+
+
+def check_batch(pf, gr, vm, va, outage, scenarios=None, tol=TOL, cfg=None, pq_all=False):
+    """Scenarios `scenarios` (all if None) in full: P, Q of all four batched
+    calls, both Jacobians and the pattern against the oracle.  With pq_all,
+    P and Q of every other scenario are compared as well."""
     import torch
     S, nb = vm.shape
     grid = pf.ybus_build(gr)
@@ -100,6 +119,12 @@ def check_batch(pf, gr, vm, va, outage, scenarios=None, tol=TOL, cfg=None):
         errs += [relerr(a, b) for a, b in zip(blocks(Js, jci, nb, Y.nnz), blocks(Jr, jci, nb, Y.nnz))]
         errs += [relerr(a, b) for a, b in zip(blocks(Jys, jci, nb, Y.nnz), blocks(Jr, jci, nb, Y.nnz))]
         assert max(errs) <= tol, (s, l, errs)
+    if pq_all and scenarios is not None:
+        rest = sorted(set(range(S)) - set(scenarios))
+        for s, (Pr, Qr) in _oracle_pq(gr, vm, va, outage, rest).items():
+            errs = [relerr(x[s], r) for x, r in ((P, Pr), (Q, Qr), (Pi, Pr), (Qi, Qr), (Py, Pr), (Qy, Qr), (Pyi, Pr),
+                                                  (Qyi, Qr))]
+            assert max(errs) <= tol, (s, errs)
     return batch
 
 
@@ -122,6 +147,49 @@ def test_ybus_batched_every_lane_count(pf, lanes):
     outage = np.array([int(nonbridge[5]), -1, 0, gr["nl"] - 1, int(nonbridge[40])], np.int32)
     vm, va = synth.voltages(300, len(outage), 23, 0, 0.93, 1.07, 0.25)
     check_batch(pf, gr, vm, va, outage, cfg=dict(ybus_lanes=lanes, ybus_block=128))
+
+
+def test_launches_alternate_between_grids_of_different_shared_memory(pf):
+    """The dynamic shared-memory limit is a per-kernel setting shared by every
+    grid and batch: a grid whose windows need little of it, launched for the
+    first time after one that needs more, must not lower it below what the
+    larger one needs (its next launches would fail)."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    grids = {"hub": hub_grid(400, 31), "small": random_grid(300, 400, 33, shift_max=0.2)}
+    state = {}
+    for key, gr in grids.items():
+        nb = gr["nb"]
+        vm, va = synth.voltages(nb, 2, 34, 0, 0.93, 1.07, 0.25)
+        Y = oracle.ybus(gr)
+        refs = [oracle.elementwise(gr, vm[s], va[s], Y) for s in range(2)]
+        state[key] = (gr, vm, va, refs, Y)
+    built = {}
+    for rnd in range(3):
+        for key in ("hub", "small"):
+            gr, vm, va, refs, Y = state[key]
+            nb = gr["nb"]
+            if key not in built:
+                grid = pf.ybus_build(gr)
+                built[key] = (grid, pf.batch_create(grid, 2, None))
+            grid, batch = built[key]
+            P = torch.empty(nb, dtype=torch.float64, device="cuda")
+            Q = torch.empty_like(P)
+            J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+            pf.jac_elementwise(grid, _d(vm[0]), _d(va[0]), P, Q, J)
+            Pb = torch.empty(2 * nb, dtype=torch.float64, device="cuda")
+            Qb = torch.empty_like(Pb)
+            Jb = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
+            pf.jac_elementwise_batched(batch, _d(vm), _d(va), Pb, Qb, Jb)
+            torch.cuda.synchronize()
+            pf.grid_check_error(grid)
+            Pr, Qr, Jr = refs[0]
+            assert relerr(P.cpu().numpy(), Pr) <= TOL and relerr(J.cpu().numpy(), Jr) <= TOL, (rnd, key)
+            Jbh = Jb.cpu().numpy()
+            for s in range(2):
+                Pr, Qr, Jr = refs[s]
+                assert relerr(Pb.cpu().numpy()[s * nb:(s + 1) * nb], Pr) <= TOL, (rnd, key, s)
+                assert relerr(Jbh[s * grid.nnzJ:(s + 1) * grid.nnzJ], Jr) <= TOL, (rnd, key, s)
 
 
 def test_batch_with_a_hub_bus(pf):
@@ -158,13 +226,14 @@ def test_batch_without_outages_equals_single_evaluation(pf):
 
 
 def test_workload3_n1_batch(pf):
-    """10,000 buses x 1,024 scenarios with distinct non-bridge outages: every
-    scenario's P and Q, and the Jacobian of 48 spread scenarios, against the
-    oracle on the grid without the branch."""
+    """10,000 buses x 1,024 scenarios with distinct non-bridge outages, against
+    the oracle on each grid without its branch: P and Q of all 1,024
+    scenarios (from all four batched calls), and the Jacobians (both methods)
+    and patterns of 48 spread scenarios."""
     from paper_2302_10736_gb300 import synth
     w = synth.workload(3)
     sample = sorted(set(np.linspace(0, 1023, 48).astype(int).tolist()))
-    batch = check_batch(pf, w, w["vm"], w["va"], w["outage"], scenarios=sample)
+    batch = check_batch(pf, w, w["vm"], w["va"], w["outage"], scenarios=sample, pq_all=True)
     assert batch.nscen == 1024
 
 

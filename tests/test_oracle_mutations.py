@@ -1,6 +1,7 @@
 """Plant plausible mistakes in a copy of the oracle (CPU only) and check that
 the pins of test_oracle_pins catch every one of them: a dropped term, a wrong
-sign, a wrong index, a transposed operand, a misplaced tap."""
+sign, a wrong index, a transposed operand, a misplaced tap, a swapped weight
+or a dropped square in the loss."""
 import os
 import shutil
 import subprocess
@@ -34,6 +35,12 @@ MUTATIONS = {
     "adj_weight": ("double rQ = 2.0 * wQ[i] * (Q[i] - Qs[i]);", "double rQ = 2.0 * wP[i] * (Q[i] - Qs[i]);"),
     # transposed Jacobian in J^T r
     "adj_transpose": ("gva[j] += J[p] * rP + J[2 * nnz + p] * rQ;", "gva[i] += J[p] * rP + J[2 * nnz + p] * rQ;"),
+    # P and Q weights swapped in the loss
+    "loss_weight_swap": ("double dp = P[i] - Ps[i], dq = Q[i] - Qs[i];\n        L += wP[i] * dp * dp + wQ[i] * dq * dq;",
+                         "double dp = P[i] - Ps[i], dq = Q[i] - Qs[i];\n        L += wQ[i] * dp * dp + wP[i] * dq * dq;"),
+    # a dropped square in the loss
+    "loss_square": ("double dp = P[i] - Ps[i], dq = Q[i] - Qs[i];\n        L += wP[i] * dp * dp + wQ[i] * dq * dq;",
+                    "double dp = P[i] - Ps[i], dq = Q[i] - Qs[i];\n        L += wP[i] * dp + wQ[i] * dq * dq;"),
 }
 
 
@@ -48,11 +55,13 @@ def _all_pins():
         "ew_eq_ybus_3": pins.pin_elementwise_equals_ybus(three_bus_plus()),
         "branch_loss": pins.pin_branch_loss(),
         "adjoint": pins.pin_adjoint(60, 80, 7),
+        "loss_closed": pins.pin_loss_closed_form(),
+        "loss_fd": pins.pin_loss_central_difference(60, 80, 7),
     }
     return errs
 
 
-LIMITS = {"two_bus": 1e-14, "branch_loss": 1e-12, "adjoint": 1e-8}
+LIMITS = {"two_bus": 1e-14, "branch_loss": 1e-12, "adjoint": 1e-8, "loss_closed": 1e-14, "loss_fd": 1e-6}
 
 
 def test_unmutated_oracle_passes_all_pins():

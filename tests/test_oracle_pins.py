@@ -165,6 +165,50 @@ def _loss_case(nb=150, nl=210, seed=7):
     return gr, Y, vm, va, Ps, Qs, wP, wQ
 
 
+def pin_loss_closed_form():
+    """The mismatch loss L = sum_i wP_i (P_i - Ps_i)^2 + wQ_i (Q_i - Qs_i)^2 on the
+    lossless two-bus line of pin_two_bus, from its closed-form injections
+    (P1 = -P2 = 10 sin 0.1, Q1 = Q2 = 10 (1 - cos 0.1)) with targets and weights
+    chosen so that every term differs (wP != wQ on each bus): a swapped weight,
+    a dropped square or a sign error changes the value."""
+    s, c = math.sin(0.1), math.cos(0.1)
+    P = (10 * s, -10 * s)
+    Q = (10 * (1 - c), 10 * (1 - c))
+    Ps, Qs = (0.3, -0.7), (0.1, 0.2)
+    wP, wQ = (1.5, 0.25), (0.75, 3.0)
+    ref = sum(wP[i] * (P[i] - Ps[i]) ** 2 + wQ[i] * (Q[i] - Qs[i]) ** 2 for i in range(2))
+    gr = two_bus_lossless()
+    Y = oracle.ybus(gr)
+    Po, Qo = oracle.inj_sparse(Y, np.array([1.0, 1.0]), np.array([0.0, -0.1]))
+    L = oracle.loss(Po, Qo, np.array(Ps), np.array(Qs), np.array(wP), np.array(wQ))
+    return abs(L - ref) / ref
+
+
+def pin_loss_central_difference(nb=150, nl=210, seed=7, ncoord=24):
+    """Central differences of oracle.loss over perturbed states (h = 1e-6, the
+    injections from oracle.inj_sparse) against the long-double central
+    differences of or_loss_central_diff, which evaluates the loss from the
+    branch list without any oracle routine: a loss with a wrong weight, a
+    dropped square or a missing bus has the wrong slope."""
+    gr, Y, vm, va, Ps, Qs, wP, wQ = _loss_case(nb, nl, seed)
+    rng = np.random.default_rng(seed + 1)
+    kinds = rng.integers(0, 2, ncoord)
+    idxs = rng.integers(0, nb, ncoord)
+    h = 1e-6
+    fd = oracle.loss_central_diff(gr, vm, va, Ps, Qs, wP, wQ, kinds, idxs, h)
+    errs = []
+    for c in range(ncoord):
+        vals = []
+        for sgn in (1.0, -1.0):
+            vm2, va2 = vm.copy(), va.copy()
+            (va2 if kinds[c] == 0 else vm2)[idxs[c]] += sgn * h
+            P, Q = oracle.inj_sparse(Y, vm2, va2)
+            vals.append(oracle.loss(P, Q, Ps, Qs, wP, wQ))
+        d = (vals[0] - vals[1]) / (2 * h)
+        errs.append(abs(d - fd[c]) / max(abs(fd).max(), 1e-300))
+    return max(errs)
+
+
 def pin_adjoint(nb=150, nl=210, seed=7):
     """J^T r and the complex-step parameter gradients against long-double
     central differences (h = 1e-7) of the loss."""
@@ -265,6 +309,14 @@ def test_dense_equals_sparse():
 
 def test_branch_loss_identity():
     assert pin_branch_loss() < 1e-12
+
+
+def test_loss_closed_form():
+    assert pin_loss_closed_form() < 1e-14
+
+
+def test_loss_slope_against_central_differences():
+    assert pin_loss_central_difference() < 1e-6
 
 
 def test_adjoint_against_central_differences():
