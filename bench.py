@@ -37,7 +37,7 @@ HBM_FALLBACK_GBS = 6800.0
 # FP64 arithmetic instructions per unit of the element-wise Jacobian kernel
 WORKLOAD_NAME = "synthetic grid, 70,000 buses / 88,000 branches, one voltage state"
 EW_OPS_PER_TERMINAL = 12   # E = V_o conj(U_q) 4, G = conj(Yc) E 4, K = v_q G 2, sum K 2
-EW_OPS_PER_BUS = 31        # fused phasor (sincos 15, 1/v 4, V 2) + diagonal entries and S (10)
+EW_OPS_PER_BUS = 16        # fused phasor (1/v 4, V 2; sin/cos on the integer pipe) + diagonal entries and S (10)
 YB_OPS_PER_NNZ = 16
 YB_OPS_PER_ROW = 16
 # DRAM bytes of one k_ew<1> launch on the 70k-bus grid (dram__bytes_read.sum + dram__bytes_write.sum

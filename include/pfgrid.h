@@ -211,11 +211,13 @@ pf_status eval_host_async(pf_grid *grid, int32_t method, const double *vm, const
  * The phasor step alone (Sec. IV-B.1 step 1), as run at the start of every
  * evaluation: for i < n, U[4i..4i+3] = {cos va_i, sin va_i, vm_i, 1/vm_i} and
  * V[2i..2i+1] = vm_i (cos va_i, sin va_i).  Device pointers; U 32-byte and V
- * 16-byte aligned (PF_EINVAL otherwise).  sin/cos by a table-driven method
- * with Cody-Waite reduction (a few ulp; the library sincos for |va| >= 2^16),
+ * 16-byte aligned (PF_EINVAL otherwise).  sin/cos in fixed-point integer
+ * arithmetic (exact reduction to turns, a 64-entry table, Taylor polynomials;
+ * absolute error within 2 ulp of 1; the library sincos for |va| >= 2^16),
  * 1/vm by two Newton steps from the hardware approximation (vm must be a
- * normal, nonzero number).  The first call on a device fills a 4 KB constant
- * table and synchronizes; make it before any stream capture.
+ * normal, nonzero number).  The first use of the library on a device uploads
+ * a 64 KB constant table and synchronizes (ybus_build does it); make it before
+ * any stream capture.
  */
 pf_status phasor(int32_t n, const double *vm, const double *va, double *U, double *V, pf_stream stream);
 

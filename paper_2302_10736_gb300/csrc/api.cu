@@ -181,7 +181,7 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
 static pf_status ew_fits(const HostEw &E, size_t *smem)
 {
     const EwSmem plan = ew_smem_plan(E.max_nbus, E.max_nt, E.max_L, true, E.max_nph);
-    *smem = plan.total + kTrigN * sizeof(double2);
+    *smem = plan.total + kTrigSmem;
     if (*smem > kMaxSmem)
         return set_error(PF_EUNSUPPORTED, "an element-wise window needs %u bytes of shared memory (max %u): a bus "
                                           "has too many branches for this library", (unsigned)*smem, kMaxSmem);

@@ -72,7 +72,7 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
         return set_error(PF_ECUDA, "batch_create: cannot query the device");
     }
     auto smem_of = [](const HostEw &L) {
-        return ew_smem_plan(L.max_nbus, L.max_nt, L.max_L, true).total + kTrigN * sizeof(double2);
+        return ew_smem_plan(L.max_nbus, L.max_nt, L.max_L, true).total + kTrigSmem;
     };
     const size_t kCtaReserve = 1024;   // shared memory the runtime keeps per resident CTA
     HostEw E;

@@ -48,7 +48,8 @@ struct BatchArgs {
     const int2 *tloc, *brl;
     const int4 *desc;
     const int2 *tnbr;
-    const double2 *yd, *tself, *tcoup, *trig;
+    const double2 *yd, *tself, *tcoup;
+    const ITrig *trig;
     const ScenOut *sc;
     const long long *joff;
     const double *vm, *va;
@@ -78,7 +79,7 @@ __device__ __forceinline__ void store_range_ll(double *x, const double *s, long 
 
 // phase 1: phasors of every scenario, in chunks of blockDim.x consecutive
 // buses so that every lane has a bus
-__device__ __forceinline__ void batch_phasors(const BatchArgs &a, const double2 *tab, bool needU)
+__device__ __forceinline__ void batch_phasors(const BatchArgs &a, const ITrig *tab, bool needU)
 {
     const int tid = threadIdx.x, TB = blockDim.x;
     const int nchunk = (a.nb + TB - 1) / TB;
@@ -89,7 +90,7 @@ __device__ __forceinline__ void batch_phasors(const BatchArgs &a, const double2 
         if (o < a.nb) {
             const long long x = (long long)s * a.nb + o;
             double sn, cs;
-            fast_sincos(a.va[x], tab, &sn, &cs);
+            int_sincos(a.va[x], tab, &sn, &cs);
             const double v = a.vm[x];
             if (needU) a.U[x] = make_double4_32a(cs, sn, v, fast_rcp(v));
             a.V[x] = make_double2(v * cs, v * sn);
@@ -136,10 +137,10 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
     int *skp = reinterpret_cast<int *>(smem + sp.kp);
     double *jst = reinterpret_cast<double *>(smem + sp.jst);
     double *spq = reinterpret_cast<double *>(smem + sp.pq);
-    double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
+    ITrig *tab = reinterpret_cast<ITrig *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x;
-    const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
-    for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
+    const ITrig *trig = a.trig + (blockIdx.x % kITrigCopies) * kITrigN;
+    for (int k = tid; k < kITrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
     batch_phasors(a, tab, JAC);
     if (!grid_barrier(gbar, a.bar, gridDim.x, 0, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
@@ -419,10 +420,10 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
     double2 *skg = reinterpret_cast<double2 *>(smem + sp.kg);
     double *spq = reinterpret_cast<double *>(smem + sp.pq);
-    double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
+    ITrig *tab = reinterpret_cast<ITrig *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x;
-    const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
-    for (int k = tid; k < kTrigN; k += TB) tab[k] = trig[k];
+    const ITrig *trig = a.trig + (blockIdx.x % kITrigCopies) * kITrigN;
+    for (int k = tid; k < kITrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
     // every scenario's phasors first, visible to all CTAs after the barrier
     batch_phasors(a, tab, true);
@@ -583,7 +584,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
     double2 *sR = reinterpret_cast<double2 *>(smem + sp.R);
     double2 *sW = reinterpret_cast<double2 *>(smem + sp.W);   // own buses: (v, 1/v)
     int *sslot = reinterpret_cast<int *>(smem + sp.slot);
-    double2 *tab = reinterpret_cast<double2 *>(smem + sp.tab);
+    ITrig *tab = reinterpret_cast<ITrig *>(smem + sp.tab);
     const int tid = threadIdx.x, TB = blockDim.x;
     const bool has = (long long)blockIdx.x < (long long)a.S * a.nwin;   // CTA-uniform
     int s = 0, w = 0, b0 = 0, nbus = 0, t0 = 0, nt = 0, nph = 0;
@@ -617,10 +618,9 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         // with the first level: behind the second-level gathers it would
         // arrive last, and the barrier before the phasors waits for it.
         const int o0 = tid < a.max_nph ? sbus[tid] : 0;
-        const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
-        double2 tv0 = make_double2(0.0, 0.0), tv1 = tv0;
-        if (tid < kTrigN) tv0 = trig[tid];
-        if (tid + TB < kTrigN) tv1 = trig[tid + TB];
+        const ITrig *trig = a.trig + (blockIdx.x % kITrigCopies) * kITrigN;
+        ITrig tv0 = {0ull, 0ull};
+        if (tid < kITrigN) tv0 = trig[tid];
         double2 yc0 = make_double2(0.0, 0.0), ym0 = make_double2(0.0, 0.0);
         int2 loc0 = make_int2(0, 0);
         int tm0 = 0;
@@ -639,9 +639,8 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             th0 = a.va[sb + o0];
             v0 = a.vm[sb + o0];
         }
-        if (tid < kTrigN) tab[tid] = tv0;
-        if (tid + TB < kTrigN) tab[tid + TB] = tv1;
-        for (int k = tid + 2 * TB; k < kTrigN; k += TB) tab[k] = trig[k];
+        if (tid < kITrigN) tab[tid] = tv0;
+        for (int k = tid + TB; k < kITrigN; k += TB) tab[k] = trig[k];
         // nothing before this barrier waits for a second-level load: what
         // depends on one (the bus metadata in shared memory, loads addressed by
         // the reduction order or the mirror terminal) comes after the phasors
@@ -657,7 +656,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             }
             sslot[j] = o;
             double sn, cs;
-            fast_sincos(th, tab, &sn, &cs);
+            int_sincos(th, tab, &sn, &cs);
             const double2 V = make_double2(v * cs, v * sn);
             sV[j] = V;
             if (j < nbus) {
@@ -943,7 +942,7 @@ cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double
     a.J = J;
     a.aligned = (!J || al16(J)) && (!P || (al16(P) && al16(Q)));
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, jac ? a.max_L : 0, jac);
-    const size_t smem = sp.total + kTrigN * sizeof(double2);
+    const size_t smem = sp.total + kTrigSmem;
     const long long items = (long long)b->S * b->nwin;
     if (jac) return coop_launch(k_ewb<true>, b->resident[1], b->tb, smem, items, s, a);
     return coop_launch(k_ewb<false>, b->resident[0], b->tb, smem, items, s, a);
@@ -979,7 +978,7 @@ cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const d
             return coop_launch(k_adj1, b->resident[3], kAdj1Threads, smem,
                                std::max<long long>(items, (g->nl + kAdj1Threads - 1) / kAdj1Threads), s, a);
     }
-    const size_t smem = ew_smem_plan(a.max_nbus, a.max_nt, 0, false).total + kTrigN * sizeof(double2);
+    const size_t smem = ew_smem_plan(a.max_nbus, a.max_nt, 0, false).total + kTrigSmem;
     return coop_launch(k_adj, b->resident[2], b->tb, smem,
                        std::max<long long>(items, (g->nl + b->tb - 1) / b->tb), s, a);
 }

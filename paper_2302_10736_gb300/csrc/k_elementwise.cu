@@ -59,7 +59,8 @@ struct EwArgs {
     int nnz, nwin, max_nbus, max_nt, max_L, max_nph, aligned;
     const int4 *desc, *bmeta;
     const int *slotbus, *town, *rorder;
-    const double2 *yd, *tcoup, *trig;
+    const double2 *yd, *tcoup;
+    const ITrig *trig;
     const int2 *tloc;
     const double *vm, *va;
     double *P, *Q, *J;
@@ -105,7 +106,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
     double2 *sW = sU + a.max_nph;                                            // (v, 1/v)
     double2 *sW2 = reinterpret_cast<double2 *>(smem + sp.w2);               // own buses: (v^2, 2 v)
     int *sord = reinterpret_cast<int *>(smem + sp.ord);                     // reduction thread -> bus
-    double2 *tab = reinterpret_cast<double2 *>(smem + sp.total);
+    ITrig *tab = reinterpret_cast<ITrig *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x;
     for (int w = blockIdx.x; w < a.nwin; w += gridDim.x) {
         if (PERSIST) __syncthreads();   // the previous window's shared-memory readers are done
@@ -118,12 +119,9 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         // the second-level gathers it would arrive at the end of the kernel's
         // whole input burst, and every warp waits for it at the barrier below
         const bool load_tab = !PERSIST || w == (int)blockIdx.x;
-        const double2 *trig = a.trig + (blockIdx.x % kTrigCopies) * kTrigN;
-        double2 tv0 = make_double2(0.0, 0.0), tv1 = tv0;
-        if (load_tab) {
-            if (tid < kTrigN) tv0 = trig[tid];
-            if (tid + TB < kTrigN) tv1 = trig[tid + TB];
-        }
+        const ITrig *trig = a.trig + (blockIdx.x % kITrigCopies) * kITrigN;
+        ITrig tv0 = {0ull, 0ull};
+        if (load_tab && tid < kITrigN) tv0 = trig[tid];
         const int b0 = d0.x, nbus = d0.y, b1 = b0 + nbus, t0 = d0.z, nt = d0.w;
         const int r0 = d1.x, L = JAC ? d1.y : 0, nph = d1.z;
 
@@ -154,9 +152,8 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                                      // barrier below may wait for a second-level load
         }
         if (load_tab) {
-            if (tid < kTrigN) tab[tid] = tv0;
-            if (tid + TB < kTrigN) tab[tid + TB] = tv1;
-            for (int k = tid + 2 * TB; k < kTrigN; k += TB) tab[k] = trig[k];
+            if (tid < kITrigN) tab[tid] = tv0;
+            for (int k = tid + TB; k < kITrigN; k += TB) tab[k] = trig[k];
         }
         __syncthreads();
 
@@ -168,7 +165,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                 v = a.vm[o];
             }
             double s, c;
-            fast_sincos(th, tab, &s, &c);
+            int_sincos(th, tab, &s, &c);
             if (JAC) {
                 sU[j] = make_double2(c, s);
                 // V and 1/v are read for the window's own buses only: warps of
@@ -393,7 +390,7 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     if (L.nwin == 0) return cudaSuccess;
     const int max_nph = L.max_nph;
     const EwSmem sp = ew_smem_plan(L.max_nbus, L.max_nt, JAC ? L.max_L : 0, JAC, max_nph);
-    const uint32_t smem = sp.total + kTrigN * (uint32_t)sizeof(double2);
+    const uint32_t smem = sp.total + kTrigSmem;
     // outputs in host memory: persistent CTAs (kEwHostCtasPerSm per SM) loop
     // over the windows, so the host link carries the first windows' outputs
     // while the later ones are evaluated

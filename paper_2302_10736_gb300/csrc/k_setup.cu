@@ -12,8 +12,10 @@
 // and the diagonal is the bus shunt plus the self constants of all terminals
 // of bus i, summed in a fixed order (no atomics).
 #include <mutex>
+#include <vector>
 
 #include "fastmath.cuh"
+#include "isincos.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
 
@@ -86,44 +88,38 @@ __global__ void k_bus_yd(int nb, const int *__restrict__ tp, const double2 *__re
     yd[i] = acc;
 }
 
-__device__ double2 g_trig_tab[kTrigCopies * kTrigN];
-
-// (cos, sin)(2 pi k / 256) by the library's sincospi (exact argument k / 128),
-// copy blockIdx.x of the table
-__global__ void k_trig_table_init()
-{
-    const int k = threadIdx.x;
-    double s, c;
-    sincospi(2.0 * k / kTrigN, &s, &c);
-    g_trig_tab[blockIdx.x * kTrigN + k] = make_double2(c, s);
-}
+// kITrigCopies copies of the first-quadrant (cos, sin) table of isincos.cuh:
+// every CTA copies one into shared memory at its start, and the copies spread
+// those reads over many L2 lines
+__device__ ITrig g_itrig_tab[kITrigCopies * kITrigN];
 
 // Phasor step (Sec. IV-B.1 step 1): U = e^{j theta} with v and 1/v (gathered
 // by the Jacobian kernels) and V = v U (gathered by the injection kernels and
-// by the element-wise Jacobian for the owner bus).  22 FP64 instructions per
-// bus (fast_sincos 15, fast_rcp 4 + the hardware approximation, V 2).
-__global__ void __launch_bounds__(kTrigN) k_phasor(int nb, const double *__restrict__ vm,
-                                                   const double *__restrict__ va, double4_32a *__restrict__ U,
-                                                   double2 *__restrict__ V)
+// by the element-wise Jacobian for the owner bus).  The sine and cosine run on
+// the integer pipe (isincos.cuh); 6 FP64 instructions per bus (fast_rcp 4 +
+// the hardware approximation, V 2).
+__global__ void __launch_bounds__(256) k_phasor(int nb, const double *__restrict__ vm,
+                                                const double *__restrict__ va, double4_32a *__restrict__ U,
+                                                double2 *__restrict__ V)
 {
-    __shared__ double2 tab[kTrigN];
+    __shared__ ITrig tab[kITrigN];
     pdl_launch_dependents();   // the evaluation kernel may start loading its static data now
-    tab[threadIdx.x] = g_trig_tab[(blockIdx.x % kTrigCopies) * kTrigN + threadIdx.x];
+    if (threadIdx.x < kITrigN) tab[threadIdx.x] = g_itrig_tab[(blockIdx.x % kITrigCopies) * kITrigN + threadIdx.x];
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     double s, c;
-    fast_sincos(va[i], tab, &s, &c);
+    int_sincos(va[i], tab, &s, &c);
     const double v = vm[i];
     U[i] = make_double4_32a(c, s, v, fast_rcp(v));
     V[i] = make_double2(v * c, v * s);
 }
 
-// Fill the trig table once per device (synchronous, first use only).
+// Upload the trig table once per device (synchronous, first use only).
 static std::mutex g_trig_mu;
-static const double2 *g_trig_ptr[256] = {nullptr};
+static const ITrig *g_trig_ptr[256] = {nullptr};
 
-const double2 *trig_table()
+const ITrig *trig_table()
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
@@ -133,21 +129,19 @@ const double2 *trig_table()
 
 cudaError_t ensure_trig_table()
 {
-    static std::mutex &mu = g_trig_mu;
-    static bool done[256] = {false};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(mu);
-    if (done[dev]) return cudaSuccess;
-    k_trig_table_init<<<kTrigCopies, kTrigN>>>();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_trig_mu);
+    if (g_trig_ptr[dev]) return cudaSuccess;
+    std::vector<ITrig> copies((size_t)kITrigCopies * kITrigN);
+    for (int c = 0; c < kITrigCopies; ++c)
+        for (int j = 0; j < kITrigN; ++j) copies[(size_t)c * kITrigN + j] = kITrigTable[j];
+    if ((e = cudaMemcpyToSymbol(g_itrig_tab, copies.data(), copies.size() * sizeof(ITrig))) != cudaSuccess) return e;
     void *p = nullptr;
-    if ((e = cudaGetSymbolAddress(&p, g_trig_tab)) != cudaSuccess) return e;
-    g_trig_ptr[dev] = static_cast<const double2 *>(p);
-    done[dev] = true;
+    if ((e = cudaGetSymbolAddress(&p, g_itrig_tab)) != cudaSuccess) return e;
+    g_trig_ptr[dev] = static_cast<const ITrig *>(p);
     return cudaSuccess;
 }
 
@@ -172,7 +166,7 @@ cudaError_t launch_ybus_values(Grid *g, const double *gs, const double *bs, cuda
 
 cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32a *U, double2 *V, cudaStream_t s)
 {
-    if (nb > 0) k_phasor<<<nblk(nb, kTrigN), kTrigN, 0, s>>>(nb, vm, va, U, V);
+    if (nb > 0) k_phasor<<<nblk(nb, 256), 256, 0, s>>>(nb, vm, va, U, V);
     return cudaGetLastError();
 }
 

@@ -139,17 +139,17 @@ __global__ void __launch_bounds__(256) k_ts_atomic(int T, int nnz, const int *__
 // V = v e^{j theta} as interleaved pairs (SEP = false) or separate arrays
 template <bool SEP>
 __global__ void __launch_bounds__(256) k_vs_phasor(int nb, const double *__restrict__ vm,
-                                                   const double *__restrict__ va, const double2 *__restrict__ trig,
+                                                   const double *__restrict__ va, const ITrig *__restrict__ trig,
                                                    double *__restrict__ V)
 {
-    __shared__ double2 tab[kTrigN];
-    for (int k = threadIdx.x; k < kTrigN; k += blockDim.x)
-        tab[k] = trig[(blockIdx.x % kTrigCopies) * kTrigN + k];
+    __shared__ ITrig tab[kITrigN];
+    for (int k = threadIdx.x; k < kITrigN; k += blockDim.x)
+        tab[k] = trig[(blockIdx.x % kITrigCopies) * kITrigN + k];
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     double s, c;
-    fast_sincos(va[i], tab, &s, &c);
+    int_sincos(va[i], tab, &s, &c);
     const double v = vm[i];
     if (SEP) {
         V[i] = v * c;

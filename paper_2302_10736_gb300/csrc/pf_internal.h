@@ -8,6 +8,7 @@
 #include <atomic>
 #include <vector>
 
+#include "isincos.cuh"
 #include "pfgrid.h"
 
 #define PF_API extern "C" __attribute__((visibility("default")))
@@ -175,6 +176,8 @@ __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max
     return p;
 }
 constexpr uint32_t kMaxSmem = 227u * 1024u;
+// shared memory of the (cos, sin) table every phasor-forming CTA holds
+constexpr uint32_t kTrigSmem = kITrigN * (uint32_t)sizeof(ITrig);
 // words of the batched kernels' grid-barrier state: parity, two counters on their own lines
 constexpr int kBarWords = 96;
 
@@ -202,7 +205,7 @@ __host__ __device__ inline Adj1Smem adj1_smem_plan(int max_nbus, int max_nt, int
     p.W = p.R + 16u * nph;
     p.slot = p.W + 16u * nbus;
     p.tab = p.slot + ((4u * nph + 15u) & ~15u);
-    p.total = p.tab + 16u * 256u;
+    p.total = p.tab + kTrigSmem;
     return p;
 }
 // threads per CTA of k_adj1
@@ -329,7 +332,7 @@ cudaError_t launch_branch_constants(Grid *g, const double *gg, const double *gb,
                                     const double *gtap, const double *gshift, cudaStream_t s);
 cudaError_t launch_ybus_values(Grid *g, const double *gs, const double *bs, cudaStream_t s);
 cudaError_t ensure_trig_table();   // once per device, synchronous
-const double2 *trig_table();       // device address of the (cos, sin) table of fastmath.cuh
+const ITrig *trig_table();         // device address of the (cos, sin) table of isincos.cuh
 cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32a *U, double2 *V, cudaStream_t s);
 cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ybus(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s);
