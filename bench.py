@@ -33,6 +33,14 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 pipe peak derived from the nominal FP64 rate: 152 SMs x 2 FP64 ops/clk x 2.07 GHz
 # (= 1.26 TFLOP/s counting an FMA as 2 flops, the nominal 1.25 TFLOP/s)
 FP64_OPS_PEAK_G = 152 * 2 * 2.070
+# the measured FP64 FMA rate of this run (measure_fp64_peak), once known
+_FP64_MEASURED = {"g": None}
+
+
+def fp64_peak_g():
+    """The FP64 roof the fractions below are taken against: the rate measured
+    in this run if there is one, else the nominal one."""
+    return _FP64_MEASURED["g"] or FP64_OPS_PEAK_G
 HBM_FALLBACK_GBS = 6800.0
 # FP64 arithmetic instructions per unit of the element-wise Jacobian kernel
 WORKLOAD_NAME = "synthetic grid, 70,000 buses / 88,000 branches, one voltage state"
@@ -56,6 +64,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and adjoint workloads")
+    ap.add_argument("--phase-probe", action="store_true",
+                    help="time the phases of the headline kernel with the phase-probe build of the library and exit")
+    ap.add_argument("--phase-probe-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-workload",
                     choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra", "newton", "sweep",
                              "study", "target"],
@@ -153,6 +164,66 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def phase_probe(args):
+    """Builds the library with the phase probe compiled in and runs the
+    headline kernel with it in a child process (PFGRID_LIB names the probe
+    build there; the default library is never instrumented)."""
+    from paper_2302_10736_gb300 import _build
+    lib = _build.build_pfgrid(phase_probe=True)
+    env = dict(os.environ, PFGRID_LIB=lib)
+    cmd = [sys.executable, os.path.abspath(__file__), "--phase-probe-child", "--steps", str(args.steps),
+           "--warmup", str(args.warmup)]
+    return subprocess.call(cmd, env=env)
+
+
+def phase_probe_child(args):
+    """Per-phase times of k_ew<1> on the 70k-bus grid (L2 flushed before every
+    launch, as in the timed loop): medians over windows and launches of each
+    phase, the spread of CTA start and end times, and the per-SM end spread."""
+    import torch
+
+    from paper_2302_10736_gb300 import pfgrid, synth
+    w = synth.workload(WORKLOAD)
+    grid = pfgrid.ybus_build(w)
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    vm, va = dev(w["vm"][0]), dev(w["va"][0])
+    P = torch.empty(w["nb"], dtype=torch.float64, device="cuda")
+    Q = torch.empty_like(P)
+    J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+    flush = L2Flush(torch)
+    names = ["loads", "phasors", "evaluation", "reduction", "stores"]
+    per = {n: [] for n in names}
+    span, end_med, start_spread, sm_end_spread, ev_us = [], [], [], [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(max(args.warmup, 3) + args.steps):
+        flush.fill_(float(k))
+        e0.record()
+        pfgrid.jac_elementwise(grid, vm, va, P, Q, J)
+        e1.record()
+        torch.cuda.synchronize()
+        if k < max(args.warmup, 3):
+            continue
+        ev_us.append(1e3 * e0.elapsed_time(e1))
+        r = pfgrid.phase_probe_read().astype(np.float64)
+        r = r[r[:, 1] > 0]
+        gt0, gt1, sm, cyc = r[:, 0], r[:, 1], r[:, 2].astype(int), r[:, 3:8]
+        ns_per_cycle = np.median((gt1 - gt0) / np.maximum(cyc[:, 4], 1))
+        d = np.diff(np.concatenate([np.zeros((len(r), 1)), cyc], axis=1), axis=1) * ns_per_cycle / 1e3
+        for i, n in enumerate(names):
+            per[n].append(float(np.median(d[:, i])))
+        t0 = gt0.min()
+        span.append((gt1.max() - t0) / 1e3)
+        end_med.append(float(np.median(gt1 - t0)) / 1e3)
+        start_spread.append((gt0.max() - t0) / 1e3)
+        sm_end = np.array([gt1[sm == m].max() for m in np.unique(sm)])
+        sm_end_spread.append((sm_end.max() - sm_end.min()) / 1e3)
+    med = lambda x: float(np.median(x))
+    print(json.dumps({"kernel": "k_ew<1>", "workload": WORKLOAD_NAME, "launches": args.steps,
+                      "event_us": med(ev_us), "cta_span_us": med(span), "cta_end_median_us": med(end_med),
+                      "cta_start_spread_us": med(start_spread), "sm_end_spread_us": med(sm_end_spread),
+                      "phase_median_us": {n: med(v) for n, v in per.items()}}), flush=True)
+
+
 def job_throughput(torch, ms_local, world, dist, device):
     """(step time, whole-job evals/s) of `world` replicas that each evaluate
     one grid per step: the job's step time is the slowest rank's."""
@@ -196,6 +267,53 @@ def time_loop(torch, fn, steps, flush, name):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+
+
+# copies of the headline grid evaluated in turn in the timed stream (16 x 19 MB
+# of grid structure, state and outputs: above the 129 MB L2)
+STREAM_COPIES = 16
+
+
+def grid_bytes(grid):
+    """Device bytes a grid's evaluation reads besides the state: Ybus CSR,
+    terminal constants and index records (an estimate for the config line)."""
+    return 4 * (grid.nb + 1) + 20 * grid.nnz + 60 * grid.nl + 60 * grid.nb
+
+
+def stream_loop(torch, fn_k, steps, name):
+    """fn_k(k) for k = 0 .. steps-1 back to back on the current stream between
+    one pair of CUDA events; mean ms per step."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push(name)
+    e0.record()
+    for k in range(steps):
+        fn_k(k)
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def measure_fp64_peak(torch, pfgrid, ctas_per_sm=8, iters=2048):
+    """FP64 FMA rate of this GPU from the library's probe kernel (best of 5
+    launches, CUDA events): 8 CTAs of 256 threads per SM, 8 independent chains
+    per thread."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    ctas = ctas_per_sm * nsm
+    pfgrid.fp64_peak_probe(ctas, 64, sink)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(5):
+        e0.record()
+        n = pfgrid.fp64_peak_probe(ctas, iters, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    g = n / (best * 1e-3) / 1e9
+    return {"gdfma_per_s": g, "per_sm_per_clock_at_max": g * 1e9 / nsm / 2.07e9, "ms": best, "dfma": n,
+            "ctas": ctas, "source": "fp64_peak_probe"}
 
 
 def graph_of(torch, fn):
@@ -384,7 +502,7 @@ def _single_workload(torch, pfgrid, synth, k, steps):
         res["%s_evals_per_s" % name] = 1e3 / (sum(t) / len(t))
     T, nb = 2 * w["nl"], w["nb"]
     ms = 1e3 / res["elementwise_evals_per_s"]
-    res["elementwise_fp64_frac"] = (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb) / (ms * 1e-3) / 1e9 / FP64_OPS_PEAK_G
+    res["elementwise_fp64_frac"] = (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb) / (ms * 1e-3) / 1e9 / fp64_peak_g()
     pfgrid.grid_check_error(grid)
     return res
 
@@ -510,7 +628,7 @@ def _n1_workload(torch, pfgrid, synth, reps):
     byt = S * (16 * nb + 16 * nb) + 8 * batch.nnzJ_total + 40 * T + 84 * nb
     out["n1_batch_10k_x1024"] = {
         "evals_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
-        "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / FP64_OPS_PEAK_G,
+        "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / fp64_peak_g(),
         "hbm_gbs": byt / (ms * 1e-3) / 1e9, "jacobian_values": batch.nnzJ_total}
     # the same batch by the Ybus method (phasor launch + row launch)
     g2 = graph_of(torch, lambda: pfgrid.jac_ybus_batched(batch, vm, va, P, Q, J))
@@ -547,9 +665,9 @@ def _adjoint_workload(torch, pfgrid, synth, reps, k):
     gp = [torch.empty(nl, dtype=torch.float64, device="cuda") for _ in range(4)]
     g = graph_of(torch, lambda: pfgrid.adjoint_elementwise(batch, vm, va, Ps, Qs, wP, wQ, L, gvm, gva, *gp))
     ms = timed_replays(torch, g, reps, "adjoint%d" % k)
-    ops = S * ((21 + 8 + 8) * nb + (10 + 22) * T + 48 * nl)
+    ops = S * ((6 + 8 + 8) * nb + (10 + 22) * T + 48 * nl)   # phasor 1/v and V (sin/cos on the integer pipe)
     res = {"loss_and_gradients_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
-           "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / FP64_OPS_PEAK_G}
+           "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / fp64_peak_g()}
     if k == 5:
         P = torch.empty(S * nb, dtype=torch.float64, device="cuda")
         Q = torch.empty_like(P)
@@ -558,7 +676,7 @@ def _adjoint_workload(torch, pfgrid, synth, reps, k):
         ms2 = timed_replays(torch, g2, reps, "batched5")
         ops2 = S * (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb)
         res.update({"jac_evals_per_s": S / (ms2 * 1e-3), "jac_ms_per_launch": ms2,
-                    "jac_fp64_frac": ops2 / (ms2 * 1e-3) / 1e9 / FP64_OPS_PEAK_G})
+                    "jac_fp64_frac": ops2 / (ms2 * 1e-3) / 1e9 / fp64_peak_g()})
         g4 = graph_of(torch, lambda: pfgrid.jac_ybus_batched(batch, vm, va, P, Q, J))
         res["ybus_batched_jac_evals_per_s"] = S * 1e3 / timed_replays(torch, g4, reps, "ybus_batched5")
         # the plain single-scenario Ybus path on the same grid, for comparison
@@ -575,12 +693,17 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.phase_probe:
+        sys.exit(phase_probe(args))
+    if args.phase_probe_child:
+        return phase_probe_child(args)
     import torch
 
     from paper_2302_10736_gb300 import pfgrid, synth
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if args.profile_workload:
+        _FP64_MEASURED["g"] = measure_fp64_peak(torch, pfgrid)["gdfma_per_s"]
         print(json.dumps(extra_workloads(torch, pfgrid, synth, max(1, args.steps), args.profile_workload)))
         return
     dist = None
@@ -600,14 +723,30 @@ def main():
     flush = L2Flush(torch)
     T = 2 * nl
 
+    # the headline stream: COPIES copies of the grid, each with its own state and
+    # outputs, evaluated in turn, so that every step's grid, state and outputs
+    # were last touched COPIES - 1 steps earlier (working set above L2)
+    copies = [(grid, vm, va, P, Q, J)]
+    for _ in range(STREAM_COPIES - 1):
+        g2 = pfgrid.ybus_build(w)
+        pfgrid.grid_set_config(g2, **cfg)
+        copies.append((g2, dev(w["vm"][0]), dev(w["va"][0]), torch.empty_like(P), torch.empty_like(Q),
+                       torch.empty_like(J)))
+    footprint = STREAM_COPIES * (grid_bytes(grid) + 8 * (4 * nb + grid.nnzJ))
+    ew_k = lambda k: pfgrid.jac_elementwise(*copies[k % STREAM_COPIES])
+    yb_k = lambda k: pfgrid.jac_ybus(*copies[k % STREAM_COPIES])
+
     ew = lambda: pfgrid.jac_elementwise(grid, vm, va, P, Q, J)
     yb = lambda: pfgrid.jac_ybus(grid, vm, va, P, Q, J)
     iew = lambda: pfgrid.inj_elementwise(grid, vm, va, P, Q)
     iyb = lambda: pfgrid.inj_ybus(grid, vm, va, P, Q)
-    for _ in range(max(args.warmup, 3)):
+    for k in range(max(args.warmup, 3)):
         for f in (ew, yb, iew, iyb):
             flush.fill_(0.0)
             f()
+    for k in range(max(args.warmup, 3) * STREAM_COPIES):
+        ew_k(k)
+        yb_k(k)
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     time.sleep(0.3)
@@ -615,15 +754,20 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    ms_stream = stream_loop(torch, ew_k, args.steps, "ew_stream")   # the timed region of the headline
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_stream_yb = stream_loop(torch, yb_k, args.steps, "ybus_stream")
+    # one evaluation at a time: L2 flushed before every step outside the events,
+    # so each step also pays its launch (the latency form)
     t_ew = time_loop(torch, ew, args.steps, flush, "ew")
     t_yb = time_loop(torch, yb, args.steps, flush, "ybus")
     t_iew = time_loop(torch, iew, args.steps, flush, "inj_ew")
     t_iyb = time_loop(torch, iyb, args.steps, flush, "inj_ybus")
-    # the headline step again after a write-only flush (L2 left full of dirty lines)
+    # the latency form again after a write-only flush (L2 left full of dirty lines)
     t_dirty = time_loop(torch, ew, args.steps, L2Flush(torch, read=False), "ew_dirty_l2")
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
     # per-kernel times: the same loops again with the library's launch tracer on
     pfgrid.grid_trace_enable(grid, 8 * args.steps + 64)
     time_loop(torch, ew, args.steps, flush, "traced_ew")
@@ -633,11 +777,15 @@ def main():
     time_loop(torch, iew, args.steps, flush, "traced_inj_ew")
     time_loop(torch, iyb, args.steps, flush, "traced_inj_ybus")
     tr_inj = pfgrid.grid_trace_read(grid)
-    clocks = sampler.stop()
     pfgrid.grid_trace_enable(grid, 0)
-    pfgrid.grid_check_error(grid)
+    # the FP64 roof of this GPU, measured under the same clocks
+    fp64_peak = measure_fp64_peak(torch, pfgrid)
+    _FP64_MEASURED["g"] = fp64_peak["gdfma_per_s"]
+    clocks = sampler.stop()
+    for c in copies:
+        pfgrid.grid_check_error(c[0])
 
-    ms_step, value = job_throughput(torch, sum(t_ew) / len(t_ew), world, dist, "cuda")
+    ms_step, value = job_throughput(torch, ms_stream, world, dist, "cuda")
 
     def kmean(tr, name):
         xs = [ms for k, ms in tr if k == name]
@@ -647,16 +795,21 @@ def main():
     ms_pu, n_pu = kmean(tr_yb, "phasor")   # the Ybus path's separate phasor step
     ms_jyb, _ = kmean(tr_yb, "jac_ybus")
     ops_ew = EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb
-    achieved = ops_ew / (ms_jew * 1e-3) / 1e9
+    # the kernel's average launch duration in the timed stream (one launch per step)
+    achieved = ops_ew / (ms_stream * 1e-3) / 1e9
     hbm, hbm_kind = hbm_peak()
     # algorithmic bytes of an element-wise injection + Jacobian evaluation: branch ends and 5 parameters
     # per branch (48 B), vm, va, shunt and P, Q per bus (48 B), one value per Jacobian slot (32 B per nnzY)
     bytes_ew = 48 * nl + 48 * nb + 32 * grid.nnz
-    roof = {"bound": "alu", "kernel": "k_ew<1>", "achieved": achieved, "peak": FP64_OPS_PEAK_G,
-            "unit": "GFP64op/s", "frac": achieved / FP64_OPS_PEAK_G, "traffic": EW_TRAFFIC_BYTES,
-            "ops_per_launch": ops_ew, "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz",
-            "hbm": {"achieved": bytes_ew / (ms_jew * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                    "frac": bytes_ew / (ms_jew * 1e-3) / 1e9 / hbm, "algorithmic_bytes": bytes_ew,
+    roof = {"bound": "alu", "kernel": "k_ew<1>", "achieved": achieved, "peak": fp64_peak["gdfma_per_s"],
+            "unit": "GFP64op/s", "frac": achieved / fp64_peak["gdfma_per_s"], "traffic": EW_TRAFFIC_BYTES,
+            "ops_per_launch": ops_ew,
+            "peak_source": "measured: fp64_peak_probe (DFMA chains on every SM) in this run",
+            "frac_of_nominal": achieved / FP64_OPS_PEAK_G,
+            "nominal_peak": FP64_OPS_PEAK_G,
+            "nominal_source": "152 SMs x 2 FP64 ops/clk x 2.07 GHz",
+            "hbm": {"achieved": bytes_ew / (ms_stream * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": bytes_ew / (ms_stream * 1e-3) / 1e9 / hbm, "algorithmic_bytes": bytes_ew,
                     "peak_source": hbm_kind}}
 
     # end to end through the C ABI with pinned host buffers
@@ -728,14 +881,19 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "nnzY": grid.nnz, "nnzJ": grid.nnzJ,
                        "global_batch": world, "seq_len": 0, "parallelism": "replicas" if world > 1 else "none",
-                       "l2": "flushed between steps outside the timed events (512 MB written, then 256 MB read, so L2 holds clean lines)",
+                       "l2": "inputs larger than L2: %d copies of the grid with their own states and outputs "
+                             "(%.0f MB) evaluated in turn, %d steps back to back between one pair of CUDA events"
+                             % (STREAM_COPIES, footprint / 1e6, args.steps),
                        "launch_config": cfg},
-            "e2e": e2e, "gpu_launches": len(tr_ew), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": e2e, "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "fp64_peak": fp64_peak,
             "compare": {
-                "elementwise_jac_evals_per_s": 1e3 / ms_step,
-                "ybus_jac_evals_per_s": 1e3 / (sum(t_yb) / len(t_yb)),
-                "elementwise_inj_evals_per_s": 1e3 / (sum(t_iew) / len(t_iew)),
-                "ybus_inj_evals_per_s": 1e3 / (sum(t_iyb) / len(t_iyb)),
+                "elementwise_jac_evals_per_s": 1e3 / ms_stream,
+                "ybus_jac_evals_per_s_stream": 1e3 / ms_stream_yb,
+                "elementwise_jac_evals_per_s_flush_per_step": 1e3 / (sum(t_ew) / len(t_ew)),
+                "ybus_jac_evals_per_s_flush_per_step": 1e3 / (sum(t_yb) / len(t_yb)),
+                "elementwise_inj_evals_per_s_flush_per_step": 1e3 / (sum(t_iew) / len(t_iew)),
+                "ybus_inj_evals_per_s_flush_per_step": 1e3 / (sum(t_iyb) / len(t_iyb)),
                 "elementwise_jac_evals_per_s_after_write_only_flush": 1e3 / (sum(t_dirty) / len(t_dirty)),
                 "kernel_ms": {"phasor": ms_pu, "jac_ew": ms_jew, "jac_ybus": ms_jyb,
                               "inj_ew": kmean(tr_inj, "inj_ew")[0], "inj_ybus": kmean(tr_inj, "inj_ybus")[0]},

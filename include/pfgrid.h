@@ -249,6 +249,30 @@ pf_status phasor(int32_t n, const double *vm, const double *va, double *U, doubl
 pf_status inj_ybus_noalloc(int32_t nb, const int32_t *rowptr, const int32_t *colidx, const double *yval,
                            const double *vm, const double *va, double *P, double *Q, pf_stream stream);
 
+/*
+ * Diagnostics: per-phase timing of the single-evaluation element-wise kernel
+ * (the paper's per-step breakdown, Table VII, measured inside the fused
+ * kernel).  Only a library built with -DPF_PHASE_PROBE records anything (its
+ * kernels then write timestamps; the default build writes none and this call
+ * returns PF_EUNSUPPORTED).  Copies the records of the last launch of
+ * jac_elementwise / inj_elementwise, for windows 0 .. min(max_windows, 8192)-1,
+ * into out (host, 8 words per window): [0] %globaltimer (ns) when the window's
+ * CTA started, [1] when it ended, [2] its SM, [3..7] clock64 cycles from the
+ * start to the end of the load, phasor, evaluation, reduction and store
+ * phases.  *nwin receives the number of windows copied.  Synchronous.
+ */
+pf_status pf_phase_probe_read(uint64_t *out, int32_t max_windows, int32_t *nwin);
+
+/*
+ * Measurement: the device's FP64 fused multiply-add throughput, the
+ * denominator of the FP64 roofline (the method's kernels are bound by the
+ * FP64 pipe on GB300).  Launches `ctas` CTAs of 256 threads, each running 8
+ * independent FMA chains for iters x 16 steps, on `stream`; the caller times
+ * the launch (CUDA events) and divides *dfma_per_launch (may be NULL) by the
+ * time.  sink: any device double (never written in practice).  No allocation.
+ */
+pf_status fp64_peak_probe(int32_t ctas, int32_t iters, double *sink, int64_t *dfma_per_launch, pf_stream stream);
+
 /* Current launch configuration. */
 pf_status grid_get_config(const pf_grid *grid, pf_config *cfg);
 

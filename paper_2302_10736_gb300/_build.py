@@ -14,6 +14,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_PFGRID = os.path.join(PKG, "libpfgrid.so")
+# the same library with the element-wise kernel's phase probe compiled in
+# (-DPF_PHASE_PROBE); never loaded unless PFGRID_LIB names it
+LIB_PFGRID_PROBE = os.path.join(PKG, "libpfgrid_probe.so")
 LIB_SYNTH = os.path.join(PKG, "synth", "libsynth.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
@@ -50,13 +53,17 @@ def pfgrid_sources():
     return srcs, hdrs
 
 
-def build_pfgrid(force=False, verbose=False, extra_flags=()):
-    """Compile every .cu/.cpp under csrc/ for sm_103a and link libpfgrid.so."""
+def build_pfgrid(force=False, verbose=False, extra_flags=(), phase_probe=False):
+    """Compile every .cu/.cpp under csrc/ for sm_103a and link libpfgrid.so
+    (libpfgrid_probe.so with the phase probe compiled in)."""
     srcs, hdrs = pfgrid_sources()
+    lib = LIB_PFGRID_PROBE if phase_probe else LIB_PFGRID
+    if phase_probe:
+        extra_flags = tuple(extra_flags) + ("-DPF_PHASE_PROBE",)
     with _lock:
-        if not force and not _stale(LIB_PFGRID, srcs + hdrs):
-            return LIB_PFGRID
-        objdir = os.path.join(PKG, "_build")
+        if not force and not _stale(lib, srcs + hdrs):
+            return lib
+        objdir = os.path.join(PKG, "_build_probe" if phase_probe else "_build")
         os.makedirs(objdir, exist_ok=True)
         nvcc = _nvcc()
         common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
@@ -79,11 +86,11 @@ def build_pfgrid(force=False, verbose=False, extra_flags=()):
         if errs:
             raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
         lib64 = os.path.join(_cuda_home(), "lib64")
-        tmp = LIB_PFGRID + ".tmp"
+        tmp = lib + ".tmp"
         _run([nvcc, "-shared", "-o", tmp] + objs + ARCH +
              ["-cudart", "shared", "-lcusolver", "-lcusparse", "-Xlinker", "-rpath," + lib64])
-        os.replace(tmp, LIB_PFGRID)
-        return LIB_PFGRID
+        os.replace(tmp, lib)
+        return lib
 
 
 def build_synth(force=False):

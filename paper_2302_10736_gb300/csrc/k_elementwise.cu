@@ -73,6 +73,29 @@ struct EwArgs {
     double *F, *Jr;
 };
 
+#ifdef PF_PHASE_PROBE
+// Phase probe (builds with -DPF_PHASE_PROBE only): thread 0 of every CTA of
+// the single-evaluation kernel records, per window, the %globaltimer at its
+// start and end, its SM, and the clock64 cycles from its start to the end of
+// each phase (loads, phasors, evaluation, reduction, stores).
+constexpr int kProbeMaxWin = 8192, kProbeSlots = 8;
+__device__ unsigned long long g_phase_probe[kProbeMaxWin * kProbeSlots];
+__device__ __forceinline__ unsigned long long probe_gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#define PF_PROBE_MARK(k)                                 \
+    do {                                                 \
+        if (probe && tid == 0) pt[k] = clock64() - pt0;  \
+    } while (0)
+#else
+#define PF_PROBE_MARK(k) \
+    do {                 \
+    } while (0)
+#endif
+
 // Write x[b0 .. b1) from shared staging `s` (element b0 at s[b0 & 1]) to
 // global memory: an unaligned head and tail element by plain stores, the
 // 16-byte aligned middle by one bulk store (issued by the calling thread).
@@ -108,7 +131,17 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
     int *sord = reinterpret_cast<int *>(smem + sp.ord);                     // reduction thread -> bus
     ITrig *tab = reinterpret_cast<ITrig *>(smem + sp.total);
     const int tid = threadIdx.x, TB = blockDim.x;
+    // programmatic dependent launch: the next kernel in the stream may start
+    // its CTAs as these exit (it waits before it reads or writes anything
+    // this kernel may still touch, see below)
+    pdl_launch_dependents();
     for (int w = blockIdx.x; w < a.nwin; w += gridDim.x) {
+#ifdef PF_PHASE_PROBE
+        const bool probe = !PERSIST && !RED && w < kProbeMaxWin;
+        const unsigned long long gt0 = probe && tid == 0 ? probe_gtimer() : 0ull;
+        const long long pt0 = clock64();
+        long long pt[5] = {0, 0, 0, 0, 0};
+#endif
         if (PERSIST) __syncthreads();   // the previous window's shared-memory readers are done
         // two levels of dependent loads: the window's records (descriptor, the
         // bus of the thread's first phasor slot), then everything they index
@@ -125,37 +158,42 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         const int b0 = d0.x, nbus = d0.y, b1 = b0 + nbus, t0 = d0.z, nt = d0.w;
         const int r0 = d1.x, L = JAC ? d1.y : 0, nph = d1.z;
 
-        // ---- loads: voltages of the first table slot, bus metadata, the first
-        // terminal, the sine/cosine table ----
+        // ---- loads of topology data (fixed when the grid's layout is built;
+        // no kernel writes them): the bus thread's metadata (a window has at
+        // most blockDim.x buses), kept in registers until the phasors are done
+        // so its latency hides behind them, and the first terminal's slots ----
+        int4 bmo = make_int4(0, 0, 0, 0);
+        int ordo = 0;
+        if (tid < nbus) {
+            bmo = a.bmeta[b0 + tid];
+            ordo = a.rorder[b0 + tid];
+        }
+        int2 nq = make_int2(0, 0);
+        int ol = 0;
+        if (tid < nt) {
+            nq = a.tloc[t0 + tid];
+            ol = a.town[t0 + tid];   // made window-local at first use: nothing before the
+                                     // barrier below may wait for a second-level load
+        }
+        // ---- the previous kernel in the stream may still run (programmatic
+        // dependent launch): the state, the parameter-dependent constants and
+        // the outputs are read and written only after it has completed ----
+        pdl_wait();
         double th = 0.0, v = 0.0;
         if (tid < nph) {
             th = a.va[o0];
             v = a.vm[o0];
         }
-        // the bus thread's metadata (a window has at most blockDim.x buses), kept
-        // in registers until the phasors are done so its latency hides behind them
-        int4 bmo = make_int4(0, 0, 0, 0);
         double2 ydo = make_double2(0.0, 0.0);
-        int ordo = 0;
-        if (tid < nbus) {
-            bmo = a.bmeta[b0 + tid];
-            ydo = a.yd[b0 + tid];
-            ordo = a.rorder[b0 + tid];
-        }
+        if (tid < nbus) ydo = a.yd[b0 + tid];
         double2 yc = make_double2(0.0, 0.0);
-        int2 nq = make_int2(0, 0);
-        int ol = 0;
-        if (tid < nt) {
-            yc = a.tcoup[t0 + tid];
-            nq = a.tloc[t0 + tid];
-            ol = a.town[t0 + tid];   // made window-local at first use: nothing before the
-                                     // barrier below may wait for a second-level load
-        }
+        if (tid < nt) yc = a.tcoup[t0 + tid];
         if (load_tab) {
             if (tid < kITrigN) tab[tid] = tv0;
             for (int k = tid + TB; k < kITrigN; k += TB) tab[k] = trig[k];
         }
         __syncthreads();
+        PF_PROBE_MARK(0);
 
         // ---- phasor table of the window (Sec. IV-B.1 step 1, own and ghost buses) ----
         for (int j = tid; j < nph; j += TB) {
@@ -190,6 +228,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
             sord[tid] = ordo;
         }
         __syncthreads();
+        PF_PROBE_MARK(1);
 
         // ---- evaluation: one terminal per thread ----
         for (int i = tid; i < nt; i += TB) {
@@ -227,6 +266,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
             }
         }
         __syncthreads();
+        PF_PROBE_MARK(2);
 
         // ---- reduction: its terminals in sorted order onto every bus ----
         const int pqs = (int)sp.pqs, par = b0 & 1;
@@ -321,6 +361,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         } else if (a.aligned) {
             fence_proxy_async_smem();
             __syncthreads();
+            PF_PROBE_MARK(3);
             if (tid == 0) {
                 if (JAC) {
                     bulk_s2g(a.J + 2 * (long long)r0, jst, 8u * (uint32_t)L);
@@ -349,6 +390,18 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                     a.Q[b0 + b] = spq[pqs + b + par];
                 }
         }
+#ifdef PF_PHASE_PROBE
+        if (probe && tid == 0) {
+            pt[4] = clock64() - pt0;
+            unsigned int smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            unsigned long long *o = g_phase_probe + (long long)w * kProbeSlots;
+            o[0] = gt0;
+            o[1] = probe_gtimer();
+            o[2] = smid;
+            for (int k = 0; k < 5; ++k) o[3 + k] = (unsigned long long)pt[k];
+        }
+#endif
         if (!PERSIST) break;
     }
 }
@@ -446,13 +499,14 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
         a.F = F;
         a.Jr = Jr;
     }
-    if (persist)
+    // the device-output kernels are launched as programmatic dependents of
+    // the previous kernel in the stream (their prologue overlaps its end)
+    if (persist) {
         k_ew_host<<<(unsigned)grid, (unsigned)L.tb, smem, s>>>(a);
-    else if (red)
-        k_ew_red<<<(unsigned)grid, (unsigned)L.tb, smem, s>>>(a);
-    else
-        k_ew<JAC><<<(unsigned)grid, (unsigned)L.tb, smem, s>>>(a);
-    return cudaGetLastError();
+        return cudaGetLastError();
+    }
+    if (red) return launch_k(k_ew_red, grid, L.tb, smem, s, true, a);
+    return launch_k(k_ew<JAC>, grid, L.tb, smem, s, true, a);
 }
 
 cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm)
@@ -490,3 +544,21 @@ cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P
 }
 
 }  // namespace pf
+
+PF_API pf_status pf_phase_probe_read(uint64_t *out, int32_t max_windows, int32_t *nwin)
+{
+#ifdef PF_PHASE_PROBE
+    using namespace pf;
+    if (!out || max_windows < 0) return set_error(PF_EINVAL, "pf_phase_probe_read: NULL output or negative size");
+    const int n = max_windows < kProbeMaxWin ? max_windows : kProbeMaxWin;
+    if (n > 0)
+        PF_CUDA(cudaMemcpyFromSymbol(out, g_phase_probe, (size_t)n * kProbeSlots * sizeof(unsigned long long)));
+    if (nwin) *nwin = n;
+    return PF_OK;
+#else
+    (void)out;
+    (void)max_windows;
+    if (nwin) *nwin = 0;
+    return pf::set_error(PF_EUNSUPPORTED, "pf_phase_probe_read: library built without -DPF_PHASE_PROBE");
+#endif
+}

@@ -105,6 +105,9 @@ __global__ void __launch_bounds__(256) k_phasor(int nb, const double *__restrict
     __shared__ ITrig tab[kITrigN];
     pdl_launch_dependents();   // the evaluation kernel may start loading its static data now
     if (threadIdx.x < kITrigN) tab[threadIdx.x] = g_itrig_tab[(blockIdx.x % kITrigCopies) * kITrigN + threadIdx.x];
+    // launched as a programmatic dependent: the previous kernel in the stream
+    // (which may read U and V, or write vm and va) has completed after this
+    pdl_wait();
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
@@ -166,8 +169,8 @@ cudaError_t launch_ybus_values(Grid *g, const double *gs, const double *bs, cuda
 
 cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32a *U, double2 *V, cudaStream_t s)
 {
-    if (nb > 0) k_phasor<<<nblk(nb, 256), 256, 0, s>>>(nb, vm, va, U, V);
-    return cudaGetLastError();
+    if (nb > 0) return launch_k(k_phasor, nblk(nb, 256), 256, 0, s, true, nb, vm, va, U, V);
+    return cudaSuccess;
 }
 
 }  // namespace pf

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict_
                                                    const double2 *__restrict__ Y, const double2 *__restrict__ V,
                                                    double *__restrict__ P, double *__restrict__ Q)
 {
+    pdl_launch_dependents();   // the next evaluation's phasor launch may start (it waits for this grid)
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int row = (int)(gid / W), lane = (int)(gid % W);
     const bool valid = row < nb;
@@ -47,12 +48,14 @@ __global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict_
 #pragma unroll
     for (int j = 0; j < kChunkW<W>; ++j) {
         const int k = lane + W * j;
-        if (k < d) {
-            jj[j] = ci[rs + k];
-            yy[j] = Y[rs + k];
-        }
+        if (k < d) jj[j] = ci[rs + k];
     }
     pdl_wait();
+#pragma unroll
+    for (int j = 0; j < kChunkW<W>; ++j) {
+        const int k = lane + W * j;
+        if (k < d) yy[j] = Y[rs + k];   // parameter-dependent: after the wait
+    }
     double Ir = 0.0, Ii = 0.0;
     for (int k0 = lane; k0 < d; k0 += W * kChunkW<W>) {
         if (k0 != lane) {
@@ -97,6 +100,7 @@ __global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__
                                                    const double4_32a *__restrict__ U, double *__restrict__ P,
                                                    double *__restrict__ Q, double *__restrict__ J)
 {
+    pdl_launch_dependents();   // the next evaluation's phasor launch may start (it waits for this grid)
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int row = (int)(gid / W), lane = (int)(gid % W);
     const bool valid = row < nb;
@@ -110,12 +114,14 @@ __global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__
 #pragma unroll
     for (int j = 0; j < kChunkW<W>; ++j) {
         const int k = lane + W * j;
-        if (k < d) {
-            jj[j] = ci[rs + k];
-            yy[j] = Y[rs + k];
-        }
+        if (k < d) jj[j] = ci[rs + k];
     }
     pdl_wait();
+#pragma unroll
+    for (int j = 0; j < kChunkW<W>; ++j) {
+        const int k = lane + W * j;
+        if (k < d) yy[j] = Y[rs + k];   // parameter-dependent: after the wait
+    }
     double Ir = 0.0, Ii = 0.0;
     double dTr = 0.0, dTi = 0.0, dVr = 0.0, dVi = 0.0;  // diagonal partials (lane that owns it)
     int kd = -1;

@@ -82,14 +82,16 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
 #pragma unroll
     for (int j = 0; j < kChunkBW<W>; ++j) {
         const int k = lane + W * j;
-        if (k < d) {
-            jj[j] = ci[rs + k];
-            yy[j] = Y[rs + k];
-        }
+        if (k < d) jj[j] = ci[rs + k];
+    }
+    pdl_wait();
+#pragma unroll
+    for (int j = 0; j < kChunkBW<W>; ++j) {
+        const int k = lane + W * j;
+        if (k < d) yy[j] = Y[rs + k];   // parameter-dependent (as the outage's constants): after the wait
     }
     RowOutage ro{-1, 0, make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
     if (valid) ro = row_outage(sc[s], i, tself, tcoup);
-    pdl_wait();
     const double2 *Vs = V + (long long)s * nb;
     double Ir = 0.0, Ii = 0.0;
     for (int k0 = lane; k0 < d; k0 += W * kChunkBW<W>) {
@@ -155,16 +157,19 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
 #pragma unroll
     for (int j = 0; j < kChunkBW<W>; ++j) {
         const int k = lane + W * j;
-        if (k < d) {
-            jj[j] = ci[rs + k];
-            yy[j] = Y[rs + k];
-        }
+        if (k < d) jj[j] = ci[rs + k];
     }
     ScenOut o{-1, -1, -1, -1, 0, 0, 0, -1};
     long long jo = 0;
     if (valid) {
         o = sc[s];
         jo = joff[s];
+    }
+    pdl_wait();
+#pragma unroll
+    for (int j = 0; j < kChunkBW<W>; ++j) {
+        const int k = lane + W * j;
+        if (k < d) yy[j] = Y[rs + k];   // parameter-dependent (as the outage's constants): after the wait
     }
     const RowOutage ro = row_outage(o, i, tself, tcoup);
     // scenario s's compacted row: start, length, and its J halves
@@ -173,7 +178,6 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
     const int ds = d - (ro.kx >= 0 ? del : 0);
     const long long nnzs = nnz - 2 * del;
     double *Js = J + jo;
-    pdl_wait();
     const double4_32a *Us = U + (long long)s * nb;
     double Ir = 0.0, Ii = 0.0;
     double dTr = 0.0, dTi = 0.0, dVr = 0.0, dVi = 0.0;   // diagonal partials (lane that owns it)

@@ -13,7 +13,8 @@ import numpy as np
 
 from . import _build
 
-LIB_PATH = _build.LIB_PFGRID
+# PFGRID_LIB may name another build of the same library (the phase-probe build)
+LIB_PATH = os.environ.get("PFGRID_LIB") or _build.LIB_PFGRID
 HEADER = os.path.join(_build.INCLUDE, "pfgrid.h")
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETOPO, PF_EDEVICE, PF_ETIMEOUT, PF_EUNSUPPORTED, PF_ENOCONV = range(9)
@@ -87,6 +88,8 @@ def _load():
                                   vp]),
         "jac_set_target_pattern": (st, [vp, vp, vp, ctypes.c_int64, vp]),
         "jac_target": (st, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "pf_phase_probe_read": (st, [vp, i32, pi32]),
+        "fp64_peak_probe": (st, [i32, i32, vp, ctypes.POINTER(ctypes.c_int64), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -402,6 +405,24 @@ def inj_ybus_study(grid, separate, vm, va, P, Q, stream=None):
     nb = grid.nb
     _check(_lib.inj_ybus_study(grid.handle, int(separate), _dptr(vm, "vm", nb), _dptr(va, "va", nb),
                                _dptr(P, "P", nb), _dptr(Q, "Q", nb), _stream(stream)), "inj_ybus_study")
+
+
+def fp64_peak_probe(ctas, iters, sink, stream=None):
+    """Launch the FP64 FMA throughput kernel; returns the FMAs it executes."""
+    n = ctypes.c_int64()
+    _check(_lib.fp64_peak_probe(int(ctas), int(iters), _dptr(sink, "sink", 1), ctypes.byref(n), _stream(stream)),
+           "fp64_peak_probe")
+    return n.value
+
+
+def phase_probe_read(max_windows=8192):
+    """Per-window phase records of the last single element-wise evaluation
+    (probe builds only): uint64 array [n, 8], see pf_phase_probe_read."""
+    out = np.zeros((max_windows, 8), np.uint64)
+    n = ctypes.c_int32()
+    _check(_lib.pf_phase_probe_read(out.ctypes.data_as(ctypes.c_void_p), int(max_windows), ctypes.byref(n)),
+           "pf_phase_probe_read")
+    return out[:n.value]
 
 
 def debug_fail_allocations(after):
