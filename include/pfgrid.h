@@ -390,20 +390,37 @@ pf_status jac_ybus_batched(pf_batch *batch, const double *vm, const double *va, 
  * Adjoint of the mismatch loss, one cooperative launch (the paper has no
  * adjoint; it differentiates the element-wise flows of Eqs. 5-7):
  *   L_s = sum_i wP_i (P_si - Pspec_i)^2 + wQ_i (Q_si - Qspec_i)^2
- * for every scenario s of the batch (outages honoured), with
+ * for every scenario s of the batch (outages honoured), and the total
+ * L_total = sum_s L_s (ascending s).  With lbar = *Lbar (device scalar; NULL
+ * means 1), the upstream gradient of L_total (an autograd caller passes
+ * dOut/dL_total here, so no caller-side scaling is needed):
  *   L [nscen]            the loss per scenario (may be NULL)
- *   gvm, gva [nscen][nb] dL_s/d|V| and dL_s/dtheta (J^T r without forming J)
- *   gg, gb, gbsh, gtap [nl]  d(sum_s L_s)/d(g, b, b_sh, tap) per branch,
+ *   Ltot [1]             L_total (may be NULL)
+ *   gvm, gva [nscen][nb] lbar dL_s/d|V| and lbar dL_s/dtheta (J^T r without forming J)
+ *   gg, gb, gbsh, gtap [nl]  lbar d(L_total)/d(g, b, b_sh, tap) per branch,
  *                        scenarios summed in ascending order (all four NULL
  *                        to skip; a branch removed in scenario s gets no
  *                        contribution from s; tap derivative at the branch's
  *                        own ratio, 1 for lines; phase shift not differentiated)
  * Pspec, Qspec, wP, wQ [nb] are shared by all scenarios.  Device pointers.
  * The loss and gradients use the grid's current parameters (grid_set_params).
+ * L and Ltot are bitwise those of loss_elementwise on the same inputs.
  */
 pf_status adjoint_elementwise(pf_batch *batch, const double *vm, const double *va, const double *Pspec,
-                              const double *Qspec, const double *wP, const double *wQ, double *L, double *gvm,
-                              double *gva, double *gg, double *gb, double *gbsh, double *gtap, pf_stream stream);
+                              const double *Qspec, const double *wP, const double *wQ, const double *Lbar, double *L,
+                              double *Ltot, double *gvm, double *gva, double *gg, double *gb, double *gbsh,
+                              double *gtap, pf_stream stream);
+
+/*
+ * The mismatch loss alone (the forward pass of the adjoint above): the
+ * injections of every scenario (Eqs. 5-7), L_s and L_total, in one
+ * cooperative launch that forms no residual or gradient.  L [nscen] and Ltot
+ * [1] are device outputs; either may be NULL, not both.  Other arguments as in
+ * adjoint_elementwise.
+ */
+pf_status loss_elementwise(pf_batch *batch, const double *vm, const double *va, const double *Pspec,
+                           const double *Qspec, const double *wP, const double *wQ, double *L, double *Ltot,
+                           pf_stream stream);
 
 /*
  * Fault injection for tests of the bounded device-side waits (no GPU fault
@@ -553,7 +570,8 @@ pf_status pf_debug_fail_allocations(int32_t after);
 #define PF_K_INJ_YBUS_BATCHED 8
 #define PF_K_JAC_YBUS_BATCHED 9
 #define PF_K_REDUCE 10       /* gather of the reduced Jacobian and mismatch vector */
-#define PF_K_COUNT 11
+#define PF_K_LOSS 11         /* the mismatch loss alone (loss_elementwise) */
+#define PF_K_COUNT 12
 
 typedef struct {
     int32_t kernel;          /* PF_K_* */

@@ -719,7 +719,7 @@ PF_API const char *pf_kernel_name(int32_t k)
 {
     static const char *names[PF_K_COUNT] = {"phasor",         "inj_ybus",       "jac_ybus",        "inj_ew",
                                             "jac_ew",         "inj_ew_batched", "jac_ew_batched",  "adjoint",
-                                            "inj_ybus_batched", "jac_ybus_batched", "reduce"};
+                                            "inj_ybus_batched", "jac_ybus_batched", "reduce", "loss"};
     return (k >= 0 && k < PF_K_COUNT) ? names[k] : "?";
 }
 

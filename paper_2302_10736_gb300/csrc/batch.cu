@@ -154,7 +154,7 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
                    (e = b->arena.alloc(&b->brl, brl.size())) ||
                    (e = cudaMemcpyAsync(b->brl, brl.data(), sizeof(int2) * brl.size(), cudaMemcpyHostToDevice, st)))) ||
         (e = b->arena.alloc(&b->U, n)) || (e = b->arena.alloc(&b->V, n)) || (e = b->arena.alloc(&b->r, n)) ||
-        (e = b->arena.alloc(&b->lpart, nw)) ||
+        (e = b->arena.alloc(&b->lpart, nw)) || (e = b->arena.alloc(&b->lscen, std::max(nscen, 1))) ||
         (nscen && (e = cudaMemcpyAsync(b->sc, b->h_sc.data(), sizeof(ScenOut) * nscen, cudaMemcpyHostToDevice, st))) ||
         (e = cudaMemcpyAsync(b->joff, b->h_joff.data(), sizeof(long long) * (nscen + 1), cudaMemcpyHostToDevice,
                              st)) ||
@@ -298,9 +298,9 @@ PF_API pf_status jac_ybus_batched(pf_batch *batch, const double *vm, const doubl
 }
 
 PF_API pf_status adjoint_elementwise(pf_batch *batch, const double *vm, const double *va, const double *Pspec,
-                                     const double *Qspec, const double *wP, const double *wQ, double *L, double *gvm,
-                                     double *gva, double *gg, double *gb, double *gbsh, double *gtap,
-                                     pf_stream stream)
+                                     const double *Qspec, const double *wP, const double *wQ, const double *Lbar,
+                                     double *L, double *Ltot, double *gvm, double *gva, double *gg, double *gb,
+                                     double *gbsh, double *gtap, pf_stream stream)
 {
     pf_status st = check_batch(batch, vm, va, "adjoint_elementwise");
     if (st) return st;
@@ -311,7 +311,21 @@ PF_API pf_status adjoint_elementwise(pf_batch *batch, const double *vm, const do
     if (any && !(gg && gb && gbsh && gtap))
         return set_error(PF_EINVAL, "adjoint_elementwise: gg, gb, gbsh, gtap must all be set or all NULL");
     TraceScope t(batch->b.g, PF_K_ADJOINT, (cudaStream_t)stream);
-    PF_CUDA(launch_adjoint(&batch->b, vm, va, Pspec, Qspec, wP, wQ, L, gvm, gva, any ? gg : nullptr, gb, gbsh, gtap,
-                           (cudaStream_t)stream));
+    PF_CUDA(launch_adjoint(&batch->b, vm, va, Pspec, Qspec, wP, wQ, Lbar, L, Ltot, gvm, gva, any ? gg : nullptr, gb,
+                           gbsh, gtap, (cudaStream_t)stream));
+    return PF_OK;
+}
+
+PF_API pf_status loss_elementwise(pf_batch *batch, const double *vm, const double *va, const double *Pspec,
+                                  const double *Qspec, const double *wP, const double *wQ, double *L, double *Ltot,
+                                  pf_stream stream)
+{
+    pf_status st = check_batch(batch, vm, va, "loss_elementwise");
+    if (st) return st;
+    if (batch->b.S == 0 || batch->b.g->nb == 0) return PF_OK;
+    if (!Pspec || !Qspec || !wP || !wQ) return set_error(PF_EINVAL, "loss_elementwise: a required array is NULL");
+    if (!L && !Ltot) return set_error(PF_EINVAL, "loss_elementwise: L and Ltot are both NULL");
+    TraceScope t(batch->b.g, PF_K_LOSS, (cudaStream_t)stream);
+    PF_CUDA(launch_loss(&batch->b, vm, va, Pspec, Qspec, wP, wQ, L, Ltot, (cudaStream_t)stream));
     return PF_OK;
 }

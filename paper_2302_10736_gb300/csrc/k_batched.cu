@@ -62,6 +62,9 @@ struct BatchArgs {
     const double *Ps, *Qs, *wP, *wQ;
     double2 *r;
     double *lpart, *L, *gvm, *gva, *gg, *gb, *gbsh, *gtap;
+    const double *Lbar;      // upstream gradient (device scalar; NULL = 1): scales every gradient
+    double *Ltot;            // sum_s L_s (may be NULL)
+    unsigned int *lcnt;      // scenarios whose L_s is written (the total's arrival count)
     const double *pg, *pb, *pbsh, *ptap, *pshift;
     const int2 *br_hk;
     const double4_32a *br_aux;
@@ -313,18 +316,47 @@ __device__ __forceinline__ void window_loss(const double *spq, int nbus, double 
     }
 }
 
+// The total loss L_total = sum_s L_s (G14), in ascending s by one thread:
+// every warp that has written L_s values publishes them and adds their count
+// to a.lcnt; the one whose count completes the S scenarios sums them and
+// resets the counter for the next launch.  Nothing waits on another CTA.
+// Called by lane 0 of the writing warp.
+__device__ __forceinline__ void loss_total_arrive(const BatchArgs &a, unsigned int nwritten)
+{
+    if (!a.Ltot || nwritten == 0) return;
+    __threadfence();
+    const unsigned int prev = atomicAdd(a.lcnt, nwritten);
+    if (prev + nwritten != (unsigned int)a.S) return;
+    __threadfence();
+    double t = 0.0;
+    int s = 0;
+    for (; s + 8 <= a.S; s += 8) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = __ldcg(a.L + s + u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t += x[u];
+    }
+    for (; s < a.S; ++s) t += __ldcg(a.L + s);
+    *a.Ltot = t;
+    *a.lcnt = 0u;
+}
+
 // The loss of every scenario from its window partial sums, one warp per
-// scenario (after the last grid barrier).
+// scenario (after the last grid barrier), then the total.
 __device__ __forceinline__ void batch_loss(const BatchArgs &a)
 {
     const int lane = threadIdx.x & 31;
     const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned int nw = 0;
     for (long long s = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < a.S; s += nwarp) {
         double acc = 0.0;
         for (int w = lane; w < a.nwin; w += 32) acc += __ldcg(a.lpart + s * a.nwin + w);
         acc = warp_sum(acc);
         if (lane == 0) a.L[s] = acc;
+        ++nw;
     }
+    if (lane == 0) loss_total_arrive(a, nw);
 }
 
 // Branch-parameter gradients: the partials of Eqs. (5)-(6) by g, b, b_sh and
@@ -410,7 +442,9 @@ __device__ __forceinline__ int2 cta_branches(const BatchArgs &a)
 }
 
 // Throughput adjoint (many items per CTA): every scenario's phasors, grid
-// barrier, injections and residuals, grid barrier, gradients.
+// barrier, injections and residuals, grid barrier, gradients.  GRAD = false:
+// the loss alone (phasors, injections, loss terms, the losses).
+template <bool GRAD>
 __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
@@ -426,7 +460,9 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     for (int k = tid; k < kITrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
     // every scenario's phasors first, visible to all CTAs after the barrier
-    batch_phasors(a, tab, true);
+    batch_phasors(a, tab, GRAD);
+    // r = 2 Lbar w dS: the upstream gradient scales every gradient below
+    const double tl = 2.0 * (a.Lbar ? *a.Lbar : 1.0);
     if (!grid_barrier(gbar, a.bar, gridDim.x, 0, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     const long long nitem = (long long)a.S * a.nwin;
@@ -471,7 +507,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
             const double dP = fma(v2, y.x, sKr) - a.Ps[o];
             const double dQ = fma(-v2, y.y, sKi) - a.Qs[o];
             const double wp = a.wP[o], wq = a.wQ[o];
-            a.r[sb + o] = make_double2(2.0 * wp * dP, 2.0 * wq * dQ);
+            if (GRAD) a.r[sb + o] = make_double2(tl * wp * dP, tl * wq * dQ);
             spq[x] = fma(wp * dP, dP, wq * dQ * dQ);
         }
         __syncthreads();
@@ -480,7 +516,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     if (!grid_barrier(gbar, a.bar, gridDim.x, 1, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     // ---- phase 3a: state gradients, one bus per thread over its own terminals ----
-    for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
+    for (long long it = blockIdx.x; GRAD && it < nitem; it += gridDim.x) {
         const int s = (int)(it / a.nwin), w = (int)(it % a.nwin);
         const ScenOut sc = a.sc[s];
         const int b0 = a.win_bus[w], b1 = a.win_bus[w + 1], nbus = b1 - b0;
@@ -550,7 +586,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     }
 
     // ---- phase 3b: branch-parameter gradients; the loss of every scenario ----
-    if (a.gg) {
+    if (GRAD && a.gg) {
         const int2 lr = cta_branches(a);
         for (int l = lr.x + tid; l < lr.y; l += TB) branch_grad(a, l, branch_const(a, l));
     }
@@ -568,6 +604,8 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
 // scenario, the gradients of the branches whose from-terminal it owns)
 //   dL/dtheta_o = sum_t <r_o, j K_t> + <r_q, -j K_m>
 //   dL/dv_o     = <r_o, 2 v_o conj(Yd_o)> + (sum_t <r_o, K_t> + <r_q, K_m>) / v_o.
+// GRAD = false: the loss alone (no mirror flows, residuals or gradients).
+template <bool GRAD>
 __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
 {
     extern __shared__ __align__(16) char smem[];
@@ -594,7 +632,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
     // from-terminal it owns, from its shared-memory phasors and residuals.
     // Several scenarios: a contiguous range of branches per CTA, summing the
     // scenarios from global memory.
-    const bool fused = a.gg && a.S == 1;
+    const bool fused = GRAD && a.gg && a.S == 1;
     int nbr = 0;                          // branches of the window (fused)
     int2 e0 = make_int2(0, 0);            // the thread's first: {window-local from-terminal, branch}
     int bo = 0;                           // the bus of the thread's first bus-loop slot
@@ -627,7 +665,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         if (tid < nt) {
             const int p = t0 + tid;
             yc0 = a.tcoup[p];
-            tm0 = a.tmir[p];
+            if (GRAD) tm0 = a.tmir[p];
             loc0 = make_int2(a.town[p], a.tloc[p].x);   // owner made window-local at first use
         }
         if (fused && tid < a.max_nbr) e0 = a.brl[(long long)w * a.max_nbr + tid];
@@ -660,12 +698,12 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             const double2 V = make_double2(v * cs, v * sn);
             sV[j] = V;
             if (j < nbus) {
-                sW[j] = make_double2(v, fast_rcp(v));
-                a.V[sb + o] = V;   // for the branch-parameter gradients
+                sW[j] = make_double2(v, GRAD ? fast_rcp(v) : 0.0);
+                if (GRAD) a.V[sb + o] = V;   // for the branch-parameter gradients
             }
         }
         batch_window_meta(a, sc, b0, b0 + nbus, t0, sbm, syd);
-        if (tid < nt) ym0 = a.tcoup[tm0];
+        if (GRAD && tid < nt) ym0 = a.tcoup[tm0];
         if (tid < 2 * nbus) {
             const int o = b0 + bo;
             spec0 = (tid & 1) ? a.Qs[o] : a.Ps[o];
@@ -679,18 +717,21 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             int2 loc = loc0;
             if (i != tid) {
                 yc = a.tcoup[p];
-                ym = a.tcoup[a.tmir[p]];
+                if (GRAD) ym = a.tcoup[a.tmir[p]];
                 loc = make_int2(a.town[p], a.tloc[p].x);
             }
             loc.x -= b0;
             const double2 Vo = sV[loc.x], Vq = sV[loc.y];
             const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);   // V_o conj(V_q)
             double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);                 // K_t
-            double Mr = fma(ym.x, Wr, -ym.y * Wi), Mi = fma(-ym.x, Wi, -ym.y * Wr);               // K_m
-            if (p == sc.ph || p == sc.pk) Kr = Ki = Mr = Mi = 0.0;   // outage branch
+            if (p == sc.ph || p == sc.pk) Kr = Ki = 0.0;   // outage branch
             sK[i] = make_double2(Kr, Ki);
-            sM[i] = make_double2(Mr, Mi);
-            sloc[i] = loc;
+            if (GRAD) {
+                double Mr = fma(ym.x, Wr, -ym.y * Wi), Mi = fma(-ym.x, Wi, -ym.y * Wr);   // K_m
+                if (p == sc.ph || p == sc.pk) Mr = Mi = 0.0;
+                sM[i] = make_double2(Mr, Mi);
+                sloc[i] = loc;
+            }
         }
         __syncthreads();
         // the first branch's constants (not thread 0: its fence on arriving at
@@ -699,6 +740,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         // ---- injections, residuals and loss terms of the own buses, two
         // threads per bus (the P and the Q part; no divergence) ----
         double lt = 0.0;   // the thread's loss terms
+        const double tl = GRAD ? 2.0 * (a.Lbar ? *a.Lbar : 1.0) : 0.0;
         {
             const double *kk = reinterpret_cast<const double *>(sK);
             double *rr = reinterpret_cast<double *>(sR);
@@ -720,9 +762,11 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
                 const double2 y = syd[b];
                 // P = v^2 Re conj(Yd) + sum Re K, Q = v^2 Im conj(Yd) + sum Im K
                 const double d = fma(v * v, im ? neg(y.y) : y.x, sk) - spec;
-                const double r = 2.0 * wt * d;
-                gr[2 * b + im] = r;
-                rr[2 * b + im] = r;
+                if (GRAD) {
+                    const double r = tl * wt * d;   // 2 Lbar w dS
+                    gr[2 * b + im] = r;
+                    rr[2 * b + im] = r;
+                }
                 lt = fma(wt * d, d, lt);
             }
         }
@@ -743,7 +787,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
     // several scenarios: the thread's first branch of the CTA's range
     int2 lr = make_int2(0, 0);
     int l0 = -1;
-    if (!fused && a.gg) {
+    if (GRAD && !fused && a.gg) {
         lr = cta_branches(a);
         l0 = lr.x + tid;
         if (tid && l0 < lr.y) bc0 = branch_const(a, l0);
@@ -752,9 +796,9 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
 
     const int jg = nbus + tid;
     double2 rg = make_double2(0.0, 0.0);
-    if (has && jg < nph) rg = a.r[sb + sslot[jg]];
-    if (tid == 0 && (fused ? tid < nbr : l0 >= 0 && l0 < lr.y)) bc0 = branch_const(a, fused ? e0.y : l0);
-    if (!fused && a.gg && l0 < lr.y) branch_grad(a, l0, bc0);
+    if (GRAD && has && jg < nph) rg = a.r[sb + sslot[jg]];
+    if (GRAD && tid == 0 && (fused ? tid < nbr : l0 >= 0 && l0 < lr.y)) bc0 = branch_const(a, fused ? e0.y : l0);
+    if (GRAD && !fused && a.gg && l0 < lr.y) branch_grad(a, l0, bc0);
     // the loss of scenario blockIdx.x (S <= items <= CTAs), by the last warp,
     // its loads in flight with the ghost residuals'
     if (a.L && blockIdx.x < (unsigned)a.S && (tid >> 5) == (TB >> 5) - 1) {
@@ -763,9 +807,12 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         double acc = 0.0;
         for (int w2 = lane; w2 < a.nwin; w2 += 32) acc += __ldcg(lp + w2);
         acc = warp_sum(acc);
-        if (lane == 0) a.L[blockIdx.x] = acc;
+        if (lane == 0) {
+            a.L[blockIdx.x] = acc;
+            loss_total_arrive(a, 1u);
+        }
     }
-    if (has) {
+    if (GRAD && has) {
         // ---- the ghost buses' residuals ----
         if (jg < nph) sR[jg] = rg;
         for (int j = jg + TB; j < nph; j += TB) sR[j] = a.r[sb + sslot[j]];
@@ -834,7 +881,7 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
             }
         }
     }
-    if (!fused && a.gg)
+    if (GRAD && !fused && a.gg)
         for (int l = l0 + TB; l < lr.y; l += TB) branch_grad(a, l, branch_const(a, l));
 }
 
@@ -948,12 +995,34 @@ cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double
     return coop_launch(k_ewb<false>, b->resident[0], b->tb, smem, items, s, a);
 }
 
-cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
-                           const double *wP, const double *wQ, double *L, double *gvm, double *gva, double *gg,
-                           double *gb, double *gbsh, double *gtap, cudaStream_t s)
+// The adjoint (grad) or the loss alone: one item per CTA (k_adj1) when every
+// (scenario, window) item fits on the GPU at once, else the throughput form.
+template <bool GRAD>
+static cudaError_t launch_adj(Batch *b, BatchArgs &a, cudaStream_t s)
 {
     Grid *g = b->g;
-    if (b->nwin == 0 || b->S == 0) return cudaSuccess;
+    const long long items = (long long)b->S * b->nwin;
+    const int r1 = GRAD ? 3 : 5, rn = GRAD ? 2 : 4;   // resident-CTA caches of the four kernels
+    const long long branch_ctas1 = GRAD ? (g->nl + kAdj1Threads - 1) / kAdj1Threads : 0;
+    const long long branch_ctas = GRAD ? (g->nl + b->tb - 1) / b->tb : 0;
+    if (b->ghost) {
+        // the form is chosen by the gradient kernel's residency for both, so that
+        // the loss alone and the adjoint sum the same terms in the same order
+        const size_t smem = adj1_smem_plan(a.max_nbus, a.max_nt, a.max_nph).total;
+        cudaError_t e = coop_resident(k_adj1<true>, b->resident[3], kAdj1Threads, smem);
+        if (e == cudaSuccess) e = coop_resident(k_adj1<GRAD>, b->resident[r1], kAdj1Threads, smem);
+        if (e != cudaSuccess) return e;
+        if (items <= b->resident[3])
+            return coop_launch(k_adj1<GRAD>, b->resident[r1], kAdj1Threads, smem,
+                               std::max<long long>(items, branch_ctas1), s, a);
+    }
+    const size_t smem = ew_smem_plan(a.max_nbus, a.max_nt, 0, false).total + kTrigSmem;
+    return coop_launch(k_adj<GRAD>, b->resident[rn], b->tb, smem, std::max<long long>(items, branch_ctas), s, a);
+}
+
+static BatchArgs loss_args(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
+                           const double *wP, const double *wQ, double *L, double *Ltot)
+{
     BatchArgs a = batch_args(b);
     a.vm = vm;
     a.va = va;
@@ -961,7 +1030,20 @@ cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const d
     a.Qs = Qs;
     a.wP = wP;
     a.wQ = wQ;
-    a.L = L;
+    a.L = L ? L : b->lscen;   // the total needs every L_s somewhere
+    a.Ltot = Ltot;
+    a.lcnt = b->g->bar + kLossCountWord;
+    return a;
+}
+
+cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
+                           const double *wP, const double *wQ, const double *Lbar, double *L, double *Ltot,
+                           double *gvm, double *gva, double *gg, double *gb, double *gbsh, double *gtap,
+                           cudaStream_t s)
+{
+    if (b->nwin == 0 || b->S == 0) return cudaSuccess;
+    BatchArgs a = loss_args(b, vm, va, Ps, Qs, wP, wQ, L, Ltot);
+    a.Lbar = Lbar;
     a.gvm = gvm;
     a.gva = gva;
     a.gg = gg;
@@ -969,18 +1051,15 @@ cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const d
     a.gbsh = gbsh;
     a.gtap = gtap;
     a.aligned = al16(gvm) && al16(gva);
-    const long long items = (long long)b->S * b->nwin;
-    if (b->ghost) {   // one item per CTA, if they all fit on the GPU at once
-        const size_t smem = adj1_smem_plan(a.max_nbus, a.max_nt, a.max_nph).total;
-        cudaError_t e = coop_resident(k_adj1, b->resident[3], kAdj1Threads, smem);
-        if (e != cudaSuccess) return e;
-        if (items <= b->resident[3])
-            return coop_launch(k_adj1, b->resident[3], kAdj1Threads, smem,
-                               std::max<long long>(items, (g->nl + kAdj1Threads - 1) / kAdj1Threads), s, a);
-    }
-    const size_t smem = ew_smem_plan(a.max_nbus, a.max_nt, 0, false).total + kTrigSmem;
-    return coop_launch(k_adj, b->resident[2], b->tb, smem,
-                       std::max<long long>(items, (g->nl + b->tb - 1) / b->tb), s, a);
+    return launch_adj<true>(b, a, s);
+}
+
+cudaError_t launch_loss(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
+                        const double *wP, const double *wQ, double *L, double *Ltot, cudaStream_t s)
+{
+    if (b->nwin == 0 || b->S == 0) return cudaSuccess;
+    BatchArgs a = loss_args(b, vm, va, Ps, Qs, wP, wQ, L, Ltot);
+    return launch_adj<false>(b, a, s);
 }
 
 }  // namespace pf

@@ -178,8 +178,10 @@ __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max
 constexpr uint32_t kMaxSmem = 227u * 1024u;
 // shared memory of the (cos, sin) table every phasor-forming CTA holds
 constexpr uint32_t kTrigSmem = kITrigN * (uint32_t)sizeof(ITrig);
-// words of the batched kernels' grid-barrier state: parity, two counters on their own lines
-constexpr int kBarWords = 96;
+// words of the batched kernels' grid-barrier state: parity, two counters on their
+// own lines, and the loss total's arrival count (k_batched.cu) on a fourth
+constexpr int kBarWords = 128;
+constexpr int kLossCountWord = 96;
 
 // Shared memory of the small-batch adjoint (k_adj1, one item per CTA): bus
 // metadata and self sums, both flows of every terminal and its two phasor
@@ -379,7 +381,10 @@ struct Batch {
     double2 *V = nullptr;            // [S][nb]
     double2 *r = nullptr;            // [S][nb] loss residual (2 wP dP, 2 wQ dQ)
     double *lpart = nullptr;         // [S][nwin] per-window loss partial sums
-    int resident[4] = {0, 0, 0, 0};  // co-resident CTAs of the batched kernels (inj, jac, adjoint, k_adj1)
+    double *lscen = nullptr;         // [S] per-scenario losses when the caller wants only their total
+    // co-resident CTAs of the batched kernels (inj, jac, adjoint, k_adj1, and
+    // the loss-only forms of the last two)
+    int resident[6] = {0, 0, 0, 0, 0, 0};
     // the batch's own element-wise windows: throughput-bound, so every thread
     // owns a bus in the reduction and loops over up to tfac terminals
     int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0;
@@ -401,8 +406,11 @@ cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double
 cudaError_t launch_ybus_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,
                                 double *J, cudaStream_t s);
 cudaError_t launch_adjoint(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
-                           const double *wP, const double *wQ, double *L, double *gvm, double *gva, double *gg,
-                           double *gb, double *gbsh, double *gtap, cudaStream_t s);
+                           const double *wP, const double *wQ, const double *Lbar, double *L, double *Ltot,
+                           double *gvm, double *gva, double *gg, double *gb, double *gbsh, double *gtap,
+                           cudaStream_t s);
+cudaError_t launch_loss(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,
+                        const double *wP, const double *wQ, double *L, double *Ltot, cudaStream_t s);
 
 }  // namespace pf
 

@@ -521,7 +521,8 @@ def _bind_batches():
         "jac_elementwise_batched": (st, [vp, vp, vp, vp, vp, vp, vp]),
         "inj_ybus_batched": (st, [vp, vp, vp, vp, vp, vp]),
         "jac_ybus_batched": (st, [vp, vp, vp, vp, vp, vp, vp]),
-        "adjoint_elementwise": (st, [vp] + [vp] * 14),
+        "adjoint_elementwise": (st, [vp] * 17),
+        "loss_elementwise": (st, [vp] * 10),
     }
     for name, (res, args) in sig.items():
         fn = getattr(_lib, name)
@@ -609,14 +610,25 @@ def jac_ybus_batched(batch, vm, va, P, Q, J, stream=None):
 
 
 def adjoint_elementwise(batch, vm, va, Pspec, Qspec, wP, wQ, L, gvm, gva, gg=None, gb=None, gbsh=None, gtap=None,
-                        stream=None):
+                        stream=None, Lbar=None, Ltot=None):
+    """Loss per scenario L [S] (may be None), its total Ltot [1] (may be None),
+    and the gradients scaled by the device scalar Lbar (None = 1)."""
     nb, nl, S = batch.grid.nb, batch.grid.nl, batch.nscen
     _check(_lib.adjoint_elementwise(batch.handle, _dptr(vm, "vm", S * nb), _dptr(va, "va", S * nb),
                                     _dptr(Pspec, "Pspec", nb), _dptr(Qspec, "Qspec", nb), _dptr(wP, "wP", nb),
-                                    _dptr(wQ, "wQ", nb), _dptr(L, "L", S), _dptr(gvm, "gvm", S * nb),
-                                    _dptr(gva, "gva", S * nb), _dptr(gg, "gg", nl), _dptr(gb, "gb", nl),
-                                    _dptr(gbsh, "gbsh", nl), _dptr(gtap, "gtap", nl), _stream(stream)),
-           "adjoint_elementwise")
+                                    _dptr(wQ, "wQ", nb), _dptr(Lbar, "Lbar", 1), _dptr(L, "L", S),
+                                    _dptr(Ltot, "Ltot", 1), _dptr(gvm, "gvm", S * nb), _dptr(gva, "gva", S * nb),
+                                    _dptr(gg, "gg", nl), _dptr(gb, "gb", nl), _dptr(gbsh, "gbsh", nl),
+                                    _dptr(gtap, "gtap", nl), _stream(stream)), "adjoint_elementwise")
+
+
+def loss_elementwise(batch, vm, va, Pspec, Qspec, wP, wQ, L=None, Ltot=None, stream=None):
+    """The mismatch loss alone: L [S] per scenario and/or their total Ltot [1]."""
+    nb, S = batch.grid.nb, batch.nscen
+    _check(_lib.loss_elementwise(batch.handle, _dptr(vm, "vm", S * nb), _dptr(va, "va", S * nb),
+                                 _dptr(Pspec, "Pspec", nb), _dptr(Qspec, "Qspec", nb), _dptr(wP, "wP", nb),
+                                 _dptr(wQ, "wQ", nb), _dptr(L, "L", S), _dptr(Ltot, "Ltot", 1), _stream(stream)),
+           "loss_elementwise")
 
 
 def _mismatch_loss_function():
@@ -627,29 +639,34 @@ def _mismatch_loss_function():
         differentiable function of the voltage states and the branch parameters.
 
         forward(batch, vm, va, g, b, bsh, tap, shift, gs, bs, Pspec, Qspec, wP, wQ)
-        sets the grid's parameters, runs the adjoint kernel once (loss and all
-        gradients) and keeps the gradients for backward."""
+        sets the grid's parameters and runs the loss alone (loss_elementwise: no
+        gradient work); backward sets them again and runs the adjoint kernel
+        with the upstream gradient as its scale, so every operation on method
+        values runs in the library."""
 
         @staticmethod
         def forward(ctx, batch, vm, va, g, b, bsh, tap, shift, gs, bs, Pspec, Qspec, wP, wQ):
-            grid = batch.grid
-            c = lambda x: x.detach().contiguous()
-            grid_set_params(grid, c(g), c(b), c(bsh), c(tap), c(shift), None if gs is None else c(gs),
-                            None if bs is None else c(bs))
-            S, nb, nl = batch.nscen, grid.nb, grid.nl
-            dev = vm.device
-            L = torch.empty(S, dtype=torch.float64, device=dev)
-            gvm = torch.empty(S * nb, dtype=torch.float64, device=dev)
-            gva = torch.empty_like(gvm)
-            gp = [torch.empty(nl, dtype=torch.float64, device=dev) for _ in range(4)]
-            adjoint_elementwise(batch, c(vm), c(va), c(Pspec), c(Qspec), c(wP), c(wQ), L, gvm, gva, *gp)
-            ctx.save_for_backward(gvm.view_as(vm), gva.view_as(va), *gp)
-            return L.sum()
+            c = lambda x: None if x is None else x.detach().contiguous()
+            params = tuple(c(x) for x in (g, b, bsh, tap, shift, gs, bs))
+            grid_set_params(batch.grid, *params)
+            state = tuple(c(x) for x in (vm, va, Pspec, Qspec, wP, wQ))
+            Ltot = torch.empty(1, dtype=torch.float64, device=vm.device)
+            loss_elementwise(batch, *state, None, Ltot)
+            ctx.batch, ctx.params, ctx.state, ctx.shapes = batch, params, state, (vm.shape, va.shape)
+            return Ltot.view(())
 
         @staticmethod
         def backward(ctx, grad):
-            gvm, gva, gg, gb, gbsh, gtap = ctx.saved_tensors
-            return (None, grad * gvm, grad * gva, grad * gg, grad * gb, grad * gbsh, grad * gtap,
+            batch, (vm, va, Ps, Qs, wP, wQ) = ctx.batch, ctx.state
+            grid = batch.grid
+            grid_set_params(grid, *ctx.params)   # the parameters of the forward pass
+            S, nb, nl, dev = batch.nscen, grid.nb, grid.nl, vm.device
+            gvm = torch.empty(S * nb, dtype=torch.float64, device=dev)
+            gva = torch.empty_like(gvm)
+            gp = [torch.empty(nl, dtype=torch.float64, device=dev) for _ in range(4)]
+            lbar = grad.detach().to(device=dev, dtype=torch.float64).reshape(1).contiguous()
+            adjoint_elementwise(batch, vm, va, Ps, Qs, wP, wQ, None, gvm, gva, *gp, Lbar=lbar)
+            return (None, gvm.view(ctx.shapes[0]), gva.view(ctx.shapes[1]), *gp,
                     None, None, None, None, None, None, None)
 
     return MismatchLoss

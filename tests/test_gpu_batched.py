@@ -392,6 +392,84 @@ def test_mismatch_loss_autograd(pf):
         assert relerr(tt.grad.cpu().numpy(), 2 * ref) <= TOL
 
 
+@pytest.mark.parametrize("nb,nl,S,form", [(2000, 2700, 3, "one item per CTA"), (10000, 13500, 8, "throughput")])
+def test_loss_alone_total_and_upstream_scale(pf, nb, nl, S, form):
+    """loss_elementwise: L_s and L_total against the oracle's loss of each
+    scenario (outages honoured); L_total is bitwise the ascending sum of the
+    L_s; adjoint_elementwise returns bitwise the same losses, and its
+    gradients with an upstream scale Lbar are Lbar times the unscaled ones.
+    Both kernel forms: a batch with fewer items than SMs (one per CTA) and a
+    larger one."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    gr, vm, va, Ps, Qs, wP, wQ = _adjoint_case(nb, nl, 61 + S, S)
+    nonbridge = np.flatnonzero(~synth.bridges(nb, gr["f"], gr["t"]))
+    outage = np.full(S, -1, np.int32)
+    outage[1::2] = nonbridge[5:5 + len(outage[1::2])]
+    grid = pf.ybus_build(gr)
+    batch = pf.batch_create(grid, S, outage)
+    args = [_d(x) for x in (vm.ravel(), va.ravel(), Ps, Qs, wP, wQ)]
+    L = torch.full((S,), np.nan, dtype=torch.float64, device="cuda")
+    Lt = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+    pf.loss_elementwise(batch, *args, L, Lt)
+    Lt_only = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+    pf.loss_elementwise(batch, *args, None, Lt_only)
+    torch.cuda.synchronize()
+    pf.grid_check_error(grid)
+    Lh = L.cpu().numpy()
+    Lr = np.zeros(S)
+    for s in range(S):
+        skip = _skip(gr["nl"], int(outage[s]))
+        Y = oracle.ybus(gr, skip=skip)
+        P, Q = oracle.inj_sparse(Y, vm[s], va[s])
+        Lr[s] = oracle.loss(P, Q, Ps, Qs, wP, wQ)
+    assert relerr(Lh, Lr) <= TOL
+    acc = 0.0
+    for x in Lh:   # ascending s
+        acc += x
+    assert Lt.item() == acc and Lt_only.item() == acc
+    # the adjoint: same losses bitwise; gradients scale with Lbar
+    outs = {}
+    for lbar in (None, 2.5):
+        La = torch.full((S,), np.nan, dtype=torch.float64, device="cuda")
+        Lta = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+        gvm = torch.empty(S * nb, dtype=torch.float64, device="cuda")
+        gva = torch.empty_like(gvm)
+        gp = [torch.empty(gr["nl"], dtype=torch.float64, device="cuda") for _ in range(4)]
+        lb = None if lbar is None else torch.full((1,), lbar, dtype=torch.float64, device="cuda")
+        pf.adjoint_elementwise(batch, *args, La, gvm, gva, *gp, Lbar=lb, Ltot=Lta)
+        torch.cuda.synchronize()
+        assert torch.equal(La, L) and torch.equal(Lta, Lt), form
+        outs[lbar] = [x.cpu().numpy() for x in [gvm, gva] + gp]
+    for a, b in zip(outs[2.5], outs[None]):
+        assert relerr(a, 2.5 * b) <= 1e-14
+
+
+def test_mismatch_loss_forward_runs_the_loss_alone(pf):
+    """The autograd forward launches the loss kernel only; the backward the
+    adjoint (library tracer)."""
+    import torch
+    gr, vm, va, Ps, Qs, wP, wQ = _adjoint_case(300, 420, 62, 2)
+    grid = pf.ybus_build(gr)
+    batch = pf.batch_create(grid, 2, None)
+    t = lambda x: _d(x)
+    vm_t = t(vm.ravel()).requires_grad_(True)
+    va_t = t(va.ravel()).requires_grad_(True)
+    g_t = t(gr["g"]).requires_grad_(True)
+    pf.grid_trace_enable(grid, 64)
+    loss = pf.MismatchLoss.apply(batch, vm_t, va_t, g_t, t(gr["b"]), t(gr["bsh"]), t(gr["tap"]), t(gr["shift"]),
+                                 t(gr["gs"]), t(gr["bs"]), t(Ps), t(Qs), t(wP), t(wQ))
+    torch.cuda.synchronize()
+    fwd = [k for k, _ in pf.grid_trace_read(grid)]
+    loss.backward()
+    torch.cuda.synchronize()
+    bwd = [k for k, _ in pf.grid_trace_read(grid)]
+    pf.grid_trace_enable(grid, 0)
+    assert "loss" in fwd and "adjoint" not in fwd, fwd
+    assert "adjoint" in bwd and "loss" not in bwd, bwd
+    assert vm_t.grad is not None and g_t.grad is not None
+
+
 def test_cuda_graph_capture_and_replay(pf):
     """The batched evaluation, the adjoint and the single evaluation can be
     captured in a CUDA graph (after one eager call) and replayed; replays give
