@@ -130,6 +130,71 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+def host_cpu():
+    """(CPU model, logical CPUs) of the host running this process."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                if ln.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return model or platform.processor() or platform.machine(), os.cpu_count() or 1
+
+
+def oracle_batch_baseline(w, kind, seconds):
+    """The oracle over the scenarios of a batched workload on all host cores
+    (one thread per core; the oracle's C calls release the GIL), scenarios in
+    order until `seconds` have passed (at least one round of one per core).
+    kind "n1": injections + Jacobian of scenario s on its grid without its
+    outage branch; "adjoint": injections, Jacobian, J^T r and the complex-step
+    branch-parameter gradients of scenario s (the loss of the 250k workload)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    model, ncpu = host_cpu()
+    S = w["nscen"]
+    Y0 = oracle.ybus(w) if kind == "adjoint" else None
+
+    def one(s):
+        if kind == "n1":
+            skip = np.zeros(w["nl"], np.uint8)
+            skip[int(w["outage"][s])] = 1
+            Y = oracle.ybus(w, skip=skip)
+            oracle.elementwise(w, w["vm"][s], w["va"][s], Y, skip=skip)
+        else:
+            P, Q, J = oracle.elementwise(w, w["vm"][s], w["va"][s], Y0)
+            oracle.adjoint_state(Y0, J, P, Q, w["Ps"], w["Qs"], w["wP"], w["wQ"])
+            oracle.adjoint_params_cstep(w, Y0, w["vm"][s], w["va"][s], w["Ps"], w["Qs"], w["wP"], w["wQ"])
+        return s
+
+    nthr = min(ncpu, S)
+    t0 = time.perf_counter()
+    done = 0
+    with ThreadPoolExecutor(nthr) as ex:
+        while done < S:
+            n = min(nthr, S - done)
+            list(ex.map(one, range(done, done + n)))
+            done += n
+            if time.perf_counter() - t0 >= seconds:
+                break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "scenarios/s", "cores": nthr, "nproc": ncpu, "cpu_model": model,
+            "kind": "oracle", "sample": "%d of the %d scenarios, %d threads, %.1f s" % (done, S, nthr, el)}
+
+
 def run_oracle_steps(w, nsteps, seconds=None):
     """Oracle element-wise injection + Jacobian on the workload; returns (evals, s)."""
     import oracle
@@ -158,7 +223,8 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "global_batch": 1, "seq_len": 0, "parallelism": "none"},
-            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": 1, "nproc": host_cpu()[1],
+                             "cpu_model": host_cpu()[0], "kind": "oracle",
                              "sample": "%d full element-wise evaluations of the 70k-bus grid" % n},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -341,17 +407,17 @@ def timed_replays(torch, g, reps, name="replays"):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_workloads(torch, pfgrid, synth, reps, only=None):
+def extra_workloads(torch, pfgrid, synth, reps, only=None, cpu_seconds=None):
     """The batched and adjoint workloads, each timed from a CUDA-graph replay
     (inputs larger than L2 for the batched ones, so no flush is needed).
     `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced", "ultra",
     "newton", "sweep", "study", "target"."""
     out = {}
     if only in (None, "n1"):
-        out.update(_n1_workload(torch, pfgrid, synth, reps))
+        out.update(_n1_workload(torch, pfgrid, synth, reps, cpu_seconds))
     for k, key, tag in ((4, "adjoint_25k", "adjoint4"), (5, "batched_jac_and_adjoint_250k_x16", "batched5")):
         if only in (None, tag):
-            out[key] = _adjoint_workload(torch, pfgrid, synth, reps, k)
+            out[key] = _adjoint_workload(torch, pfgrid, synth, reps, k, cpu_seconds)
     if only in (None, "permuted"):
         out["c2_random_bus_order"] = _permuted_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "reduced"):
@@ -609,7 +675,7 @@ def _permuted_workload(torch, pfgrid, synth, steps):
     return res
 
 
-def _n1_workload(torch, pfgrid, synth, reps):
+def _n1_workload(torch, pfgrid, synth, reps, cpu_seconds=None):
     out = {}
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
@@ -644,10 +710,12 @@ def _n1_workload(torch, pfgrid, synth, reps):
         g3 = graph_of(torch, lambda: fn(grid, vm[:nb], va[:nb], P1, Q1, J1))
         out["n1_batch_10k_x1024"][key] = 1e3 / timed_replays(torch, g3, reps, "n1_single")
     pfgrid.grid_check_error(grid)
+    if cpu_seconds:
+        out["n1_batch_10k_x1024"]["cpu_baseline"] = oracle_batch_baseline(w, "n1", cpu_seconds)
     return out
 
 
-def _adjoint_workload(torch, pfgrid, synth, reps, k):
+def _adjoint_workload(torch, pfgrid, synth, reps, k, cpu_seconds=None):
     """Adjoint of the mismatch loss on workload k (25k buses x 1, or 250k x 16
     with the batched Jacobian and the single-scenario Ybus Jacobian beside it)."""
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
@@ -686,6 +754,11 @@ def _adjoint_workload(torch, pfgrid, synth, reps, k):
         g3 = graph_of(torch, lambda: pfgrid.jac_ybus(grid, vm[:nb], va[:nb], P1, Q1, J1))
         res["single_scenario_ybus_jac_evals_per_s"] = 1e3 / timed_replays(torch, g3, reps, "ybus5")
     pfgrid.grid_check_error(grid)
+    if cpu_seconds:
+        import oracle
+        Y = oracle.ybus(w)
+        Psh, Qsh = oracle.inj_sparse(Y, w["vm2"], w["va2"])
+        res["cpu_baseline"] = oracle_batch_baseline(dict(w, Ps=Psh, Qs=Qsh), "adjoint", cpu_seconds)
     return res
 
 
@@ -864,13 +937,16 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, el = run_oracle_steps(w, None, seconds=args.cpu_seconds)
-        cpu = {"value": n / el, "unit": "evals/s", "cores": 1, "kind": "oracle",
-               "sample": "%d full element-wise evaluations (P, Q, J) of the 70k-bus grid, single thread" % n}
+        model, ncpu = host_cpu()
+        cpu = {"value": n / el, "unit": "evals/s", "cores": 1, "nproc": ncpu, "cpu_model": model, "kind": "oracle",
+               "sample": "%d full element-wise evaluations (P, Q, J) of the 70k-bus grid, single thread "
+                         "(one evaluation has no independent parts to spread over cores)" % n}
 
     extra = None
     if rank == 0 and not args.no_extra:
         try:
-            extra = extra_workloads(torch, pfgrid, synth, max(3, min(args.steps, 20)))
+            extra = extra_workloads(torch, pfgrid, synth, max(3, min(args.steps, 20)),
+                                    cpu_seconds=None if args.no_cpu_baseline else min(args.cpu_seconds, 5.0))
         except Exception as ex:  # reported, never silently replaced
             extra = {"error": str(ex)}
 
