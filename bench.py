@@ -685,6 +685,8 @@ def _n1_workload(torch, pfgrid, synth, reps, cpu_seconds=None):
     S, nb, T = w["nscen"], w["nb"], 2 * w["nl"]
     batch = pfgrid.batch_create(grid, S, w["outage"])
     vm, va = dev(w["vm"]), dev(w["va"])
+    default_cfg = pfgrid.batch_get_config(batch)
+    tuned_cfg = pfgrid.batch_autotune(batch, vm, va, reps=3)
     P = torch.empty(S * nb, dtype=torch.float64, device="cuda")
     Q = torch.empty_like(P)
     J = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
@@ -695,7 +697,8 @@ def _n1_workload(torch, pfgrid, synth, reps, cpu_seconds=None):
     out["n1_batch_10k_x1024"] = {
         "evals_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
         "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / fp64_peak_g(),
-        "hbm_gbs": byt / (ms * 1e-3) / 1e9, "jacobian_values": batch.nnzJ_total}
+        "hbm_gbs": byt / (ms * 1e-3) / 1e9, "jacobian_values": batch.nnzJ_total,
+        "launch_config": tuned_cfg, "default_launch_config": default_cfg}
     # the same batch by the Ybus method (phasor launch + row launch)
     g2 = graph_of(torch, lambda: pfgrid.jac_ybus_batched(batch, vm, va, P, Q, J))
     ms2 = timed_replays(torch, g2, reps, "n1_batch_ybus")
@@ -723,6 +726,10 @@ def _adjoint_workload(torch, pfgrid, synth, reps, k, cpu_seconds=None):
     grid = pfgrid.ybus_build(w)
     S, nb, nl, T = w["nscen"], w["nb"], w["nl"], 2 * w["nl"]
     batch = pfgrid.batch_create(grid, S, None)
+    default_cfg = pfgrid.batch_get_config(batch)
+    # the adjoint is this workload's main call: tune for it (and the Jacobian beside it)
+    tuned_cfg = pfgrid.batch_autotune(batch, dev(w["vm"]), dev(w["va"]), reps=3,
+                                      kernels=pfgrid.PF_TUNE_ADJOINT | pfgrid.PF_TUNE_JAC | pfgrid.PF_TUNE_YBUS)
     Ps = torch.empty(nb, dtype=torch.float64, device="cuda")
     Qs = torch.empty_like(Ps)
     pfgrid.inj_elementwise(grid, dev(w["vm2"]), dev(w["va2"]), Ps, Qs)
@@ -735,6 +742,7 @@ def _adjoint_workload(torch, pfgrid, synth, reps, k, cpu_seconds=None):
     ms = timed_replays(torch, g, reps, "adjoint%d" % k)
     ops = S * ((6 + 8 + 8) * nb + (10 + 22) * T + 48 * nl)   # phasor 1/v and V (sin/cos on the integer pipe)
     res = {"loss_and_gradients_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
+           "launch_config": tuned_cfg, "default_launch_config": default_cfg,
            "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / fp64_peak_g()}
     if k == 5:
         P = torch.empty(S * nb, dtype=torch.float64, device="cuda")

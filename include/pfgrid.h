@@ -316,6 +316,19 @@ pf_status grid_selfcheck(const pf_grid_desc *desc, int32_t window, int32_t nwin_
 
 typedef struct pf_batch pf_batch;   /* opaque; S scenarios over one grid */
 
+/* Launch configuration of a batch's kernels (batch_set_config, batch_autotune). */
+typedef struct {
+    int32_t window;                /* threads per CTA of the batched element-wise kernels, 128 or 256: a
+                                      window holds at most this many consecutive buses */
+    int32_t terminals_per_thread;  /* 1, 2 or 3: a window holds at most window x this many terminals */
+    int32_t ctas_per_sm;           /* CTAs per SM of the persistent batched launches: 0 = as many as fit,
+                                      else at most this many (1 .. 8) */
+    int32_t adjoint_form;          /* 0: one (scenario, window) item per CTA when they all fit at once,
+                                      else the persistent form; 1: the persistent form always */
+    int32_t ybus_lanes;            /* lanes per row of the batched Ybus kernels: 1, 2, 4, 8, 16 or 32 */
+    int32_t ybus_block;            /* threads per CTA of the batched Ybus kernels (multiple of 32, <= 512) */
+} pf_batch_config;
+
 /*
  * A batch of `nscen` scenarios over `grid` (the grid must outlive the batch).
  * Scenario s has its own voltage state and, when outage != NULL and
@@ -327,7 +340,9 @@ typedef struct pf_batch pf_batch;   /* opaque; S scenarios over one grid */
  * (batch_jac_offsets), nnzJ_s = 4 (nnzY - 2 removed).  outage is a host array
  * read during the call; values outside [-1, nl) give PF_EINVAL.  Allocates
  * the batch workspaces (phasors and residuals, 64 bytes per scenario-bus) and
- * synchronizes `stream`.
+ * synchronizes `stream`.  If the environment variable PFGRID_TUNE_CACHE names
+ * a tuning cache file (written by batch_autotune) that holds a configuration
+ * for this GPU and the batch's size class, the batch starts with it.
  */
 pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outage, pf_stream stream, pf_batch **out);
 
@@ -336,6 +351,55 @@ void batch_destroy(pf_batch *batch);
 
 /* Number of scenarios and total Jacobian values of the batch (either may be NULL). */
 pf_status batch_info(const pf_batch *batch, int32_t *nscen, int64_t *nnzJ_total);
+
+/* The batch's current launch configuration. */
+pf_status batch_get_config(const pf_batch *batch, pf_batch_config *cfg);
+
+/*
+ * Set the batch's launch configuration (PF_EINVAL for values outside the
+ * ranges of pf_batch_config; PF_EUNSUPPORTED when a window would exceed
+ * shared memory).  A new window size or terminal cap rebuilds the batch's
+ * windows (host work and upload; synchronizes `stream`).  Results do not
+ * depend on the configuration except for the rounding of loss sums: every
+ * bus and Jacobian entry is summed in the same order whatever the windows.
+ */
+pf_status batch_set_config(pf_batch *batch, const pf_batch_config *cfg, pf_stream stream);
+
+/*
+ * Autotuner of the batched launches (no counterpart in the paper): times
+ * `reps` launches (CUDA events on `stream`) of the kernels selected in
+ * `kernels` (PF_TUNE_* bits; 0 means PF_TUNE_JAC | PF_TUNE_YBUS) with the
+ * states vm, va [nscen * nb].  The element-wise shape (window size x terminal
+ * cap x CTAs per SM, and the adjoint's form when it is selected) minimizes the
+ * summed time of jac_elementwise_batched and/or adjoint_elementwise (timed with
+ * targets 0 and weights 1); the batched Ybus shape (lanes x CTA size) that of
+ * jac_ybus_batched.  Keeps the fastest, writes it to *best (may be NULL) and,
+ * when PFGRID_TUNE_CACHE names a file, stores it there under batch_tune_key.
+ * Allocates temporary outputs (the batch's full Jacobian, the adjoint's
+ * arrays) and synchronizes.
+ */
+#define PF_TUNE_JAC 1        /* jac_elementwise_batched */
+#define PF_TUNE_YBUS 2       /* jac_ybus_batched */
+#define PF_TUNE_ADJOINT 4    /* adjoint_elementwise */
+pf_status batch_autotune(pf_batch *batch, const double *vm, const double *va, int32_t kernels, int32_t reps,
+                         pf_stream stream, pf_batch_config *best);
+
+/*
+ * The tuning-cache key of a batch: the GPU's name, the kernel family and the
+ * size class (buses and scenarios rounded up to powers of two, with or
+ * without outages), as a NUL-terminated string in buf[0 .. len).
+ */
+pf_status batch_tune_key(const pf_batch *batch, char *buf, int32_t len);
+
+/*
+ * The tuning cache itself, a JSON file mapping keys to pf_batch_config
+ * fields: look a key up (*found = 1 and *cfg filled when present; a missing
+ * file is an empty cache), or store a configuration under a key (the file is
+ * rewritten through a temporary and a rename; other keys are kept).  Host
+ * only; keys may not contain '"' or '\\'.
+ */
+pf_status pf_tune_cache_lookup(const char *path, const char *key, pf_batch_config *cfg, int32_t *found);
+pf_status pf_tune_cache_store(const char *path, const char *key, const pf_batch_config *cfg);
 
 /* Device pointer (owned by the batch) to the offsets joff [nscen + 1] of each
    scenario's Jacobian values in the batch's J array. */

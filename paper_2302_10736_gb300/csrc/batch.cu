@@ -33,6 +33,117 @@ static ScenOut scen_outage(const HostTopo &H, int l)
 
 }  // namespace pf
 
+namespace pf {
+
+// The window plan of a batch: windows of at most tb buses and tfac x tb
+// terminals (tfac = 0: the largest of 3, 2, 1 at which four CTAs of the
+// batched Jacobian kernel share an SM's shared memory - its register budget
+// allows four; with three, barrier and load stalls leave more of the FP64
+// pipe idle: 1.53 against 1.47 ms for 1,024 N-1 scenarios of the 10,000-bus
+// grid - else the largest at which one fits).  When the batch has fewer
+// (scenario, window) items than the GPU has SMs, the windows are cut at equal
+// cost into about one item per SM (more CTAs would only make the grid
+// barriers dearer) and the adjoint keeps each item on one CTA (ghost).
+pf_status batch_plan(const Grid *g, int nscen, int tb, int tfac, HostEw &E, bool &ghost)
+{
+    int dev = 0, nsm = 0, smem_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+        return set_error(PF_ECUDA, "batch: cannot query the device");
+    auto smem_of = [](const HostEw &L) {
+        return ew_smem_plan(L.max_nbus, L.max_nt, L.max_L, true).total + kTrigSmem;
+    };
+    const size_t kCtaReserve = 1024;   // shared memory the runtime keeps per resident CTA
+    bool have = false;
+    for (int tf = tfac ? tfac : 3; tf >= (tfac ? tfac : 1); --tf) {
+        HostEw F;
+        if (pf_status hs = host_ew(g->topo, tb, F, tf)) return hs;
+        const size_t sm = smem_of(F);
+        if (sm > kMaxSmem) continue;
+        const bool four = 4 * (sm + kCtaReserve) <= (size_t)smem_sm;
+        if (!have || four) {
+            E = std::move(F);
+            have = true;
+        }
+        if (four) break;
+    }
+    if (!have) return set_error(PF_EUNSUPPORTED, "batch: a window of %d buses / %d terminals per thread exceeds "
+                                "shared memory", tb, tfac);
+    ghost = false;
+    if (nscen > 0 && (long long)nscen * E.nwin < nsm) {
+        HostEw F;
+        const int target = (nsm + nscen - 1) / nscen;
+        if (host_ew(g->topo, tb, F, E.tfac, target) == PF_OK && F.nwin > E.nwin && smem_of(F) <= kMaxSmem)
+            E = std::move(F);
+        // latency-bound: the adjoint keeps each item on one CTA (k_adj1), which
+        // forms its window's phasors itself (with its ghost buses) instead of a
+        // separate phase and grid barrier
+        ghost = adj1_smem_plan(E.max_nbus, E.max_nt, E.max_nph).total <= kMaxSmem;
+    }
+#ifdef PF_SELFCHECK
+    if (pf_status hs = host_selfcheck(g->topo, E)) return hs;
+#endif
+    return PF_OK;
+}
+
+// Upload a window plan, replacing the batch's previous one (synchronizes st).
+pf_status batch_upload(Batch *b, HostEw &E, bool ghost, cudaStream_t st)
+{
+    const Grid *g = b->g;
+    // the small-batch adjoint's per-window branch lists; their counts ride in
+    // the otherwise unused desc[2w+1].w
+    std::vector<int2> brl;
+    int max_nbr = 0;
+    if (ghost) {
+        std::vector<int> nbr;
+        if (pf_status hs = host_window_branches(g->topo, E, brl, nbr, max_nbr)) return hs;
+        for (int w = 0; w < E.nwin; ++w) E.desc[2 * w + 1].w = nbr[w];
+    }
+    cudaError_t e = cudaStreamSynchronize(st);   // no launch in flight still reads the old plan
+    if (e != cudaSuccess) return cuda_error(e, "batch layout");
+    for (void *p : {(void *)b->win_bus, (void *)b->rorder, (void *)b->desc, (void *)b->slotbus, (void *)b->tloc,
+                    (void *)b->brl, (void *)b->lpart})
+        b->arena.release(p);
+    b->win_bus = b->rorder = b->slotbus = nullptr;
+    b->desc = nullptr;
+    b->tloc = b->brl = nullptr;
+    b->lpart = nullptr;
+    const size_t nw = (size_t)std::max(b->S, 1) * std::max(E.nwin, 1);
+    if ((e = b->arena.alloc(&b->win_bus, E.win_bus.size())) ||
+        (e = cudaMemcpyAsync(b->win_bus, E.win_bus.data(), sizeof(int) * E.win_bus.size(), cudaMemcpyHostToDevice,
+                             st)) ||
+        (e = b->arena.alloc(&b->rorder, E.rorder.size())) ||
+        (e = cudaMemcpyAsync(b->rorder, E.rorder.data(), sizeof(int) * E.rorder.size(), cudaMemcpyHostToDevice,
+                             st)) ||
+        (ghost && ((e = b->arena.alloc(&b->desc, E.desc.size())) || (e = b->arena.alloc(&b->slotbus, E.slotbus.size())) ||
+                   (e = b->arena.alloc(&b->tloc, E.tloc.size())) ||
+                   (e = cudaMemcpyAsync(b->desc, E.desc.data(), sizeof(int4) * E.desc.size(), cudaMemcpyHostToDevice,
+                                        st)) ||
+                   (e = cudaMemcpyAsync(b->slotbus, E.slotbus.data(), sizeof(int) * E.slotbus.size(),
+                                        cudaMemcpyHostToDevice, st)) ||
+                   (e = cudaMemcpyAsync(b->tloc, E.tloc.data(), sizeof(int2) * E.tloc.size(), cudaMemcpyHostToDevice,
+                                        st)) ||
+                   (e = b->arena.alloc(&b->brl, std::max<size_t>(brl.size(), 1))) ||
+                   (!brl.empty() &&
+                    (e = cudaMemcpyAsync(b->brl, brl.data(), sizeof(int2) * brl.size(), cudaMemcpyHostToDevice, st))))) ||
+        (e = b->arena.alloc(&b->lpart, nw)) || (e = cudaStreamSynchronize(st)))
+        return cuda_error(e, "batch layout");
+    b->tb = E.tb;
+    b->tfac = E.tfac;
+    b->nwin = E.nwin;
+    b->max_L = E.max_L;
+    b->max_nt = E.max_nt;
+    b->max_nbus = E.max_nbus;
+    b->ghost = ghost ? 1 : 0;
+    b->max_nph = E.max_nph;
+    b->max_nbr = max_nbr;
+    for (int &r : b->resident) r = 0;   // shared memory and CTA counts change with the plan
+    return PF_OK;
+}
+
+}  // namespace pf
+
 PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outage, pf_stream stream, pf_batch **out)
 {
     if (!out) return set_error(PF_EINVAL, "batch_create: out is NULL");
@@ -54,107 +165,36 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
     for (int s = 0; s < nscen; ++s) {
         b->h_sc[s] = scen_outage(g->topo, outage ? outage[s] : -1);
         b->h_joff[s + 1] = b->h_joff[s] + 4LL * (g->nnz - 2 * b->h_sc[s].del);
+        b->has_outage |= b->h_sc[s].l >= 0;
     }
-    // The batch's own windows: 256 buses and up to tfac x 256 terminals each,
-    // so that every thread owns a bus in the reduction.  tfac is the largest of
-    // 3, 2, 1 at which four CTAs of the batched Jacobian kernel share an SM's
-    // shared memory (its register budget allows four; with three, barrier and
-    // load stalls leave more of the FP64 pipe idle: 1.53 against 1.47 ms for
-    // 1,024 N-1 scenarios of the 10,000-bus grid), else the largest at which
-    // one fits.  When the batch has fewer (scenario, window) items than the
-    // GPU has SMs, the windows are cut at equal cost into about one item per
-    // SM (more CTAs would only make the grid barriers dearer).
-    int dev = 0, nsm = 0, smem_sm = 0;
+    int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete pb;
         return set_error(PF_ECUDA, "batch_create: cannot query the device");
     }
-    auto smem_of = [](const HostEw &L) {
-        return ew_smem_plan(L.max_nbus, L.max_nt, L.max_L, true).total + kTrigSmem;
-    };
-    const size_t kCtaReserve = 1024;   // shared memory the runtime keeps per resident CTA
+    b->cfg.window = 256;
+    b->cfg.terminals_per_thread = 0;   // chosen by batch_plan
+    b->cfg.ctas_per_sm = 0;
+    b->cfg.adjoint_form = 0;
+    b->cfg.ybus_lanes = g->cfg.ybus_lanes;
+    b->cfg.ybus_block = g->cfg.ybus_block;
+    cudaStream_t st = (cudaStream_t)stream;
     HostEw E;
-    bool have = false;
-    for (int tfac = 3; tfac >= 1; --tfac) {
-        HostEw F;
-        pf_status hs = host_ew(g->topo, 256, F, tfac);
-        if (hs) {
-            delete pb;
-            return hs;
-        }
-        const size_t sm = smem_of(F);
-        if (sm > kMaxSmem) continue;
-        const bool four = 4 * (sm + kCtaReserve) <= (size_t)smem_sm;
-        if (!have || four) {
-            E = std::move(F);
-            have = true;
-        }
-        if (four) break;
-    }
-    if (!have) {
-        delete pb;
-        return set_error(PF_EUNSUPPORTED, "batch_create: a window exceeds shared memory");
-    }
     bool ghost = false;
-    if (nscen > 0 && (long long)nscen * E.nwin < nsm) {
-        HostEw F;
-        const int target = (nsm + nscen - 1) / nscen;
-        if (host_ew(g->topo, 256, F, E.tfac, target) == PF_OK && F.nwin > E.nwin && smem_of(F) <= kMaxSmem)
-            E = std::move(F);
-        // latency-bound: the adjoint keeps each item on one CTA (k_adj1), which
-        // forms its window's phasors itself (with its ghost buses) instead of a
-        // separate phase and grid barrier
-        ghost = adj1_smem_plan(E.max_nbus, E.max_nt, E.max_nph).total <= kMaxSmem;
-    }
-#ifdef PF_SELFCHECK
-    if (pf_status hs = host_selfcheck(g->topo, E)) {
+    pf_status hs = batch_plan(g, nscen, b->cfg.window, 0, E, ghost);
+    if (hs == PF_OK) hs = batch_upload(b, E, ghost, st);
+    if (hs != PF_OK) {
+        b->arena.free_all();
         delete pb;
         return hs;
     }
-#endif
-    b->tb = E.tb;
-    b->nwin = E.nwin;
-    b->max_L = E.max_L;
-    b->max_nt = E.max_nt;
-    b->max_nbus = E.max_nbus;
-    b->ghost = ghost ? 1 : 0;
-    b->max_nph = E.max_nph;
-    // the small-batch adjoint's per-window branch lists; their counts ride in
-    // the otherwise unused desc[2w+1].w
-    std::vector<int2> brl;
-    if (ghost) {
-        std::vector<int> nbr;
-        if (pf_status hs = host_window_branches(g->topo, E, brl, nbr, b->max_nbr)) {
-            delete pb;
-            return hs;
-        }
-        for (int w = 0; w < E.nwin; ++w) E.desc[2 * w + 1].w = nbr[w];
-    }
-    cudaStream_t st = (cudaStream_t)stream;
+    b->cfg.terminals_per_thread = b->tfac;
     const size_t n = (size_t)nscen * g->nb;
-    const size_t nw = (size_t)nscen * std::max(b->nwin, 1);
     cudaError_t e = cudaSuccess;
     if ((e = b->arena.alloc(&b->sc, std::max(nscen, 1))) || (e = b->arena.alloc(&b->joff, nscen + 1)) ||
-        (e = b->arena.alloc(&b->win_bus, E.win_bus.size())) ||
-        (e = cudaMemcpyAsync(b->win_bus, E.win_bus.data(), sizeof(int) * E.win_bus.size(), cudaMemcpyHostToDevice,
-                             st)) ||
-        (e = b->arena.alloc(&b->rorder, E.rorder.size())) ||
-        (e = cudaMemcpyAsync(b->rorder, E.rorder.data(), sizeof(int) * E.rorder.size(), cudaMemcpyHostToDevice,
-                             st)) ||
-        (ghost && ((e = b->arena.alloc(&b->desc, E.desc.size())) || (e = b->arena.alloc(&b->slotbus, E.slotbus.size())) ||
-                   (e = b->arena.alloc(&b->tloc, E.tloc.size())) ||
-                   (e = cudaMemcpyAsync(b->desc, E.desc.data(), sizeof(int4) * E.desc.size(), cudaMemcpyHostToDevice,
-                                        st)) ||
-                   (e = cudaMemcpyAsync(b->slotbus, E.slotbus.data(), sizeof(int) * E.slotbus.size(),
-                                        cudaMemcpyHostToDevice, st)) ||
-                   (e = cudaMemcpyAsync(b->tloc, E.tloc.data(), sizeof(int2) * E.tloc.size(), cudaMemcpyHostToDevice,
-                                        st)) ||
-                   (e = b->arena.alloc(&b->brl, brl.size())) ||
-                   (e = cudaMemcpyAsync(b->brl, brl.data(), sizeof(int2) * brl.size(), cudaMemcpyHostToDevice, st)))) ||
         (e = b->arena.alloc(&b->U, n)) || (e = b->arena.alloc(&b->V, n)) || (e = b->arena.alloc(&b->r, n)) ||
-        (e = b->arena.alloc(&b->lpart, nw)) || (e = b->arena.alloc(&b->lscen, std::max(nscen, 1))) ||
+        (e = b->arena.alloc(&b->lscen, std::max(nscen, 1))) ||
         (nscen && (e = cudaMemcpyAsync(b->sc, b->h_sc.data(), sizeof(ScenOut) * nscen, cudaMemcpyHostToDevice, st))) ||
         (e = cudaMemcpyAsync(b->joff, b->h_joff.data(), sizeof(long long) * (nscen + 1), cudaMemcpyHostToDevice,
                              st)) ||
@@ -162,6 +202,12 @@ PF_API pf_status batch_create(pf_grid *grid, int32_t nscen, const int32_t *outag
         b->arena.free_all();
         delete pb;
         return cuda_error(e, "batch_create");
+    }
+    // a tuned configuration for this GPU and size class, if a cache file holds one
+    if ((hs = batch_apply_cached(b, st)) != PF_OK) {
+        b->arena.free_all();
+        delete pb;
+        return hs;
     }
     *out = pb;
     return PF_OK;

@@ -957,15 +957,18 @@ static cudaError_t coop_resident(K kernel, int &resident, int tb, size_t smem)
     return cudaSuccess;
 }
 
-// Cooperative launch of min(items, co-resident) CTAs of tb threads.
+// Cooperative launch of min(items, co-resident, cap) CTAs of tb threads (cap
+// <= 0: none).
 template <typename K>
 static cudaError_t coop_launch(K kernel, int &resident, int tb, size_t smem, long long items, cudaStream_t s,
-                               const BatchArgs &a)
+                               const BatchArgs &a, long long cap = 0)
 {
     cudaError_t e = coop_resident(kernel, resident, tb, smem);
     if (e != cudaSuccess) return e;
+    long long grid = std::min<long long>(items, resident);
+    if (cap > 0) grid = std::min(grid, cap);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)std::max<long long>(1, std::min<long long>(items, resident)));
+    cfg.gridDim = dim3((unsigned)std::max<long long>(1, grid));
     cfg.blockDim = dim3((unsigned)tb);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -991,8 +994,9 @@ cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, jac ? a.max_L : 0, jac);
     const size_t smem = sp.total + kTrigSmem;
     const long long items = (long long)b->S * b->nwin;
-    if (jac) return coop_launch(k_ewb<true>, b->resident[1], b->tb, smem, items, s, a);
-    return coop_launch(k_ewb<false>, b->resident[0], b->tb, smem, items, s, a);
+    const long long cap = (long long)b->cfg.ctas_per_sm * b->nsm;
+    if (jac) return coop_launch(k_ewb<true>, b->resident[1], b->tb, smem, items, s, a, cap);
+    return coop_launch(k_ewb<false>, b->resident[0], b->tb, smem, items, s, a, cap);
 }
 
 // The adjoint (grad) or the loss alone: one item per CTA (k_adj1) when every
@@ -1005,7 +1009,7 @@ static cudaError_t launch_adj(Batch *b, BatchArgs &a, cudaStream_t s)
     const int r1 = GRAD ? 3 : 5, rn = GRAD ? 2 : 4;   // resident-CTA caches of the four kernels
     const long long branch_ctas1 = GRAD ? (g->nl + kAdj1Threads - 1) / kAdj1Threads : 0;
     const long long branch_ctas = GRAD ? (g->nl + b->tb - 1) / b->tb : 0;
-    if (b->ghost) {
+    if (b->ghost && b->cfg.adjoint_form == 0) {
         // the form is chosen by the gradient kernel's residency for both, so that
         // the loss alone and the adjoint sum the same terms in the same order
         const size_t smem = adj1_smem_plan(a.max_nbus, a.max_nt, a.max_nph).total;
@@ -1017,7 +1021,8 @@ static cudaError_t launch_adj(Batch *b, BatchArgs &a, cudaStream_t s)
                                std::max<long long>(items, branch_ctas1), s, a);
     }
     const size_t smem = ew_smem_plan(a.max_nbus, a.max_nt, 0, false).total + kTrigSmem;
-    return coop_launch(k_adj<GRAD>, b->resident[rn], b->tb, smem, std::max<long long>(items, branch_ctas), s, a);
+    return coop_launch(k_adj<GRAD>, b->resident[rn], b->tb, smem, std::max<long long>(items, branch_ctas), s, a,
+                       (long long)b->cfg.ctas_per_sm * b->nsm);
 }
 
 static BatchArgs loss_args(Batch *b, const double *vm, const double *va, const double *Ps, const double *Qs,

@@ -259,7 +259,7 @@ static cudaError_t inj_b(const Batch *b, double *P, double *Q, cudaStream_t s)
 {
     const Grid *g = b->g;
     const long long threads = (long long)b->S * g->nb * W;
-    const int blk = g->cfg.ybus_block;
+    const int blk = b->cfg.ybus_block;
     return launch_k(k_inj_ybus_b<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, b->S, g->nb,
                     (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, (const double2 *)g->tself,
                     (const double2 *)g->tcoup, (const ScenOut *)b->sc, (const double2 *)b->V, P, Q);
@@ -270,7 +270,7 @@ static cudaError_t jac_b(const Batch *b, double *P, double *Q, double *J, cudaSt
 {
     const Grid *g = b->g;
     const long long threads = (long long)b->S * g->nb * W;
-    const int blk = g->cfg.ybus_block;
+    const int blk = b->cfg.ybus_block;
     return launch_k(k_jac_ybus_b<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, b->S, g->nb, g->nnz,
                     (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, (const double2 *)g->tself,
                     (const double2 *)g->tcoup, (const ScenOut *)b->sc, (const long long *)b->joff,
@@ -285,7 +285,7 @@ cudaError_t launch_ybus_batched(Batch *b, bool jac, const double *vm, const doub
     cudaError_t e = launch_phasor(b->S * g->nb, vm, va, b->U, b->V, s);
     if (e != cudaSuccess) return e;
     if (jac) {
-        switch (g->cfg.ybus_lanes) {
+        switch (b->cfg.ybus_lanes) {
         case 1: return jac_b<1>(b, P, Q, J, s);
         case 2: return jac_b<2>(b, P, Q, J, s);
         case 4: return jac_b<4>(b, P, Q, J, s);
@@ -294,7 +294,7 @@ cudaError_t launch_ybus_batched(Batch *b, bool jac, const double *vm, const doub
         default: return jac_b<32>(b, P, Q, J, s);
         }
     }
-    switch (g->cfg.ybus_lanes) {
+    switch (b->cfg.ybus_lanes) {
     case 1: return inj_b<1>(b, P, Q, s);
     case 2: return inj_b<2>(b, P, Q, s);
     case 4: return inj_b<4>(b, P, Q, s);

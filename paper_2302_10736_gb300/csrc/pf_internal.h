@@ -372,6 +372,9 @@ struct ScenOut {
 struct Batch {
     Grid *g = nullptr;
     int S = 0;
+    int nsm = 0;                     // SMs of the device the batch was made on
+    int has_outage = 0;              // some scenario removes a branch
+    pf_batch_config cfg{};           // launch configuration (batch_set_config, batch_autotune)
     DevArena arena;
     std::vector<ScenOut> h_sc;
     std::vector<long long> h_joff;   // [S+1]
@@ -387,7 +390,7 @@ struct Batch {
     int resident[6] = {0, 0, 0, 0, 0, 0};
     // the batch's own element-wise windows: throughput-bound, so every thread
     // owns a bus in the reduction and loops over up to tfac terminals
-    int tb = 0, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0;
+    int tb = 0, tfac = 1, nwin = 0, max_L = 0, max_nt = 0, max_nbus = 0;
     int *win_bus = nullptr;          // [nwin+1]
     int *rorder = nullptr;           // [nb] the reductions' thread-to-bus map (HostEw::rorder)
     // small batches (about one item per SM): the adjoint runs k_adj1, one
@@ -400,6 +403,14 @@ struct Batch {
     int max_nbr = 0;
     int2 *brl = nullptr;             // [nwin * max_nbr] the window's branches (host_window_branches)
 };
+
+// the batch's window plan for a configuration (batch.cu), its upload, and the
+// tuned configuration of the batch's size class from the cache file named by
+// PFGRID_TUNE_CACHE, if any (batch_tune.cu)
+pf_status batch_plan(const Grid *g, int nscen, int tb, int tfac, HostEw &E, bool &ghost);
+pf_status batch_upload(Batch *b, HostEw &E, bool ghost, cudaStream_t st);
+pf_status batch_apply_cached(Batch *b, cudaStream_t st);
+pf_status batch_apply_config(Batch *b, const pf_batch_config &c, cudaStream_t st);
 
 cudaError_t launch_ew_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,
                               double *J, cudaStream_t s);

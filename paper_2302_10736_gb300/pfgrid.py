@@ -41,6 +41,14 @@ class pf_config(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class pf_batch_config(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int32), ("terminals_per_thread", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("adjoint_form", ctypes.c_int32), ("ybus_lanes", ctypes.c_int32), ("ybus_block", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class pf_trace_rec(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("ms", ctypes.c_float)]
 
@@ -522,6 +530,13 @@ def _bind_batches():
         "inj_ybus_batched": (st, [vp, vp, vp, vp, vp, vp]),
         "jac_ybus_batched": (st, [vp, vp, vp, vp, vp, vp, vp]),
         "adjoint_elementwise": (st, [vp] * 17),
+        "batch_get_config": (st, [vp, ctypes.POINTER(pf_batch_config)]),
+        "batch_set_config": (st, [vp, ctypes.POINTER(pf_batch_config), vp]),
+        "batch_autotune": (st, [vp, vp, vp, i32, i32, vp, ctypes.POINTER(pf_batch_config)]),
+        "batch_tune_key": (st, [vp, ctypes.c_char_p, i32]),
+        "pf_tune_cache_lookup": (st, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(pf_batch_config),
+                                      ctypes.POINTER(i32)]),
+        "pf_tune_cache_store": (st, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(pf_batch_config)]),
         "loss_elementwise": (st, [vp] * 10),
     }
     for name, (res, args) in sig.items():
@@ -561,6 +576,50 @@ def batch_create(grid, nscen, outage=None, stream=None):
     out = ctypes.c_void_p()
     _check(_lib.batch_create(grid.handle, int(nscen), p, _stream(stream), ctypes.byref(out)), "batch_create")
     return Batch(out.value, grid)
+
+
+def batch_get_config(batch):
+    c = pf_batch_config()
+    _check(_lib.batch_get_config(batch.handle, ctypes.byref(c)), "batch_get_config")
+    return c.as_dict()
+
+
+def batch_set_config(batch, stream=None, **kw):
+    c = pf_batch_config(**{**batch_get_config(batch), **kw})
+    _check(_lib.batch_set_config(batch.handle, ctypes.byref(c), _stream(stream)), "batch_set_config")
+
+
+PF_TUNE_JAC, PF_TUNE_YBUS, PF_TUNE_ADJOINT = 1, 2, 4
+
+
+def batch_autotune(batch, vm, va, reps=5, kernels=0, stream=None):
+    """Tune the batch's launch shapes on the states vm, va for the kernels in
+    `kernels` (PF_TUNE_* bits, 0 = Jacobians of both methods); returns the
+    chosen configuration (stored in the PFGRID_TUNE_CACHE file when set)."""
+    n = batch.nscen * batch.grid.nb
+    c = pf_batch_config()
+    _check(_lib.batch_autotune(batch.handle, _dptr(vm, "vm", n), _dptr(va, "va", n), int(kernels), int(reps),
+                               _stream(stream), ctypes.byref(c)), "batch_autotune")
+    return c.as_dict()
+
+
+def batch_tune_key(batch):
+    buf = ctypes.create_string_buffer(512)
+    _check(_lib.batch_tune_key(batch.handle, buf, 512), "batch_tune_key")
+    return buf.value.decode()
+
+
+def tune_cache_lookup(path, key):
+    """The configuration stored under key in the tuning cache file, or None."""
+    c, found = pf_batch_config(), ctypes.c_int32()
+    _check(_lib.pf_tune_cache_lookup(os.fsencode(path), key.encode(), ctypes.byref(c), ctypes.byref(found)),
+           "pf_tune_cache_lookup")
+    return c.as_dict() if found.value else None
+
+
+def tune_cache_store(path, key, cfg):
+    c = pf_batch_config(**cfg)
+    _check(_lib.pf_tune_cache_store(os.fsencode(path), key.encode(), ctypes.byref(c)), "pf_tune_cache_store")
 
 
 def batch_jac_offsets(batch):

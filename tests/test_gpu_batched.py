@@ -470,6 +470,94 @@ def test_mismatch_loss_forward_runs_the_loss_alone(pf):
     assert vm_t.grad is not None and g_t.grad is not None
 
 
+def test_every_batch_launch_shape_gives_the_same_results(pf):
+    """Every launch configuration the autotuner may pick (window size x
+    terminal cap x CTAs per SM, both adjoint forms, every batched-Ybus lane
+    count): the batched Jacobians are bitwise those of the default shape (the
+    sums per bus do not depend on the windows), the adjoint matches the oracle
+    within 1e-12."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    gr, vm, va, Ps, Qs, wP, wQ = _adjoint_case(2000, 2700, 67, 4)
+    nonbridge = np.flatnonzero(~synth.bridges(2000, gr["f"], gr["t"]))
+    outage = np.array([-1, nonbridge[3], nonbridge[70], -1], np.int32)
+    grid = pf.ybus_build(gr)
+    batch = pf.batch_create(grid, 4, outage)
+    args = [_d(x) for x in (vm.ravel(), va.ravel())]
+    spec = [_d(x) for x in (Ps, Qs, wP, wQ)]
+    n = 4 * 2000
+
+    def run():
+        P, Q = torch.empty(n, dtype=torch.float64, device="cuda"), torch.empty(n, dtype=torch.float64, device="cuda")
+        J = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
+        Py, Qy = torch.empty_like(P), torch.empty_like(Q)
+        Jy = torch.empty_like(J)
+        pf.jac_elementwise_batched(batch, *args, P, Q, J)
+        pf.jac_ybus_batched(batch, *args, Py, Qy, Jy)
+        L = torch.empty(4, dtype=torch.float64, device="cuda")
+        gvm, gva = torch.empty(n, dtype=torch.float64, device="cuda"), torch.empty(n, dtype=torch.float64, device="cuda")
+        gp = [torch.empty(gr["nl"], dtype=torch.float64, device="cuda") for _ in range(4)]
+        pf.adjoint_elementwise(batch, *args, *spec, L, gvm, gva, *gp)
+        torch.cuda.synchronize()
+        pf.grid_check_error(grid)
+        return [x.cpu().numpy() for x in (P, Q, J, Py, Qy, Jy)], [x.cpu().numpy() for x in [L, gvm, gva] + gp]
+
+    ref, _ = run()
+    Lr, gvmr, gvar, gpr = oracle_adjoint(gr, vm, va, Ps, Qs, wP, wQ, outage)
+    shapes = 0
+    for window in (128, 256):
+        for tpt in (1, 2, 3):
+            for cps in (0, 1, 3):
+                for form in (0, 1):
+                    lanes = (1, 2, 4, 8, 16, 32)[shapes % 6]
+                    try:
+                        pf.batch_set_config(batch, window=window, terminals_per_thread=tpt, ctas_per_sm=cps,
+                                            adjoint_form=form, ybus_lanes=lanes, ybus_block=128 * (1 + shapes % 3))
+                    except pf.PfError as e:   # a window shape that does not fit in shared memory
+                        assert e.status == pf.PF_EUNSUPPORTED
+                        continue
+                    got, adj = run()
+                    cfg = pf.batch_get_config(batch)
+                    for a, b in zip(got[:3], ref[:3]):
+                        assert np.array_equal(a, b), cfg
+                    for a, b in zip(got[3:], ref[3:]):
+                        assert relerr(a, b) <= TOL, cfg
+                    L, gvm, gva = adj[:3]
+                    assert relerr(L, Lr) <= TOL and relerr(gvm.reshape(4, 2000), gvmr) <= TOL, cfg
+                    assert relerr(gva.reshape(4, 2000), gvar) <= TOL, cfg
+                    for a, b in zip(adj[3:], gpr):
+                        assert relerr(a, b) <= TOL, cfg
+                    shapes += 1
+    assert shapes >= 12
+
+
+def test_batch_autotune_and_its_cache(pf, tmp_path, monkeypatch):
+    """batch_autotune picks a valid configuration, stores it under the
+    batch's key in the PFGRID_TUNE_CACHE file, and a new batch of the same
+    size class starts with it; results stay bitwise those of the default."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    path = str(tmp_path / "tune.json")
+    monkeypatch.setenv("PFGRID_TUNE_CACHE", path)
+    gr = random_grid(3000, 4100, 68)
+    nonbridge = np.flatnonzero(~synth.bridges(3000, gr["f"], gr["t"]))
+    outage = np.array(nonbridge[:16], np.int32)
+    vm, va = synth.voltages(3000, 16, 68, 0, 0.93, 1.07, 0.25)
+    grid = pf.ybus_build(gr)
+    batch = pf.batch_create(grid, 16, outage)
+    J0 = torch.empty(batch.nnzJ_total, dtype=torch.float64, device="cuda")
+    pf.jac_elementwise_batched(batch, _d(vm.ravel()), _d(va.ravel()), None, None, J0)
+    best = pf.batch_autotune(batch, _d(vm.ravel()), _d(va.ravel()), reps=2)
+    assert best == pf.batch_get_config(batch)
+    assert pf.tune_cache_lookup(path, pf.batch_tune_key(batch)) == best
+    J1 = torch.empty_like(J0)
+    pf.jac_elementwise_batched(batch, _d(vm.ravel()), _d(va.ravel()), None, None, J1)
+    batch2 = pf.batch_create(grid, 16, outage[::-1].copy())
+    assert pf.batch_get_config(batch2) == best
+    torch.cuda.synchronize()
+    assert torch.equal(J0, J1)
+
+
 def test_cuda_graph_capture_and_replay(pf):
     """The batched evaluation, the adjoint and the single evaluation can be
     captured in a CUDA graph (after one eager call) and replayed; replays give
