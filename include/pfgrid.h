@@ -568,6 +568,23 @@ pf_status jac_target(pf_grid *grid, int32_t method, const double *vm, const doub
                      double *Jt, pf_stream stream);
 
 /*
+ * Solve J_r dx = F for the reduced Newton system of the grid's bus types
+ * (the step the paper hands to a sparse direct solver, KLU): Jr [nnz] holds
+ * the reduced Jacobian's values in jac_reduced's CSC order, F [n] the right-hand
+ * side, dx [n] receives the solution (device pointers).  Sparse LU without
+ * pivoting on a fill-reducing order: the first call after grid_set_bus_types
+ * analyses the pattern on the host (minimum-degree order of the buses,
+ * symbolic factorization, level schedule), allocates the factor storage and
+ * synchronizes; make it before any stream capture.  Every later call is one
+ * cooperative launch: numeric factorization with the forward solve, then the
+ * backward solve, bitwise repeatable.  A zero or non-finite pivot sets the
+ * grid's device error word (grid_check_error reports PF_EDEVICE); no pivoting
+ * means the matrix must admit LU in that order, which the power-flow Jacobians
+ * of this library's grids do (their 2 x 2 bus blocks dominate).
+ */
+pf_status jac_reduced_solve(pf_grid *grid, const double *Jr, const double *F, double *dx, pf_stream stream);
+
+/*
  * Newton-Raphson power flow on the GPU (not in the paper, which stops at the
  * Jacobian a Newton step needs): starting from vm, va [nb] (device, updated
  * in place), repeat
@@ -635,7 +652,8 @@ pf_status pf_debug_fail_allocations(int32_t after);
 #define PF_K_JAC_YBUS_BATCHED 9
 #define PF_K_REDUCE 10       /* gather of the reduced Jacobian and mismatch vector */
 #define PF_K_LOSS 11         /* the mismatch loss alone (loss_elementwise) */
-#define PF_K_COUNT 12
+#define PF_K_LU 12           /* sparse LU solve of the reduced system (jac_reduced_solve) */
+#define PF_K_COUNT 13
 
 typedef struct {
     int32_t kernel;          /* PF_K_* */

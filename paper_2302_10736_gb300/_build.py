@@ -88,7 +88,7 @@ def build_pfgrid(force=False, verbose=False, extra_flags=(), phase_probe=False):
         lib64 = os.path.join(_cuda_home(), "lib64")
         tmp = lib + ".tmp"
         _run([nvcc, "-shared", "-o", tmp] + objs + ARCH +
-             ["-cudart", "shared", "-lcusolver", "-lcusparse", "-Xlinker", "-rpath," + lib64])
+             ["-cudart", "shared", "-Xlinker", "-rpath," + lib64])
         os.replace(tmp, lib)
         return lib
 

@@ -349,7 +349,6 @@ PF_API void grid_destroy(pf_grid *grid)
 {
     if (!grid) return;
     trace_free(&grid->g);
-    newton_free(&grid->g);
     grid->g.arena.free_all();
     delete grid;
 }
@@ -608,6 +607,8 @@ PF_API pf_status grid_check_error(pf_grid *grid, pf_stream stream)
     PF_CUDA(cudaMemsetAsync(grid->g.bar, 0, kBarWords * sizeof(unsigned int), s));
     PF_CUDA(cudaStreamSynchronize(s));
     if (h == DEV_TIMEOUT) return set_error(PF_ETIMEOUT, "a device-side wait gave up (error word %d)", h);
+    if (h == DEV_SINGULAR)
+        return set_error(PF_EDEVICE, "jac_reduced_solve met a zero or non-finite pivot (error word %d)", h);
     return set_error(PF_EDEVICE, "a kernel reported device error word %d", h);
 }
 
@@ -719,7 +720,7 @@ PF_API const char *pf_kernel_name(int32_t k)
 {
     static const char *names[PF_K_COUNT] = {"phasor",         "inj_ybus",       "jac_ybus",        "inj_ew",
                                             "jac_ew",         "inj_ew_batched", "jac_ew_batched",  "adjoint",
-                                            "inj_ybus_batched", "jac_ybus_batched", "reduce", "loss"};
+                                            "inj_ybus_batched", "jac_ybus_batched", "reduce", "loss", "lu"};
     return (k >= 0 && k < PF_K_COUNT) ? names[k] : "?";
 }
 

@@ -1,0 +1,586 @@
+// lu.cu - sparse LU solve of the reduced Newton system J_r dx = F on the GPU
+// (the paper hands the Jacobian to a sparse direct solver, KLU, and does not
+// study the solve; this is this library's own).
+//
+// Analysis (host, once per set of bus types):
+//   * J_r is structurally symmetric when equation P_i is paired with unknown
+//     theta_i and Q_i with v_i, so its pattern is that of a graph on the
+//     buses; the buses are ordered by minimum degree (each elimination joins
+//     the eliminated bus's neighbours into a clique; ties to the lowest bus),
+//     which keeps the factor close to the matrix on power grids (about 1.5
+//     times its entries on the synthetic grids), and a bus's unknowns stay
+//     adjacent (theta, then v).
+//   * Symbolic factorization of the permuted pattern: the elimination tree and
+//     the pattern of L by row subtrees; U has the transposed pattern, so one
+//     index structure (CSC of L) serves both factors: Lx[p] = L(Li[p], j) and
+//     Ux[p] = U(j, Li[p]) for p in Lp[j] .. Lp[j+1].
+//   * The columns grouped by height in the elimination tree: a column depends
+//     only on its descendants, which are all lower.
+//
+// Numeric phase (GPU, one cooperative launch per solve), left-looking Crout
+// factorization without pivoting in gather form: the analysis lists, for every
+// factor slot (i, j), the pairs of slots (L(i, k), U(k, j)) - and for the
+// mirrored U(j, i) the pairs (L(j, k), U(k, i)) - over the k below j that
+// update it, ascending, so every slot is one independent sum:
+//   d   = A(j, j) - sum_k L(j, k) U(k, j)          U(j, j) = d
+//   y_j = F_j    - sum_k L(j, k) y_k               (forward solve, fused)
+//   L(i, j) = (A(i, j) - sum_k L(i, k) U(k, j)) / d,  U(j, i) = A(j, i) - sum_k L(j, k) U(k, i)
+// then the backward solve x_j = (y_j - sum_i U(j, i) x_i) / U(j, j) from the
+// root down.  Levels are separated by grid barriers (bounded waits).  Wide
+// levels give a warp to a column (a lane per slot); on the narrow top of the
+// tree, where the dependency chain is, every slot of a level's columns gets a
+// warp of its own (its lanes splitting the slot's sum; each warp forms its
+// column's pivot itself, the same way), and the backward solve of that part
+// runs in one CTA with CTA barriers.  Every gather issues four loads per lane
+// before using them.  Every sum has a fixed order (sequential, or lane-strided
+// partial sums joined by a fixed shuffle tree): the results are bitwise
+// repeatable.  Values written by
+// other CTAs are read with L1-bypassing loads.  A zero or non-finite pivot
+// sets the grid's error word (no trap).
+#include <algorithm>
+#include <set>
+#include <vector>
+
+#include "fastmath.cuh"
+#include "pf_internal.h"
+#include "ptx.cuh"
+
+namespace pf {
+
+namespace {
+
+constexpr uint64_t kLuBarrierNs = 2000000000ull;   // bounded grid-barrier wait (2 s)
+constexpr int kLuThreads = 512;
+constexpr int kLuChainCols = 4;   // levels at most this wide at the top go to one CTA
+
+struct LuArgs {
+    int n, nnzA, H, chain;
+    const int *Lp, *Li, *Rp, *Rk, *Rq, *lvl_ptr, *lvl_col, *perm, *amap, *gptr, *item_ptr;
+    const int2 *gsrc;    // per update term of a slot: {L(i, k) slot, U(k, j) slot}
+    const int2 *items;   // narrow levels: {column, slot or -1} per warp item
+    const double *A, *F;
+    double *Lx, *Ux, *D, *y, *dx;
+    unsigned int *bar;
+    int *err;
+};
+
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+
+__device__ __forceinline__ double warp_sum_d(double x)
+{
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+}
+
+__device__ __forceinline__ void pivot_check(const LuArgs &a, double d)
+{
+    if (!(fabs(d) > 0.0) || !isfinite(d)) atomicExch(a.err, DEV_SINGULAR);
+}
+
+// sum over g in [g0, g1) of Lx[src[g].x] Ux[src[g].y] (and, with `mirror`,
+// of Lx[src[g].y] Ux[src[g].x]) by the lanes of a warp, lane-strided, four
+// terms in flight per lane, joined by a fixed shuffle tree (all lanes get it)
+__device__ __forceinline__ double2 warp_dot_pairs(const LuArgs &a, int g0, int g1, int lane)
+{
+    double sl = 0.0, su = 0.0;
+    for (int g = g0 + lane; g < g1; g += 128) {
+        int2 t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = g + 32 * u < g1 ? a.gsrc[g + 32 * u] : make_int2(-1, -1);
+        double lx[4], uy[4], ly[4], ux[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (t[u].x >= 0) {
+                lx[u] = ldcg(a.Lx + t[u].x);
+                uy[u] = ldcg(a.Ux + t[u].y);
+                ly[u] = ldcg(a.Lx + t[u].y);
+                ux[u] = ldcg(a.Ux + t[u].x);
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (t[u].x >= 0) {
+                sl = fma(lx[u], uy[u], sl);
+                su = fma(ly[u], ux[u], su);
+            }
+    }
+    return make_double2(warp_sum_d(sl), warp_sum_d(su));
+}
+
+// the pivot sum sum_k L(j, k) U(k, j) and the forward term sum_k L(j, k) y_k of
+// column j by a warp (the same lane order as warp_dot_pairs)
+__device__ __forceinline__ double2 warp_pivot_terms(const LuArgs &a, int j, int lane)
+{
+    double dd = 0.0, yy = 0.0;
+    const int r1 = a.Rp[j + 1];
+    for (int r = a.Rp[j] + lane; r < r1; r += 128) {
+        int q[4], k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            q[u] = r + 32 * u < r1 ? a.Rq[r + 32 * u] : -1;
+            k[u] = r + 32 * u < r1 ? a.Rk[r + 32 * u] : 0;
+        }
+        double l[4], uu[4], yk[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q[u] >= 0) {
+                l[u] = ldcg(a.Lx + q[u]);
+                uu[u] = ldcg(a.Ux + q[u]);
+                yk[u] = ldcg(a.y + k[u]);
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q[u] >= 0) {
+                dd = fma(l[u], uu[u], dd);
+                yy = fma(l[u], yk[u], yy);
+            }
+    }
+    return make_double2(warp_sum_d(dd), warp_sum_d(yy));
+}
+
+// One column by one warp (wide levels): its pivot, then a lane per slot, the
+// slot's update terms in order, four in flight.
+__device__ __forceinline__ void lu_column_warp(const LuArgs &a, int j, int lane)
+{
+    const double2 t = warp_pivot_terms(a, j, lane);
+    const double d = ldcg(a.D + j) - t.x, yj = ldcg(a.y + j) - t.y;
+    const double inv = fast_rcp(d);
+    for (int p = a.Lp[j] + lane; p < a.Lp[j + 1]; p += 32) {
+        double sl = ldcg(a.Lx + p), su = ldcg(a.Ux + p);
+        const int g1 = a.gptr[p + 1];
+        for (int g = a.gptr[p]; g < g1; g += 4) {
+            int2 s4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s4[u] = g + u < g1 ? a.gsrc[g + u] : make_int2(-1, -1);
+            double lx[4], uy[4], ly[4], ux[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (s4[u].x >= 0) {
+                    lx[u] = ldcg(a.Lx + s4[u].x);
+                    uy[u] = ldcg(a.Ux + s4[u].y);
+                    ly[u] = ldcg(a.Lx + s4[u].y);
+                    ux[u] = ldcg(a.Ux + s4[u].x);
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (s4[u].x >= 0) {
+                    sl = fma(-lx[u], uy[u], sl);
+                    su = fma(-ly[u], ux[u], su);
+                }
+        }
+        a.Lx[p] = sl * inv;
+        a.Ux[p] = su;
+    }
+    if (lane == 0) {
+        pivot_check(a, d);
+        a.D[j] = d;
+        a.y[j] = yj;
+    }
+}
+
+// One item of a narrow level (a warp): slot p of column j (p < 0: the column
+// has no slot below the diagonal); every item of a column forms its pivot the
+// same way, the column's first item also writes the pivot and y_j.
+__device__ __forceinline__ void lu_item(const LuArgs &a, int j, int p, int lane)
+{
+    const double2 t = warp_pivot_terms(a, j, lane);
+    const double d = ldcg(a.D + j) - t.x;
+    if (p >= 0) {
+        const double2 s = warp_dot_pairs(a, a.gptr[p], a.gptr[p + 1], lane);
+        if (lane == 0) {
+            a.Lx[p] = (ldcg(a.Lx + p) - s.x) * fast_rcp(d);
+            a.Ux[p] = ldcg(a.Ux + p) - s.y;
+        }
+    }
+    if (lane == 0 && (p < 0 || p == a.Lp[j])) {
+        pivot_check(a, d);
+        a.D[j] = d;
+        a.y[j] = ldcg(a.y + j) - t.y;
+    }
+}
+
+// x_j of the backward solve, in place of y_j (one warp)
+__device__ __forceinline__ void lu_back(const LuArgs &a, int j, int lane)
+{
+    const int p0 = a.Lp[j], p1 = a.Lp[j + 1];
+    double s = 0.0;
+    for (int p = p0 + lane; p < p1; p += 32) s = fma(ldcg(a.Ux + p), ldcg(a.y + a.Li[p]), s);
+    s = warp_sum_d(s);
+    if (lane == 0) {
+        const double x = (ldcg(a.y + j) - s) * fast_rcp(ldcg(a.D + j));
+        a.y[j] = x;
+        a.dx[a.perm[j]] = x;
+    }
+}
+
+__global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
+{
+    const GridBar gbar = grid_barrier_begin(a.bar);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp_cta = blockDim.x >> 5;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gthreads = (long long)gridDim.x * blockDim.x;
+    const int gwarp = (int)(gtid >> 5), gwarps = (int)(gthreads >> 5);
+    const int nnzL = a.Lp[a.n];
+    unsigned int bk = 0;
+    // ---- the factor storage zeroed, then A and the right-hand side scattered in ----
+    for (long long t = gtid; t < nnzL; t += gthreads) {
+        a.Lx[t] = 0.0;
+        a.Ux[t] = 0.0;
+    }
+    if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
+    for (long long e = gtid; e < a.nnzA; e += gthreads) {
+        const int code = a.amap[e], slot = code >> 2;
+        const double v = a.A[e];
+        if ((code & 3) == 0)
+            a.Lx[slot] = v;
+        else if ((code & 3) == 1)
+            a.Ux[slot] = v;
+        else
+            a.D[slot] = v;
+    }
+    for (long long j = gtid; j < a.n; j += gthreads) a.y[j] = a.F[a.perm[j]];
+    if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
+    // ---- factorization and forward solve, level by level ----
+    for (int h = 0; h < a.chain; ++h) {
+        const int c0 = a.lvl_ptr[h], nc = a.lvl_ptr[h + 1] - c0;
+        for (int t = gwarp; t < nc; t += gwarps) lu_column_warp(a, a.lvl_col[c0 + t], lane);
+        if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
+    }
+    // ---- the narrow top: a warp per (column, slot) item, all CTAs ----
+    for (int h = a.chain; h < a.H; ++h) {
+        const int i0 = a.item_ptr[h - a.chain], ni = a.item_ptr[h - a.chain + 1] - i0;
+        for (int t = gwarp; t < ni; t += gwarps) {
+            const int2 it = a.items[i0 + t];
+            lu_item(a, it.x, it.y, lane);
+        }
+        if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
+    }
+    // ---- the backward solve of the narrow top in CTA 0 (CTA barriers only) ----
+    if (blockIdx.x == 0) {
+        for (int h = a.H - 1; h >= a.chain; --h) {
+            const int c0 = a.lvl_ptr[h], nc = a.lvl_ptr[h + 1] - c0;
+            for (int t = warp; t < nc; t += nwarp_cta) lu_back(a, a.lvl_col[c0 + t], lane);
+            __syncthreads();
+        }
+    }
+    if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
+    // ---- backward solve below the top, from the highest level down ----
+    for (int h = a.chain - 1; h >= 0; --h) {
+        const int c0 = a.lvl_ptr[h], nc = a.lvl_ptr[h + 1] - c0;
+        for (int t = gwarp; t < nc; t += gwarps) lu_back(a, a.lvl_col[c0 + t], lane);
+        if (h > 0 && !grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
+    }
+}
+
+// ------------------------------------------------------------ analysis ----
+
+// Minimum-degree order of an undirected graph (explicit elimination: the
+// neighbours of each eliminated node become a clique; ties to the lowest node).
+std::vector<int> min_degree_order(std::vector<std::vector<int>> adj)
+{
+    const int n = (int)adj.size();
+    std::set<std::pair<int, int>> pq;
+    for (int u = 0; u < n; ++u) pq.insert({(int)adj[u].size(), u});
+    std::vector<char> gone(n, 0);
+    std::vector<int> order;
+    order.reserve(n);
+    std::vector<int> merged;
+    while (!pq.empty()) {
+        const int u = pq.begin()->second;
+        pq.erase(pq.begin());
+        gone[u] = 1;
+        order.push_back(u);
+        const std::vector<int> nb = adj[u];   // sorted, live nodes only
+        for (int v : nb) {
+            pq.erase({(int)adj[v].size(), v});
+            merged.clear();
+            std::set_union(adj[v].begin(), adj[v].end(), nb.begin(), nb.end(), std::back_inserter(merged));
+            adj[v].clear();
+            for (int x : merged)
+                if (x != v && x != u) adj[v].push_back(x);
+            pq.insert({(int)adj[v].size(), v});
+        }
+        adj[u].clear();
+        adj[u].shrink_to_fit();
+    }
+    return order;
+}
+
+}  // namespace
+
+pf_status host_lu(int nb, int n, int npvpq, const std::vector<int> &colptr, const std::vector<int> &rowidx,
+                  const std::vector<int> &fmap, HostLu &L)
+{
+    L = HostLu{};
+    L.n = n;
+    // bus graph of the unknowns' buses (every unknown's bus has a theta unknown)
+    std::vector<int> node(nb, -1), bus_of;
+    for (int k = 0; k < npvpq; ++k) {
+        node[fmap[k]] = (int)bus_of.size();
+        bus_of.push_back(fmap[k]);
+    }
+    const int B = (int)bus_of.size();
+    std::vector<std::vector<int>> adj(B);
+    for (int c = 0; c < n; ++c)
+        for (int p = colptr[c]; p < colptr[c + 1]; ++p) {
+            const int u = node[fmap[rowidx[p]]], v = node[fmap[c]];
+            if (u < 0 || v < 0) return set_error(PF_EINVAL, "jac_reduced_solve: an unknown without a bus angle");
+            if (u != v) {
+                adj[u].push_back(v);
+                adj[v].push_back(u);
+            }
+        }
+    for (auto &a : adj) {
+        std::sort(a.begin(), a.end());
+        a.erase(std::unique(a.begin(), a.end()), a.end());
+    }
+    const std::vector<int> border = min_degree_order(adj);
+    // unknowns in elimination order: each bus's theta, then its v
+    std::vector<int> vidx(nb, -1);
+    for (int k = npvpq; k < n; ++k) vidx[fmap[k]] = k;
+    L.perm.reserve(n);
+    std::vector<int> tidx(nb, -1);
+    for (int k = 0; k < npvpq; ++k) tidx[fmap[k]] = k;
+    for (int u : border) {
+        const int b = bus_of[u];
+        L.perm.push_back(tidx[b]);
+        if (vidx[b] >= 0) L.perm.push_back(vidx[b]);
+    }
+    if ((int)L.perm.size() != n) return set_error(PF_EINVAL, "jac_reduced_solve: unknowns do not match buses");
+    std::vector<int> iperm(n);
+    for (int i = 0; i < n; ++i) iperm[L.perm[i]] = i;
+    // lower pattern of the permuted (symmetrised) matrix, row by row
+    std::vector<std::vector<int>> low(n);
+    for (int c = 0; c < n; ++c)
+        for (int p = colptr[c]; p < colptr[c + 1]; ++p) {
+            const int i = iperm[rowidx[p]], j = iperm[c];
+            if (i > j) low[i].push_back(j);
+            if (j > i) low[j].push_back(i);
+        }
+    for (auto &r : low) {
+        std::sort(r.begin(), r.end());
+        r.erase(std::unique(r.begin(), r.end()), r.end());
+    }
+    // elimination tree and the rows of L by row subtrees
+    std::vector<int> parent(n, -1), flag(n, -1), cnt(n, 0);
+    std::vector<std::vector<int>> lrow(n);
+    for (int i = 0; i < n; ++i) {
+        flag[i] = i;
+        for (int k : low[i]) {
+            while (k != -1 && flag[k] != i) {
+                if (parent[k] == -1) parent[k] = i;
+                lrow[i].push_back(k);
+                cnt[k]++;
+                flag[k] = i;
+                k = parent[k];
+            }
+        }
+        std::sort(lrow[i].begin(), lrow[i].end());
+    }
+    L.Lp.assign(n + 1, 0);
+    for (int j = 0; j < n; ++j) L.Lp[j + 1] = L.Lp[j] + cnt[j];
+    const long long nnzL = L.Lp[n];
+    if (nnzL >= (1LL << 29)) return set_error(PF_EUNSUPPORTED, "jac_reduced_solve: factor too large");
+    L.Li.assign(nnzL, 0);
+    L.Rp.assign(n + 1, 0);
+    L.Rk.reserve(nnzL);
+    L.Rq.reserve(nnzL);
+    std::vector<int> fill(L.Lp.begin(), L.Lp.end() - 1);
+    for (int i = 0; i < n; ++i) {   // rows ascending: every column's rows come out ascending
+        for (int k : lrow[i]) {
+            L.Rk.push_back(k);
+            L.Rq.push_back(fill[k]);
+            L.Li[fill[k]++] = i;
+        }
+        L.Rp[i + 1] = (int)L.Rk.size();
+        std::vector<int>().swap(lrow[i]);
+    }
+    // the update terms of every slot p = (i, j) of column j: for each k of row j
+    // (ascending), the pairs {slot of L(i, k), slot of L(j, k)} over the rows i of
+    // column k below j (all of them are in column j's pattern)
+    auto slot_of = [&](int col, int row) {
+        const auto b = L.Li.begin() + L.Lp[col], e = L.Li.begin() + L.Lp[col + 1];
+        return (int)(std::lower_bound(b, e, row) - L.Li.begin());
+    };
+    L.gptr.assign(nnzL + 1, 0);
+    for (int j = 0; j < n; ++j)
+        for (int r = L.Rp[j]; r < L.Rp[j + 1]; ++r) {
+            const int k = L.Rk[r], q = L.Rq[r];
+            for (int pp = q + 1; pp < L.Lp[k + 1]; ++pp) L.gptr[slot_of(j, L.Li[pp]) + 1]++;
+        }
+    for (long long p = 0; p < nnzL; ++p) L.gptr[p + 1] += L.gptr[p];
+    if (L.gptr[nnzL] >= (1LL << 30)) return set_error(PF_EUNSUPPORTED, "jac_reduced_solve: factorization too large");
+    L.gsrc.assign(L.gptr[nnzL], make_int2(0, 0));
+    {
+        std::vector<int> gf(L.gptr.begin(), L.gptr.end() - 1);
+        for (int j = 0; j < n; ++j)
+            for (int r = L.Rp[j]; r < L.Rp[j + 1]; ++r) {
+                const int k = L.Rk[r], q = L.Rq[r];
+                for (int pp = q + 1; pp < L.Lp[k + 1]; ++pp) L.gsrc[gf[slot_of(j, L.Li[pp])]++] = make_int2(pp, q);
+            }
+    }
+    // levels by height in the tree
+    std::vector<int> height(n, 0);
+    for (int j = 0; j < n; ++j)
+        if (parent[j] >= 0) height[parent[j]] = std::max(height[parent[j]], height[j] + 1);
+    L.H = n ? *std::max_element(height.begin(), height.end()) + 1 : 0;
+    L.lvl_ptr.assign(L.H + 1, 0);
+    for (int j = 0; j < n; ++j) L.lvl_ptr[height[j] + 1]++;
+    for (int h = 0; h < L.H; ++h) L.lvl_ptr[h + 1] += L.lvl_ptr[h];
+    L.lvl_col.assign(n, 0);
+    std::vector<int> lf(L.lvl_ptr.begin(), L.lvl_ptr.end() - 1);
+    for (int j = 0; j < n; ++j) L.lvl_col[lf[height[j]]++] = j;
+    L.chain = L.H;
+    while (L.chain > 0 && L.lvl_ptr[L.chain] - L.lvl_ptr[L.chain - 1] <= kLuChainCols) --L.chain;
+    // the narrow levels' work items: every slot of every column (a column
+    // without slots below the diagonal still needs its pivot: slot -1)
+    L.item_ptr.assign(L.H - L.chain + 1, 0);
+    for (int h = L.chain; h < L.H; ++h) {
+        for (int t = L.lvl_ptr[h]; t < L.lvl_ptr[h + 1]; ++t) {
+            const int j = L.lvl_col[t];
+            if (L.Lp[j + 1] == L.Lp[j]) L.items.push_back(make_int2(j, -1));
+            for (int p = L.Lp[j]; p < L.Lp[j + 1]; ++p) L.items.push_back(make_int2(j, p));
+        }
+        L.item_ptr[h - L.chain + 1] = (int)L.items.size();
+    }
+    // every entry of J_r (CSC order) to its factor slot: 4 slot + {0: L, 1: U, 2: diagonal}
+    const int nnzA = colptr[n];
+    L.amap.assign(nnzA, 0);
+    const auto &pos = slot_of;
+    for (int c = 0; c < n; ++c)
+        for (int p = colptr[c]; p < colptr[c + 1]; ++p) {
+            const int i = iperm[rowidx[p]], j = iperm[c];
+            if (i == j)
+                L.amap[p] = 4 * j + 2;
+            else if (i > j)
+                L.amap[p] = 4 * pos(j, i) + 0;
+            else
+                L.amap[p] = 4 * pos(i, j) + 1;
+        }
+    return PF_OK;
+}
+
+// Upload the plan of the grid's current bus types and size its workspace.
+pf_status lu_prepare(Grid *g, cudaStream_t s)
+{
+    if (g->lu_ready) return PF_OK;
+    HostLu L;
+    if (pf_status st = host_lu(g->nb, g->red_n, g->red_npvpq, g->red_h_colptr, g->red_h_rowidx, g->red_h_fmap, L))
+        return st;
+    const size_t nnzL = (size_t)L.Lp[L.n];
+    auto up = [&](int **dst, const std::vector<int> &v) -> cudaError_t {
+        cudaError_t e = g->arena.alloc(dst, std::max<size_t>(v.size(), 1));
+        if (e == cudaSuccess && !v.empty())
+            e = cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        return e;
+    };
+    cudaError_t e;
+    if ((e = up(&g->lu_Lp, L.Lp)) || (e = up(&g->lu_Li, L.Li)) || (e = up(&g->lu_Rp, L.Rp)) ||
+        (e = up(&g->lu_Rk, L.Rk)) || (e = up(&g->lu_Rq, L.Rq)) || (e = up(&g->lu_lvl_ptr, L.lvl_ptr)) ||
+        (e = up(&g->lu_lvl_col, L.lvl_col)) || (e = up(&g->lu_perm, L.perm)) || (e = up(&g->lu_amap, L.amap)) ||
+        (e = up(&g->lu_gptr, L.gptr)) || (e = up(&g->lu_item_ptr, L.item_ptr)) ||
+        (e = g->arena.alloc(&g->lu_items, std::max<size_t>(L.items.size(), 1))) ||
+        (!L.items.empty() && (e = cudaMemcpyAsync(g->lu_items, L.items.data(), L.items.size() * sizeof(int2),
+                                                  cudaMemcpyHostToDevice, s))) ||
+        (e = g->arena.alloc(&g->lu_gsrc, std::max<size_t>(L.gsrc.size(), 1))) ||
+        (!L.gsrc.empty() && (e = cudaMemcpyAsync(g->lu_gsrc, L.gsrc.data(), L.gsrc.size() * sizeof(int2),
+                                                 cudaMemcpyHostToDevice, s))) ||
+        (e = g->arena.alloc(&g->lu_Lx, std::max<size_t>(nnzL, 1))) ||
+        (e = g->arena.alloc(&g->lu_Ux, std::max<size_t>(nnzL, 1))) ||
+        (e = g->arena.alloc(&g->lu_D, std::max(L.n, 1))) || (e = g->arena.alloc(&g->lu_y, std::max(L.n, 1))) ||
+        (e = cudaStreamSynchronize(s)))
+        return cuda_error(e, "jac_reduced_solve: set-up");
+    g->lu_n = L.n;
+    g->lu_H = L.H;
+    g->lu_chain = L.chain;
+    g->lu_widest = 1;
+    for (int h = 0; h < L.H; ++h) g->lu_widest = std::max(g->lu_widest, L.lvl_ptr[h + 1] - L.lvl_ptr[h]);
+    g->lu_nnzL = (long long)nnzL;
+    g->lu_ready = 1;
+    return PF_OK;
+}
+
+void lu_release(Grid *g)
+{
+    for (void *p : {(void *)g->lu_Lp, (void *)g->lu_Li, (void *)g->lu_Rp, (void *)g->lu_Rk, (void *)g->lu_Rq,
+                    (void *)g->lu_lvl_ptr, (void *)g->lu_lvl_col, (void *)g->lu_perm, (void *)g->lu_amap,
+                    (void *)g->lu_Lx, (void *)g->lu_Ux, (void *)g->lu_D, (void *)g->lu_y, (void *)g->lu_gptr,
+                    (void *)g->lu_gsrc, (void *)g->lu_item_ptr, (void *)g->lu_items})
+        g->arena.release(p);
+    g->lu_Lp = g->lu_Li = g->lu_Rp = g->lu_Rk = g->lu_Rq = g->lu_lvl_ptr = g->lu_lvl_col = g->lu_perm = g->lu_amap =
+        g->lu_gptr = g->lu_item_ptr = nullptr;
+    g->lu_gsrc = g->lu_items = nullptr;
+    g->lu_Lx = g->lu_Ux = g->lu_D = g->lu_y = nullptr;
+    g->lu_ready = 0;
+}
+
+cudaError_t launch_lu_solve(Grid *g, const double *Jr, const double *F, double *dx, cudaStream_t s)
+{
+    if (g->lu_n == 0) return cudaSuccess;
+    LuArgs a{};
+    a.n = g->lu_n;
+    a.nnzA = (int)g->red_nnz;
+    a.H = g->lu_H;
+    a.chain = g->lu_chain;
+    a.Lp = g->lu_Lp;
+    a.Li = g->lu_Li;
+    a.Rp = g->lu_Rp;
+    a.Rk = g->lu_Rk;
+    a.Rq = g->lu_Rq;
+    a.lvl_ptr = g->lu_lvl_ptr;
+    a.lvl_col = g->lu_lvl_col;
+    a.perm = g->lu_perm;
+    a.amap = g->lu_amap;
+    a.gptr = g->lu_gptr;
+    a.gsrc = g->lu_gsrc;
+    a.item_ptr = g->lu_item_ptr;
+    a.items = g->lu_items;
+    a.A = Jr;
+    a.F = F;
+    a.Lx = g->lu_Lx;
+    a.Ux = g->lu_Ux;
+    a.D = g->lu_D;
+    a.y = g->lu_y;
+    a.dx = dx;
+    a.bar = g->bar;
+    a.err = g->err;
+    if (g->lu_resident == 0) {
+        int per_sm = 0, dev = 0, nsm = 0;
+        cudaError_t e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_solve, kLuThreads, 0)) ||
+            (e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
+            return e;
+        // one CTA per SM at most: the widest levels have a few thousand columns,
+        // and more CTAs make every grid barrier dearer
+        g->lu_resident = std::max(1, std::min(per_sm, 1) * nsm);
+    }
+    // a warp per column of the widest level (the leaves) at most
+    const int ctas = std::max(1, (g->lu_widest + kLuThreads / 32 - 1) / (kLuThreads / 32));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::max(1, std::min(g->lu_resident, ctas)));
+    cfg.blockDim = dim3(kLuThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_lu_solve, a);
+}
+
+}  // namespace pf
+
+using namespace pf;
+
+PF_API pf_status jac_reduced_solve(pf_grid *grid, const double *Jr, const double *F, double *dx, pf_stream stream)
+{
+    if (!grid) return set_error(PF_EINVAL, "jac_reduced_solve: grid is NULL");
+    Grid *g = &grid->g;
+    if (!g->red_set) return set_error(PF_EINVAL, "jac_reduced_solve: call grid_set_bus_types first");
+    if (g->red_n == 0) return PF_OK;
+    if (!Jr || !F || !dx) return set_error(PF_EINVAL, "jac_reduced_solve: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (pf_status st = lu_prepare(g, s)) return st;
+    TraceScope t(g, PF_K_LU, s);
+    PF_CUDA(launch_lu_solve(g, Jr, F, dx, s));
+    return PF_OK;
+}

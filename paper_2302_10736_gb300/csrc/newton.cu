@@ -2,15 +2,11 @@
 //
 // The paper computes the injections and the Jacobian that a Newton step
 // needs and hands the Jacobian to a sparse direct solver; this file closes the
-// loop on the GPU.  Iteration k: the full evaluation (Ybus or element-wise
-// method) into the grid's scratch, the gather of the mismatch F and of the
-// reduced Jacobian J_r in row-major order (reduced.cu), max |F| to the host
-// (the only host round trip besides the solver's), then J_r dx = F by
-// cuSOLVER's sparse QR on the device and x <- x - dx, with x the angles of
-// the PV and PQ buses and the magnitudes of the PQ buses.
-#include <cusolverSp.h>
-#include <cusparse.h>
-
+// loop on the GPU.  Iteration k: the mismatch F and the reduced Jacobian J_r
+// in CSC order (jac_reduced: one launch by the element-wise method), max |F|
+// to the host (the only host round trip), then J_r dx = F by the library's
+// sparse LU (lu.cu, one cooperative launch) and x <- x - dx, with x the
+// angles of the PV and PQ buses and the magnitudes of the PQ buses.
 #include <algorithm>
 #include <cstring>
 
@@ -45,19 +41,7 @@ __global__ void __launch_bounds__(256) k_newton_update(int n, int npvpq, const i
     }
 }
 
-pf_status solver_error(cusolverStatus_t st, const char *what)
-{
-    return set_error(PF_ECUDA, "%s: cuSOLVER status %d", what, (int)st);
-}
-
 }  // namespace
-
-void newton_free(Grid *g)
-{
-    if (g->nt_solver) cusolverSpDestroy((cusolverSpHandle_t)g->nt_solver);
-    if (g->nt_descr) cusparseDestroyMatDescr((cusparseMatDescr_t)g->nt_descr);
-    g->nt_solver = g->nt_descr = nullptr;
-}
 
 }  // namespace pf
 
@@ -75,49 +59,40 @@ PF_API pf_status powerflow_newton(pf_grid *grid, int32_t method, double *vm, dou
     if (!(tol >= 0.0) || max_iter < 0) return set_error(PF_EINVAL, "powerflow_newton: tol < 0 or max_iter < 0");
     if (iterations) *iterations = 0;
     if (mismatch) *mismatch = 0.0;
-    const int n = g->red_n, nnz = (int)g->red_nnz;
+    const int n = g->red_n;
+    const long long nnz = g->red_nnz;
     if (g->nb == 0 || n == 0) return PF_OK;
     if (!vm || !va || !Pspec || !Qspec) return set_error(PF_EINVAL, "powerflow_newton: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    if (!g->nt_solver) {
-        cusolverSpHandle_t h;
-        cusparseMatDescr_t d;
-        cusolverStatus_t cs = cusolverSpCreate(&h);
-        if (cs != CUSOLVER_STATUS_SUCCESS) return solver_error(cs, "cusolverSpCreate");
-        g->nt_solver = h;
-        if (cusparseCreateMatDescr(&d) != CUSPARSE_STATUS_SUCCESS)
-            return set_error(PF_ECUDA, "powerflow_newton: cusparseCreateMatDescr failed");
-        cusparseSetMatType(d, CUSPARSE_MATRIX_TYPE_GENERAL);
-        cusparseSetMatIndexBase(d, CUSPARSE_INDEX_BASE_ZERO);
-        g->nt_descr = d;
-    }
     if (!g->nt_dx) {
         double **const out[3] = {&g->nt_F, &g->nt_J, &g->nt_dx};
-        const size_t sz[3] = {(size_t)n, (size_t)std::max(nnz, 1), (size_t)n};
+        const size_t sz[3] = {(size_t)n, (size_t)std::max<long long>(nnz, 1), (size_t)n};
         PF_CUDA(alloc_all(g->arena, out, sz));
     }
     if (!g->nt_max) PF_CUDA(g->arena.alloc(&g->nt_max, 1));
-    cusolverSpHandle_t h = (cusolverSpHandle_t)g->nt_solver;
-    cusolverStatus_t cs = cusolverSpSetStream(h, s);
-    if (cs != CUSOLVER_STATUS_SUCCESS) return solver_error(cs, "cusolverSpSetStream");
+    if (pf_status st = lu_prepare(g, s)) return st;
     int dev = 0, nsm = 0;
     PF_CUDA(cudaGetDevice(&dev));
     PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = std::max(1, std::min((n + 255) / 256, 4 * nsm));
     for (int it = 0;; ++it) {
-        pf_status st = method == 0 ? jac_ybus(grid, vm, va, g->red_P, g->red_Q, g->red_J, stream)
-                                   : jac_elementwise(grid, vm, va, g->red_P, g->red_Q, g->red_J, stream);
+        pf_status st = jac_reduced(grid, method, vm, va, Pspec, Qspec, g->nt_F, g->nt_J, stream);
         if (st) return st;
-        {
-            TraceScope t(g, PF_K_REDUCE, s);
-            PF_CUDA(launch_reduce(g, g->red_jmap_csr, Pspec, Qspec, g->nt_F, g->nt_J, s));
-        }
         PF_CUDA(cudaMemsetAsync(g->nt_max, 0, sizeof(unsigned long long), s));
         k_absmax<<<blocks, 256, 0, s>>>(n, g->nt_F, g->nt_max);
         PF_CUDA(cudaGetLastError());
         unsigned long long bits = 0;
+        int derr = 0;
         PF_CUDA(cudaMemcpyAsync(&bits, g->nt_max, sizeof(bits), cudaMemcpyDeviceToHost, s));
+        PF_CUDA(cudaMemcpyAsync(&derr, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
         PF_CUDA(cudaStreamSynchronize(s));
+        if (derr == DEV_SINGULAR) {   // the previous iteration's factorization met a zero pivot
+            PF_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+            PF_CUDA(cudaStreamSynchronize(s));
+            return set_error(PF_ENOCONV, "powerflow_newton: zero or non-finite pivot in the reduced Jacobian's LU "
+                                         "at iteration %d", it - 1);
+        }
+        if (derr != DEV_OK) return grid_check_error(grid, stream);
         double fmax;
         std::memcpy(&fmax, &bits, sizeof(fmax));
         if (iterations) *iterations = it;
@@ -126,13 +101,10 @@ PF_API pf_status powerflow_newton(pf_grid *grid, int32_t method, double *vm, dou
         if (it == max_iter)
             return set_error(PF_ENOCONV, "powerflow_newton: max |F| = %g after %d iterations (tol %g)", fmax, it,
                              tol);
-        int singular = -1;
-        cs = cusolverSpDcsrlsvqr(h, n, nnz, (cusparseMatDescr_t)g->nt_descr, g->nt_J, g->red_rowptr, g->red_colidx,
-                                 g->nt_F, 1e-14, 1, g->nt_dx, &singular);
-        if (cs != CUSOLVER_STATUS_SUCCESS) return solver_error(cs, "cusolverSpDcsrlsvqr");
-        if (singular >= 0)
-            return set_error(PF_ENOCONV, "powerflow_newton: reduced Jacobian singular (pivot %d) at iteration %d",
-                             singular, it);
+        {
+            TraceScope t(g, PF_K_LU, s);
+            PF_CUDA(launch_lu_solve(g, g->nt_J, g->nt_F, g->nt_dx, s));
+        }
         k_newton_update<<<blocks, 256, 0, s>>>(n, g->red_npvpq, g->red_fmap, g->nt_dx, vm, va);
         PF_CUDA(cudaGetLastError());
     }

@@ -28,7 +28,7 @@ cudaError_t ensure_dyn_smem(const void *kernel, size_t bytes);
     } while (0)
 
 // device error word codes (written by kernels, read by grid_check_error)
-enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADINDEX = 2 };
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADINDEX = 2, DEV_SINGULAR = 3 };
 
 // ------------------------------------------------- device buffer owner --
 // Test hook (pf_debug_fail_allocations): when >= 0, the number of device
@@ -279,11 +279,21 @@ struct Grid {
     int *tgt_map = nullptr;
     double *tgt_J = nullptr;
     double *red_P = nullptr, *red_Q = nullptr, *red_J = nullptr;
-    // Newton-Raphson workspace (powerflow_newton): F, J_r (CSR), step, max |F|;
-    // sparse-solver handles (cusolverSpHandle_t, cusparseMatDescr_t)
+    // host copies of the reduced pattern (the LU analysis reads them)
+    std::vector<int> red_h_colptr, red_h_rowidx, red_h_fmap;
+    // Newton-Raphson workspace (powerflow_newton): F, J_r (CSC), step, max |F|
     double *nt_F = nullptr, *nt_J = nullptr, *nt_dx = nullptr;
     unsigned long long *nt_max = nullptr;
-    void *nt_solver = nullptr, *nt_descr = nullptr;
+    // sparse LU of the reduced system (lu.cu): plan of the current bus types
+    // (CSC of L's pattern, row structures, levels, permutation, value map) and
+    // the factor storage
+    int lu_ready = 0, lu_n = 0, lu_H = 0, lu_chain = 0, lu_resident = 0, lu_widest = 0;
+    long long lu_nnzL = 0;
+    int *lu_Lp = nullptr, *lu_Li = nullptr, *lu_Rp = nullptr, *lu_Rk = nullptr, *lu_Rq = nullptr;
+    int *lu_lvl_ptr = nullptr, *lu_lvl_col = nullptr, *lu_perm = nullptr, *lu_amap = nullptr, *lu_gptr = nullptr;
+    int *lu_item_ptr = nullptr;
+    int2 *lu_gsrc = nullptr, *lu_items = nullptr;
+    double *lu_Lx = nullptr, *lu_Ux = nullptr, *lu_D = nullptr, *lu_y = nullptr;
     // tracer: events [2 * capacity], kernel id per record
     std::vector<cudaEvent_t> tr_ev;
     std::vector<int> tr_kernel;
@@ -351,10 +361,28 @@ cudaError_t launch_jac_ew_reduced(Grid *g, const double *vm, const double *va, c
 cudaError_t launch_jac_ew_mapped(Grid *g, const double *vm, const double *va, double *P, double *Q, const int *map,
                                  double *Jt, cudaStream_t s);
 
-// reduced Newton system (reduced.cu, newton.cu)
+// reduced Newton system (reduced.cu)
 cudaError_t launch_reduce(Grid *g, const int *map, const double *Pspec, const double *Qspec, double *F, double *Jr,
                           cudaStream_t s);
-void newton_free(Grid *g);
+
+// sparse LU of the reduced system (lu.cu): the host analysis of a reduced
+// pattern (permutation new -> reduced index, CSC of L's pattern, per column the
+// (k, position of L(j, k)) pairs of its row, columns by tree height, the top
+// levels narrow enough for one CTA from `chain` on, and each reduced entry's
+// factor slot 4 slot + {0 L, 1 U, 2 diagonal}), its upload, and the solve
+struct HostLu {
+    int n = 0, H = 0, chain = 0;
+    std::vector<int> perm, Lp, Li, Rp, Rk, Rq, lvl_ptr, lvl_col, amap;
+    std::vector<int> gptr;    // [nnzL + 1] update terms of every factor slot
+    std::vector<int2> gsrc;   // {slot of L(i, k), slot of L(j, k)}, k ascending per slot
+    std::vector<int> item_ptr;   // [H - chain + 1] the narrow levels' items
+    std::vector<int2> items;     // {column, slot or -1}
+};
+pf_status host_lu(int nb, int n, int npvpq, const std::vector<int> &colptr, const std::vector<int> &rowidx,
+                  const std::vector<int> &fmap, HostLu &L);
+pf_status lu_prepare(Grid *g, cudaStream_t s);
+void lu_release(Grid *g);
+cudaError_t launch_lu_solve(Grid *g, const double *Jr, const double *F, double *dx, cudaStream_t s);
 
 // ----------------------------------------------------------- batches ----
 // S scenarios over one grid: per-scenario voltage states and an optional N-1

@@ -209,6 +209,10 @@ PF_API pf_status grid_set_bus_types(pf_grid *grid, const int32_t *bus_type, pf_s
     g->red_npvpq = R.npvpq;
     g->red_nnz = R.colptr.back();
     PF_CUDA(cudaStreamSynchronize(s));   // R's vectors are freed on return
+    lu_release(g);                       // the LU plan belongs to the previous bus types
+    g->red_h_colptr = R.colptr;
+    g->red_h_rowidx = R.rowidx;
+    g->red_h_fmap = R.fmap;
     g->red_set = 1;
     return PF_OK;
 }

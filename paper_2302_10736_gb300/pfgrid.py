@@ -96,6 +96,7 @@ def _load():
                                   vp]),
         "jac_set_target_pattern": (st, [vp, vp, vp, ctypes.c_int64, vp]),
         "jac_target": (st, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "jac_reduced_solve": (st, [vp, vp, vp, vp, vp]),
         "pf_phase_probe_read": (st, [vp, i32, pi32]),
         "fp64_peak_probe": (st, [i32, i32, vp, ctypes.POINTER(ctypes.c_int64), vp]),
     }
@@ -498,6 +499,14 @@ def jac_target(grid, method, vm, va, P, Q, Jt, stream=None):
     nnz = getattr(grid, "_target_nnz", 0)
     _check(_lib.jac_target(grid.handle, int(m), _dptr(vm, "vm", nb), _dptr(va, "va", nb), _dptr(P, "P", nb),
                            _dptr(Q, "Q", nb), _dptr(Jt, "Jt", nnz), _stream(stream)), "jac_target")
+
+
+def jac_reduced_solve(grid, Jr, F, dx, stream=None):
+    """dx [n] with J_r dx = F, J_r given by its values Jr [nnz] in jac_reduced's
+    CSC order (the library's sparse LU)."""
+    n, _, nnz = jac_reduced_info(grid)
+    _check(_lib.jac_reduced_solve(grid.handle, _dptr(Jr, "Jr", nnz), _dptr(F, "F", n), _dptr(dx, "dx", n),
+                                  _stream(stream)), "jac_reduced_solve")
 
 
 def powerflow_newton(grid, method, vm, va, Pspec, Qspec, tol=1e-10, max_iter=20, stream=None):
