@@ -69,7 +69,7 @@ def parse_args(argv=None):
     ap.add_argument("--phase-probe-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-workload",
                     choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra", "newton", "sweep",
-                             "study", "target"],
+                             "study", "target", "replicated"],
                     help="run only this batched/adjoint workload (few launches, for profilers) and exit")
     return ap.parse_args(argv)
 
@@ -426,6 +426,8 @@ def extra_workloads(torch, pfgrid, synth, reps, only=None, cpu_seconds=None):
         out["target_pattern_70k"] = _target_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "ultra"):
         out["single_410k"] = _single_workload(torch, pfgrid, synth, 6, max(reps, 20))
+    if only in (None, "replicated"):
+        out["replicated_82k"] = _replicated_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "study"):
         out["two_step_study_70k"] = _study_workload(torch, pfgrid, synth, max(reps, 20))
     if only in (None, "sweep"):
@@ -511,6 +513,35 @@ def _size_sweep(torch, pfgrid, synth, steps):
     for r in rows:
         for name in ("elementwise", "ybus", "elementwise_inj", "ybus_inj"):
             r["%s_ratio_to_118" % name] = r["%s_us" % name] / base["%s_us" % name]
+    return rows
+
+
+def _replicated_workload(torch, pfgrid, synth, steps):
+    """The paper's ultra-large cases (Sec. V-C): the 82k-bus grid repeated 2 to
+    5 times as disjoint copies (164k to 410k buses); single evaluations of
+    injections + Jacobian by both methods, L2 flushed between steps."""
+    dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    flush = L2Flush(torch)
+    rows = []
+    for copies in (2, 3, 4, 5):
+        w = synth.replicated_workload(copies)
+        grid = pfgrid.ybus_build(w)
+        vm, va = dev(w["vm"][0]), dev(w["va"][0])
+        pfgrid.grid_autotune(grid, vm, va, reps=10)
+        P = torch.empty(w["nb"], dtype=torch.float64, device="cuda")
+        Q = torch.empty_like(P)
+        J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+        row = {"copies": copies, "nb": w["nb"], "nl": w["nl"]}
+        for name, fn in (("elementwise", pfgrid.jac_elementwise), ("ybus", pfgrid.jac_ybus)):
+            f = lambda: fn(grid, vm, va, P, Q, J)
+            for _ in range(3):
+                f()
+            t = time_loop(torch, f, steps, flush, "replicated_%s" % name)
+            row["%s_us" % name] = 1e3 * sum(t) / len(t)
+        row["ybus_over_elementwise"] = row["ybus_us"] / row["elementwise_us"]
+        pfgrid.grid_check_error(grid)
+        rows.append(row)
+        del grid
     return rows
 
 

@@ -89,6 +89,8 @@ typedef struct {
     int32_t ybus_block;     /* threads per CTA of the CSR kernels (multiple of 32, <= 512) */
     int32_t ew_window;      /* threads per CTA of the element-wise kernels: 128 or 256; a CTA owns a
                                window of consecutive buses with at most that many buses and terminals */
+    int32_t ybus_fused;     /* Ybus method: 1 = the phasor step fused into the row kernel (one launch; each
+                               entry forms its column's phasor), 0 = the phasor step as its own launch */
 } pf_config;
 
 /* Human-readable name of a status code (static string). */

@@ -302,6 +302,7 @@ PF_API pf_status ybus_build(const pf_grid_desc *d, pf_stream stream, pf_grid **o
     g->cfg.ybus_lanes = 4;
     g->cfg.ybus_block = 256;
     g->cfg.ew_window = 256;
+    g->cfg.ybus_fused = 1;
     if ((st = host_topology(d->nb, d->nl, d->from, d->to, g->topo))) {
         delete pg;
         return st;
@@ -400,6 +401,11 @@ PF_API pf_status inj_ybus(pf_grid *grid, const double *vm, const double *va, dou
     if (g->nb == 0) return PF_OK;
     if (!P || !Q) return set_error(PF_EINVAL, "inj_ybus: P or Q is NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    if (g->cfg.ybus_fused) {   // one launch: the phasors formed inside the row kernel
+        TraceScope t(g, PF_K_INJ_YBUS, s);
+        PF_CUDA(launch_ybus_fused(g, false, vm, va, P, Q, nullptr, s));
+        return PF_OK;
+    }
     {
         TraceScope t(g, PF_K_PHASOR, s);
         PF_CUDA(launch_phasor(g->nb, vm, va, g->ph_u, g->ph_v, s));
@@ -437,6 +443,11 @@ PF_API pf_status jac_ybus(pf_grid *grid, const double *vm, const double *va, dou
     if (!J) return set_error(PF_EINVAL, "jac_ybus: J is NULL");
     if ((P == nullptr) != (Q == nullptr)) return set_error(PF_EINVAL, "jac_ybus: P and Q must both be set or both NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    if (g->cfg.ybus_fused) {   // one launch: the phasors formed inside the row kernel
+        TraceScope t(g, PF_K_JAC_YBUS, s);
+        PF_CUDA(launch_ybus_fused(g, true, vm, va, P, Q, J, s));
+        return PF_OK;
+    }
     {
         TraceScope t(g, PF_K_PHASOR, s);
         PF_CUDA(launch_phasor(g->nb, vm, va, g->ph_u, g->ph_v, s));
@@ -582,6 +593,7 @@ PF_API pf_status grid_set_config(pf_grid *grid, const pf_config *cfg, pf_stream 
     if (!valid_lanes(cfg->ybus_lanes)) return set_error(PF_EINVAL, "ybus_lanes must be 1, 2, 4, 8, 16 or 32");
     if (cfg->ybus_block < 32 || cfg->ybus_block > 512 || cfg->ybus_block % 32)
         return set_error(PF_EINVAL, "ybus_block must be a multiple of 32 in [32, 512]");
+    if (cfg->ybus_fused != 0 && cfg->ybus_fused != 1) return set_error(PF_EINVAL, "ybus_fused must be 0 or 1");
     Grid *g = &grid->g;
     cudaStream_t s = (cudaStream_t)stream;
     if (cfg->ew_window != g->ew.tb) {
@@ -673,18 +685,22 @@ PF_API pf_status grid_autotune(pf_grid *grid, const double *vm, const double *va
     pf_config cfg = g->cfg, keep = g->cfg;
     float best_y = 1e30f, best_e = 1e30f;
     const int lanes[] = {1, 2, 4, 8, 16, 32}, blocks[] = {128, 256, 512};
-    for (int w : lanes)
-        for (int bk : blocks) {
-            g->cfg.ybus_lanes = w;
-            g->cfg.ybus_block = bk;
-            float ms;
-            if ((st = time_it(&ms, reps, s, run_jac_ybus, &ctx))) goto out;
-            if (ms < best_y) {
-                best_y = ms;
-                cfg.ybus_lanes = w;
-                cfg.ybus_block = bk;
+    for (int fused : {0, 1})
+        for (int w : lanes)
+            for (int bk : blocks) {
+                g->cfg.ybus_fused = fused;
+                g->cfg.ybus_lanes = w;
+                g->cfg.ybus_block = bk;
+                float ms;
+                if ((st = time_it(&ms, reps, s, run_jac_ybus, &ctx))) goto out;
+                if (ms < best_y) {
+                    best_y = ms;
+                    cfg.ybus_fused = fused;
+                    cfg.ybus_lanes = w;
+                    cfg.ybus_block = bk;
+                }
             }
-        }
+    g->cfg.ybus_fused = cfg.ybus_fused;
     g->cfg.ybus_lanes = cfg.ybus_lanes;
     g->cfg.ybus_block = cfg.ybus_block;
     for (int win : {128, 256}) {

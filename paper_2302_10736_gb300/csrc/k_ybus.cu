@@ -16,9 +16,17 @@
 // Values are written straight into the canonical J layout, i.e. the copy of
 // Alg. 2 with its index arrays in closed form.
 //
-// The row's first entries (column index and Y value, static data) are
-// loaded before the programmatic-dependent-launch wait; the phasor gathers of
-// a chunk are issued together before its arithmetic.
+// The row's first column indices (topology) are loaded before the
+// programmatic-dependent-launch wait; the phasor gathers of a chunk are issued
+// together before its arithmetic.
+//
+// Two forms: the paper's step 1 as its own launch (k_phasor writes U, V for
+// every bus, the row kernels gather them), or fused (k_ybus_fused: each lane
+// forms the phasors of its entries' columns from vm, va itself, with the
+// integer-pipe sine/cosine of isincos.cuh, so one launch evaluates and nothing
+// goes through memory in between; a bus's phasor is formed once per entry of
+// its column, about 3.5 times on these grids).
+#include "fastmath.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
 
@@ -192,6 +200,150 @@ __global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__
     if (lane == 0 && P) {
         P[row] = Sr;
         Q[row] = Si;
+    }
+}
+
+// Injections (JAC = false) or injections and Jacobian (JAC = true) with the
+// phasor step fused: W lanes per row, each forming U_j = e^{j theta_j}, v_j for
+// its entries and the row's own V_i.
+template <int W, bool JAC>
+__global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *__restrict__ rp,
+                                                     const int *__restrict__ ci, const double2 *__restrict__ Y,
+                                                     const double *__restrict__ vm, const double *__restrict__ va,
+                                                     const ITrig *__restrict__ trig, double *__restrict__ P,
+                                                     double *__restrict__ Q, double *__restrict__ J)
+{
+    __shared__ ITrig tab[kITrigN];
+    pdl_launch_dependents();
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = (int)(gid / W), lane = (int)(gid % W);
+    const bool valid = row < nb;
+    int rs = 0, d = 0;
+    int jj[kChunkW<W>];
+    if (valid) {
+        rs = rp[row];
+        d = rp[row + 1] - rs;
+    }
+#pragma unroll
+    for (int j = 0; j < kChunkW<W>; ++j) {
+        const int k = lane + W * j;
+        if (k < d) jj[j] = ci[rs + k];
+    }
+    for (int k = threadIdx.x; k < kITrigN; k += blockDim.x) tab[k] = trig[(blockIdx.x % kITrigCopies) * kITrigN + k];
+    pdl_wait();   // the state and the Ybus values may be the previous kernel's
+    double2 yy[kChunkW<W>];
+#pragma unroll
+    for (int j = 0; j < kChunkW<W>; ++j) {
+        const int k = lane + W * j;
+        if (k < d) yy[j] = Y[rs + k];
+    }
+    const double thi = valid ? va[row] : 0.0, vi = valid ? vm[row] : 0.0;
+    __syncthreads();   // the table
+    double si, cs;
+    int_sincos(thi, tab, &si, &cs);
+    const double Vr = vi * cs, Vi = vi * si;
+    double Ir = 0.0, Ii = 0.0;
+    double dTr = 0.0, dTi = 0.0, dVr = 0.0, dVi = 0.0;   // diagonal partials (lane that owns it)
+    int kd = -1;
+    for (int k0 = lane; k0 < d; k0 += W * kChunkW<W>) {
+        if (k0 != lane) {
+#pragma unroll
+            for (int j = 0; j < kChunkW<W>; ++j) {
+                const int k = k0 + W * j;
+                if (k < d) {
+                    jj[j] = ci[rs + k];
+                    yy[j] = Y[rs + k];
+                }
+            }
+        }
+        double thj[kChunkW<W>], vj[kChunkW<W>];
+#pragma unroll
+        for (int j = 0; j < kChunkW<W>; ++j)
+            if (k0 + W * j < d) {
+                thj[j] = va[jj[j]];
+                vj[j] = vm[jj[j]];
+            }
+#pragma unroll
+        for (int j = 0; j < kChunkW<W>; ++j) {
+            const int k = k0 + W * j;
+            if (k < d) {
+                double s, c;
+                int_sincos(thj[j], tab, &s, &c);
+                if (JAC) {
+                    const double YUr = fma(yy[j].x, c, -yy[j].y * s);   // Y_ij U_j
+                    const double YUi = fma(yy[j].x, s, yy[j].y * c);
+                    const double sVr = fma(Vr, YUr, Vi * YUi);          // V_i conj(YU)
+                    const double sVi = fma(Vi, YUr, -Vr * YUi);
+                    Ir = fma(vj[j], YUr, Ir);
+                    Ii = fma(vj[j], YUi, Ii);
+                    const double sTr = vj[j] * sVi, sTi = -vj[j] * sVr;   // -j v_j dS/dv_j
+                    if (jj[j] == row) {
+                        kd = k;
+                        dTr = sTr;
+                        dTi = sTi;
+                        dVr = sVr;
+                        dVi = sVi;
+                    } else {
+                        const int p = 2 * rs + k;
+                        J[p] = sTr;
+                        J[p + d] = sVr;
+                        J[2 * nnz + p] = sTi;
+                        J[2 * nnz + p + d] = sVi;
+                    }
+                } else {
+                    const double Vjr = vj[j] * c, Vji = vj[j] * s;
+                    Ir = fma(yy[j].x, Vjr, Ir);
+                    Ir = fma(-yy[j].y, Vji, Ir);
+                    Ii = fma(yy[j].x, Vji, Ii);
+                    Ii = fma(yy[j].y, Vjr, Ii);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+        Ir += __shfl_xor_sync(0xffffffffu, Ir, off, W);
+        Ii += __shfl_xor_sync(0xffffffffu, Ii, off, W);
+    }
+    if (!valid) return;
+    const double Sr = fma(Vr, Ir, Vi * Ii), Si = fma(Vi, Ir, -Vr * Ii);
+    if (JAC && kd >= 0) {
+        dTr -= Si;                        // + j S_i
+        dTi += Sr;
+        dVr += fma(Ir, cs, Ii * si);      // + conj(I_i) U_i
+        dVi += fma(Ir, si, -Ii * cs);
+        const int p = 2 * rs + kd;
+        J[p] = dTr;
+        J[p + d] = dVr;
+        J[2 * nnz + p] = dTi;
+        J[2 * nnz + p + d] = dVi;
+    }
+    if (lane == 0 && P) {
+        P[row] = Sr;
+        Q[row] = Si;
+    }
+}
+
+template <int W, bool JAC>
+static cudaError_t fused_w(const Grid *g, const double *vm, const double *va, double *P, double *Q, double *J,
+                           cudaStream_t s)
+{
+    const long long threads = (long long)g->nb * W;
+    const int blk = g->cfg.ybus_block;
+    return launch_k(k_ybus_fused<W, JAC>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, g->nnz,
+                    (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, vm, va, trig_table(), P, Q, J);
+}
+
+cudaError_t launch_ybus_fused(const Grid *g, bool jac, const double *vm, const double *va, double *P, double *Q,
+                              double *J, cudaStream_t s)
+{
+    switch (g->cfg.ybus_lanes) {
+    case 1: return jac ? fused_w<1, true>(g, vm, va, P, Q, J, s) : fused_w<1, false>(g, vm, va, P, Q, J, s);
+    case 2: return jac ? fused_w<2, true>(g, vm, va, P, Q, J, s) : fused_w<2, false>(g, vm, va, P, Q, J, s);
+    case 4: return jac ? fused_w<4, true>(g, vm, va, P, Q, J, s) : fused_w<4, false>(g, vm, va, P, Q, J, s);
+    case 8: return jac ? fused_w<8, true>(g, vm, va, P, Q, J, s) : fused_w<8, false>(g, vm, va, P, Q, J, s);
+    case 16: return jac ? fused_w<16, true>(g, vm, va, P, Q, J, s) : fused_w<16, false>(g, vm, va, P, Q, J, s);
+    default: return jac ? fused_w<32, true>(g, vm, va, P, Q, J, s) : fused_w<32, false>(g, vm, va, P, Q, J, s);
     }
 }
 

@@ -348,6 +348,9 @@ const ITrig *trig_table();         // device address of the (cos, sin) table of 
 cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32a *U, double2 *V, cudaStream_t s);
 cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s);
 cudaError_t launch_jac_ybus(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s);
+// the Ybus method with the phasor step fused into the row kernel (one launch)
+cudaError_t launch_ybus_fused(const Grid *g, bool jac, const double *vm, const double *va, double *P, double *Q,
+                              double *J, cudaStream_t s);
 // element-wise: one CTA per window (phasors of its own and ghost buses, evaluation, reduction)
 cudaError_t ew_blocks_per_sm(int tb, size_t smem, int *per_sm);   // CTAs of k_ew<true> that fit on one SM
 cudaError_t launch_inj_ew(Grid *g, const double *vm, const double *va, double *P, double *Q, cudaStream_t s);

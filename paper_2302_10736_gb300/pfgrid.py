@@ -35,7 +35,8 @@ class pf_grid_desc(ctypes.Structure):
 
 
 class pf_config(ctypes.Structure):
-    _fields_ = [("ybus_lanes", ctypes.c_int32), ("ybus_block", ctypes.c_int32), ("ew_window", ctypes.c_int32)]
+    _fields_ = [("ybus_lanes", ctypes.c_int32), ("ybus_block", ctypes.c_int32), ("ew_window", ctypes.c_int32),
+                ("ybus_fused", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -14,6 +14,10 @@ Workloads (seed = 20230221 + workload number; sub-streams per quantity):
   5  250,000 buses / 330,000 branches, 16 states + loss data as in 4
   6  410,000 buses / 541,000 branches, one state (the size of the paper's
      largest replicated grid)
+Replicated grids (replicated_workload): an 82,000-bus / 104,121-branch grid
+(the bus and line counts of the paper's SyntheticUSA case) repeated 2 to 5
+times as disjoint copies, 164,000 to 410,000 buses (the paper's ultra-large
+cases, Sec. V-C).
 """
 import ctypes
 import os
@@ -33,6 +37,8 @@ WORKLOADS = {
     6: dict(nb=410000, nl=541000, pv=0.20, nscen=1),
 }
 BASE_SEED = 20230221
+# the 82k-bus base of the replicated grids: bus and line counts of SyntheticUSA
+REPLICA_BASE = dict(nb=82000, nl=104121, pv=0.20)
 
 
 def _load():
@@ -160,3 +166,37 @@ def workload(k, nscen=None):
         gr["vm2"], gr["va2"] = vm2[0], va2[0]
         gr["wP"], gr["wQ"] = weights(w["nb"], seed)
     return gr
+
+
+def replicated(base, copies):
+    """`copies` disjoint copies of a grid: copy c's buses are c * nb + the
+    base bus, its branches the base branches between them (every bus and line
+    duplicated, no tie between copies)."""
+    nb, nl = int(base["nb"]), int(base["nl"])
+    off_b = np.repeat(np.arange(copies, dtype=np.int64) * nb, nl)
+    out = dict(nb=nb * copies, nl=nl * copies)
+    out["f"] = (np.tile(base["f"].astype(np.int64), copies) + off_b).astype(np.int32)
+    out["t"] = (np.tile(base["t"].astype(np.int64), copies) + off_b).astype(np.int32)
+    for key in ("g", "b", "bsh", "tap", "shift"):
+        out[key] = np.tile(base[key], copies)
+    for key in ("gs", "bs", "bustype", "x", "y"):
+        if key in base:
+            out[key] = np.tile(base[key], copies)
+    return out
+
+
+def replicated_workload(copies, same_state=False):
+    """The 82k-bus base grid repeated `copies` times (2 .. 5 in the paper) with
+    one voltage state: drawn for the whole grid, or (same_state) the base
+    grid's state repeated in every copy."""
+    seed = BASE_SEED + 7
+    base = grid(REPLICA_BASE["nb"], REPLICA_BASE["nl"], seed, pv_frac=REPLICA_BASE["pv"])
+    out = replicated(base, copies)
+    if same_state:
+        vm, va = voltages(base["nb"], 1, seed)
+        vm, va = np.tile(vm, (1, copies)), np.tile(va, (1, copies))
+    else:
+        vm, va = voltages(out["nb"], 1, seed)
+    out.update(workload="replicated_82k_x%d" % copies, seed=seed, nscen=1, vm=vm, va=va, copies=copies,
+               base_nb=base["nb"], base_nl=base["nl"])
+    return out

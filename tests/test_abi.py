@@ -107,3 +107,19 @@ def test_layout_selfcheck_random_numbering(window, target):
     from paper_2302_10736_gb300 import pfgrid, synth
     w = synth.renumber_buses(synth.workload(1), 99)
     pfgrid.grid_selfcheck(w, window, target)
+
+
+def test_replicated_grid_structure():
+    """Host-only: the replicated 82k construction duplicates every bus and line
+    with offset bus numbers and joins no copy to another."""
+    from paper_2302_10736_gb300 import synth
+    base = synth.grid(500, 660, 5)
+    rep = synth.replicated(base, 3)
+    assert rep["nb"] == 1500 and rep["nl"] == 1980
+    for c in range(3):
+        sl = slice(c * 660, (c + 1) * 660)
+        assert np.array_equal(rep["f"][sl], base["f"] + 500 * c) and np.array_equal(rep["t"][sl], base["t"] + 500 * c)
+        assert np.array_equal(rep["g"][sl], base["g"]) and np.array_equal(rep["gs"][c * 500:(c + 1) * 500], base["gs"])
+    assert np.all(rep["f"] // 500 == rep["t"] // 500)   # no branch between copies
+    w = synth.replicated_workload(2)
+    assert w["nb"] == 164000 and w["nl"] == 2 * 104121

@@ -161,12 +161,16 @@ def test_large_angles(pf):
 
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("window", [128, 256])
-def test_every_launch_configuration(pf, lanes, window):
+@pytest.mark.parametrize("fused", [0, 1])
+def test_every_launch_configuration(pf, lanes, window, fused):
+    """Every Ybus lane count, both forms of the Ybus method (the phasor step as
+    its own launch, or fused into the row kernel) and both element-wise
+    window sizes against the oracle."""
     gr = random_grid(1500, 2100, 10, shift_max=0.2)
     vm, va = random_state(1500, 10)
     grid = pf.ybus_build(gr)
-    pf.grid_set_config(grid, ybus_lanes=lanes, ew_window=window, ybus_block=256)
-    assert pf.grid_get_config(grid)["ew_window"] == window
+    pf.grid_set_config(grid, ybus_lanes=lanes, ew_window=window, ybus_block=256, ybus_fused=fused)
+    assert pf.grid_get_config(grid)["ew_window"] == window and pf.grid_get_config(grid)["ybus_fused"] == fused
     check_against_oracle(pf, gr, vm, va, grid=grid)
 
 
@@ -466,3 +470,45 @@ def test_storage_layout_study(pf, separate):
         res.append((P.cpu().numpy(), Q.cpu().numpy()))
     assert relerr(res[0][0], Pr) <= TOL and relerr(res[0][1], Qr) <= TOL
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_replicated_82k_grid(pf):
+    """The paper's ultra-large construction (Sec. V-C): the 82k-bus grid
+    repeated twice as disjoint copies, the same state in both.  Every copy's
+    P, Q and Jacobian block are bitwise those of the single 82k grid (both
+    methods); the whole grid matches the oracle within 1e-12."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    w = synth.replicated_workload(2, same_state=True)
+    base_nb = w["base_nb"]
+    base = {k: w[k] for k in ("g", "b", "bsh", "tap", "shift")}
+    half_l = w["base_nl"]
+    base = dict(nb=base_nb, nl=half_l, f=w["f"][:half_l], t=w["t"][:half_l], g=w["g"][:half_l], b=w["b"][:half_l],
+                bsh=w["bsh"][:half_l], tap=w["tap"][:half_l], shift=w["shift"][:half_l], gs=w["gs"][:base_nb],
+                bs=w["bs"][:base_nb])
+    vm, va = w["vm"][0], w["va"][0]
+    out = {}
+    for key, gr, n in (("full", w, w["nb"]), ("base", base, base_nb)):
+        grid = pf.ybus_build(gr)
+        for m, fn in ((1, pf.jac_elementwise), (0, pf.jac_ybus)):
+            P = torch.empty(n, dtype=torch.float64, device="cuda")
+            Q = torch.empty_like(P)
+            J = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+            fn(grid, _d(vm[:n]), _d(va[:n]), P, Q, J)
+            torch.cuda.synchronize()
+            out[key, m] = (P.cpu().numpy(), Q.cpu().numpy(), J.cpu().numpy(), grid.nnz)
+        pf.grid_check_error(grid)
+    for m in (0, 1):
+        P, Q, J, nnz = out["full", m]
+        Pb, Qb, Jb, nnzb = out["base", m]
+        assert nnz == 2 * nnzb
+        for c in range(2):
+            assert np.array_equal(P[c * base_nb:(c + 1) * base_nb], Pb)
+            assert np.array_equal(Q[c * base_nb:(c + 1) * base_nb], Qb)
+            assert np.array_equal(J[2 * c * nnzb:2 * (c + 1) * nnzb], Jb[:2 * nnzb])
+            assert np.array_equal(J[2 * nnz + 2 * c * nnzb:2 * nnz + 2 * (c + 1) * nnzb], Jb[2 * nnzb:])
+    Y = oracle.ybus(w)
+    Pr, Qr, Jr = oracle.elementwise(w, vm, va, Y)
+    for m in (0, 1):
+        P, Q, J, _ = out["full", m]
+        assert relerr(P, Pr) <= TOL and relerr(Q, Qr) <= TOL and relerr(J, Jr) <= TOL
