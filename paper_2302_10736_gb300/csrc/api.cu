@@ -141,6 +141,16 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
     if ((st = upload(a, &g->tpos, H.tpos, s))) return st;
     if ((st = upload(a, &g->tp, H.tp, s))) return st;
     if ((st = upload(a, &g->kd, H.kd, s))) return st;
+    {
+        std::vector<int> yrow(nb);
+        for (int c0 = 0; c0 < nb; c0 += kYbusRowChunk) {
+            const int c1 = std::min(nb, c0 + kYbusRowChunk);
+            for (int i = c0; i < c1; ++i) yrow[i] = i;
+            std::stable_sort(yrow.begin() + c0, yrow.begin() + c1,
+                             [&](int x, int y) { return H.rp[x + 1] - H.rp[x] > H.rp[y + 1] - H.rp[y]; });
+        }
+        if ((st = upload(a, &g->yrow, yrow, s))) return st;
+    }
     if ((st = upload(a, &g->tnbr, H.tnbr, s))) return st;
     if ((st = upload(a, &g->town, H.town, s))) return st;
     if ((st = upload(a, &g->tmir, H.tmir, s))) return st;

@@ -38,14 +38,16 @@ template <int W>
 constexpr int kChunkW = W >= 4 ? 1 : (W == 2 ? 2 : 4);
 
 template <int W>
-__global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict__ rp, const int *__restrict__ ci,
+__global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict__ yrow, const int *__restrict__ rp,
+                                                   const int *__restrict__ ci,
                                                    const double2 *__restrict__ Y, const double2 *__restrict__ V,
                                                    double *__restrict__ P, double *__restrict__ Q)
 {
     pdl_launch_dependents();   // the next evaluation's phasor launch may start (it waits for this grid)
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = (int)(gid / W), lane = (int)(gid % W);
-    const bool valid = row < nb;
+    const int grp = (int)(gid / W), lane = (int)(gid % W);
+    const bool valid = grp < nb;
+    const int row = valid ? yrow[grp] : 0;
     int rs = 0, d = 0;
     int jj[kChunkW<W>];
     double2 yy[kChunkW<W>];
@@ -103,15 +105,17 @@ __global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict_
 }
 
 template <int W>
-__global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__restrict__ rp,
+__global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__restrict__ yrow,
+                                                   const int *__restrict__ rp,
                                                    const int *__restrict__ ci, const double2 *__restrict__ Y,
                                                    const double4_32a *__restrict__ U, double *__restrict__ P,
                                                    double *__restrict__ Q, double *__restrict__ J)
 {
     pdl_launch_dependents();   // the next evaluation's phasor launch may start (it waits for this grid)
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = (int)(gid / W), lane = (int)(gid % W);
-    const bool valid = row < nb;
+    const int grp = (int)(gid / W), lane = (int)(gid % W);
+    const bool valid = grp < nb;
+    const int row = valid ? yrow[grp] : 0;
     int rs = 0, d = 0;
     int jj[kChunkW<W>];
     double2 yy[kChunkW<W>];
@@ -207,7 +211,8 @@ __global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__
 // phasor step fused: W lanes per row, each forming U_j = e^{j theta_j}, v_j for
 // its entries and the row's own V_i.
 template <int W, bool JAC>
-__global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *__restrict__ rp,
+__global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *__restrict__ yrow,
+                                                     const int *__restrict__ rp,
                                                      const int *__restrict__ ci, const double2 *__restrict__ Y,
                                                      const double *__restrict__ vm, const double *__restrict__ va,
                                                      const ITrig *__restrict__ trig, double *__restrict__ P,
@@ -216,8 +221,9 @@ __global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *
     __shared__ ITrig tab[kITrigN];
     pdl_launch_dependents();
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = (int)(gid / W), lane = (int)(gid % W);
-    const bool valid = row < nb;
+    const int grp = (int)(gid / W), lane = (int)(gid % W);
+    const bool valid = grp < nb;
+    const int row = valid ? yrow[grp] : 0;
     int rs = 0, d = 0;
     int jj[kChunkW<W>];
     if (valid) {
@@ -331,7 +337,7 @@ static cudaError_t fused_w(const Grid *g, const double *vm, const double *va, do
     const long long threads = (long long)g->nb * W;
     const int blk = g->cfg.ybus_block;
     return launch_k(k_ybus_fused<W, JAC>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, g->nnz,
-                    (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, vm, va, trig_table(), P, Q, J);
+                    (const int *)g->yrow, (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, vm, va, trig_table(), P, Q, J);
 }
 
 cudaError_t launch_ybus_fused(const Grid *g, bool jac, const double *vm, const double *va, double *P, double *Q,
@@ -352,7 +358,8 @@ static cudaError_t inj_w(const Grid *g, const double2 *V, double *P, double *Q, 
 {
     const long long threads = (long long)g->nb * W;
     const int blk = g->cfg.ybus_block;
-    return launch_k(k_inj_ybus<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, (const int *)g->rp,
+    return launch_k(k_inj_ybus<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, (const int *)g->yrow,
+                    (const int *)g->rp,
                     (const int *)g->ci, (const double2 *)g->yv, V, P, Q);
 }
 
@@ -362,7 +369,7 @@ static cudaError_t jac_w(const Grid *g, const double4_32a *U, double *P, double 
     const long long threads = (long long)g->nb * W;
     const int blk = g->cfg.ybus_block;
     return launch_k(k_jac_ybus<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, g->nnz,
-                    (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, U, P, Q, J);
+                    (const int *)g->yrow, (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, U, P, Q, J);
 }
 
 cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s)

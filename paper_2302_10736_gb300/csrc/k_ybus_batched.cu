@@ -60,7 +60,8 @@ __device__ __forceinline__ bool scen_value(const RowOutage &r, int i, int k, int
 }
 
 template <int W>
-__global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__restrict__ rp,
+__global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__restrict__ yrow,
+                                                     const int *__restrict__ rp,
                                                      const int *__restrict__ ci, const double2 *__restrict__ Y,
                                                      const double2 *__restrict__ tself,
                                                      const double2 *__restrict__ tcoup,
@@ -71,7 +72,8 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
     const long long row = gid / W;
     const int lane = (int)(gid % W);
     const bool valid = row < (long long)S * nb;
-    const int s = valid ? (int)(row / nb) : 0, i = valid ? (int)(row % nb) : 0;
+    // rows of each chunk by decreasing length (Grid::yrow)
+    const int s = valid ? (int)(row / nb) : 0, i = valid ? yrow[(int)(row % nb)] : 0;
     int rs = 0, d = 0;
     int jj[kChunkBW<W>];
     double2 yy[kChunkBW<W>];
@@ -127,13 +129,14 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
     }
     if (valid && lane == 0) {
         const double2 Vi = Vs[i];
-        P[row] = fma(Vi.x, Ir, Vi.y * Ii);   // S = V conj(I)
-        Q[row] = fma(Vi.y, Ir, -Vi.x * Ii);
+        P[(long long)s * nb + i] = fma(Vi.x, Ir, Vi.y * Ii);   // S = V conj(I)
+        Q[(long long)s * nb + i] = fma(Vi.y, Ir, -Vi.x * Ii);
     }
 }
 
 template <int W>
-__global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, const int *__restrict__ rp,
+__global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, const int *__restrict__ yrow,
+                                                     const int *__restrict__ rp,
                                                      const int *__restrict__ ci, const double2 *__restrict__ Y,
                                                      const double2 *__restrict__ tself,
                                                      const double2 *__restrict__ tcoup,
@@ -146,7 +149,8 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
     const long long row = gid / W;
     const int lane = (int)(gid % W);
     const bool valid = row < (long long)S * nb;
-    const int s = valid ? (int)(row / nb) : 0, i = valid ? (int)(row % nb) : 0;
+    // rows of each chunk by decreasing length (Grid::yrow)
+    const int s = valid ? (int)(row / nb) : 0, i = valid ? yrow[(int)(row % nb)] : 0;
     int rs = 0, d = 0;
     int jj[kChunkBW<W>];
     double2 yy[kChunkBW<W>];
@@ -249,8 +253,8 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
         Js[2 * nnzs + p + ds] = dVi;
     }
     if (lane == 0 && P) {
-        P[row] = Sr;
-        Q[row] = Si;
+        P[(long long)s * nb + i] = Sr;
+        Q[(long long)s * nb + i] = Si;
     }
 }
 
@@ -261,6 +265,7 @@ static cudaError_t inj_b(const Batch *b, double *P, double *Q, cudaStream_t s)
     const long long threads = (long long)b->S * g->nb * W;
     const int blk = b->cfg.ybus_block;
     return launch_k(k_inj_ybus_b<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, b->S, g->nb,
+                    (const int *)g->yrow,
                     (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, (const double2 *)g->tself,
                     (const double2 *)g->tcoup, (const ScenOut *)b->sc, (const double2 *)b->V, P, Q);
 }
@@ -272,6 +277,7 @@ static cudaError_t jac_b(const Batch *b, double *P, double *Q, double *J, cudaSt
     const long long threads = (long long)b->S * g->nb * W;
     const int blk = b->cfg.ybus_block;
     return launch_k(k_jac_ybus_b<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, b->S, g->nb, g->nnz,
+                    (const int *)g->yrow,
                     (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, (const double2 *)g->tself,
                     (const double2 *)g->tcoup, (const ScenOut *)b->sc, (const long long *)b->joff,
                     (const double4_32a *)b->U, P, Q, J);

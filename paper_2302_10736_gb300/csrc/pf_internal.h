@@ -176,6 +176,7 @@ __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max
     return p;
 }
 constexpr uint32_t kMaxSmem = 227u * 1024u;
+constexpr int kYbusRowChunk = 256;
 // shared memory of the (cos, sin) table every phasor-forming CTA holds
 constexpr uint32_t kTrigSmem = kITrigN * (uint32_t)sizeof(ITrig);
 // words of the batched kernels' grid-barrier state: parity, two counters on their
@@ -230,6 +231,10 @@ struct Grid {
     HostTopo topo;
     // Ybus (device)
     int *rp = nullptr, *ci = nullptr;
+    // the Ybus row kernels' thread-to-row map: each chunk of kYbusRowChunk rows
+    // by decreasing length (ties in row order), so a warp's rows take equally
+    // many loop trips and FP64 warp instructions keep their lanes busy
+    int *yrow = nullptr;
     double2 *yv = nullptr;
     int *ybeg = nullptr, *yend = nullptr, *ydiag = nullptr;
     int *kd = nullptr;                     // [nb] diagonal position per row
