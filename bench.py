@@ -184,15 +184,17 @@ def oracle_batch_baseline(w, kind, seconds):
     t0 = time.perf_counter()
     done = 0
     with ThreadPoolExecutor(nthr) as ex:
-        while done < S:
-            n = min(nthr, S - done)
-            list(ex.map(one, range(done, done + n)))
-            done += n
+        # scenarios in order (again from the first once all are done) until the
+        # time is up, a whole round of nthr at a time
+        while True:
+            list(ex.map(one, [(done + i) % S for i in range(nthr)]))
+            done += nthr
             if time.perf_counter() - t0 >= seconds:
                 break
     el = time.perf_counter() - t0
     return {"value": done / el, "unit": "scenarios/s", "cores": nthr, "nproc": ncpu, "cpu_model": model,
-            "kind": "oracle", "sample": "%d of the %d scenarios, %d threads, %.1f s" % (done, S, nthr, el)}
+            "kind": "oracle", "sample": "%d scenario evaluations (%d distinct), %d threads, %.1f s"
+                                        % (done, min(done, S), nthr, el)}
 
 
 def run_oracle_steps(w, nsteps, seconds=None):
