@@ -348,17 +348,38 @@ def grid_bytes(grid):
     return 4 * (grid.nb + 1) + 20 * grid.nnz + 60 * grid.nl + 60 * grid.nb
 
 
-def stream_loop(torch, fn_k, steps, name):
+STREAM_HOST_MARGIN_S = 40e-6   # host time allowed per queued launch of a stream
+
+
+def stream_loop(torch, fn_k, steps, name, info=None):
     """fn_k(k) for k = 0 .. steps-1 back to back on the current stream between
-    one pair of CUDA events; mean ms per step."""
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push(name)
-    e0.record()
-    for k in range(steps):
-        fn_k(k)
-    e1.record()
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
+    one pair of CUDA events; mean ms per step.  A device-side wait (torch's
+    spin kernel, before the first event) holds the GPU while the host queues
+    all the launches, so the device time is the GPU's own back-to-back rate
+    and not the host's launch rate (the end-to-end number includes the host).
+    If the host took longer than the wait, the run is repeated with a longer
+    one."""
+    margin = STREAM_HOST_MARGIN_S
+    for _ in range(4):
+        wait_s = steps * margin + 1e-3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        torch.cuda._sleep(int(wait_s * 2.1e9))
+        t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push(name)
+        e0.record()
+        for k in range(steps):
+            fn_k(k)
+        e1.record()
+        torch.cuda.nvtx.range_pop()
+        host_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        if host_s < 0.8 * wait_s:
+            break
+        margin *= 2.0
+    if info is not None:
+        info["host_enqueue_us_per_step"] = host_s / steps * 1e6
+        info["device_wait_ms"] = wait_s * 1e3
     return e0.elapsed_time(e1) / steps
 
 
@@ -868,7 +889,8 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ms_stream = stream_loop(torch, ew_k, args.steps, "ew_stream")   # the timed region of the headline
+    stream_info = {}
+    ms_stream = stream_loop(torch, ew_k, args.steps, "ew_stream", stream_info)   # the timed region of the headline
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -1001,6 +1023,10 @@ def main():
                        "l2": "inputs larger than L2: %d copies of the grid with their own states and outputs "
                              "(%.0f MB) evaluated in turn, %d steps back to back between one pair of CUDA events"
                              % (STREAM_COPIES, footprint / 1e6, args.steps),
+                       "launch_queue": "all %d launches queued behind a device-side wait of %.1f ms before the "
+                                       "first event (host: %.1f us per launch), so the device time is the GPU's "
+                                       "back-to-back rate" % (args.steps, stream_info["device_wait_ms"],
+                                                              stream_info["host_enqueue_us_per_step"]),
                        "launch_config": cfg},
             "e2e": e2e, "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "fp64_peak": fp64_peak,

@@ -172,6 +172,8 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
     PF_CUDA(a.alloc(&g->yv, (size_t)g->nnz));
     PF_CUDA(a.alloc(&g->tself, (size_t)T));
     PF_CUDA(a.alloc(&g->tcoup, (size_t)T));
+    PF_CUDA(a.alloc(&g->tcfx, (size_t)T));
+    PF_CUDA(a.alloc(&g->tce, (size_t)T));
     PF_CUDA(a.alloc(&g->br_aux, (size_t)g->nl));
     PF_CUDA(a.alloc(&g->bus_ysh, (size_t)nb));
     PF_CUDA(a.alloc(&g->ph_u, (size_t)nb));

@@ -185,8 +185,9 @@ __host__ __device__ __forceinline__ double q62_to_double(int64_t v)
     return bits_dbl(u ? (bits | sg) : 0ull);
 }
 
-// sin x and cos x for |x| < 2^16 (finite); tab: the 64-entry first-quadrant table
-__host__ __device__ __forceinline__ void int_sincos_core(double x, const ITrig *tab, double *s_out, double *c_out)
+// cos x and sin x for |x| < 2^16 (finite) as fractions scaled by 2^62 (|.| <= 2^62);
+// tab: the 64-entry first-quadrant table
+__host__ __device__ __forceinline__ void int_sincos_fix(double x, const ITrig *tab, int64_t *c_out, int64_t *s_out)
 {
     using namespace isc;
     const uint64_t bits = dbl_bits(x);
@@ -238,6 +239,15 @@ __host__ __device__ __forceinline__ void int_sincos_core(double x, const ITrig *
         cq = -cq;
         sq = -sq;
     }
+    *c_out = cq;
+    *s_out = sq;
+}
+
+// sin x and cos x for |x| < 2^16 (finite), each rounded once to the nearest double
+__host__ __device__ __forceinline__ void int_sincos_core(double x, const ITrig *tab, double *s_out, double *c_out)
+{
+    int64_t cq, sq;
+    int_sincos_fix(x, tab, &cq, &sq);
     *c_out = q62_to_double(cq);
     *s_out = q62_to_double(sq);
 }

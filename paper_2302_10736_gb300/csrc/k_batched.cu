@@ -34,6 +34,7 @@
 // parameter gradients come from the partials of Eqs. (5)-(6) by g, b, b_sh and
 // the tap, one thread per branch summing the scenarios in ascending order.
 #include "fastmath.cuh"
+#include "fixrot.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
 
@@ -49,6 +50,8 @@ struct BatchArgs {
     const int4 *desc;
     const int2 *tnbr;
     const double2 *yd, *tself, *tcoup;
+    const longlong2 *tcfx;
+    const int *tce;
     const ITrig *trig;
     const ScenOut *sc;
     const long long *joff;
@@ -101,6 +104,27 @@ __device__ __forceinline__ void batch_phasors(const BatchArgs &a, const ITrig *t
     }
 }
 
+// phase 1 of the Jacobian and injection batches: the phasors in the
+// fixed-point form of the single evaluation (fixrot.cuh), U[x] = {2^62 cos,
+// 2^62 sin (64-bit integers, stored bit for bit), v, 1/v (Jacobian only)}
+__device__ __forceinline__ void batch_phasors_fix(const BatchArgs &a, const ITrig *tab, bool jac)
+{
+    const int tid = threadIdx.x, TB = blockDim.x;
+    const int nchunk = (a.nb + TB - 1) / TB;
+    const long long nitem = (long long)a.S * nchunk;
+    for (long long it = blockIdx.x; it < nitem; it += gridDim.x) {
+        const int s = (int)(it / nchunk), c = (int)(it % nchunk);
+        const int o = c * TB + tid;
+        if (o < a.nb) {
+            const long long x = (long long)s * a.nb + o;
+            int64_t C, S;
+            int_sincos_q62(a.va[x], tab, &C, &S);
+            const double v = a.vm[x];
+            a.U[x] = make_double4_32a(__longlong_as_double(C), __longlong_as_double(S), v, jac ? fast_rcp(v) : 0.0);
+        }
+    }
+}
+
 // Window metadata of item (s, w) into shared memory, corrected for the
 // scenario's outage: {J-slice row offset, row length, diagonal position,
 // first terminal} per bus and the self sum Yd without the outage branch.
@@ -145,7 +169,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
     const ITrig *trig = a.trig + (blockIdx.x % kITrigCopies) * kITrigN;
     for (int k = tid; k < kITrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
-    batch_phasors(a, tab, JAC);
+    batch_phasors_fix(a, tab, JAC);
     if (!grid_barrier(gbar, a.bar, gridDim.x, 0, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
 
     const long long nitem = (long long)a.S * a.nwin;
@@ -177,15 +201,23 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
         __syncthreads();
         for (int i = tid; i < nt; i += TB) {
             const int p = t0 + i;
-            const double2 yc = a.tcoup[p];
+            const longlong2 yf = a.tcfx[p];
+            const int ey = a.tce[p];
             const int2 nq = a.tnbr[p];
             const int ol = a.town[p] - b0, o = b0 + ol;
             const bool masked = p == sc.ph || p == sc.pk;
-            const double2 Vo = a.V[sb + o];
+            // G = conj(Yc) V_o conj(U_q) on the integer pipe, as in the single evaluation
+            const double4_32a uo = a.U[sb + o], uq = a.U[sb + nq.x];
+            const int64_t Co = __double_as_longlong(uo.x), So = __double_as_longlong(uo.y);
+            const int64_t Cq = __double_as_longlong(uq.x), Sq = __double_as_longlong(uq.y);
+            int64_t Ar, Ai;
+            fix_phasor(Co, So, uo.z, &Ar, &Ai);
+            double Gr, Gi;
+            if (Ar == kFixNaN || Cq == kFixNaN || ey == 0 || !fix_G_fast(Ar, Ai, uo.z, Cq, Sq, yf.x, yf.y, ey, &Gr, &Gi)) {
+                const double2 yc = a.tcoup[p];
+                fix_G(Ar, Ai, uo.z, Co, So, Cq, Sq, 0, 0, 0, yc.x, yc.y, &Gr, &Gi);
+            }
             if (JAC) {
-                const double4_32a uq = a.U[sb + nq.x];
-                double Er = fma(Vo.x, uq.x, Vo.y * uq.y), Ei = fma(Vo.y, uq.x, -Vo.x * uq.y);
-                double Gr = fma(yc.x, Er, yc.y * Ei), Gi = fma(yc.x, Ei, -yc.y * Er);
                 if (masked) Gr = Gi = 0.0;
                 const double Kr = uq.z * Gr, Ki = uq.z * Gi;
                 const int kp = nq.y & EW_KMASK;
@@ -203,9 +235,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
                     jst[Ls + pos + d] = Gi;
                 }
             } else {
-                const double2 Vq = a.V[sb + nq.x];
-                const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
-                double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);
+                double Kr = uq.z * Gr, Ki = uq.z * Gi;
                 if (masked) Kr = Ki = 0.0;
                 skg[i] = make_double2(Kr, Ki);
             }
@@ -244,7 +274,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
                     }
                 }
                 const double4_32a uo = x == tid ? ub : a.U[sb + b0 + b];
-                const double v = uo.z, iv = uo.w, v2 = v * v, tv = v + v;
+                const double v = uo.z, iv = uo.w, v2 = v * v, tv = fix_twice(v);
                 const int pos = bm.x + bm.z;
                 jst[pos] = neg(sKi);
                 jst[pos + d] = fma(tv, y.x, sKr * iv);
@@ -919,6 +949,8 @@ static BatchArgs batch_args(Batch *b)
     a.yd = g->bus_yd;
     a.tself = g->tself;
     a.tcoup = g->tcoup;
+    a.tcfx = g->tcfx;
+    a.tce = g->tce;
     a.trig = trig_table();
     a.sc = b->sc;
     a.joff = b->joff;

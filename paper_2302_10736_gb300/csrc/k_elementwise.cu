@@ -19,8 +19,11 @@
 // cosine of the angle difference.  Its 8 partials (16 per branch):
 //     dS_t/dtheta_q = -j K_t            dS_t/dv_q = K_t / v_q = conj(Yc_t) V_o conj(U_q)
 //     dS_t/dtheta_o = +j K_t            dS_t/dv_o = 2 v_o conj(Ys_t) + K_t / v_o
-// The thread computes E = V_o conj(U_q), G = conj(Yc_t) E (= dS_t/dv_q) and
-// K_t = v_q G: 10 FP64 instructions, all 32 lanes busy.
+// The thread computes G = conj(Yc_t) V_o conj(U_q) (= dS_t/dv_q) in 64-bit
+// fixed point on the integer pipe (fixrot.cuh: the phasor table holds U as
+// 2^62-scaled integers and V_o in block floating point, the setup Yc_t), then
+// K_t = v_q G: 2 FP64 instructions.  The injections alone take the same steps
+// (K_t only).
 //
 // Reduction step (Eq. 7 and the copy-add of Fig. 2, without atomics).
 // Terminals are stored sorted by (owner, other bus), so a CTA owns a window of
@@ -50,6 +53,7 @@
 #include <algorithm>
 
 #include "fastmath.cuh"
+#include "fixrot.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
 
@@ -60,6 +64,8 @@ struct EwArgs {
     const int4 *desc, *bmeta;
     const int *slotbus, *town, *rorder;
     const double2 *yd, *tcoup;
+    const longlong2 *tcfx;
+    const int *tce;
     const ITrig *trig;
     const int2 *tloc;
     const double *vm, *va;
@@ -124,9 +130,9 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
     int *skp = reinterpret_cast<int *>(smem + sp.kp);
     double *jst = reinterpret_cast<double *>(smem + sp.jst);
     double *spq = reinterpret_cast<double *>(smem + sp.pq);
-    double2 *sV = reinterpret_cast<double2 *>(smem + sp.ph);                 // v e^{j theta}
-    double2 *sU = sV + a.max_nph;                                            // (cos, sin)
-    double2 *sW = sU + a.max_nph;                                            // (v, 1/v)
+    longlong2 *sA = reinterpret_cast<longlong2 *>(smem + sp.ph);             // own buses: V in block floating point
+    longlong2 *sU = sA + a.max_nph;                                          // 2^62 (cos, sin)
+    double2 *sW = reinterpret_cast<double2 *>(sU + a.max_nph);               // (v, 1/v)
     double2 *sW2 = reinterpret_cast<double2 *>(smem + sp.w2);               // own buses: (v^2, 2 v)
     int *sord = reinterpret_cast<int *>(smem + sp.ord);                     // reduction thread -> bus
     ITrig *tab = reinterpret_cast<ITrig *>(smem + sp.total);
@@ -186,8 +192,12 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         }
         double2 ydo = make_double2(0.0, 0.0);
         if (tid < nbus) ydo = a.yd[b0 + tid];
-        double2 yc = make_double2(0.0, 0.0);
-        if (tid < nt) yc = a.tcoup[t0 + tid];
+        longlong2 yf = make_longlong2(0, 0);
+        int ey = 0;
+        if (tid < nt) {
+            yf = a.tcfx[t0 + tid];
+            ey = a.tce[t0 + tid];
+        }
         if (load_tab) {
             if (tid < kITrigN) tab[tid] = tv0;
             for (int k = tid + TB; k < kITrigN; k += TB) tab[k] = trig[k];
@@ -202,25 +212,28 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                 th = a.va[o];
                 v = a.vm[o];
             }
-            double s, c;
-            int_sincos(th, tab, &s, &c);
-            if (JAC) {
-                sU[j] = make_double2(c, s);
-                // V and 1/v are read for the window's own buses only: warps of
-                // ghost slots skip them (a warp-uniform branch), mixed warps
-                // form them for all lanes; and (v^2, 2 v) for the reduction,
-                // formed once per bus instead of by both threads of its pair
-                double iv = 0.0;
-                if (__any_sync(__activemask(), j < nbus)) {
-                    sV[j] = make_double2(v * c, v * s);
-                    iv = fast_rcp(v);
-                    if (j < nbus) sW2[j] = make_double2(v * v, v + v);
-                }
-                sW[j] = make_double2(v, iv);
-            } else {
-                sV[j] = make_double2(v * c, v * s);
-                if (j < nbus) sW2[j].x = v * v;
+            int64_t C, S;
+            int_sincos_q62(th, tab, &C, &S);
+            sU[j] = make_longlong2(C, S);
+            double iv = 0.0;
+            if (j < nbus) {
+                int64_t ar, ai;
+                fix_phasor(C, S, v, &ar, &ai);
+                sA[j] = make_longlong2(ar, ai);
             }
+            if (JAC) {
+                // 1/v is read for the window's own buses only: warps of ghost
+                // slots skip it (a warp-uniform branch), mixed warps form it
+                // for all lanes; and (v^2, 2 v) for the reduction, formed once
+                // per bus instead of by both threads of its pair
+                if (__any_sync(__activemask(), j < nbus)) {
+                    iv = fast_rcp(v);
+                    if (j < nbus) sW2[j] = make_double2(v * v, fix_twice(v));
+                }
+            } else if (j < nbus) {
+                sW2[j].x = v * v;
+            }
+            sW[j] = make_double2(v, iv);
         }
         if (tid < nbus) {
             sbm[tid] = bmo;
@@ -233,20 +246,25 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         // ---- evaluation: one terminal per thread ----
         for (int i = tid; i < nt; i += TB) {
             if (i != tid) {
-                yc = a.tcoup[t0 + i];
+                yf = a.tcfx[t0 + i];
+                ey = a.tce[t0 + i];
                 nq = a.tloc[t0 + i];
                 ol = a.town[t0 + i];
             }
             ol -= b0;
-            const double2 Vo = sV[ol];
+            // G = conj(Yc) V_o conj(U_q) = dS_t/dv_q on the integer pipe (FP64
+            // products for the values the fixed-point form does not hold)
+            const longlong2 A = sA[ol], uq = sU[nq.x];
+            const double vo = sW[ol].x, vq = sW[nq.x].x;
+            double Gr, Gi;
+            if (A.x == kFixNaN || uq.x == kFixNaN || ey == 0 ||
+                !fix_G_fast(A.x, A.y, vo, uq.x, uq.y, yf.x, yf.y, ey, &Gr, &Gi)) {
+                const longlong2 uo = sU[ol];
+                const double2 yc = a.tcoup[t0 + i];
+                fix_G(A.x, A.y, vo, uo.x, uo.y, uq.x, uq.y, 0, 0, 0, yc.x, yc.y, &Gr, &Gi);
+            }
+            const double Kr = vq * Gr, Ki = vq * Gi;   // K_t = v_q G
             if (JAC) {
-                const double2 uq = sU[nq.x];
-                const double vq = sW[nq.x].x;
-                const double Er = fma(Vo.x, uq.x, Vo.y * uq.y);   // V_o conj(U_q)
-                const double Ei = fma(Vo.y, uq.x, -Vo.x * uq.y);
-                const double Gr = fma(yc.x, Er, yc.y * Ei);       // conj(Yc) E = dS_t/dv_q
-                const double Gi = fma(yc.x, Ei, -yc.y * Er);
-                const double Kr = vq * Gr, Ki = vq * Gi;           // K_t = v_q G
                 skg[2 * i] = make_double2(Kr, Ki);
                 skg[2 * i + 1] = make_double2(Gr, Gi);
                 skp[i] = nq.y;
@@ -259,10 +277,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                     jst[L + pos + d] = Gi;   // J22
                 }
             } else {
-                const double2 Vq = sV[nq.x];
-                const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y);   // V_o conj(V_q)
-                const double Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
-                skg[i] = make_double2(fma(yc.x, Wr, yc.y * Wi), fma(yc.x, Wi, -yc.y * Wr));   // K_t
+                skg[i] = make_double2(Kr, Ki);
             }
         }
         __syncthreads();
@@ -484,6 +499,8 @@ static cudaError_t launch_ew(Grid *g, const double *vm, const double *va, double
     a.town = g->town;
     a.yd = g->bus_yd;
     a.tcoup = g->tcoup;
+    a.tcfx = g->tcfx;
+    a.tce = g->tce;
     a.trig = trig_table();
     a.tloc = L.tloc;
     a.vm = vm;

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "fastmath.cuh"
+#include "fixrot.cuh"
 #include "isincos.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
@@ -34,6 +35,7 @@ __global__ void k_branch_constants(int nl, const double *__restrict__ g, const d
                                    const double *__restrict__ bsh, const double *__restrict__ tap,
                                    const double *__restrict__ shift, const int *__restrict__ tpos,
                                    double2 *__restrict__ tself, double2 *__restrict__ tcoup,
+                                   longlong2 *__restrict__ tcfx, int *__restrict__ tce,
                                    double4_32a *__restrict__ aux)
 {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,6 +54,12 @@ __global__ void k_branch_constants(int nl, const double *__restrict__ g, const d
     tcoup[ph] = make_double2(-ar * im, -ai * im);
     tself[pk] = ys_k;
     tcoup[pk] = make_double2(-br * im, -bi * im);
+    // the coupling constants in the block floating point of the element-wise kernels
+    int64_t fr, fi;
+    tce[ph] = fix_coupling(-ar * im, -ai * im, &fr, &fi);
+    tcfx[ph] = make_longlong2(fr, fi);
+    tce[pk] = fix_coupling(-br * im, -bi * im, &fr, &fi);
+    tcfx[pk] = make_longlong2(fr, fi);
     aux[l] = make_double4_32a(im, cp, sp, -(bl + half));   // for the parameter gradients of the adjoint
 }
 
@@ -153,7 +161,7 @@ cudaError_t launch_branch_constants(Grid *g, const double *gg, const double *gb,
 {
     if (g->nl > 0)
         k_branch_constants<<<nblk(g->nl, 256), 256, 0, s>>>(g->nl, gg, gb, gbsh, gtap, gshift, g->tpos, g->tself,
-                                                            g->tcoup, g->br_aux);
+                                                            g->tcoup, g->tcfx, g->tce, g->br_aux);
     return cudaGetLastError();
 }
 

@@ -157,8 +157,8 @@ struct EwSmem {
     uint32_t bm, yd, kg, kp, jst, pq, pqs, ph, ord, w2, total;
 };
 // max_nph > 0 (the single-evaluation kernel) adds a phasor table of that many
-// slots: V = v e^{j theta}, and with the Jacobian also (cos, sin) and (v, 1/v),
-// each a double2 array, and the ord and w2 arrays
+// slots: V of the own buses in block floating point and 2^62 (cos, sin), each
+// a pair of 64-bit integers, and (v, 1/v), and the ord and w2 arrays
 __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max_L, bool jac, int max_nph = 0)
 {
     EwSmem p;
@@ -170,7 +170,7 @@ __host__ __device__ inline EwSmem ew_smem_plan(int max_nbus, int max_nt, int max
     p.jst = p.kp + (jac ? ((4u * (uint32_t)max_nt + 15u) & ~15u) : 0u);
     p.pq = p.jst + (jac ? 16u * (uint32_t)max_L : 0u);
     p.ph = p.pq + 16u * p.pqs;
-    p.ord = p.ph + (jac ? 48u : 16u) * (uint32_t)max_nph;
+    p.ord = p.ph + 48u * (uint32_t)max_nph;
     p.w2 = p.ord + (max_nph > 0 ? (4u * (uint32_t)max_nbus + 15u) & ~15u : 0u);
     p.total = p.w2 + (max_nph > 0 ? 16u * (uint32_t)max_nbus : 0u);
     return p;
@@ -243,6 +243,10 @@ struct Grid {
     // terminals in sorted order (device)
     int *tp = nullptr;                     // [nb+1]
     double2 *tself = nullptr, *tcoup = nullptr;
+    // Yc in block floating point (fixrot.cuh): tcfx 2^(tce - 1085), tce = 0 where
+    // it is not representable (the kernels then take tcoup)
+    longlong2 *tcfx = nullptr;
+    int *tce = nullptr;
     int2 *br_hk = nullptr;                 // [nl] end buses (from, to) of branch l
     double4_32a *br_aux = nullptr;         // [nl] {1/m, cos phi, sin phi, -(b + b_sh/2)} of branch l (with the constants)
     int2 *tnbr = nullptr;                  // {other bus, kpos | EW_ACCUM}
