@@ -170,6 +170,8 @@ static pf_status upload_topology(Grid *g, cudaStream_t s)
     if ((st = upload(a, &g->jrp, H.jrp, s))) return st;
     if ((st = upload(a, &g->jci, H.jci, s))) return st;
     PF_CUDA(a.alloc(&g->yv, (size_t)g->nnz));
+    PF_CUDA(a.alloc(&g->yfx, (size_t)g->nnz));
+    PF_CUDA(a.alloc(&g->yce, (size_t)g->nnz));
     PF_CUDA(a.alloc(&g->tself, (size_t)T));
     PF_CUDA(a.alloc(&g->tcoup, (size_t)T));
     PF_CUDA(a.alloc(&g->tcfx, (size_t)T));
@@ -420,11 +422,12 @@ PF_API pf_status inj_ybus(pf_grid *grid, const double *vm, const double *va, dou
     }
     {
         TraceScope t(g, PF_K_PHASOR, s);
-        PF_CUDA(launch_phasor(g->nb, vm, va, g->ph_u, g->ph_v, s));
+        PF_CUDA(launch_phasor_fix(g->nb, vm, va, g->ph_u, s));
     }
     {
         TraceScope t(g, PF_K_INJ_YBUS, s);
-        PF_CUDA(launch_inj_ybus(g, g->ph_v, P, Q, s));
+        PF_CUDA(launch_ybus_rows(g, 1, false, nullptr, nullptr, g->ph_u, false, P, Q, nullptr, g->cfg.ybus_lanes,
+                                 g->cfg.ybus_block, s));
     }
     return PF_OK;
 }
@@ -462,11 +465,12 @@ PF_API pf_status jac_ybus(pf_grid *grid, const double *vm, const double *va, dou
     }
     {
         TraceScope t(g, PF_K_PHASOR, s);
-        PF_CUDA(launch_phasor(g->nb, vm, va, g->ph_u, g->ph_v, s));
+        PF_CUDA(launch_phasor_fix(g->nb, vm, va, g->ph_u, s));
     }
     {
         TraceScope t(g, PF_K_JAC_YBUS, s);
-        PF_CUDA(launch_jac_ybus(g, g->ph_u, P, Q, J, s));
+        PF_CUDA(launch_ybus_rows(g, 1, false, nullptr, nullptr, g->ph_u, true, P, Q, J, g->cfg.ybus_lanes,
+                                 g->cfg.ybus_block, s));
     }
     return PF_OK;
 }

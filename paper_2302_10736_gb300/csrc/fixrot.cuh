@@ -129,11 +129,12 @@ __host__ __device__ __forceinline__ void fix_E(int64_t Ar, int64_t Ai, double vo
         fix_E_fast(Ar, Ai, vo, Cq, Sq, er, ei);
 }
 
-// Yc = (yr, yi) in block floating point: (*fr, *fi) 2^(e - 1085) with e the
-// larger biased exponent of yr, yi (the larger component exact, in [2^62,
-// 2^63)); returns e, or 0 if Yc is zero, subnormal, non-finite or beyond the
-// exponent range (the kernels then multiply in FP64).  Setup arithmetic.
-__host__ __device__ __forceinline__ int fix_coupling(double yr, double yi, int64_t *fr, int64_t *fi)
+// A complex constant y = (yr, yi) (a coupling constant Yc, a Ybus value) in
+// block floating point: (*fr, *fi) 2^(e - 1085) with e the larger biased
+// exponent of yr, yi (the larger component exact, in [2^62, 2^63)); returns e,
+// or 0 if y is zero, subnormal, non-finite or beyond the exponent range (the
+// kernels then multiply in FP64).  Setup arithmetic.
+__host__ __device__ __forceinline__ int fix_block(double yr, double yi, int64_t *fr, int64_t *fi)
 {
     const int er = fix_vexp(yr), ei = fix_vexp(yi);
     const int e = er > ei ? er : ei;
@@ -153,22 +154,68 @@ __host__ __device__ __forceinline__ int fix_coupling(double yr, double yi, int64
     return e;
 }
 
+// a conj(b) 2^-64 and a b 2^-64 of two fixed-point complex numbers (the high
+// words of the products; |a| |b| < 2^126)
+__host__ __device__ __forceinline__ void fix_mul_conj(int64_t ar, int64_t ai, int64_t br, int64_t bi, int64_t *r,
+                                                      int64_t *i)
+{
+    *r = s64_mulhi(ar, br) + s64_mulhi(ai, bi);
+    *i = s64_mulhi(ai, br) - s64_mulhi(ar, bi);
+}
+__host__ __device__ __forceinline__ void fix_mul(int64_t ar, int64_t ai, int64_t br, int64_t bi, int64_t *r,
+                                                 int64_t *i)
+{
+    *r = s64_mulhi(ar, br) - s64_mulhi(ai, bi);
+    *i = s64_mulhi(ar, bi) + s64_mulhi(ai, br);
+}
+
 // G = conj(Yc) V_o conj(U_q) (= dS_t/dv_q) entirely in fixed point: (Ar, Ai) =
 // fix_phasor(Co, So, vo) and (Cq, Sq) = U_q not the marker, (Yr, Yi, ey) =
-// fix_coupling(Yc) with ey != 0.  Returns false (nothing written) when the
+// fix_block(Yc) with ey != 0.  Returns false (nothing written) when the
 // product's exponent leaves the range of normal doubles.
 __host__ __device__ __forceinline__ bool fix_G_fast(int64_t Ar, int64_t Ai, double vo, int64_t Cq, int64_t Sq,
                                                     int64_t Yr, int64_t Yi, int ey, double *gr, double *gi)
 {
     const int e1 = ey + fix_vexp(vo) - 1017;   // G = g 2^(ey + e_o - 2102), |g| < 2^59
     if (e1 < 64 || e1 > 2046) return false;
-    const int64_t br = s64_mulhi(Ar, Cq) + s64_mulhi(Ai, Sq);   // E = B 2^(e_o - 1081)
-    const int64_t bi = s64_mulhi(Ai, Cq) - s64_mulhi(Ar, Sq);
-    const int64_t g_r = s64_mulhi(Yr, br) + s64_mulhi(Yi, bi);
-    const int64_t g_i = s64_mulhi(Yr, bi) - s64_mulhi(Yi, br);
+    int64_t br, bi, g_r, g_i;
+    fix_mul_conj(Ar, Ai, Cq, Sq, &br, &bi);   // E = B 2^(e_o - 1081)
+    fix_mul_conj(br, bi, Yr, Yi, &g_r, &g_i);   // conj(Yc) E
     *gr = fix_to_double(g_r, e1);
     *gi = fix_to_double(g_i, e1);
     return true;
+}
+
+// The Ybus method's products for entry (i, j) in fixed point (Eqs. 3-4):
+// YU = Y_ij U_j (|yu| < 2^62, YU = yu 2^(ey - 1083)) and dS_i/dv_j =
+// V_i conj(YU), from (Yr, Yi, ey) = fix_block(Y_ij) with ey != 0, (C, S) = U_j
+// and (Ar, Ai) = fix_phasor of V_i, neither the marker.  Returns false
+// (nothing written) when dS_i/dv_j's exponent leaves the range of normal
+// doubles.
+__host__ __device__ __forceinline__ bool fix_ybus_entry(int64_t Yr, int64_t Yi, int ey, int64_t C, int64_t S,
+                                                        int64_t Ar, int64_t Ai, double vi, double *yur,
+                                                        double *yui, double *svr, double *svi)
+{
+    const int e1 = ey + fix_vexp(vi) - 1017;   // dS/dv = sv 2^(ey + e_i - 2102), |sv| < 2^59
+    if (e1 < 64 || e1 > 2046) return false;
+    int64_t ur, ui, sr, si;
+    fix_mul(Yr, Yi, C, S, &ur, &ui);
+    fix_mul_conj(Ar, Ai, ur, ui, &sr, &si);
+    *yur = fix_to_double(ur, ey + 2);
+    *yui = fix_to_double(ui, ey + 2);
+    *svr = fix_to_double(sr, e1);
+    *svi = fix_to_double(si, e1);
+    return true;
+}
+
+// Y_ij U_j alone (the injections): yu 2^(ey - 1083) rounded to doubles
+__host__ __device__ __forceinline__ void fix_ybus_yu(int64_t Yr, int64_t Yi, int ey, int64_t C, int64_t S,
+                                                     double *yur, double *yui)
+{
+    int64_t ur, ui;
+    fix_mul(Yr, Yi, C, S, &ur, &ui);
+    *yur = fix_to_double(ur, ey + 2);
+    *yui = fix_to_double(ui, ey + 2);
 }
 
 // G = conj(Yc) E: the fixed-point product where it applies, else E (fixed

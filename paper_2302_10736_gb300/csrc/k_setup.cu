@@ -56,9 +56,9 @@ __global__ void k_branch_constants(int nl, const double *__restrict__ g, const d
     tcoup[pk] = make_double2(-br * im, -bi * im);
     // the coupling constants in the block floating point of the element-wise kernels
     int64_t fr, fi;
-    tce[ph] = fix_coupling(-ar * im, -ai * im, &fr, &fi);
+    tce[ph] = fix_block(-ar * im, -ai * im, &fr, &fi);
     tcfx[ph] = make_longlong2(fr, fi);
-    tce[pk] = fix_coupling(-br * im, -bi * im, &fr, &fi);
+    tce[pk] = fix_block(-br * im, -bi * im, &fr, &fi);
     tcfx[pk] = make_longlong2(fr, fi);
     aux[l] = make_double4_32a(im, cp, sp, -(bl + half));   // for the parameter gradients of the adjoint
 }
@@ -66,7 +66,7 @@ __global__ void k_branch_constants(int nl, const double *__restrict__ g, const d
 __global__ void k_ybus_values(int nnz, const int *__restrict__ ybeg, const int *__restrict__ yend,
                               const int *__restrict__ ydiag, const double2 *__restrict__ tself,
                               const double2 *__restrict__ tcoup, const double2 *__restrict__ bus_ysh,
-                              double2 *__restrict__ yv)
+                              double2 *__restrict__ yv, longlong2 *__restrict__ yfx, int *__restrict__ yce)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnz) return;
@@ -79,6 +79,9 @@ __global__ void k_ybus_values(int nnz, const int *__restrict__ ybeg, const int *
         acc.y += c.y;
     }
     yv[e] = acc;
+    int64_t fr, fi;
+    yce[e] = fix_block(acc.x, acc.y, &fr, &fi);   // the fixed-point form of the Ybus kernels
+    yfx[e] = make_longlong2(fr, fi);
 }
 
 // Per-bus self sum Yd = y_sh + sum of the self constants of the bus's
@@ -126,6 +129,24 @@ __global__ void __launch_bounds__(256) k_phasor(int nb, const double *__restrict
     V[i] = make_double2(v * c, v * s);
 }
 
+// The phasor step in the fixed-point form of the batched Ybus kernels
+// (fixrot.cuh): U = {2^62 cos, 2^62 sin (64-bit integers stored bit for bit),
+// v, 0}; no FP64 instruction.
+__global__ void __launch_bounds__(256) k_phasor_fix(int nb, const double *__restrict__ vm,
+                                                    const double *__restrict__ va, double4_32a *__restrict__ U)
+{
+    __shared__ ITrig tab[kITrigN];
+    pdl_launch_dependents();
+    if (threadIdx.x < kITrigN) tab[threadIdx.x] = g_itrig_tab[(blockIdx.x % kITrigCopies) * kITrigN + threadIdx.x];
+    pdl_wait();
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int64_t c, s;
+    int_sincos_q62(va[i], tab, &c, &s);
+    U[i] = make_double4_32a(__longlong_as_double(c), __longlong_as_double(s), vm[i], 0.0);
+}
+
 // Upload the trig table once per device (synchronous, first use only).
 static std::mutex g_trig_mu;
 static const ITrig *g_trig_ptr[256] = {nullptr};
@@ -170,9 +191,15 @@ cudaError_t launch_ybus_values(Grid *g, const double *gs, const double *bs, cuda
     if (g->nb > 0) k_bus_shunt<<<nblk(g->nb, 256), 256, 0, s>>>(g->nb, gs, bs, g->bus_ysh);
     if (g->nnz > 0)
         k_ybus_values<<<nblk(g->nnz, 256), 256, 0, s>>>(g->nnz, g->ybeg, g->yend, g->ydiag, g->tself, g->tcoup,
-                                                        g->bus_ysh, g->yv);
+                                                        g->bus_ysh, g->yv, g->yfx, g->yce);
     if (g->nb > 0) k_bus_yd<<<nblk(g->nb, 256), 256, 0, s>>>(g->nb, g->tp, g->tself, g->bus_ysh, g->bus_yd);
     return cudaGetLastError();
+}
+
+cudaError_t launch_phasor_fix(int nb, const double *vm, const double *va, double4_32a *U, cudaStream_t s)
+{
+    if (nb > 0) return launch_k(k_phasor_fix, nblk(nb, 256), 256, 0, s, true, nb, vm, va, U);
+    return cudaSuccess;
 }
 
 cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32a *U, double2 *V, cudaStream_t s)

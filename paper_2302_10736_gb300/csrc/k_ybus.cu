@@ -20,13 +20,16 @@
 // programmatic-dependent-launch wait; the phasor gathers of a chunk are issued
 // together before its arithmetic.
 //
-// Two forms: the paper's step 1 as its own launch (k_phasor writes U, V for
-// every bus, the row kernels gather them), or fused (k_ybus_fused: each lane
-// forms the phasors of its entries' columns from vm, va itself, with the
-// integer-pipe sine/cosine of isincos.cuh, so one launch evaluates and nothing
-// goes through memory in between; a bus's phasor is formed once per entry of
-// its column, about 3.5 times on these grids).
+// Two forms: the paper's step 1 as its own launch (k_phasor_fix writes the
+// fixed-point phasors of every bus once, and the row kernels of
+// k_ybus_batched.cu gather them, as for a batch of one scenario without
+// outage), or fused (k_ybus_fused: each lane forms the phasors of its entries'
+// columns from vm, va itself, with the integer-pipe sine/cosine of
+// isincos.cuh, so one launch evaluates and nothing goes through memory in
+// between; a bus's phasor is formed once per entry of its column, about 3.5
+// times on these grids).  The autotuner picks the form.
 #include "fastmath.cuh"
+#include "fixrot.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
 
@@ -37,183 +40,20 @@ namespace pf {
 template <int W>
 constexpr int kChunkW = W >= 4 ? 1 : (W == 2 ? 2 : 4);
 
-template <int W>
-__global__ void __launch_bounds__(512) k_inj_ybus(int nb, const int *__restrict__ yrow, const int *__restrict__ rp,
-                                                   const int *__restrict__ ci,
-                                                   const double2 *__restrict__ Y, const double2 *__restrict__ V,
-                                                   double *__restrict__ P, double *__restrict__ Q)
-{
-    pdl_launch_dependents();   // the next evaluation's phasor launch may start (it waits for this grid)
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int grp = (int)(gid / W), lane = (int)(gid % W);
-    const bool valid = grp < nb;
-    const int row = valid ? yrow[grp] : 0;
-    int rs = 0, d = 0;
-    int jj[kChunkW<W>];
-    double2 yy[kChunkW<W>];
-    if (valid) {
-        rs = rp[row];
-        d = rp[row + 1] - rs;
-    }
-#pragma unroll
-    for (int j = 0; j < kChunkW<W>; ++j) {
-        const int k = lane + W * j;
-        if (k < d) jj[j] = ci[rs + k];
-    }
-    pdl_wait();
-#pragma unroll
-    for (int j = 0; j < kChunkW<W>; ++j) {
-        const int k = lane + W * j;
-        if (k < d) yy[j] = Y[rs + k];   // parameter-dependent: after the wait
-    }
-    double Ir = 0.0, Ii = 0.0;
-    for (int k0 = lane; k0 < d; k0 += W * kChunkW<W>) {
-        if (k0 != lane) {
-#pragma unroll
-            for (int j = 0; j < kChunkW<W>; ++j) {
-                const int k = k0 + W * j;
-                if (k < d) {
-                    jj[j] = ci[rs + k];
-                    yy[j] = Y[rs + k];
-                }
-            }
-        }
-        double2 vv[kChunkW<W>];
-#pragma unroll
-        for (int j = 0; j < kChunkW<W>; ++j)
-            if (k0 + W * j < d) vv[j] = V[jj[j]];
-#pragma unroll
-        for (int j = 0; j < kChunkW<W>; ++j) {
-            if (k0 + W * j < d) {
-                Ir = fma(yy[j].x, vv[j].x, Ir);
-                Ir = fma(-yy[j].y, vv[j].y, Ir);
-                Ii = fma(yy[j].x, vv[j].y, Ii);
-                Ii = fma(yy[j].y, vv[j].x, Ii);
-            }
-        }
-    }
-#pragma unroll
-    for (int off = W / 2; off > 0; off >>= 1) {
-        Ir += __shfl_xor_sync(0xffffffffu, Ir, off, W);
-        Ii += __shfl_xor_sync(0xffffffffu, Ii, off, W);
-    }
-    if (valid && lane == 0) {
-        const double2 Vi = V[row];
-        P[row] = fma(Vi.x, Ir, Vi.y * Ii);   // S = V conj(I)
-        Q[row] = fma(Vi.y, Ir, -Vi.x * Ii);
-    }
-}
-
-template <int W>
-__global__ void __launch_bounds__(512) k_jac_ybus(int nb, int nnz, const int *__restrict__ yrow,
-                                                   const int *__restrict__ rp,
-                                                   const int *__restrict__ ci, const double2 *__restrict__ Y,
-                                                   const double4_32a *__restrict__ U, double *__restrict__ P,
-                                                   double *__restrict__ Q, double *__restrict__ J)
-{
-    pdl_launch_dependents();   // the next evaluation's phasor launch may start (it waits for this grid)
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int grp = (int)(gid / W), lane = (int)(gid % W);
-    const bool valid = grp < nb;
-    const int row = valid ? yrow[grp] : 0;
-    int rs = 0, d = 0;
-    int jj[kChunkW<W>];
-    double2 yy[kChunkW<W>];
-    if (valid) {
-        rs = rp[row];
-        d = rp[row + 1] - rs;
-    }
-#pragma unroll
-    for (int j = 0; j < kChunkW<W>; ++j) {
-        const int k = lane + W * j;
-        if (k < d) jj[j] = ci[rs + k];
-    }
-    pdl_wait();
-#pragma unroll
-    for (int j = 0; j < kChunkW<W>; ++j) {
-        const int k = lane + W * j;
-        if (k < d) yy[j] = Y[rs + k];   // parameter-dependent: after the wait
-    }
-    double Ir = 0.0, Ii = 0.0;
-    double dTr = 0.0, dTi = 0.0, dVr = 0.0, dVi = 0.0;  // diagonal partials (lane that owns it)
-    int kd = -1;
-    double4_32a ui = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    if (valid) ui = U[row];
-    const double Vr = ui.z * ui.x, Vi = ui.z * ui.y;
-    for (int k0 = lane; k0 < d; k0 += W * kChunkW<W>) {
-        if (k0 != lane) {
-#pragma unroll
-            for (int j = 0; j < kChunkW<W>; ++j) {
-                const int k = k0 + W * j;
-                if (k < d) {
-                    jj[j] = ci[rs + k];
-                    yy[j] = Y[rs + k];
-                }
-            }
-        }
-        double4_32a uu[kChunkW<W>];
-#pragma unroll
-        for (int j = 0; j < kChunkW<W>; ++j)
-            if (k0 + W * j < d) uu[j] = U[jj[j]];
-#pragma unroll
-        for (int j = 0; j < kChunkW<W>; ++j) {
-            const int k = k0 + W * j;
-            if (k < d) {
-                const double YUr = fma(yy[j].x, uu[j].x, -yy[j].y * uu[j].y);
-                const double YUi = fma(yy[j].x, uu[j].y, yy[j].y * uu[j].x);
-                const double sVr = fma(Vr, YUr, Vi * YUi);    // V_i conj(YU)
-                const double sVi = fma(Vi, YUr, -Vr * YUi);
-                const double vj = uu[j].z;
-                Ir = fma(vj, YUr, Ir);
-                Ii = fma(vj, YUi, Ii);
-                const double sTr = vj * sVi, sTi = -vj * sVr;   // -j v_j dS/dv_j
-                if (jj[j] == row) {
-                    kd = k;
-                    dTr = sTr;
-                    dTi = sTi;
-                    dVr = sVr;
-                    dVi = sVi;
-                } else {
-                    const int p = 2 * rs + k;
-                    J[p] = sTr;
-                    J[p + d] = sVr;
-                    J[2 * nnz + p] = sTi;
-                    J[2 * nnz + p + d] = sVi;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int off = W / 2; off > 0; off >>= 1) {
-        Ir += __shfl_xor_sync(0xffffffffu, Ir, off, W);
-        Ii += __shfl_xor_sync(0xffffffffu, Ii, off, W);
-    }
-    if (!valid) return;
-    const double Sr = fma(Vr, Ir, Vi * Ii), Si = fma(Vi, Ir, -Vr * Ii);
-    if (kd >= 0) {
-        dTr -= Si;                           // + j S_i  (= j V_i conj(I_i))
-        dTi += Sr;
-        dVr += fma(Ir, ui.x, Ii * ui.y);     // + conj(I_i) U_i
-        dVi += fma(Ir, ui.y, -Ii * ui.x);
-        const int p = 2 * rs + kd;
-        J[p] = dTr;
-        J[p + d] = dVr;
-        J[2 * nnz + p] = dTi;
-        J[2 * nnz + p + d] = dVi;
-    }
-    if (lane == 0 && P) {
-        P[row] = Sr;
-        Q[row] = Si;
-    }
-}
-
 // Injections (JAC = false) or injections and Jacobian (JAC = true) with the
 // phasor step fused: W lanes per row, each forming U_j = e^{j theta_j}, v_j for
-// its entries and the row's own V_i.
+// its entries and the row's own V_i.  With the Jacobian the complex products
+// Y_ij U_j and V_i conj(Y_ij U_j) run in 64-bit fixed point on the integer
+// pipe (fixrot.cuh, from the 2^62-scaled sine and cosine and the setup's
+// block-floating Ybus values), the sums I_i = sum_j v_j (Y_ij U_j),
+// S_i = V_i conj(I_i) and the Jacobian scalings by v_j in FP64 (values the
+// fixed-point form does not hold take FP64 products); the injections alone
+// take FP64 products.
 template <int W, bool JAC>
 __global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *__restrict__ yrow,
                                                      const int *__restrict__ rp,
                                                      const int *__restrict__ ci, const double2 *__restrict__ Y,
+                                                     const longlong2 *__restrict__ Yf, const int *__restrict__ Ye,
                                                      const double *__restrict__ vm, const double *__restrict__ va,
                                                      const ITrig *__restrict__ trig, double *__restrict__ P,
                                                      double *__restrict__ Q, double *__restrict__ J)
@@ -237,17 +77,30 @@ __global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *
     }
     for (int k = threadIdx.x; k < kITrigN; k += blockDim.x) tab[k] = trig[(blockIdx.x % kITrigCopies) * kITrigN + k];
     pdl_wait();   // the state and the Ybus values may be the previous kernel's
+    // the Jacobian takes the block-floating values, the injections the doubles
+    longlong2 yf[kChunkW<W>];
+    int ye[kChunkW<W>];
     double2 yy[kChunkW<W>];
 #pragma unroll
     for (int j = 0; j < kChunkW<W>; ++j) {
         const int k = lane + W * j;
-        if (k < d) yy[j] = Y[rs + k];
+        if (k < d) {
+            if (JAC) {
+                yf[j] = Yf[rs + k];
+                ye[j] = Ye[rs + k];
+            } else {
+                yy[j] = Y[rs + k];
+            }
+        }
     }
     const double thi = valid ? va[row] : 0.0, vi = valid ? vm[row] : 0.0;
     __syncthreads();   // the table
-    double si, cs;
-    int_sincos(thi, tab, &si, &cs);
+    int64_t Crow, Srow;   // 2^62 (cos, sin) of the row's own angle
+    int_sincos_q62(thi, tab, &Crow, &Srow);
+    const double cs = fix_q62_or_nan(Crow), si = Crow == kFixNaN ? cs : q62_to_double(Srow);
     const double Vr = vi * cs, Vi = vi * si;
+    int64_t Ari = kFixNaN, Aii = 0;
+    if (JAC) fix_phasor(Crow, Srow, vi, &Ari, &Aii);
     double Ir = 0.0, Ii = 0.0;
     double dTr = 0.0, dTi = 0.0, dVr = 0.0, dVi = 0.0;   // diagonal partials (lane that owns it)
     int kd = -1;
@@ -258,7 +111,12 @@ __global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *
                 const int k = k0 + W * j;
                 if (k < d) {
                     jj[j] = ci[rs + k];
-                    yy[j] = Y[rs + k];
+                    if (JAC) {
+                        yf[j] = Yf[rs + k];
+                        ye[j] = Ye[rs + k];
+                    } else {
+                        yy[j] = Y[rs + k];
+                    }
                 }
             }
         }
@@ -272,14 +130,21 @@ __global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *
 #pragma unroll
         for (int j = 0; j < kChunkW<W>; ++j) {
             const int k = k0 + W * j;
-            if (k < d) {
-                double s, c;
-                int_sincos(thj[j], tab, &s, &c);
-                if (JAC) {
-                    const double YUr = fma(yy[j].x, c, -yy[j].y * s);   // Y_ij U_j
-                    const double YUi = fma(yy[j].x, s, yy[j].y * c);
-                    const double sVr = fma(Vr, YUr, Vi * YUi);          // V_i conj(YU)
-                    const double sVi = fma(Vi, YUr, -Vr * YUi);
+            if (k < d && JAC) {
+                int64_t C, S;
+                int_sincos_q62(thj[j], tab, &C, &S);
+                double YUr, YUi;   // Y_ij U_j
+                {
+                    double sVr, sVi;   // V_i conj(YU)
+                    if (ye[j] == 0 || C == kFixNaN || Ari == kFixNaN ||
+                        !fix_ybus_entry(yf[j].x, yf[j].y, ye[j], C, S, Ari, Aii, vi, &YUr, &YUi, &sVr, &sVi)) {
+                        const double2 y = Y[rs + k];
+                        const double c = fix_q62_or_nan(C), s = C == kFixNaN ? c : q62_to_double(S);
+                        YUr = fma(y.x, c, -y.y * s);
+                        YUi = fma(y.x, s, y.y * c);
+                        sVr = fma(Vr, YUr, Vi * YUi);
+                        sVi = fma(Vi, YUr, -Vr * YUi);
+                    }
                     Ir = fma(vj[j], YUr, Ir);
                     Ii = fma(vj[j], YUi, Ii);
                     const double sTr = vj[j] * sVi, sTi = -vj[j] * sVr;   // -j v_j dS/dv_j
@@ -296,13 +161,17 @@ __global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *
                         J[2 * nnz + p] = sTi;
                         J[2 * nnz + p + d] = sVi;
                     }
-                } else {
-                    const double Vjr = vj[j] * c, Vji = vj[j] * s;
-                    Ir = fma(yy[j].x, Vjr, Ir);
-                    Ir = fma(-yy[j].y, Vji, Ir);
-                    Ii = fma(yy[j].x, Vji, Ii);
-                    Ii = fma(yy[j].y, Vjr, Ii);
                 }
+            } else if (k < d) {
+                // the injections alone: I_i += Y_ij V_j by FP64 products (the
+                // per-entry sine and cosine already load the integer pipe)
+                double s, c;
+                int_sincos(thj[j], tab, &s, &c);
+                const double Vjr = vj[j] * c, Vji = vj[j] * s;
+                Ir = fma(yy[j].x, Vjr, Ir);
+                Ir = fma(-yy[j].y, Vji, Ir);
+                Ii = fma(yy[j].x, Vji, Ii);
+                Ii = fma(yy[j].y, Vjr, Ii);
             }
         }
     }
@@ -337,7 +206,8 @@ static cudaError_t fused_w(const Grid *g, const double *vm, const double *va, do
     const long long threads = (long long)g->nb * W;
     const int blk = g->cfg.ybus_block;
     return launch_k(k_ybus_fused<W, JAC>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, g->nnz,
-                    (const int *)g->yrow, (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, vm, va, trig_table(), P, Q, J);
+                    (const int *)g->yrow, (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv,
+                    (const longlong2 *)g->yfx, (const int *)g->yce, vm, va, trig_table(), P, Q, J);
 }
 
 cudaError_t launch_ybus_fused(const Grid *g, bool jac, const double *vm, const double *va, double *P, double *Q,
@@ -350,49 +220,6 @@ cudaError_t launch_ybus_fused(const Grid *g, bool jac, const double *vm, const d
     case 8: return jac ? fused_w<8, true>(g, vm, va, P, Q, J, s) : fused_w<8, false>(g, vm, va, P, Q, J, s);
     case 16: return jac ? fused_w<16, true>(g, vm, va, P, Q, J, s) : fused_w<16, false>(g, vm, va, P, Q, J, s);
     default: return jac ? fused_w<32, true>(g, vm, va, P, Q, J, s) : fused_w<32, false>(g, vm, va, P, Q, J, s);
-    }
-}
-
-template <int W>
-static cudaError_t inj_w(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s)
-{
-    const long long threads = (long long)g->nb * W;
-    const int blk = g->cfg.ybus_block;
-    return launch_k(k_inj_ybus<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, (const int *)g->yrow,
-                    (const int *)g->rp,
-                    (const int *)g->ci, (const double2 *)g->yv, V, P, Q);
-}
-
-template <int W>
-static cudaError_t jac_w(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s)
-{
-    const long long threads = (long long)g->nb * W;
-    const int blk = g->cfg.ybus_block;
-    return launch_k(k_jac_ybus<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, g->nb, g->nnz,
-                    (const int *)g->yrow, (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, U, P, Q, J);
-}
-
-cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s)
-{
-    switch (g->cfg.ybus_lanes) {
-    case 1: return inj_w<1>(g, V, P, Q, s);
-    case 2: return inj_w<2>(g, V, P, Q, s);
-    case 4: return inj_w<4>(g, V, P, Q, s);
-    case 8: return inj_w<8>(g, V, P, Q, s);
-    case 16: return inj_w<16>(g, V, P, Q, s);
-    default: return inj_w<32>(g, V, P, Q, s);
-    }
-}
-
-cudaError_t launch_jac_ybus(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s)
-{
-    switch (g->cfg.ybus_lanes) {
-    case 1: return jac_w<1>(g, U, P, Q, J, s);
-    case 2: return jac_w<2>(g, U, P, Q, J, s);
-    case 4: return jac_w<4>(g, U, P, Q, J, s);
-    case 8: return jac_w<8>(g, U, P, Q, J, s);
-    case 16: return jac_w<16>(g, U, P, Q, J, s);
-    default: return jac_w<32>(g, U, P, Q, J, s);
     }
 }
 

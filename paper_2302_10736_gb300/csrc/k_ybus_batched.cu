@@ -12,7 +12,12 @@
 // J + joff[s] (the closed form of k_batched.cu):
 //   rowptr_s[i] = rowptr[i] - del ([h < i] + [k < i]),  d_s(i) = d(i) - del [i in {h, k}],
 //   k_s = k - del [k > position of the removed entry in row i].
-// Phasors of all scenarios come first, from the flat phasor kernel.
+// Phasors of all scenarios come first, from the flat phasor kernel, in the
+// fixed-point form (2^62-scaled cosine and sine); the complex products of the
+// base entries run in fixed point on the integer pipe as in k_ybus_fused, the
+// entries an outage changes (and values the fixed-point form does not hold)
+// in FP64.
+#include "fixrot.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
 
@@ -59,15 +64,45 @@ __device__ __forceinline__ bool scen_value(const RowOutage &r, int i, int k, int
     return true;
 }
 
-template <int W>
+// U[x] = {2^62 cos, 2^62 sin (64-bit integers stored bit for bit), v, -}
+__device__ __forceinline__ void unpack_u(const double4_32a &u, int64_t *C, int64_t *S)
+{
+    *C = __double_as_longlong(u.x);
+    *S = __double_as_longlong(u.y);
+}
+
+// Y_ij U_j of base entry k (column j) of row i in the scenario, in fixed point
+// unless the outage changes the entry; false if the entry has left the
+// scenario's pattern.  The changed entries and the values the fixed-point form
+// does not hold: FP64 products.
+__device__ __forceinline__ bool scen_yu(const RowOutage &ro, int i, int k, int j, const double2 *Y, long long e,
+                                        const longlong2 &yf, int ye, int64_t C, int64_t S, double *yur, double *yui)
+{
+    if (k == ro.kx && ro.del) return false;
+    const bool changed = k == ro.kx || (j == i && ro.kx >= 0);
+    if (!changed && ye != 0 && C != kFixNaN) {
+        fix_ybus_yu(yf.x, yf.y, ye, C, S, yur, yui);
+        return true;
+    }
+    double2 y = Y[e];
+    scen_value(ro, i, k, j, y);
+    const double c = fix_q62_or_nan(C), s = C == kFixNaN ? c : q62_to_double(S);
+    *yur = fma(y.x, c, -y.y * s);
+    *yui = fma(y.x, s, y.y * c);
+    return true;
+}
+
+template <int W, bool OUT>
 __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__restrict__ yrow,
                                                      const int *__restrict__ rp,
                                                      const int *__restrict__ ci, const double2 *__restrict__ Y,
+                                                     const longlong2 *__restrict__ Yf, const int *__restrict__ Ye,
                                                      const double2 *__restrict__ tself,
                                                      const double2 *__restrict__ tcoup,
-                                                     const ScenOut *__restrict__ sc, const double2 *__restrict__ V,
+                                                     const ScenOut *__restrict__ sc, const double4_32a *__restrict__ U,
                                                      double *__restrict__ P, double *__restrict__ Q)
 {
+    pdl_launch_dependents();   // the next phasor launch may start (it waits for this grid)
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long row = gid / W;
     const int lane = (int)(gid % W);
@@ -76,7 +111,8 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
     const int s = valid ? (int)(row / nb) : 0, i = valid ? yrow[(int)(row % nb)] : 0;
     int rs = 0, d = 0;
     int jj[kChunkBW<W>];
-    double2 yy[kChunkBW<W>];
+    longlong2 yf[kChunkBW<W>];
+    int ye[kChunkBW<W>];
     if (valid) {
         rs = rp[i];
         d = rp[i + 1] - rs;
@@ -90,11 +126,14 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
 #pragma unroll
     for (int j = 0; j < kChunkBW<W>; ++j) {
         const int k = lane + W * j;
-        if (k < d) yy[j] = Y[rs + k];   // parameter-dependent (as the outage's constants): after the wait
+        if (k < d) {   // parameter-dependent (as the outage's constants): after the wait
+            yf[j] = Yf[rs + k];
+            ye[j] = Ye[rs + k];
+        }
     }
     RowOutage ro{-1, 0, make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-    if (valid) ro = row_outage(sc[s], i, tself, tcoup);
-    const double2 *Vs = V + (long long)s * nb;
+    if (OUT && valid) ro = row_outage(sc[s], i, tself, tcoup);
+    const double4_32a *Us = U + (long long)s * nb;
     double Ir = 0.0, Ii = 0.0;
     for (int k0 = lane; k0 < d; k0 += W * kChunkBW<W>) {
         if (k0 != lane) {
@@ -103,22 +142,26 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
                 const int k = k0 + W * j;
                 if (k < d) {
                     jj[j] = ci[rs + k];
-                    yy[j] = Y[rs + k];
+                    yf[j] = Yf[rs + k];
+                    ye[j] = Ye[rs + k];
                 }
             }
         }
-        double2 vv[kChunkBW<W>];
+        double4_32a uu[kChunkBW<W>];
 #pragma unroll
         for (int j = 0; j < kChunkBW<W>; ++j)
-            if (k0 + W * j < d) vv[j] = Vs[jj[j]];
+            if (k0 + W * j < d) uu[j] = Us[jj[j]];
 #pragma unroll
         for (int j = 0; j < kChunkBW<W>; ++j) {
-            double2 y = yy[j];
-            if (k0 + W * j < d && scen_value(ro, i, k0 + W * j, jj[j], y)) {
-                Ir = fma(y.x, vv[j].x, Ir);
-                Ir = fma(-y.y, vv[j].y, Ir);
-                Ii = fma(y.x, vv[j].y, Ii);
-                Ii = fma(y.y, vv[j].x, Ii);
+            const int k = k0 + W * j;
+            if (k < d) {
+                int64_t C, Sn;
+                unpack_u(uu[j], &C, &Sn);
+                double YUr, YUi;
+                if (scen_yu(ro, i, k, jj[j], Y, rs + k, yf[j], ye[j], C, Sn, &YUr, &YUi)) {
+                    Ir = fma(uu[j].z, YUr, Ir);   // I_i += Y_ij V_j
+                    Ii = fma(uu[j].z, YUi, Ii);
+                }
             }
         }
     }
@@ -128,16 +171,21 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
         Ii += __shfl_xor_sync(0xffffffffu, Ii, off, W);
     }
     if (valid && lane == 0) {
-        const double2 Vi = Vs[i];
-        P[(long long)s * nb + i] = fma(Vi.x, Ir, Vi.y * Ii);   // S = V conj(I)
-        Q[(long long)s * nb + i] = fma(Vi.y, Ir, -Vi.x * Ii);
+        const double4_32a ui = Us[i];
+        int64_t C, Sn;
+        unpack_u(ui, &C, &Sn);
+        const double cs = fix_q62_or_nan(C), sn = C == kFixNaN ? cs : q62_to_double(Sn);
+        const double Vr = ui.z * cs, Vi = ui.z * sn;
+        P[(long long)s * nb + i] = fma(Vr, Ir, Vi * Ii);   // S = V conj(I)
+        Q[(long long)s * nb + i] = fma(Vi, Ir, -Vr * Ii);
     }
 }
 
-template <int W>
+template <int W, bool OUT>
 __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, const int *__restrict__ yrow,
                                                      const int *__restrict__ rp,
                                                      const int *__restrict__ ci, const double2 *__restrict__ Y,
+                                                     const longlong2 *__restrict__ Yf, const int *__restrict__ Ye,
                                                      const double2 *__restrict__ tself,
                                                      const double2 *__restrict__ tcoup,
                                                      const ScenOut *__restrict__ sc,
@@ -145,6 +193,7 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
                                                      const double4_32a *__restrict__ U, double *__restrict__ P,
                                                      double *__restrict__ Q, double *__restrict__ J)
 {
+    pdl_launch_dependents();   // the next phasor launch may start (it waits for this grid)
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long row = gid / W;
     const int lane = (int)(gid % W);
@@ -153,7 +202,8 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
     const int s = valid ? (int)(row / nb) : 0, i = valid ? yrow[(int)(row % nb)] : 0;
     int rs = 0, d = 0;
     int jj[kChunkBW<W>];
-    double2 yy[kChunkBW<W>];
+    longlong2 yf[kChunkBW<W>];
+    int ye[kChunkBW<W>];
     if (valid) {
         rs = rp[i];
         d = rp[i + 1] - rs;
@@ -163,9 +213,10 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
         const int k = lane + W * j;
         if (k < d) jj[j] = ci[rs + k];
     }
+    // without outages every scenario's Jacobian is the base pattern, 4 nnz values apart
     ScenOut o{-1, -1, -1, -1, 0, 0, 0, -1};
-    long long jo = 0;
-    if (valid) {
+    long long jo = 4LL * nnz * s;
+    if (OUT && valid) {
         o = sc[s];
         jo = joff[s];
     }
@@ -173,7 +224,10 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
 #pragma unroll
     for (int j = 0; j < kChunkBW<W>; ++j) {
         const int k = lane + W * j;
-        if (k < d) yy[j] = Y[rs + k];   // parameter-dependent (as the outage's constants): after the wait
+        if (k < d) {   // parameter-dependent (as the outage's constants): after the wait
+            yf[j] = Yf[rs + k];
+            ye[j] = Ye[rs + k];
+        }
     }
     const RowOutage ro = row_outage(o, i, tself, tcoup);
     // scenario s's compacted row: start, length, and its J halves
@@ -188,7 +242,12 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
     int kd = -1;
     double4_32a ui = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     if (valid) ui = Us[i];
-    const double Vr = ui.z * ui.x, Vi = ui.z * ui.y;
+    int64_t Crow, Srow;
+    unpack_u(ui, &Crow, &Srow);
+    const double cs = fix_q62_or_nan(Crow), sn = Crow == kFixNaN ? cs : q62_to_double(Srow);
+    const double vi = ui.z, Vr = vi * cs, Vi = vi * sn;
+    int64_t Ari, Aii;
+    fix_phasor(Crow, Srow, vi, &Ari, &Aii);
     for (int k0 = lane; k0 < d; k0 += W * kChunkBW<W>) {
         if (k0 != lane) {
 #pragma unroll
@@ -196,7 +255,8 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
                 const int k = k0 + W * j;
                 if (k < d) {
                     jj[j] = ci[rs + k];
-                    yy[j] = Y[rs + k];
+                    yf[j] = Yf[rs + k];
+                    ye[j] = Ye[rs + k];
                 }
             }
         }
@@ -207,30 +267,38 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
 #pragma unroll
         for (int j = 0; j < kChunkBW<W>; ++j) {
             const int k = k0 + W * j;
-            double2 y = yy[j];
-            if (k < d && scen_value(ro, i, k, jj[j], y)) {
-                const double YUr = fma(y.x, uu[j].x, -y.y * uu[j].y);
-                const double YUi = fma(y.x, uu[j].y, y.y * uu[j].x);
-                const double sVr = fma(Vr, YUr, Vi * YUi);    // V_i conj(YU)
-                const double sVi = fma(Vi, YUr, -Vr * YUi);
-                const double vj = uu[j].z;
-                Ir = fma(vj, YUr, Ir);
-                Ii = fma(vj, YUi, Ii);
-                const double sTr = vj * sVi, sTi = -vj * sVr;   // -j v_j dS/dv_j
-                const int ks = k - ((del && ro.kx >= 0 && k > ro.kx) ? 1 : 0);
-                if (jj[j] == i) {
-                    kd = ks;
-                    dTr = sTr;
-                    dTi = sTi;
-                    dVr = sVr;
-                    dVi = sVi;
-                } else {
-                    const long long p = 2LL * rss + ks;
-                    Js[p] = sTr;
-                    Js[p + ds] = sVr;
-                    Js[2 * nnzs + p] = sTi;
-                    Js[2 * nnzs + p + ds] = sVi;
-                }
+            if (k >= d || (k == ro.kx && del)) continue;   // beyond the row, or left the scenario's pattern
+            int64_t C, Sn;
+            unpack_u(uu[j], &C, &Sn);
+            const bool changed = k == ro.kx || (jj[j] == i && ro.kx >= 0);
+            double YUr, YUi, sVr, sVi;   // Y_ij U_j and V_i conj(YU)
+            if (changed || ye[j] == 0 || C == kFixNaN || Ari == kFixNaN ||
+                !fix_ybus_entry(yf[j].x, yf[j].y, ye[j], C, Sn, Ari, Aii, vi, &YUr, &YUi, &sVr, &sVi)) {
+                double2 y = Y[rs + k];
+                scen_value(ro, i, k, jj[j], y);
+                const double c = fix_q62_or_nan(C), sj = C == kFixNaN ? c : q62_to_double(Sn);
+                YUr = fma(y.x, c, -y.y * sj);
+                YUi = fma(y.x, sj, y.y * c);
+                sVr = fma(Vr, YUr, Vi * YUi);
+                sVi = fma(Vi, YUr, -Vr * YUi);
+            }
+            const double vj = uu[j].z;
+            Ir = fma(vj, YUr, Ir);
+            Ii = fma(vj, YUi, Ii);
+            const double sTr = vj * sVi, sTi = -vj * sVr;   // -j v_j dS/dv_j
+            const int ks = k - ((del && ro.kx >= 0 && k > ro.kx) ? 1 : 0);
+            if (jj[j] == i) {
+                kd = ks;
+                dTr = sTr;
+                dTi = sTi;
+                dVr = sVr;
+                dVi = sVi;
+            } else {
+                const long long p = 2LL * rss + ks;
+                Js[p] = sTr;
+                Js[p + ds] = sVr;
+                Js[2 * nnzs + p] = sTi;
+                Js[2 * nnzs + p + ds] = sVi;
             }
         }
     }
@@ -244,8 +312,8 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
     if (kd >= 0) {
         dTr -= Si;                           // + j S_i  (= j V_i conj(I_i))
         dTi += Sr;
-        dVr += fma(Ir, ui.x, Ii * ui.y);     // + conj(I_i) U_i
-        dVi += fma(Ir, ui.y, -Ii * ui.x);
+        dVr += fma(Ir, cs, Ii * sn);         // + conj(I_i) U_i
+        dVi += fma(Ir, sn, -Ii * cs);
         const long long p = 2LL * rss + kd;
         Js[p] = dTr;
         Js[p + ds] = dVr;
@@ -258,29 +326,45 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
     }
 }
 
-template <int W>
-static cudaError_t inj_b(const Batch *b, double *P, double *Q, cudaStream_t s)
+template <int W, bool OUT>
+static cudaError_t rows_w(const Grid *g, int S, const ScenOut *sc, const long long *joff, const double4_32a *U,
+                          bool jac, double *P, double *Q, double *J, int blk, cudaStream_t s)
 {
-    const Grid *g = b->g;
-    const long long threads = (long long)b->S * g->nb * W;
-    const int blk = b->cfg.ybus_block;
-    return launch_k(k_inj_ybus_b<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, b->S, g->nb,
-                    (const int *)g->yrow,
-                    (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, (const double2 *)g->tself,
-                    (const double2 *)g->tcoup, (const ScenOut *)b->sc, (const double2 *)b->V, P, Q);
+    const long long threads = (long long)S * g->nb * W;
+    const int grid = (int)((threads + blk - 1) / blk);
+    if (jac)
+        return launch_k(k_jac_ybus_b<W, OUT>, grid, blk, 0, s, true, S, g->nb, g->nnz, (const int *)g->yrow,
+                        (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, (const longlong2 *)g->yfx,
+                        (const int *)g->yce, (const double2 *)g->tself, (const double2 *)g->tcoup, sc, joff, U, P,
+                        Q, J);
+    return launch_k(k_inj_ybus_b<W, OUT>, grid, blk, 0, s, true, S, g->nb, (const int *)g->yrow,
+                    (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, (const longlong2 *)g->yfx,
+                    (const int *)g->yce, (const double2 *)g->tself, (const double2 *)g->tcoup, sc, U, P, Q);
 }
 
-template <int W>
-static cudaError_t jac_b(const Batch *b, double *P, double *Q, double *J, cudaStream_t s)
+template <bool OUT>
+static cudaError_t rows(const Grid *g, int S, const ScenOut *sc, const long long *joff, const double4_32a *U,
+                        bool jac, double *P, double *Q, double *J, int lanes, int blk, cudaStream_t s)
 {
-    const Grid *g = b->g;
-    const long long threads = (long long)b->S * g->nb * W;
-    const int blk = b->cfg.ybus_block;
-    return launch_k(k_jac_ybus_b<W>, (int)((threads + blk - 1) / blk), blk, 0, s, true, b->S, g->nb, g->nnz,
-                    (const int *)g->yrow,
-                    (const int *)g->rp, (const int *)g->ci, (const double2 *)g->yv, (const double2 *)g->tself,
-                    (const double2 *)g->tcoup, (const ScenOut *)b->sc, (const long long *)b->joff,
-                    (const double4_32a *)b->U, P, Q, J);
+    switch (lanes) {
+    case 1: return rows_w<1, OUT>(g, S, sc, joff, U, jac, P, Q, J, blk, s);
+    case 2: return rows_w<2, OUT>(g, S, sc, joff, U, jac, P, Q, J, blk, s);
+    case 4: return rows_w<4, OUT>(g, S, sc, joff, U, jac, P, Q, J, blk, s);
+    case 8: return rows_w<8, OUT>(g, S, sc, joff, U, jac, P, Q, J, blk, s);
+    case 16: return rows_w<16, OUT>(g, S, sc, joff, U, jac, P, Q, J, blk, s);
+    default: return rows_w<32, OUT>(g, S, sc, joff, U, jac, P, Q, J, blk, s);
+    }
+}
+
+// The row kernels over S scenarios from phasors U in the fixed-point form
+// (launch_phasor_fix); sc and joff only with outages (out)
+cudaError_t launch_ybus_rows(const Grid *g, int S, bool out, const ScenOut *sc, const long long *joff,
+                             const double4_32a *U, bool jac, double *P, double *Q, double *J, int lanes, int blk,
+                             cudaStream_t s)
+{
+    if (S == 0 || g->nb == 0) return cudaSuccess;
+    return out ? rows<true>(g, S, sc, joff, U, jac, P, Q, J, lanes, blk, s)
+               : rows<false>(g, S, sc, joff, U, jac, P, Q, J, lanes, blk, s);
 }
 
 cudaError_t launch_ybus_batched(Batch *b, bool jac, const double *vm, const double *va, double *P, double *Q,
@@ -288,26 +372,10 @@ cudaError_t launch_ybus_batched(Batch *b, bool jac, const double *vm, const doub
 {
     const Grid *g = b->g;
     if (b->S == 0 || g->nb == 0) return cudaSuccess;
-    cudaError_t e = launch_phasor(b->S * g->nb, vm, va, b->U, b->V, s);
+    cudaError_t e = launch_phasor_fix(b->S * g->nb, vm, va, b->U, s);
     if (e != cudaSuccess) return e;
-    if (jac) {
-        switch (b->cfg.ybus_lanes) {
-        case 1: return jac_b<1>(b, P, Q, J, s);
-        case 2: return jac_b<2>(b, P, Q, J, s);
-        case 4: return jac_b<4>(b, P, Q, J, s);
-        case 8: return jac_b<8>(b, P, Q, J, s);
-        case 16: return jac_b<16>(b, P, Q, J, s);
-        default: return jac_b<32>(b, P, Q, J, s);
-        }
-    }
-    switch (b->cfg.ybus_lanes) {
-    case 1: return inj_b<1>(b, P, Q, s);
-    case 2: return inj_b<2>(b, P, Q, s);
-    case 4: return inj_b<4>(b, P, Q, s);
-    case 8: return inj_b<8>(b, P, Q, s);
-    case 16: return inj_b<16>(b, P, Q, s);
-    default: return inj_b<32>(b, P, Q, s);
-    }
+    return launch_ybus_rows(g, b->S, b->has_outage, b->sc, b->joff, b->U, jac, P, Q, J, b->cfg.ybus_lanes,
+                            b->cfg.ybus_block, s);
 }
 
 }  // namespace pf

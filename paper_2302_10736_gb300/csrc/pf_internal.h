@@ -236,6 +236,10 @@ struct Grid {
     // many loop trips and FP64 warp instructions keep their lanes busy
     int *yrow = nullptr;
     double2 *yv = nullptr;
+    // the Ybus values in block floating point (fixrot.cuh): yfx 2^(yce - 1085),
+    // yce = 0 where a value is not representable (the kernels then take yv)
+    longlong2 *yfx = nullptr;
+    int *yce = nullptr;
     int *ybeg = nullptr, *yend = nullptr, *ydiag = nullptr;
     int *kd = nullptr;                     // [nb] diagonal position per row
     // J pattern (device)
@@ -355,8 +359,11 @@ cudaError_t launch_ybus_values(Grid *g, const double *gs, const double *bs, cuda
 cudaError_t ensure_trig_table();   // once per device, synchronous
 const ITrig *trig_table();         // device address of the (cos, sin) table of isincos.cuh
 cudaError_t launch_phasor(int nb, const double *vm, const double *va, double4_32a *U, double2 *V, cudaStream_t s);
-cudaError_t launch_inj_ybus(const Grid *g, const double2 *V, double *P, double *Q, cudaStream_t s);
-cudaError_t launch_jac_ybus(const Grid *g, const double4_32a *U, double *P, double *Q, double *J, cudaStream_t s);
+cudaError_t launch_phasor_fix(int nb, const double *vm, const double *va, double4_32a *U, cudaStream_t s);
+struct ScenOut;
+cudaError_t launch_ybus_rows(const Grid *g, int S, bool out, const ScenOut *sc, const long long *joff,
+                             const double4_32a *U, bool jac, double *P, double *Q, double *J, int lanes, int blk,
+                             cudaStream_t s);
 // the Ybus method with the phasor step fused into the row kernel (one launch)
 cudaError_t launch_ybus_fused(const Grid *g, bool jac, const double *vm, const double *va, double *P, double *Q,
                               double *J, cudaStream_t s);
