@@ -83,9 +83,26 @@ __device__ __forceinline__ void store_range_ll(double *x, const double *s, long 
     if ((b1 - ge) & 1) x[b1 - 1] = s[b1 - 1 - b0 + par];
 }
 
-// phase 1: phasors of every scenario, in chunks of blockDim.x consecutive
-// buses so that every lane has a bus
-__device__ __forceinline__ void batch_phasors(const BatchArgs &a, const ITrig *tab, bool needU)
+// V = v (c, s) as doubles from the fixed-point phasor: the block-floating
+// value rounded on the integer pipe, or FP64 products where the fixed-point
+// form does not hold
+__device__ __forceinline__ double2 fix_V_double(int64_t C, int64_t S, double v)
+{
+    int64_t ar, ai;
+    fix_phasor(C, S, v, &ar, &ai);
+    if (ar != kFixNaN) {
+        const int e1 = fix_vexp(v) + 2;   // V = A 2^(e - 1083)
+        return make_double2(fix_to_double(ar, e1), fix_to_double(ai, e1));
+    }
+    const double c = fix_q62_or_nan(C), s = C == kFixNaN ? c : q62_to_double(S);
+    return make_double2(v * c, v * s);
+}
+
+// phase 1 of the adjoint: the fixed-point phasors of every scenario as in
+// batch_phasors_fix (1/v with the gradients), and V as doubles for the
+// branch-parameter gradients; chunks of blockDim.x consecutive buses, so that
+// every lane has a bus
+__device__ __forceinline__ void batch_phasors_adj(const BatchArgs &a, const ITrig *tab, bool grad)
 {
     const int tid = threadIdx.x, TB = blockDim.x;
     const int nchunk = (a.nb + TB - 1) / TB;
@@ -95,13 +112,33 @@ __device__ __forceinline__ void batch_phasors(const BatchArgs &a, const ITrig *t
         const int o = c * TB + tid;
         if (o < a.nb) {
             const long long x = (long long)s * a.nb + o;
-            double sn, cs;
-            int_sincos(a.va[x], tab, &sn, &cs);
+            int64_t C, S;
+            int_sincos_q62(a.va[x], tab, &C, &S);
             const double v = a.vm[x];
-            if (needU) a.U[x] = make_double4_32a(cs, sn, v, fast_rcp(v));
-            a.V[x] = make_double2(v * cs, v * sn);
+            a.U[x] = make_double4_32a(__longlong_as_double(C), __longlong_as_double(S), v, grad ? fast_rcp(v) : 0.0);
+            if (grad) a.V[x] = fix_V_double(C, S, v);
         }
     }
+}
+
+// G = conj(Yc_p) V_o conj(U_q) of terminal p (owner o, other bus q) of the
+// scenario whose fixed-point phasors start at U: fixed point on the integer
+// pipe where it applies (fixrot.cuh), else FP64 products.  *vq = v_q.
+__device__ __forceinline__ void batch_G(const BatchArgs &a, const double4_32a *U, int p, int o, int q, double *gr,
+                                        double *gi, double *vq)
+{
+    const longlong2 yf = a.tcfx[p];
+    const int ey = a.tce[p];
+    const double4_32a uo = U[o], uq = U[q];
+    const int64_t Co = __double_as_longlong(uo.x), So = __double_as_longlong(uo.y);
+    const int64_t Cq = __double_as_longlong(uq.x), Sq = __double_as_longlong(uq.y);
+    int64_t Ar, Ai;
+    fix_phasor(Co, So, uo.z, &Ar, &Ai);
+    if (Ar == kFixNaN || Cq == kFixNaN || ey == 0 || !fix_G_fast(Ar, Ai, uo.z, Cq, Sq, yf.x, yf.y, ey, gr, gi)) {
+        const double2 yc = a.tcoup[p];
+        fix_G(Ar, Ai, uo.z, Co, So, Cq, Sq, 0, 0, 0, yc.x, yc.y, gr, gi);
+    }
+    *vq = uq.z;
 }
 
 // phase 1 of the Jacobian and injection batches: the phasors in the
@@ -201,25 +238,15 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
         __syncthreads();
         for (int i = tid; i < nt; i += TB) {
             const int p = t0 + i;
-            const longlong2 yf = a.tcfx[p];
-            const int ey = a.tce[p];
             const int2 nq = a.tnbr[p];
             const int ol = a.town[p] - b0, o = b0 + ol;
             const bool masked = p == sc.ph || p == sc.pk;
             // G = conj(Yc) V_o conj(U_q) on the integer pipe, as in the single evaluation
-            const double4_32a uo = a.U[sb + o], uq = a.U[sb + nq.x];
-            const int64_t Co = __double_as_longlong(uo.x), So = __double_as_longlong(uo.y);
-            const int64_t Cq = __double_as_longlong(uq.x), Sq = __double_as_longlong(uq.y);
-            int64_t Ar, Ai;
-            fix_phasor(Co, So, uo.z, &Ar, &Ai);
-            double Gr, Gi;
-            if (Ar == kFixNaN || Cq == kFixNaN || ey == 0 || !fix_G_fast(Ar, Ai, uo.z, Cq, Sq, yf.x, yf.y, ey, &Gr, &Gi)) {
-                const double2 yc = a.tcoup[p];
-                fix_G(Ar, Ai, uo.z, Co, So, Cq, Sq, 0, 0, 0, yc.x, yc.y, &Gr, &Gi);
-            }
+            double Gr, Gi, vq;
+            batch_G(a, a.U + sb, p, o, nq.x, &Gr, &Gi, &vq);
             if (JAC) {
                 if (masked) Gr = Gi = 0.0;
-                const double Kr = uq.z * Gr, Ki = uq.z * Gi;
+                const double Kr = vq * Gr, Ki = vq * Gi;
                 const int kp = nq.y & EW_KMASK;
                 const int kps = kp - del * ((o == sc.h && kp > sc.kh) + (o == sc.k && kp > sc.kk));
                 const bool gone = del && ((o == sc.h && kp == sc.kh) || (o == sc.k && kp == sc.kk));
@@ -235,7 +262,7 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
                     jst[Ls + pos + d] = Gi;
                 }
             } else {
-                double Kr = uq.z * Gr, Ki = uq.z * Gi;
+                double Kr = vq * Gr, Ki = vq * Gi;
                 if (masked) Kr = Ki = 0.0;
                 skg[i] = make_double2(Kr, Ki);
             }
@@ -490,7 +517,7 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
     for (int k = tid; k < kITrigN; k += TB) tab[k] = trig[k];
     __syncthreads();
     // every scenario's phasors first, visible to all CTAs after the barrier
-    batch_phasors(a, tab, GRAD);
+    batch_phasors_adj(a, tab, GRAD);
     // r = 2 Lbar w dS: the upstream gradient scales every gradient below
     const double tl = 2.0 * (a.Lbar ? *a.Lbar : 1.0);
     if (!grid_barrier(gbar, a.bar, gridDim.x, 0, a.err, DEV_TIMEOUT, kBatchBarrierNs)) return;
@@ -508,10 +535,9 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         batch_window_meta(a, sc, b0, b1, t0, sbm, syd);
         for (int i = tid; i < nt; i += TB) {
             const int p = t0 + i;
-            const double2 yc = a.tcoup[p];
-            const double2 Vo = a.V[sb + a.town[p]], Vq = a.V[sb + a.tnbr[p].x];
-            const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);
-            double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);
+            double Gr, Gi, vq;   // K_t = v_q G, G = conj(Yc) V_o conj(U_q)
+            batch_G(a, a.U + sb, p, a.town[p], a.tnbr[p].x, &Gr, &Gi, &vq);
+            double Kr = vq * Gr, Ki = vq * Gi;
             if (p == sc.ph || p == sc.pk) Kr = Ki = 0.0;
             skg[i] = make_double2(Kr, Ki);
         }
@@ -558,13 +584,15 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
         __syncthreads();
         for (int i = tid; i < nt; i += TB) {
             const int p = t0 + i;
-            const double2 yc = a.tcoup[p], ym = a.tcoup[a.tmir[p]];
             const int q = a.town[p], o = a.tnbr[p].x;   // q owns the terminal, o is the other end
-            const double2 Vq = a.V[sb + q], Vo = a.V[sb + o];
             const double2 rq = a.r[sb + q], ro = a.r[sb + o];
-            const double Wr = fma(Vq.x, Vo.x, Vq.y * Vo.y), Wi = fma(Vq.y, Vo.x, -Vq.x * Vo.y);   // V_q conj(V_o)
-            const double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);           // K_t
-            const double Mr = fma(ym.x, Wr, -ym.y * Wi), Mi = fma(-ym.x, Wi, -ym.y * Wr);         // K_m = conj(Yc_m) conj(W)
+            // K_t = conj(Yc_t) V_q conj(V_o) = v_o G_t and the mirror's K_m =
+            // conj(Yc_m) V_o conj(V_q) = v_q G_m, the G on the integer pipe
+            double gtr, gti, gmr, gmi, vo, vq;
+            batch_G(a, a.U + sb, p, q, o, &gtr, &gti, &vo);
+            batch_G(a, a.U + sb, a.tmir[p], o, q, &gmr, &gmi, &vq);
+            const double Kr = vo * gtr, Ki = vo * gti;
+            const double Mr = vq * gmr, Mi = vq * gmi;
             double th = fma(-rq.x, Ki, rq.y * Kr) + fma(ro.x, Mi, -ro.y * Mr);
             double vv = fma(rq.x, Kr, rq.y * Ki) + fma(ro.x, Mr, ro.y * Mi);
             if (p == sc.ph || p == sc.pk) th = vv = 0.0;
@@ -626,9 +654,10 @@ __global__ void __launch_bounds__(256, 4) k_adj(BatchArgs a)
 // Small-batch adjoint: one (scenario, window) item per CTA (the launch has a
 // CTA for every item) and one grid barrier.  Before the barrier the item
 // forms the phasors of its own and ghost buses (slot j's bus in slotbus),
-// both flows of every terminal from the same W = V_o conj(V_q) (o owns the
-// terminal): K_t = conj(Yc_t) W and the mirror's K_m = conj(Yc_m) conj(W),
-// then its buses' injections and residuals.  All of it stays in shared
+// both flows of every terminal (o owns the terminal): K_t = conj(Yc_t) V_o
+// conj(V_q) and the mirror's K_m = conj(Yc_m) V_q conj(V_o), the complex
+// products in fixed point on the integer pipe (fixrot.cuh), then its buses'
+// injections and residuals.  All of it stays in shared
 // memory, so after the barrier the item reads back only its ghost buses'
 // residuals (one L2 round trip) before the state gradients (and, for a single
 // scenario, the gradients of the branches whose from-terminal it owns)
@@ -651,6 +680,9 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
     double2 *sV = reinterpret_cast<double2 *>(smem + sp.V);
     double2 *sR = reinterpret_cast<double2 *>(smem + sp.R);
     double2 *sW = reinterpret_cast<double2 *>(smem + sp.W);   // own buses: (v, 1/v)
+    longlong2 *sUf = reinterpret_cast<longlong2 *>(smem + sp.uf);   // 2^62 (cos, sin)
+    longlong2 *sAf = reinterpret_cast<longlong2 *>(smem + sp.af);   // V in block floating point
+    double *svs = reinterpret_cast<double *>(smem + sp.vs);         // v
     int *sslot = reinterpret_cast<int *>(smem + sp.slot);
     ITrig *tab = reinterpret_cast<ITrig *>(smem + sp.tab);
     const int tid = threadIdx.x, TB = blockDim.x;
@@ -689,12 +721,14 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         const ITrig *trig = a.trig + (blockIdx.x % kITrigCopies) * kITrigN;
         ITrig tv0 = {0ull, 0ull};
         if (tid < kITrigN) tv0 = trig[tid];
-        double2 yc0 = make_double2(0.0, 0.0), ym0 = make_double2(0.0, 0.0);
+        longlong2 yf0 = make_longlong2(0, 0), ymf0 = make_longlong2(0, 0);
+        int ey0 = 0, eym0 = 0;
         int2 loc0 = make_int2(0, 0);
         int tm0 = 0;
         if (tid < nt) {
             const int p = t0 + tid;
-            yc0 = a.tcoup[p];
+            yf0 = a.tcfx[p];
+            ey0 = a.tce[p];
             if (GRAD) tm0 = a.tmir[p];
             loc0 = make_int2(a.town[p], a.tloc[p].x);   // owner made window-local at first use
         }
@@ -723,17 +757,33 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
                 v = a.vm[sb + o];
             }
             sslot[j] = o;
-            double sn, cs;
-            int_sincos(th, tab, &sn, &cs);
-            const double2 V = make_double2(v * cs, v * sn);
+            // the fixed-point phasor (fixrot.cuh) and V as doubles (the
+            // block-floating value rounded on the integer pipe where it holds)
+            int64_t C, S, ar, ai;
+            int_sincos_q62(th, tab, &C, &S);
+            fix_phasor(C, S, v, &ar, &ai);
+            double2 V;
+            if (ar != kFixNaN) {
+                const int e1 = fix_vexp(v) + 2;   // V = A 2^(e - 1083)
+                V = make_double2(fix_to_double(ar, e1), fix_to_double(ai, e1));
+            } else {
+                const double c = fix_q62_or_nan(C), sn = C == kFixNaN ? c : q62_to_double(S);
+                V = make_double2(v * c, v * sn);
+            }
             sV[j] = V;
+            sUf[j] = make_longlong2(C, S);
+            sAf[j] = make_longlong2(ar, ai);
+            svs[j] = v;
             if (j < nbus) {
                 sW[j] = make_double2(v, GRAD ? fast_rcp(v) : 0.0);
                 if (GRAD) a.V[sb + o] = V;   // for the branch-parameter gradients
             }
         }
         batch_window_meta(a, sc, b0, b0 + nbus, t0, sbm, syd);
-        if (GRAD && tid < nt) ym0 = a.tcoup[tm0];
+        if (GRAD && tid < nt) {
+            ymf0 = a.tcfx[tm0];
+            eym0 = a.tce[tm0];
+        }
         if (tid < 2 * nbus) {
             const int o = b0 + bo;
             spec0 = (tid & 1) ? a.Qs[o] : a.Ps[o];
@@ -743,21 +793,43 @@ __global__ void __launch_bounds__(kAdj1Threads, 1) k_adj1(BatchArgs a)
         // ---- both flows of every terminal ----
         for (int i = tid; i < nt; i += TB) {
             const int p = t0 + i;
-            double2 yc = yc0, ym = ym0;
+            longlong2 yf = yf0, ymf = ymf0;
+            int ey = ey0, eym = eym0, tm = tm0;
             int2 loc = loc0;
             if (i != tid) {
-                yc = a.tcoup[p];
-                if (GRAD) ym = a.tcoup[a.tmir[p]];
+                yf = a.tcfx[p];
+                ey = a.tce[p];
+                if (GRAD) {
+                    tm = a.tmir[p];
+                    ymf = a.tcfx[tm];
+                    eym = a.tce[tm];
+                }
                 loc = make_int2(a.town[p], a.tloc[p].x);
             }
             loc.x -= b0;
-            const double2 Vo = sV[loc.x], Vq = sV[loc.y];
-            const double Wr = fma(Vo.x, Vq.x, Vo.y * Vq.y), Wi = fma(Vo.y, Vq.x, -Vo.x * Vq.y);   // V_o conj(V_q)
-            double Kr = fma(yc.x, Wr, yc.y * Wi), Ki = fma(yc.x, Wi, -yc.y * Wr);                 // K_t
+            // K_t = conj(Yc_t) V_o conj(V_q) = v_q G_t and the mirror's K_m =
+            // conj(Yc_m) V_q conj(V_o) = v_o G_m, the G on the integer pipe
+            const longlong2 Ao = sAf[loc.x], Uq = sUf[loc.y];
+            const double vo = svs[loc.x], vq = svs[loc.y];
+            double gr, gi;
+            if (Ao.x == kFixNaN || Uq.x == kFixNaN || ey == 0 ||
+                !fix_G_fast(Ao.x, Ao.y, vo, Uq.x, Uq.y, yf.x, yf.y, ey, &gr, &gi)) {
+                const longlong2 Uo = sUf[loc.x];
+                const double2 yc = a.tcoup[p];
+                fix_G(Ao.x, Ao.y, vo, Uo.x, Uo.y, Uq.x, Uq.y, 0, 0, 0, yc.x, yc.y, &gr, &gi);
+            }
+            double Kr = vq * gr, Ki = vq * gi;
             if (p == sc.ph || p == sc.pk) Kr = Ki = 0.0;   // outage branch
             sK[i] = make_double2(Kr, Ki);
             if (GRAD) {
-                double Mr = fma(ym.x, Wr, -ym.y * Wi), Mi = fma(-ym.x, Wi, -ym.y * Wr);   // K_m
+                const longlong2 Aq = sAf[loc.y], Uo = sUf[loc.x];
+                double mr, mi;
+                if (Aq.x == kFixNaN || Uo.x == kFixNaN || eym == 0 ||
+                    !fix_G_fast(Aq.x, Aq.y, vq, Uo.x, Uo.y, ymf.x, ymf.y, eym, &mr, &mi)) {
+                    const double2 ym = a.tcoup[tm];
+                    fix_G(Aq.x, Aq.y, vq, Uq.x, Uq.y, Uo.x, Uo.y, 0, 0, 0, ym.x, ym.y, &mr, &mi);
+                }
+                double Mr = vo * mr, Mi = vo * mi;
                 if (p == sc.ph || p == sc.pk) Mr = Mi = 0.0;
                 sM[i] = make_double2(Mr, Mi);
                 sloc[i] = loc;

@@ -186,11 +186,11 @@ constexpr int kLossCountWord = 96;
 
 // Shared memory of the small-batch adjoint (k_adj1, one item per CTA): bus
 // metadata and self sums, both flows of every terminal and its two phasor
-// slots, loss / gradient staging, the phasor,
-// residual and bus-name tables of the own and ghost slots, (v, 1/v) of the
-// own buses, the sine/cosine table.
+// slots, loss / gradient staging, the phasor (as doubles and in the fixed-point
+// form), residual and bus-name tables of the own and ghost slots, (v, 1/v) of
+// the own buses, the sine/cosine table.
 struct Adj1Smem {
-    uint32_t bm, yd, K, M, loc, pq, V, R, W, slot, tab, total, pqs;
+    uint32_t bm, yd, K, M, loc, pq, V, R, W, uf, af, vs, slot, tab, total, pqs;
 };
 __host__ __device__ inline Adj1Smem adj1_smem_plan(int max_nbus, int max_nt, int max_nph)
 {
@@ -206,7 +206,10 @@ __host__ __device__ inline Adj1Smem adj1_smem_plan(int max_nbus, int max_nt, int
     p.V = p.pq + 16u * p.pqs;
     p.R = p.V + 16u * nph;
     p.W = p.R + 16u * nph;
-    p.slot = p.W + 16u * nbus;
+    p.uf = p.W + 16u * nbus;   // per slot: 2^62 (cos, sin), V in block floating point, v (fixrot.cuh)
+    p.af = p.uf + 16u * nph;
+    p.vs = p.af + 16u * nph;
+    p.slot = p.vs + 8u * ((nph + 1u) & ~1u);
     p.tab = p.slot + ((4u * nph + 15u) & ~15u);
     p.total = p.tab + kTrigSmem;
     return p;
