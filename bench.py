@@ -44,13 +44,17 @@ def fp64_peak_g():
 HBM_FALLBACK_GBS = 6800.0
 # FP64 arithmetic instructions per unit of the element-wise Jacobian kernel
 WORKLOAD_NAME = "synthetic grid, 70,000 buses / 88,000 branches, one voltage state"
+# (the method's operations in its plain FP64 form: the roofline's algorithmic count)
 EW_OPS_PER_TERMINAL = 12   # E = V_o conj(U_q) 4, G = conj(Yc) E 4, K = v_q G 2, sum K 2
-EW_OPS_PER_BUS = 16        # fused phasor (1/v 4, V 2; sin/cos on the integer pipe) + diagonal entries and S (10)
+EW_OPS_PER_BUS = 16        # phasor (1/v 4, V 2, v^2 1, 2v 1; sin/cos on the integer pipe) + diagonal entries and S (8)
+# of which the kernel runs E, G, V and 2v in fixed point on the integer pipes: what is left on the FP64 pipe
+EW_FP64_PIPE_PER_TERMINAL = 4   # K = v_q G 2, sum K 2
+EW_FP64_PIPE_PER_BUS = 13       # 1/v 4, v^2 1, diagonal entries and S 8
 YB_OPS_PER_NNZ = 16
 YB_OPS_PER_ROW = 16
 # DRAM bytes of one k_ew<1> launch on the 70k-bus grid (dram__bytes_read.sum + dram__bytes_write.sum
 # of an ncu capture of that launch); None whenever the kernel changes, until it is captured again
-EW_TRAFFIC_BYTES = 9423616
+EW_TRAFFIC_BYTES = None
 
 
 def parse_args(argv=None):
@@ -940,6 +944,9 @@ def main():
     roof = {"bound": "alu", "kernel": "k_ew<1>", "achieved": achieved, "peak": fp64_peak["gdfma_per_s"],
             "unit": "GFP64op/s", "frac": achieved / fp64_peak["gdfma_per_s"], "traffic": EW_TRAFFIC_BYTES,
             "ops_per_launch": ops_ew,
+            "ops_note": "the method's operations in plain FP64 form (12 per terminal, 16 per bus); the kernel runs "
+                        "8 per terminal and 3 per bus of them in 64-bit fixed point on the integer pipes, %d on "
+                        "the FP64 pipe" % (EW_FP64_PIPE_PER_TERMINAL * T + EW_FP64_PIPE_PER_BUS * nb),
             "peak_source": "measured: fp64_peak_probe (DFMA chains on every SM) in this run",
             "frac_of_nominal": achieved / FP64_OPS_PEAK_G,
             "nominal_peak": FP64_OPS_PEAK_G,

@@ -133,6 +133,17 @@ pf_status grid_set_params(pf_grid *grid, const double *g, const double *b, const
 pf_status ybus_get(const pf_grid *grid, int32_t *nnz, const int32_t **rowptr, const int32_t **colidx,
                    const double **values);
 
+/*
+ * The element-wise method's windows of consecutive buses (Sec. IV-C on the
+ * GPU: one CTA per window, its terminals and ghost buses with it), for
+ * inspection: window w is out[5w .. 5w+4] = {first bus, buses, first sorted
+ * terminal, terminals, phasor slots (own and ghost buses)}.  Fills at most
+ * max_windows windows (out may be NULL to query *nwin only; caller-owned
+ * host memory).  Synchronous (a device-to-host copy).  Errors: PF_EINVAL for a
+ * NULL grid, PF_ECUDA.
+ */
+pf_status grid_ew_windows(const pf_grid *grid, int32_t *out, int32_t max_windows, int32_t *nwin);
+
 /* Device pointers to the canonical J pattern (owned by the grid):
    rowptr [2nb+1], colidx [nnzJ]. */
 pf_status jac_pattern(const pf_grid *grid, int32_t *nnzJ, const int32_t **rowptr, const int32_t **colidx);

@@ -377,6 +377,27 @@ PF_API pf_status grid_info(const pf_grid *grid, int32_t *nb, int32_t *nl, int32_
     return PF_OK;
 }
 
+PF_API pf_status grid_ew_windows(const pf_grid *grid, int32_t *out, int32_t max_windows, int32_t *nwin)
+{
+    if (!grid) return set_error(PF_EINVAL, "grid_ew_windows: grid is NULL");
+    const Grid *g = &grid->g;
+    const int n = g->ew.nwin;
+    if (nwin) *nwin = n;
+    if (!out || max_windows <= 0 || n == 0) return PF_OK;
+    const int m = n < max_windows ? n : max_windows;
+    std::vector<int4> d(2 * (size_t)m);
+    PF_CUDA(cudaMemcpy(d.data(), g->ew.desc, d.size() * sizeof(int4), cudaMemcpyDeviceToHost));
+    for (int w = 0; w < m; ++w) {
+        int32_t *o = out + 5 * (size_t)w;
+        o[0] = d[2 * w].x;
+        o[1] = d[2 * w].y;
+        o[2] = d[2 * w].z;
+        o[3] = d[2 * w].w;
+        o[4] = d[2 * w + 1].z;
+    }
+    return PF_OK;
+}
+
 PF_API pf_status grid_set_params(pf_grid *grid, const double *g_, const double *b_, const double *bsh_,
                                  const double *tap_, const double *shift_, const double *gs_, const double *bs_,
                                  pf_stream stream)

@@ -10,7 +10,8 @@
 //      the 53-bit significand m, and phi = frac(x / (2 pi)) as a 64-bit
 //      fixed-point fraction of a turn, from the product of m with the first
 //      128 bits of 1/(2 pi) (floor(2^129 / pi)).  |x| < 2^16 keeps every bit
-//      of phi that matters inside that product.
+//      of phi that matters inside that product; |x| < 4 needs only its upper
+//      64 bits (phi then within one unit of its last place).
 //   2. Table method (Tang 1990): the nearest of 256 points a_k = 2 pi k / 256,
 //      k = round(256 phi), leaves rho = x - a_k with |rho| <= pi / 256; k's top
 //      two bits select the quadrant and its low six bits one of 64 entries
@@ -194,12 +195,17 @@ __host__ __device__ __forceinline__ void int_sincos_fix(double x, const ITrig *t
     const int e = (int)((bits >> 52) & 0x7ff);
     const uint64_t m = (bits & 0x000fffffffffffffull) | (e ? (1ull << 52) : 0ull);
     // m C, C = floor(2^129 / pi): its words above 2^64 (the lowest word only
-    // holds bits far below the 64 fraction bits kept)
-    const uint64_t H0 = u64_mulhi(m, kInv2PiLo);
+    // holds bits far below the 64 fraction bits kept).  For |x| < 4 the
+    // product with C's lowest word (below 2^53) moves the fraction of a turn
+    // by less than one unit of its last place (2^-64) and is left out.
     const uint64_t L1 = m * kInv2PiHi;
     const uint64_t H1 = u64_mulhi(m, kInv2PiHi);
-    const uint64_t P1 = L1 + H0;
-    const uint64_t P2 = H1 + (P1 < L1 ? 1ull : 0ull);
+    uint64_t P1 = L1, P2 = H1;
+    if (e > 1024) {
+        const uint64_t H0 = u64_mulhi(m, kInv2PiLo);
+        P1 = L1 + H0;
+        P2 = H1 + (P1 < L1 ? 1ull : 0ull);
+    }
     // x / (2 pi) = m C 2^(e - 1205): the fraction of a turn is bits
     // [s, s + 64) of (P2, P1) with s = 1077 - e (>= 39 for |x| < 2^16)
     int s = 1077 - (e ? e : 1);

@@ -303,12 +303,16 @@ __global__ void __launch_bounds__(256, 4) k_ewb(BatchArgs a)
                 const double4_32a uo = x == tid ? ub : a.U[sb + b0 + b];
                 const double v = uo.z, iv = uo.w, v2 = v * v, tv = fix_twice(v);
                 const int pos = bm.x + bm.z;
+                // 2 v conj(Yd) + sum K / v and S = v^2 conj(Yd) + sum K, in the
+                // single evaluation's order of operations (its products are
+                // rounded before the sums: __dmul_rn keeps them from being
+                // contracted into FMAs here)
                 jst[pos] = neg(sKi);
-                jst[pos + d] = fma(tv, y.x, sKr * iv);
+                jst[pos + d] = fma(sKr, iv, __dmul_rn(tv, y.x));
                 jst[Ls + pos] = sKr;
-                jst[Ls + pos + d] = fma(-tv, y.y, sKi * iv);
-                spq[b + par] = fma(v2, y.x, sKr);
-                spq[pqs + b + par] = fma(-v2, y.y, sKi);
+                jst[Ls + pos + d] = fma(sKi, iv, neg(__dmul_rn(tv, y.y)));
+                spq[b + par] = sKr + __dmul_rn(v2, y.x);
+                spq[pqs + b + par] = sKi + neg(__dmul_rn(v2, y.y));
             } else {
                 for (int i = i1; i < tend; ++i) {
                     sKr += skg[i].x;

@@ -126,6 +126,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
     const EwSmem sp = ew_smem_plan(a.max_nbus, a.max_nt, JAC ? a.max_L : 0, JAC, a.max_nph);
     int4 *sbm = reinterpret_cast<int4 *>(smem + sp.bm);
     double2 *syd = reinterpret_cast<double2 *>(smem + sp.yd);
+    double2 *sSv = syd;   // the Jacobian kernels keep v^2 conj(Yd) where the others keep Yd
     double2 *skg = reinterpret_cast<double2 *>(smem + sp.kg);
     int *skp = reinterpret_cast<int *>(smem + sp.kp);
     double *jst = reinterpret_cast<double *>(smem + sp.jst);
@@ -183,7 +184,17 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         }
         // ---- the previous kernel in the stream may still run (programmatic
         // dependent launch): the state, the parameter-dependent constants and
-        // the outputs are read and written only after it has completed ----
+        // the outputs are read and written only after it has completed; their
+        // lines are only brought into L2 before (prefetches return no data) ----
+        if (tid < nph) {
+            prefetch_l2(a.va + o0);
+            prefetch_l2(a.vm + o0);
+        }
+        if (tid < nbus) prefetch_l2(a.yd + b0 + tid);
+        if (tid < nt) {
+            prefetch_l2(a.tcfx + t0 + tid);
+            prefetch_l2(a.tce + t0 + tid);
+        }
         pdl_wait();
         double th = 0.0, v = 0.0;
         if (tid < nph) {
@@ -224,11 +235,17 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
             if (JAC) {
                 // 1/v is read for the window's own buses only: warps of ghost
                 // slots skip it (a warp-uniform branch), mixed warps form it
-                // for all lanes; and (v^2, 2 v) for the reduction, formed once
-                // per bus instead of by both threads of its pair
+                // for all lanes; and the parameter-and-magnitude terms of the
+                // reduction, 2 v conj(Yd) and v^2 conj(Yd), formed once per bus
+                // here (where the FP64 pipe is idle) instead of by both threads
+                // of its pair (slot j < nbus is bus j, whose Yd thread j holds)
                 if (__any_sync(__activemask(), j < nbus)) {
                     iv = fast_rcp(v);
-                    if (j < nbus) sW2[j] = make_double2(v * v, fix_twice(v));
+                    if (j < nbus) {
+                        const double tv = fix_twice(v), v2 = v * v;
+                        sW2[j] = make_double2(__dmul_rn(tv, ydo.x), neg(__dmul_rn(tv, ydo.y)));   // 2 v conj(Yd)
+                        sSv[j] = make_double2(__dmul_rn(v2, ydo.x), neg(__dmul_rn(v2, ydo.y)));   // v^2 conj(Yd)
+                    }
                 }
             } else if (j < nbus) {
                 sW2[j].x = v * v;
@@ -237,7 +254,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         }
         if (tid < nbus) {
             sbm[tid] = bmo;
-            syd[tid] = ydo;
+            if (!JAC) syd[tid] = ydo;
             sord[tid] = ordo;
         }
         __syncthreads();
@@ -316,14 +333,12 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
                         }
                     }
                 }
-                const double2 y = syd[b], w2 = sW2[b];
-                const double iv = sW[b].y, v2 = w2.x, tv = w2.y;
-                // real part: Re conj(Yd) = y.x; imaginary part: Im conj(Yd) = -y.y (sign flips are exact)
-                const double yr = im ? neg(y.y) : y.x;
+                const double2 dv = sW2[b], sv = sSv[b];   // 2 v conj(Yd), v^2 conj(Yd)
+                const double iv = sW[b].y;
                 const int pos = bm.x + bm.z;
-                jst[(im ? 0 : L) + pos] = neg_if(sK, im);             // Re / Im of j sum K
-                jst[(im ? L : 0) + pos + d] = fma(tv, yr, sK * iv);   // 2 v conj(Yd) + sum K / v
-                spq[(im ? pqs : 0) + b + par] = fma(v2, yr, sK);      // S = v^2 conj(Yd) + sum K
+                jst[(im ? 0 : L) + pos] = neg_if(sK, im);                  // Re / Im of j sum K
+                jst[(im ? L : 0) + pos + d] = fma(sK, iv, im ? dv.y : dv.x);   // 2 v conj(Yd) + sum K / v
+                spq[(im ? pqs : 0) + b + par] = sK + (im ? sv.y : sv.x);      // S = v^2 conj(Yd) + sum K
             }
         } else {
             // two threads per bus as above; v^2 from the phasor phase

@@ -9,6 +9,11 @@ namespace pf {
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Bring the line of a valid global address into L2 (a hint: no data returned,
+// no ordering; L2 is the point of coherence, so a later load after a
+// programmatic-dependent-launch wait still sees what the previous grid wrote)
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");

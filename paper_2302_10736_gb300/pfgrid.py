@@ -100,6 +100,7 @@ def _load():
         "jac_reduced_solve": (st, [vp, vp, vp, vp, vp]),
         "pf_phase_probe_read": (st, [vp, i32, pi32]),
         "fp64_peak_probe": (st, [i32, i32, vp, ctypes.POINTER(ctypes.c_int64), vp]),
+        "grid_ew_windows": (st, [vp, vp, i32, pi32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -392,6 +393,17 @@ def kernel_name(k):
 
 def grid_trace_enable(grid, capacity):
     _check(_lib.grid_trace_enable(grid.handle, int(capacity)), "grid_trace_enable")
+
+
+def grid_ew_windows(grid):
+    """The element-wise windows: int32 array [nwin, 5] of {first bus, buses,
+    first terminal, terminals, phasor slots}."""
+    n = ctypes.c_int32()
+    _check(_lib.grid_ew_windows(grid.handle, None, 0, ctypes.byref(n)), "grid_ew_windows")
+    out = np.zeros((max(n.value, 0), 5), dtype=np.int32)
+    if n.value:
+        _check(_lib.grid_ew_windows(grid.handle, out.ctypes.data, n.value, ctypes.byref(n)), "grid_ew_windows")
+    return out
 
 
 def grid_trace_read(grid, cap=1 << 16):

@@ -43,7 +43,7 @@ int main()
             sincos_fix_host(tho, &Co, &So);
             sincos_fix_host(thq, &Cq, &Sq);
             pf::fix_phasor(Co, So, vo, &Ar, &Ai);
-            const int ey = pf::fix_coupling(yr, yi, &Yr, &Yi);
+            const int ey = pf::fix_block(yr, yi, &Yr, &Yi);
             double gr, gi;
             pf::fix_G(Ar, Ai, vo, Co, So, Cq, Sq, Yr, Yi, ey, yr, yi, &gr, &gi);
             std::printf("%.17g %.17g\n", gr, gi);

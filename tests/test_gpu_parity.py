@@ -512,3 +512,20 @@ def test_replicated_82k_grid(pf):
     for m in (0, 1):
         P, Q, J, _ = out["full", m]
         assert relerr(P, Pr) <= TOL and relerr(Q, Qr) <= TOL and relerr(J, Jr) <= TOL
+
+
+def test_ew_windows_cover_the_grid(pf):
+    """The element-wise windows (grid_ew_windows) are consecutive runs of buses
+    that cover the grid, each with all of its terminals, within the CTA's
+    thread count, and with at least its own buses as phasor slots."""
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    for window in (128, 256):
+        grid = pf.ybus_build(w)
+        pf.grid_set_config(grid, ew_window=window)
+        win = pf.grid_ew_windows(grid)
+        assert win.shape[1] == 5 and len(win) >= 1
+        b0, nbus, t0, nt, nph = win.T
+        assert b0[0] == 0 and np.all(b0[1:] == b0[:-1] + nbus[:-1]) and b0[-1] + nbus[-1] == grid.nb
+        assert t0[0] == 0 and np.all(t0[1:] == t0[:-1] + nt[:-1]) and t0[-1] + nt[-1] == 2 * grid.nl
+        assert np.all((nbus >= 1) & (nbus <= window) & (nt <= window) & (nph >= nbus))
