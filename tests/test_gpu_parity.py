@@ -529,3 +529,69 @@ def test_ew_windows_cover_the_grid(pf):
         assert b0[0] == 0 and np.all(b0[1:] == b0[:-1] + nbus[:-1]) and b0[-1] + nbus[-1] == grid.nb
         assert t0[0] == 0 and np.all(t0[1:] == t0[:-1] + nt[:-1]) and t0[-1] + nt[-1] == 2 * grid.nl
         assert np.all((nbus >= 1) & (nbus <= window) & (nt <= window) & (nph >= nbus))
+
+
+def test_values_outside_the_fixed_point_range(pf):
+    """The fixed-point products' fallbacks to FP64 products, through every
+    kernel: voltage magnitudes below 2^-960 (the block-floating phasor does
+    not hold them), angles beyond 2^16 (library sine and cosine, then
+    scaled), and a branch whose constants are near 1e-300 (their block
+    floating point does not hold them), each against the oracle."""
+    gr = random_grid(600, 820, 31, shift_max=0.2)
+    vm, va = random_state(600, 31)
+    vm = vm.copy()
+    va = va.copy()
+    vm[[3, 40, 599]] = [1e-300, 3e-299, 1e-295]
+    check_against_oracle(pf, gr, vm, va)
+    # beyond 2^16 radians the element-wise oracle's cos(theta_o - theta_q) loses
+    # about one ulp of theta (1e-11 at 1e5) in the rounded difference; the
+    # Ybus oracle's per-bus phasors do not, and both methods equal it exactly
+    va2 = va.copy()
+    va2[[5, 77, 300]] = [1.0e5, -3.0e6, 65536.5]
+    Y = oracle.ybus(gr)
+    jrp, jci = oracle.jac_pattern(Y)
+    P_ref, Q_ref = oracle.inj_sparse(Y, vm, va2)
+    J_ref = oracle.jac_ybus(Y, vm, va2)
+    grid = pf.ybus_build(gr)
+    for name, (P, Q, J) in gpu_eval(pf, grid, vm, va2).items():
+        assert relerr(P, P_ref) <= TOL and relerr(Q, Q_ref) <= TOL, name
+        if J is not None:
+            for a, b in zip(blocks(J, jci, 600, Y.nnz), blocks(J_ref, jci, 600, Y.nnz)):
+                assert relerr(a, b) <= TOL, name
+    gr2 = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in gr.items()}
+    gr2["g"][[0, 11]] = [1e-300, 2e-301]
+    gr2["b"][[0, 11]] = [-3e-300, 0.0]
+    gr2["bsh"][[0, 11]] = 0.0
+    check_against_oracle(pf, gr2, *random_state(600, 32))
+
+
+def test_nan_state_propagates_like_the_oracle(pf):
+    """A NaN angle or magnitude gives NaN exactly where the oracle's FP64
+    evaluation does (the fixed-point paths hand such values to FP64
+    products), and the finite outputs still match.  A NaN magnitude v_j: both
+    GPU methods form dS_i/dv_j = V_i conj(Y_ij U_j) (or conj(Yc) V_o conj(U_q)),
+    which does not involve v_j, as the Ybus oracle does; the element-wise
+    oracle's formula for it does, so the Ybus oracle is the reference there."""
+    gr = random_grid(400, 560, 33)
+    Y = oracle.ybus(gr)
+    grid = pf.ybus_build(gr)
+    jrp, jci = oracle.jac_pattern(Y)
+    for which in ("va", "vm"):
+        vm, va = random_state(400, 33)
+        vm, va = vm.copy(), va.copy()
+        (va if which == "va" else vm)[[7, 250]] = np.nan
+        with np.errstate(invalid="ignore"):
+            P_ref, Q_ref = oracle.inj_sparse(Y, vm, va)
+            J_ref = oracle.jac_ybus(Y, vm, va)
+            Pe, Qe, Je = oracle.elementwise(gr, vm, va, Y)
+        res = gpu_eval(pf, grid, vm, va)
+        refs = {"inj_ybus": (P_ref, Q_ref, None), "jac_ybus": (P_ref, Q_ref, J_ref),
+                "inj_elementwise": (Pe, Qe, None),
+                "jac_elementwise": (Pe, Qe, Je if which == "va" else J_ref)}
+        for name, out in res.items():
+            for x, r in zip(out, refs[name]):
+                if x is None:
+                    continue
+                assert np.array_equal(np.isnan(x), np.isnan(r)), (which, name)
+                ok = ~np.isnan(r)
+                assert relerr(x[ok], r[ok]) <= TOL, (which, name)
