@@ -138,9 +138,13 @@ __global__ void __launch_bounds__(256) k_phasor_fix(int nb, const double *__rest
     __shared__ ITrig tab[kITrigN];
     pdl_launch_dependents();
     if (threadIdx.x < kITrigN) tab[threadIdx.x] = g_itrig_tab[(blockIdx.x % kITrigCopies) * kITrigN + threadIdx.x];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nb) {   // the state: into L2 before the wait (no data returned), read after it
+        prefetch_l2(va + i);
+        prefetch_l2(vm + i);
+    }
     pdl_wait();
     __syncthreads();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     int64_t c, s;
     int_sincos_q62(va[i], tab, &c, &s);

@@ -76,7 +76,27 @@ __global__ void __launch_bounds__(512) k_ybus_fused(int nb, int nnz, const int *
         if (k < d) jj[j] = ci[rs + k];
     }
     for (int k = threadIdx.x; k < kITrigN; k += blockDim.x) tab[k] = trig[(blockIdx.x % kITrigCopies) * kITrigN + k];
-    pdl_wait();   // the state and the Ybus values may be the previous kernel's
+    // the state and the Ybus values may be the previous kernel's: their lines
+    // are only brought into L2 before the wait (prefetches return no data)
+    if (valid) {
+        prefetch_l2(va + row);
+        prefetch_l2(vm + row);
+    }
+#pragma unroll
+    for (int j = 0; j < kChunkW<W>; ++j) {
+        const int k = lane + W * j;
+        if (k < d) {
+            prefetch_l2(va + jj[j]);
+            prefetch_l2(vm + jj[j]);
+            if (JAC) {
+                prefetch_l2(Yf + rs + k);
+                prefetch_l2(Ye + rs + k);
+            } else {
+                prefetch_l2(Y + rs + k);
+            }
+        }
+    }
+    pdl_wait();
     // the Jacobian takes the block-floating values, the injections the doubles
     longlong2 yf[kChunkW<W>];
     int ye[kChunkW<W>];

@@ -120,7 +120,11 @@ __global__ void __launch_bounds__(512) k_inj_ybus_b(int S, int nb, const int *__
 #pragma unroll
     for (int j = 0; j < kChunkBW<W>; ++j) {
         const int k = lane + W * j;
-        if (k < d) jj[j] = ci[rs + k];
+        if (k < d) {
+            jj[j] = ci[rs + k];
+            prefetch_l2(Yf + rs + k);   // parameter data: into L2 before the wait, read after it
+            prefetch_l2(Ye + rs + k);
+        }
     }
     pdl_wait();
 #pragma unroll
@@ -211,7 +215,11 @@ __global__ void __launch_bounds__(512) k_jac_ybus_b(int S, int nb, int nnz, cons
 #pragma unroll
     for (int j = 0; j < kChunkBW<W>; ++j) {
         const int k = lane + W * j;
-        if (k < d) jj[j] = ci[rs + k];
+        if (k < d) {
+            jj[j] = ci[rs + k];
+            prefetch_l2(Yf + rs + k);   // parameter data: into L2 before the wait, read after it
+            prefetch_l2(Ye + rs + k);
+        }
     }
     // without outages every scenario's Jacobian is the base pattern, 4 nnz values apart
     ScenOut o{-1, -1, -1, -1, 0, 0, 0, -1};
