@@ -886,6 +886,8 @@ def main():
     for k in range(max(args.warmup, 3) * STREAM_COPIES):
         ew_k(k)
         yb_k(k)
+        pfgrid.inj_elementwise(*copies[k % STREAM_COPIES][:5])
+        pfgrid.inj_ybus(*copies[k % STREAM_COPIES][:5])
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     time.sleep(0.3)
@@ -899,6 +901,11 @@ def main():
     if dist:
         dist.barrier()
     ms_stream_yb = stream_loop(torch, yb_k, args.steps, "ybus_stream")
+    # the injections alone, in the same stream form
+    ms_stream_iew = stream_loop(torch, lambda k: pfgrid.inj_elementwise(*copies[k % STREAM_COPIES][:5]),
+                                args.steps, "inj_ew_stream")
+    ms_stream_iyb = stream_loop(torch, lambda k: pfgrid.inj_ybus(*copies[k % STREAM_COPIES][:5]),
+                                args.steps, "inj_ybus_stream")
     # one evaluation at a time: L2 flushed before every step outside the events,
     # so each step also pays its launch (the latency form)
     t_ew = time_loop(torch, ew, args.steps, flush, "ew")
@@ -1040,6 +1047,8 @@ def main():
             "compare": {
                 "elementwise_jac_evals_per_s": 1e3 / ms_stream,
                 "ybus_jac_evals_per_s_stream": 1e3 / ms_stream_yb,
+                "elementwise_inj_evals_per_s_stream": 1e3 / ms_stream_iew,
+                "ybus_inj_evals_per_s_stream": 1e3 / ms_stream_iyb,
                 "elementwise_jac_evals_per_s_flush_per_step": 1e3 / (sum(t_ew) / len(t_ew)),
                 "ybus_jac_evals_per_s_flush_per_step": 1e3 / (sum(t_yb) / len(t_yb)),
                 "elementwise_inj_evals_per_s_flush_per_step": 1e3 / (sum(t_iew) / len(t_iew)),
