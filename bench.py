@@ -290,10 +290,43 @@ def phase_probe_child(args):
         sm_end = np.array([gt1[sm == m].max() for m in np.unique(sm)])
         sm_end_spread.append((sm_end.max() - sm_end.min()) / 1e3)
     med = lambda x: float(np.median(x))
+    # the same kernel as the last launch of a stream of 40 over 16 grid copies
+    # (the headline's form): when its launch wait returned, and what follows
+    copies = [(grid, vm, va, P, Q, J)]
+    for _ in range(STREAM_COPIES - 1):
+        g2 = pfgrid.ybus_build(w)
+        copies.append((g2, dev(w["vm"][0]), dev(w["va"][0]), torch.empty_like(P), torch.empty_like(Q),
+                       torch.empty_like(J)))
+    for k in range(3 * STREAM_COPIES):
+        pfgrid.jac_elementwise(*copies[k % STREAM_COPIES])
+    sper = {n: [] for n in names}
+    rel_spread, post_span, post_med, end_spread = [], [], [], []
+    for _ in range(max(3, min(args.steps, 20))):
+        torch.cuda.synchronize()
+        torch.cuda._sleep(int(2.1e9 * 2e-3))
+        for k in range(40):
+            pfgrid.jac_elementwise(*copies[k % STREAM_COPIES])
+        torch.cuda.synchronize()
+        r = pfgrid.phase_probe_read().astype(np.float64)
+        r = r[r[:, 1] > 0]
+        gt0, gt1, cyc, gtw = r[:, 0], r[:, 1], r[:, 3:8], r[:, 8]
+        ns_per_cycle = np.median((gt1 - gt0) / np.maximum(cyc[:, 4], 1))
+        d = np.diff(np.concatenate([np.zeros((len(r), 1)), cyc], axis=1), axis=1) * ns_per_cycle / 1e3
+        for i, n in enumerate(names):
+            sper[n].append(float(np.median(d[:, i])))
+        rel_spread.append((gtw.max() - gtw.min()) / 1e3)
+        post_span.append((gt1.max() - gtw.min()) / 1e3)
+        post_med.append(float(np.median(gt1 - gtw)) / 1e3)
+        end_spread.append((gt1.max() - np.median(gt1)) / 1e3)
     print(json.dumps({"kernel": "k_ew<1>", "workload": WORKLOAD_NAME, "launches": args.steps,
                       "event_us": med(ev_us), "cta_span_us": med(span), "cta_end_median_us": med(end_med),
                       "cta_start_spread_us": med(start_spread), "sm_end_spread_us": med(sm_end_spread),
-                      "phase_median_us": {n: med(v) for n, v in per.items()}}), flush=True)
+                      "phase_median_us": {n: med(v) for n, v in per.items()},
+                      "stream": {"phase_median_us": {n: med(v) for n, v in sper.items()},
+                                 "wait_release_spread_us": med(rel_spread),
+                                 "first_release_to_last_end_us": med(post_span),
+                                 "release_to_end_median_us": med(post_med),
+                                 "last_end_after_median_end_us": med(end_spread)}}), flush=True)
 
 
 def job_throughput(torch, ms_local, world, dist, device):

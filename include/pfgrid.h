@@ -269,10 +269,12 @@ pf_status inj_ybus_noalloc(int32_t nb, const int32_t *rowptr, const int32_t *col
  * kernels then write timestamps; the default build writes none and this call
  * returns PF_EUNSUPPORTED).  Copies the records of the last launch of
  * jac_elementwise / inj_elementwise, for windows 0 .. min(max_windows, 8192)-1,
- * into out (host, 8 words per window): [0] %globaltimer (ns) when the window's
+ * into out (host, 9 words per window): [0] %globaltimer (ns) when the window's
  * CTA started, [1] when it ended, [2] its SM, [3..7] clock64 cycles from the
  * start to the end of the load, phasor, evaluation, reduction and store
- * phases.  *nwin receives the number of windows copied.  Synchronous.
+ * phases, [8] %globaltimer when its wait for the previous kernel in the
+ * stream (programmatic dependent launch) returned.  *nwin receives the number
+ * of windows copied.  Synchronous.
  */
 pf_status pf_phase_probe_read(uint64_t *out, int32_t max_windows, int32_t *nwin);
 

@@ -82,9 +82,10 @@ struct EwArgs {
 #ifdef PF_PHASE_PROBE
 // Phase probe (builds with -DPF_PHASE_PROBE only): thread 0 of every CTA of
 // the single-evaluation kernel records, per window, the %globaltimer at its
-// start and end, its SM, and the clock64 cycles from its start to the end of
-// each phase (loads, phasors, evaluation, reduction, stores).
-constexpr int kProbeMaxWin = 8192, kProbeSlots = 8;
+// start and end, its SM, the clock64 cycles from its start to the end of each
+// phase (loads, phasors, evaluation, reduction, stores), and the %globaltimer
+// when its programmatic-dependent-launch wait returned.
+constexpr int kProbeMaxWin = 8192, kProbeSlots = 9;
 __device__ unsigned long long g_phase_probe[kProbeMaxWin * kProbeSlots];
 __device__ __forceinline__ unsigned long long probe_gtimer()
 {
@@ -148,6 +149,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
         const unsigned long long gt0 = probe && tid == 0 ? probe_gtimer() : 0ull;
         const long long pt0 = clock64();
         long long pt[5] = {0, 0, 0, 0, 0};
+        unsigned long long gtw = 0ull;
 #endif
         if (PERSIST) __syncthreads();   // the previous window's shared-memory readers are done
         // two levels of dependent loads: the window's records (descriptor, the
@@ -196,6 +198,9 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
             prefetch_l2(a.tce + t0 + tid);
         }
         pdl_wait();
+#ifdef PF_PHASE_PROBE
+        if (probe && tid == 0) gtw = probe_gtimer();
+#endif
         double th = 0.0, v = 0.0;
         if (tid < nph) {
             th = a.va[o0];
@@ -430,6 +435,7 @@ __device__ __forceinline__ void ew_windows(const EwArgs &a)
             o[1] = probe_gtimer();
             o[2] = smid;
             for (int k = 0; k < 5; ++k) o[3 + k] = (unsigned long long)pt[k];
+            o[8] = gtw;
         }
 #endif
         if (!PERSIST) break;

@@ -439,8 +439,8 @@ def fp64_peak_probe(ctas, iters, sink, stream=None):
 
 def phase_probe_read(max_windows=8192):
     """Per-window phase records of the last single element-wise evaluation
-    (probe builds only): uint64 array [n, 8], see pf_phase_probe_read."""
-    out = np.zeros((max_windows, 8), np.uint64)
+    (probe builds only): uint64 array [n, 9], see pf_phase_probe_read."""
+    out = np.zeros((max_windows, 9), np.uint64)
     n = ctypes.c_int32()
     _check(_lib.pf_phase_probe_read(out.ctypes.data_as(ctypes.c_void_p), int(max_windows), ctypes.byref(n)),
            "pf_phase_probe_read")
