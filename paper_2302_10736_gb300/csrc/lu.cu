@@ -26,17 +26,24 @@
 //   y_j = F_j    - sum_k L(j, k) y_k               (forward solve, fused)
 //   L(i, j) = (A(i, j) - sum_k L(i, k) U(k, j)) / d,  U(j, i) = A(j, i) - sum_k L(j, k) U(k, i)
 // then the backward solve x_j = (y_j - sum_i U(j, i) x_i) / U(j, j) from the
-// root down.  Levels are separated by grid barriers (bounded waits).  Wide
-// levels give a warp to a column (a lane per slot); on the narrow top of the
-// tree, where the dependency chain is, every slot of a level's columns gets a
-// warp of its own (its lanes splitting the slot's sum; each warp forms its
-// column's pivot itself, the same way), and the backward solve of that part
-// runs in one CTA with CTA barriers.  Every gather issues four loads per lane
-// before using them.  Every sum has a fixed order (sequential, or lane-strided
-// partial sums joined by a fixed shuffle tree): the results are bitwise
-// repeatable.  Values written by
-// other CTAs are read with L1-bypassing loads.  A zero or non-finite pivot
-// sets the grid's error word (no trap).
+// root down.  No barrier separates the levels: a column depends only on its
+// descendants in the elimination tree, so every work item waits for its
+// column's children to be finished (per-column counters, bounded waits) and
+// the work runs as soon as its inputs exist, along the tree's critical path
+// rather than level by level.  Work items are in level order and the warps
+// take them in that order from a shared counter, so the lowest unfinished item
+// has a warp and its inputs, and can always run (all CTAs are resident:
+// cooperative launch).  Wide levels give a warp to a
+// column (a lane per slot); on the narrow top of the tree every slot of a
+// column gets a warp of its own (its lanes splitting the slot's sum; each warp
+// forms its column's pivot itself, the same way); the backward solve gives a
+// warp to a column, which waits for its parent.  Every gather issues four loads
+// per lane before using them.  Every sum has a fixed order (sequential, or
+// lane-strided partial sums joined by a fixed shuffle tree): the results are
+// bitwise repeatable.  Values written by other CTAs are read with
+// L1-bypassing loads after an acquire load of the counter that announced them.
+// A zero or non-finite pivot sets the grid's error word (no trap); a wait that
+// runs out (2 s) sets it to a time-out and ends the warp.
 #include <algorithm>
 #include <set>
 #include <vector>
@@ -51,18 +58,73 @@ namespace {
 
 constexpr uint64_t kLuBarrierNs = 2000000000ull;   // bounded grid-barrier wait (2 s)
 constexpr int kLuThreads = 512;
-constexpr int kLuChainCols = 4;   // levels at most this wide at the top go to one CTA
+constexpr int kLuChainCols = 4;   // levels at most this wide at the top: one work item per slot
 
 struct LuArgs {
-    int n, nnzA, H, chain;
-    const int *Lp, *Li, *Rp, *Rk, *Rq, *lvl_ptr, *lvl_col, *perm, *amap, *gptr, *item_ptr;
-    const int2 *gsrc;    // per update term of a slot: {L(i, k) slot, U(k, j) slot}
-    const int2 *items;   // narrow levels: {column, slot or -1} per warp item
+    int n, nnzA, nfitems;
+    const int *Lp, *Li, *Rp, *Rk, *Rq, *perm, *amap, *gptr;
+    const int *need, *cptr, *cidx, *parent, *bcols;
+    const int2 *gsrc;     // per update term of a slot: {L(i, k) slot, U(k, j) slot}
+    const int2 *fitems;   // {column, -2 (whole column) or slot or -1 (pivot only)}, level order
     const double *A, *F;
     double *Lx, *Ux, *D, *y, *dx;
+    double *piv;          // [n] the pivots U(j, j) (D keeps A(j, j): every item of a column reads it)
+    int *done;            // [2n + 1]: finished items of column j at j, x_j written at n + j, the item counter
     unsigned int *bar;
     int *err;
 };
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long lu_gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait until *p >= target, at most kLuBarrierNs; false (and the grid's error
+// word set to a time-out) if it never gets there
+__device__ __forceinline__ bool lu_wait(const LuArgs &a, const int *p, int target)
+{
+    if (ld_acquire(p) >= target) return true;
+    const unsigned long long t0 = lu_gtimer();
+    for (;;) {
+        __nanosleep(20);
+        if (ld_acquire(p) >= target) return true;
+        if (lu_gtimer() - t0 > kLuBarrierNs) {
+            atomicExch(a.err, DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// every child of column j in the elimination tree finished (the lanes wait for
+// different children); false on a time-out (all lanes agree)
+__device__ __forceinline__ bool lu_wait_children(const LuArgs &a, int j, int lane)
+{
+    bool ok = true;
+    for (int t = a.cptr[j] + lane; t < a.cptr[j + 1]; t += 32) {
+        const int c = a.cidx[t];
+        ok = ok && lu_wait(a, a.done + c, a.need[c]);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    __syncwarp();   // orders the waiting lanes' acquires before every lane's reads
+    return ok;
+}
+
+// the warp's writes visible, then one more finished item of column j
+__device__ __forceinline__ void lu_finish(const LuArgs &a, int *cnt, int lane)
+{
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicAdd(cnt, 1);
+}
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 
@@ -172,7 +234,7 @@ __device__ __forceinline__ void lu_column_warp(const LuArgs &a, int j, int lane)
     }
     if (lane == 0) {
         pivot_check(a, d);
-        a.D[j] = d;
+        a.piv[j] = d;
         a.y[j] = yj;
     }
 }
@@ -193,7 +255,7 @@ __device__ __forceinline__ void lu_item(const LuArgs &a, int j, int p, int lane)
     }
     if (lane == 0 && (p < 0 || p == a.Lp[j])) {
         pivot_check(a, d);
-        a.D[j] = d;
+        a.piv[j] = d;
         a.y[j] = ldcg(a.y + j) - t.y;
     }
 }
@@ -206,7 +268,7 @@ __device__ __forceinline__ void lu_back(const LuArgs &a, int j, int lane)
     for (int p = p0 + lane; p < p1; p += 32) s = fma(ldcg(a.Ux + p), ldcg(a.y + a.Li[p]), s);
     s = warp_sum_d(s);
     if (lane == 0) {
-        const double x = (ldcg(a.y + j) - s) * fast_rcp(ldcg(a.D + j));
+        const double x = (ldcg(a.y + j) - s) * fast_rcp(ldcg(a.piv + j));
         a.y[j] = x;
         a.dx[a.perm[j]] = x;
     }
@@ -215,17 +277,19 @@ __device__ __forceinline__ void lu_back(const LuArgs &a, int j, int lane)
 __global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
 {
     const GridBar gbar = grid_barrier_begin(a.bar);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp_cta = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
     const int gwarp = (int)(gtid >> 5), gwarps = (int)(gthreads >> 5);
     const int nnzL = a.Lp[a.n];
     unsigned int bk = 0;
-    // ---- the factor storage zeroed, then A and the right-hand side scattered in ----
+    // ---- the factor storage and the counters zeroed, then A and the
+    // right-hand side scattered in ----
     for (long long t = gtid; t < nnzL; t += gthreads) {
         a.Lx[t] = 0.0;
         a.Ux[t] = 0.0;
     }
+    for (long long t = gtid; t < 2LL * a.n + 1; t += gthreads) a.done[t] = 0;   // and the item counter
     if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
     for (long long e = gtid; e < a.nnzA; e += gthreads) {
         const int code = a.amap[e], slot = code >> 2;
@@ -239,35 +303,34 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
     }
     for (long long j = gtid; j < a.n; j += gthreads) a.y[j] = a.F[a.perm[j]];
     if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
-    // ---- factorization and forward solve, level by level ----
-    for (int h = 0; h < a.chain; ++h) {
-        const int c0 = a.lvl_ptr[h], nc = a.lvl_ptr[h + 1] - c0;
-        for (int t = gwarp; t < nc; t += gwarps) lu_column_warp(a, a.lvl_col[c0 + t], lane);
-        if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
-    }
-    // ---- the narrow top: a warp per (column, slot) item, all CTAs ----
-    for (int h = a.chain; h < a.H; ++h) {
-        const int i0 = a.item_ptr[h - a.chain], ni = a.item_ptr[h - a.chain + 1] - i0;
-        for (int t = gwarp; t < ni; t += gwarps) {
-            const int2 it = a.items[i0 + t];
-            lu_item(a, it.x, it.y, lane);
+    // ---- every warp takes the next item (factorization and forward solve in
+    // level order, then the backward solve from the root down) from a shared
+    // counter, waits for what the item depends on, and runs it ----
+    (void)gwarp;
+    (void)gwarps;
+    int *next = a.done + 2LL * a.n;
+    const int nall = a.nfitems + a.n;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(next, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= nall) break;
+        if (t < a.nfitems) {   // once the column's children are finished
+            const int2 it = a.fitems[t];
+            if (!lu_wait_children(a, it.x, lane)) return;
+            if (it.y == -2)
+                lu_column_warp(a, it.x, lane);
+            else
+                lu_item(a, it.x, it.y, lane);
+            lu_finish(a, a.done + it.x, lane);
+        } else {   // x_j once its parent's is written (the root's once its own factorization is finished)
+            const int j = a.bcols[t - a.nfitems], pj = a.parent[j];
+            const bool ok = pj >= 0 ? lu_wait(a, a.done + a.n + pj, 1) : lu_wait(a, a.done + j, a.need[j]);
+            if (!__all_sync(0xffffffffu, ok)) return;
+            __syncwarp();
+            lu_back(a, j, lane);
+            lu_finish(a, a.done + a.n + j, lane);
         }
-        if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
-    }
-    // ---- the backward solve of the narrow top in CTA 0 (CTA barriers only) ----
-    if (blockIdx.x == 0) {
-        for (int h = a.H - 1; h >= a.chain; --h) {
-            const int c0 = a.lvl_ptr[h], nc = a.lvl_ptr[h + 1] - c0;
-            for (int t = warp; t < nc; t += nwarp_cta) lu_back(a, a.lvl_col[c0 + t], lane);
-            __syncthreads();
-        }
-    }
-    if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
-    // ---- backward solve below the top, from the highest level down ----
-    for (int h = a.chain - 1; h >= 0; --h) {
-        const int c0 = a.lvl_ptr[h], nc = a.lvl_ptr[h + 1] - c0;
-        for (int t = gwarp; t < nc; t += gwarps) lu_back(a, a.lvl_col[c0 + t], lane);
-        if (h > 0 && !grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
     }
 }
 
@@ -429,19 +492,39 @@ pf_status host_lu(int nb, int n, int npvpq, const std::vector<int> &colptr, cons
     L.lvl_col.assign(n, 0);
     std::vector<int> lf(L.lvl_ptr.begin(), L.lvl_ptr.end() - 1);
     for (int j = 0; j < n; ++j) L.lvl_col[lf[height[j]]++] = j;
+    // levels at most kLuChainCols wide from the top down: every slot of their
+    // columns is a work item of its own (a column without slots below the
+    // diagonal still needs its pivot: slot -1); below them a column is one item
     L.chain = L.H;
     while (L.chain > 0 && L.lvl_ptr[L.chain] - L.lvl_ptr[L.chain - 1] <= kLuChainCols) --L.chain;
-    // the narrow levels' work items: every slot of every column (a column
-    // without slots below the diagonal still needs its pivot: slot -1)
-    L.item_ptr.assign(L.H - L.chain + 1, 0);
-    for (int h = L.chain; h < L.H; ++h) {
+    L.need.assign(n, 0);
+    for (int h = 0; h < L.H; ++h)
         for (int t = L.lvl_ptr[h]; t < L.lvl_ptr[h + 1]; ++t) {
             const int j = L.lvl_col[t];
-            if (L.Lp[j + 1] == L.Lp[j]) L.items.push_back(make_int2(j, -1));
-            for (int p = L.Lp[j]; p < L.Lp[j + 1]; ++p) L.items.push_back(make_int2(j, p));
+            if (h < L.chain) {
+                L.fitems.push_back(make_int2(j, -2));
+            } else {
+                if (L.Lp[j + 1] == L.Lp[j]) L.fitems.push_back(make_int2(j, -1));
+                for (int p = L.Lp[j]; p < L.Lp[j + 1]; ++p) L.fitems.push_back(make_int2(j, p));
+            }
+            L.need[j] = h < L.chain ? 1 : std::max(1, L.Lp[j + 1] - L.Lp[j]);
         }
-        L.item_ptr[h - L.chain + 1] = (int)L.items.size();
+    // the elimination tree's children (CSR) and parents
+    L.parent = parent;
+    L.cptr.assign(n + 1, 0);
+    for (int j = 0; j < n; ++j)
+        if (parent[j] >= 0) L.cptr[parent[j] + 1]++;
+    for (int j = 0; j < n; ++j) L.cptr[j + 1] += L.cptr[j];
+    L.cidx.assign(L.cptr[n], 0);
+    {
+        std::vector<int> cf(L.cptr.begin(), L.cptr.end() - 1);
+        for (int j = 0; j < n; ++j)
+            if (parent[j] >= 0) L.cidx[cf[parent[j]]++] = j;
     }
+    // the backward solve's columns from the highest level down
+    L.bcols.reserve(n);
+    for (int h = L.H - 1; h >= 0; --h)
+        for (int t = L.lvl_ptr[h]; t < L.lvl_ptr[h + 1]; ++t) L.bcols.push_back(L.lvl_col[t]);
     // every entry of J_r (CSC order) to its factor slot: 4 slot + {0: L, 1: U, 2: diagonal}
     const int nnzA = colptr[n];
     L.amap.assign(nnzA, 0);
@@ -477,21 +560,24 @@ pf_status lu_prepare(Grid *g, cudaStream_t s)
     if ((e = up(&g->lu_Lp, L.Lp)) || (e = up(&g->lu_Li, L.Li)) || (e = up(&g->lu_Rp, L.Rp)) ||
         (e = up(&g->lu_Rk, L.Rk)) || (e = up(&g->lu_Rq, L.Rq)) || (e = up(&g->lu_lvl_ptr, L.lvl_ptr)) ||
         (e = up(&g->lu_lvl_col, L.lvl_col)) || (e = up(&g->lu_perm, L.perm)) || (e = up(&g->lu_amap, L.amap)) ||
-        (e = up(&g->lu_gptr, L.gptr)) || (e = up(&g->lu_item_ptr, L.item_ptr)) ||
-        (e = g->arena.alloc(&g->lu_items, std::max<size_t>(L.items.size(), 1))) ||
-        (!L.items.empty() && (e = cudaMemcpyAsync(g->lu_items, L.items.data(), L.items.size() * sizeof(int2),
-                                                  cudaMemcpyHostToDevice, s))) ||
+        (e = up(&g->lu_gptr, L.gptr)) || (e = up(&g->lu_need, L.need)) || (e = up(&g->lu_cptr, L.cptr)) ||
+        (e = up(&g->lu_cidx, L.cidx)) || (e = up(&g->lu_parent, L.parent)) || (e = up(&g->lu_bcols, L.bcols)) ||
+        (e = g->arena.alloc(&g->lu_done, 2 * (size_t)L.n + 1)) ||
+        (e = g->arena.alloc(&g->lu_fitems, std::max<size_t>(L.fitems.size(), 1))) ||
+        (!L.fitems.empty() && (e = cudaMemcpyAsync(g->lu_fitems, L.fitems.data(), L.fitems.size() * sizeof(int2),
+                                                   cudaMemcpyHostToDevice, s))) ||
         (e = g->arena.alloc(&g->lu_gsrc, std::max<size_t>(L.gsrc.size(), 1))) ||
         (!L.gsrc.empty() && (e = cudaMemcpyAsync(g->lu_gsrc, L.gsrc.data(), L.gsrc.size() * sizeof(int2),
                                                  cudaMemcpyHostToDevice, s))) ||
         (e = g->arena.alloc(&g->lu_Lx, std::max<size_t>(nnzL, 1))) ||
         (e = g->arena.alloc(&g->lu_Ux, std::max<size_t>(nnzL, 1))) ||
-        (e = g->arena.alloc(&g->lu_D, std::max(L.n, 1))) || (e = g->arena.alloc(&g->lu_y, std::max(L.n, 1))) ||
+        (e = g->arena.alloc(&g->lu_D, std::max(2 * L.n, 1))) || (e = g->arena.alloc(&g->lu_y, std::max(L.n, 1))) ||
         (e = cudaStreamSynchronize(s)))
         return cuda_error(e, "jac_reduced_solve: set-up");
     g->lu_n = L.n;
     g->lu_H = L.H;
     g->lu_chain = L.chain;
+    g->lu_nfitems = (int)L.fitems.size();
     g->lu_widest = 1;
     for (int h = 0; h < L.H; ++h) g->lu_widest = std::max(g->lu_widest, L.lvl_ptr[h + 1] - L.lvl_ptr[h]);
     g->lu_nnzL = (long long)nnzL;
@@ -504,11 +590,13 @@ void lu_release(Grid *g)
     for (void *p : {(void *)g->lu_Lp, (void *)g->lu_Li, (void *)g->lu_Rp, (void *)g->lu_Rk, (void *)g->lu_Rq,
                     (void *)g->lu_lvl_ptr, (void *)g->lu_lvl_col, (void *)g->lu_perm, (void *)g->lu_amap,
                     (void *)g->lu_Lx, (void *)g->lu_Ux, (void *)g->lu_D, (void *)g->lu_y, (void *)g->lu_gptr,
-                    (void *)g->lu_gsrc, (void *)g->lu_item_ptr, (void *)g->lu_items})
+                    (void *)g->lu_gsrc, (void *)g->lu_need, (void *)g->lu_cptr, (void *)g->lu_cidx,
+                    (void *)g->lu_parent, (void *)g->lu_bcols, (void *)g->lu_done, (void *)g->lu_fitems})
         g->arena.release(p);
     g->lu_Lp = g->lu_Li = g->lu_Rp = g->lu_Rk = g->lu_Rq = g->lu_lvl_ptr = g->lu_lvl_col = g->lu_perm = g->lu_amap =
-        g->lu_gptr = g->lu_item_ptr = nullptr;
-    g->lu_gsrc = g->lu_items = nullptr;
+        g->lu_gptr = nullptr;
+    g->lu_need = g->lu_cptr = g->lu_cidx = g->lu_parent = g->lu_bcols = g->lu_done = nullptr;
+    g->lu_gsrc = g->lu_fitems = nullptr;
     g->lu_Lx = g->lu_Ux = g->lu_D = g->lu_y = nullptr;
     g->lu_ready = 0;
 }
@@ -519,26 +607,29 @@ cudaError_t launch_lu_solve(Grid *g, const double *Jr, const double *F, double *
     LuArgs a{};
     a.n = g->lu_n;
     a.nnzA = (int)g->red_nnz;
-    a.H = g->lu_H;
-    a.chain = g->lu_chain;
+    a.nfitems = g->lu_nfitems;
     a.Lp = g->lu_Lp;
     a.Li = g->lu_Li;
     a.Rp = g->lu_Rp;
     a.Rk = g->lu_Rk;
     a.Rq = g->lu_Rq;
-    a.lvl_ptr = g->lu_lvl_ptr;
-    a.lvl_col = g->lu_lvl_col;
     a.perm = g->lu_perm;
     a.amap = g->lu_amap;
     a.gptr = g->lu_gptr;
     a.gsrc = g->lu_gsrc;
-    a.item_ptr = g->lu_item_ptr;
-    a.items = g->lu_items;
+    a.need = g->lu_need;
+    a.cptr = g->lu_cptr;
+    a.cidx = g->lu_cidx;
+    a.parent = g->lu_parent;
+    a.bcols = g->lu_bcols;
+    a.fitems = g->lu_fitems;
+    a.done = g->lu_done;
     a.A = Jr;
     a.F = F;
     a.Lx = g->lu_Lx;
     a.Ux = g->lu_Ux;
     a.D = g->lu_D;
+    a.piv = g->lu_D + g->lu_n;
     a.y = g->lu_y;
     a.dx = dx;
     a.bar = g->bar;

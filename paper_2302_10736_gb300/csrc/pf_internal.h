@@ -307,8 +307,10 @@ struct Grid {
     long long lu_nnzL = 0;
     int *lu_Lp = nullptr, *lu_Li = nullptr, *lu_Rp = nullptr, *lu_Rk = nullptr, *lu_Rq = nullptr;
     int *lu_lvl_ptr = nullptr, *lu_lvl_col = nullptr, *lu_perm = nullptr, *lu_amap = nullptr, *lu_gptr = nullptr;
-    int *lu_item_ptr = nullptr;
-    int2 *lu_gsrc = nullptr, *lu_items = nullptr;
+    int *lu_need = nullptr, *lu_cptr = nullptr, *lu_cidx = nullptr, *lu_parent = nullptr, *lu_bcols = nullptr;
+    int *lu_done = nullptr;   // [2n + 1] per column: finished factorization items, backward solve done; the item counter
+    int lu_nfitems = 0;
+    int2 *lu_gsrc = nullptr, *lu_fitems = nullptr;
     double *lu_Lx = nullptr, *lu_Ux = nullptr, *lu_D = nullptr, *lu_y = nullptr;
     // tracer: events [2 * capacity], kernel id per record
     std::vector<cudaEvent_t> tr_ev;
@@ -397,8 +399,13 @@ struct HostLu {
     std::vector<int> perm, Lp, Li, Rp, Rk, Rq, lvl_ptr, lvl_col, amap;
     std::vector<int> gptr;    // [nnzL + 1] update terms of every factor slot
     std::vector<int2> gsrc;   // {slot of L(i, k), slot of L(j, k)}, k ascending per slot
-    std::vector<int> item_ptr;   // [H - chain + 1] the narrow levels' items
-    std::vector<int2> items;     // {column, slot or -1}
+    // dependency-driven schedule: the factorization's work items in level order
+    // ({column, -2}: the whole column by one warp; {column, slot or -1}: one slot
+    // of a column of the narrow top), the items of every column, the columns'
+    // children in the elimination tree (CSR) and parents, and the columns of the
+    // backward solve from the root down
+    std::vector<int2> fitems;
+    std::vector<int> need, cptr, cidx, parent, bcols;
 };
 pf_status host_lu(int nb, int n, int npvpq, const std::vector<int> &colptr, const std::vector<int> &rowidx,
                   const std::vector<int> &fmap, HostLu &L);
