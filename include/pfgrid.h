@@ -17,6 +17,16 @@
  *   Voltages are polar: vm = |V| (the "V_m" of Eq. 4), va = theta (rad).
  *   All values are IEEE FP64; indices int32.
  *
+ * Numerics
+ *   Inputs, outputs and every sum are FP64.  Inside the kernels the sine and
+ *   cosine of the angles and the complex products (V_o conj(U_q), conj(Yc) E,
+ *   Y_ij U_j, V_i conj(Y_ij U_j)) are computed in 64-bit fixed point on the
+ *   integer pipes and rounded once to FP64: within 2^-53 of the product's
+ *   magnitude before that rounding, at least as accurate as FP64 products.
+ *   Non-finite values and magnitudes outside about 2^-960 .. 2^957 take FP64
+ *   products (IEEE semantics, NaN propagated).  The element-wise Jacobian's
+ *   diagonal uses 1/vm, so vm must be a normal, nonzero number there.
+ *
  *   Ybus pattern: every diagonal (i, i) plus (h, k) and (k, h) of every
  *   branch; parallel branches share one entry; columns sorted; explicit zeros
  *   kept (Sec. IV-B.2).
