@@ -987,6 +987,8 @@ def main():
             "ops_note": "the method's operations in plain FP64 form (12 per terminal, 16 per bus); the kernel runs "
                         "8 per terminal and 3 per bus of them in 64-bit fixed point on the integer pipes, %d on "
                         "the FP64 pipe" % (EW_FP64_PIPE_PER_TERMINAL * T + EW_FP64_PIPE_PER_BUS * nb),
+            "fp64_pipe_frac": (EW_FP64_PIPE_PER_TERMINAL * T + EW_FP64_PIPE_PER_BUS * nb) / (ms_stream * 1e-3) / 1e9
+                              / fp64_peak["gdfma_per_s"],
             "peak_source": "measured: fp64_peak_probe (DFMA chains on every SM) in this run",
             "frac_of_nominal": achieved / FP64_OPS_PEAK_G,
             "nominal_peak": FP64_OPS_PEAK_G,
