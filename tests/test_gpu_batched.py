@@ -223,6 +223,22 @@ def test_batch_without_outages_equals_single_evaluation(pf):
         pf.jac_elementwise(grid, _d(vm[s]), _d(va[s]), P1, Q1, J1)
         assert torch.equal(P[s * 2000:(s + 1) * 2000], P1) and torch.equal(Q[s * 2000:(s + 1) * 2000], Q1)
         assert torch.equal(J[s * grid.nnzJ:(s + 1) * grid.nnzJ], J1)
+    # the Ybus method: the single evaluation's separate form runs the batch's
+    # row kernel for one scenario, so with the same lanes it agrees bit for bit
+    bc = pf.batch_get_config(batch)
+    pf.grid_set_config(grid, ybus_lanes=bc["ybus_lanes"], ybus_block=bc["ybus_block"], ybus_fused=0)
+    pf.jac_ybus_batched(batch, _d(vm), _d(va), P, Q, J)
+    Pi, Qi = torch.empty_like(P), torch.empty_like(Q)
+    pf.inj_ybus_batched(batch, _d(vm), _d(va), Pi, Qi)
+    for s in range(3):
+        P1 = torch.empty(2000, dtype=torch.float64, device="cuda")
+        Q1 = torch.empty_like(P1)
+        J1 = torch.empty(grid.nnzJ, dtype=torch.float64, device="cuda")
+        pf.jac_ybus(grid, _d(vm[s]), _d(va[s]), P1, Q1, J1)
+        assert torch.equal(P[s * 2000:(s + 1) * 2000], P1) and torch.equal(Q[s * 2000:(s + 1) * 2000], Q1)
+        assert torch.equal(J[s * grid.nnzJ:(s + 1) * grid.nnzJ], J1)
+        pf.inj_ybus(grid, _d(vm[s]), _d(va[s]), P1, Q1)
+        assert torch.equal(Pi[s * 2000:(s + 1) * 2000], P1) and torch.equal(Qi[s * 2000:(s + 1) * 2000], Q1)
 
 
 def test_workload3_n1_batch(pf):
