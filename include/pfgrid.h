@@ -21,8 +21,8 @@
  *   Inputs, outputs and every sum are FP64.  Inside the kernels the sine and
  *   cosine of the angles and the complex products (V_o conj(U_q), conj(Yc) E,
  *   Y_ij U_j, V_i conj(Y_ij U_j)) are computed in 64-bit fixed point on the
- *   integer pipes and rounded once to FP64: within 2^-53 of the product's
- *   magnitude before that rounding, at least as accurate as FP64 products.
+ *   integer pipes and rounded once to FP64: within 2^-52 of the product's
+ *   magnitude after that rounding, at least as accurate as FP64 products.
  *   Non-finite values and magnitudes outside about 2^-960 .. 2^957 take FP64
  *   products (IEEE semantics, NaN propagated).  The element-wise Jacobian's
  *   diagonal uses 1/vm, so vm must be a normal, nonzero number there.

@@ -14,15 +14,17 @@
 //   * V_o in block floating point: A = floor(M C / 2^64), floor(M S / 2^64) with
 //     M = 2^10 times the 53-bit significand of v_o, so that V_o = A 2^(e - 1083)
 //     with e the biased exponent of v_o, |A| < 2^61;
-//   * B = A conj(U_q) by four signed multiply-highs: E = B 2^(e - 1081), |B| < 2^60;
+//   * B = A conj(U_q) by three signed multiply-highs (Gauss's complex product):
+//     E = B 2^(e - 1081), |B| < 2^60;
 //   * Yc_t in block floating point (its larger component exact, per-terminal
-//     exponent, formed at setup) and G = conj(Yc) B by four more;
+//     exponent, formed at setup) and G = conj(Yc) B by three more;
 //   * each component of G (or of E) rounded once to the nearest double (ties
 //     away from zero) by a leading-zero count and a shift.
 //
 // The truncations leave an absolute error below 2^-56 |v_o| = 2^-56 |E| in
-// each component of E before its rounding, and below 2^-53 |G| in each
-// component of G (the FP64 products they replace round four times at 2^-53).
+// each component of E before its rounding, and about 2^-53 |G| in each
+// component of G, so that after its rounding each component of G is within
+// 2^-52 |G| (the FP64 products they replace round four times at 2^-53).
 // Angles that are not finite, v_o with a biased exponent outside
 // [kFixExpMin, kFixExpMax] (zero, subnormal, or beyond 2^957 in magnitude),
 // and Yc or products outside the range take FP64 products instead
@@ -130,10 +132,11 @@ __host__ __device__ __forceinline__ void fix_E(int64_t Ar, int64_t Ai, double vo
 }
 
 // A complex constant y = (yr, yi) (a coupling constant Yc, a Ybus value) in
-// block floating point: (*fr, *fi) 2^(e - 1085) with e the larger biased
-// exponent of yr, yi (the larger component exact, in [2^62, 2^63)); returns e,
-// or 0 if y is zero, subnormal, non-finite or beyond the exponent range (the
-// kernels then multiply in FP64).  Setup arithmetic.
+// block floating point: (*fr, *fi) 2^(e - 1084) with e the larger biased
+// exponent of yr, yi (the larger component exact, in [2^61, 2^62), so that the
+// sums of components in fix_mul stay below 2^63); returns e, or 0 if y is
+// zero, subnormal, non-finite or beyond the exponent range (the kernels then
+// multiply in FP64).  Setup arithmetic.
 __host__ __device__ __forceinline__ int fix_block(double yr, double yi, int64_t *fr, int64_t *fi)
 {
     const int er = fix_vexp(yr), ei = fix_vexp(yi);
@@ -143,7 +146,7 @@ __host__ __device__ __forceinline__ int fix_block(double yr, double yi, int64_t 
         *fi = 0;
         return 0;
     }
-    const double sc = bits_dbl((uint64_t)(1085 - e + 1023) << 52);   // 2^(1085 - e), exact products
+    const double sc = bits_dbl((uint64_t)(1084 - e + 1023) << 52);   // 2^(1084 - e), exact products
 #ifdef __CUDA_ARCH__
     *fr = __double2ll_rn(yr * sc);
     *fi = __double2ll_rn(yi * sc);
@@ -154,19 +157,24 @@ __host__ __device__ __forceinline__ int fix_block(double yr, double yi, int64_t 
     return e;
 }
 
-// a conj(b) 2^-64 and a b 2^-64 of two fixed-point complex numbers (the high
-// words of the products; |a| |b| < 2^126)
+// a conj(b) 2^-64 and a b 2^-64 of two fixed-point complex numbers by three
+// multiply-highs each (Gauss's product: k1 = br (ar + ai), then a conj(b) =
+// (k1 - ai (br - bi), k1 - ar (br + bi)) and a b = (k1 - ai (br + bi),
+// k1 + ar (bi - br))); every component sum of a and of b must stay below 2^63
+// in magnitude, and each result component is within 2 units of the exact one
 __host__ __device__ __forceinline__ void fix_mul_conj(int64_t ar, int64_t ai, int64_t br, int64_t bi, int64_t *r,
                                                       int64_t *i)
 {
-    *r = s64_mulhi(ar, br) + s64_mulhi(ai, bi);
-    *i = s64_mulhi(ai, br) - s64_mulhi(ar, bi);
+    const int64_t k1 = s64_mulhi(br, ar + ai);
+    *r = k1 - s64_mulhi(ai, br - bi);
+    *i = k1 - s64_mulhi(ar, br + bi);
 }
 __host__ __device__ __forceinline__ void fix_mul(int64_t ar, int64_t ai, int64_t br, int64_t bi, int64_t *r,
                                                  int64_t *i)
 {
-    *r = s64_mulhi(ar, br) - s64_mulhi(ai, bi);
-    *i = s64_mulhi(ar, bi) + s64_mulhi(ai, br);
+    const int64_t k1 = s64_mulhi(br, ar + ai);
+    *r = k1 - s64_mulhi(ai, br + bi);
+    *i = k1 + s64_mulhi(ar, bi - br);
 }
 
 // G = conj(Yc) V_o conj(U_q) (= dS_t/dv_q) entirely in fixed point: (Ar, Ai) =
@@ -176,7 +184,7 @@ __host__ __device__ __forceinline__ void fix_mul(int64_t ar, int64_t ai, int64_t
 __host__ __device__ __forceinline__ bool fix_G_fast(int64_t Ar, int64_t Ai, double vo, int64_t Cq, int64_t Sq,
                                                     int64_t Yr, int64_t Yi, int ey, double *gr, double *gi)
 {
-    const int e1 = ey + fix_vexp(vo) - 1017;   // G = g 2^(ey + e_o - 2102), |g| < 2^59
+    const int e1 = ey + fix_vexp(vo) - 1016;   // G = g 2^(ey + e_o - 2101), |g| < 2^58
     if (e1 < 64 || e1 > 2046) return false;
     int64_t br, bi, g_r, g_i;
     fix_mul_conj(Ar, Ai, Cq, Sq, &br, &bi);   // E = B 2^(e_o - 1081)
@@ -187,7 +195,7 @@ __host__ __device__ __forceinline__ bool fix_G_fast(int64_t Ar, int64_t Ai, doub
 }
 
 // The Ybus method's products for entry (i, j) in fixed point (Eqs. 3-4):
-// YU = Y_ij U_j (|yu| < 2^62, YU = yu 2^(ey - 1083)) and dS_i/dv_j =
+// YU = Y_ij U_j (|yu| < 2^61, YU = yu 2^(ey - 1082)) and dS_i/dv_j =
 // V_i conj(YU), from (Yr, Yi, ey) = fix_block(Y_ij) with ey != 0, (C, S) = U_j
 // and (Ar, Ai) = fix_phasor of V_i, neither the marker.  Returns false
 // (nothing written) when dS_i/dv_j's exponent leaves the range of normal
@@ -196,26 +204,26 @@ __host__ __device__ __forceinline__ bool fix_ybus_entry(int64_t Yr, int64_t Yi, 
                                                         int64_t Ar, int64_t Ai, double vi, double *yur,
                                                         double *yui, double *svr, double *svi)
 {
-    const int e1 = ey + fix_vexp(vi) - 1017;   // dS/dv = sv 2^(ey + e_i - 2102), |sv| < 2^59
+    const int e1 = ey + fix_vexp(vi) - 1016;   // dS/dv = sv 2^(ey + e_i - 2101), |sv| < 2^58
     if (e1 < 64 || e1 > 2046) return false;
     int64_t ur, ui, sr, si;
     fix_mul(Yr, Yi, C, S, &ur, &ui);
     fix_mul_conj(Ar, Ai, ur, ui, &sr, &si);
-    *yur = fix_to_double(ur, ey + 2);
-    *yui = fix_to_double(ui, ey + 2);
+    *yur = fix_to_double(ur, ey + 3);
+    *yui = fix_to_double(ui, ey + 3);
     *svr = fix_to_double(sr, e1);
     *svi = fix_to_double(si, e1);
     return true;
 }
 
-// Y_ij U_j alone (the injections): yu 2^(ey - 1083) rounded to doubles
+// Y_ij U_j alone (the injections): yu 2^(ey - 1082) rounded to doubles
 __host__ __device__ __forceinline__ void fix_ybus_yu(int64_t Yr, int64_t Yi, int ey, int64_t C, int64_t S,
                                                      double *yur, double *yui)
 {
     int64_t ur, ui;
     fix_mul(Yr, Yi, C, S, &ur, &ui);
-    *yur = fix_to_double(ur, ey + 2);
-    *yui = fix_to_double(ui, ey + 2);
+    *yur = fix_to_double(ur, ey + 3);
+    *yui = fix_to_double(ui, ey + 3);
 }
 
 // G = conj(Yc) E: the fixed-point product where it applies, else E (fixed

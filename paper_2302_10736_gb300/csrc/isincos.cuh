@@ -17,7 +17,8 @@
 //      two bits select the quadrant and its low six bits one of 64 entries
 //      (cos a_j, sin a_j) of the first quadrant, held as 62-bit fractions.
 //   3. Taylor polynomials of sin rho (to rho^7) and 1 - cos rho (to rho^6) in
-//      fixed point; the first omitted terms are below 2e-20.
+//      fixed point; the first omitted terms are below 2e-20; the products
+//      feeding the three smallest terms use 32-bit multiplies.
 //   4. cos(a_j + rho), sin(a_j + rho) by the angle-addition formulas, the
 //      quadrant by swapping and negating, and each result rounded once to the
 //      nearest double (leading-zero count, shift, round half up).
@@ -173,6 +174,14 @@ __host__ __device__ __forceinline__ int clz64(uint64_t u)
 #endif
 }
 
+// a b 2^-64 from the upper 32 bits of a (a < 2^62) and of b 2^-sb (below 2^32):
+// one 32 x 32-bit product, for the polynomial terms that need few bits (the
+// truncations are below 2^-29 of the product)
+__host__ __device__ __forceinline__ uint64_t mulhi_short(uint64_t a, uint64_t b, int sb)
+{
+    return ((uint64_t)(uint32_t)(a >> 32) * (uint64_t)(uint32_t)(b >> sb)) >> (32 - sb);
+}
+
 // v 2^-62 as the nearest double (ties rounded up in magnitude), |v| <= 2^63
 __host__ __device__ __forceinline__ double q62_to_double(int64_t v)
 {
@@ -222,11 +231,13 @@ __host__ __device__ __forceinline__ void int_sincos_fix(double x, const ITrig *t
     const uint64_t X = u64_mulhi(u << 8, kTwoPi61);                // |rho| 2^69
     const uint64_t A = u64_mulhi(X, X);                            // rho^2 2^74
     // |sin rho| = |rho| (1 - rho^2 (1/6 - rho^2 (1/120 - rho^2 / 5040)))
-    const uint64_t p3 = kInv120 - u64_mulhi(A, kInv5040_54);       // 2^64
-    const uint64_t p2 = kInv6 - (u64_mulhi(A, p3) >> 10);          // 2^64
+    // (A < 2^62; the terms rho^7 / 5040, rho^5 / 120 and rho^6 / 720 need 6,
+    // 25 and 16 significant bits of their products: 32-bit products suffice)
+    const uint64_t p3 = kInv120 - mulhi_short(A, kInv5040_54, 10);  // 2^64
+    const uint64_t p2 = kInv6 - (mulhi_short(A, p3, 26) >> 10);     // 2^64
     const uint64_t sr = X - (u64_mulhi(X, u64_mulhi(A, p2)) >> 10);   // |sin rho| 2^69
     // 1 - cos rho = rho^2 (1/2 - rho^2 (1/24 - rho^2 / 720))
-    const uint64_t q2 = kInv24 - u64_mulhi(A, kInv720_54);         // 2^64
+    const uint64_t q2 = kInv24 - mulhi_short(A, kInv720_54, 13);    // 2^64
     const uint64_t q1 = (1ull << 63) - (u64_mulhi(A, q2) >> 10);   // 2^64
     const uint64_t cm = u64_mulhi(A, q1);                          // (1 - cos rho) 2^74
     const ITrig t = tab[k & (kITrigN - 1)];                        // 2^62

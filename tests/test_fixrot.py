@@ -108,13 +108,14 @@ def test_fallback_keeps_ieee_semantics(host):
 
 
 def test_coupling_product_against_50_digit_reference(host):
-    """G = conj(Yc) E with Yc in block floating point: |G - G_ref| <= 1.6 *
-    2^-53 |Yc| |v_o| per component (fixed-point truncations below 2^-53 |G|,
-    plus one rounding); Yc of every magnitude, one component zero or tiny."""
+    """G = conj(Yc) E with Yc in block floating point: |G - G_ref| <= 2.25 *
+    2^-53 |Yc| |v_o| per component (fixed-point truncations below about 2^-53
+    |G|, plus one rounding of at most 2^-53 |G|); Yc of every magnitude, one
+    component zero or tiny."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 50
     rng = np.random.default_rng(7)
-    n = 3000
+    n = 6000
     vo = np.concatenate([rng.uniform(0.9, 1.1, n), 10.0 ** rng.uniform(-200, 200, n)])
     tho = np.concatenate([rng.normal(0, 0.3, n), rng.uniform(-6e4, 6e4, n)])
     thq = np.concatenate([tho[:n] + rng.normal(0, 0.05, n), rng.uniform(-6e4, 6e4, n)])
@@ -129,7 +130,7 @@ def test_coupling_product_against_50_digit_reference(host):
         er, ei = mp.mpf(vo[k]) * mp.cos(d), mp.mpf(vo[k]) * mp.sin(d)
         gr = mp.mpf(yr[k]) * er + mp.mpf(yi[k]) * ei   # conj(Yc) E
         gi = mp.mpf(yr[k]) * ei - mp.mpf(yi[k]) * er
-        bound = 1.6 * EPS * float(abs(vo[k]) * mp.sqrt(mp.mpf(yr[k]) ** 2 + mp.mpf(yi[k]) ** 2))
+        bound = 2.25 * EPS * float(abs(vo[k]) * mp.sqrt(mp.mpf(yr[k]) ** 2 + mp.mpf(yi[k]) ** 2))
         assert abs(float(mp.mpf(r[k, 0]) - gr)) <= bound, k
         assert abs(float(mp.mpf(r[k, 1]) - gi)) <= bound, k
 
