@@ -599,11 +599,14 @@ pf_status jac_target(pf_grid *grid, int32_t method, const double *vm, const doub
  * side, dx [n] receives the solution (device pointers).  Sparse LU without
  * pivoting on a fill-reducing order: the first call after grid_set_bus_types
  * analyses the pattern on the host (minimum-degree order of the buses,
- * symbolic factorization, level schedule), allocates the factor storage and
- * synchronizes; make it before any stream capture.  Every later call is one
- * cooperative launch: numeric factorization with the forward solve, then the
- * backward solve, bitwise repeatable.  A zero or non-finite pivot sets the
- * grid's device error word (grid_check_error reports PF_EDEVICE); no pivoting
+ * symbolic factorization, the dependency schedule of the elimination tree),
+ * allocates the factor storage and synchronizes; make it before any stream
+ * capture.  Every later call is one cooperative launch: numeric factorization
+ * with the forward solve, then the backward solve, each column started when the
+ * columns it depends on are done (bounded waits), bitwise repeatable.  A zero
+ * or non-finite pivot sets the grid's device error word (grid_check_error
+ * reports PF_EDEVICE), a wait that runs out (2 s) sets it to a time-out
+ * (grid_check_error reports PF_ETIMEOUT and clears it); no pivoting
  * means the matrix must admit LU in that order, which the power-flow Jacobians
  * of this library's grids do (their 2 x 2 bus blocks dominate).
  */
