@@ -54,7 +54,7 @@ YB_OPS_PER_NNZ = 16
 YB_OPS_PER_ROW = 16
 # DRAM bytes of one k_ew<1> launch on the 70k-bus grid (dram__bytes_read.sum + dram__bytes_write.sum
 # of an ncu capture of that launch); None whenever the kernel changes, until it is captured again
-EW_TRAFFIC_BYTES = None
+EW_TRAFFIC_BYTES = 9941504
 
 
 def parse_args(argv=None):
