@@ -33,14 +33,19 @@
 // rather than level by level.  Work items are in level order and the warps
 // take them in that order from a shared counter, so the lowest unfinished item
 // has a warp and its inputs, and can always run (all CTAs are resident:
-// cooperative launch).  Wide levels give a warp to a
-// column (a lane per slot); on the narrow top of the tree every slot of a
-// column gets a warp of its own (its lanes splitting the slot's sum; each warp
-// forms its column's pivot itself, the same way); the backward solve gives a
-// warp to a column, which waits for its parent.  Every gather issues four loads
-// per lane before using them.  Every sum has a fixed order (sequential, or
-// lane-strided partial sums joined by a fixed shuffle tree): the results are
-// bitwise repeatable.  Values written by other CTAs are read with
+// cooperative launch).  Wide levels give a warp to a column (a lane per
+// slot); on the upper levels (those with no more slots than the launch has
+// warps) every slot of a column gets a warp of its own (its lanes splitting
+// the slot's sum; each warp forms its column's pivot itself, the same way);
+// the backward solve gives a warp to a column,
+// which waits for its own factorization and then for its parent.  What an
+// item needs that no other item writes - its index lists and its own slots'
+// values of A and F - is loaded before its wait, and after the wait all its
+// loads of other columns' factor values are in flight at once (four terms per
+// lane), so a level of the tree costs one round trip to L2 for the values,
+// one for the release of the results and one for the next item's acquire.
+// Every sum has a fixed order (sequential, or lane-strided partial sums
+// joined by a fixed shuffle tree): the results are bitwise repeatable.  Values written by other CTAs are read with
 // L1-bypassing loads after an acquire load of the counter that announced them.
 // A zero or non-finite pivot sets the grid's error word (no trap); a wait that
 // runs out (2 s) sets it to a time-out and ends the warp.
@@ -57,8 +62,7 @@ namespace pf {
 namespace {
 
 constexpr uint64_t kLuBarrierNs = 2000000000ull;   // bounded grid-barrier wait (2 s)
-constexpr int kLuThreads = 512;
-constexpr int kLuChainCols = 4;   // levels at most this wide at the top: one work item per slot
+constexpr int kLuThreads = 384;
 
 struct LuArgs {
     int n, nnzA, nfitems;
@@ -139,47 +143,106 @@ __device__ __forceinline__ void pivot_check(const LuArgs &a, double d)
     if (!(fabs(d) > 0.0) || !isfinite(d)) atomicExch(a.err, DEV_SINGULAR);
 }
 
-// sum over g in [g0, g1) of Lx[src[g].x] Ux[src[g].y] (and, with `mirror`,
-// of Lx[src[g].y] Ux[src[g].x]) by the lanes of a warp, lane-strided, four
-// terms in flight per lane, joined by a fixed shuffle tree (all lanes get it)
-__device__ __forceinline__ double2 warp_dot_pairs(const LuArgs &a, int g0, int g1, int lane)
+// The static part of a work item - index lists fixed by the analysis, and the
+// values of A and F in the item's own slots, which no other item writes - is
+// loaded before the item's wait, so that after it only the factor values of
+// its descendants remain to be read (one round trip instead of three).
+
+// row j's (slot, column) pairs, the first 128 (four per lane, lane-strided)
+struct LuRow {
+    int r, r1;   // the next entry after the loaded ones, the row's end
+    int q[4], k[4];
+};
+
+__device__ __forceinline__ void lu_row_load(const LuArgs &a, int j, int lane, LuRow &w)
 {
-    double sl = 0.0, su = 0.0;
-    for (int g = g0 + lane; g < g1; g += 128) {
-        int2 t[4];
+    const int r0 = a.Rp[j] + lane;
+    w.r1 = a.Rp[j + 1];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) t[u] = g + 32 * u < g1 ? a.gsrc[g + 32 * u] : make_int2(-1, -1);
-        double lx[4], uy[4], ly[4], ux[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (t[u].x >= 0) {
-                lx[u] = ldcg(a.Lx + t[u].x);
-                uy[u] = ldcg(a.Ux + t[u].y);
-                ly[u] = ldcg(a.Lx + t[u].y);
-                ux[u] = ldcg(a.Ux + t[u].x);
-            }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (t[u].x >= 0) {
-                sl = fma(lx[u], uy[u], sl);
-                su = fma(ly[u], ux[u], su);
-            }
+    for (int u = 0; u < 4; ++u) {
+        const int r = r0 + 32 * u;
+        w.q[u] = r < w.r1 ? a.Rq[r] : -1;
+        w.k[u] = r < w.r1 ? a.Rk[r] : 0;
     }
-    return make_double2(warp_sum_d(sl), warp_sum_d(su));
+    w.r = r0 + 128;
 }
 
-// the pivot sum sum_k L(j, k) U(k, j) and the forward term sum_k L(j, k) y_k of
-// column j by a warp (the same lane order as warp_dot_pairs)
-__device__ __forceinline__ double2 warp_pivot_terms(const LuArgs &a, int j, int lane)
+// a slot's update pairs {L(i, k) slot, U(k, j) slot}, the first four of the
+// lane's share: lane-strided (`stride` 32, a warp per slot) or consecutive
+// (`stride` 1, a lane per slot)
+struct LuSlot {
+    int g, g1;
+    int2 s[4];
+};
+
+__device__ __forceinline__ void lu_slot_load(const LuArgs &a, int p, int g0, int stride, LuSlot &w)
+{
+    w.g1 = a.gptr[p + 1];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int g = g0 + stride * u;
+        w.s[u] = g < w.g1 ? a.gsrc[g] : make_int2(-1, -1);
+    }
+    w.g = g0 + 4 * stride;
+}
+
+// the values of the loaded pairs (after the wait)
+struct LuRowVal {
+    double l[4], uu[4], yk[4];
+};
+struct LuSlotVal {
+    double lx[4], uy[4], ly[4], ux[4];
+};
+
+// (a term the lane does not have reads as 0 x 0, which leaves a sum unchanged
+// but for the sign of a zero; the indices are not needed after the loads)
+__device__ __forceinline__ void lu_row_fetch(const LuArgs &a, const LuRow &w, bool fwd, LuRowVal &v)
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const bool h = w.q[u] >= 0;
+        v.l[u] = h ? ldcg(a.Lx + w.q[u]) : 0.0;
+        v.uu[u] = h ? ldcg(a.Ux + w.q[u]) : 0.0;
+        v.yk[u] = h && fwd ? ldcg(a.y + w.k[u]) : 0.0;
+    }
+}
+
+__device__ __forceinline__ void lu_slot_fetch(const LuArgs &a, const LuSlot &w, LuSlotVal &v)
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const bool h = w.s[u].x >= 0;
+        v.lx[u] = h ? ldcg(a.Lx + w.s[u].x) : 0.0;
+        v.uy[u] = h ? ldcg(a.Ux + w.s[u].y) : 0.0;
+        v.ly[u] = h ? ldcg(a.Lx + w.s[u].y) : 0.0;
+        v.ux[u] = h ? ldcg(a.Ux + w.s[u].x) : 0.0;
+    }
+}
+
+// the lane's part of sum_k L(j, k) U(k, j) and sum_k L(j, k) y_k: the fetched
+// four (first), then the rest of its share of row j, four in flight (rest);
+// lane-strided, so every lane adds its terms in ascending order
+__device__ __forceinline__ double2 lu_row_first(const LuRowVal &v)
 {
     double dd = 0.0, yy = 0.0;
-    const int r1 = a.Rp[j + 1];
-    for (int r = a.Rp[j] + lane; r < r1; r += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        dd = fma(v.l[u], v.uu[u], dd);
+        yy = fma(v.l[u], v.yk[u], yy);
+    }
+    return make_double2(dd, yy);
+}
+
+__device__ __forceinline__ double2 lu_row_rest(const LuArgs &a, const LuRow &w, double2 t)
+{
+    double dd = t.x, yy = t.y;
+    #pragma unroll 1
+    for (int r = w.r; r < w.r1; r += 128) {
         int q[4], k[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            q[u] = r + 32 * u < r1 ? a.Rq[r + 32 * u] : -1;
-            k[u] = r + 32 * u < r1 ? a.Rk[r + 32 * u] : 0;
+            q[u] = r + 32 * u < w.r1 ? a.Rq[r + 32 * u] : -1;
+            k[u] = r + 32 * u < w.r1 ? a.Rk[r + 32 * u] : 0;
         }
         double l[4], uu[4], yk[4];
 #pragma unroll
@@ -196,82 +259,170 @@ __device__ __forceinline__ double2 warp_pivot_terms(const LuArgs &a, int j, int 
                 yy = fma(l[u], yk[u], yy);
             }
     }
-    return make_double2(warp_sum_d(dd), warp_sum_d(yy));
+    return make_double2(dd, yy);
 }
 
-// One column by one warp (wide levels): its pivot, then a lane per slot, the
-// slot's update terms in order, four in flight.
-__device__ __forceinline__ void lu_column_warp(const LuArgs &a, int j, int lane)
+// sl - sum L(i, k) U(k, j) and su - sum L(j, k) U(k, i) over the lane's share
+// of a slot's pairs: the fetched four (first), then the rest (`stride` as
+// loaded), four in flight, in ascending order (rest)
+__device__ __forceinline__ double2 lu_slot_first(const LuSlotVal &v, double sl, double su)
 {
-    const double2 t = warp_pivot_terms(a, j, lane);
-    const double d = ldcg(a.D + j) - t.x, yj = ldcg(a.y + j) - t.y;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        sl = fma(-v.lx[u], v.uy[u], sl);
+        su = fma(-v.ly[u], v.ux[u], su);
+    }
+    return make_double2(sl, su);
+}
+
+__device__ __forceinline__ double2 lu_slot_rest(const LuArgs &a, const LuSlot &w, int stride, double2 t)
+{
+    double sl = t.x, su = t.y;
+    #pragma unroll 1
+    for (int g = w.g; g < w.g1; g += 4 * stride) {
+        int2 s4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s4[u] = g + stride * u < w.g1 ? a.gsrc[g + stride * u] : make_int2(-1, -1);
+        double lx[4], uy[4], ly[4], ux[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (s4[u].x >= 0) {
+                lx[u] = ldcg(a.Lx + s4[u].x);
+                uy[u] = ldcg(a.Ux + s4[u].y);
+                ly[u] = ldcg(a.Lx + s4[u].y);
+                ux[u] = ldcg(a.Ux + s4[u].x);
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (s4[u].x >= 0) {
+                sl = fma(-lx[u], uy[u], sl);
+                su = fma(-ly[u], ux[u], su);
+            }
+    }
+    return make_double2(sl, su);
+}
+
+// A factorization item's static part: its row (the pivot and forward terms),
+// and either the lane's first slot of column j (a warp per column: p0 = -2)
+// or the slot's first pairs (a warp per slot p0 = p >= 0; -1: no slot), with
+// A(j, j), F_j's place in y and the slot's values of A
+struct LuItem {
+    LuRow row;
+    LuSlot slot;
+    int j, p, pfirst, pend;   // column; the lane's (column warp) or the item's slot (-1: none); column j's slots
+    bool colwarp;
+    double d0, y0, l0, u0;    // A(j, j), y_j before the update, the slot's A values (the lane sums' start)
+};
+
+__device__ __forceinline__ void lu_item_load(const LuArgs &a, int j, int p0, int lane, LuItem &it)
+{
+    it.j = j;
+    it.colwarp = p0 == -2;
+    lu_row_load(a, j, lane, it.row);
+    it.pfirst = a.Lp[j];
+    it.pend = a.Lp[j + 1];
+    it.d0 = ldcg(a.D + j);
+    it.y0 = ldcg(a.y + j);
+    it.p = it.colwarp ? (it.pfirst + lane < it.pend ? it.pfirst + lane : -1) : p0;
+    it.l0 = it.u0 = 0.0;
+    it.slot.g = it.slot.g1 = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) it.slot.s[u] = make_int2(-1, -1);
+    if (it.p >= 0) {
+        const int g0 = a.gptr[it.p];
+        lu_slot_load(a, it.p, it.colwarp ? g0 : g0 + lane, it.colwarp ? 1 : 32, it.slot);
+        it.l0 = ldcg(a.Lx + it.p);
+        it.u0 = ldcg(a.Ux + it.p);
+    }
+}
+
+// One factorization item by one warp, after its wait.  A whole column (wide
+// levels, `it.colwarp`): its pivot, then a lane per slot, each slot's update
+// terms in order, four in flight.  One slot of a narrow level's column (p < 0:
+// the column has no slot below the diagonal): the lanes split the slot's
+// terms; every item of a column forms its pivot the same way, and the
+// column's first item also writes the pivot and y_j.
+__device__ __forceinline__ void lu_factor(const LuArgs &a, const LuItem &it, int lane)
+{
+    // y_j is formed by a column warp and by a column's first item only
+    const bool fwd = it.colwarp || it.p < 0 || it.p == it.pfirst;
+    LuRowVal rv;
+    LuSlotVal sv;
+    lu_row_fetch(a, it.row, fwd, rv);
+    lu_slot_fetch(a, it.slot, sv);
+    double2 t = lu_row_first(rv);
+    // a lane's own slot (column warp) starts from A's values, the lane sums of
+    // a warp's slot from 0
+    double2 s = lu_slot_first(sv, it.colwarp ? it.l0 : 0.0, it.colwarp ? it.u0 : 0.0);
+    t = lu_row_rest(a, it.row, t);
+    s = lu_slot_rest(a, it.slot, it.colwarp ? 1 : 32, s);
+    const double d = it.d0 - warp_sum_d(t.x), yj = it.y0 - warp_sum_d(t.y);
     const double inv = fast_rcp(d);
-    for (int p = a.Lp[j] + lane; p < a.Lp[j + 1]; p += 32) {
-        double sl = ldcg(a.Lx + p), su = ldcg(a.Ux + p);
-        const int g1 = a.gptr[p + 1];
-        for (int g = a.gptr[p]; g < g1; g += 4) {
-            int2 s4[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) s4[u] = g + u < g1 ? a.gsrc[g + u] : make_int2(-1, -1);
-            double lx[4], uy[4], ly[4], ux[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (s4[u].x >= 0) {
-                    lx[u] = ldcg(a.Lx + s4[u].x);
-                    uy[u] = ldcg(a.Ux + s4[u].y);
-                    ly[u] = ldcg(a.Lx + s4[u].y);
-                    ux[u] = ldcg(a.Ux + s4[u].x);
-                }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (s4[u].x >= 0) {
-                    sl = fma(-lx[u], uy[u], sl);
-                    su = fma(-ly[u], ux[u], su);
-                }
+    if (it.colwarp) {
+        if (it.p >= 0) {
+            a.Lx[it.p] = s.x * inv;
+            a.Ux[it.p] = s.y;
+            // slots beyond the warp's first 32
+#pragma unroll 1
+            for (int p = it.p + 32; p < it.pend; p += 32) {
+                LuSlot w;
+                w.g = a.gptr[p];
+                w.g1 = a.gptr[p + 1];
+                const double2 s2 = lu_slot_rest(a, w, 1, make_double2(ldcg(a.Lx + p), ldcg(a.Ux + p)));
+                a.Lx[p] = s2.x * inv;
+                a.Ux[p] = s2.y;
+            }
         }
-        a.Lx[p] = sl * inv;
-        a.Ux[p] = su;
-    }
-    if (lane == 0) {
-        pivot_check(a, d);
-        a.piv[j] = d;
-        a.y[j] = yj;
-    }
-}
-
-// One item of a narrow level (a warp): slot p of column j (p < 0: the column
-// has no slot below the diagonal); every item of a column forms its pivot the
-// same way, the column's first item also writes the pivot and y_j.
-__device__ __forceinline__ void lu_item(const LuArgs &a, int j, int p, int lane)
-{
-    const double2 t = warp_pivot_terms(a, j, lane);
-    const double d = ldcg(a.D + j) - t.x;
-    if (p >= 0) {
-        const double2 s = warp_dot_pairs(a, a.gptr[p], a.gptr[p + 1], lane);
+    } else if (it.p >= 0) {
+        // the lane sums were formed as 0 - terms: their warp sum is minus the
+        // slot's sum
+        const double sx = warp_sum_d(s.x), sy = warp_sum_d(s.y);
         if (lane == 0) {
-            a.Lx[p] = (ldcg(a.Lx + p) - s.x) * fast_rcp(d);
-            a.Ux[p] = ldcg(a.Ux + p) - s.y;
+            a.Lx[it.p] = (it.l0 + sx) * inv;
+            a.Ux[it.p] = it.u0 + sy;
         }
     }
-    if (lane == 0 && (p < 0 || p == a.Lp[j])) {
+    if (lane == 0 && fwd) {
         pivot_check(a, d);
-        a.piv[j] = d;
-        a.y[j] = ldcg(a.y + j) - t.y;
+        a.piv[it.j] = d;
+        a.y[it.j] = yj;
     }
 }
 
-// x_j of the backward solve, in place of y_j (one warp)
-__device__ __forceinline__ void lu_back(const LuArgs &a, int j, int lane)
+// x_j of the backward solve, in place of y_j (one warp): the column's rows are
+// loaded before any wait, its U values, y_j and pivot once its own
+// factorization is finished, the x of its rows (its ancestors) once its
+// parent's x is written; false on a time-out (all lanes agree)
+__device__ __forceinline__ bool lu_back(const LuArgs &a, int j, int lane)
 {
-    const int p0 = a.Lp[j], p1 = a.Lp[j + 1];
+    const int p0 = a.Lp[j] + lane, p1 = a.Lp[j + 1], pj = a.parent[j], need = a.need[j], pm = a.perm[j];
+    int li[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) li[u] = p0 + 32 * u < p1 ? a.Li[p0 + 32 * u] : -1;
+    if (!__all_sync(0xffffffffu, lu_wait(a, a.done + j, need))) return false;
+    __syncwarp();
+    double ux[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (li[u] >= 0) ux[u] = ldcg(a.Ux + p0 + 32 * u);
+    const double yj = ldcg(a.y + j), pv = ldcg(a.piv + j);
+    if (pj >= 0) {
+        if (!__all_sync(0xffffffffu, lu_wait(a, a.done + a.n + pj, 1))) return false;
+        __syncwarp();
+    }
     double s = 0.0;
-    for (int p = p0 + lane; p < p1; p += 32) s = fma(ldcg(a.Ux + p), ldcg(a.y + a.Li[p]), s);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (li[u] >= 0) s = fma(ux[u], ldcg(a.y + li[u]), s);
+    #pragma unroll 1
+    for (int p = p0 + 128; p < p1; p += 32) s = fma(ldcg(a.Ux + p), ldcg(a.y + a.Li[p]), s);
     s = warp_sum_d(s);
     if (lane == 0) {
-        const double x = (ldcg(a.y + j) - s) * fast_rcp(ldcg(a.piv + j));
+        const double x = (yj - s) * fast_rcp(pv);
         a.y[j] = x;
-        a.dx[a.perm[j]] = x;
+        a.dx[pm] = x;
     }
+    return true;
 }
 
 __global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
@@ -316,19 +467,15 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= nall) break;
         if (t < a.nfitems) {   // once the column's children are finished
-            const int2 it = a.fitems[t];
-            if (!lu_wait_children(a, it.x, lane)) return;
-            if (it.y == -2)
-                lu_column_warp(a, it.x, lane);
-            else
-                lu_item(a, it.x, it.y, lane);
-            lu_finish(a, a.done + it.x, lane);
-        } else {   // x_j once its parent's is written (the root's once its own factorization is finished)
-            const int j = a.bcols[t - a.nfitems], pj = a.parent[j];
-            const bool ok = pj >= 0 ? lu_wait(a, a.done + a.n + pj, 1) : lu_wait(a, a.done + j, a.need[j]);
-            if (!__all_sync(0xffffffffu, ok)) return;
-            __syncwarp();
-            lu_back(a, j, lane);
+            const int2 fi = a.fitems[t];
+            LuItem it;
+            lu_item_load(a, fi.x, fi.y, lane, it);
+            if (!lu_wait_children(a, fi.x, lane)) return;
+            lu_factor(a, it, lane);
+            lu_finish(a, a.done + fi.x, lane);
+        } else {   // x_j once its own factorization is finished and its parent's x is written
+            const int j = a.bcols[t - a.nfitems];
+            if (!lu_back(a, j, lane)) return;
             lu_finish(a, a.done + a.n + j, lane);
         }
     }
@@ -371,7 +518,7 @@ std::vector<int> min_degree_order(std::vector<std::vector<int>> adj)
 }  // namespace
 
 pf_status host_lu(int nb, int n, int npvpq, const std::vector<int> &colptr, const std::vector<int> &rowidx,
-                  const std::vector<int> &fmap, HostLu &L)
+                  const std::vector<int> &fmap, int slot_warps, HostLu &L)
 {
     L = HostLu{};
     L.n = n;
@@ -492,11 +639,26 @@ pf_status host_lu(int nb, int n, int npvpq, const std::vector<int> &colptr, cons
     L.lvl_col.assign(n, 0);
     std::vector<int> lf(L.lvl_ptr.begin(), L.lvl_ptr.end() - 1);
     for (int j = 0; j < n; ++j) L.lvl_col[lf[height[j]]++] = j;
-    // levels at most kLuChainCols wide from the top down: every slot of their
-    // columns is a work item of its own (a column without slots below the
-    // diagonal still needs its pivot: slot -1); below them a column is one item
+    // From the top down, every level whose columns have at most as many slots
+    // as the launch has warps (the widest level's width, or the warps of one
+    // CTA per SM if fewer): every slot of its columns is a work item of its own
+    // (a column without slots below the diagonal still needs its pivot: slot
+    // -1), whose lanes split the slot's update terms, so that a slot costs one
+    // round of loads however many terms it has; below them (wide levels of
+    // short columns) a column is one item, a lane per slot.
+    int widest = 1;
+    for (int h = 0; h < L.H; ++h) widest = std::max(widest, L.lvl_ptr[h + 1] - L.lvl_ptr[h]);
+    const long long budget = std::min<long long>(widest, (long long)slot_warps);
+    auto level_items = [&](int h) {
+        long long c = 0;
+        for (int t = L.lvl_ptr[h]; t < L.lvl_ptr[h + 1]; ++t) {
+            const int j = L.lvl_col[t];
+            c += std::max(1, L.Lp[j + 1] - L.Lp[j]);
+        }
+        return c;
+    };
     L.chain = L.H;
-    while (L.chain > 0 && L.lvl_ptr[L.chain] - L.lvl_ptr[L.chain - 1] <= kLuChainCols) --L.chain;
+    while (L.chain > 0 && level_items(L.chain - 1) <= budget) --L.chain;
     L.need.assign(n, 0);
     for (int h = 0; h < L.H; ++h)
         for (int t = L.lvl_ptr[h]; t < L.lvl_ptr[h + 1]; ++t) {
@@ -547,7 +709,12 @@ pf_status lu_prepare(Grid *g, cudaStream_t s)
 {
     if (g->lu_ready) return PF_OK;
     HostLu L;
-    if (pf_status st = host_lu(g->nb, g->red_n, g->red_npvpq, g->red_h_colptr, g->red_h_rowidx, g->red_h_fmap, L))
+    // the warps of one CTA per SM: an upper bound of the launch's warps
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cuda_error(cudaGetLastError(), "jac_reduced_solve: device attributes");
+    if (pf_status st = host_lu(g->nb, g->red_n, g->red_npvpq, g->red_h_colptr, g->red_h_rowidx, g->red_h_fmap,
+                               std::max(1, nsm) * (kLuThreads / 32), L))
         return st;
     const size_t nnzL = (size_t)L.Lp[L.n];
     auto up = [&](int **dst, const std::vector<int> &v) -> cudaError_t {

@@ -408,7 +408,7 @@ struct HostLu {
     std::vector<int> need, cptr, cidx, parent, bcols;
 };
 pf_status host_lu(int nb, int n, int npvpq, const std::vector<int> &colptr, const std::vector<int> &rowidx,
-                  const std::vector<int> &fmap, HostLu &L);
+                  const std::vector<int> &fmap, int slot_warps, HostLu &L);
 pf_status lu_prepare(Grid *g, cudaStream_t s);
 void lu_release(Grid *g);
 cudaError_t launch_lu_solve(Grid *g, const double *Jr, const double *F, double *dx, cudaStream_t s);
