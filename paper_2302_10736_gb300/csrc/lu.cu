@@ -53,6 +53,8 @@
 #include <set>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "fastmath.cuh"
 #include "pf_internal.h"
 #include "ptx.cuh"
@@ -63,9 +65,19 @@ namespace {
 
 constexpr uint64_t kLuBarrierNs = 2000000000ull;   // bounded grid-barrier wait (2 s)
 constexpr int kLuThreads = 384;
+// the tail: the top of the elimination tree factored as a dense block by one
+// thread-block cluster (shared memory spread over its CTAs)
+constexpr int kLuTailCtas = 8;
+constexpr int kLuTailThreads = 512;
+constexpr int kLuTailMax = 384;   // columns: 48 rows of 384 doubles per CTA
+constexpr int kLuTailMin = 16;    // a shorter top chain stays in the dynamic schedule
+constexpr int kLuTailWidth = 2;   // the tail holds columns of levels at most this wide
 
 struct LuArgs {
-    int n, nnzA, nfitems;
+    int n, nnzA, nfitems, nbcols;
+    int T0, LpT0;   // the tail's first column and first factor slot (n, nnz(L): no tail)
+    int fr0, fr1;   // the tail's frontier in cidx: the columns outside it whose parent is in it
+    int mode;       // 0 the whole solve; 1 zero, scatter, factorization (the tail's outside terms only); 2 the backward solve outside the tail
     const int *Lp, *Li, *Rp, *Rk, *Rq, *perm, *amap, *gptr;
     const int *need, *cptr, *cidx, *parent, *bcols;
     const int2 *gsrc;     // per update term of a slot: {L(i, k) slot, U(k, j) slot}
@@ -73,7 +85,7 @@ struct LuArgs {
     const double *A, *F;
     double *Lx, *Ux, *D, *y, *dx;
     double *piv;          // [n] the pivots U(j, j) (D keeps A(j, j): every item of a column reads it)
-    int *done;            // [2n + 1]: finished items of column j at j, x_j written at n + j, the item counter
+    int *done;            // [2n + 2]: finished items of column j at j, x_j written at n + j, the item counters
     unsigned int *bar;
     int *err;
 };
@@ -113,7 +125,10 @@ __device__ __forceinline__ bool lu_wait(const LuArgs &a, const int *p, int targe
 __device__ __forceinline__ bool lu_wait_children(const LuArgs &a, int j, int lane)
 {
     bool ok = true;
-    for (int t = a.cptr[j] + lane; t < a.cptr[j + 1]; t += 32) {
+    // a column of the tail reads the outside columns of its whole subtree: it
+    // waits for the tail's frontier
+    const int c0 = j >= a.T0 ? a.fr0 : a.cptr[j], c1 = j >= a.T0 ? a.fr1 : a.cptr[j + 1];
+    for (int t = c0 + lane; t < c1; t += 32) {
         const int c = a.cidx[t];
         ok = ok && lu_wait(a, a.done + c, a.need[c]);
     }
@@ -161,8 +176,8 @@ __device__ __forceinline__ void lu_row_load(const LuArgs &a, int j, int lane, Lu
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int r = r0 + 32 * u;
-        w.q[u] = r < w.r1 ? a.Rq[r] : -1;
         w.k[u] = r < w.r1 ? a.Rk[r] : 0;
+        w.q[u] = r < w.r1 && w.k[u] < a.T0 ? a.Rq[r] : -1;   // k in the tail: the dense phase's term
     }
     w.r = r0 + 128;
 }
@@ -182,6 +197,7 @@ __device__ __forceinline__ void lu_slot_load(const LuArgs &a, int p, int g0, int
     for (int u = 0; u < 4; ++u) {
         const int g = g0 + stride * u;
         w.s[u] = g < w.g1 ? a.gsrc[g] : make_int2(-1, -1);
+        if (w.s[u].y >= a.LpT0) w.s[u] = make_int2(-1, -1);   // k in the tail: the dense phase's term
     }
     w.g = g0 + 4 * stride;
 }
@@ -241,8 +257,8 @@ __device__ __forceinline__ double2 lu_row_rest(const LuArgs &a, const LuRow &w, 
         int q[4], k[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            q[u] = r + 32 * u < w.r1 ? a.Rq[r + 32 * u] : -1;
             k[u] = r + 32 * u < w.r1 ? a.Rk[r + 32 * u] : 0;
+            q[u] = r + 32 * u < w.r1 && k[u] < a.T0 ? a.Rq[r + 32 * u] : -1;
         }
         double l[4], uu[4], yk[4];
 #pragma unroll
@@ -282,7 +298,10 @@ __device__ __forceinline__ double2 lu_slot_rest(const LuArgs &a, const LuSlot &w
     for (int g = w.g; g < w.g1; g += 4 * stride) {
         int2 s4[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s4[u] = g + stride * u < w.g1 ? a.gsrc[g + stride * u] : make_int2(-1, -1);
+        for (int u = 0; u < 4; ++u) {
+            s4[u] = g + stride * u < w.g1 ? a.gsrc[g + stride * u] : make_int2(-1, -1);
+            if (s4[u].y >= a.LpT0) s4[u] = make_int2(-1, -1);
+        }
         double lx[4], uy[4], ly[4], ux[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -341,9 +360,12 @@ __device__ __forceinline__ void lu_item_load(const LuArgs &a, int j, int p0, int
 // terms in order, four in flight.  One slot of a narrow level's column (p < 0:
 // the column has no slot below the diagonal): the lanes split the slot's
 // terms; every item of a column forms its pivot the same way, and the
-// column's first item also writes the pivot and y_j.
+// column's first item also writes the pivot and y_j.  A column of the tail
+// (j >= T0) takes only the terms of columns outside it and keeps its
+// numerators, pivot and y_j unfinished for the dense phase.
 __device__ __forceinline__ void lu_factor(const LuArgs &a, const LuItem &it, int lane)
 {
+    const bool tail = it.j >= a.T0;
     // y_j is formed by a column warp and by a column's first item only
     const bool fwd = it.colwarp || it.p < 0 || it.p == it.pfirst;
     LuRowVal rv;
@@ -378,12 +400,12 @@ __device__ __forceinline__ void lu_factor(const LuArgs &a, const LuItem &it, int
         // slot's sum
         const double sx = warp_sum_d(s.x), sy = warp_sum_d(s.y);
         if (lane == 0) {
-            a.Lx[it.p] = (it.l0 + sx) * inv;
+            a.Lx[it.p] = tail ? it.l0 + sx : (it.l0 + sx) * inv;
             a.Ux[it.p] = it.u0 + sy;
         }
     }
     if (lane == 0 && fwd) {
-        pivot_check(a, d);
+        if (!tail) pivot_check(a, d);
         a.piv[it.j] = d;
         a.y[it.j] = yj;
     }
@@ -427,46 +449,49 @@ __device__ __forceinline__ bool lu_back(const LuArgs &a, int j, int lane)
 
 __global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
 {
-    const GridBar gbar = grid_barrier_begin(a.bar);
+    const GridBar gbar = a.mode != 2 ? grid_barrier_begin(a.bar) : GridBar{nullptr, 0u};
     const int lane = threadIdx.x & 31;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
     const int gwarp = (int)(gtid >> 5), gwarps = (int)(gthreads >> 5);
     const int nnzL = a.Lp[a.n];
     unsigned int bk = 0;
-    // ---- the factor storage and the counters zeroed, then A and the
-    // right-hand side scattered in ----
-    for (long long t = gtid; t < nnzL; t += gthreads) {
-        a.Lx[t] = 0.0;
-        a.Ux[t] = 0.0;
+    if (a.mode != 2) {
+        // ---- the factor storage and the counters zeroed, then A and the
+        // right-hand side scattered in ----
+        for (long long t = gtid; t < nnzL; t += gthreads) {
+            a.Lx[t] = 0.0;
+            a.Ux[t] = 0.0;
+        }
+        for (long long t = gtid; t < 2LL * a.n + 2; t += gthreads) a.done[t] = 0;   // and the item counters
+        if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
+        for (long long e = gtid; e < a.nnzA; e += gthreads) {
+            const int code = a.amap[e], slot = code >> 2;
+            const double v = a.A[e];
+            if ((code & 3) == 0)
+                a.Lx[slot] = v;
+            else if ((code & 3) == 1)
+                a.Ux[slot] = v;
+            else
+                a.D[slot] = v;
+        }
+        for (long long j = gtid; j < a.n; j += gthreads) a.y[j] = a.F[a.perm[j]];
+        if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
     }
-    for (long long t = gtid; t < 2LL * a.n + 1; t += gthreads) a.done[t] = 0;   // and the item counter
-    if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
-    for (long long e = gtid; e < a.nnzA; e += gthreads) {
-        const int code = a.amap[e], slot = code >> 2;
-        const double v = a.A[e];
-        if ((code & 3) == 0)
-            a.Lx[slot] = v;
-        else if ((code & 3) == 1)
-            a.Ux[slot] = v;
-        else
-            a.D[slot] = v;
-    }
-    for (long long j = gtid; j < a.n; j += gthreads) a.y[j] = a.F[a.perm[j]];
-    if (!grid_barrier(gbar, a.bar, gridDim.x, bk++, a.err, DEV_TIMEOUT, kLuBarrierNs)) return;
     // ---- every warp takes the next item (factorization and forward solve in
     // level order, then the backward solve from the root down) from a shared
     // counter, waits for what the item depends on, and runs it ----
     (void)gwarp;
     (void)gwarps;
-    int *next = a.done + 2LL * a.n;
-    const int nall = a.nfitems + a.n;
+    int *next = a.done + 2LL * a.n + (a.mode == 2 ? 1 : 0);
+    const int nf = a.mode == 2 ? 0 : a.nfitems;
+    const int nall = nf + (a.mode == 1 ? 0 : a.nbcols);
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(next, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= nall) break;
-        if (t < a.nfitems) {   // once the column's children are finished
+        if (t < nf) {   // once the column's children are finished
             const int2 fi = a.fitems[t];
             LuItem it;
             lu_item_load(a, fi.x, fi.y, lane, it);
@@ -474,11 +499,109 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
             lu_factor(a, it, lane);
             lu_finish(a, a.done + fi.x, lane);
         } else {   // x_j once its own factorization is finished and its parent's x is written
-            const int j = a.bcols[t - a.nfitems];
+            const int j = a.bcols[t - nf];
             if (!lu_back(a, j, lane)) return;
             lu_finish(a, a.done + a.n + j, lane);
         }
     }
+}
+
+// The tail (columns T0 .. n-1, the top of the elimination tree, where the
+// dynamic schedule would pay a chain of L2 round trips per column) as a dense
+// block of m = n - T0 rows and columns, by one cluster of kLuTailCtas CTAs:
+// row i of the block lives in the shared memory of CTA i mod C (row-cyclic,
+// so every step's rows are spread over all CTAs), and the CTAs read the
+// current pivot row and y_k, x_k from each other's shared memory.  On entry
+// the tail's slots hold A's values less the terms of the columns outside the
+// tail (L numerators, U values, the pivots' and y's partial sums); the kernel
+// finishes them right-looking in the same order of terms as a column of the
+// dynamic schedule (k ascending, one fused multiply-add per term), then solves
+// U x = y backward, writes x_j into y_j and dx, and marks the tail's x
+// written for the backward solve of the columns below it.  Cluster barriers
+// are hardware barriers every CTA passes the same number of times.
+__global__ void __cluster_dims__(kLuTailCtas, 1, 1) __launch_bounds__(kLuTailThreads, 1) k_lu_tail(LuArgs a)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) double tsm[];
+    constexpr int C = kLuTailCtas;
+    const int rank = (int)cl.block_rank();
+    const int T0 = a.T0, m = a.n - T0, R = (m + C - 1) / C;
+    const int tid = threadIdx.x, TB = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = TB >> 5;
+    double *S = tsm;                        // [R][m]: block rows rank, rank + C, rank + 2C, ...
+    double *yv = S + (size_t)R * m;         // [R] y, then the right-hand side of the backward solve
+    double *lc = yv + R;                    // [R] the current step's multipliers
+    double *xl = lc + R;                    // [R] x
+    double *prow = xl + R;                  // [m] the current pivot row
+    double *sc = prow + m;                  // [1] the current y_k
+    const int nown = rank < m ? (m - 1 - rank) / C + 1 : 0;   // rows of this CTA
+    // ---- the block: column jj's slots give L(ii, jj) to row ii's CTA and
+    // U(jj, ii) to row jj's ----
+    for (int t = tid; t < R * m; t += TB) S[t] = 0.0;
+    __syncthreads();
+    for (int jj = wid; jj < m; jj += nw) {
+        const int j = T0 + jj;
+        for (int p = a.Lp[j] + lane; p < a.Lp[j + 1]; p += 32) {
+            const int ii = a.Li[p] - T0;
+            if (ii % C == rank) S[(size_t)(ii / C) * m + jj] = __ldcg(a.Lx + p);
+            if (jj % C == rank) S[(size_t)(jj / C) * m + ii] = __ldcg(a.Ux + p);
+        }
+        if (lane == 0 && jj % C == rank) {
+            S[(size_t)(jj / C) * m + jj] = __ldcg(a.piv + j);
+            yv[jj / C] = __ldcg(a.y + j);
+        }
+    }
+    cl.sync();
+    // ---- factorization and forward solve, one pivot per step ----
+    for (int k = 0; k < m; ++k) {
+        const int own = k % C, kr = k / C;
+        const double *Sk = cl.map_shared_rank(S, own) + (size_t)kr * m;
+        for (int c = k + tid; c < m; c += TB) prow[c] = Sk[c];
+        if (tid == 0) sc[0] = *cl.map_shared_rank(yv + kr, own);
+        __syncthreads();
+        const double d = prow[k], inv = fast_rcp(d), yk = sc[0];
+        if (rank == own && tid == 0) pivot_check(a, d);
+        const int r0 = (k + C - rank) / C;   // this CTA's first row below k
+        for (int r = r0 + tid; r < nown; r += TB) {
+            const double l = S[(size_t)r * m + k] * inv;
+            lc[r] = l;
+            S[(size_t)r * m + k] = l;
+            yv[r] = fma(-l, yk, yv[r]);
+        }
+        __syncthreads();
+        for (int r = r0 + wid; r < nown; r += nw) {
+            const double l = lc[r];
+            double *Sr = S + (size_t)r * m;
+            for (int c = k + 1 + lane; c < m; c += 32) Sr[c] = fma(-l, prow[c], Sr[c]);
+        }
+        cl.sync();
+    }
+    // ---- backward solve: x_k by row k's CTA, then every CTA takes the term
+    // of x_k out of its rows above k ----
+    for (int k = m - 1; k >= 0; --k) {
+        const int own = k % C, kr = k / C;
+        if (rank == own && tid == 0) xl[kr] = yv[kr] * fast_rcp(S[(size_t)kr * m + k]);
+        cl.sync();
+        const double xk = *cl.map_shared_rank(xl + kr, own);
+        const int rend = k > rank ? (k - 1 - rank) / C + 1 : 0;   // this CTA's rows above k
+        for (int r = tid; r < rend; r += TB) yv[r] = fma(-S[(size_t)r * m + k], xk, yv[r]);
+        __syncthreads();
+    }
+    // ---- x out, and the tail's x marked written ----
+    for (int r = tid; r < nown; r += TB) {
+        const int j = T0 + r * C + rank;
+        a.y[j] = xl[r];
+        a.dx[a.perm[j]] = xl[r];
+        a.done[a.n + j] = 1;
+    }
+    cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// shared memory of k_lu_tail for a tail of m columns
+size_t lu_tail_smem(int m)
+{
+    const size_t R = (size_t)(m + kLuTailCtas - 1) / kLuTailCtas;
+    return sizeof(double) * (R * (size_t)m + 3 * R + (size_t)m + 1);
 }
 
 // ------------------------------------------------------------ analysis ----
@@ -659,34 +782,57 @@ pf_status host_lu(int nb, int n, int npvpq, const std::vector<int> &colptr, cons
     };
     L.chain = L.H;
     while (L.chain > 0 && level_items(L.chain - 1) <= budget) --L.chain;
+    // the tail for the dense phase: the longest run of columns n-1, n-2, ...
+    // (closed under the tree's ancestors, like every final run) on levels at
+    // most kLuTailWidth wide, at most kLuTailMax columns; none below kLuTailMin
+    int T0 = n;
+    while (T0 > 0 && n - T0 < kLuTailMax) {
+        const int h = height[T0 - 1];
+        if (L.lvl_ptr[h + 1] - L.lvl_ptr[h] > kLuTailWidth) break;
+        --T0;
+    }
+    if (n - T0 < kLuTailMin) T0 = n;
+    L.T0 = T0;
+    // (the tail's items last: they wait for its whole frontier, and every item
+    // waits only for items before it in the list)
     L.need.assign(n, 0);
-    for (int h = 0; h < L.H; ++h)
-        for (int t = L.lvl_ptr[h]; t < L.lvl_ptr[h + 1]; ++t) {
-            const int j = L.lvl_col[t];
-            if (h < L.chain) {
-                L.fitems.push_back(make_int2(j, -2));
-            } else {
-                if (L.Lp[j + 1] == L.Lp[j]) L.fitems.push_back(make_int2(j, -1));
-                for (int p = L.Lp[j]; p < L.Lp[j + 1]; ++p) L.fitems.push_back(make_int2(j, p));
+    for (int pass = 0; pass < 2; ++pass)
+        for (int h = 0; h < L.H; ++h)
+            for (int t = L.lvl_ptr[h]; t < L.lvl_ptr[h + 1]; ++t) {
+                const int j = L.lvl_col[t];
+                if ((j >= T0) != (pass == 1)) continue;
+                if (h < L.chain && j < T0) {
+                    L.fitems.push_back(make_int2(j, -2));
+                } else {
+                    if (L.Lp[j + 1] == L.Lp[j]) L.fitems.push_back(make_int2(j, -1));
+                    for (int p = L.Lp[j]; p < L.Lp[j + 1]; ++p) L.fitems.push_back(make_int2(j, p));
+                }
+                L.need[j] = h < L.chain && j < T0 ? 1 : std::max(1, L.Lp[j + 1] - L.Lp[j]);
             }
-            L.need[j] = h < L.chain ? 1 : std::max(1, L.Lp[j + 1] - L.Lp[j]);
-        }
     // the elimination tree's children (CSR) and parents
     L.parent = parent;
+    // (outside the tail; the tail's columns wait for its frontier, the columns
+    // outside it whose parent is in it, listed after the children)
     L.cptr.assign(n + 1, 0);
     for (int j = 0; j < n; ++j)
-        if (parent[j] >= 0) L.cptr[parent[j] + 1]++;
+        if (parent[j] >= 0 && parent[j] < T0) L.cptr[parent[j] + 1]++;
     for (int j = 0; j < n; ++j) L.cptr[j + 1] += L.cptr[j];
     L.cidx.assign(L.cptr[n], 0);
     {
         std::vector<int> cf(L.cptr.begin(), L.cptr.end() - 1);
         for (int j = 0; j < n; ++j)
-            if (parent[j] >= 0) L.cidx[cf[parent[j]]++] = j;
+            if (parent[j] >= 0 && parent[j] < T0) L.cidx[cf[parent[j]]++] = j;
     }
-    // the backward solve's columns from the highest level down
+    L.fr0 = (int)L.cidx.size();
+    for (int j = 0; j < T0; ++j)
+        if (parent[j] >= T0) L.cidx.push_back(j);
+    L.fr1 = (int)L.cidx.size();
+    if (L.cidx.empty()) L.cidx.push_back(0);
+    // the backward solve's columns outside the tail from the highest level down
     L.bcols.reserve(n);
     for (int h = L.H - 1; h >= 0; --h)
-        for (int t = L.lvl_ptr[h]; t < L.lvl_ptr[h + 1]; ++t) L.bcols.push_back(L.lvl_col[t]);
+        for (int t = L.lvl_ptr[h]; t < L.lvl_ptr[h + 1]; ++t)
+            if (L.lvl_col[t] < T0) L.bcols.push_back(L.lvl_col[t]);
     // every entry of J_r (CSC order) to its factor slot: 4 slot + {0: L, 1: U, 2: diagonal}
     const int nnzA = colptr[n];
     L.amap.assign(nnzA, 0);
@@ -729,7 +875,7 @@ pf_status lu_prepare(Grid *g, cudaStream_t s)
         (e = up(&g->lu_lvl_col, L.lvl_col)) || (e = up(&g->lu_perm, L.perm)) || (e = up(&g->lu_amap, L.amap)) ||
         (e = up(&g->lu_gptr, L.gptr)) || (e = up(&g->lu_need, L.need)) || (e = up(&g->lu_cptr, L.cptr)) ||
         (e = up(&g->lu_cidx, L.cidx)) || (e = up(&g->lu_parent, L.parent)) || (e = up(&g->lu_bcols, L.bcols)) ||
-        (e = g->arena.alloc(&g->lu_done, 2 * (size_t)L.n + 1)) ||
+        (e = g->arena.alloc(&g->lu_done, 2 * (size_t)L.n + 2)) ||
         (e = g->arena.alloc(&g->lu_fitems, std::max<size_t>(L.fitems.size(), 1))) ||
         (!L.fitems.empty() && (e = cudaMemcpyAsync(g->lu_fitems, L.fitems.data(), L.fitems.size() * sizeof(int2),
                                                    cudaMemcpyHostToDevice, s))) ||
@@ -745,6 +891,11 @@ pf_status lu_prepare(Grid *g, cudaStream_t s)
     g->lu_H = L.H;
     g->lu_chain = L.chain;
     g->lu_nfitems = (int)L.fitems.size();
+    g->lu_nbcols = (int)L.bcols.size();
+    g->lu_T0 = L.T0;
+    g->lu_LpT0 = L.Lp[L.T0];
+    g->lu_fr0 = L.fr0;
+    g->lu_fr1 = L.fr1;
     g->lu_widest = 1;
     for (int h = 0; h < L.H; ++h) g->lu_widest = std::max(g->lu_widest, L.lvl_ptr[h + 1] - L.lvl_ptr[h]);
     g->lu_nnzL = (long long)nnzL;
@@ -775,6 +926,11 @@ cudaError_t launch_lu_solve(Grid *g, const double *Jr, const double *F, double *
     a.n = g->lu_n;
     a.nnzA = (int)g->red_nnz;
     a.nfitems = g->lu_nfitems;
+    a.nbcols = g->lu_nbcols;
+    a.T0 = g->lu_T0;
+    a.LpT0 = g->lu_LpT0;
+    a.fr0 = g->lu_fr0;
+    a.fr1 = g->lu_fr1;
     a.Lp = g->lu_Lp;
     a.Li = g->lu_Li;
     a.Rp = g->lu_Rp;
@@ -822,6 +978,20 @@ cudaError_t launch_lu_solve(Grid *g, const double *Jr, const double *F, double *
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (a.T0 >= a.n) {   // no tail: one launch
+        a.mode = 0;
+        return cudaLaunchKernelEx(&cfg, k_lu_solve, a);
+    }
+    // the factorization outside the tail and the tail's outside terms; the
+    // tail by one cluster; the backward solve outside the tail
+    a.mode = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_lu_solve, a);
+    if (e != cudaSuccess) return e;
+    const size_t tsm = lu_tail_smem(a.n - a.T0);
+    if ((e = ensure_dyn_smem(reinterpret_cast<const void *>(k_lu_tail), tsm))) return e;
+    k_lu_tail<<<kLuTailCtas, kLuTailThreads, tsm, s>>>(a);
+    if ((e = cudaGetLastError())) return e;
+    a.mode = 2;
     return cudaLaunchKernelEx(&cfg, k_lu_solve, a);
 }
 

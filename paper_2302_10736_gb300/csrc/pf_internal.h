@@ -309,7 +309,8 @@ struct Grid {
     int *lu_lvl_ptr = nullptr, *lu_lvl_col = nullptr, *lu_perm = nullptr, *lu_amap = nullptr, *lu_gptr = nullptr;
     int *lu_need = nullptr, *lu_cptr = nullptr, *lu_cidx = nullptr, *lu_parent = nullptr, *lu_bcols = nullptr;
     int *lu_done = nullptr;   // [2n + 1] per column: finished factorization items, backward solve done; the item counter
-    int lu_nfitems = 0;
+    int lu_nfitems = 0, lu_nbcols = 0, lu_T0 = 0, lu_LpT0 = 0;   // items; the tail's first column and slot
+    int lu_fr0 = 0, lu_fr1 = 0;                                  // the tail's frontier in lu_cidx
     int2 *lu_gsrc = nullptr, *lu_fitems = nullptr;
     double *lu_Lx = nullptr, *lu_Ux = nullptr, *lu_D = nullptr, *lu_y = nullptr;
     // tracer: events [2 * capacity], kernel id per record
@@ -396,6 +397,8 @@ cudaError_t launch_reduce(Grid *g, const int *map, const double *Pspec, const do
 // factor slot 4 slot + {0 L, 1 U, 2 diagonal}), its upload, and the solve
 struct HostLu {
     int n = 0, H = 0, chain = 0;
+    int T0 = 0;             // the tail (columns T0 .. n-1) factored as a dense block; n: none
+    int fr0 = 0, fr1 = 0;   // the tail's frontier (the columns outside it whose parent is in it) in cidx
     std::vector<int> perm, Lp, Li, Rp, Rk, Rq, lvl_ptr, lvl_col, amap;
     std::vector<int> gptr;    // [nnzL + 1] update terms of every factor slot
     std::vector<int2> gsrc;   // {slot of L(i, k), slot of L(j, k)}, k ascending per slot
