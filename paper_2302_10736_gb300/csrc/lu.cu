@@ -511,14 +511,17 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
 // block of m = n - T0 rows and columns, by one cluster of kLuTailCtas CTAs:
 // row i of the block lives in the shared memory of CTA i mod C (row-cyclic,
 // so every step's rows are spread over all CTAs), and the CTAs read the
-// current pivot row and y_k, x_k from each other's shared memory.  On entry
+// current pivot row, y_k and x_k from each other's shared memory.  On entry
 // the tail's slots hold A's values less the terms of the columns outside the
 // tail (L numerators, U values, the pivots' and y's partial sums); the kernel
 // finishes them right-looking in the same order of terms as a column of the
-// dynamic schedule (k ascending, one fused multiply-add per term), then solves
-// U x = y backward, writes x_j into y_j and dx, and marks the tail's x
-// written for the backward solve of the columns below it.  Cluster barriers
-// are hardware barriers every CTA passes the same number of times.
+// dynamic schedule (k ascending, one fused multiply-add per term), solving
+// L y = F on the way, then solves U x = y backward, writes x_j into y_j and
+// dx, and marks the tail's x written for the backward solve below it.  One
+// cluster barrier per step (a warp per row in the factorization, a thread per
+// row in the backward solve, so that no other barrier is needed there).
+// Cluster barriers are hardware barriers every CTA passes the same number of
+// times.
 __global__ void __cluster_dims__(kLuTailCtas, 1, 1) __launch_bounds__(kLuTailThreads, 1) k_lu_tail(LuArgs a)
 {
     namespace cg = cooperative_groups;
@@ -530,10 +533,8 @@ __global__ void __cluster_dims__(kLuTailCtas, 1, 1) __launch_bounds__(kLuTailThr
     const int tid = threadIdx.x, TB = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = TB >> 5;
     double *S = tsm;                        // [R][m]: block rows rank, rank + C, rank + 2C, ...
     double *yv = S + (size_t)R * m;         // [R] y, then the right-hand side of the backward solve
-    double *lc = yv + R;                    // [R] the current step's multipliers
-    double *xl = lc + R;                    // [R] x
-    double *prow = xl + R;                  // [m] the current pivot row
-    double *sc = prow + m;                  // [1] the current y_k
+    double *xl = yv + R;                    // [R] x
+    double *prow = xl + R;                  // [m + 1] the current pivot row (columns k .. m-1) and y_k
     const int nown = rank < m ? (m - 1 - rank) / C + 1 : 0;   // rows of this CTA
     // ---- the block: column jj's slots give L(ii, jj) to row ii's CTA and
     // U(jj, ii) to row jj's ----
@@ -552,40 +553,36 @@ __global__ void __cluster_dims__(kLuTailCtas, 1, 1) __launch_bounds__(kLuTailThr
         }
     }
     cl.sync();
-    // ---- factorization and forward solve, one pivot per step ----
+    // ---- factorization and forward solve, one pivot per step: the pivot row
+    // copied in, then a warp per row below it ----
     for (int k = 0; k < m; ++k) {
         const int own = k % C, kr = k / C;
         const double *Sk = cl.map_shared_rank(S, own) + (size_t)kr * m;
         for (int c = k + tid; c < m; c += TB) prow[c] = Sk[c];
-        if (tid == 0) sc[0] = *cl.map_shared_rank(yv + kr, own);
+        if (tid == TB - 1) prow[m] = *cl.map_shared_rank(yv + kr, own);
         __syncthreads();
-        const double d = prow[k], inv = fast_rcp(d), yk = sc[0];
+        const double d = prow[k], inv = fast_rcp(d), yk = prow[m];
         if (rank == own && tid == 0) pivot_check(a, d);
-        const int r0 = (k + C - rank) / C;   // this CTA's first row below k
-        for (int r = r0 + tid; r < nown; r += TB) {
-            const double l = S[(size_t)r * m + k] * inv;
-            lc[r] = l;
-            S[(size_t)r * m + k] = l;
-            yv[r] = fma(-l, yk, yv[r]);
-        }
-        __syncthreads();
-        for (int r = r0 + wid; r < nown; r += nw) {
-            const double l = lc[r];
+        for (int r = (k + C - rank) / C + wid; r < nown; r += nw) {   // this CTA's rows below k
             double *Sr = S + (size_t)r * m;
+            const double l = Sr[k] * inv;
             for (int c = k + 1 + lane; c < m; c += 32) Sr[c] = fma(-l, prow[c], Sr[c]);
+            __syncwarp();
+            if (lane == 0) {
+                Sr[k] = l;
+                yv[r] = fma(-l, yk, yv[r]);
+            }
         }
         cl.sync();
     }
-    // ---- backward solve: x_k by row k's CTA, then every CTA takes the term
-    // of x_k out of its rows above k ----
+    // ---- backward solve: thread r keeps row r's right-hand side; x_k by the
+    // thread of row k, then every row above k takes its term out ----
     for (int k = m - 1; k >= 0; --k) {
         const int own = k % C, kr = k / C;
-        if (rank == own && tid == 0) xl[kr] = yv[kr] * fast_rcp(S[(size_t)kr * m + k]);
+        if (rank == own && tid == kr) xl[kr] = yv[kr] * fast_rcp(S[(size_t)kr * m + k]);
         cl.sync();
-        const double xk = *cl.map_shared_rank(xl + kr, own);
-        const int rend = k > rank ? (k - 1 - rank) / C + 1 : 0;   // this CTA's rows above k
-        for (int r = tid; r < rend; r += TB) yv[r] = fma(-S[(size_t)r * m + k], xk, yv[r]);
-        __syncthreads();
+        if (tid < nown && tid * C + rank < k)
+            yv[tid] = fma(-S[(size_t)tid * m + k], *cl.map_shared_rank(xl + kr, own), yv[tid]);
     }
     // ---- x out, and the tail's x marked written ----
     for (int r = tid; r < nown; r += TB) {
@@ -601,7 +598,7 @@ __global__ void __cluster_dims__(kLuTailCtas, 1, 1) __launch_bounds__(kLuTailThr
 size_t lu_tail_smem(int m)
 {
     const size_t R = (size_t)(m + kLuTailCtas - 1) / kLuTailCtas;
-    return sizeof(double) * (R * (size_t)m + 3 * R + (size_t)m + 1);
+    return sizeof(double) * (R * (size_t)m + 2 * R + (size_t)m + 1);
 }
 
 // ------------------------------------------------------------ analysis ----
