@@ -601,9 +601,14 @@ pf_status jac_target(pf_grid *grid, int32_t method, const double *vm, const doub
  * analyses the pattern on the host (minimum-degree order of the buses,
  * symbolic factorization, the dependency schedule of the elimination tree),
  * allocates the factor storage and synchronizes; make it before any stream
- * capture.  Every later call is one cooperative launch: numeric factorization
- * with the forward solve, then the backward solve, each column started when the
- * columns it depends on are done (bounded waits), bitwise repeatable.  A zero
+ * capture.  Every later call is asynchronous: a cooperative launch for the
+ * numeric factorization with the forward solve, each column started when the
+ * columns it depends on are done (bounded waits); where the top of the
+ * elimination tree is a run of at least 16 narrow levels, a launch of one
+ * 8-CTA thread-block cluster for it (a dense block in shared memory, both
+ * triangular solves), then a cooperative launch for the backward solve below
+ * it (otherwise the backward solve ends the first launch).  Bitwise
+ * repeatable.  A zero
  * or non-finite pivot sets the grid's device error word (grid_check_error
  * reports PF_EDEVICE), a wait that runs out (2 s) sets it to a time-out
  * (grid_check_error reports PF_ETIMEOUT and clears it); no pivoting
@@ -617,8 +622,8 @@ pf_status jac_reduced_solve(pf_grid *grid, const double *Jr, const double *F, do
  * Jacobian a Newton step needs): starting from vm, va [nb] (device, updated
  * in place), repeat
  *   full evaluation by `method` (0 Ybus, 1 element-wise) -> F and J_r
- *   (the reduced system of jac_reduced, J_r row-major) -> stop when
- *   max |F| <= tol -> solve J_r dx = F (cuSOLVER sparse QR, on the device)
+ *   (the reduced system of jac_reduced, J_r in CSC order) -> stop when
+ *   max |F| <= tol -> solve J_r dx = F (jac_reduced_solve's sparse LU)
  *   -> theta_pvpq -= dx[0 .. n_pvpq), v_pq -= dx[n_pvpq .. n)
  * at most max_iter steps.  Requires grid_set_bus_types; PV and reference
  * magnitudes and reference angles stay as given.  *iterations and *mismatch

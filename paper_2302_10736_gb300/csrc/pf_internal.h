@@ -283,7 +283,6 @@ struct Grid {
     int red_set = 0, red_n = 0, red_npvpq = 0;
     long long red_nnz = 0;
     int *red_colptr = nullptr, *red_rowidx = nullptr, *red_jmap = nullptr, *red_fmap = nullptr;
-    int *red_rowptr = nullptr, *red_colidx = nullptr, *red_jmap_csr = nullptr;   // the same matrix row-major
     // inverse maps for the fused element-wise path: the reduced (CSC) index of
     // every canonical J position, and of every bus's P and Q equation (-1: not kept)
     int *red_jinv = nullptr;

@@ -24,7 +24,6 @@ namespace {
 struct HostReduced {
     int n = 0, npvpq = 0, npq = 0;
     std::vector<int> colptr, rowidx, jmap, fmap;
-    std::vector<int> rowptr, colidx, jmap_csr;   // row-major copy (the Newton solver's input)
     std::vector<int> jinv;                       // [4 nnzY] reduced (CSC) index of each canonical position, or -1
     std::vector<int2> binv;                      // [nb] reduced index of the bus's P and Q equation, or -1
 };
@@ -69,23 +68,6 @@ pf_status host_reduced(const HostTopo &H, const int *bt, HostReduced &R)
             R.rowidx[fill[c]] = red[Rw];
             R.jmap[fill[c]++] = p;
         }
-    }
-    // row-major: canonical rows ascending; within a row the theta block then
-    // the v block, each ascending, so the reduced columns come out ascending
-    R.rowptr.assign(R.n + 1, 0);
-    R.colidx.clear();
-    R.jmap_csr.clear();
-    R.colidx.reserve(nnz);
-    R.jmap_csr.reserve(nnz);
-    for (int Rw = 0; Rw < 2 * nb; ++Rw) {
-        if (red[Rw] < 0) continue;
-        for (int p = H.jrp[Rw]; p < H.jrp[Rw + 1]; ++p) {
-            const int c = red[H.jci[p]];
-            if (c < 0) continue;
-            R.colidx.push_back(c);
-            R.jmap_csr.push_back(p);
-        }
-        R.rowptr[red[Rw] + 1] = (int)R.colidx.size();
     }
     // inverse maps for the fused element-wise path
     R.jinv.assign(H.jci.size(), -1);
@@ -153,7 +135,7 @@ __global__ void __launch_bounds__(256) k_reduce(int n, int npvpq, int nnz, const
 }  // namespace
 
 // The gather after a full evaluation into the grid's scratch: F, and the
-// reduced values in the order of `map` (column- or row-major).
+// reduced values in the order of `map` (CSC).
 cudaError_t launch_reduce(Grid *g, const int *map, const double *Pspec, const double *Qspec, double *F, double *Jr,
                           cudaStream_t s)
 {
@@ -184,20 +166,17 @@ PF_API pf_status grid_set_bus_types(pf_grid *grid, const int32_t *bus_type, pf_s
     cudaStream_t s = (cudaStream_t)stream;
     PF_CUDA(cudaStreamSynchronize(s));   // no launch may still read the old map
     for (void *p : {(void *)g->red_colptr, (void *)g->red_rowidx, (void *)g->red_jmap, (void *)g->red_fmap,
-                    (void *)g->red_rowptr, (void *)g->red_colidx, (void *)g->red_jmap_csr, (void *)g->red_jinv,
+                    (void *)g->red_jinv,
                     (void *)g->red_binv, (void *)g->nt_F, (void *)g->nt_J, (void *)g->nt_dx})
         if (p) g->arena.release(p);
     g->red_colptr = g->red_rowidx = g->red_jmap = g->red_fmap = nullptr;
-    g->red_rowptr = g->red_colidx = g->red_jmap_csr = g->red_jinv = nullptr;
+    g->red_jinv = nullptr;
     g->red_binv = nullptr;
     g->nt_F = g->nt_J = g->nt_dx = nullptr;   // sized by n and nnz: re-allocated by the next Newton solve
     g->red_set = 0;
     if ((st = upload_vec(g->arena, &g->red_colptr, R.colptr, s)) ||
         (st = upload_vec(g->arena, &g->red_rowidx, R.rowidx, s)) ||
         (st = upload_vec(g->arena, &g->red_jmap, R.jmap, s)) || (st = upload_vec(g->arena, &g->red_fmap, R.fmap, s)) ||
-        (st = upload_vec(g->arena, &g->red_rowptr, R.rowptr, s)) ||
-        (st = upload_vec(g->arena, &g->red_colidx, R.colidx, s)) ||
-        (st = upload_vec(g->arena, &g->red_jmap_csr, R.jmap_csr, s)) ||
         (st = upload_vec(g->arena, &g->red_jinv, R.jinv, s)) || (st = upload_vec(g->arena, &g->red_binv, R.binv, s)))
         return st;
     if (!g->red_J) {
