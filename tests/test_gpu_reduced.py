@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gridcases import hub_grid, make_grid, random_grid, random_state, relerr, two_bus_lossless
+from gridcases import hub_grid, make_grid, random_grid, random_state, relerr, series, two_bus_lossless
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -257,6 +257,48 @@ def test_lu_solve_matches_a_dense_solve(pf, case):
     Fh, xh = F.cpu().numpy(), dx.cpu().numpy()
     ref = np.linalg.solve(A.toarray(), Fh)
     assert relerr(xh, ref) <= 1e-10
+    assert backward_error(A, xh, Fh) <= 1e-13
+    assert torch.equal(dx, dx2)
+
+
+def chain_grid(nb, seed):
+    """A radial line of nb buses (bus i to bus i + 1) with random series
+    admittances and charging: minimum degree eliminates its buses from one
+    end, so its elimination tree is a single chain of columns."""
+    rng = np.random.default_rng(seed)
+    branches = []
+    for i in range(nb - 1):
+        g, b = series(rng.uniform(0.005, 0.02), rng.uniform(0.05, 0.2))
+        branches.append((i, i + 1, g, b, rng.uniform(0.0, 0.05), 1.0, 0.0))
+    return make_grid(nb, branches)
+
+
+@pytest.mark.parametrize("nb", [6, 12, 200, 400])
+def test_lu_solve_on_a_chain(pf, nb):
+    """The solve on radial lines, whose reduced systems (n = 2 (nb - 1)) are
+    all narrow levels: 6 buses (n = 10) stay below the dense tail's minimum
+    of 16 columns (one launch); 12 buses (n = 22) are a tail from the first
+    column on; 200 and 400 buses (n = 398, 798) have the largest tail, 384
+    columns, above 14 and 414 columns of the dynamic schedule.  Solution
+    within 1e-10 (max-norm relative) of LAPACK's pivoting dense solve,
+    normwise backward error below 1e-13, two solves bitwise equal."""
+    import torch
+    import scipy.sparse as sp
+    gr = chain_grid(nb, 300 + nb)
+    bt = np.ones(nb, np.int32)
+    bt[0] = 3
+    grid, F, Jr, n = _solve_case(pf, gr, bt, 301 + nb)
+    assert n == 2 * (nb - 1)
+    dx = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+    dx2 = torch.full_like(dx, np.nan)
+    pf.jac_reduced_solve(grid, Jr, F, dx)
+    pf.jac_reduced_solve(grid, Jr, F, dx2)
+    torch.cuda.synchronize()
+    pf.grid_check_error(grid)
+    colptr, rowidx = pf.jac_reduced_pattern(grid)
+    A = sp.csc_matrix((Jr.cpu().numpy(), rowidx, colptr), shape=(n, n))
+    Fh, xh = F.cpu().numpy(), dx.cpu().numpy()
+    assert relerr(xh, np.linalg.solve(A.toarray(), Fh)) <= 1e-10
     assert backward_error(A, xh, Fh) <= 1e-13
     assert torch.equal(dx, dx2)
 
