@@ -75,6 +75,8 @@ def parse_args(argv=None):
                     choices=["n1", "adjoint4", "batched5", "permuted", "reduced", "ultra", "newton", "sweep",
                              "study", "target", "replicated"],
                     help="run only this batched/adjoint workload (few launches, for profilers) and exit")
+    ap.add_argument("--scenarios", type=int, default=None,
+                    help="with --profile-workload n1: the first N scenarios of the 1,024 (a smaller case for profilers)")
     return ap.parse_args(argv)
 
 
@@ -467,14 +469,14 @@ def timed_replays(torch, g, reps, name="replays"):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_workloads(torch, pfgrid, synth, reps, only=None, cpu_seconds=None):
+def extra_workloads(torch, pfgrid, synth, reps, only=None, cpu_seconds=None, n1_scenarios=None):
     """The batched and adjoint workloads, each timed from a CUDA-graph replay
     (inputs larger than L2 for the batched ones, so no flush is needed).
     `only` restricts the run to one of "n1", "adjoint4", "batched5", "permuted", "reduced", "ultra",
     "newton", "sweep", "study", "target"."""
     out = {}
     if only in (None, "n1"):
-        out.update(_n1_workload(torch, pfgrid, synth, reps, cpu_seconds))
+        out.update(_n1_workload(torch, pfgrid, synth, reps, cpu_seconds, n1_scenarios))
     for k, key, tag in ((4, "adjoint_25k", "adjoint4"), (5, "batched_jac_and_adjoint_250k_x16", "batched5")):
         if only in (None, tag):
             out[key] = _adjoint_workload(torch, pfgrid, synth, reps, k, cpu_seconds)
@@ -766,12 +768,13 @@ def _permuted_workload(torch, pfgrid, synth, steps):
     return res
 
 
-def _n1_workload(torch, pfgrid, synth, reps, cpu_seconds=None):
+def _n1_workload(torch, pfgrid, synth, reps, cpu_seconds=None, nscen=None):
     out = {}
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
     # N-1 batch: 10,000 buses x 1,024 scenarios, each without a distinct non-bridge branch
-    w = synth.workload(3)
+    # (nscen: the first nscen of them)
+    w = synth.workload(3, nscen=nscen)
     grid = pfgrid.ybus_build(w)
     S, nb, T = w["nscen"], w["nb"], 2 * w["nl"]
     batch = pfgrid.batch_create(grid, S, w["outage"])
@@ -785,7 +788,8 @@ def _n1_workload(torch, pfgrid, synth, reps, cpu_seconds=None):
     ms = timed_replays(torch, g, reps, "n1_batch")
     ops = S * (EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb)
     byt = S * (16 * nb + 16 * nb) + 8 * batch.nnzJ_total + 40 * T + 84 * nb
-    out["n1_batch_10k_x1024"] = {
+    name = "n1_batch_10k_x%d" % S
+    out[name] = {
         "evals_per_s": S / (ms * 1e-3), "ms_per_launch": ms, "launches": 1, "graph": True,
         "fp64_gops": ops / (ms * 1e-3) / 1e9, "fp64_frac": ops / (ms * 1e-3) / 1e9 / fp64_peak_g(),
         "hbm_gbs": byt / (ms * 1e-3) / 1e9, "jacobian_values": batch.nnzJ_total,
@@ -793,8 +797,7 @@ def _n1_workload(torch, pfgrid, synth, reps, cpu_seconds=None):
     # the same batch by the Ybus method (phasor launch + row launch)
     g2 = graph_of(torch, lambda: pfgrid.jac_ybus_batched(batch, vm, va, P, Q, J))
     ms2 = timed_replays(torch, g2, reps, "n1_batch_ybus")
-    out["n1_batch_10k_x1024"].update({"ybus_evals_per_s": S / (ms2 * 1e-3), "ybus_ms_per_launch": ms2,
-                                      "ybus_launches": 2})
+    out[name].update({"ybus_evals_per_s": S / (ms2 * 1e-3), "ybus_ms_per_launch": ms2, "ybus_launches": 2})
     # the plain single-scenario paths on the base grid, one state per launch (L2 warm)
     P1 = torch.empty(nb, dtype=torch.float64, device="cuda")
     Q1 = torch.empty_like(P1)
@@ -802,10 +805,10 @@ def _n1_workload(torch, pfgrid, synth, reps, cpu_seconds=None):
     for key, fn in (("single_elementwise_evals_per_s", pfgrid.jac_elementwise),
                     ("single_ybus_evals_per_s", pfgrid.jac_ybus)):
         g3 = graph_of(torch, lambda: fn(grid, vm[:nb], va[:nb], P1, Q1, J1))
-        out["n1_batch_10k_x1024"][key] = 1e3 / timed_replays(torch, g3, reps, "n1_single")
+        out[name][key] = 1e3 / timed_replays(torch, g3, reps, "n1_single")
     pfgrid.grid_check_error(grid)
     if cpu_seconds:
-        out["n1_batch_10k_x1024"]["cpu_baseline"] = oracle_batch_baseline(w, "n1", cpu_seconds)
+        out[name]["cpu_baseline"] = oracle_batch_baseline(w, "n1", cpu_seconds)
     return out
 
 
@@ -876,7 +879,8 @@ def main():
     torch.cuda.set_device(local)
     if args.profile_workload:
         _FP64_MEASURED["g"] = measure_fp64_peak(torch, pfgrid)["gdfma_per_s"]
-        print(json.dumps(extra_workloads(torch, pfgrid, synth, max(1, args.steps), args.profile_workload)))
+        print(json.dumps(extra_workloads(torch, pfgrid, synth, max(1, args.steps), args.profile_workload,
+                                         n1_scenarios=args.scenarios)))
         return
     dist = None
     if world > 1:
