@@ -388,17 +388,24 @@ def grid_bytes(grid):
 
 
 STREAM_HOST_MARGIN_S = 40e-6   # host time allowed per queued launch of a stream
+# CUDA streams the headline's stream of independent evaluations alternates over:
+# the CTAs of two evaluations then share the SMs in different phases of their
+# windows (the integer-pipe phasor and coupling phases of one beside the FP64
+# reduction of the other), which one launch alone cannot do
+HEADLINE_STREAMS = 2
 
 
-def stream_loop(torch, fn_k, steps, name, info=None):
-    """fn_k(k) for k = 0 .. steps-1 back to back on the current stream between
-    one pair of CUDA events; mean ms per step.  A device-side wait (torch's
-    spin kernel, before the first event) holds the GPU while the host queues
-    all the launches, so the device time is the GPU's own back-to-back rate
-    and not the host's launch rate (the end-to-end number includes the host).
-    If the host took longer than the wait, the run is repeated with a longer
-    one."""
+def stream_loop(torch, fn_k, steps, name, info=None, nstreams=1):
+    """fn_k(k, stream) for k = 0 .. steps-1 back to back between one pair of
+    CUDA events, step k on CUDA stream k mod nstreams (nstreams = 1: the
+    current stream; stream None); mean ms per step.  A device-side wait
+    (torch's spin kernel, before the first event) holds the GPU while the
+    host queues all the launches, so the device time is the GPU's own
+    back-to-back rate and not the host's launch rate (the end-to-end number
+    includes the host).  If the host took longer than the wait, the run is
+    repeated with a longer one."""
     margin = STREAM_HOST_MARGIN_S
+    streams = [torch.cuda.Stream() for _ in range(nstreams)] if nstreams > 1 else [None]
     for _ in range(4):
         wait_s = steps * margin + 1e-3
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -407,8 +414,20 @@ def stream_loop(torch, fn_k, steps, name, info=None):
         t0 = time.perf_counter()
         torch.cuda.nvtx.range_push(name)
         e0.record()
+        if nstreams > 1:   # every stream starts after the first event
+            go = torch.cuda.Event()
+            go.record()
+            for st in streams:
+                st.wait_event(go)
         for k in range(steps):
-            fn_k(k)
+            st = streams[k % len(streams)]
+            fn_k(k, st.cuda_stream if st is not None else None)
+        if nstreams > 1:   # the second event after every stream's last step
+            cur = torch.cuda.current_stream()
+            for st in streams:
+                done = torch.cuda.Event()
+                done.record(st)
+                cur.wait_event(done)
         e1.record()
         torch.cuda.nvtx.range_pop()
         host_s = time.perf_counter() - t0
@@ -909,8 +928,10 @@ def main():
         copies.append((g2, dev(w["vm"][0]), dev(w["va"][0]), torch.empty_like(P), torch.empty_like(Q),
                        torch.empty_like(J)))
     footprint = STREAM_COPIES * (grid_bytes(grid) + 8 * (4 * nb + grid.nnzJ))
-    ew_k = lambda k: pfgrid.jac_elementwise(*copies[k % STREAM_COPIES])
-    yb_k = lambda k: pfgrid.jac_ybus(*copies[k % STREAM_COPIES])
+    # (with two streams step k goes to stream k mod 2 and copy k mod 16: the
+    # streams never share a copy's outputs)
+    ew_k = lambda k, st=None: pfgrid.jac_elementwise(*copies[k % STREAM_COPIES], stream=st)
+    yb_k = lambda k, st=None: pfgrid.jac_ybus(*copies[k % STREAM_COPIES], stream=st)
 
     ew = lambda: pfgrid.jac_elementwise(grid, vm, va, P, Q, J)
     yb = lambda: pfgrid.jac_ybus(grid, vm, va, P, Q, J)
@@ -933,16 +954,20 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     stream_info = {}
-    ms_stream = stream_loop(torch, ew_k, args.steps, "ew_stream", stream_info)   # the timed region of the headline
+    # the timed region of the headline
+    ms_stream = stream_loop(torch, ew_k, args.steps, "ew_stream", stream_info, nstreams=HEADLINE_STREAMS)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms_stream_yb = stream_loop(torch, yb_k, args.steps, "ybus_stream")
+    ms_stream_yb = stream_loop(torch, yb_k, args.steps, "ybus_stream", nstreams=HEADLINE_STREAMS)
+    # the same streams on one CUDA stream: back-to-back launches of one evaluation at a time
+    ms_stream1 = stream_loop(torch, ew_k, args.steps, "ew_stream_one")
+    ms_stream1_yb = stream_loop(torch, yb_k, args.steps, "ybus_stream_one")
     # the injections alone, in the same stream form
-    ms_stream_iew = stream_loop(torch, lambda k: pfgrid.inj_elementwise(*copies[k % STREAM_COPIES][:5]),
-                                args.steps, "inj_ew_stream")
-    ms_stream_iyb = stream_loop(torch, lambda k: pfgrid.inj_ybus(*copies[k % STREAM_COPIES][:5]),
-                                args.steps, "inj_ybus_stream")
+    ms_stream_iew = stream_loop(torch, lambda k, st: pfgrid.inj_elementwise(*copies[k % STREAM_COPIES][:5], stream=st),
+                                args.steps, "inj_ew_stream", nstreams=HEADLINE_STREAMS)
+    ms_stream_iyb = stream_loop(torch, lambda k, st: pfgrid.inj_ybus(*copies[k % STREAM_COPIES][:5], stream=st),
+                                args.steps, "inj_ybus_stream", nstreams=HEADLINE_STREAMS)
     # one evaluation at a time: L2 flushed before every step outside the events,
     # so each step also pays its launch (the latency form)
     t_ew = time_loop(torch, ew, args.steps, flush, "ew")
@@ -979,7 +1004,9 @@ def main():
     ms_pu, n_pu = kmean(tr_yb, "phasor")   # the Ybus path's separate phasor step
     ms_jyb, _ = kmean(tr_yb, "jac_ybus")
     ops_ew = EW_OPS_PER_TERMINAL * T + EW_OPS_PER_BUS * nb
-    # the kernel's average launch duration in the timed stream (one launch per step)
+    # the device's aggregate rate over the timed region: the method's operations
+    # per evaluation x evaluations per second (one launch per evaluation, two in
+    # flight at a time on two CUDA streams; the one-stream rate is beside it)
     achieved = ops_ew / (ms_stream * 1e-3) / 1e9
     hbm, hbm_kind = hbm_peak()
     # algorithmic bytes of an element-wise injection + Jacobian evaluation: branch ends and 5 parameters
@@ -991,6 +1018,11 @@ def main():
             "ops_note": "the method's operations in plain FP64 form (12 per terminal, 16 per bus); the kernel runs "
                         "8 per terminal and 3 per bus of them in 64-bit fixed point on the integer pipes, %d on "
                         "the FP64 pipe" % (EW_FP64_PIPE_PER_TERMINAL * T + EW_FP64_PIPE_PER_BUS * nb),
+            "rate_note": "achieved = operations per evaluation x evaluations per second over the timed region "
+                         "(%d CUDA streams, two evaluations' CTAs sharing the SMs); on one stream, launches back "
+                         "to back: %.2f us per launch, frac %.3f" % (HEADLINE_STREAMS, ms_stream1 * 1e3,
+                                                                     ops_ew / (ms_stream1 * 1e-3) / 1e9
+                                                                     / fp64_peak["gdfma_per_s"]),
             "fp64_pipe_frac": (EW_FP64_PIPE_PER_TERMINAL * T + EW_FP64_PIPE_PER_BUS * nb) / (ms_stream * 1e-3) / 1e9
                               / fp64_peak["gdfma_per_s"],
             "peak_source": "measured: fp64_peak_probe (DFMA chains on every SM) in this run",
@@ -1076,6 +1108,8 @@ def main():
                        "l2": "inputs larger than L2: %d copies of the grid with their own states and outputs "
                              "(%.0f MB) evaluated in turn, %d steps back to back between one pair of CUDA events"
                              % (STREAM_COPIES, footprint / 1e6, args.steps),
+                       "streams": "step k on CUDA stream k mod %d (independent evaluations: each reads its own "
+                                  "copy's state and writes all its outputs)" % HEADLINE_STREAMS,
                        "launch_queue": "all %d launches queued behind a device-side wait of %.1f ms before the "
                                        "first event (host: %.1f us per launch), so the device time is the GPU's "
                                        "back-to-back rate" % (args.steps, stream_info["device_wait_ms"],
@@ -1086,6 +1120,8 @@ def main():
             "compare": {
                 "elementwise_jac_evals_per_s": 1e3 / ms_stream,
                 "ybus_jac_evals_per_s_stream": 1e3 / ms_stream_yb,
+                "elementwise_jac_evals_per_s_one_stream": 1e3 / ms_stream1,
+                "ybus_jac_evals_per_s_one_stream": 1e3 / ms_stream1_yb,
                 "elementwise_inj_evals_per_s_stream": 1e3 / ms_stream_iew,
                 "ybus_inj_evals_per_s_stream": 1e3 / ms_stream_iyb,
                 "elementwise_jac_evals_per_s_flush_per_step": 1e3 / (sum(t_ew) / len(t_ew)),
