@@ -191,13 +191,14 @@ pf_status jac_ybus(pf_grid *grid, const double *vm, const double *va, double *P,
  * atomics onto the diagonal slot of its bus and the off-diagonal slot of its
  * (bus, other bus) pair.  Same arguments as jac_ybus.
  *
- * Throughput of many independent evaluations (every call of this section):
- * one call keeps the CTAs of an SM in the same phase of their windows (the
- * integer pipes busy in the sine/cosine and coupling products, then the FP64
- * pipe in the bus sums); calls issued on two CUDA streams, each with its own
- * outputs, share the SMs in different phases (on a GB300, 70,000-bus grid:
- * 6.7 against 8.5 us per evaluation).  A grid may serve both streams: the
- * evaluations only read it.
+ * Throughput of many independent evaluations: one call keeps the CTAs of an
+ * SM in the same phase of their windows (the integer pipes busy in the
+ * sine/cosine and coupling products, then the FP64 pipe in the bus sums);
+ * calls issued on two CUDA streams, each with its own outputs, share the SMs
+ * in different phases (on a GB300, 70,000-bus grid: 6.7 against 8.5 us per
+ * evaluation).  Element-wise calls only read the grid, so one grid may serve
+ * both streams; Ybus-method calls use the grid's phasor workspace and need a
+ * grid per stream.
  */
 pf_status jac_elementwise(pf_grid *grid, const double *vm, const double *va, double *P, double *Q, double *J,
                           pf_stream stream);
