@@ -453,7 +453,6 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
     const int lane = threadIdx.x & 31;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
-    const int gwarp = (int)(gtid >> 5), gwarps = (int)(gthreads >> 5);
     const int nnzL = a.Lp[a.n];
     unsigned int bk = 0;
     if (a.mode != 2) {
@@ -481,8 +480,6 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(LuArgs a)
     // ---- every warp takes the next item (factorization and forward solve in
     // level order, then the backward solve from the root down) from a shared
     // counter, waits for what the item depends on, and runs it ----
-    (void)gwarp;
-    (void)gwarps;
     int *next = a.done + 2LL * a.n + (a.mode == 2 ? 1 : 0);
     const int nf = a.mode == 2 ? 0 : a.nfitems;
     const int nall = nf + (a.mode == 1 ? 0 : a.nbcols);
