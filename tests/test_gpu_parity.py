@@ -186,6 +186,40 @@ def test_bitwise_determinism(pf):
                 assert np.array_equal(x.view(np.uint64), y.view(np.uint64)), k
 
 
+def test_elementwise_calls_on_two_streams_share_a_grid(pf):
+    """Element-wise evaluations only read the grid: 16 calls with different
+    states interleaved on two CUDA streams over one grid, each with its own
+    outputs, give bit for bit the results of the same calls one after the
+    other on one stream (and the Ybus method's on a grid per stream)."""
+    import torch
+    from paper_2302_10736_gb300 import synth
+    w = synth.workload(1)
+    grid = pf.ybus_build(w)
+    grids_y = [grid, pf.ybus_build(w)]
+    rng = np.random.default_rng(77)
+    nb, nj, n = grid.nb, grid.nnzJ, 16
+    vm = [_d(w["vm"][0] * rng.uniform(0.98, 1.02, nb)) for _ in range(n)]
+    va = [_d(w["va"][0] + rng.normal(0, 0.05, nb)) for _ in range(n)]
+    out = lambda: [tuple(torch.full((m,), np.nan, dtype=torch.float64, device="cuda") for m in (nb, nb, nj))
+                   for _ in range(n)]
+    for method in ("elementwise", "ybus"):
+        fn = pf.jac_elementwise if method == "elementwise" else pf.jac_ybus
+        seq, par = out(), out()
+        for k in range(n):
+            g = grid if method == "elementwise" else grids_y[k % 2]
+            fn(g, vm[k], va[k], *seq[k])
+        torch.cuda.synchronize()
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        for k in range(n):
+            g = grid if method == "elementwise" else grids_y[k % 2]
+            fn(g, vm[k], va[k], *par[k], stream=streams[k % 2])
+        torch.cuda.synchronize()
+        pf.grid_check_error(grid)
+        for k in range(n):
+            for x, y in zip(seq[k], par[k]):
+                assert torch.equal(x, y), (method, k)
+
+
 def test_eval_host_matches_device(pf):
     from paper_2302_10736_gb300 import synth
     w = synth.workload(1)
