@@ -17,38 +17,51 @@
 //   * The columns grouped by height in the elimination tree: a column depends
 //     only on its descendants, which are all lower.
 //
-// Numeric phase (GPU, one cooperative launch per solve), left-looking Crout
-// factorization without pivoting in gather form: the analysis lists, for every
-// factor slot (i, j), the pairs of slots (L(i, k), U(k, j)) - and for the
-// mirrored U(j, i) the pairs (L(j, k), U(k, i)) - over the k below j that
-// update it, ascending, so every slot is one independent sum:
+// Numeric phase (GPU), left-looking Crout factorization without pivoting in
+// gather form: the analysis lists, for every factor slot (i, j), the pairs of
+// slots (L(i, k), U(k, j)) - and for the mirrored U(j, i) the pairs
+// (L(j, k), U(k, i)) - over the k below j that update it, ascending, so every
+// slot is one independent sum:
 //   d   = A(j, j) - sum_k L(j, k) U(k, j)          U(j, j) = d
 //   y_j = F_j    - sum_k L(j, k) y_k               (forward solve, fused)
 //   L(i, j) = (A(i, j) - sum_k L(i, k) U(k, j)) / d,  U(j, i) = A(j, i) - sum_k L(j, k) U(k, i)
 // then the backward solve x_j = (y_j - sum_i U(j, i) x_i) / U(j, j) from the
-// root down.  No barrier separates the levels: a column depends only on its
-// descendants in the elimination tree, so every work item waits for its
-// column's children to be finished (per-column counters, bounded waits) and
-// the work runs as soon as its inputs exist, along the tree's critical path
-// rather than level by level.  Work items are in level order and the warps
-// take them in that order from a shared counter, so the lowest unfinished item
-// has a warp and its inputs, and can always run (all CTAs are resident:
-// cooperative launch).  Wide levels give a warp to a column (a lane per
-// slot); on the upper levels (those with no more slots than the launch has
-// warps) every slot of a column gets a warp of its own (its lanes splitting
-// the slot's sum; each warp forms its column's pivot itself, the same way);
-// the backward solve gives a warp to a column,
-// which waits for its own factorization and then for its parent.  What an
-// item needs that no other item writes - its index lists and its own slots'
-// values of A and F - is loaded before its wait, and after the wait all its
-// loads of other columns' factor values are in flight at once (four terms per
-// lane), so a level of the tree costs one round trip to L2 for the values,
+// root down.
+//
+// The dynamic schedule (k_lu_solve, a cooperative launch).  No barrier
+// separates the levels: a column depends only on its descendants in the
+// elimination tree, so every work item waits for its column's children to be
+// finished (per-column counters, bounded waits) and the work runs as soon as
+// its inputs exist, along the tree's critical path rather than level by level.
+// Work items are in level order and the warps take them in that order from a
+// shared counter, so the lowest unfinished item has a warp and its inputs, and
+// can always run (all CTAs are resident: cooperative launch).  Wide levels
+// give a warp to a column (a lane per slot); on the upper levels (those with
+// no more slots than the launch has warps) every slot of a column gets a warp
+// of its own (its lanes splitting the slot's sum; each warp forms its
+// column's pivot itself, the same way); the backward solve gives a warp to a
+// column, which waits for its own factorization and then for its parent.
+// What an item needs that no other item writes - its index lists and its own
+// slots' values of A and F - is loaded before its wait, and after the wait all
+// its loads of other columns' factor values are in flight at once (four terms
+// per lane), so a level of the tree costs one round trip to L2 for the values,
 // one for the release of the results and one for the next item's acquire.
-// Every sum has a fixed order (sequential, or lane-strided partial sums
-// joined by a fixed shuffle tree): the results are bitwise repeatable.  Values written by other CTAs are read with
-// L1-bypassing loads after an acquire load of the counter that announced them.
-// A zero or non-finite pivot sets the grid's error word (no trap); a wait that
-// runs out (2 s) sets it to a time-out and ends the warp.
+// Values written by other CTAs are read with L1-bypassing loads after an
+// acquire load of the counter that announced them.
+//
+// The tail (k_lu_tail, one thread-block cluster).  At the top of the tree the
+// levels hold one or two columns each, and the schedule above would pay a
+// chain of round trips per column.  The longest run of final columns T0 .. n-1
+// on such levels (closed under the tree's ancestors) is factored as a dense
+// block in the cluster's shared memory; the dynamic launch computes only its
+// entries' terms over the columns outside it (parallel items, after the tail's
+// frontier is finished), and a second dynamic launch solves backward below it.
+// Without a tail (fewer than kLuTailMin such columns) one launch does it all.
+//
+// Every sum has a fixed order (sequential, or lane-strided partial sums joined
+// by a fixed shuffle tree): the results are bitwise repeatable.  A zero or
+// non-finite pivot sets the grid's error word (no trap); a wait that runs out
+// (2 s) sets it to a time-out and ends the warp.
 #include <algorithm>
 #include <set>
 #include <vector>
